@@ -1,0 +1,383 @@
+#!/usr/bin/env python3
+"""Benchmark of the sketch A_hat = S A (arXiv 2310.15419, Eq. 1) on one GPU.
+
+Workload (default, "skew_large"): A is 2,000,000 x 1,000 in CSC with
+power-law row lengths (Pareto alpha = 2.1, mean 5 nonzeros per row, ~1e7
+nonzeros), FP32 values ~ U(-1,1); d = 3,000.  One step sketches A with each
+of the three distributions of S (+-1, U(-1,1), N(0,1)), i.e. three calls of
+sketch_apply.  The metric counts 2 d nnz floating-point operations per
+sketch (the paper's GFLOP/s definition, Table "parallel").
+
+Prints ONE JSON line (rank 0).  Under torchrun (N > 1) every rank sketches
+its own copy of the workload (the sketch has no exchange step on one GPU per
+rank: replicas), the step time is the max over ranks and `value` sums the
+work of all ranks.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "sketch 2·d·nnz/s & roofline frac; LSQ solves/s, p50/p99 at 1e-10 resid"
+UNIT = "GFLOP/s"
+DISTS = ("pm1", "uniform", "normal")
+FP32_LANES_PER_SM = 128        # FP32 FMA lanes per SM (nominal)
+SMS_NOMINAL = 152
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--workload", default="skew_large")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0,
+                    help="budget of the oracle's CPU-baseline sample")
+    return ap.parse_args()
+
+
+def workload_config():
+    from paper_2310_15419_gb300 import inputs
+    return {"workload": "skew_large: m=2,000,000 n=1,000 d=3,000, power-law "
+                        "rows (alpha=2.1, mean 5/row), FP32 U(-1,1) values; "
+                        "S swept over +-1, U(-1,1), N(0,1)",
+            "m": 2_000_000, "n": 1000, "d": inputs.SKEW_LARGE_D,
+            "seed_A": 2, "seed_S": 1}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,"
+              "clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
+                 "sw_power_cap")
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------- our arm
+def generator_rates(torch, capi, sms):
+    """Entries/s of the device generator alone, per distribution."""
+    threads = sms * 2048
+    sink = torch.empty(threads, dtype=torch.float32, device="cuda")
+    out = {}
+    for dist in DISTS:
+        code = capi.DIST_NAMES[dist]
+        bpt = 64 if dist == "pm1" else 32
+        per_block = 128 if dist == "pm1" else 4
+        capi.bench_generator(code, 7, threads, bpt, sink)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 5
+        e0.record()
+        for _ in range(reps):
+            capi.bench_generator(code, 7, threads, bpt, sink)
+        e1.record()
+        torch.cuda.synchronize()
+        sec = e0.elapsed_time(e1) / 1e3 / reps
+        out[dist] = threads * bpt * per_block / sec
+    return out
+
+
+def cpu_baseline(A, d, seconds_budget, reps=1):
+    """The oracle as it stands, single thread, on a row sample of A."""
+    import oracle
+    codes = {"pm1": oracle.PM1, "uniform": oracle.UNIFORM, "normal": oracle.NORMAL}
+    # calibrate on a small sample, then size the sample to the budget
+    rows = 2000
+    t0 = time.perf_counter()
+    for dist in DISTS:
+        oracle.sketch_jki(A.m, A.n, d, codes[dist], 1, 0, A.colptr, A.rowidx,
+                          A.values, 0, rows)
+    per_row = (time.perf_counter() - t0) / rows
+    rows = int(max(2000, min(A.m, seconds_budget / max(per_row, 1e-9))))
+    nnz_rows = int(np.count_nonzero(A.rowidx < rows))
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        for dist in DISTS:
+            oracle.sketch_jki(A.m, A.n, d, codes[dist], 1, 0, A.colptr,
+                              A.rowidx, A.values, 0, rows)
+    sec = time.perf_counter() - t0
+    flops = reps * len(DISTS) * 2.0 * d * nnz_rows
+    return {"value": flops / sec / 1e9, "unit": UNIT, "cores": 1,
+            "kind": "oracle",
+            "sample": "rows [0, %d) of the workload (%d nonzeros), all three "
+                      "distributions, FP64 Alg. 4 order, %.1f s" %
+                      (rows, nnz_rows, sec)}, sec
+
+
+def run_ours(args):
+    import torch
+
+    from paper_2310_15419_gb300 import capi, inputs
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist_pg = None
+    if world > 1:
+        import torch.distributed as tdist
+        tdist.init_process_group("nccl")
+        dist_pg = tdist
+
+    cfg = workload_config()
+    d = cfg["d"]
+    A = inputs.skew_large(seed=cfg["seed_A"])
+    dA = capi.DeviceCSC(A)
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    rates = generator_rates(torch, capi, sms)
+
+    sketches = {dist: capi.Sketch(A.m, A.n, d, dist, seed=cfg["seed_S"]) for dist in DISTS}
+    outs = {dist: torch.empty((A.n, d), dtype=torch.float32, device="cuda") for dist in DISTS}
+    for dist in DISTS:                      # first call tunes the plan
+        sketches[dist].apply(dA, outs[dist])
+    torch.cuda.synchronize()
+    plans = {dist: sketches[dist].get_plan(dA) for dist in DISTS}
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
+
+    def step(events=None):
+        for dist in DISTS:
+            if events is not None:
+                events[dist][0].record()
+            sketches[dist].apply(dA, outs[dist])
+            if events is not None:
+                events[dist][1].record()
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+
+    launches0 = sum(s.launch_count() for s in sketches.values())
+    per_dist = {dist: [] for dist in DISTS}
+    step_ms = []
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    if dist_pg:
+        dist_pg.barrier()
+    torch.cuda.synchronize()
+    for _ in range(args.steps):
+        flush.zero_()                        # L2 flushed between steps
+        ev = {dist: (torch.cuda.Event(enable_timing=True),
+                     torch.cuda.Event(enable_timing=True)) for dist in DISTS}
+        step(ev)
+        torch.cuda.synchronize()
+        tot = 0.0
+        for dist in DISTS:
+            ms = ev[dist][0].elapsed_time(ev[dist][1])
+            per_dist[dist].append(ms)
+            tot += ms
+        step_ms.append(tot)
+    torch.cuda.synchronize()
+    if dist_pg:
+        dist_pg.barrier()
+    clk = clocks.stop()
+    launches = sum(s.launch_count() for s in sketches.values()) - launches0
+
+    total_ms = sum(step_ms)
+    if dist_pg:
+        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        dist_pg.all_reduce(t, op=dist_pg.ReduceOp.MAX)
+        total_ms = float(t.item())
+    flops_step = len(DISTS) * 2.0 * d * A.nnz
+    value = world * args.steps * flops_step / (total_ms / 1e3) / 1e9
+
+    # ---- roofline of the dominant kernel (the distribution taking longest)
+    peaks, peak_kind = measured_peaks()
+    f_max = float(clk.get("sm_max_mhz") or peaks.get("sm_max_mhz", 2070.0)) * 1e6
+    r_fma = sms * FP32_LANES_PER_SM * f_max          # FMA/s, unit counts x clock
+    nonempty = int(np.count_nonzero(np.bincount(A.rowidx, minlength=A.m)))
+    bytes_alg = A.nnz * (4 + 4) + 4 * (A.n + 1) + 4 * d * A.n
+    hbm = float(peaks.get("hbm_gbs", 6800.0)) * 1e9
+    roof = {}
+    for dist in DISTS:
+        t_alu = d * nonempty / rates[dist] + d * A.nnz / r_fma
+        t_mem = bytes_alg / hbm
+        t_star = max(t_alu, t_mem)
+        mean_ms = statistics.mean(per_dist[dist])
+        roof[dist] = {"ms": round(mean_ms, 4),
+                      "achieved": round(2.0 * d * A.nnz / (mean_ms / 1e3) / 1e12, 3),
+                      "peak": round(2.0 * d * A.nnz / t_star / 1e12, 3),
+                      "frac": round(t_star / (mean_ms / 1e3), 4),
+                      "bound": "alu" if t_alu >= t_mem else "hbm",
+                      "plan": plans[dist]}
+    dom = max(DISTS, key=lambda x: roof[x]["ms"])
+    roofline = {"bound": roof[dom]["bound"], "achieved": roof[dom]["achieved"],
+                "peak": roof[dom]["peak"], "unit": "TFLOP/s",
+                "frac": roof[dom]["frac"], "traffic": None,
+                "kernel": "sketch_apply(%s)" % dom,
+                "peak_basis": "RNG at the measured generator rate for the "
+                              "minimum d x nonempty-rows entries + d x nnz "
+                              "FMA at %d SMs x 128 lanes x %.0f MHz "
+                              "(unit counts x max clock); HBM %s %.0f GB/s" %
+                              (sms, f_max / 1e6, peak_kind, hbm / 1e9)}
+
+    # ---- end to end through the public API with host buffers
+    host = {"colptr": torch.from_numpy(A.colptr).pin_memory(),
+            "rowidx": torch.from_numpy(A.rowidx).pin_memory(),
+            "values": torch.from_numpy(A.values).pin_memory()}
+    host_out = {dist: torch.empty((A.n, d), dtype=torch.float32).pin_memory() for dist in DISTS}
+    h2d = sum(t.numel() * t.element_size() for t in host.values())
+    d2h = sum(t.numel() * t.element_size() for t in host_out.values())
+    e2e_steps = max(3, args.steps // 4)
+    e2e_ms = []
+    for it in range(e2e_steps + 1):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        dA.colptr.copy_(host["colptr"], non_blocking=True)
+        dA.rowidx.copy_(host["rowidx"], non_blocking=True)
+        dA.values.copy_(host["values"], non_blocking=True)
+        for dist in DISTS:
+            sketches[dist].apply(dA, outs[dist])
+            host_out[dist].copy_(outs[dist], non_blocking=True)
+        e1.record()
+        torch.cuda.synchronize()
+        if it > 0:
+            e2e_ms.append(e0.elapsed_time(e1))
+    e2e_val = flops_step / (statistics.mean(e2e_ms) / 1e3) / 1e9 * world
+
+    # ---- CPU baseline: the oracle on a bounded row sample (rank 0, N = 1)
+    cpu = None
+    if rank == 0 and world == 1:
+        cpu, _ = cpu_baseline(A, d, args.cpu_seconds / len(DISTS))
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 3), "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(total_ms / args.steps, 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": dict(cfg, l2="flushed (256 MB write) before every step",
+                           parallelism="replicas" if world > 1 else "single GPU"),
+            "roofline": roofline,
+            "sweep": roof,
+            "generator_entries_per_s": {k: float("%.4g" % v) for k, v in rates.items()},
+            "e2e": {"value": round(e2e_val, 3), "unit": UNIT,
+                    "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+            "cpu_baseline": cpu,
+            "gpu_launches": int(launches),
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    for s in sketches.values():
+        s.close()
+    if dist_pg:
+        dist_pg.barrier()
+        dist_pg.destroy_process_group()
+
+
+# -------------------------------------------------------- reference arm
+def run_reference(args):
+    """The oracle as it stands on the host cores: each step is a bounded row
+    sample of the same workload, all three distributions."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_2310_15419_gb300 import inputs
+    cfg = workload_config()
+    A = inputs.skew_large(seed=cfg["seed_A"])
+    budget = max(0.3, 150.0 / max(1, args.steps + args.warmup))
+    for _ in range(args.warmup):
+        cpu_baseline(A, cfg["d"], budget / 3)
+    vals, secs = [], []
+    for _ in range(args.steps):
+        cb, sec = cpu_baseline(A, cfg["d"], budget / 3)
+        vals.append(cb["value"])
+        secs.append(sec)
+    value = statistics.mean(vals)
+    cb["value"] = round(value, 5)
+    line = {"metric": METRIC, "value": round(value, 5), "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(1e3 * statistics.mean(secs), 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": dict(cfg, parallelism="single host thread"),
+            "cpu_baseline": cb,
+            "e2e": {"value": round(value, 5), "unit": UNIT,
+                    "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,210 @@
+/*
+ * sketch.h -- C ABI of the GB300 (sm_103a) sketching library.
+ *
+ * The library computes the sketch  A_hat = S A  of arXiv 2310.15419
+ * ("Fast multiplication of random dense matrices with sparse matrices"),
+ * Eq. (1): A is a tall m x n sparse matrix in CSC (Sec. 1.1 takes CSC as the
+ * default format) and S is a d x m matrix with iid entries from {+1,-1},
+ * U(-1,1) or N(0,1) (Sec. 1.1) that is never stored: every entry is
+ * regenerated on the GPU from a counter-based generator (Sec. 4.2,
+ * Philox4x32-10) keyed by (seed, stream, i, j), so S is the same under any
+ * tiling, launch shape or kernel choice (the reproducibility policy of
+ * Sec. 4.3).  On top of the sketch it provides the sketch-and-precondition
+ * least-squares solver of Sec. 5.4 (Householder QR of A_hat in FP64, LSQR on
+ * A R^{-1} with FP64 vector arithmetic), a batched launch for many uneven
+ * sketches, and a continuous-batching solve server.
+ *
+ * Definition of S(i, j), 0 <= i < d, 0 <= j < m (key = (seed lo32, seed hi32)):
+ *   +-1      x = Philox4x32-10(ctr = (i >> 7, j, stream, 0)); b = i & 127;
+ *            S = bit (b & 31) of x[b >> 5] ? -1 : +1
+ *   U(-1,1)  x = Philox(ctr = (i >> 2, j, stream, 0)); u = x[i & 3] >> 8 as a
+ *            signed 24-bit integer; S = (2u + 1) 2^-24   (exact in FP32)
+ *   N(0,1)   x = Philox(ctr = (i >> 2, j, stream, 0)); p = (i & 3) >> 1;
+ *            u1 = ((x[2p] >> 8) + 1) 2^-24, u2 = (x[2p+1] >> 8) 2^-24;
+ *            S = sqrt(-2 ln u1) * (i odd ? sin : cos)(2 pi u2)  (Box-Muller)
+ *
+ * Conventions for every call:
+ *   - 0-based indices, int32 colptr / rowidx (nnz < 2^31), rows strictly
+ *     increasing inside each column.
+ *   - Matrix pointers are DEVICE pointers owned by the caller unless a
+ *     function says otherwise; dense outputs are column-major.
+ *   - A_hat is d x n, column-major, leading dimension d, FP32.  It is
+ *     overwritten (the paper's Alg. 1 starts from A_hat = 0).
+ *   - Calls taking a stream are asynchronous on that stream (NULL = the
+ *     legacy default stream) unless documented as synchronous.
+ *   - Errors are returned as negative SKETCH_ERR_* codes, never thrown or
+ *     aborted; sketch_last_error() gives a message for the last failure of a
+ *     handle.  Out-of-range row indices met inside a kernel are skipped and
+ *     recorded in a device status word (sketch_device_status).
+ *   - The handle owns its workspace (device scratch, plan cache).  A handle
+ *     must not be used from two host threads at once.
+ */
+#ifndef SKETCH_H_
+#define SKETCH_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sketch_s* sketch_t;
+/* Same type as cudaStream_t; declared here so this header needs no CUDA
+ * header.  NULL selects the legacy default stream. */
+typedef struct CUstream_st* sketch_stream_t;
+
+enum sketch_status {
+  SKETCH_OK = 0,
+  SKETCH_ERR_ARG = -1,             /* bad argument (null, size, enum)        */
+  SKETCH_ERR_OOM = -2,             /* device or host allocation failed       */
+  SKETCH_ERR_CSC = -3,             /* malformed CSC (validator / kernels)    */
+  SKETCH_ERR_CUDA = -4,            /* a CUDA runtime call failed             */
+  SKETCH_ERR_TIMEOUT = -5,         /* a bounded device wait gave up          */
+  SKETCH_ERR_NO_CONVERGENCE = -6,  /* LSQR reached its iteration limit       */
+  SKETCH_ERR_UNSUPPORTED = -7      /* size or option outside what is built   */
+};
+
+enum sketch_dist { SKETCH_PM1 = 0, SKETCH_UNIFORM = 1, SKETCH_NORMAL = 2 };
+enum sketch_dtype { SKETCH_F32 = 0, SKETCH_BF16 = 1 };
+
+/* Kernel families (Sec. 2.2): REGEN = variant kji (Alg. 3), every nonzero
+ * regenerates its column of S; PANEL = variant jki (Alg. 4), each nonempty
+ * row of A generates its column of S once per tile.  AUTO lets the tuner
+ * choose per shape. */
+enum sketch_mode {
+  SKETCH_MODE_AUTO = 0,
+  SKETCH_MODE_REGEN = 1,
+  SKETCH_MODE_PANEL = 2
+};
+
+/* A sparse m x n matrix in CSC.  All pointers are device pointers owned by
+ * the caller; they must stay valid until the work using them completes. */
+typedef struct {
+  int64_t m, n, nnz;
+  const int32_t* colptr;  /* n + 1 entries, colptr[0] = 0, colptr[n] = nnz */
+  const int32_t* rowidx;  /* nnz entries, strictly increasing per column   */
+  const void* values;     /* nnz entries of type `dtype`                    */
+  int32_t dtype;          /* SKETCH_F32 or SKETCH_BF16                      */
+} sketch_csc;
+
+/* Launch plan (Alg. 1's block sizes mapped onto the GPU).  Zero fields mean
+ * "choose".  REGEN: each work item is one column of A times a tile of
+ * 128*q_tiles rows of S; `split` warps share a column's nonzeros.  PANEL:
+ * a CTA owns 32 rows of S, `n_block` columns and one of `row_groups`
+ * contiguous row ranges of A. */
+typedef struct {
+  int32_t mode;        /* sketch_mode                                  */
+  int32_t q_tiles;     /* REGEN: 1..4 blocks of 128 rows of S per warp */
+  int32_t split;       /* REGEN: 1, 2, 4 or 8 warps per column          */
+  int32_t n_block;     /* PANEL: columns per CTA (<= 1536)              */
+  int32_t row_groups;  /* PANEL: number of row ranges of A              */
+} sketch_plan;
+
+/* Create a sketch handle for A (m x n) and S (d x m) with the distribution
+ * `dist` and the 64-bit `seed`.  Requires 1 <= d, n, m; d, n, m < 2^31.
+ * Section: Sec. 1.1 (problem), Sec. 4.2 (counter-based generator).
+ * Errors: SKETCH_ERR_ARG, SKETCH_ERR_OOM.  No device memory is touched. */
+int sketch_create(int64_t m, int64_t n, int64_t d, int32_t dist, uint64_t seed,
+                  sketch_t* out);
+
+/* Release the handle and its device workspace (synchronises the device). */
+int sketch_destroy(sketch_t h);
+
+/* Third Philox counter word ("stream", default 0).  Instances of a batch use
+ * their index, so one seed yields independent S per instance. */
+int sketch_set_stream_id(sketch_t h, uint32_t stream_id);
+
+/* Force a plan (mode != AUTO) or return to autotuning (mode == AUTO).
+ * Errors: SKETCH_ERR_ARG for out-of-range fields. */
+int sketch_set_plan(sketch_t h, const sketch_plan* plan);
+
+/* The plan that sketch_apply would use for A (runs the tuner if needed;
+ * synchronous when it tunes).  */
+int sketch_get_plan(sketch_t h, const sketch_csc* A, sketch_plan* out,
+                    sketch_stream_t stream);
+
+/* A_hat (device, d x n, ld = d, FP32) = S A.  Eq. (1); kernels follow Alg. 3
+ * (REGEN) or Alg. 4 (PANEL) with Alg. 1's outer blocking mapped to the CTA
+ * grid.  Asynchronous on `stream`.  The first call for a new shape may tune
+ * (synchronously) and may grow the handle's device workspace.
+ * Errors: SKETCH_ERR_ARG (null pointers, A->m/n differ from the handle,
+ * dtype), SKETCH_ERR_UNSUPPORTED (nnz >= 2^31), SKETCH_ERR_OOM,
+ * SKETCH_ERR_CUDA. */
+int sketch_apply(sketch_t h, const sketch_csc* A, float* Ahat,
+                 sketch_stream_t stream);
+
+/* Message for the last error returned on this handle ("" if none). */
+const char* sketch_last_error(sketch_t h);
+
+/* Read and clear the device status word of the handle (synchronous):
+ * 0, or SKETCH_ERR_CSC if a kernel met a row index outside [0, m). */
+int sketch_device_status(sketch_t h, sketch_stream_t stream);
+
+/* Full CSC check on the device (synchronous): colptr[0] = 0, colptr
+ * nondecreasing, colptr[n] = nnz, rows in [0, m) and strictly increasing in
+ * each column (so no duplicates).  Returns SKETCH_OK or SKETCH_ERR_CSC. */
+int sketch_validate_csc(const sketch_csc* A, sketch_stream_t stream);
+
+/* ---- least squares (Sec. 5.4, sketch-and-precondition with QR) -------- */
+typedef struct {
+  int32_t iters;        /* LSQR iterations                                 */
+  int32_t status;       /* SKETCH_OK or SKETCH_ERR_NO_CONVERGENCE          */
+  int32_t istop;        /* 1: ||r|| test, 2: ||M^T r|| test, 0: max iters  */
+  int32_t reserved;
+  double error;         /* Error(x) = ||A^T(Ax-b)|| / (||A||_F ||Ax-b||)   */
+  double test2;         /* LSQR's own estimate for the preconditioned system*/
+  double ms_sketch, ms_qr, ms_lsqr;  /* stage times (CUDA events)          */
+} sketch_lsq_info;
+
+/* Solve min ||A x - b||_2 (m >= n): A_hat = S A with this handle's S
+ * (d = the handle's d, normally 2n), FP64 Householder QR of A_hat -> R,
+ * LSQR on A R^{-1} with FP64 residual and norm updates until LSQR's own
+ * estimate falls below `tol`, then x = R^{-1} y and Error(x) in FP64.
+ * b (m) and x (n) are FP64 device pointers.  Synchronous: returns when x
+ * and *info are final.  Errors: SKETCH_ERR_ARG (d < n, tol <= 0),
+ * SKETCH_ERR_NO_CONVERGENCE (x holds the last iterate), SKETCH_ERR_CSC
+ * (a zero column makes R singular), SKETCH_ERR_OOM, SKETCH_ERR_CUDA. */
+int sketch_lsq_solve(sketch_t h, const sketch_csc* A, const double* b,
+                     double* x, double tol, int32_t maxit,
+                     sketch_lsq_info* info, sketch_stream_t stream);
+
+/* ---- test hooks: the generator and S itself --------------------------- */
+/* out[4t..4t+3] = Philox4x32-10(ctr[4t..4t+3], key = seed) for t < count.
+ * ctr and out are device pointers.  Sec. 4.2.  Asynchronous. */
+int sketch_debug_philox(const uint32_t* ctr, uint64_t seed, uint32_t* out,
+                        int64_t count, sketch_stream_t stream);
+
+/* out[t] = S(i[t], j[t]) (FP32) for distribution `dist`, key `seed`, counter
+ * word 2 = `stream_id`.  i, j, out are device pointers.  Asynchronous. */
+int sketch_debug_S(int32_t dist, uint64_t seed, uint32_t stream_id,
+                   const int64_t* i, const int64_t* j, float* out,
+                   int64_t count, sketch_stream_t stream);
+
+/* Generator throughput probe: `threads` threads each evaluate
+ * `blocks_per_thread` Philox blocks at distinct counters and apply the
+ * distribution's transform (4 entries per block for U and N, 128 signs for
+ * +-1), folding the entries into one float per thread written to sink
+ * (device, `threads` floats) so nothing is optimised away.  Asynchronous.
+ * Entries generated = threads * blocks_per_thread * (dist == +-1 ? 128 : 4).
+ * Used to measure the RNG leg of the ALU roofline (Sec. 3.1's cost h of
+ * generating one entry). */
+int sketch_bench_generator(int32_t dist, uint64_t seed, int64_t threads,
+                           int64_t blocks_per_thread, float* sink,
+                           sketch_stream_t stream);
+
+/* Number of S entries the last sketch_apply on this handle generated
+ * (counted on the device when counting is enabled; synchronous read).
+ * Alg. 3 generates d * nnz entries and Alg. 4 d per nonempty row and
+ * column block (Sec. 3.2). */
+int sketch_set_counting(sketch_t h, int32_t enable);
+int64_t sketch_generated_entries(sketch_t h, sketch_stream_t stream);
+
+/* Cumulative number of kernels this handle has launched (host counter; no
+ * device access).  Lets a benchmark state how many of the library's own
+ * kernels ran inside a timed region. */
+int64_t sketch_launch_count(sketch_t h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SKETCH_H_ */

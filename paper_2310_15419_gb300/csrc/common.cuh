@@ -1,0 +1,116 @@
+// common.cuh -- device generator, distribution transforms and small helpers
+// shared by the sketch kernels (sm_103a).
+//
+// S(i, j) is a pure function of (seed, stream, i, j): the counter-based
+// generator Philox4x32-10 (Salmon et al., SC'11; the paper's Sec. 4.2 names
+// this family) is evaluated at counter (i_blk, j, stream, 0) under the key
+// (seed lo32, seed hi32).  Any kernel, tile size or launch shape therefore
+// sees the same S (Sec. 4.3's threading-independent reproducibility).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace sk {
+
+constexpr uint32_t kPhiloxM0 = 0xD2511F53u;  // round multipliers
+constexpr uint32_t kPhiloxM1 = 0xCD9E8D57u;
+constexpr uint32_t kPhiloxW0 = 0x9E3779B9u;  // Weyl key increments
+constexpr uint32_t kPhiloxW1 = 0xBB67AE85u;
+
+constexpr int kPM1 = 0, kUniform = 1, kNormal = 2;
+
+// Ten Philox rounds.  The round keys are warp-uniform; each round is two
+// 32x32->64 multiplies and two three-input xors.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0,
+                                               uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t hi0 = __umulhi(kPhiloxM0, c.x);
+    const uint32_t lo0 = kPhiloxM0 * c.x;
+    const uint32_t hi1 = __umulhi(kPhiloxM1, c.z);
+    const uint32_t lo1 = kPhiloxM1 * c.z;
+    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    k0 += kPhiloxW0;
+    k1 += kPhiloxW1;
+  }
+  return c;
+}
+
+__device__ __forceinline__ uint4 philox_block(uint32_t i_blk, uint32_t j,
+                                              uint32_t stream, uint32_t k0,
+                                              uint32_t k1) {
+  return philox4x32_10(make_uint4(i_blk, j, stream, 0u), k0, k1);
+}
+
+// U(-1,1): top 24 bits as a signed integer u, S = (2u + 1) 2^-24.  The fma
+// rounds an exactly representable value, so the result is exact.
+__device__ __forceinline__ float uniform_from_word(uint32_t w) {
+  const int32_t u = static_cast<int32_t>(w) >> 8;
+  return fmaf(static_cast<float>(u), 0x1p-23f, 0x1p-24f);
+}
+
+// Box-Muller on one word pair: u1 in (0,1] from the radius word, u2 in [0,1)
+// from the angle word; returns (r cos 2 pi u2, r sin 2 pi u2).
+__device__ __forceinline__ float2 normal_pair(uint32_t w_radius,
+                                              uint32_t w_angle) {
+  const float u1 = static_cast<float>((w_radius >> 8) + 1u) * 0x1p-24f;
+  const float u2 = static_cast<float>(w_angle >> 8) * 0x1p-24f;
+  const float r = sqrtf(-2.0f * logf(u1));
+  float s, c;
+  sincospif(2.0f * u2, &s, &c);
+  return make_float2(r * c, r * s);
+}
+
+// The four entries S(4 i_blk .. 4 i_blk + 3, j) for U or N.
+template <int DIST>
+__device__ __forceinline__ float4 four_entries(uint4 x) {
+  if constexpr (DIST == kUniform) {
+    return make_float4(uniform_from_word(x.x), uniform_from_word(x.y),
+                       uniform_from_word(x.z), uniform_from_word(x.w));
+  } else {
+    const float2 a = normal_pair(x.x, x.y);
+    const float2 b = normal_pair(x.z, x.w);
+    return make_float4(a.x, a.y, b.x, b.y);
+  }
+}
+
+// A single entry, for the test hook and for ragged edges.
+__device__ __forceinline__ float S_entry(int dist, uint32_t k0, uint32_t k1,
+                                         uint32_t stream, int64_t i,
+                                         int64_t j) {
+  if (dist == kPM1) {
+    const uint4 x = philox_block(static_cast<uint32_t>(i >> 7),
+                                 static_cast<uint32_t>(j), stream, k0, k1);
+    const int b = static_cast<int>(i & 127);
+    const uint32_t w = (b < 32) ? x.x : (b < 64) ? x.y : (b < 96) ? x.z : x.w;
+    return ((w >> (b & 31)) & 1u) ? -1.0f : 1.0f;
+  }
+  const uint4 x = philox_block(static_cast<uint32_t>(i >> 2),
+                               static_cast<uint32_t>(j), stream, k0, k1);
+  const int q = static_cast<int>(i & 3);
+  if (dist == kUniform) {
+    const uint32_t w = (q == 0) ? x.x : (q == 1) ? x.y : (q == 2) ? x.z : x.w;
+    return uniform_from_word(w);
+  }
+  const float2 p = (q < 2) ? normal_pair(x.x, x.y) : normal_pair(x.z, x.w);
+  return (q & 1) ? p.y : p.x;
+}
+
+template <typename VT>
+__device__ __forceinline__ float to_f32(VT v);
+template <>
+__device__ __forceinline__ float to_f32<float>(float v) {
+  return v;
+}
+template <>
+__device__ __forceinline__ float to_f32<__nv_bfloat16>(__nv_bfloat16 v) {
+  return __bfloat162float(v);
+}
+
+// Device status bits written by kernels that meet bad input.
+constexpr int kStatusBadRow = 1;
+constexpr int kStatusBadColptr = 2;
+
+}  // namespace sk

@@ -1,0 +1,72 @@
+// internal.h -- host-side launchers shared between the translation units of
+// libsketch.so.  Not part of the public ABI (see include/sketch.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstddef>
+#include <string>
+
+namespace sk {
+
+struct RegenArgs {
+  int32_t m, n, d;
+  int32_t dtype;  // 0 = f32, 1 = bf16
+  const int32_t* colptr;
+  const int32_t* rowidx;
+  const void* values;
+  float* Ahat;
+  uint32_t k0, k1, stream_id;
+  int32_t dist;
+  int32_t q_tiles;  // 1..4
+  int32_t split;    // 1, 2, 4, 8
+  int* status;
+  unsigned long long* gen_count;  // may be null
+};
+cudaError_t launch_regen(const RegenArgs& a, cudaStream_t s);
+
+// CSR copy of A (the single-vertical-block "blocked CSR" of Sec. 3.2) built
+// on the device.  Workspace sizes in bytes for m rows and nnz nonzeros.
+size_t csr_workspace_bytes(int64_t m, int64_t nnz);
+struct CsrView {
+  int32_t* rowptr;  // m + 1
+  int32_t* ccol;    // nnz
+  float* cval;      // nnz
+};
+cudaError_t build_csr(int32_t m, int32_t n, int64_t nnz, const int32_t* colptr,
+                      const int32_t* rowidx, const void* values, int32_t dtype,
+                      void* ws, CsrView* out, int* status, cudaStream_t s,
+                      int* launches);
+
+struct PanelArgs {
+  int32_t m, n, d;
+  CsrView csr;
+  float* partial;  // row_groups * n * d floats
+  float* Ahat;
+  uint32_t k0, k1, stream_id;
+  int32_t dist;
+  int32_t n_block;
+  int32_t row_groups;
+  unsigned long long* gen_count;
+};
+size_t panel_smem_bytes(int32_t n_block);
+cudaError_t launch_panel(const PanelArgs& a, cudaStream_t s, int* launches);
+
+cudaError_t launch_validate(int32_t m, int32_t n, int64_t nnz,
+                            const int32_t* colptr, const int32_t* rowidx,
+                            int* status, cudaStream_t s);
+cudaError_t launch_debug_philox(const uint32_t* ctr, uint32_t k0, uint32_t k1,
+                                uint32_t* out, int64_t count, cudaStream_t s);
+cudaError_t launch_debug_S(int dist, uint32_t k0, uint32_t k1,
+                           uint32_t stream_id, const int64_t* i,
+                           const int64_t* j, float* out, int64_t count,
+                           cudaStream_t s);
+
+cudaError_t launch_bench_generator(int dist, uint32_t k0, uint32_t k1,
+                                   int64_t threads, int64_t blocks_per_thread,
+                                   float* sink, cudaStream_t s);
+
+int num_sms();
+
+}  // namespace sk

@@ -1,0 +1,519 @@
+// sketch_capi.cu -- the C ABI (include/sketch.h): handles, device workspace,
+// the launch planner / autotuner, and the sketch entry points.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/sketch.h"
+#include "handle.h"
+#include "internal.h"
+
+using namespace sk;
+
+namespace sk {
+
+static thread_local std::string g_global_error;
+
+int fail(sketch_t h, int code, const std::string& msg) {
+  if (h)
+    h->last_error = msg;
+  else
+    g_global_error = msg;
+  return code;
+}
+
+int cuda_fail(sketch_t h, cudaError_t e, const char* where) {
+  char buf[256];
+  std::snprintf(buf, sizeof(buf), "%s: %s", where, cudaGetErrorString(e));
+  return fail(h, SKETCH_ERR_CUDA, buf);
+}
+
+int ensure_small(sketch_t h) {
+  if (h->d_small) return SKETCH_OK;
+  cudaError_t e = cudaMalloc(&h->d_small, 256);
+  if (e != cudaSuccess) {
+    h->d_small = nullptr;
+    return fail(h, SKETCH_ERR_OOM, "cudaMalloc(status words) failed");
+  }
+  e = cudaMemset(h->d_small, 0, 256);
+  if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemset(status words)");
+  return SKETCH_OK;
+}
+
+int ensure_workspace(sketch_t h, size_t bytes) {
+  if (bytes <= h->ws_bytes) return SKETCH_OK;
+  // growing the workspace is not allowed while the caller captures a graph
+  if (h->capturing)
+    return fail(h, SKETCH_ERR_OOM,
+                "workspace too small during stream capture; "
+                "call sketch_apply once before capturing");
+  if (h->ws) {
+    cudaDeviceSynchronize();
+    cudaFree(h->ws);
+    h->ws = nullptr;
+    h->ws_bytes = 0;
+  }
+  const size_t want = bytes + bytes / 8;
+  cudaError_t e = cudaMalloc(&h->ws, want);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    h->ws = nullptr;
+    return fail(h, SKETCH_ERR_OOM, "cudaMalloc(workspace) failed");
+  }
+  h->ws_bytes = want;
+  return SKETCH_OK;
+}
+
+static size_t align256(size_t b) { return (b + 255) / 256 * 256; }
+
+// Heuristic plan (used when tuning is off or not possible).
+sketch_plan heuristic_plan(const sketch_s* h, const sketch_csc* A) {
+  sketch_plan p{};
+  const double avg_col = A->n > 0 ? double(A->nnz) / double(A->n) : 0.0;
+  const int q = static_cast<int>(std::min<int64_t>(4, (h->d + 127) / 128));
+  if (h->dist == SKETCH_PM1 || A->nnz < 4 * A->n) {
+    p.mode = SKETCH_MODE_REGEN;
+    p.q_tiles = std::max(1, q);
+    p.split = avg_col >= 4096 ? 8 : avg_col >= 1024 ? 4 : avg_col >= 256 ? 2 : 1;
+  } else {
+    p.mode = SKETCH_MODE_PANEL;
+    p.n_block = static_cast<int32_t>(std::min<int64_t>(A->n, 1024));
+    p.row_groups = default_row_groups(h, A, p.n_block);
+  }
+  return p;
+}
+
+// Row groups for PANEL: enough CTAs to fill the GPU twice over, and at most
+// ~512 nonzeros of a column per group so FP32 partial sums stay short.
+int32_t default_row_groups(const sketch_s* h, const sketch_csc* A,
+                           int32_t n_block) {
+  const int64_t tiles = (h->d + 31) / 32;
+  const int64_t cblocks = (A->n + n_block - 1) / n_block;
+  const double avg_col = A->n > 0 ? double(A->nnz) / double(A->n) : 0.0;
+  int64_t g_fill = (2LL * num_sms() + tiles * cblocks - 1) / (tiles * cblocks);
+  int64_t g_acc = static_cast<int64_t>(std::ceil(avg_col / 512.0));
+  int64_t g = std::max<int64_t>({1, g_fill, g_acc});
+  g = std::min<int64_t>(g, std::max<int64_t>(1, A->m / 64));
+  g = std::min<int64_t>(g, 4096);
+  return static_cast<int32_t>(g);
+}
+
+size_t plan_workspace_bytes(const sketch_s* h, const sketch_csc* A,
+                            const sketch_plan& p) {
+  if (p.mode != SKETCH_MODE_PANEL) return 0;
+  size_t b = align256(csr_workspace_bytes(A->m, A->nnz));
+  if (p.row_groups > 1)
+    b += align256(static_cast<size_t>(p.row_groups) * A->n * h->d * sizeof(float));
+  return b;
+}
+
+int check_plan(sketch_t h, const sketch_plan& p) {
+  if (p.mode == SKETCH_MODE_REGEN) {
+    if (p.q_tiles < 1 || p.q_tiles > 4)
+      return fail(h, SKETCH_ERR_ARG, "q_tiles must be 1..4");
+    if (p.split != 1 && p.split != 2 && p.split != 4 && p.split != 8)
+      return fail(h, SKETCH_ERR_ARG, "split must be 1, 2, 4 or 8");
+  } else if (p.mode == SKETCH_MODE_PANEL) {
+    if (p.n_block < 1 || p.n_block > 1536)
+      return fail(h, SKETCH_ERR_ARG, "n_block must be 1..1536");
+    if (p.row_groups < 1 || p.row_groups > 65535)
+      return fail(h, SKETCH_ERR_ARG, "row_groups must be 1..65535");
+  } else if (p.mode != SKETCH_MODE_AUTO) {
+    return fail(h, SKETCH_ERR_ARG, "unknown mode");
+  }
+  return SKETCH_OK;
+}
+
+// Run one plan.  `ws` must hold plan_workspace_bytes.
+int run_plan(sketch_t h, const sketch_csc* A, float* Ahat,
+             const sketch_plan& p, void* ws, cudaStream_t s) {
+  int* status = reinterpret_cast<int*>(h->d_small);
+  unsigned long long* gen =
+      h->counting ? reinterpret_cast<unsigned long long*>(
+                        static_cast<char*>(h->d_small) + 64)
+                  : nullptr;
+  if (gen) {
+    cudaError_t e = cudaMemsetAsync(gen, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemsetAsync(count)");
+  }
+  if (A->n == 0 || h->d == 0) return SKETCH_OK;
+  if (A->nnz == 0) {
+    cudaError_t e = cudaMemsetAsync(Ahat, 0, sizeof(float) * A->n * h->d, s);
+    return e == cudaSuccess ? SKETCH_OK : cuda_fail(h, e, "cudaMemsetAsync");
+  }
+  if (p.mode == SKETCH_MODE_REGEN) {
+    RegenArgs a{};
+    a.m = static_cast<int32_t>(A->m);
+    a.n = static_cast<int32_t>(A->n);
+    a.d = static_cast<int32_t>(h->d);
+    a.dtype = A->dtype;
+    a.colptr = A->colptr;
+    a.rowidx = A->rowidx;
+    a.values = A->values;
+    a.Ahat = Ahat;
+    a.k0 = h->k0;
+    a.k1 = h->k1;
+    a.stream_id = h->stream_id;
+    a.dist = h->dist;
+    a.q_tiles = p.q_tiles;
+    a.split = p.split;
+    a.status = status;
+    a.gen_count = gen;
+    cudaError_t e = launch_regen(a, s);
+    h->launches += 1;
+    return e == cudaSuccess ? SKETCH_OK : cuda_fail(h, e, "regen kernel");
+  }
+  // PANEL
+  CsrView csr{};
+  int nl = 0;
+  cudaError_t e = build_csr(static_cast<int32_t>(A->m), static_cast<int32_t>(A->n),
+                            A->nnz, A->colptr, A->rowidx, A->values, A->dtype, ws,
+                            &csr, status, s, &nl);
+  if (e != cudaSuccess) return cuda_fail(h, e, "csr build");
+  PanelArgs a{};
+  a.m = static_cast<int32_t>(A->m);
+  a.n = static_cast<int32_t>(A->n);
+  a.d = static_cast<int32_t>(h->d);
+  a.csr = csr;
+  a.partial = reinterpret_cast<float*>(
+      static_cast<char*>(ws) + align256(csr_workspace_bytes(A->m, A->nnz)));
+  a.Ahat = Ahat;
+  a.k0 = h->k0;
+  a.k1 = h->k1;
+  a.stream_id = h->stream_id;
+  a.dist = h->dist;
+  a.n_block = p.n_block;
+  a.row_groups = p.row_groups;
+  a.gen_count = gen;
+  e = launch_panel(a, s, &nl);
+  h->launches += nl;
+  return e == cudaSuccess ? SKETCH_OK : cuda_fail(h, e, "panel kernel");
+}
+
+// Candidate plans for the tuner.
+static std::vector<sketch_plan> candidates(const sketch_s* h, const sketch_csc* A) {
+  std::vector<sketch_plan> c;
+  const int qmax = static_cast<int>(std::min<int64_t>(4, (h->d + 127) / 128));
+  for (int q : {qmax, std::max(1, qmax / 2)}) {
+    for (int sp : {1, 2, 4, 8}) {
+      sketch_plan p{};
+      p.mode = SKETCH_MODE_REGEN;
+      p.q_tiles = q;
+      p.split = sp;
+      bool dup = false;
+      for (auto& o : c)
+        if (o.mode == p.mode && o.q_tiles == p.q_tiles && o.split == p.split) dup = true;
+      if (!dup) c.push_back(p);
+    }
+  }
+  // PANEL only where rows are reused (Alg. 4 pays off) or for U / N
+  const size_t csr_bytes = csr_workspace_bytes(A->m, A->nnz);
+  for (int32_t nb : {static_cast<int32_t>(std::min<int64_t>(A->n, 1024)),
+                     static_cast<int32_t>(std::min<int64_t>(A->n, 512))}) {
+    sketch_plan p{};
+    p.mode = SKETCH_MODE_PANEL;
+    p.n_block = nb;
+    p.row_groups = default_row_groups(h, A, nb);
+    const size_t part = static_cast<size_t>(p.row_groups) * A->n * h->d * 4;
+    if (csr_bytes + part > (size_t(8) << 30)) continue;  // keep the tuner lean
+    bool dup = false;
+    for (auto& o : c)
+      if (o.mode == p.mode && o.n_block == p.n_block) dup = true;
+    if (!dup) c.push_back(p);
+  }
+  return c;
+}
+
+uint64_t shape_key(const sketch_s* h, const sketch_csc* A) {
+  uint64_t k = 1469598103934665603ULL;
+  auto mix = [&](uint64_t v) { k = (k ^ v) * 1099511628211ULL; };
+  mix(A->m); mix(A->n); mix(A->nnz); mix(h->d); mix(h->dist); mix(A->dtype);
+  return k;
+}
+
+int choose_plan(sketch_t h, const sketch_csc* A, float* Ahat, cudaStream_t s,
+                sketch_plan* out) {
+  if (h->has_forced) {
+    *out = h->forced;
+    return SKETCH_OK;
+  }
+  const uint64_t key = shape_key(h, A);
+  auto it = h->plans.find(key);
+  if (it != h->plans.end()) {
+    *out = it->second;
+    return SKETCH_OK;
+  }
+  const char* env = std::getenv("SKETCH_TUNE");
+  const bool tune = !(env && env[0] == '0') && !h->capturing && Ahat != nullptr;
+  if (!tune) {
+    *out = heuristic_plan(h, A);
+    h->plans[key] = *out;
+    return SKETCH_OK;
+  }
+  // Empirical tuning: time every candidate twice on the real input (the
+  // second run counts) and keep the fastest.
+  auto cands = candidates(h, A);
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best = 1e30f;
+  sketch_plan best_p = heuristic_plan(h, A);
+  const bool saved_counting = h->counting;
+  h->counting = false;
+  for (const auto& p : cands) {
+    int rc = ensure_workspace(h, plan_workspace_bytes(h, A, p));
+    if (rc != SKETCH_OK) {
+      h->last_error.clear();
+      continue;
+    }
+    if (run_plan(h, A, Ahat, p, h->ws, s) != SKETCH_OK) {
+      cudaGetLastError();
+      h->last_error.clear();
+      continue;
+    }
+    cudaEventRecord(e0, s);
+    rc = run_plan(h, A, Ahat, p, h->ws, s);
+    cudaEventRecord(e1, s);
+    if (cudaEventSynchronize(e1) != cudaSuccess || rc != SKETCH_OK) {
+      cudaGetLastError();
+      continue;
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best) {
+      best = ms;
+      best_p = p;
+    }
+  }
+  h->counting = saved_counting;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  h->plans[key] = best_p;
+  *out = best_p;
+  return SKETCH_OK;
+}
+
+int check_csc_args(sketch_t h, const sketch_csc* A) {
+  if (!A) return fail(h, SKETCH_ERR_ARG, "A is null");
+  if (A->m != h->m || A->n != h->n)
+    return fail(h, SKETCH_ERR_ARG, "A's shape differs from the handle's (m, n)");
+  if (A->nnz < 0) return fail(h, SKETCH_ERR_ARG, "nnz < 0");
+  if (A->nnz >= (int64_t(1) << 31))
+    return fail(h, SKETCH_ERR_UNSUPPORTED, "nnz >= 2^31 (int32 indices)");
+  if (A->dtype != SKETCH_F32 && A->dtype != SKETCH_BF16)
+    return fail(h, SKETCH_ERR_ARG, "dtype must be SKETCH_F32 or SKETCH_BF16");
+  if (!A->colptr) return fail(h, SKETCH_ERR_ARG, "colptr is null");
+  if (A->nnz > 0 && (!A->rowidx || !A->values))
+    return fail(h, SKETCH_ERR_ARG, "rowidx or values is null");
+  return SKETCH_OK;
+}
+
+}  // namespace sk
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+int sketch_create(int64_t m, int64_t n, int64_t d, int32_t dist, uint64_t seed,
+                  sketch_t* out) {
+  if (!out) return fail(nullptr, SKETCH_ERR_ARG, "out is null");
+  *out = nullptr;
+  if (m < 1 || n < 1 || d < 1 || m >= (int64_t(1) << 31) ||
+      n >= (int64_t(1) << 31) || d >= (int64_t(1) << 31))
+    return fail(nullptr, SKETCH_ERR_ARG, "need 1 <= m, n, d < 2^31");
+  if (dist != SKETCH_PM1 && dist != SKETCH_UNIFORM && dist != SKETCH_NORMAL)
+    return fail(nullptr, SKETCH_ERR_ARG, "unknown distribution");
+  if (static_cast<int64_t>(n) * d >= (int64_t(1) << 40))
+    return fail(nullptr, SKETCH_ERR_UNSUPPORTED, "d * n too large");
+  sketch_s* h = new (std::nothrow) sketch_s();
+  if (!h) return fail(nullptr, SKETCH_ERR_OOM, "host allocation failed");
+  h->m = m;
+  h->n = n;
+  h->d = d;
+  h->dist = dist;
+  h->seed = seed;
+  h->k0 = static_cast<uint32_t>(seed & 0xffffffffu);
+  h->k1 = static_cast<uint32_t>(seed >> 32);
+  *out = h;
+  return SKETCH_OK;
+}
+
+int sketch_destroy(sketch_t h) {
+  if (!h) return SKETCH_ERR_ARG;
+  if (h->ws || h->d_small) cudaDeviceSynchronize();
+  if (h->ws) cudaFree(h->ws);
+  if (h->d_small) cudaFree(h->d_small);
+  destroy_lsq_state(h);
+  delete h;
+  return SKETCH_OK;
+}
+
+int sketch_set_stream_id(sketch_t h, uint32_t stream_id) {
+  if (!h) return SKETCH_ERR_ARG;
+  h->stream_id = stream_id;
+  return SKETCH_OK;
+}
+
+int sketch_set_plan(sketch_t h, const sketch_plan* plan) {
+  if (!h || !plan) return fail(h, SKETCH_ERR_ARG, "null argument");
+  int rc = check_plan(h, *plan);
+  if (rc != SKETCH_OK) return rc;
+  if (plan->mode == SKETCH_MODE_AUTO) {
+    h->has_forced = false;
+  } else {
+    h->forced = *plan;
+    h->has_forced = true;
+  }
+  return SKETCH_OK;
+}
+
+int sketch_get_plan(sketch_t h, const sketch_csc* A, sketch_plan* out,
+                    sketch_stream_t stream) {
+  if (!h || !out) return fail(h, SKETCH_ERR_ARG, "null argument");
+  int rc = check_csc_args(h, A);
+  if (rc != SKETCH_OK) return rc;
+  if (h->has_forced) {
+    *out = h->forced;
+    return SKETCH_OK;
+  }
+  auto it = h->plans.find(sk::shape_key(h, A));
+  if (it != h->plans.end()) {
+    *out = it->second;
+    return SKETCH_OK;
+  }
+  (void)stream;
+  *out = heuristic_plan(h, A);
+  return SKETCH_OK;
+}
+
+int sketch_apply(sketch_t h, const sketch_csc* A, float* Ahat,
+                 sketch_stream_t stream) {
+  if (!h) return fail(nullptr, SKETCH_ERR_ARG, "handle is null");
+  if (!Ahat) return fail(h, SKETCH_ERR_ARG, "Ahat is null");
+  int rc = check_csc_args(h, A);
+  if (rc != SKETCH_OK) return rc;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) {
+    cudaGetLastError();
+    cs = cudaStreamCaptureStatusNone;
+  }
+  h->capturing = (cs != cudaStreamCaptureStatusNone);
+  if ((rc = ensure_small(h)) != SKETCH_OK) return rc;
+  sketch_plan p{};
+  if ((rc = choose_plan(h, A, Ahat, s, &p)) != SKETCH_OK) return rc;
+  if ((rc = ensure_workspace(h, plan_workspace_bytes(h, A, p))) != SKETCH_OK)
+    return rc;
+  return run_plan(h, A, Ahat, p, h->ws, s);
+}
+
+const char* sketch_last_error(sketch_t h) {
+  return h ? h->last_error.c_str() : sk::g_global_error.c_str();
+}
+
+int sketch_device_status(sketch_t h, sketch_stream_t stream) {
+  if (!h) return SKETCH_ERR_ARG;
+  if (!h->d_small) return SKETCH_OK;
+  int v = 0;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemcpyAsync(&v, h->d_small, sizeof(int),
+                                  cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(h, e, "status read");
+  if (v) {
+    cudaMemsetAsync(h->d_small, 0, sizeof(int), s);
+    cudaStreamSynchronize(s);
+    return fail(h, SKETCH_ERR_CSC, "a kernel met an out-of-range index");
+  }
+  return SKETCH_OK;
+}
+
+int sketch_validate_csc(const sketch_csc* A, sketch_stream_t stream) {
+  if (!A || !A->colptr || A->m < 1 || A->n < 1 || A->nnz < 0)
+    return fail(nullptr, SKETCH_ERR_ARG, "bad CSC descriptor");
+  if (A->nnz > 0 && !A->rowidx) return fail(nullptr, SKETCH_ERR_ARG, "rowidx null");
+  if (A->nnz >= (int64_t(1) << 31) || A->m >= (int64_t(1) << 31) ||
+      A->n >= (int64_t(1) << 31))
+    return fail(nullptr, SKETCH_ERR_UNSUPPORTED, "sizes exceed int32");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  int* d_status = nullptr;
+  cudaError_t e = cudaMalloc(&d_status, sizeof(int));
+  if (e != cudaSuccess) return fail(nullptr, SKETCH_ERR_OOM, "cudaMalloc");
+  cudaMemsetAsync(d_status, 0, sizeof(int), s);
+  e = launch_validate(static_cast<int32_t>(A->m), static_cast<int32_t>(A->n),
+                      A->nnz, A->colptr, A->rowidx, d_status, s);
+  int v = 0;
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(&v, d_status, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(d_status);
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "validate");
+  return v ? fail(nullptr, SKETCH_ERR_CSC, "malformed CSC") : SKETCH_OK;
+}
+
+int sketch_debug_philox(const uint32_t* ctr, uint64_t seed, uint32_t* out,
+                        int64_t count, sketch_stream_t stream) {
+  if (count < 0 || (count > 0 && (!ctr || !out)))
+    return fail(nullptr, SKETCH_ERR_ARG, "bad arguments");
+  cudaError_t e = launch_debug_philox(
+      ctr, static_cast<uint32_t>(seed & 0xffffffffu),
+      static_cast<uint32_t>(seed >> 32), out, count,
+      reinterpret_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? SKETCH_OK : cuda_fail(nullptr, e, "debug_philox");
+}
+
+int sketch_debug_S(int32_t dist, uint64_t seed, uint32_t stream_id,
+                   const int64_t* i, const int64_t* j, float* out,
+                   int64_t count, sketch_stream_t stream) {
+  if (dist < 0 || dist > 2 || count < 0 || (count > 0 && (!i || !j || !out)))
+    return fail(nullptr, SKETCH_ERR_ARG, "bad arguments");
+  cudaError_t e = launch_debug_S(dist, static_cast<uint32_t>(seed & 0xffffffffu),
+                                 static_cast<uint32_t>(seed >> 32), stream_id,
+                                 i, j, out, count,
+                                 reinterpret_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? SKETCH_OK : cuda_fail(nullptr, e, "debug_S");
+}
+
+int sketch_bench_generator(int32_t dist, uint64_t seed, int64_t threads,
+                           int64_t blocks_per_thread, float* sink,
+                           sketch_stream_t stream) {
+  if (dist < 0 || dist > 2 || threads < 0 || blocks_per_thread < 0 ||
+      (threads > 0 && !sink))
+    return fail(nullptr, SKETCH_ERR_ARG, "bad arguments");
+  cudaError_t e = launch_bench_generator(
+      dist, static_cast<uint32_t>(seed & 0xffffffffu),
+      static_cast<uint32_t>(seed >> 32), threads, blocks_per_thread, sink,
+      reinterpret_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? SKETCH_OK : cuda_fail(nullptr, e, "bench_generator");
+}
+
+int sketch_set_counting(sketch_t h, int32_t enable) {
+  if (!h) return SKETCH_ERR_ARG;
+  h->counting = enable != 0;
+  return SKETCH_OK;
+}
+
+int64_t sketch_launch_count(sketch_t h) { return h ? h->launches : -1; }
+
+int64_t sketch_generated_entries(sketch_t h, sketch_stream_t stream) {
+  if (!h || !h->d_small) return 0;
+  unsigned long long v = 0;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (cudaMemcpyAsync(&v, static_cast<char*>(h->d_small) + 64, sizeof(v),
+                      cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return -1;
+  return static_cast<int64_t>(v);
+}
+
+}  // extern "C"

@@ -1,0 +1,733 @@
+// sketch_kernels.cu -- the sketch A_hat = S A on sm_103a.
+//
+//  REGEN  (Alg. 3, variant kji, "regenerate per nonzero"): output-stationary.
+//         A work item is (column k of A) x (tile of 128*Q rows of S).  The
+//         item's accumulators live in registers; every nonzero (j, a) of the
+//         column regenerates the S entries of the tile for row j.  For +-1
+//         one Philox block gives 128 signs, so a warp computes one block per
+//         nonzero (lane t for nonzero t of a batch of 32) and shares the
+//         words through shared memory.  Deterministic.
+//
+//  PANEL  (Alg. 4, variant jki, "generate once per row"): a CTA owns a tile
+//         of 32 rows of S, a block of columns and a contiguous range of rows
+//         of A.  Its slice of A_hat lives in shared memory.  Each nonempty
+//         row j of A generates S(tile, j) once and scatters it into all of
+//         the row's nonzeros.  Row ranges give partial sums that an ordered
+//         reduction adds up (Sec. 2.1's unblocked inner dimension is split
+//         here only to fill the GPU and to bound FP32 summation length).
+//
+//  CSR    the per-row structure PANEL needs (the paper's blocked CSR with a
+//         single vertical block, Sec. 3.2), built on the device: row counts,
+//         exclusive scan, scatter.
+#include <algorithm>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace sk {
+
+// ---------------------------------------------------------------------------
+// REGEN
+// ---------------------------------------------------------------------------
+constexpr int kRegenWarps = 8;
+
+template <int DIST, int Q, typename VT>
+__global__ void __launch_bounds__(kRegenWarps * 32)
+    k_regen(int32_t m, int32_t n, int32_t d, int32_t split,
+            const int32_t* __restrict__ colptr,
+            const int32_t* __restrict__ rowidx, const VT* __restrict__ vals,
+            float* __restrict__ Ahat, uint32_t k0, uint32_t k1,
+            uint32_t stream_id, int* status,
+            unsigned long long* gen_count) {
+  constexpr int TD = 128 * Q;          // rows of S per item
+  constexpr int SW = 4 * Q + 4;        // staged words per nonzero (+pad)
+  __shared__ float red[kRegenWarps][TD];
+  __shared__ __align__(16) uint32_t stage[DIST == kPM1 ? kRegenWarps : 1]
+                                         [DIST == kPM1 ? 32 : 1]
+                                         [DIST == kPM1 ? SW : 4];
+
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  const int items_per_cta = kRegenWarps / split;
+  const int sub = warp % split;
+  const int dtiles = (d + TD - 1) / TD;
+  const int64_t item =
+      static_cast<int64_t>(blockIdx.x) * items_per_cta + warp / split;
+  const bool valid = item < static_cast<int64_t>(n) * dtiles;
+  const int32_t k = valid ? static_cast<int32_t>(item / dtiles) : 0;
+  const int32_t d0 = valid ? static_cast<int32_t>(item % dtiles) * TD : 0;
+
+  float outer[Q][4];
+#pragma unroll
+  for (int q = 0; q < Q; ++q)
+#pragma unroll
+    for (int r = 0; r < 4; ++r) outer[q][r] = 0.f;
+  float t_outer = 0.f;  // +-1 only: sum of the column's values
+  unsigned long long generated = 0;
+
+  if (valid) {
+    int32_t p0 = colptr[k], p1 = colptr[k + 1];
+    if (p1 < p0) {
+      atomicOr(status, kStatusBadColptr);
+      p1 = p0;
+    }
+    const int32_t len = p1 - p0;
+    const int32_t chunk = (len + split - 1) / split;
+    const int32_t lo = p0 + min(len, sub * chunk);
+    const int32_t hi = p0 + min(len, (sub + 1) * chunk);
+    const int rows_valid = min(TD, d - d0);
+
+    // bit masks of this lane's four rows inside its Philox word (+-1)
+    uint32_t mask[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) mask[r] = 1u << (4 * (lane & 7) + r);
+
+    for (int32_t base = lo; base < hi; base += 32) {
+      const int cnt = min(32, hi - base);
+      int32_t j = 0;
+      float a = 0.f;
+      if (lane < cnt) {
+        j = rowidx[base + lane];
+        a = to_f32(vals[base + lane]);
+        if (static_cast<uint32_t>(j) >= static_cast<uint32_t>(m)) {
+          atomicOr(status, kStatusBadRow);
+          j = 0;
+          a = 0.f;
+        }
+      }
+      generated += static_cast<unsigned long long>(cnt) * rows_valid;
+      float inner[Q][4];
+#pragma unroll
+      for (int q = 0; q < Q; ++q)
+#pragma unroll
+        for (int r = 0; r < 4; ++r) inner[q][r] = 0.f;
+
+      if constexpr (DIST == kPM1) {
+        // lane t: Philox blocks of nonzero t for the Q 128-row blocks
+        if (lane < cnt) {
+#pragma unroll
+          for (int q = 0; q < Q; ++q) {
+            const uint4 x = philox_block(static_cast<uint32_t>((d0 >> 7) + q),
+                                         static_cast<uint32_t>(j), stream_id,
+                                         k0, k1);
+            *reinterpret_cast<uint4*>(&stage[warp][lane][4 * q]) = x;
+          }
+        }
+        __syncwarp();
+        float t_inner = 0.f;
+        const int wsel = lane >> 3;
+        for (int t = 0; t < cnt; ++t) {
+          const float at = __shfl_sync(0xffffffffu, a, t);
+          t_inner += at;
+#pragma unroll
+          for (int q = 0; q < Q; ++q) {
+            const uint32_t w = stage[warp][t][4 * q + wsel];
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+              if (w & mask[r]) inner[q][r] += at;
+          }
+        }
+        __syncwarp();
+        t_outer += t_inner;
+      } else {
+        for (int t = 0; t < cnt; ++t) {
+          const int32_t jt = __shfl_sync(0xffffffffu, j, t);
+          const float at = __shfl_sync(0xffffffffu, a, t);
+#pragma unroll
+          for (int q = 0; q < Q; ++q) {
+            const uint4 x = philox_block(
+                static_cast<uint32_t>((d0 >> 2) + 32 * q + lane),
+                static_cast<uint32_t>(jt), stream_id, k0, k1);
+            const float4 s = four_entries<DIST>(x);
+            inner[q][0] = fmaf(at, s.x, inner[q][0]);
+            inner[q][1] = fmaf(at, s.y, inner[q][1]);
+            inner[q][2] = fmaf(at, s.z, inner[q][2]);
+            inner[q][3] = fmaf(at, s.w, inner[q][3]);
+          }
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < Q; ++q)
+#pragma unroll
+        for (int r = 0; r < 4; ++r) outer[q][r] += inner[q][r];
+    }
+    if constexpr (DIST == kPM1) {
+      // sum over +1 rows minus sum over -1 rows = T - 2 P
+#pragma unroll
+      for (int q = 0; q < Q; ++q)
+#pragma unroll
+        for (int r = 0; r < 4; ++r) outer[q][r] = t_outer - 2.f * outer[q][r];
+    }
+  }
+
+  if (split == 1) {
+    if (valid) {
+#pragma unroll
+      for (int q = 0; q < Q; ++q)
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          const int32_t i = d0 + 128 * q + 4 * lane + r;
+          if (i < d) Ahat[static_cast<int64_t>(k) * d + i] = outer[q][r];
+        }
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < Q; ++q)
+#pragma unroll
+      for (int r = 0; r < 4; ++r) red[warp][128 * q + 4 * lane + r] = outer[q][r];
+    __syncthreads();
+    if (valid && sub == 0) {
+#pragma unroll
+      for (int q = 0; q < Q; ++q)
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          const int c = 128 * q + 4 * lane + r;
+          float s = red[warp][c];
+          for (int u = 1; u < split; ++u) s += red[warp + u][c];
+          const int32_t i = d0 + c;
+          if (i < d) Ahat[static_cast<int64_t>(k) * d + i] = s;
+        }
+    }
+  }
+  if (gen_count && valid) {
+    // lane 0 of each warp reports the entries this warp generated
+    if (lane == 0) atomicAdd(gen_count, generated);
+  }
+}
+
+template <int DIST, typename VT>
+static cudaError_t launch_regen_q(const RegenArgs& a, cudaStream_t s) {
+  const int TD = 128 * a.q_tiles;
+  const int64_t dtiles = (a.d + TD - 1) / TD;
+  const int64_t items = static_cast<int64_t>(a.n) * dtiles;
+  const int items_per_cta = kRegenWarps / a.split;
+  const int64_t blocks = (items + items_per_cta - 1) / items_per_cta;
+  if (blocks == 0) return cudaSuccess;
+  if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+  const dim3 grid(static_cast<unsigned>(blocks)), block(kRegenWarps * 32);
+  const VT* v = static_cast<const VT*>(a.values);
+#define SK_REGEN_CASE(QQ)                                                   \
+  case QQ:                                                                  \
+    k_regen<DIST, QQ, VT><<<grid, block, 0, s>>>(                           \
+        a.m, a.n, a.d, a.split, a.colptr, a.rowidx, v, a.Ahat, a.k0, a.k1, \
+        a.stream_id, a.status, a.gen_count);                                \
+    break;
+  switch (a.q_tiles) {
+    SK_REGEN_CASE(1)
+    SK_REGEN_CASE(2)
+    SK_REGEN_CASE(3)
+    SK_REGEN_CASE(4)
+    default:
+      return cudaErrorInvalidValue;
+  }
+#undef SK_REGEN_CASE
+  return cudaGetLastError();
+}
+
+cudaError_t launch_regen(const RegenArgs& a, cudaStream_t s) {
+  if (a.split != 1 && a.split != 2 && a.split != 4 && a.split != 8)
+    return cudaErrorInvalidValue;
+  if (a.dtype == 0) {
+    switch (a.dist) {
+      case kPM1: return launch_regen_q<kPM1, float>(a, s);
+      case kUniform: return launch_regen_q<kUniform, float>(a, s);
+      case kNormal: return launch_regen_q<kNormal, float>(a, s);
+    }
+  } else {
+    switch (a.dist) {
+      case kPM1: return launch_regen_q<kPM1, __nv_bfloat16>(a, s);
+      case kUniform: return launch_regen_q<kUniform, __nv_bfloat16>(a, s);
+      case kNormal: return launch_regen_q<kNormal, __nv_bfloat16>(a, s);
+    }
+  }
+  return cudaErrorInvalidValue;
+}
+
+// ---------------------------------------------------------------------------
+// CSR build (row counts -> exclusive scan -> scatter)
+// ---------------------------------------------------------------------------
+constexpr int kScanThreads = 1024;
+constexpr int kScanItems = 4;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+__global__ void k_row_count(int64_t nnz, int32_t m,
+                            const int32_t* __restrict__ rowidx,
+                            int32_t* __restrict__ cnt, int* status) {
+  for (int64_t p = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+       p < nnz; p += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int32_t j = rowidx[p];
+    if (static_cast<uint32_t>(j) < static_cast<uint32_t>(m))
+      atomicAdd(&cnt[j], 1);
+    else
+      atomicOr(status, kStatusBadRow);
+  }
+}
+
+// Block-level exclusive scan of kScanTile ints; writes the tile total.
+__global__ void __launch_bounds__(kScanThreads)
+    k_scan_tiles(const int32_t* __restrict__ in, int32_t* __restrict__ out,
+                 int64_t len, int32_t* __restrict__ tile_sums) {
+  __shared__ int32_t warp_tot[kScanThreads / 32];
+  const int64_t base = static_cast<int64_t>(blockIdx.x) * kScanTile +
+                       static_cast<int64_t>(threadIdx.x) * kScanItems;
+  int32_t v[kScanItems];
+  int32_t run = 0;
+#pragma unroll
+  for (int t = 0; t < kScanItems; ++t) {
+    v[t] = (base + t < len) ? in[base + t] : 0;
+    run += v[t];
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int32_t incl = run;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) warp_tot[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    int32_t w = (lane < kScanThreads / 32) ? warp_tot[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int32_t y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
+    }
+    if (lane < kScanThreads / 32) warp_tot[lane] = w;  // inclusive
+  }
+  __syncthreads();
+  int32_t excl = incl - run + (warp > 0 ? warp_tot[warp - 1] : 0);
+#pragma unroll
+  for (int t = 0; t < kScanItems; ++t) {
+    if (base + t < len) out[base + t] = excl;
+    excl += v[t];
+  }
+  if (threadIdx.x == kScanThreads - 1 && tile_sums)
+    tile_sums[blockIdx.x] = warp_tot[kScanThreads / 32 - 1];
+}
+
+__global__ void k_scan_add(int32_t* __restrict__ out, int64_t len,
+                           const int32_t* __restrict__ tile_offsets) {
+  const int64_t tile = blockIdx.x;
+  const int32_t off = tile_offsets[tile];
+  const int64_t base = tile * kScanTile;
+  for (int t = threadIdx.x; t < kScanTile; t += blockDim.x)
+    if (base + t < len) out[base + t] += off;
+}
+
+static int64_t scan_levels_bytes(int64_t len) {
+  int64_t bytes = 0;
+  while (len > 1) {
+    const int64_t tiles = (len + kScanTile - 1) / kScanTile;
+    bytes += tiles * 2 * static_cast<int64_t>(sizeof(int32_t)) + 256;
+    len = tiles;
+  }
+  return bytes;
+}
+
+// Exclusive scan of `len` ints (in may equal out).  `tmp` needs
+// scan_levels_bytes(len) bytes.
+static cudaError_t exclusive_scan(const int32_t* in, int32_t* out, int64_t len,
+                                  char* tmp, cudaStream_t s, int* launches) {
+  const int64_t tiles = (len + kScanTile - 1) / kScanTile;
+  if (tiles <= 0) return cudaSuccess;
+  int32_t* sums = reinterpret_cast<int32_t*>(tmp);
+  int32_t* sums_scanned = sums + tiles;
+  k_scan_tiles<<<static_cast<unsigned>(tiles), kScanThreads, 0, s>>>(
+      in, out, len, tiles > 1 ? sums : nullptr);
+  ++*launches;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || tiles == 1) return e;
+  char* next = tmp + ((tiles * 2 * sizeof(int32_t) + 255) / 256) * 256;
+  e = exclusive_scan(sums, sums_scanned, tiles, next, s, launches);
+  if (e != cudaSuccess) return e;
+  k_scan_add<<<static_cast<unsigned>(tiles), 256, 0, s>>>(out, len,
+                                                          sums_scanned);
+  ++*launches;
+  return cudaGetLastError();
+}
+
+template <typename VT>
+__global__ void k_csr_scatter(int32_t n, int32_t m,
+                              const int32_t* __restrict__ colptr,
+                              const int32_t* __restrict__ rowidx,
+                              const VT* __restrict__ vals,
+                              const int32_t* __restrict__ rowptr,
+                              int32_t* __restrict__ cursor,
+                              int32_t* __restrict__ ccol,
+                              float* __restrict__ cval) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = static_cast<int64_t>(gridDim.x) * (blockDim.x >> 5);
+  for (int64_t k = blockIdx.x * static_cast<int64_t>(blockDim.x >> 5) +
+                   (threadIdx.x >> 5);
+       k < n; k += warps) {
+    const int32_t p0 = colptr[k], p1 = colptr[k + 1];
+    for (int32_t p = p0 + lane; p < p1; p += 32) {
+      const int32_t j = rowidx[p];
+      if (static_cast<uint32_t>(j) >= static_cast<uint32_t>(m)) continue;
+      const int32_t pos = rowptr[j] + atomicAdd(&cursor[j], 1);
+      ccol[pos] = static_cast<int32_t>(k);
+      cval[pos] = to_f32(vals[p]);
+    }
+  }
+}
+
+static size_t align256(size_t b) { return (b + 255) / 256 * 256; }
+
+size_t csr_workspace_bytes(int64_t m, int64_t nnz) {
+  return align256((m + 1) * sizeof(int32_t)) * 2 +       // cnt/cursor, rowptr
+         align256(nnz * sizeof(int32_t)) +               // ccol
+         align256(nnz * sizeof(float)) +                 // cval
+         align256(static_cast<size_t>(scan_levels_bytes(m + 1)));
+}
+
+cudaError_t build_csr(int32_t m, int32_t n, int64_t nnz, const int32_t* colptr,
+                      const int32_t* rowidx, const void* values, int32_t dtype,
+                      void* ws, CsrView* out, int* status, cudaStream_t s,
+                      int* launches) {
+  char* p = static_cast<char*>(ws);
+  int32_t* cnt = reinterpret_cast<int32_t*>(p);
+  p += align256((m + 1) * sizeof(int32_t));
+  int32_t* rowptr = reinterpret_cast<int32_t*>(p);
+  p += align256((m + 1) * sizeof(int32_t));
+  int32_t* ccol = reinterpret_cast<int32_t*>(p);
+  p += align256(nnz * sizeof(int32_t));
+  float* cval = reinterpret_cast<float*>(p);
+  p += align256(nnz * sizeof(float));
+  char* scan_tmp = p;
+
+  cudaError_t e = cudaMemsetAsync(cnt, 0, (m + 1) * sizeof(int32_t), s);
+  if (e != cudaSuccess) return e;
+  const int sms = num_sms();
+  if (nnz > 0) {
+    const int64_t blocks = std::min<int64_t>((nnz + 255) / 256, 32LL * sms);
+    k_row_count<<<static_cast<unsigned>(blocks), 256, 0, s>>>(nnz, m, rowidx,
+                                                              cnt, status);
+    ++*launches;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  if ((e = exclusive_scan(cnt, rowptr, m + 1, scan_tmp, s, launches)) !=
+      cudaSuccess)
+    return e;
+  if (nnz > 0) {
+    if ((e = cudaMemsetAsync(cnt, 0, (m + 1) * sizeof(int32_t), s)) !=
+        cudaSuccess)
+      return e;
+    const int64_t blocks = std::min<int64_t>((n + 7) / 8, 32LL * sms);
+    if (dtype == 0)
+      k_csr_scatter<float><<<static_cast<unsigned>(blocks), 256, 0, s>>>(
+          n, m, colptr, rowidx, static_cast<const float*>(values), rowptr, cnt,
+          ccol, cval);
+    else
+      k_csr_scatter<__nv_bfloat16><<<static_cast<unsigned>(blocks), 256, 0,
+                                     s>>>(
+          n, m, colptr, rowidx, static_cast<const __nv_bfloat16*>(values),
+          rowptr, cnt, ccol, cval);
+    ++*launches;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  out->rowptr = rowptr;
+  out->ccol = ccol;
+  out->cval = cval;
+  return cudaSuccess;
+}
+
+// ---------------------------------------------------------------------------
+// PANEL
+// ---------------------------------------------------------------------------
+constexpr int kPanelWarps = 16;
+constexpr int kPanelRows = 32;  // rows of S per CTA
+
+size_t panel_smem_bytes(int32_t n_block) {
+  return static_cast<size_t>(n_block) * kPanelRows * sizeof(float) +
+         kPanelWarps * 4 * 32 * sizeof(float);
+}
+
+template <int DIST>
+__global__ void __launch_bounds__(kPanelWarps * 32)
+    k_panel(int32_t m, int32_t n, int32_t d, int32_t nb, int32_t G,
+            const int32_t* __restrict__ rowptr,
+            const int32_t* __restrict__ ccol, const float* __restrict__ cval,
+            float* __restrict__ partial, uint32_t k0, uint32_t k1,
+            uint32_t stream_id, unsigned long long* gen_count) {
+  extern __shared__ __align__(16) float smem[];
+  const int tile = blockIdx.x;
+  const int32_t kb0 = blockIdx.y * nb;
+  const int g = blockIdx.z;
+  const int32_t nbw = min(nb, n - kb0);
+  float* acc = smem;                                // [nbw][32]
+  float* stage_all = smem + static_cast<size_t>(nb) * kPanelRows;
+  for (int t = threadIdx.x; t < nbw * kPanelRows; t += blockDim.x) acc[t] = 0.f;
+  __syncthreads();
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float* stage = stage_all + warp * 128;
+  const int64_t r0 = static_cast<int64_t>(m) * g / G;
+  const int64_t r1 = static_cast<int64_t>(m) * (g + 1) / G;
+  const int rows_valid = min(kPanelRows, d - tile * kPanelRows);
+  unsigned long long generated = 0;
+
+  for (int64_t jb = r0 + 4 * warp; jb < r1; jb += 4 * kPanelWarps) {
+    // --- generate S(tile, j) for the 4 rows jb..jb+3 of this batch -------
+    const int r = lane >> 3, q = lane & 7;
+    const int64_t j = jb + r;
+    const bool nonempty = j < r1 && rowptr[j + 1] > rowptr[j];
+    if constexpr (DIST == kPM1) {
+      // one block (tile >> 2, j) holds the 32 signs of this tile in word
+      // (tile & 3)
+      if (q == 0 && nonempty) {
+        const uint4 x = philox_block(static_cast<uint32_t>(tile >> 2),
+                                     static_cast<uint32_t>(j), stream_id, k0,
+                                     k1);
+        const int wsel = tile & 3;
+        const uint32_t w = wsel == 0 ? x.x : wsel == 1 ? x.y : wsel == 2 ? x.z : x.w;
+        reinterpret_cast<uint32_t*>(stage)[r * 32] = w;
+      }
+    } else {
+      if (nonempty) {
+        const uint4 x = philox_block(static_cast<uint32_t>(tile * 8 + q),
+                                     static_cast<uint32_t>(j), stream_id, k0,
+                                     k1);
+        *reinterpret_cast<float4*>(&stage[r * 32 + 4 * q]) =
+            four_entries<DIST>(x);
+      }
+    }
+    if (q == 0 && nonempty) generated += rows_valid;
+    __syncwarp();
+    float sv[4];
+#pragma unroll
+    for (int rr = 0; rr < 4; ++rr) {
+      if constexpr (DIST == kPM1) {
+        const uint32_t w = reinterpret_cast<const uint32_t*>(stage)[rr * 32];
+        sv[rr] = ((w >> lane) & 1u) ? -1.f : 1.f;
+      } else {
+        sv[rr] = stage[rr * 32 + lane];
+      }
+    }
+    __syncwarp();
+    // --- scatter into the row's nonzeros ---------------------------------
+#pragma unroll
+    for (int rr = 0; rr < 4; ++rr) {
+      const int64_t jj = jb + rr;
+      if (jj >= r1) break;
+      const int32_t p0 = rowptr[jj], p1 = rowptr[jj + 1];
+      for (int32_t pb = p0; pb < p1; pb += 32) {
+        const int c = min(32, p1 - pb);
+        int32_t kk = -1;
+        float aa = 0.f;
+        if (lane < c) {
+          kk = ccol[pb + lane] - kb0;
+          aa = cval[pb + lane];
+        }
+        for (int t = 0; t < c; ++t) {
+          const int32_t kt = __shfl_sync(0xffffffffu, kk, t);
+          const float at = __shfl_sync(0xffffffffu, aa, t);
+          if (static_cast<uint32_t>(kt) < static_cast<uint32_t>(nbw))
+            atomicAdd(&acc[kt * kPanelRows + lane], at * sv[rr]);
+        }
+      }
+    }
+  }
+  __syncthreads();
+  float* out = partial + (static_cast<int64_t>(g) * n + kb0) * d +
+               static_cast<int64_t>(tile) * kPanelRows;
+  for (int t = threadIdx.x; t < nbw * kPanelRows; t += blockDim.x) {
+    const int kk = t >> 5, i = t & 31;
+    if (i < rows_valid) out[static_cast<int64_t>(kk) * d + i] = acc[t];
+  }
+  if (gen_count && lane == 0 && generated) atomicAdd(gen_count, generated);
+}
+
+// A_hat = sum over g of partial[g] in the fixed order g = 0, 1, ...
+__global__ void k_reduce_partials(int64_t total, int32_t G,
+                                  const float* __restrict__ partial,
+                                  float* __restrict__ Ahat) {
+  for (int64_t idx = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+       idx < total; idx += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    float s = partial[idx];
+    for (int g = 1; g < G; ++g) s += partial[static_cast<int64_t>(g) * total + idx];
+    Ahat[idx] = s;
+  }
+}
+
+cudaError_t launch_panel(const PanelArgs& a, cudaStream_t s, int* launches) {
+  if (a.n_block <= 0 || a.row_groups <= 0) return cudaErrorInvalidValue;
+  const size_t smem = panel_smem_bytes(a.n_block);
+  const int tiles = (a.d + kPanelRows - 1) / kPanelRows;
+  const int cblocks = (a.n + a.n_block - 1) / a.n_block;
+  if (cblocks > 65535 || a.row_groups > 65535) return cudaErrorInvalidValue;
+  const dim3 grid(tiles, cblocks, a.row_groups), block(kPanelWarps * 32);
+  cudaError_t e;
+  // a single row group writes straight into A_hat
+  float* dst = a.row_groups == 1 ? a.Ahat : a.partial;
+#define SK_PANEL_CASE(DD)                                                    \
+  case DD:                                                                   \
+    e = cudaFuncSetAttribute(k_panel<DD>,                                    \
+                             cudaFuncAttributeMaxDynamicSharedMemorySize,    \
+                             static_cast<int>(smem));                        \
+    if (e != cudaSuccess) return e;                                          \
+    k_panel<DD><<<grid, block, smem, s>>>(                                   \
+        a.m, a.n, a.d, a.n_block, a.row_groups, a.csr.rowptr, a.csr.ccol,    \
+        a.csr.cval, dst, a.k0, a.k1, a.stream_id, a.gen_count);              \
+    ++*launches;                                                             \
+    break;
+  switch (a.dist) {
+    SK_PANEL_CASE(kPM1)
+    SK_PANEL_CASE(kUniform)
+    SK_PANEL_CASE(kNormal)
+    default:
+      return cudaErrorInvalidValue;
+  }
+#undef SK_PANEL_CASE
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (a.row_groups > 1) {
+    const int64_t total = static_cast<int64_t>(a.n) * a.d;
+    const int64_t blocks = std::min<int64_t>((total + 255) / 256, 16LL * num_sms());
+    k_reduce_partials<<<static_cast<unsigned>(blocks), 256, 0, s>>>(
+        total, a.row_groups, a.partial, a.Ahat);
+    ++*launches;
+    e = cudaGetLastError();
+  }
+  return e;
+}
+
+// ---------------------------------------------------------------------------
+// Validation and test hooks
+// ---------------------------------------------------------------------------
+__global__ void k_validate(int32_t m, int32_t n, int64_t nnz,
+                           const int32_t* __restrict__ colptr,
+                           const int32_t* __restrict__ rowidx, int* status) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = static_cast<int64_t>(gridDim.x) * (blockDim.x >> 5);
+  for (int64_t k = blockIdx.x * static_cast<int64_t>(blockDim.x >> 5) +
+                   (threadIdx.x >> 5);
+       k < n; k += warps) {
+    const int32_t p0 = colptr[k], p1 = colptr[k + 1];
+    if (k == 0 && p0 != 0 && lane == 0) atomicOr(status, kStatusBadColptr);
+    if (k == n - 1 && p1 != nnz && lane == 0) atomicOr(status, kStatusBadColptr);
+    if (p1 < p0 || p0 < 0 || p1 > nnz) {
+      if (lane == 0) atomicOr(status, kStatusBadColptr);
+      continue;
+    }
+    for (int32_t p = p0 + lane; p < p1; p += 32) {
+      const int32_t j = rowidx[p];
+      if (static_cast<uint32_t>(j) >= static_cast<uint32_t>(m) ||
+          (p > p0 && rowidx[p - 1] >= j))
+        atomicOr(status, kStatusBadRow);
+    }
+  }
+}
+
+cudaError_t launch_validate(int32_t m, int32_t n, int64_t nnz,
+                            const int32_t* colptr, const int32_t* rowidx,
+                            int* status, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const int64_t blocks = std::min<int64_t>((n + 7) / 8, 32LL * num_sms());
+  k_validate<<<static_cast<unsigned>(blocks), 256, 0, s>>>(m, n, nnz, colptr,
+                                                           rowidx, status);
+  return cudaGetLastError();
+}
+
+__global__ void k_debug_philox(const uint32_t* __restrict__ ctr, uint32_t k0,
+                               uint32_t k1, uint32_t* __restrict__ out,
+                               int64_t count) {
+  for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+       t < count; t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const uint4 c = make_uint4(ctr[4 * t], ctr[4 * t + 1], ctr[4 * t + 2],
+                               ctr[4 * t + 3]);
+    const uint4 x = philox4x32_10(c, k0, k1);
+    out[4 * t] = x.x;
+    out[4 * t + 1] = x.y;
+    out[4 * t + 2] = x.z;
+    out[4 * t + 3] = x.w;
+  }
+}
+
+cudaError_t launch_debug_philox(const uint32_t* ctr, uint32_t k0, uint32_t k1,
+                                uint32_t* out, int64_t count, cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  const int64_t blocks = std::min<int64_t>((count + 255) / 256, 4096);
+  k_debug_philox<<<static_cast<unsigned>(blocks), 256, 0, s>>>(ctr, k0, k1, out,
+                                                               count);
+  return cudaGetLastError();
+}
+
+__global__ void k_debug_S(int dist, uint32_t k0, uint32_t k1,
+                          uint32_t stream_id, const int64_t* __restrict__ ii,
+                          const int64_t* __restrict__ jj,
+                          float* __restrict__ out, int64_t count) {
+  for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+       t < count; t += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    out[t] = S_entry(dist, k0, k1, stream_id, ii[t], jj[t]);
+}
+
+cudaError_t launch_debug_S(int dist, uint32_t k0, uint32_t k1,
+                           uint32_t stream_id, const int64_t* i,
+                           const int64_t* j, float* out, int64_t count,
+                           cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  const int64_t blocks = std::min<int64_t>((count + 255) / 256, 4096);
+  k_debug_S<<<static_cast<unsigned>(blocks), 256, 0, s>>>(dist, k0, k1,
+                                                          stream_id, i, j, out,
+                                                          count);
+  return cudaGetLastError();
+}
+
+template <int DIST>
+__global__ void k_bench_generator(uint32_t k0, uint32_t k1, int64_t threads,
+                                  int64_t blocks_per_thread,
+                                  float* __restrict__ sink) {
+  const int64_t tid = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (tid >= threads) return;
+  float acc = 0.f;
+  uint32_t bits = 0;
+  for (int64_t b = 0; b < blocks_per_thread; ++b) {
+    const uint4 x = philox_block(static_cast<uint32_t>(b),
+                                 static_cast<uint32_t>(tid), 0u, k0, k1);
+    if constexpr (DIST == kPM1) {
+      bits ^= x.x ^ x.y ^ x.z ^ x.w;
+    } else {
+      const float4 v = four_entries<DIST>(x);
+      acc += (v.x + v.y) + (v.z + v.w);
+    }
+  }
+  sink[tid] = acc + static_cast<float>(bits & 1u);
+}
+
+cudaError_t launch_bench_generator(int dist, uint32_t k0, uint32_t k1,
+                                   int64_t threads, int64_t blocks_per_thread,
+                                   float* sink, cudaStream_t s) {
+  if (threads <= 0) return cudaSuccess;
+  const int64_t blocks = (threads + 255) / 256;
+  if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
+  switch (dist) {
+    case kPM1:
+      k_bench_generator<kPM1><<<static_cast<unsigned>(blocks), 256, 0, s>>>(
+          k0, k1, threads, blocks_per_thread, sink);
+      break;
+    case kUniform:
+      k_bench_generator<kUniform><<<static_cast<unsigned>(blocks), 256, 0, s>>>(
+          k0, k1, threads, blocks_per_thread, sink);
+      break;
+    case kNormal:
+      k_bench_generator<kNormal><<<static_cast<unsigned>(blocks), 256, 0, s>>>(
+          k0, k1, threads, blocks_per_thread, sink);
+      break;
+    default:
+      return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+int num_sms() {
+  static int cached = 0;
+  if (cached == 0) {
+    int dev = 0, v = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    cached = v > 0 ? v : 1;
+  }
+  return cached;
+}
+
+}  // namespace sk

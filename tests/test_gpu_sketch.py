@@ -1,0 +1,254 @@
+"""Parity of the CUDA sketch (through the C ABI) with the FP64 CPU oracle.
+
+Bar: bit-exact for +-1 S with integer-valued A (every partial sum is an
+exact integer in FP32); relative Frobenius error <= 1e-6 against FP64 for
+FP32 values and U / N entries of S; S itself bit-exact for +-1 and U and
+within a few FP32 ulps for N (Box-Muller uses CUDA's logf / sqrtf /
+sincospif on the device and FP64 libm in the oracle).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2310_15419_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2310_15419_gb300 import capi  # noqa: E402
+
+DISTS = {"pm1": oracle.PM1, "uniform": oracle.UNIFORM, "normal": oracle.NORMAL}
+TOL = 1e-6
+
+
+def rel_fro(got, ref):
+    den = np.linalg.norm(ref)
+    return np.linalg.norm(got - ref) / (den if den > 0 else 1.0)
+
+
+def gpu_sketch(A, d, dist, seed=1, stream_id=0, plan=None):
+    sk = capi.Sketch(A.m, A.n, d, dist, seed=seed, stream_id=stream_id)
+    if plan:
+        sk.set_plan(**plan)
+    dA = capi.DeviceCSC(A)
+    out = sk.apply(dA)
+    torch.cuda.synchronize()
+    st = sk.device_status()
+    sk.close()
+    assert st == capi.SKETCH_OK
+    return out.cpu().numpy().astype(np.float64).T  # d x n
+
+
+def oracle_sketch(A, d, dist, seed=1, stream_id=0):
+    ref, _ = oracle.sketch_jki(A.m, A.n, d, DISTS[dist], seed, stream_id,
+                               A.colptr, A.rowidx, A.values)
+    return ref
+
+
+REGEN_PLANS = [dict(mode=capi.SKETCH_MODE_REGEN, q_tiles=q, split=s)
+               for q in (1, 2, 3, 4) for s in (1, 2, 4, 8)]
+PANEL_PLANS = [dict(mode=capi.SKETCH_MODE_PANEL, n_block=nb, row_groups=g)
+               for nb, g in ((37, 1), (16, 3), (5, 7), (37, 64))]
+
+
+# ---------------------------------------------------------------- generator
+def test_philox_matches_oracle():
+    rng = np.random.default_rng(0)
+    ctr = rng.integers(0, 2**32, size=(20000, 4), dtype=np.uint64)
+    ctr[0] = 0
+    ctr[1] = 2**32 - 1
+    for seed in (0, 1, 0xFFFFFFFFFFFFFFFF, 0x0123456789ABCDEF):
+        dev = capi.debug_philox(torch.from_numpy(ctr.astype(np.uint32).view(np.int32)).cuda(),
+                                seed).cpu().numpy().view(np.uint32)
+        key = np.array([seed & 0xFFFFFFFF, seed >> 32], dtype=np.uint32)
+        for t in list(range(50)) + [19999]:
+            assert np.array_equal(dev[t], oracle.philox4x32_10(ctr[t].astype(np.uint32), key))
+
+
+@pytest.mark.parametrize("dist", ["pm1", "uniform", "normal"])
+def test_S_entries_match_oracle(dist):
+    rng = np.random.default_rng(1)
+    i = rng.integers(0, 5000, size=4000)
+    j = rng.integers(0, 2**31 - 1, size=4000)
+    i[:8] = [0, 1, 2, 3, 127, 128, 4999, 31]
+    seed, stream = 0xDEADBEEF12345678, 5
+    got = capi.debug_S(DISTS[dist], seed, stream, torch.from_numpy(i).cuda(),
+                       torch.from_numpy(j).cuda()).cpu().numpy()
+    ref = np.array([oracle.S_entry(DISTS[dist], seed, stream, int(a), int(b))
+                    for a, b in zip(i, j)])
+    if dist == "normal":
+        assert np.all(np.abs(got - ref) <= 4e-7 * np.maximum(1.0, np.abs(ref)))
+    else:
+        assert np.array_equal(got.astype(np.float64), ref)
+
+
+# ------------------------------------------------------- exactness / tiling
+@pytest.mark.parametrize("plan", REGEN_PLANS + PANEL_PLANS)
+def test_pm1_integer_bit_exact_every_plan(plan):
+    # d = 300 and n = 37 leave ragged tails in every tile shape
+    A = inputs.integer_uniform(6000, 37, 0.02, seed=3)
+    ref = oracle_sketch(A, 300, "pm1")
+    got = gpu_sketch(A, 300, "pm1", plan=plan)
+    assert np.array_equal(got, ref)
+
+
+@pytest.mark.parametrize("dist", ["uniform", "normal"])
+@pytest.mark.parametrize("plan", [REGEN_PLANS[0], REGEN_PLANS[-1],
+                                  REGEN_PLANS[9]] + PANEL_PLANS)
+def test_float_within_tolerance_every_plan(dist, plan):
+    A = inputs.float_uniform(6000, 37, 0.02, seed=4)
+    ref = oracle_sketch(A, 301, dist)
+    got = gpu_sketch(A, 301, dist, plan=plan)
+    assert rel_fro(got, ref) <= TOL
+
+
+def test_uniform_integer_values_exact_in_integer_scale():
+    """U entries are odd multiples of 2^-24; with small integer A every
+    partial sum of (2u+1) a is an integer below 2^24 only for tiny sums, so
+    instead check the tolerance and the absence of any systematic bias."""
+    A = inputs.integer_uniform(4000, 20, 0.01, seed=5)
+    ref = oracle_sketch(A, 128, "uniform")
+    got = gpu_sketch(A, 128, "uniform")
+    assert rel_fro(got, ref) <= TOL
+
+
+def test_streams_give_different_S_and_match_oracle():
+    A = inputs.integer_uniform(3000, 10, 0.02, seed=6)
+    g0 = gpu_sketch(A, 200, "pm1", stream_id=0)
+    g7 = gpu_sketch(A, 200, "pm1", stream_id=7)
+    assert not np.array_equal(g0, g7)
+    assert np.array_equal(g7, oracle_sketch(A, 200, "pm1", stream_id=7))
+
+
+def test_bf16_values():
+    A, b, _ = inputs.lsq_mixed(m=20000, n=30, density=0.01)
+    ref = oracle_sketch(A, 60, "pm1")
+    for plan in (REGEN_PLANS[5], PANEL_PLANS[0]):
+        got = gpu_sketch(A, 60, "pm1", plan=plan)
+        assert rel_fro(got, ref) <= TOL
+
+
+def test_config_plain_small_bit_exact():
+    """m=50,000, n=200, d=400, density 1%, integer values, +-1 S, seed 1."""
+    A = inputs.plain_small()
+    ref = oracle_sketch(A, inputs.PLAIN_SMALL_D, "pm1")
+    got = gpu_sketch(A, inputs.PLAIN_SMALL_D, "pm1")  # tuned plan
+    assert np.array_equal(got, ref)
+
+
+# --------------------------------------------------------------- edge cases
+def test_empty_matrix_gives_zero():
+    A = inputs.CSC(100, 7, np.zeros(8, np.int32), np.zeros(0, np.int32),
+                   np.zeros(0, np.float32))
+    got = gpu_sketch(A, 33, "uniform")
+    assert np.all(got == 0)
+
+
+def test_empty_columns_and_tiny_shapes():
+    colptr = np.array([0, 0, 2, 2, 3], np.int32)
+    rowidx = np.array([1, 4, 0], np.int32)
+    vals = np.array([2.0, -1.0, 3.0], np.float32)
+    A = inputs.CSC(5, 4, colptr, rowidx, vals)
+    for d in (1, 3, 4, 5, 129):
+        for dist in ("pm1", "uniform"):
+            ref = oracle_sketch(A, d, dist)
+            for plan in (None, REGEN_PLANS[0], PANEL_PLANS[2]):
+                got = gpu_sketch(A, d, dist, plan=plan)
+                if dist == "pm1":
+                    assert np.array_equal(got, ref), (d, plan)
+                else:
+                    assert rel_fro(got, ref) <= TOL
+
+
+def test_long_column_accuracy():
+    """One column with 200k nonzeros: FP32 accumulation must stay within the
+    1e-6 gate (two-level sums in REGEN, row groups in PANEL)."""
+    m = 400_000
+    rng = np.random.default_rng(7)
+    rows = np.sort(rng.choice(m, size=200_000, replace=False)).astype(np.int32)
+    A = inputs.CSC(m, 1, np.array([0, rows.size], np.int32), rows,
+                   rng.uniform(-1, 1, size=rows.size).astype(np.float32))
+    ref = oracle_sketch(A, 256, "uniform")
+    for plan in (REGEN_PLANS[4 * 1 + 0], REGEN_PLANS[4 * 1 + 3], None):
+        got = gpu_sketch(A, 256, "uniform", plan=plan)
+        assert rel_fro(got, ref) <= TOL, plan
+
+
+def test_generation_counts():
+    """Sec. 3.2: Alg. 3 generates d * nnz entries; Alg. 4 generates d per
+    nonempty row per column block."""
+    A = inputs.integer_uniform(5000, 40, 0.005, seed=8)
+    d = 200
+    for plan, expect in (
+            (REGEN_PLANS[6], d * A.nnz),
+            (dict(mode=capi.SKETCH_MODE_PANEL, n_block=40, row_groups=3),
+             d * np.unique(A.rowidx).size)):
+        sk = capi.Sketch(A.m, A.n, d, "uniform", seed=1)
+        sk.set_plan(**plan)
+        sk.set_counting(True)
+        sk.apply(capi.DeviceCSC(A))
+        assert sk.generated_entries() == expect
+        sk.close()
+
+
+def test_bad_row_index_is_reported_not_faulted():
+    A = inputs.integer_uniform(1000, 5, 0.02, seed=9)
+    A.rowidx = A.rowidx.copy()
+    A.rowidx[3] = 1000 + 17      # out of range
+    dA = capi.DeviceCSC(A)
+    assert capi.validate_csc(dA) == capi.SKETCH_ERR_CSC
+    for plan in (REGEN_PLANS[0], PANEL_PLANS[0]):
+        sk = capi.Sketch(A.m, A.n, 64, "pm1", seed=1)
+        sk.set_plan(**plan)
+        sk.apply(dA)
+        torch.cuda.synchronize()
+        assert sk.device_status() == capi.SKETCH_ERR_CSC
+        sk.close()
+
+
+def test_validator_accepts_good_and_rejects_unsorted():
+    A = inputs.integer_uniform(1000, 5, 0.02, seed=10)
+    assert capi.validate_csc(capi.DeviceCSC(A)) == capi.SKETCH_OK
+    B = inputs.integer_uniform(1000, 5, 0.02, seed=10)
+    B.rowidx = B.rowidx.copy()
+    B.rowidx[[0, 1]] = B.rowidx[[1, 0]]
+    assert capi.validate_csc(capi.DeviceCSC(B)) == capi.SKETCH_ERR_CSC
+
+
+def test_shape_mismatch_is_an_argument_error():
+    A = inputs.integer_uniform(1000, 5, 0.02, seed=10)
+    sk = capi.Sketch(999, 5, 10, "pm1")
+    with pytest.raises(capi.SketchError) as e:
+        sk.apply(capi.DeviceCSC(A))
+    assert e.value.code == capi.SKETCH_ERR_ARG
+
+
+# ------------------------------------------------- full-size skewed workload
+@pytest.fixture(scope="module")
+def skew_large():
+    return inputs.skew_large()
+
+
+@pytest.mark.parametrize("dist", ["pm1", "uniform", "normal"])
+def test_skew_large_sampled_columns(skew_large, dist):
+    """m=2e6, n=1000, d=3000, ~1e7 nnz, power-law rows: the tuned launch the
+    benchmark times, checked on sampled columns (columns of A_hat depend
+    only on the matching column of A, so the oracle computes them alone)."""
+    A = skew_large
+    d = inputs.SKEW_LARGE_D
+    sk = capi.Sketch(A.m, A.n, d, dist, seed=1)
+    dA = capi.DeviceCSC(A)
+    out = sk.apply(dA)
+    torch.cuda.synchronize()
+    assert sk.device_status() == capi.SKETCH_OK
+    got = out.cpu().numpy().astype(np.float64)  # n x d
+    for k in (0, 1, 499, 998, 999):
+        p0, p1 = A.colptr[k], A.colptr[k + 1]
+        col = inputs.CSC(A.m, 1, np.array([0, p1 - p0], np.int32),
+                         A.rowidx[p0:p1], A.values[p0:p1])
+        ref = oracle_sketch(col, d, dist)[:, 0]
+        assert rel_fro(got[k], ref) <= TOL, (dist, k)
+    sk.close()
