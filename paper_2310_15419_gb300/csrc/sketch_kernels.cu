@@ -31,8 +31,16 @@ namespace sk {
 // ---------------------------------------------------------------------------
 constexpr int kRegenWarps = 8;
 
+// sum += x with Kahan compensation c (no reassociation: plain FP32 ops)
+__device__ __forceinline__ void kahan_add(float& sum, float& c, float x) {
+  const float y = __fsub_rn(x, c);
+  const float t = __fadd_rn(sum, y);
+  c = __fsub_rn(__fsub_rn(t, sum), y);
+  sum = t;
+}
+
 template <int DIST, int Q, typename VT>
-__global__ void __launch_bounds__(kRegenWarps * 32)
+__global__ void __launch_bounds__(kRegenWarps * 32, 2)
     k_regen(int32_t m, int32_t n, int32_t d, int32_t split,
             const int32_t* __restrict__ colptr,
             const int32_t* __restrict__ rowidx, const VT* __restrict__ vals,
@@ -57,12 +65,15 @@ __global__ void __launch_bounds__(kRegenWarps * 32)
   const int32_t k = valid ? static_cast<int32_t>(item / dtiles) : 0;
   const int32_t d0 = valid ? static_cast<int32_t>(item % dtiles) * TD : 0;
 
-  float outer[Q][4];
+  // Two-level sums: a batch of 32 nonzeros accumulates in `inner`, batch
+  // sums are added to `outer` with Kahan compensation (`comp`), so the FP32
+  // error stays near one rounding per batch however long the column is.
+  float outer[Q][4], comp[Q][4];
 #pragma unroll
   for (int q = 0; q < Q; ++q)
 #pragma unroll
-    for (int r = 0; r < 4; ++r) outer[q][r] = 0.f;
-  float t_outer = 0.f;  // +-1 only: sum of the column's values
+    for (int r = 0; r < 4; ++r) outer[q][r] = comp[q][r] = 0.f;
+  float t_outer = 0.f, t_comp = 0.f;  // +-1 only: sum of the column's values
   unsigned long long generated = 0;
 
   if (valid) {
@@ -128,7 +139,7 @@ __global__ void __launch_bounds__(kRegenWarps * 32)
           }
         }
         __syncwarp();
-        t_outer += t_inner;
+        kahan_add(t_outer, t_comp, t_inner);
       } else {
         for (int t = 0; t < cnt; ++t) {
           const int32_t jt = __shfl_sync(0xffffffffu, j, t);
@@ -149,7 +160,7 @@ __global__ void __launch_bounds__(kRegenWarps * 32)
 #pragma unroll
       for (int q = 0; q < Q; ++q)
 #pragma unroll
-        for (int r = 0; r < 4; ++r) outer[q][r] += inner[q][r];
+        for (int r = 0; r < 4; ++r) kahan_add(outer[q][r], comp[q][r], inner[q][r]);
     }
     if constexpr (DIST == kPM1) {
       // sum over +1 rows minus sum over -1 rows = T - 2 P
@@ -190,7 +201,7 @@ __global__ void __launch_bounds__(kRegenWarps * 32)
     }
   }
   if (gen_count && valid) {
-    // lane 0 of each warp reports the entries this warp generated
+    // every lane holds the same warp-uniform count; lane 0 reports it
     if (lane == 0) atomicAdd(gen_count, generated);
   }
 }
@@ -437,14 +448,15 @@ cudaError_t build_csr(int32_t m, int32_t n, int64_t nnz, const int32_t* colptr,
 // ---------------------------------------------------------------------------
 constexpr int kPanelWarps = 16;
 constexpr int kPanelRows = 32;  // rows of S per CTA
+constexpr int kBatchRows = 8;   // rows of A a warp takes at a time
 
 size_t panel_smem_bytes(int32_t n_block) {
   return static_cast<size_t>(n_block) * kPanelRows * sizeof(float) +
-         kPanelWarps * 4 * 32 * sizeof(float);
+         kPanelWarps * kBatchRows * 32 * sizeof(float);
 }
 
 template <int DIST>
-__global__ void __launch_bounds__(kPanelWarps * 32)
+__global__ void __launch_bounds__(kPanelWarps * 32, 1)
     k_panel(int32_t m, int32_t n, int32_t d, int32_t nb, int32_t G,
             const int32_t* __restrict__ rowptr,
             const int32_t* __restrict__ ccol, const float* __restrict__ cval,
@@ -461,42 +473,57 @@ __global__ void __launch_bounds__(kPanelWarps * 32)
   __syncthreads();
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  float* stage = stage_all + warp * 128;
-  const int64_t r0 = static_cast<int64_t>(m) * g / G;
-  const int64_t r1 = static_cast<int64_t>(m) * (g + 1) / G;
+  float* stage = stage_all + warp * (kBatchRows * 32);
+  const int32_t r0 = static_cast<int32_t>(static_cast<int64_t>(m) * g / G);
+  const int32_t r1 = static_cast<int32_t>(static_cast<int64_t>(m) * (g + 1) / G);
   const int rows_valid = min(kPanelRows, d - tile * kPanelRows);
   unsigned long long generated = 0;
 
-  for (int64_t jb = r0 + 4 * warp; jb < r1; jb += 4 * kPanelWarps) {
-    // --- generate S(tile, j) for the 4 rows jb..jb+3 of this batch -------
-    const int r = lane >> 3, q = lane & 7;
-    const int64_t j = jb + r;
-    const bool nonempty = j < r1 && rowptr[j + 1] > rowptr[j];
-    if constexpr (DIST == kPM1) {
-      // one block (tile >> 2, j) holds the 32 signs of this tile in word
-      // (tile & 3)
-      if (q == 0 && nonempty) {
-        const uint4 x = philox_block(static_cast<uint32_t>(tile >> 2),
-                                     static_cast<uint32_t>(j), stream_id, k0,
-                                     k1);
-        const int wsel = tile & 3;
-        const uint32_t w = wsel == 0 ? x.x : wsel == 1 ? x.y : wsel == 2 ? x.z : x.w;
-        reinterpret_cast<uint32_t*>(stage)[r * 32] = w;
-      }
-    } else {
-      if (nonempty) {
-        const uint4 x = philox_block(static_cast<uint32_t>(tile * 8 + q),
-                                     static_cast<uint32_t>(j), stream_id, k0,
-                                     k1);
-        *reinterpret_cast<float4*>(&stage[r * 32 + 4 * q]) =
-            four_entries<DIST>(x);
-      }
+  for (int32_t jb = r0 + kBatchRows * warp; jb < r1;
+       jb += kBatchRows * kPanelWarps) {
+    // --- row pointers of the batch: one load, lanes 0..kBatchRows ---------
+    const int32_t rp = rowptr[min(jb + min(lane, kBatchRows), r1)];
+    const int32_t p_beg = __shfl_sync(0xffffffffu, rp, 0);
+    const int32_t p_end = __shfl_sync(0xffffffffu, rp, kBatchRows);
+    if (p_beg == p_end) continue;  // the whole batch is empty
+    // --- first chunk of the batch's nonzeros (contiguous in the CSR) ------
+    int32_t chunk = p_beg;
+    int32_t kk = -1;
+    float aa = 0.f;
+    if (chunk + lane < p_end) {
+      kk = ccol[chunk + lane] - kb0;
+      aa = cval[chunk + lane];
     }
-    if (q == 0 && nonempty) generated += rows_valid;
-    __syncwarp();
-    float sv[4];
+    // --- generate S(tile, j) once for every nonempty row of the batch -----
 #pragma unroll
-    for (int rr = 0; rr < 4; ++rr) {
+    for (int h = 0; h < kBatchRows / 4; ++h) {
+      const int r = 4 * h + (lane >> 3), q = lane & 7;
+      const int32_t lo = __shfl_sync(0xffffffffu, rp, r);
+      const int32_t hi = __shfl_sync(0xffffffffu, rp, r + 1);
+      const bool nonempty = hi > lo;  // rows past r1 have lo == hi
+      const uint32_t j = static_cast<uint32_t>(jb + r);
+      if constexpr (DIST == kPM1) {
+        // block (tile >> 2, j) holds this tile's 32 signs in word (tile & 3)
+        if (q == 0 && nonempty) {
+          const uint4 x = philox_block(static_cast<uint32_t>(tile >> 2), j,
+                                       stream_id, k0, k1);
+          const int wsel = tile & 3;
+          const uint32_t w = wsel == 0 ? x.x : wsel == 1 ? x.y : wsel == 2 ? x.z : x.w;
+          reinterpret_cast<uint32_t*>(stage)[r * 32] = w;
+        }
+      } else {
+        if (nonempty) {
+          const uint4 x = philox_block(static_cast<uint32_t>(tile * 8 + q), j,
+                                       stream_id, k0, k1);
+          *reinterpret_cast<float4*>(&stage[r * 32 + 4 * q]) = four_entries<DIST>(x);
+        }
+      }
+      if (q == 0 && nonempty) generated += rows_valid;
+    }
+    __syncwarp();
+    float sv[kBatchRows];
+#pragma unroll
+    for (int rr = 0; rr < kBatchRows; ++rr) {
       if constexpr (DIST == kPM1) {
         const uint32_t w = reinterpret_cast<const uint32_t*>(stage)[rr * 32];
         sv[rr] = ((w >> lane) & 1u) ? -1.f : 1.f;
@@ -505,26 +532,25 @@ __global__ void __launch_bounds__(kPanelWarps * 32)
       }
     }
     __syncwarp();
-    // --- scatter into the row's nonzeros ---------------------------------
+    // --- scatter each row's S column into its nonzeros --------------------
 #pragma unroll
-    for (int rr = 0; rr < 4; ++rr) {
-      const int64_t jj = jb + rr;
-      if (jj >= r1) break;
-      const int32_t p0 = rowptr[jj], p1 = rowptr[jj + 1];
-      for (int32_t pb = p0; pb < p1; pb += 32) {
-        const int c = min(32, p1 - pb);
-        int32_t kk = -1;
-        float aa = 0.f;
-        if (lane < c) {
-          kk = ccol[pb + lane] - kb0;
-          aa = cval[pb + lane];
+    for (int rr = 0; rr < kBatchRows; ++rr) {
+      const int32_t lo = __shfl_sync(0xffffffffu, rp, rr);
+      const int32_t hi = __shfl_sync(0xffffffffu, rp, rr + 1);
+      for (int32_t e = lo; e < hi; ++e) {
+        if (e - chunk >= 32) {  // warp-uniform: next chunk of nonzeros
+          chunk += 32;
+          kk = -1;
+          aa = 0.f;
+          if (chunk + lane < p_end) {
+            kk = ccol[chunk + lane] - kb0;
+            aa = cval[chunk + lane];
+          }
         }
-        for (int t = 0; t < c; ++t) {
-          const int32_t kt = __shfl_sync(0xffffffffu, kk, t);
-          const float at = __shfl_sync(0xffffffffu, aa, t);
-          if (static_cast<uint32_t>(kt) < static_cast<uint32_t>(nbw))
-            atomicAdd(&acc[kt * kPanelRows + lane], at * sv[rr]);
-        }
+        const int32_t kt = __shfl_sync(0xffffffffu, kk, e - chunk);
+        const float at = __shfl_sync(0xffffffffu, aa, e - chunk);
+        if (static_cast<uint32_t>(kt) < static_cast<uint32_t>(nbw))
+          atomicAdd(&acc[kt * kPanelRows + lane], at * sv[rr]);
       }
     }
   }
@@ -532,10 +558,16 @@ __global__ void __launch_bounds__(kPanelWarps * 32)
   float* out = partial + (static_cast<int64_t>(g) * n + kb0) * d +
                static_cast<int64_t>(tile) * kPanelRows;
   for (int t = threadIdx.x; t < nbw * kPanelRows; t += blockDim.x) {
-    const int kk = t >> 5, i = t & 31;
-    if (i < rows_valid) out[static_cast<int64_t>(kk) * d + i] = acc[t];
+    const int kk2 = t >> 5, i = t & 31;
+    if (i < rows_valid) out[static_cast<int64_t>(kk2) * d + i] = acc[t];
   }
-  if (gen_count && lane == 0 && generated) atomicAdd(gen_count, generated);
+  if (gen_count) {
+    // lanes 0, 8, 16, 24 counted different rows: sum over the warp
+    unsigned long long tot = generated;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
+    if (lane == 0 && tot) atomicAdd(gen_count, tot);
+  }
 }
 
 // A_hat = sum over g of partial[g] in the fixed order g = 0, 1, ...
