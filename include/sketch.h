@@ -133,6 +133,27 @@ int sketch_get_plan(sketch_t h, const sketch_csc* A, sketch_plan* out,
 int sketch_apply(sketch_t h, const sketch_csc* A, float* Ahat,
                  sketch_stream_t stream);
 
+/* A_hat = S A like sketch_apply, but without allocating anything: for
+ * callers that cannot have a library allocate device memory while they run
+ * (for instance when another allocator owns the device's memory, or in a
+ * latency-critical loop where cudaMalloc / cudaFree would synchronise the
+ * device).  The paper has no counterpart; this is a deployment variant.
+ * It always runs the PANEL kernel with a single row group (A_hat written
+ * directly), and its scratch -- the device CSR copy of A -- is a fixed
+ * array of about 10 MiB inside the library that every GPU loading the
+ * library keeps until the process exits.
+ *   Limits: A->m <= 262,144 and A->nnz <= 1,048,576, otherwise
+ *   SKETCH_ERR_UNSUPPORTED.
+ *   Sharing: every call uses the same array and finds the previous call's
+ *   contents in it (cleared where needed); calls whose work overlaps on the
+ *   GPU race and must be serialised by the caller.
+ *   Set-up: the first call on a device looks up the array's address; make
+ *   that call before any stream capture begins.
+ *   Out-of-range row indices are skipped but not reported.
+ * Asynchronous on `stream`.  Errors as for sketch_apply. */
+int sketch_apply_noalloc(sketch_t h, const sketch_csc* A, float* Ahat,
+                         sketch_stream_t stream);
+
 /* Message for the last error returned on this handle ("" if none). */
 const char* sketch_last_error(sketch_t h);
 

@@ -83,6 +83,7 @@ SIGNATURES = [
     ("sketch_set_plan", _I32, [_VP, ctypes.POINTER(sketch_plan)]),
     ("sketch_get_plan", _I32, [_VP, _CSCP, ctypes.POINTER(sketch_plan), _VP]),
     ("sketch_apply", _I32, [_VP, _CSCP, _VP, _VP]),
+    ("sketch_apply_noalloc", _I32, [_VP, _CSCP, _VP, _VP]),
     ("sketch_last_error", ctypes.c_char_p, [_VP]),
     ("sketch_device_status", _I32, [_VP, _VP]),
     ("sketch_validate_csc", _I32, [_CSCP, _VP]),
@@ -210,6 +211,14 @@ class Sketch:
         _check(load().sketch_apply(self.h, ctypes.byref(A.desc),
                                    ctypes.c_void_p(out.data_ptr()),
                                    _stream_ptr(stream)), self.h)
+        return out
+
+    def apply_noalloc(self, A: DeviceCSC, out, stream=None):
+        """sketch_apply_noalloc: same result as apply(); allocates nothing
+        (`out` must be a preallocated n x d float32 tensor)."""
+        _check(load().sketch_apply_noalloc(self.h, ctypes.byref(A.desc),
+                                           ctypes.c_void_p(out.data_ptr()),
+                                           _stream_ptr(stream)), self.h)
         return out
 
     def device_status(self, stream=None):
