@@ -47,15 +47,23 @@ def parse():
     ap.add_argument("--workload", default="skew_large")
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="budget of the oracle's CPU-baseline sample")
+    # profiling aids (the default run uses none of them)
+    ap.add_argument("--rows", type=int, default=2_000_000,
+                    help="rows of A (smaller cases for ncu captures)")
+    ap.add_argument("--dists", default="pm1,uniform,normal")
+    ap.add_argument("--mode", choices=("auto", "regen", "panel", "tile"),
+                    default="auto", help="force one kernel family")
+    ap.add_argument("--no-cpu", action="store_true",
+                    help="skip the oracle's CPU baseline")
     return ap.parse_args()
 
 
-def workload_config():
+def workload_config(rows=2_000_000):
     from paper_2310_15419_gb300 import inputs
-    return {"workload": "skew_large: m=2,000,000 n=1,000 d=3,000, power-law "
+    return {"workload": "skew_large: m=%s n=1,000 d=3,000, power-law "
                         "rows (alpha=2.1, mean 5/row), FP32 U(-1,1) values; "
-                        "S swept over +-1, U(-1,1), N(0,1)",
-            "m": 2_000_000, "n": 1000, "d": inputs.SKEW_LARGE_D,
+                        "S swept over +-1, U(-1,1), N(0,1)" % format(rows, ","),
+            "m": rows, "n": 1000, "d": inputs.SKEW_LARGE_D,
             "seed_A": 2, "seed_S": 1}
 
 
@@ -189,14 +197,25 @@ def run_ours(args):
         tdist.init_process_group("nccl")
         dist_pg = tdist
 
-    cfg = workload_config()
+    global DISTS
+    DISTS = tuple(args.dists.split(","))
+    cfg = workload_config(args.rows)
     d = cfg["d"]
-    A = inputs.skew_large(seed=cfg["seed_A"])
+    A = inputs.skew_large(seed=cfg["seed_A"], m=args.rows)
     dA = capi.DeviceCSC(A)
     sms = torch.cuda.get_device_properties(local).multi_processor_count
     rates = generator_rates(torch, capi, sms)
 
     sketches = {dist: capi.Sketch(A.m, A.n, d, dist, seed=cfg["seed_S"]) for dist in DISTS}
+    if args.mode != "auto":
+        for dist, sk in sketches.items():
+            if args.mode == "regen":
+                sk.set_plan(capi.SKETCH_MODE_REGEN, q_tiles=4, split=8)
+            elif args.mode == "panel":
+                sk.set_plan(capi.SKETCH_MODE_PANEL, n_block=min(A.n, 1024), row_groups=40)
+            else:
+                sk.set_plan(capi.SKETCH_MODE_TILE, panel_rows=1536, row_groups=80,
+                            cols_per_warp=64 if A.n > 256 else 16)
     outs = {dist: torch.empty((A.n, d), dtype=torch.float32, device="cuda") for dist in DISTS}
     for dist in DISTS:                      # first call tunes the plan
         sketches[dist].apply(dA, outs[dist])
@@ -310,7 +329,7 @@ def run_ours(args):
 
     # ---- CPU baseline: the oracle on a bounded row sample (rank 0, N = 1)
     cpu = None
-    if rank == 0 and world == 1:
+    if rank == 0 and world == 1 and not args.no_cpu:
         cpu, _ = cpu_baseline(A, d, args.cpu_seconds / len(DISTS))
 
     if rank == 0:
@@ -347,8 +366,8 @@ def run_reference(args):
     if rank != 0:
         return
     from paper_2310_15419_gb300 import inputs
-    cfg = workload_config()
-    A = inputs.skew_large(seed=cfg["seed_A"])
+    cfg = workload_config(args.rows)
+    A = inputs.skew_large(seed=cfg["seed_A"], m=args.rows)
     budget = max(0.3, 150.0 / max(1, args.steps + args.warmup))
     for _ in range(args.warmup):
         cpu_baseline(A, cfg["d"], budget / 3)

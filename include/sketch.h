@@ -69,12 +69,15 @@ enum sketch_dtype { SKETCH_F32 = 0, SKETCH_BF16 = 1 };
 
 /* Kernel families (Sec. 2.2): REGEN = variant kji (Alg. 3), every nonzero
  * regenerates its column of S; PANEL = variant jki (Alg. 4), each nonempty
- * row of A generates its column of S once per tile.  AUTO lets the tuner
- * choose per shape. */
+ * row of A generates its column of S once per tile and scatters it into the
+ * row's nonzeros; TILE = the three-level blocking of Sec. 3.1's model
+ * (S_sub d1 x m1 generated once, reused by every column of A_sub m1 x n1),
+ * swept in CSC order.  AUTO lets the tuner choose per shape. */
 enum sketch_mode {
   SKETCH_MODE_AUTO = 0,
   SKETCH_MODE_REGEN = 1,
-  SKETCH_MODE_PANEL = 2
+  SKETCH_MODE_PANEL = 2,
+  SKETCH_MODE_TILE = 3
 };
 
 /* A sparse m x n matrix in CSC.  All pointers are device pointers owned by
@@ -87,17 +90,20 @@ typedef struct {
   int32_t dtype;          /* SKETCH_F32 or SKETCH_BF16                      */
 } sketch_csc;
 
-/* Launch plan (Alg. 1's block sizes mapped onto the GPU).  Zero fields mean
- * "choose".  REGEN: each work item is one column of A times a tile of
- * 128*q_tiles rows of S; `split` warps share a column's nonzeros.  PANEL:
- * a CTA owns 32 rows of S, `n_block` columns and one of `row_groups`
- * contiguous row ranges of A. */
+/* Launch plan (Alg. 1's block sizes mapped onto the GPU).  REGEN: each work
+ * item is one column of A times a tile of 128*q_tiles rows of S; `split`
+ * warps share a column's nonzeros.  PANEL: a CTA owns 32 rows of S,
+ * `n_block` columns and one of `row_groups` contiguous row ranges of A.
+ * TILE: a CTA owns 32 rows of S (d1), 16*cols_per_warp columns (n1) and one
+ * of `row_groups` ranges of panels of `panel_rows` rows of A (m1). */
 typedef struct {
-  int32_t mode;        /* sketch_mode                                  */
-  int32_t q_tiles;     /* REGEN: 1..4 blocks of 128 rows of S per warp */
-  int32_t split;       /* REGEN: 1, 2, 4 or 8 warps per column          */
-  int32_t n_block;     /* PANEL: columns per CTA (<= 1536)              */
-  int32_t row_groups;  /* PANEL: number of row ranges of A              */
+  int32_t mode;          /* sketch_mode                                   */
+  int32_t q_tiles;       /* REGEN: 1..4 blocks of 128 rows of S per warp  */
+  int32_t split;         /* REGEN: 1, 2, 4 or 8 warps per column           */
+  int32_t n_block;       /* PANEL: columns per CTA (<= 1536)               */
+  int32_t row_groups;    /* PANEL, TILE: number of row ranges of A         */
+  int32_t panel_rows;    /* TILE: rows of A per panel, 8..1664 (m1)        */
+  int32_t cols_per_warp; /* TILE: 4, 16 or 64                              */
 } sketch_plan;
 
 /* Create a sketch handle for A (m x n) and S (d x m) with the distribution

@@ -29,7 +29,7 @@ SKETCH_ERR_UNSUPPORTED = -7
 
 SKETCH_PM1, SKETCH_UNIFORM, SKETCH_NORMAL = 0, 1, 2
 SKETCH_F32, SKETCH_BF16 = 0, 1
-SKETCH_MODE_AUTO, SKETCH_MODE_REGEN, SKETCH_MODE_PANEL = 0, 1, 2
+SKETCH_MODE_AUTO, SKETCH_MODE_REGEN, SKETCH_MODE_PANEL, SKETCH_MODE_TILE = 0, 1, 2, 3
 
 DIST_NAMES = {"pm1": SKETCH_PM1, "uniform": SKETCH_UNIFORM,
               "normal": SKETCH_NORMAL}
@@ -51,7 +51,8 @@ class sketch_csc(ctypes.Structure):
 class sketch_plan(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("q_tiles", ctypes.c_int32),
                 ("split", ctypes.c_int32), ("n_block", ctypes.c_int32),
-                ("row_groups", ctypes.c_int32)]
+                ("row_groups", ctypes.c_int32), ("panel_rows", ctypes.c_int32),
+                ("cols_per_warp", ctypes.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -192,8 +193,9 @@ class Sketch:
             pass
 
     def set_plan(self, mode=SKETCH_MODE_AUTO, q_tiles=0, split=0, n_block=0,
-                 row_groups=0):
-        p = sketch_plan(mode, q_tiles, split, n_block, row_groups)
+                 row_groups=0, panel_rows=0, cols_per_warp=0):
+        p = sketch_plan(mode, q_tiles, split, n_block, row_groups, panel_rows,
+                        cols_per_warp)
         _check(load().sketch_set_plan(self.h, ctypes.byref(p)), self.h)
 
     def get_plan(self, A: DeviceCSC, stream=None) -> dict:

@@ -53,6 +53,28 @@ struct PanelArgs {
 size_t panel_smem_bytes(int32_t n_block);
 cudaError_t launch_panel(const PanelArgs& a, cudaStream_t s, int* launches);
 
+struct TileArgs {
+  int32_t m, n, d;
+  int64_t nnz;
+  int32_t dtype;
+  const int32_t* colptr;
+  const int32_t* rowidx;
+  const void* values;
+  float* Ahat;
+  uint32_t k0, k1, stream_id;
+  int32_t dist;
+  int32_t R;    // rows of A per panel (m1)
+  int32_t G;    // row groups (partial sums)
+  int32_t cpw;  // columns per warp: 4, 16 or 64 (n1 = 16 * cpw per CTA)
+  int* status;
+  unsigned long long* gen_count;
+};
+size_t tile_workspace_bytes(int64_t m, int64_t n, int64_t d, int64_t nnz,
+                            int32_t R, int32_t G);
+size_t tile_smem_bytes(int32_t R);
+cudaError_t launch_tile(const TileArgs& a, void* ws, cudaStream_t s,
+                        int* launches);
+
 cudaError_t launch_validate(int32_t m, int32_t n, int64_t nnz,
                             const int32_t* colptr, const int32_t* rowidx,
                             int* status, cudaStream_t s);

@@ -75,6 +75,27 @@ int ensure_workspace(sketch_t h, size_t bytes) {
 
 static size_t align256(size_t b) { return (b + 255) / 256 * 256; }
 
+// TILE plan for a panel height R: columns per warp covering n (up to 1024
+// per CTA), and row groups that fill the GPU and keep each column's partial
+// sums to ~512 terms.
+sketch_plan tile_plan(const sketch_s* h, const sketch_csc* A, int32_t R) {
+  sketch_plan p{};
+  p.mode = SKETCH_MODE_TILE;
+  p.panel_rows = R;
+  p.cols_per_warp = A->n <= 64 ? 4 : A->n <= 256 ? 16 : 64;
+  const int64_t tiles = (h->d + 31) / 32;
+  const int64_t cblocks = (A->n + 16 * p.cols_per_warp - 1) / (16 * p.cols_per_warp);
+  const int64_t P = (A->m + R - 1) / R;
+  const double avg_col = A->n > 0 ? double(A->nnz) / double(A->n) : 0.0;
+  const int per_sm = R <= 768 ? 2 : 1;
+  int64_t g_fill = (2LL * per_sm * num_sms() + tiles * cblocks - 1) / (tiles * cblocks);
+  int64_t g_acc = static_cast<int64_t>(std::ceil(avg_col / 512.0));
+  int64_t g = std::max<int64_t>({1, g_fill, g_acc});
+  g = std::min<int64_t>({g, P, 4096});
+  p.row_groups = static_cast<int32_t>(std::max<int64_t>(1, g));
+  return p;
+}
+
 // Heuristic plan (used when tuning is off or not possible).
 sketch_plan heuristic_plan(const sketch_s* h, const sketch_csc* A) {
   sketch_plan p{};
@@ -85,9 +106,7 @@ sketch_plan heuristic_plan(const sketch_s* h, const sketch_csc* A) {
     p.q_tiles = std::max(1, q);
     p.split = avg_col >= 4096 ? 8 : avg_col >= 1024 ? 4 : avg_col >= 256 ? 2 : 1;
   } else {
-    p.mode = SKETCH_MODE_PANEL;
-    p.n_block = static_cast<int32_t>(std::min<int64_t>(A->n, 1024));
-    p.row_groups = default_row_groups(h, A, p.n_block);
+    p = tile_plan(h, A, 1536);
   }
   return p;
 }
@@ -109,6 +128,8 @@ int32_t default_row_groups(const sketch_s* h, const sketch_csc* A,
 
 size_t plan_workspace_bytes(const sketch_s* h, const sketch_csc* A,
                             const sketch_plan& p) {
+  if (p.mode == SKETCH_MODE_TILE)
+    return tile_workspace_bytes(A->m, A->n, h->d, A->nnz, p.panel_rows, p.row_groups);
   if (p.mode != SKETCH_MODE_PANEL) return 0;
   size_t b = align256(csr_workspace_bytes(A->m, A->nnz));
   if (p.row_groups > 1)
@@ -125,6 +146,13 @@ int check_plan(sketch_t h, const sketch_plan& p) {
   } else if (p.mode == SKETCH_MODE_PANEL) {
     if (p.n_block < 1 || p.n_block > 1536)
       return fail(h, SKETCH_ERR_ARG, "n_block must be 1..1536");
+    if (p.row_groups < 1 || p.row_groups > 65535)
+      return fail(h, SKETCH_ERR_ARG, "row_groups must be 1..65535");
+  } else if (p.mode == SKETCH_MODE_TILE) {
+    if (p.panel_rows < 8 || p.panel_rows > 1664)
+      return fail(h, SKETCH_ERR_ARG, "panel_rows must be 8..1664");
+    if (p.cols_per_warp != 4 && p.cols_per_warp != 16 && p.cols_per_warp != 64)
+      return fail(h, SKETCH_ERR_ARG, "cols_per_warp must be 4, 16 or 64");
     if (p.row_groups < 1 || p.row_groups > 65535)
       return fail(h, SKETCH_ERR_ARG, "row_groups must be 1..65535");
   } else if (p.mode != SKETCH_MODE_AUTO) {
@@ -172,6 +200,32 @@ int run_plan(sketch_t h, const sketch_csc* A, float* Ahat,
     h->launches += 1;
     return e == cudaSuccess ? SKETCH_OK : cuda_fail(h, e, "regen kernel");
   }
+  if (p.mode == SKETCH_MODE_TILE) {
+    TileArgs a{};
+    a.m = static_cast<int32_t>(A->m);
+    a.n = static_cast<int32_t>(A->n);
+    a.d = static_cast<int32_t>(h->d);
+    a.nnz = A->nnz;
+    a.dtype = A->dtype;
+    a.colptr = A->colptr;
+    a.rowidx = A->rowidx;
+    a.values = A->values;
+    a.Ahat = Ahat;
+    a.k0 = h->k0;
+    a.k1 = h->k1;
+    a.stream_id = h->stream_id;
+    a.dist = h->dist;
+    a.R = p.panel_rows;
+    a.G = std::min<int32_t>(p.row_groups,
+                            static_cast<int32_t>((A->m + p.panel_rows - 1) / p.panel_rows));
+    a.cpw = p.cols_per_warp;
+    a.status = status;
+    a.gen_count = gen;
+    int nl = 0;
+    cudaError_t e = launch_tile(a, ws, s, &nl);
+    h->launches += nl;
+    return e == cudaSuccess ? SKETCH_OK : cuda_fail(h, e, "tile kernel");
+  }
   // PANEL
   CsrView csr{};
   int nl = 0;
@@ -214,6 +268,13 @@ static std::vector<sketch_plan> candidates(const sketch_s* h, const sketch_csc* 
         if (o.mode == p.mode && o.q_tiles == p.q_tiles && o.split == p.split) dup = true;
       if (!dup) c.push_back(p);
     }
+  }
+  // TILE with one or two CTAs per SM
+  for (int32_t R : {1536, 768}) {
+    sketch_plan p = tile_plan(h, A, R);
+    if (tile_workspace_bytes(A->m, A->n, h->d, A->nnz, R, p.row_groups) <=
+        (size_t(8) << 30))
+      c.push_back(p);
   }
   // PANEL only where rows are reused (Alg. 4 pays off) or for U / N
   const size_t csr_bytes = csr_workspace_bytes(A->m, A->nnz);

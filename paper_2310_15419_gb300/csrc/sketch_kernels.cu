@@ -623,6 +623,263 @@ cudaError_t launch_panel(const PanelArgs& a, cudaStream_t s, int* launches) {
   return e;
 }
 
+
+// ---------------------------------------------------------------------------
+// TILE: the three-level blocking of Sec. 3.1 (S_sub d1 x m1, A_sub m1 x n1).
+// A CTA owns a tile of 32 rows of S (d1 = 32) and a range of row panels of A
+// (m1 = R rows each) for a block of columns (n1 = 16 * CPW).  Per panel it
+// generates S(tile, panel) ONCE into shared memory -- d1 * m1 entries, the
+// minimum -- then every warp sweeps its columns in CSC order with register
+// accumulators (lane = row of S), reading S from shared memory.  No atomics;
+// each output is written once per row group, so results are deterministic.
+// ---------------------------------------------------------------------------
+constexpr int kTileWarps = 16;
+
+// Panel-major copy of A for TILE: nonzeros sorted by (panel, column, row),
+// each stored as (row within its panel, value bits).  For panel p and column
+// k the nonzeros are packed[off[p * (n + 1) + k] .. off[p * (n + 1) + k + 1]),
+// so a warp's contiguous column range is one contiguous range of memory.
+
+// pp[p * n + k] = first position of column k whose row is >= p * R
+// (p = 0..P): a binary search over the column's sorted rows.
+__global__ void k_panel_pointers(int32_t n, int32_t P, int32_t R,
+                                 const int32_t* __restrict__ colptr,
+                                 const int32_t* __restrict__ rowidx,
+                                 int32_t* __restrict__ pp) {
+  const int64_t total = static_cast<int64_t>(P + 1) * n;
+  for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+       t < total; t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int32_t p = static_cast<int32_t>(t / n), k = static_cast<int32_t>(t % n);
+    int32_t lo = colptr[k], hi = colptr[k + 1];
+    const int64_t key = static_cast<int64_t>(p) * R;
+    while (lo < hi) {
+      const int32_t mid = lo + ((hi - lo) >> 1);
+      if (rowidx[mid] < key) lo = mid + 1; else hi = mid;
+    }
+    pp[t] = lo;
+  }
+}
+
+// cnt[p * (n + 1) + k] = pp[p + 1][k] - pp[p][k]; slot (p, n) and the final
+// cell are 0, so an exclusive scan gives the panel-major offsets.
+__global__ void k_panel_counts(int32_t n, int32_t P, const int32_t* __restrict__ pp,
+                               int32_t* __restrict__ cnt) {
+  const int64_t cells = static_cast<int64_t>(P) * (n + 1) + 1;
+  for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+       t < cells; t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t p = t / (n + 1), k = t % (n + 1);
+    cnt[t] = (p < P && k < n) ? pp[(p + 1) * n + k] - pp[p * n + k] : 0;
+  }
+}
+
+// One thread per (panel, column) segment copies it to its panel-major slot
+// as (row within the panel, value bits).  A row outside the panel (unsorted
+// or out-of-range input) becomes (0, 0.0) and is flagged.
+template <typename VT>
+__global__ void k_panel_copy(int32_t n, int32_t P, int32_t R, int32_t m,
+                             const int32_t* __restrict__ rowidx,
+                             const VT* __restrict__ vals,
+                             const int32_t* __restrict__ pp,
+                             const int32_t* __restrict__ off,
+                             int2* __restrict__ packed, int* status) {
+  const int64_t total = static_cast<int64_t>(P) * n;
+  for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+       t < total; t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t p = t / n, k = t % n;
+    const int32_t lo = pp[t], hi = pp[t + n];
+    int32_t dst = off[p * (n + 1) + k];
+    const int32_t j0 = static_cast<int32_t>(p * R);
+    for (int32_t e = lo; e < hi; ++e, ++dst) {
+      const int32_t jl = rowidx[e] - j0;
+      if (static_cast<uint32_t>(jl) < static_cast<uint32_t>(R) && j0 + jl < m) {
+        packed[dst] = make_int2(jl, __float_as_int(to_f32(vals[e])));
+      } else {
+        atomicOr(status, kStatusBadRow);
+        packed[dst] = make_int2(0, 0);
+      }
+    }
+  }
+}
+
+template <int DIST, int CPW>
+__global__ void __launch_bounds__(kTileWarps * 32, 1)
+    k_tile(int32_t m, int32_t n, int32_t d, int32_t R, int32_t P, int32_t G,
+           const int2* __restrict__ packed, const int32_t* __restrict__ off,
+           float* __restrict__ out, uint32_t k0, uint32_t k1,
+           uint32_t stream_id, unsigned long long* gen_count) {
+  extern __shared__ __align__(16) float S_tile[];  // [R][32]
+  const int tile = blockIdx.x;
+  const int g = blockIdx.z;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // this warp's columns: kw0 .. kw0 + ncol - 1 (contiguous)
+  const int32_t kw0 = blockIdx.y * (kTileWarps * CPW) + warp * CPW;
+  const int32_t ncol = max(0, min(CPW, n - kw0));
+  const int32_t pa = static_cast<int32_t>(static_cast<int64_t>(P) * g / G);
+  const int32_t pb = static_cast<int32_t>(static_cast<int64_t>(P) * (g + 1) / G);
+  const int rows_valid = min(32, d - tile * 32);
+  constexpr int OFFR = (CPW + 32) / 32;  // registers holding CPW + 1 offsets
+
+  float acc[CPW];
+#pragma unroll
+  for (int c = 0; c < CPW; ++c) acc[c] = 0.f;
+  unsigned long long generated = 0;
+
+  for (int32_t p = pa; p < pb; ++p) {
+    const int32_t j0 = p * R;
+    const int32_t rows = min(R, m - j0);
+    // ---- this warp's column offsets for the panel, and an L1 prefetch of
+    //      its (contiguous) nonzeros, issued before the S tile is generated
+    int32_t offv[OFFR];
+    const int32_t* offp = off + static_cast<int64_t>(p) * (n + 1) + kw0;
+#pragma unroll
+    for (int u = 0; u < OFFR; ++u) {
+      const int c = lane + 32 * u;
+      offv[u] = (ncol > 0 && c <= ncol) ? offp[c] : 0;
+    }
+    if (ncol > 0) {
+      const int32_t e_lo = __shfl_sync(0xffffffffu, offv[0], 0);
+      const int32_t e_hi = __shfl_sync(0xffffffffu, offv[ncol >> 5], ncol & 31);
+      for (int32_t e = e_lo + 16 * lane; e < e_hi; e += 16 * 32)
+        asm volatile("prefetch.global.L1 [%0];" ::"l"(packed + e));
+    }
+    // ---- S(tile, j0 .. j0 + rows) once into shared memory ---------------
+    for (int idx = threadIdx.x; idx < rows * 8; idx += kTileWarps * 32) {
+      const int jl = idx >> 3, q = idx & 7;
+      const uint32_t j = static_cast<uint32_t>(j0 + jl);
+      float4 v;
+      if constexpr (DIST == kPM1) {
+        const uint4 x = philox_block(static_cast<uint32_t>(tile >> 2), j,
+                                     stream_id, k0, k1);
+        const int wsel = tile & 3;
+        const uint32_t w = (wsel == 0 ? x.x : wsel == 1 ? x.y : wsel == 2 ? x.z : x.w) >> (4 * q);
+        v = make_float4((w & 1u) ? -1.f : 1.f, (w & 2u) ? -1.f : 1.f,
+                        (w & 4u) ? -1.f : 1.f, (w & 8u) ? -1.f : 1.f);
+      } else {
+        v = four_entries<DIST>(philox_block(static_cast<uint32_t>(tile * 8 + q), j,
+                                            stream_id, k0, k1));
+      }
+      *reinterpret_cast<float4*>(&S_tile[jl * 32 + 4 * q]) = v;
+    }
+    generated += static_cast<unsigned long long>(rows) * rows_valid;
+    __syncthreads();
+    // ---- sweep the columns: broadcast loads of (row, value), S from smem --
+#pragma unroll
+    for (int c = 0; c < CPW; ++c) {
+      if (c < ncol) {  // warp-uniform
+        const int32_t lo = __shfl_sync(0xffffffffu, offv[c >> 5], c & 31);
+        const int32_t hi = __shfl_sync(0xffffffffu, offv[(c + 1) >> 5], (c + 1) & 31);
+        float v = 0.f;
+#pragma unroll 4
+        for (int32_t e = lo; e < hi; ++e) {
+          const int2 ja = packed[e];  // same address in every lane: broadcast
+          v = fmaf(__int_as_float(ja.y), S_tile[ja.x * 32 + lane], v);
+        }
+        acc[c] += v;
+      }
+    }
+    __syncthreads();
+  }
+  // ---- write this row group's partial sums -------------------------------
+#pragma unroll
+  for (int c = 0; c < CPW; ++c) {
+    if (c < ncol && lane < rows_valid)
+      out[(static_cast<int64_t>(g) * n + kw0 + c) * d + tile * 32 + lane] = acc[c];
+  }
+  if (gen_count && threadIdx.x == 0 && generated) atomicAdd(gen_count, generated);
+}
+
+size_t tile_workspace_bytes(int64_t m, int64_t n, int64_t d, int64_t nnz,
+                            int32_t R, int32_t G) {
+  const int64_t P = (m + R - 1) / R;
+  const int64_t cells = P * (n + 1) + 1;
+  size_t b = align256(nnz * sizeof(int2)) + align256((P + 1) * n * sizeof(int32_t)) +
+             2 * align256(cells * sizeof(int32_t)) +
+             align256(static_cast<size_t>(scan_levels_bytes(cells)));
+  if (G > 1) b += align256(static_cast<size_t>(G) * n * d * sizeof(float));
+  return b;
+}
+
+size_t tile_smem_bytes(int32_t R) { return static_cast<size_t>(R) * 32 * sizeof(float); }
+
+cudaError_t launch_tile(const TileArgs& a, void* ws, cudaStream_t s, int* launches) {
+  if (a.R < 8 || a.G < 1 || a.cpw < 1) return cudaErrorInvalidValue;
+  const int64_t P = (static_cast<int64_t>(a.m) + a.R - 1) / a.R;
+  const int64_t cells = P * (a.n + 1) + 1;
+  char* p = static_cast<char*>(ws);
+  int2* packed = reinterpret_cast<int2*>(p);
+  p += align256(a.nnz * sizeof(int2));
+  int32_t* pp = reinterpret_cast<int32_t*>(p);
+  p += align256((P + 1) * a.n * sizeof(int32_t));
+  int32_t* cnt = reinterpret_cast<int32_t*>(p);
+  p += align256(cells * sizeof(int32_t));
+  int32_t* off = reinterpret_cast<int32_t*>(p);
+  p += align256(cells * sizeof(int32_t));
+  char* scan_tmp = p;
+  p += align256(static_cast<size_t>(scan_levels_bytes(cells)));
+  float* partial = reinterpret_cast<float*>(p);
+  const int sms = num_sms();
+  cudaError_t e;
+  {
+    auto grid_for = [&](int64_t work) {
+      return static_cast<unsigned>(std::max<int64_t>(1, std::min<int64_t>((work + 255) / 256, 32LL * sms)));
+    };
+    k_panel_pointers<<<grid_for((P + 1) * a.n), 256, 0, s>>>(
+        a.n, static_cast<int32_t>(P), a.R, a.colptr, a.rowidx, pp);
+    ++*launches;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_panel_counts<<<grid_for(cells), 256, 0, s>>>(a.n, static_cast<int32_t>(P), pp, cnt);
+    ++*launches;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = exclusive_scan(cnt, off, cells, scan_tmp, s, launches)) != cudaSuccess) return e;
+    if (a.dtype == 0)
+      k_panel_copy<float><<<grid_for(P * a.n), 256, 0, s>>>(
+          a.n, static_cast<int32_t>(P), a.R, a.m, a.rowidx,
+          static_cast<const float*>(a.values), pp, off, packed, a.status);
+    else
+      k_panel_copy<__nv_bfloat16><<<grid_for(P * a.n), 256, 0, s>>>(
+          a.n, static_cast<int32_t>(P), a.R, a.m, a.rowidx,
+          static_cast<const __nv_bfloat16*>(a.values), pp, off, packed, a.status);
+    ++*launches;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  const int cols_per_cta = kTileWarps * a.cpw;
+  const int tiles = (a.d + 31) / 32;
+  const int cblocks = (a.n + cols_per_cta - 1) / cols_per_cta;
+  if (cblocks > 65535 || a.G > 65535) return cudaErrorInvalidValue;
+  const dim3 grid(tiles, cblocks, a.G), block(kTileWarps * 32);
+  const size_t smem = tile_smem_bytes(a.R);
+  float* dst = a.G == 1 ? a.Ahat : partial;
+#define SK_TILE_CASE(DD, CC)                                                     \
+  if (a.dist == DD && a.cpw == CC) {                                             \
+    e = cudaFuncSetAttribute(k_tile<DD, CC>,                                     \
+                             cudaFuncAttributeMaxDynamicSharedMemorySize,        \
+                             static_cast<int>(smem));                            \
+    if (e != cudaSuccess) return e;                                              \
+    k_tile<DD, CC><<<grid, block, smem, s>>>(a.m, a.n, a.d, a.R,                 \
+                                             static_cast<int32_t>(P), a.G,       \
+                                             packed, off, dst, a.k0, a.k1,       \
+                                             a.stream_id, a.gen_count);          \
+    ++*launches;                                                                 \
+    launched = true;                                                             \
+  }
+  bool launched = false;
+  SK_TILE_CASE(kPM1, 4) SK_TILE_CASE(kPM1, 16) SK_TILE_CASE(kPM1, 64)
+  SK_TILE_CASE(kUniform, 4) SK_TILE_CASE(kUniform, 16) SK_TILE_CASE(kUniform, 64)
+  SK_TILE_CASE(kNormal, 4) SK_TILE_CASE(kNormal, 16) SK_TILE_CASE(kNormal, 64)
+#undef SK_TILE_CASE
+  if (!launched) return cudaErrorInvalidValue;
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (a.G > 1) {
+    const int64_t total = static_cast<int64_t>(a.n) * a.d;
+    const int64_t blocks = std::min<int64_t>((total + 255) / 256, 16LL * sms);
+    k_reduce_partials<<<static_cast<unsigned>(blocks), 256, 0, s>>>(total, a.G,
+                                                                    partial, a.Ahat);
+    ++*launches;
+    e = cudaGetLastError();
+  }
+  return e;
+}
+
 // ---------------------------------------------------------------------------
 // Validation and test hooks
 // ---------------------------------------------------------------------------

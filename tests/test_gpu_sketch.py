@@ -52,6 +52,9 @@ REGEN_PLANS = [dict(mode=capi.SKETCH_MODE_REGEN, q_tiles=q, split=s)
                for q in (1, 2, 3, 4) for s in (1, 2, 4, 8)]
 PANEL_PLANS = [dict(mode=capi.SKETCH_MODE_PANEL, n_block=nb, row_groups=g)
                for nb, g in ((37, 1), (16, 3), (5, 7), (37, 64))]
+TILE_PLANS = [dict(mode=capi.SKETCH_MODE_TILE, panel_rows=r, row_groups=g,
+                   cols_per_warp=c)
+              for r, g, c in ((1536, 1, 4), (768, 3, 16), (100, 7, 64), (8, 50, 4))]
 
 
 # ---------------------------------------------------------------- generator
@@ -86,7 +89,7 @@ def test_S_entries_match_oracle(dist):
 
 
 # ------------------------------------------------------- exactness / tiling
-@pytest.mark.parametrize("plan", REGEN_PLANS + PANEL_PLANS)
+@pytest.mark.parametrize("plan", REGEN_PLANS + PANEL_PLANS + TILE_PLANS)
 def test_pm1_integer_bit_exact_every_plan(plan):
     # d = 300 and n = 37 leave ragged tails in every tile shape
     A = inputs.integer_uniform(6000, 37, 0.02, seed=3)
@@ -97,7 +100,7 @@ def test_pm1_integer_bit_exact_every_plan(plan):
 
 @pytest.mark.parametrize("dist", ["uniform", "normal"])
 @pytest.mark.parametrize("plan", [REGEN_PLANS[0], REGEN_PLANS[-1],
-                                  REGEN_PLANS[9]] + PANEL_PLANS)
+                                  REGEN_PLANS[9]] + PANEL_PLANS + TILE_PLANS)
 def test_float_within_tolerance_every_plan(dist, plan):
     A = inputs.float_uniform(6000, 37, 0.02, seed=4)
     ref = oracle_sketch(A, 301, dist)
@@ -126,7 +129,7 @@ def test_streams_give_different_S_and_match_oracle():
 def test_bf16_values():
     A, b, _ = inputs.lsq_mixed(m=20000, n=30, density=0.01)
     ref = oracle_sketch(A, 60, "pm1")
-    for plan in (REGEN_PLANS[5], PANEL_PLANS[0]):
+    for plan in (REGEN_PLANS[5], PANEL_PLANS[0], TILE_PLANS[1]):
         got = gpu_sketch(A, 60, "pm1", plan=plan)
         assert rel_fro(got, ref) <= TOL
 
@@ -155,7 +158,7 @@ def test_empty_columns_and_tiny_shapes():
     for d in (1, 3, 4, 5, 129):
         for dist in ("pm1", "uniform"):
             ref = oracle_sketch(A, d, dist)
-            for plan in (None, REGEN_PLANS[0], PANEL_PLANS[2]):
+            for plan in (None, REGEN_PLANS[0], PANEL_PLANS[2], TILE_PLANS[3]):
                 got = gpu_sketch(A, d, dist, plan=plan)
                 if dist == "pm1":
                     assert np.array_equal(got, ref), (d, plan)
@@ -172,7 +175,9 @@ def test_long_column_accuracy():
     A = inputs.CSC(m, 1, np.array([0, rows.size], np.int32), rows,
                    rng.uniform(-1, 1, size=rows.size).astype(np.float32))
     ref = oracle_sketch(A, 256, "uniform")
-    for plan in (REGEN_PLANS[4 * 1 + 0], REGEN_PLANS[4 * 1 + 3], None):
+    for plan in (REGEN_PLANS[4 * 1 + 0], REGEN_PLANS[4 * 1 + 3], None,
+                 dict(mode=capi.SKETCH_MODE_TILE, panel_rows=1536,
+                      row_groups=400, cols_per_warp=4)):
         got = gpu_sketch(A, 256, "uniform", plan=plan)
         assert rel_fro(got, ref) <= TOL, plan
 
@@ -185,7 +190,9 @@ def test_generation_counts():
     for plan, expect in (
             (REGEN_PLANS[6], d * A.nnz),
             (dict(mode=capi.SKETCH_MODE_PANEL, n_block=40, row_groups=3),
-             d * np.unique(A.rowidx).size)):
+             d * np.unique(A.rowidx).size),
+            (dict(mode=capi.SKETCH_MODE_TILE, panel_rows=1000, row_groups=2,
+                  cols_per_warp=4), d * A.m)):
         sk = capi.Sketch(A.m, A.n, d, "uniform", seed=1)
         sk.set_plan(**plan)
         sk.set_counting(True)
@@ -200,7 +207,7 @@ def test_bad_row_index_is_reported_not_faulted():
     A.rowidx[3] = 1000 + 17      # out of range
     dA = capi.DeviceCSC(A)
     assert capi.validate_csc(dA) == capi.SKETCH_ERR_CSC
-    for plan in (REGEN_PLANS[0], PANEL_PLANS[0]):
+    for plan in (REGEN_PLANS[0], PANEL_PLANS[0], TILE_PLANS[0]):
         sk = capi.Sketch(A.m, A.n, 64, "pm1", seed=1)
         sk.set_plan(**plan)
         sk.apply(dA)
