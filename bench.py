@@ -214,7 +214,7 @@ def run_ours(args):
             elif args.mode == "panel":
                 sk.set_plan(capi.SKETCH_MODE_PANEL, n_block=min(A.n, 1024), row_groups=40)
             else:
-                sk.set_plan(capi.SKETCH_MODE_TILE, panel_rows=1536, row_groups=80,
+                sk.set_plan(capi.SKETCH_MODE_TILE, panel_rows=1024, row_groups=80,
                             cols_per_warp=64 if A.n > 256 else 16)
     outs = {dist: torch.empty((A.n, d), dtype=torch.float32, device="cuda") for dist in DISTS}
     for dist in DISTS:                      # first call tunes the plan

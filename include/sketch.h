@@ -102,7 +102,7 @@ typedef struct {
   int32_t split;         /* REGEN: 1, 2, 4 or 8 warps per column           */
   int32_t n_block;       /* PANEL: columns per CTA (<= 1536)               */
   int32_t row_groups;    /* PANEL, TILE: number of row ranges of A         */
-  int32_t panel_rows;    /* TILE: rows of A per panel, 8..1664 (m1)        */
+  int32_t panel_rows;    /* TILE: rows of A per panel, 8..1152 (m1)        */
   int32_t cols_per_warp; /* TILE: 4, 16 or 64                              */
 } sketch_plan;
 

@@ -87,7 +87,7 @@ sketch_plan tile_plan(const sketch_s* h, const sketch_csc* A, int32_t R) {
   const int64_t cblocks = (A->n + 16 * p.cols_per_warp - 1) / (16 * p.cols_per_warp);
   const int64_t P = (A->m + R - 1) / R;
   const double avg_col = A->n > 0 ? double(A->nnz) / double(A->n) : 0.0;
-  const int per_sm = R <= 768 ? 2 : 1;
+  const int per_sm = 1;
   int64_t g_fill = (2LL * per_sm * num_sms() + tiles * cblocks - 1) / (tiles * cblocks);
   int64_t g_acc = static_cast<int64_t>(std::ceil(avg_col / 512.0));
   int64_t g = std::max<int64_t>({1, g_fill, g_acc});
@@ -106,7 +106,7 @@ sketch_plan heuristic_plan(const sketch_s* h, const sketch_csc* A) {
     p.q_tiles = std::max(1, q);
     p.split = avg_col >= 4096 ? 8 : avg_col >= 1024 ? 4 : avg_col >= 256 ? 2 : 1;
   } else {
-    p = tile_plan(h, A, 1536);
+    p = tile_plan(h, A, 1024);
   }
   return p;
 }
@@ -149,8 +149,8 @@ int check_plan(sketch_t h, const sketch_plan& p) {
     if (p.row_groups < 1 || p.row_groups > 65535)
       return fail(h, SKETCH_ERR_ARG, "row_groups must be 1..65535");
   } else if (p.mode == SKETCH_MODE_TILE) {
-    if (p.panel_rows < 8 || p.panel_rows > 1664)
-      return fail(h, SKETCH_ERR_ARG, "panel_rows must be 8..1664");
+    if (p.panel_rows < 8 || p.panel_rows > 1152)
+      return fail(h, SKETCH_ERR_ARG, "panel_rows must be 8..1152");
     if (p.cols_per_warp != 4 && p.cols_per_warp != 16 && p.cols_per_warp != 64)
       return fail(h, SKETCH_ERR_ARG, "cols_per_warp must be 4, 16 or 64");
     if (p.row_groups < 1 || p.row_groups > 65535)
@@ -269,8 +269,8 @@ static std::vector<sketch_plan> candidates(const sketch_s* h, const sketch_csc* 
       if (!dup) c.push_back(p);
     }
   }
-  // TILE with one or two CTAs per SM
-  for (int32_t R : {1536, 768}) {
+  // TILE panel heights (the S tile takes R * 128 bytes of shared memory)
+  for (int32_t R : {1024, 512}) {
     sketch_plan p = tile_plan(h, A, R);
     if (tile_workspace_bytes(A->m, A->n, h->d, A->nnz, R, p.row_groups) <=
         (size_t(8) << 30))

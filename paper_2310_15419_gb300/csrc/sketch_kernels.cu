@@ -634,6 +634,7 @@ cudaError_t launch_panel(const PanelArgs& a, cudaStream_t s, int* launches) {
 // each output is written once per row group, so results are deterministic.
 // ---------------------------------------------------------------------------
 constexpr int kTileWarps = 16;
+constexpr int kTileWarpBuf = 512;  // staged nonzeros per warp per panel
 
 // Panel-major copy of A for TILE: nonzeros sorted by (panel, column, row),
 // each stored as (row within its panel, value bits).  For panel p and column
@@ -673,7 +674,8 @@ __global__ void k_panel_counts(int32_t n, int32_t P, const int32_t* __restrict__
 }
 
 // One thread per (panel, column) segment copies it to its panel-major slot
-// as (row within the panel, value bits).  A row outside the panel (unsorted
+// as (32 * row within the panel, value bits): the row pre-scaled to its
+// offset in the [R][32] S tile.  A row outside the panel (unsorted
 // or out-of-range input) becomes (0, 0.0) and is flagged.
 template <typename VT>
 __global__ void k_panel_copy(int32_t n, int32_t P, int32_t R, int32_t m,
@@ -692,7 +694,7 @@ __global__ void k_panel_copy(int32_t n, int32_t P, int32_t R, int32_t m,
     for (int32_t e = lo; e < hi; ++e, ++dst) {
       const int32_t jl = rowidx[e] - j0;
       if (static_cast<uint32_t>(jl) < static_cast<uint32_t>(R) && j0 + jl < m) {
-        packed[dst] = make_int2(jl, __float_as_int(to_f32(vals[e])));
+        packed[dst] = make_int2(jl * 32, __float_as_int(to_f32(vals[e])));
       } else {
         atomicOr(status, kStatusBadRow);
         packed[dst] = make_int2(0, 0);
@@ -707,16 +709,21 @@ __global__ void __launch_bounds__(kTileWarps * 32, 1)
            const int2* __restrict__ packed, const int32_t* __restrict__ off,
            float* __restrict__ out, uint32_t k0, uint32_t k1,
            uint32_t stream_id, unsigned long long* gen_count) {
-  extern __shared__ __align__(16) float S_tile[];  // [R][32]
+  // shared memory: S tile [R][32] floats, then per-warp nonzero buffers
+  extern __shared__ __align__(16) float smem[];
+  float* S_tile = smem;
+  int2* ent_all = reinterpret_cast<int2*>(smem + static_cast<size_t>(R) * 32);
   const int tile = blockIdx.x;
   const int g = blockIdx.z;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int2* ent = ent_all + warp * kTileWarpBuf;
   // this warp's columns: kw0 .. kw0 + ncol - 1 (contiguous)
   const int32_t kw0 = blockIdx.y * (kTileWarps * CPW) + warp * CPW;
   const int32_t ncol = max(0, min(CPW, n - kw0));
   const int32_t pa = static_cast<int32_t>(static_cast<int64_t>(P) * g / G);
   const int32_t pb = static_cast<int32_t>(static_cast<int64_t>(P) * (g + 1) / G);
   const int rows_valid = min(32, d - tile * 32);
+  const float* S_lane = S_tile + lane;
   constexpr int OFFR = (CPW + 32) / 32;  // registers holding CPW + 1 offsets
 
   float acc[CPW];
@@ -727,8 +734,8 @@ __global__ void __launch_bounds__(kTileWarps * 32, 1)
   for (int32_t p = pa; p < pb; ++p) {
     const int32_t j0 = p * R;
     const int32_t rows = min(R, m - j0);
-    // ---- this warp's column offsets for the panel, and an L1 prefetch of
-    //      its (contiguous) nonzeros, issued before the S tile is generated
+    // ---- this warp's column offsets and nonzeros (one contiguous range),
+    //      loaded before the S tile is generated so the loads overlap it
     int32_t offv[OFFR];
     const int32_t* offp = off + static_cast<int64_t>(p) * (n + 1) + kw0;
 #pragma unroll
@@ -736,11 +743,12 @@ __global__ void __launch_bounds__(kTileWarps * 32, 1)
       const int c = lane + 32 * u;
       offv[u] = (ncol > 0 && c <= ncol) ? offp[c] : 0;
     }
+    int32_t e_lo = 0, e_hi = 0;
     if (ncol > 0) {
-      const int32_t e_lo = __shfl_sync(0xffffffffu, offv[0], 0);
-      const int32_t e_hi = __shfl_sync(0xffffffffu, offv[ncol >> 5], ncol & 31);
-      for (int32_t e = e_lo + 16 * lane; e < e_hi; e += 16 * 32)
-        asm volatile("prefetch.global.L1 [%0];" ::"l"(packed + e));
+      e_lo = __shfl_sync(0xffffffffu, offv[0], 0);
+      e_hi = __shfl_sync(0xffffffffu, offv[ncol >> 5], ncol & 31);
+      const int32_t cnt = min(e_hi - e_lo, kTileWarpBuf);
+      for (int32_t t = lane; t < cnt; t += 32) ent[t] = packed[e_lo + t];
     }
     // ---- S(tile, j0 .. j0 + rows) once into shared memory ---------------
     for (int idx = threadIdx.x; idx < rows * 8; idx += kTileWarps * 32) {
@@ -762,17 +770,26 @@ __global__ void __launch_bounds__(kTileWarps * 32, 1)
     }
     generated += static_cast<unsigned long long>(rows) * rows_valid;
     __syncthreads();
-    // ---- sweep the columns: broadcast loads of (row, value), S from smem --
+    // ---- sweep the columns: entries (row * 32, value) broadcast from the
+    //      warp's buffer (or from global memory past its capacity)
+    const int32_t buf_end = e_lo + kTileWarpBuf;
 #pragma unroll
     for (int c = 0; c < CPW; ++c) {
       if (c < ncol) {  // warp-uniform
         const int32_t lo = __shfl_sync(0xffffffffu, offv[c >> 5], c & 31);
         const int32_t hi = __shfl_sync(0xffffffffu, offv[(c + 1) >> 5], (c + 1) & 31);
         float v = 0.f;
+        if (hi <= buf_end) {
 #pragma unroll 4
-        for (int32_t e = lo; e < hi; ++e) {
-          const int2 ja = packed[e];  // same address in every lane: broadcast
-          v = fmaf(__int_as_float(ja.y), S_tile[ja.x * 32 + lane], v);
+          for (int32_t e = lo; e < hi; ++e) {
+            const int2 ja = ent[e - e_lo];
+            v = fmaf(__int_as_float(ja.y), S_lane[ja.x], v);
+          }
+        } else {
+          for (int32_t e = lo; e < hi; ++e) {
+            const int2 ja = packed[e];
+            v = fmaf(__int_as_float(ja.y), S_lane[ja.x], v);
+          }
         }
         acc[c] += v;
       }
@@ -799,7 +816,9 @@ size_t tile_workspace_bytes(int64_t m, int64_t n, int64_t d, int64_t nnz,
   return b;
 }
 
-size_t tile_smem_bytes(int32_t R) { return static_cast<size_t>(R) * 32 * sizeof(float); }
+size_t tile_smem_bytes(int32_t R) {
+  return static_cast<size_t>(R) * 32 * sizeof(float) + kTileWarps * kTileWarpBuf * sizeof(int2);
+}
 
 cudaError_t launch_tile(const TileArgs& a, void* ws, cudaStream_t s, int* launches) {
   if (a.R < 8 || a.G < 1 || a.cpw < 1) return cudaErrorInvalidValue;

@@ -54,7 +54,7 @@ PANEL_PLANS = [dict(mode=capi.SKETCH_MODE_PANEL, n_block=nb, row_groups=g)
                for nb, g in ((37, 1), (16, 3), (5, 7), (37, 64))]
 TILE_PLANS = [dict(mode=capi.SKETCH_MODE_TILE, panel_rows=r, row_groups=g,
                    cols_per_warp=c)
-              for r, g, c in ((1536, 1, 4), (768, 3, 16), (100, 7, 64), (8, 50, 4))]
+              for r, g, c in ((1024, 1, 4), (768, 3, 16), (100, 7, 64), (8, 50, 4))]
 
 
 # ---------------------------------------------------------------- generator
@@ -176,7 +176,7 @@ def test_long_column_accuracy():
                    rng.uniform(-1, 1, size=rows.size).astype(np.float32))
     ref = oracle_sketch(A, 256, "uniform")
     for plan in (REGEN_PLANS[4 * 1 + 0], REGEN_PLANS[4 * 1 + 3], None,
-                 dict(mode=capi.SKETCH_MODE_TILE, panel_rows=1536,
+                 dict(mode=capi.SKETCH_MODE_TILE, panel_rows=1024,
                       row_groups=400, cols_per_warp=4)):
         got = gpu_sketch(A, 256, "uniform", plan=plan)
         assert rel_fro(got, ref) <= TOL, plan
