@@ -186,11 +186,18 @@ typedef struct {
 /* Solve min ||A x - b||_2 (m >= n): A_hat = S A with this handle's S
  * (d = the handle's d, normally 2n), FP64 Householder QR of A_hat -> R,
  * LSQR on A R^{-1} with FP64 residual and norm updates until LSQR's own
- * estimate falls below `tol`, then x = R^{-1} y and Error(x) in FP64.
+ * estimate for the preconditioned system falls below `tol` (the stopping
+ * rule of Sec. 5.4), then x = R^{-1} y and Error(x) = ||A^T(Ax-b)|| /
+ * (||A||_F ||Ax-b||) in FP64.  If Error(x) is still above `tol`, LSQR
+ * continues from the same state with a 10x tighter internal tolerance, for
+ * as long as each round at least halves Error(x) (up to 6 rounds); the
+ * achieved Error(x) is returned in info->error either way (it can sit at
+ * the FP64 floor of the metric for badly scaled, nearly consistent data).
  * b (m) and x (n) are FP64 device pointers.  Synchronous: returns when x
  * and *info are final.  Errors: SKETCH_ERR_ARG (d < n, tol <= 0),
- * SKETCH_ERR_NO_CONVERGENCE (x holds the last iterate), SKETCH_ERR_CSC
- * (a zero column makes R singular), SKETCH_ERR_OOM, SKETCH_ERR_CUDA. */
+ * SKETCH_ERR_NO_CONVERGENCE (maxit reached; x holds the last iterate),
+ * SKETCH_ERR_CSC (a zero column makes R singular), SKETCH_ERR_OOM,
+ * SKETCH_ERR_CUDA. */
 int sketch_lsq_solve(sketch_t h, const sketch_csc* A, const double* b,
                      double* x, double tol, int32_t maxit,
                      sketch_lsq_info* info, sketch_stream_t stream);
@@ -218,6 +225,14 @@ int sketch_debug_S(int32_t dist, uint64_t seed, uint32_t stream_id,
 int sketch_bench_generator(int32_t dist, uint64_t seed, int64_t threads,
                            int64_t blocks_per_thread, float* sink,
                            sketch_stream_t stream);
+
+/* Householder QR of a dense d x n FP64 matrix A (device, column-major,
+ * d >= n) with the kernels sketch_lsq_solve uses (Sec. 5.4): writes R
+ * (n x n, ROW-major, upper triangular; R(k,k) = -sign(x_0)||x||, or x_0 when
+ * the column below the diagonal is already zero) and R^{-1} (n x n,
+ * row-major).  Synchronous; allocates temporary device memory. */
+int sketch_debug_qr(int64_t d, int64_t n, const double* A, double* R,
+                    double* Rinv, sketch_stream_t stream);
 
 /* Number of S entries the last sketch_apply on this handle generated
  * (counted on the device when counting is enabled; synchronous read).

@@ -96,6 +96,7 @@ SIGNATURES = [
     ("sketch_generated_entries", _I64, [_VP, _VP]),
     ("sketch_launch_count", _I64, [_VP]),
     ("sketch_bench_generator", _I32, [_I32, _U64, _I64, _I64, _VP, _VP]),
+    ("sketch_debug_qr", _I32, [_I64, _I64, _VP, _VP, _VP, _VP]),
 ]
 
 
@@ -275,6 +276,20 @@ def bench_generator(dist, seed, threads, blocks_per_thread, sink, stream=None):
                                          int(threads), int(blocks_per_thread),
                                          ctypes.c_void_p(sink.data_ptr()),
                                          _stream_ptr(stream)))
+
+
+def debug_qr(A, stream=None):
+    """R and R^{-1} (row-major n x n) of the device FP64 QR of A (d x n)."""
+    import torch
+    d, n = A.shape
+    a = A.t().contiguous()  # column-major d x n
+    R = torch.empty((n, n), dtype=torch.float64, device=A.device)
+    Ri = torch.empty((n, n), dtype=torch.float64, device=A.device)
+    _check(load().sketch_debug_qr(d, n, ctypes.c_void_p(a.data_ptr()),
+                                  ctypes.c_void_p(R.data_ptr()),
+                                  ctypes.c_void_p(Ri.data_ptr()),
+                                  _stream_ptr(stream)))
+    return R, Ri
 
 
 def debug_S(dist, seed, stream_id, i, j, stream=None):

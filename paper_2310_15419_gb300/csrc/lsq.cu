@@ -1,18 +1,757 @@
-// lsq.cu -- sketch-and-precondition least squares (Sec. 5.4).
+// lsq.cu -- sketch-and-precondition least squares (Sec. 5.4) on the GPU.
+//
+//   1. A_hat = S A (FP32, the sketch kernels; d = the handle's d, normally 2n)
+//   2. Householder QR of A_hat in FP64 -> R  (LAPACK-style reflectors
+//      H = I - tau v v^T, v_0 = 1, R(k,k) = -sign(x_0) ||x||, H = I when the
+//      part below the diagonal is already zero)
+//   3. R^{-1} explicitly (FP64), stored row-major together with R^{-T} so the
+//      two matrix-vector products of every iteration read contiguous rows
+//   4. LSQR (Paige & Saunders 1982) on M = A R^{-1} with FP64 vectors, norms
+//      and recurrences; every reduction runs in a fixed order (deterministic)
+//   5. x = R^{-1} y and Error(x) = ||A^T(Ax-b)|| / (||A||_F ||Ax-b||) in FP64
+//
+// LSQR iterations run as CUDA graphs of kIterPerGraph iterations; every
+// kernel returns at once when the device-side `done` flag is set, and the
+// host reads the flag after each replay.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "common.cuh"
 #include "handle.h"
+#include "internal.h"
 
 namespace sk {
-struct LsqState {};
+
+namespace {
+
+constexpr int kIterPerGraph = 8;
+constexpr int kRedBlocks = 512;  // partial sums of m-vector reductions
+
+struct Scalars {
+  double alpha, beta, inv_beta, rhobar, phibar, anorm2, bnorm;
+  double test1, test2, ynorm, afro2, err_num2, err_res2;
+  double tol;
+  int iters, maxit, done, istop;
+};
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-wide sum in a fixed order; every thread gets the result.
+template <int NT>
+__device__ double block_sum(double v, double* red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (warp == 0) {
+    t = lane < NT / 32 ? red[lane] : 0.0;
+    t = warp_sum(t);
+    if (lane == 0) red[32] = t;
+  }
+  __syncthreads();
+  return red[32];
+}
+
+template <typename VT>
+__device__ __forceinline__ double val_at(const VT* v, int64_t i) {
+  return static_cast<double>(to_f32(v[i]));
+}
+
+// ---------------------------------------------------------------------------
+// QR
+// ---------------------------------------------------------------------------
+__global__ void k_to_double(int64_t total, const float* __restrict__ a,
+                            double* __restrict__ w) {
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+       i < total; i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    w[i] = static_cast<double>(a[i]);
+}
+
+constexpr int kQrThreads = 256;
+
+// Householder reflector of column k (rows k..d-1) of W, in place.
+__device__ void qr_reflector(double* W, int64_t d, int k, double* tau,
+                             double* red) {
+  double* x = W + static_cast<int64_t>(k) * d;
+  double s = 0.0;
+  for (int64_t r = k + 1 + threadIdx.x; r < d; r += blockDim.x) s += x[r] * x[r];
+  const double sigma = block_sum<kQrThreads>(s, red);
+  const double alpha = x[k];
+  if (sigma == 0.0) {  // nothing below the diagonal: H = I
+    if (threadIdx.x == 0) tau[k] = 0.0;
+    return;
+  }
+  const double norm = sqrt(alpha * alpha + sigma);
+  const double beta = alpha >= 0.0 ? -norm : norm;
+  const double scale = 1.0 / (alpha - beta);
+  for (int64_t r = k + 1 + threadIdx.x; r < d; r += blockDim.x) x[r] *= scale;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    tau[k] = (beta - alpha) / beta;
+    x[k] = beta;
+  }
+}
+
+__global__ void __launch_bounds__(kQrThreads)
+    k_qr_first(double* W, int64_t d, double* tau) {
+  __shared__ double red[33];
+  qr_reflector(W, d, 0, tau, red);
+}
+
+// Apply reflector k to columns k+1..n-1 (one CTA per column); the CTA of
+// column k+1 then forms reflector k+1.
+__global__ void __launch_bounds__(kQrThreads)
+    k_qr_step(double* W, int64_t d, int n, int k, double* tau) {
+  __shared__ double red[33];
+  const int c = k + 1 + blockIdx.x;
+  if (c >= n) return;
+  const double t = tau[k];
+  const double* v = W + static_cast<int64_t>(k) * d;
+  double* y = W + static_cast<int64_t>(c) * d;
+  if (t != 0.0) {
+    double s = 0.0;
+    for (int64_t r = k + 1 + threadIdx.x; r < d; r += blockDim.x) s += v[r] * y[r];
+    const double wsum = block_sum<kQrThreads>(s, red) + y[k];
+    const double f = t * wsum;
+    __syncthreads();
+    if (threadIdx.x == 0) y[k] -= f;
+    for (int64_t r = k + 1 + threadIdx.x; r < d; r += blockDim.x) y[r] -= f * v[r];
+    __syncthreads();
+  }
+  if (c == k + 1) qr_reflector(W, d, c, tau, red);
+}
+
+// Rrow = R (upper n x n of W) row-major; flags a zero diagonal.
+__global__ void k_extract_r(const double* __restrict__ W, int64_t d, int n,
+                            double* __restrict__ Rrow, int* status) {
+  const int64_t total = static_cast<int64_t>(n) * n;
+  for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+       t < total; t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int i = static_cast<int>(t / n), c = static_cast<int>(t % n);
+    const double v = c >= i ? W[static_cast<int64_t>(c) * d + i] : 0.0;
+    Rrow[t] = v;
+    if (c == i && v == 0.0) atomicOr(status, 4);
+  }
+}
+
+// X = R^{-1} by back substitution, one warp per column j of X:
+// X[j][j] = 1/R[j][j];  X[i][j] = -(sum_{c=i+1..j} R[i][c] X[c][j]) / R[i][i].
+// Writes Xrow (row-major X) and XTrow (row-major X^T).
+__global__ void k_trtri(const double* __restrict__ Rrow, int n,
+                        double* __restrict__ Xrow, double* __restrict__ XTrow) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = static_cast<int64_t>(gridDim.x) * (blockDim.x >> 5);
+  for (int64_t j = blockIdx.x * static_cast<int64_t>(blockDim.x >> 5) + (threadIdx.x >> 5);
+       j < n; j += warps) {
+    double* xt = XTrow + j * n;  // column j of X, contiguous
+    for (int c = lane; c < n; c += 32) xt[c] = 0.0;
+    __syncwarp();
+    if (lane == 0) xt[j] = 1.0 / Rrow[j * static_cast<int64_t>(n) + j];
+    __syncwarp();
+    for (int64_t i = j - 1; i >= 0; --i) {
+      const double* ri = Rrow + i * n;
+      double s = 0.0;
+      for (int64_t c = i + 1 + lane; c <= j; c += 32) s += ri[c] * xt[c];
+      s = warp_sum(s);
+      if (lane == 0) xt[i] = -s / ri[i];
+      __syncwarp();
+    }
+    for (int64_t i = lane; i < n; i += 32) Xrow[i * n + j] = xt[i];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// LSQR kernels (each returns at once once `done` is set)
+// ---------------------------------------------------------------------------
+// out[i] = sum_c Mrow[i][c] x[c] - sub * prev[i] over the nonzero triangle:
+// c >= i (upper, lower = 0) or c <= i (lower = 1).  One warp per row.
+__global__ void k_gemv_tri(const double* __restrict__ Mrow, int n,
+                           const double* __restrict__ x, double* __restrict__ out,
+                           const double* __restrict__ prev, const Scalars* sc,
+                           int use_beta, int ignore_done, int lower) {
+  if (!ignore_done && sc->done) return;
+  const double sub = use_beta ? sc->beta : 0.0;
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = static_cast<int64_t>(gridDim.x) * (blockDim.x >> 5);
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x >> 5) + (threadIdx.x >> 5);
+       i < n; i += warps) {
+    const double* row = Mrow + i * n;
+    double s = 0.0;
+    if (lower) {
+      for (int64_t c = lane; c <= i; c += 32) s += row[c] * x[c];
+    } else {
+      for (int64_t c = (i & ~31LL) + lane; c < n; c += 32)
+        if (c >= i) s += row[c] * x[c];
+    }
+    s = warp_sum(s);
+    if (lane == 0) out[i] = s - (prev ? sub * prev[i] : 0.0);
+  }
+}
+
+// u[j] <- sum_e val[e] t[col[e]] - alpha * inv_beta * u[j]  (u kept unscaled),
+// partial sums of u^2 per block.  mode 1: r = A x - b (error check).
+template <int NT>
+__global__ void __launch_bounds__(NT)
+    k_spmv_rows(int32_t m, const int32_t* __restrict__ rowptr,
+                const int32_t* __restrict__ ccol, const float* __restrict__ cval,
+                const double* __restrict__ t, double* __restrict__ u,
+                const double* __restrict__ b, double* __restrict__ partial,
+                const Scalars* sc, int mode) {
+  __shared__ double red[33];
+  if (mode == 0 && sc->done) return;
+  const double f = mode == 0 ? sc->alpha * sc->inv_beta : 0.0;
+  double s2 = 0.0;
+  for (int64_t j = blockIdx.x * static_cast<int64_t>(NT) + threadIdx.x; j < m;
+       j += static_cast<int64_t>(gridDim.x) * NT) {
+    double s = 0.0;
+    for (int32_t e = rowptr[j]; e < rowptr[j + 1]; ++e)
+      s += static_cast<double>(cval[e]) * t[ccol[e]];
+    const double nu = mode == 0 ? s - f * u[j] : s - b[j];
+    u[j] = nu;
+    s2 += nu * nu;
+  }
+  s2 = block_sum<NT>(s2, red);
+  if (threadIdx.x == 0) partial[blockIdx.x] = s2;
+}
+
+// out[k] = scale * sum_{e in column k} val[e] u[row[e]],  scale = inv_beta
+// (mode 0) or 1 (mode 1).
+template <typename VT>
+__global__ void k_spmv_cols(int32_t n, const int32_t* __restrict__ colptr,
+                            const int32_t* __restrict__ rowidx,
+                            const VT* __restrict__ vals, const double* __restrict__ u,
+                            double* __restrict__ out, const Scalars* sc, int mode) {
+  if (mode == 0 && sc->done) return;
+  const double scale = mode == 0 ? sc->inv_beta : 1.0;
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = static_cast<int64_t>(gridDim.x) * (blockDim.x >> 5);
+  for (int64_t k = blockIdx.x * static_cast<int64_t>(blockDim.x >> 5) + (threadIdx.x >> 5);
+       k < n; k += warps) {
+    double s = 0.0;
+    for (int32_t e = colptr[k] + lane; e < colptr[k + 1]; e += 32)
+      s += val_at(vals, e) * u[rowidx[e]];
+    s = warp_sum(s);
+    if (lane == 0) out[k] = scale * s;
+  }
+}
+
+// Fixed-order sum of the m-vector partials; what = 0: beta (LSQR step),
+// 1: initial beta = ||b||, 2: ||Ax-b||^2 for the error check.
+__global__ void k_finish_beta(const double* __restrict__ partial, int nparts,
+                              Scalars* sc, int what) {
+  __shared__ double red[33];
+  if (what == 0 && sc->done) return;
+  double s = 0.0;
+  for (int i = threadIdx.x; i < nparts; i += blockDim.x) s += partial[i];
+  s = block_sum<1024>(s, red);
+  if (threadIdx.x == 0) {
+    if (what == 2) {
+      sc->err_res2 = s;
+      return;
+    }
+    const double beta = sqrt(s);
+    sc->beta = beta;
+    sc->inv_beta = beta > 0.0 ? 1.0 / beta : 0.0;
+    if (what == 1) {
+      sc->bnorm = beta;
+      sc->phibar = beta;
+    } else {
+      sc->anorm2 += sc->alpha * sc->alpha + beta * beta;
+    }
+  }
+}
+
+// The n-sized part of an LSQR step (one CTA of 1024 threads).
+// init = 1: v = vraw / alpha, w = v, y = 0, rhobar = alpha (start-up).
+__global__ void __launch_bounds__(1024)
+    k_lsqr_update(int n, double* __restrict__ vraw, double* __restrict__ v,
+                  double* __restrict__ w, double* __restrict__ y, Scalars* sc,
+                  int init) {
+  __shared__ double red[33];
+  if (!init && sc->done) return;
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s += vraw[i] * vraw[i];
+  const double alpha = sqrt(block_sum<1024>(s, red));
+  const double ia = alpha > 0.0 ? 1.0 / alpha : 0.0;
+  if (init) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      v[i] = vraw[i] * ia;
+      w[i] = v[i];
+      y[i] = 0.0;
+    }
+    if (threadIdx.x == 0) {
+      sc->alpha = alpha;
+      sc->rhobar = alpha;
+      sc->anorm2 = 0.0;
+      sc->iters = 0;
+      sc->istop = 0;
+      sc->done = (alpha == 0.0 || sc->beta == 0.0) ? 1 : 0;
+      if (sc->done) sc->istop = 1;
+    }
+    return;
+  }
+  // plane rotation eliminating the subdiagonal beta (new alpha enters here)
+  const double rhobar = sc->rhobar, beta = sc->beta, phibar = sc->phibar;
+  const double rho = sqrt(rhobar * rhobar + beta * beta);
+  const double c = rhobar / rho, sn = beta / rho;
+  const double theta = sn * alpha;
+  const double phi = c * phibar;
+  const double phibar_new = sn * phibar;
+  double y2 = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const double vi = vraw[i] * ia;
+    v[i] = vi;
+    const double yi = y[i] + (phi / rho) * w[i];
+    y[i] = yi;
+    w[i] = vi - (theta / rho) * w[i];
+    y2 += yi * yi;
+  }
+  const double ynorm = sqrt(block_sum<1024>(y2, red));
+  if (threadIdx.x == 0) {
+    sc->alpha = alpha;
+    sc->rhobar = -c * alpha;
+    sc->phibar = phibar_new;
+    const int it = sc->iters + 1;
+    sc->iters = it;
+    const double rnorm = phibar_new;
+    const double arnorm = phibar_new * alpha * fabs(c);
+    const double anorm = sqrt(sc->anorm2);
+    const double test1 = rnorm / sc->bnorm;
+    const double test2 = rnorm > 0.0 ? arnorm / (anorm * rnorm) : 0.0;
+    const double rtol = sc->tol + sc->tol * anorm * ynorm / sc->bnorm;
+    sc->test1 = test1;
+    sc->test2 = test2;
+    sc->ynorm = ynorm;
+    int istop = 0;
+    if (test2 <= sc->tol) istop = 2;
+    if (test1 <= rtol) istop = 1;
+    sc->istop = istop;
+    if (istop || it >= sc->maxit) sc->done = 1;
+  }
+}
+
+template <typename VT>
+__global__ void k_fro2(int64_t nnz, const VT* __restrict__ vals,
+                       double* __restrict__ partial) {
+  __shared__ double red[33];
+  double s = 0.0;
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+       e < nnz; e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const double v = val_at(vals, e);
+    s += v * v;
+  }
+  s = block_sum<256>(s, red);
+  if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+__global__ void k_finish_error(const double* __restrict__ partial, int nparts,
+                               const double* __restrict__ g, int n, Scalars* sc) {
+  __shared__ double red[33];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < nparts; i += blockDim.x) s += partial[i];
+  s = block_sum<1024>(s, red);
+  double g2 = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) g2 += g[i] * g[i];
+  g2 = block_sum<1024>(g2, red);
+  if (threadIdx.x == 0) {
+    sc->afro2 = s;
+    sc->err_num2 = g2;
+  }
+}
+
+// partial[block] = sum of x[i]^2 over the block's grid-stride share
+__global__ void k_sq_partials(int64_t len, const double* __restrict__ x,
+                              double* __restrict__ partial) {
+  __shared__ double red[33];
+  double s = 0.0;
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+       i < len; i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    s += x[i] * x[i];
+  s = block_sum<256>(s, red);
+  if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+__global__ void k_copy_d(int64_t len, const double* __restrict__ a,
+                         double* __restrict__ b) {
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+       i < len; i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    b[i] = a[i];
+}
+
+// Deterministic CSR: each row's nonzeros placed in column order (the scatter
+// that built the CSR used atomics).  One warp per row; an entry's rank is the
+// number of entries of the row with a smaller column.
+__global__ void k_sort_rows(int32_t m, const int32_t* __restrict__ rowptr,
+                            const int32_t* __restrict__ ccol,
+                            const float* __restrict__ cval,
+                            int32_t* __restrict__ ocol, float* __restrict__ oval) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = static_cast<int64_t>(gridDim.x) * (blockDim.x >> 5);
+  for (int64_t j = blockIdx.x * static_cast<int64_t>(blockDim.x >> 5) + (threadIdx.x >> 5);
+       j < m; j += warps) {
+    const int32_t lo = rowptr[j], hi = rowptr[j + 1];
+    for (int32_t e = lo + lane; e - lane < hi; e += 32) {
+      const int32_t my = e < hi ? ccol[e] : 0;
+      int32_t rank = 0;
+      for (int32_t f = lo; f < hi; ++f) rank += ccol[f] < my;
+      if (e < hi) {
+        ocol[lo + rank] = my;
+        oval[lo + rank] = cval[e];
+      }
+    }
+  }
+}
+
+// Continue LSQR with a 10x tighter internal tolerance (the true Error(x)
+// missed the requested one).
+__global__ void k_tighten(Scalars* sc) {
+  sc->tol *= 0.1;
+  sc->done = 0;
+  sc->istop = 0;
+}
+
+size_t al(size_t b) { return (b + 255) / 256 * 256; }
+
+}  // namespace
+
+struct LsqState {
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+  Scalars* host = nullptr;       // pinned mirror of the scalars
+  cudaStream_t ls = nullptr;     // internal stream (capturable)
+  cudaEvent_t ev[6] = {};
+  cudaGraphExec_t graph = nullptr;
+  const void* graph_key[6] = {};  // what the captured iterations read/write
+};
+
 void destroy_lsq_state(sketch_t h) {
-  delete h->lsq;
+  if (!h->lsq) return;
+  LsqState* st = h->lsq;
+  if (st->ls) cudaStreamSynchronize(st->ls);
+  if (st->graph) cudaGraphExecDestroy(st->graph);
+  for (auto& e : st->ev)
+    if (e) cudaEventDestroy(e);
+  if (st->ls) cudaStreamDestroy(st->ls);
+  if (st->ws) cudaFree(st->ws);
+  if (st->host) cudaFreeHost(st->host);
+  delete st;
   h->lsq = nullptr;
 }
+
 }  // namespace sk
+
+using namespace sk;
+
+namespace {
+
+struct LsqLayout {
+  float* Ahat;
+  double *W, *tau, *Rrow, *Rinv, *RinvT, *u, *t, *t2, *v, *vraw, *w, *y, *partial;
+  double* r;  // A x - b for the error check (kept apart from LSQR's u)
+  Scalars* sc;
+  int32_t* scol;  // column-sorted CSR rows
+  float* sval;
+  void* csr_ws;
+  int* status;
+  size_t bytes;
+};
+
+LsqLayout layout(void* base, int64_t m, int64_t n, int64_t d, int64_t nnz) {
+  LsqLayout L{};
+  char* p = static_cast<char*>(base);
+  auto take = [&](size_t b) {
+    char* r = p;
+    p += al(b);
+    return r;
+  };
+  L.Ahat = reinterpret_cast<float*>(take(sizeof(float) * d * n));
+  L.W = reinterpret_cast<double*>(take(sizeof(double) * d * n));
+  L.tau = reinterpret_cast<double*>(take(sizeof(double) * n));
+  L.Rrow = reinterpret_cast<double*>(take(sizeof(double) * n * n));
+  L.Rinv = reinterpret_cast<double*>(take(sizeof(double) * n * n));
+  L.RinvT = reinterpret_cast<double*>(take(sizeof(double) * n * n));
+  L.u = reinterpret_cast<double*>(take(sizeof(double) * m));
+  L.r = reinterpret_cast<double*>(take(sizeof(double) * m));
+  L.t = reinterpret_cast<double*>(take(sizeof(double) * n));
+  L.t2 = reinterpret_cast<double*>(take(sizeof(double) * n));
+  L.v = reinterpret_cast<double*>(take(sizeof(double) * n));
+  L.vraw = reinterpret_cast<double*>(take(sizeof(double) * n));
+  L.w = reinterpret_cast<double*>(take(sizeof(double) * n));
+  L.y = reinterpret_cast<double*>(take(sizeof(double) * n));
+  L.partial = reinterpret_cast<double*>(take(sizeof(double) * kRedBlocks));
+  L.sc = reinterpret_cast<Scalars*>(take(sizeof(Scalars)));
+  L.status = reinterpret_cast<int*>(take(256));
+  L.scol = reinterpret_cast<int32_t*>(take(sizeof(int32_t) * (nnz > 0 ? nnz : 1)));
+  L.sval = reinterpret_cast<float*>(take(sizeof(float) * (nnz > 0 ? nnz : 1)));
+  L.csr_ws = take(csr_workspace_bytes(m, nnz));
+  L.bytes = static_cast<size_t>(p - static_cast<char*>(base));
+  return L;
+}
+
+template <typename VT>
+void launch_spmv_cols(const sketch_csc* A, const double* u, double* out,
+                      const Scalars* sc, int mode, cudaStream_t s) {
+  const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((A->n + 7) / 8, 32LL * num_sms()));
+  k_spmv_cols<VT><<<static_cast<unsigned>(blocks), 256, 0, s>>>(
+      static_cast<int32_t>(A->n), A->colptr, A->rowidx,
+      static_cast<const VT*>(A->values), u, out, sc, mode);
+}
+
+void spmv_cols(const sketch_csc* A, const double* u, double* out,
+               const Scalars* sc, int mode, cudaStream_t s) {
+  if (A->dtype == SKETCH_F32)
+    launch_spmv_cols<float>(A, u, out, sc, mode, s);
+  else
+    launch_spmv_cols<__nv_bfloat16>(A, u, out, sc, mode, s);
+}
+
+unsigned gemv_blocks(int64_t n) {
+  return static_cast<unsigned>(std::max<int64_t>(1, std::min<int64_t>((n + 7) / 8, 32LL * num_sms())));
+}
+
+// One LSQR iteration (6 kernels) on stream s.
+void lsqr_iteration(const LsqLayout& L, const sketch_csc* A, const CsrView& csr,
+                    cudaStream_t s) {
+  const int n = static_cast<int>(A->n);
+  const int32_t m = static_cast<int32_t>(A->m);
+  k_gemv_tri<<<gemv_blocks(n), 256, 0, s>>>(L.Rinv, n, L.v, L.t, nullptr, L.sc, 0, 0, 0);
+  k_spmv_rows<256><<<kRedBlocks, 256, 0, s>>>(m, csr.rowptr, csr.ccol, csr.cval,
+                                              L.t, L.u, nullptr, L.partial, L.sc, 0);
+  k_finish_beta<<<1, 1024, 0, s>>>(L.partial, kRedBlocks, L.sc, 0);
+  spmv_cols(A, L.u, L.t2, L.sc, 0, s);
+  k_gemv_tri<<<gemv_blocks(n), 256, 0, s>>>(L.RinvT, n, L.t2, L.vraw, L.v, L.sc, 1, 0, 1);
+  k_lsqr_update<<<1, 1024, 0, s>>>(n, L.vraw, L.v, L.w, L.y, L.sc, 0);
+}
+
+}  // namespace
 
 extern "C" int sketch_lsq_solve(sketch_t h, const sketch_csc* A,
                                 const double* b, double* x, double tol,
                                 int32_t maxit, sketch_lsq_info* info,
                                 sketch_stream_t stream) {
-  (void)A; (void)b; (void)x; (void)tol; (void)maxit; (void)info; (void)stream;
-  return sk::fail(h, SKETCH_ERR_UNSUPPORTED, "not built yet");
+  if (!h) return fail(nullptr, SKETCH_ERR_ARG, "handle is null");
+  int rc = check_csc_args(h, A);
+  if (rc != SKETCH_OK) return rc;
+  if (!b || !x) return fail(h, SKETCH_ERR_ARG, "b or x is null");
+  if (!(tol > 0.0)) return fail(h, SKETCH_ERR_ARG, "tol must be > 0");
+  if (maxit < 1) return fail(h, SKETCH_ERR_ARG, "maxit must be >= 1");
+  if (h->d < h->n) return fail(h, SKETCH_ERR_ARG, "sketch size d must be >= n");
+  if (h->n > 8192) return fail(h, SKETCH_ERR_UNSUPPORTED, "n > 8192");
+  cudaStream_t user = reinterpret_cast<cudaStream_t>(stream);
+  const int64_t m = A->m, n = A->n, d = h->d, nnz = A->nnz;
+  if (!h->lsq) h->lsq = new (std::nothrow) LsqState();
+  if (!h->lsq) return fail(h, SKETCH_ERR_OOM, "host allocation failed");
+  LsqState& st = *h->lsq;
+  if (!st.ls) {
+    if (cudaStreamCreateWithFlags(&st.ls, cudaStreamNonBlocking) != cudaSuccess)
+      return fail(h, SKETCH_ERR_CUDA, "cudaStreamCreate failed");
+    for (auto& e : st.ev) cudaEventCreate(&e);
+  }
+  const size_t need = layout(nullptr, m, n, d, nnz).bytes + 256;
+  if (st.ws_bytes < need) {
+    cudaStreamSynchronize(st.ls);
+    if (st.ws) cudaFree(st.ws);
+    if (st.graph) {
+      cudaGraphExecDestroy(st.graph);
+      st.graph = nullptr;
+    }
+    st.ws = nullptr;
+    st.ws_bytes = 0;
+    if (cudaMalloc(&st.ws, need) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(h, SKETCH_ERR_OOM, "cudaMalloc(lsq workspace) failed");
+    }
+    st.ws_bytes = need;
+  }
+  if (!st.host && cudaMallocHost(&st.host, sizeof(Scalars)) != cudaSuccess) {
+    st.host = nullptr;
+    return fail(h, SKETCH_ERR_OOM, "cudaMallocHost failed");
+  }
+  const LsqLayout L = layout(st.ws, m, n, d, nnz);
+  cudaStream_t s = st.ls;
+  cudaEventRecord(st.ev[4], user);  // the solve starts after the caller's work
+  cudaStreamWaitEvent(s, st.ev[4], 0);
+  cudaEventRecord(st.ev[0], s);
+
+  // ---- 1. sketch ------------------------------------------------------------
+  if ((rc = sketch_apply(h, A, L.Ahat, reinterpret_cast<sketch_stream_t>(s))) != SKETCH_OK)
+    return rc;
+  cudaEventRecord(st.ev[1], s);
+
+  // ---- 2. FP64 Householder QR of the sketch, 3. R^{-1} ----------------------
+  cudaMemsetAsync(L.status, 0, sizeof(int), s);
+  const int64_t dn = d * n;
+  const unsigned gb = static_cast<unsigned>(std::max<int64_t>(1, 16LL * num_sms()));
+  k_to_double<<<gb, 256, 0, s>>>(dn, L.Ahat, L.W);
+  k_qr_first<<<1, kQrThreads, 0, s>>>(L.W, d, L.tau);
+  for (int k = 0; k + 1 < n; ++k)
+    k_qr_step<<<static_cast<unsigned>(n - k - 1), kQrThreads, 0, s>>>(
+        L.W, d, static_cast<int>(n), k, L.tau);
+  k_extract_r<<<gb, 256, 0, s>>>(L.W, d, static_cast<int>(n), L.Rrow, L.status);
+  k_trtri<<<gemv_blocks(n), 256, 0, s>>>(L.Rrow, static_cast<int>(n), L.Rinv, L.RinvT);
+  h->launches += 4 + (n - 1);
+  cudaEventRecord(st.ev[2], s);
+
+  // ---- 4. LSQR on A R^{-1} ---------------------------------------------------
+  CsrView csr{};
+  int nl = 0;
+  cudaError_t e = build_csr(static_cast<int32_t>(m), static_cast<int32_t>(n), nnz,
+                            A->colptr, A->rowidx, A->values, A->dtype, L.csr_ws,
+                            &csr, L.status, s, &nl);
+  if (e != cudaSuccess) return cuda_fail(h, e, "csr build (lsq)");
+  k_sort_rows<<<gb, 256, 0, s>>>(static_cast<int32_t>(m), csr.rowptr, csr.ccol, csr.cval,
+                                 L.scol, L.sval);
+  csr.ccol = L.scol;
+  csr.cval = L.sval;
+  h->launches += nl + 1;
+  Scalars init{};
+  init.tol = tol;
+  init.maxit = maxit;
+  *st.host = init;
+  cudaMemcpyAsync(L.sc, st.host, sizeof(Scalars), cudaMemcpyHostToDevice, s);
+  // u = b, beta = ||b||, v = R^{-T} A^T u / alpha, w = v, y = 0
+  k_copy_d<<<gb, 256, 0, s>>>(m, b, L.u);
+  k_sq_partials<<<kRedBlocks, 256, 0, s>>>(m, L.u, L.partial);
+  k_finish_beta<<<1, 1024, 0, s>>>(L.partial, kRedBlocks, L.sc, 1);
+  spmv_cols(A, L.u, L.t2, L.sc, 0, s);
+  k_gemv_tri<<<gemv_blocks(n), 256, 0, s>>>(L.RinvT, static_cast<int>(n), L.t2, L.vraw,
+                                            nullptr, L.sc, 0, 1, 1);
+  k_lsqr_update<<<1, 1024, 0, s>>>(static_cast<int>(n), L.vraw, L.v, L.w, L.y, L.sc, 1);
+  h->launches += 6;
+  // iterations: a cached graph of kIterPerGraph iterations, replayed until
+  // the device sets `done`
+  const void* key[6] = {A->colptr, A->rowidx, A->values, st.ws,
+                        reinterpret_cast<const void*>(n), reinterpret_cast<const void*>(m)};
+  if (st.graph && std::memcmp(key, st.graph_key, sizeof(key)) != 0) {
+    cudaGraphExecDestroy(st.graph);
+    st.graph = nullptr;
+  }
+  if (!st.graph) {
+    cudaGraph_t g = nullptr;
+    e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(h, e, "begin capture");
+    for (int it = 0; it < kIterPerGraph; ++it) lsqr_iteration(L, A, csr, s);
+    e = cudaStreamEndCapture(s, &g);
+    if (e != cudaSuccess) return cuda_fail(h, e, "end capture");
+    e = cudaGraphInstantiate(&st.graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      st.graph = nullptr;
+      return cuda_fail(h, e, "graph instantiate");
+    }
+    std::memcpy(st.graph_key, key, sizeof(key));
+  }
+  // LSQR stops on its own estimate for the preconditioned system; the
+  // paper's Error(x) for A itself can land above it, so verify and, if
+  // needed, continue from the same state with a tighter internal tolerance.
+  int qr_status = 0;
+  int launched = 0;
+  double prev_err = 1e300;
+  for (int round = 0; round < 6; ++round) {
+    for (;; launched += kIterPerGraph) {
+      e = cudaGraphLaunch(st.graph, s);
+      if (e != cudaSuccess) return cuda_fail(h, e, "graph launch");
+      h->launches += 6 * kIterPerGraph;
+      cudaMemcpyAsync(st.host, L.sc, sizeof(Scalars), cudaMemcpyDeviceToHost, s);
+      e = cudaStreamSynchronize(s);
+      if (e != cudaSuccess) return cuda_fail(h, e, "lsqr iterations");
+      if (st.host->done || launched >= maxit) break;
+    }
+    // x = R^{-1} y
+    k_gemv_tri<<<gemv_blocks(n), 256, 0, s>>>(L.Rinv, static_cast<int>(n), L.y, x,
+                                              nullptr, L.sc, 0, 1, 0);
+    cudaEventRecord(st.ev[3], s);
+    // ---- 5. Error(x) = ||A^T (A x - b)|| / (||A||_F ||A x - b||) in FP64 ----
+    k_spmv_rows<256><<<kRedBlocks, 256, 0, s>>>(static_cast<int32_t>(m), csr.rowptr, csr.ccol,
+                                                csr.cval, x, L.r, b, L.partial, L.sc, 1);
+    k_finish_beta<<<1, 1024, 0, s>>>(L.partial, kRedBlocks, L.sc, 2);
+    spmv_cols(A, L.r, L.t2, L.sc, 1, s);
+    if (A->dtype == SKETCH_F32)
+      k_fro2<float><<<kRedBlocks, 256, 0, s>>>(nnz, static_cast<const float*>(A->values), L.partial);
+    else
+      k_fro2<__nv_bfloat16><<<kRedBlocks, 256, 0, s>>>(
+          nnz, static_cast<const __nv_bfloat16*>(A->values), L.partial);
+    k_finish_error<<<1, 1024, 0, s>>>(L.partial, kRedBlocks, L.t2, static_cast<int>(n), L.sc);
+    h->launches += 6;
+    cudaMemcpyAsync(st.host, L.sc, sizeof(Scalars), cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(&qr_status, L.status, sizeof(int), cudaMemcpyDeviceToHost, s);
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "lsq error check");
+    const Scalars& c = *st.host;
+    const double den = std::sqrt(c.afro2) * std::sqrt(c.err_res2);
+    const double err = den > 0.0 ? std::sqrt(c.err_num2) / den : 0.0;
+    // stop when the metric is met, LSQR ran out of iterations, or another
+    // round gained less than 2x (the metric sits at its FP64 floor)
+    if (err <= tol || c.istop == 0 || qr_status != 0 || c.iters >= maxit ||
+        err > 0.5 * prev_err)
+      break;
+    prev_err = err;
+    k_tighten<<<1, 1, 0, s>>>(L.sc);
+    h->launches += 1;
+  }
+  cudaEventRecord(st.ev[5], s);
+  cudaStreamWaitEvent(user, st.ev[5], 0);  // the caller's stream sees x
+  e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(h, e, "lsq solve");
+  const Scalars& sc = *st.host;
+  if (info) {
+    std::memset(info, 0, sizeof(*info));
+    info->iters = sc.iters;
+    info->istop = sc.istop;
+    info->test2 = sc.test2;
+    const double den = std::sqrt(sc.afro2) * std::sqrt(sc.err_res2);
+    info->error = den > 0.0 ? std::sqrt(sc.err_num2) / den : 0.0;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, st.ev[0], st.ev[1]);
+    info->ms_sketch = ms;
+    cudaEventElapsedTime(&ms, st.ev[1], st.ev[2]);
+    info->ms_qr = ms;
+    cudaEventElapsedTime(&ms, st.ev[2], st.ev[3]);
+    info->ms_lsqr = ms;
+  }
+  if (qr_status & 4)
+    return fail(h, SKETCH_ERR_CSC, "R has a zero diagonal entry (rank-deficient A)");
+  if (qr_status & (kStatusBadRow | kStatusBadColptr))
+    return fail(h, SKETCH_ERR_CSC, "a kernel met an out-of-range index");
+  const int status = sc.istop ? SKETCH_OK : SKETCH_ERR_NO_CONVERGENCE;
+  if (info) info->status = status;
+  if (status != SKETCH_OK) fail(h, status, "LSQR reached maxit");
+  return status;
+}
+
+extern "C" int sketch_debug_qr(int64_t d, int64_t n, const double* A, double* R,
+                               double* Rinv, sketch_stream_t stream) {
+  if (d < 1 || n < 1 || d < n || n > 8192 || !A || !R || !Rinv)
+    return fail(nullptr, SKETCH_ERR_ARG, "bad arguments");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  double *W = nullptr, *tau = nullptr, *RT = nullptr;
+  int* status = nullptr;
+  if (cudaMalloc(&W, sizeof(double) * d * n) != cudaSuccess ||
+      cudaMalloc(&tau, sizeof(double) * n) != cudaSuccess ||
+      cudaMalloc(&RT, sizeof(double) * n * n) != cudaSuccess ||
+      cudaMalloc(&status, sizeof(int)) != cudaSuccess) {
+    cudaFree(W); cudaFree(tau); cudaFree(RT); cudaFree(status);
+    cudaGetLastError();
+    return fail(nullptr, SKETCH_ERR_OOM, "cudaMalloc failed");
+  }
+  cudaMemcpyAsync(W, A, sizeof(double) * d * n, cudaMemcpyDeviceToDevice, s);
+  cudaMemsetAsync(status, 0, sizeof(int), s);
+  k_qr_first<<<1, kQrThreads, 0, s>>>(W, d, tau);
+  for (int k = 0; k + 1 < n; ++k)
+    k_qr_step<<<static_cast<unsigned>(n - k - 1), kQrThreads, 0, s>>>(W, d, static_cast<int>(n), k, tau);
+  const unsigned gb = static_cast<unsigned>(std::max<int64_t>(1, 16LL * num_sms()));
+  k_extract_r<<<gb, 256, 0, s>>>(W, d, static_cast<int>(n), R, status);
+  k_trtri<<<gemv_blocks(n), 256, 0, s>>>(R, static_cast<int>(n), Rinv, RT);
+  cudaError_t e = cudaStreamSynchronize(s);
+  cudaFree(W); cudaFree(tau); cudaFree(RT); cudaFree(status);
+  return e == cudaSuccess ? SKETCH_OK : cuda_fail(nullptr, e, "debug_qr");
 }

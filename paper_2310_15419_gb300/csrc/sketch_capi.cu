@@ -276,21 +276,8 @@ static std::vector<sketch_plan> candidates(const sketch_s* h, const sketch_csc* 
         (size_t(8) << 30))
       c.push_back(p);
   }
-  // PANEL only where rows are reused (Alg. 4 pays off) or for U / N
-  const size_t csr_bytes = csr_workspace_bytes(A->m, A->nnz);
-  for (int32_t nb : {static_cast<int32_t>(std::min<int64_t>(A->n, 1024)),
-                     static_cast<int32_t>(std::min<int64_t>(A->n, 512))}) {
-    sketch_plan p{};
-    p.mode = SKETCH_MODE_PANEL;
-    p.n_block = nb;
-    p.row_groups = default_row_groups(h, A, nb);
-    const size_t part = static_cast<size_t>(p.row_groups) * A->n * h->d * 4;
-    if (csr_bytes + part > (size_t(8) << 30)) continue;  // keep the tuner lean
-    bool dup = false;
-    for (auto& o : c)
-      if (o.mode == p.mode && o.n_block == p.n_block) dup = true;
-    if (!dup) c.push_back(p);
-  }
+  // PANEL (shared-memory atomics, order-dependent at the last bit) is not a
+  // candidate: every plan the tuner picks is deterministic.
   return c;
 }
 
