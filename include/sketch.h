@@ -172,6 +172,39 @@ int sketch_device_status(sketch_t h, sketch_stream_t stream);
  * each column (so no duplicates).  Returns SKETCH_OK or SKETCH_ERR_CSC. */
 int sketch_validate_csc(const sketch_csc* A, sketch_stream_t stream);
 
+/* ---- many uneven sketches in one persistent launch ---------------------- */
+typedef struct sketch_batch_s* sketch_batch_t;
+
+/* Prepare a batch: instance i computes Ahats[i] = S_i As[i] with handle
+ * handles[i] (its own m, n, d and Philox stream id; all handles must share
+ * one distribution).  Builds a device work list of (instance, column, tile of
+ * 128*q rows of S) items sorted by decreasing nonzero count, and picks q by
+ * timing each candidate once on the real batch (so it runs the batch, on
+ * `stream`, synchronously).  Alg. 3's per-column work (Sec. 2.2) with
+ * Alg. 1's outer blocking spread over instances.  Pointers in As / Ahats are
+ * device pointers that must stay valid for the life of the batch.
+ * Errors: SKETCH_ERR_ARG, SKETCH_ERR_UNSUPPORTED (mixed distributions),
+ * SKETCH_ERR_OOM, SKETCH_ERR_CUDA. */
+int sketch_batch_create(int32_t count, const sketch_t* handles,
+                        const sketch_csc* As, float* const* Ahats,
+                        sketch_stream_t stream, sketch_batch_t* out);
+
+/* Run the whole batch: one counter reset and one persistent kernel launch on
+ * `stream` (asynchronous, no allocation, so it can be captured in a CUDA
+ * graph and replayed). */
+int sketch_batch_apply(sketch_batch_t b, sketch_stream_t stream);
+
+/* Tile height chosen (q: 128*q rows of S per item), number of work items and
+ * launches so far. */
+int sketch_batch_info(sketch_batch_t b, int32_t* q_tiles, int64_t* n_items,
+                      int64_t* launches);
+
+/* Read and clear-free check of the batch's device status word (synchronous):
+ * SKETCH_OK or SKETCH_ERR_CSC. */
+int sketch_batch_status(sketch_batch_t b, sketch_stream_t stream);
+
+int sketch_batch_destroy(sketch_batch_t b);
+
 /* ---- least squares (Sec. 5.4, sketch-and-precondition with QR) -------- */
 typedef struct {
   int32_t iters;        /* LSQR iterations                                 */

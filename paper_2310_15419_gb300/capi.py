@@ -97,6 +97,13 @@ SIGNATURES = [
     ("sketch_launch_count", _I64, [_VP]),
     ("sketch_bench_generator", _I32, [_I32, _U64, _I64, _I64, _VP, _VP]),
     ("sketch_debug_qr", _I32, [_I64, _I64, _VP, _VP, _VP, _VP]),
+    ("sketch_batch_create", _I32, [_I32, ctypes.POINTER(_VP), _CSCP,
+                                   ctypes.POINTER(_VP), _VP, ctypes.POINTER(_VP)]),
+    ("sketch_batch_apply", _I32, [_VP, _VP]),
+    ("sketch_batch_info", _I32, [_VP, ctypes.POINTER(_I32), ctypes.POINTER(_I64),
+                                 ctypes.POINTER(_I64)]),
+    ("sketch_batch_status", _I32, [_VP, _VP]),
+    ("sketch_batch_destroy", _I32, [_VP]),
 ]
 
 
@@ -252,6 +259,51 @@ class Sketch:
         d = info.as_dict()
         d["rc"] = rc
         return x, d
+
+
+class Batch:
+    """Many uneven sketches in one persistent launch (sketch_batch_*)."""
+
+    def __init__(self, sketches, mats, outs=None, stream=None):
+        import torch
+        lib = load()
+        self.sketches, self.mats = list(sketches), list(mats)
+        if outs is None:
+            outs = [torch.empty((A.n, sk.d), dtype=torch.float32, device="cuda")
+                    for sk, A in zip(self.sketches, self.mats)]
+        self.outs = list(outs)
+        cnt = len(self.sketches)
+        H = (ctypes.c_void_p * cnt)(*[sk.h.value for sk in self.sketches])
+        D = (sketch_csc * cnt)(*[A.desc for A in self.mats])
+        O = (ctypes.c_void_p * cnt)(*[o.data_ptr() for o in self.outs])
+        b = ctypes.c_void_p()
+        _check(lib.sketch_batch_create(cnt, H, D, O, _stream_ptr(stream),
+                                       ctypes.byref(b)))
+        self.b = b
+
+    def apply(self, stream=None):
+        _check(load().sketch_batch_apply(self.b, _stream_ptr(stream)))
+        return self.outs
+
+    def info(self):
+        q, n, l = ctypes.c_int32(), ctypes.c_int64(), ctypes.c_int64()
+        _check(load().sketch_batch_info(self.b, ctypes.byref(q), ctypes.byref(n),
+                                        ctypes.byref(l)))
+        return {"q_tiles": q.value, "items": n.value, "launches": l.value}
+
+    def status(self, stream=None):
+        return load().sketch_batch_status(self.b, _stream_ptr(stream))
+
+    def close(self):
+        if getattr(self, "b", None):
+            load().sketch_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def validate_csc(A: DeviceCSC, stream=None) -> int:

@@ -26,6 +26,26 @@ struct RegenArgs {
 };
 cudaError_t launch_regen(const RegenArgs& a, cudaStream_t s);
 
+// One instance of a batched sketch (device-resident descriptor).
+struct BatchInstance {
+  const int32_t* colptr;
+  const int32_t* rowidx;
+  const void* values;
+  float* Ahat;
+  int32_t m, n, d, dtype;
+  uint32_t k0, k1, stream_id, pad;
+};
+// One work item: column `column` of instance `instance`, rows of S
+// [tile * 128 * Q, (tile + 1) * 128 * Q).
+struct BatchItem {
+  int32_t instance, column, tile, pad;
+};
+cudaError_t launch_regen_batched(int dist, int q_tiles, const BatchInstance* inst,
+                                 const BatchItem* items, int64_t n_items,
+                                 unsigned long long* counter, int* status,
+                                 int blocks, cudaStream_t s);
+int batched_blocks_per_sm(int dist, int q_tiles);
+
 // CSR copy of A (the single-vertical-block "blocked CSR" of Sec. 3.2) built
 // on the device.  Workspace sizes in bytes for m rows and nnz nonzeros.
 size_t csr_workspace_bytes(int64_t m, int64_t nnz);

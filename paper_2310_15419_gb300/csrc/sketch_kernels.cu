@@ -39,6 +39,109 @@ __device__ __forceinline__ void kahan_add(float& sum, float& c, float x) {
   sum = t;
 }
 
+// One warp accumulates column nonzeros [lo, hi) against rows d0 .. d0+128Q-1
+// of S; lane L owns rows d0 + 128 q + 4 L + r.  On return outer[q][r] holds
+// the column's contribution to those rows.  `stage` is the warp's slice of
+// the shared staging buffer (+-1 only).  Returns the S entries generated.
+template <int DIST, int Q, typename VT>
+__device__ __forceinline__ unsigned long long regen_accumulate(
+    int32_t lo, int32_t hi, int32_t m, int32_t d0, int rows_valid,
+    const int32_t* __restrict__ rowidx, const VT* __restrict__ vals,
+    uint32_t k0, uint32_t k1, uint32_t stream_id, int* status,
+    uint32_t (*stage)[4 * Q + 4], float (&outer)[Q][4]) {
+  const int lane = threadIdx.x & 31;
+  // Two-level sums: a batch of 32 nonzeros accumulates in `inner`, batch
+  // sums are added to `outer` with Kahan compensation (`comp`), so the FP32
+  // error stays near one rounding per batch however long the column is.
+  float comp[Q][4];
+#pragma unroll
+  for (int q = 0; q < Q; ++q)
+#pragma unroll
+    for (int r = 0; r < 4; ++r) outer[q][r] = comp[q][r] = 0.f;
+  float t_outer = 0.f, t_comp = 0.f;  // +-1 only: sum of the column's values
+  unsigned long long generated = 0;
+  // bit masks of this lane's four rows inside its Philox word (+-1)
+  uint32_t mask[4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r) mask[r] = 1u << (4 * (lane & 7) + r);
+
+  for (int32_t base = lo; base < hi; base += 32) {
+    const int cnt = min(32, hi - base);
+    int32_t j = 0;
+    float a = 0.f;
+    if (lane < cnt) {
+      j = rowidx[base + lane];
+      a = to_f32(vals[base + lane]);
+      if (static_cast<uint32_t>(j) >= static_cast<uint32_t>(m)) {
+        atomicOr(status, kStatusBadRow);
+        j = 0;
+        a = 0.f;
+      }
+    }
+    generated += static_cast<unsigned long long>(cnt) * rows_valid;
+    float inner[Q][4];
+#pragma unroll
+    for (int q = 0; q < Q; ++q)
+#pragma unroll
+      for (int r = 0; r < 4; ++r) inner[q][r] = 0.f;
+
+    if constexpr (DIST == kPM1) {
+      // lane t: Philox blocks of nonzero t for the Q 128-row blocks
+      if (lane < cnt) {
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+          const uint4 x = philox_block(static_cast<uint32_t>((d0 >> 7) + q),
+                                       static_cast<uint32_t>(j), stream_id, k0, k1);
+          *reinterpret_cast<uint4*>(&stage[lane][4 * q]) = x;
+        }
+      }
+      __syncwarp();
+      float t_inner = 0.f;
+      const int wsel = lane >> 3;
+      for (int t = 0; t < cnt; ++t) {
+        const float at = __shfl_sync(0xffffffffu, a, t);
+        t_inner += at;
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+          const uint32_t w = stage[t][4 * q + wsel];
+#pragma unroll
+          for (int r = 0; r < 4; ++r)
+            if (w & mask[r]) inner[q][r] += at;
+        }
+      }
+      __syncwarp();
+      kahan_add(t_outer, t_comp, t_inner);
+    } else {
+      for (int t = 0; t < cnt; ++t) {
+        const int32_t jt = __shfl_sync(0xffffffffu, j, t);
+        const float at = __shfl_sync(0xffffffffu, a, t);
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+          const uint4 x = philox_block(static_cast<uint32_t>((d0 >> 2) + 32 * q + lane),
+                                       static_cast<uint32_t>(jt), stream_id, k0, k1);
+          const float4 sv = four_entries<DIST>(x);
+          inner[q][0] = fmaf(at, sv.x, inner[q][0]);
+          inner[q][1] = fmaf(at, sv.y, inner[q][1]);
+          inner[q][2] = fmaf(at, sv.z, inner[q][2]);
+          inner[q][3] = fmaf(at, sv.w, inner[q][3]);
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < Q; ++q)
+#pragma unroll
+      for (int r = 0; r < 4; ++r) kahan_add(outer[q][r], comp[q][r], inner[q][r]);
+  }
+  if constexpr (DIST == kPM1) {
+    // sum over +1 rows minus sum over -1 rows = T - 2 P
+#pragma unroll
+    for (int q = 0; q < Q; ++q)
+#pragma unroll
+      for (int r = 0; r < 4; ++r) outer[q][r] = t_outer - 2.f * outer[q][r];
+  }
+  return generated;
+}
+
 template <int DIST, int Q, typename VT>
 __global__ void __launch_bounds__(kRegenWarps * 32, 2)
     k_regen(int32_t m, int32_t n, int32_t d, int32_t split,
@@ -50,9 +153,7 @@ __global__ void __launch_bounds__(kRegenWarps * 32, 2)
   constexpr int TD = 128 * Q;          // rows of S per item
   constexpr int SW = 4 * Q + 4;        // staged words per nonzero (+pad)
   __shared__ float red[kRegenWarps][TD];
-  __shared__ __align__(16) uint32_t stage[DIST == kPM1 ? kRegenWarps : 1]
-                                         [DIST == kPM1 ? 32 : 1]
-                                         [DIST == kPM1 ? SW : 4];
+  __shared__ __align__(16) uint32_t stage[kRegenWarps][DIST == kPM1 ? 32 : 1][SW];
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
@@ -65,15 +166,11 @@ __global__ void __launch_bounds__(kRegenWarps * 32, 2)
   const int32_t k = valid ? static_cast<int32_t>(item / dtiles) : 0;
   const int32_t d0 = valid ? static_cast<int32_t>(item % dtiles) * TD : 0;
 
-  // Two-level sums: a batch of 32 nonzeros accumulates in `inner`, batch
-  // sums are added to `outer` with Kahan compensation (`comp`), so the FP32
-  // error stays near one rounding per batch however long the column is.
-  float outer[Q][4], comp[Q][4];
+  float outer[Q][4];
 #pragma unroll
   for (int q = 0; q < Q; ++q)
 #pragma unroll
-    for (int r = 0; r < 4; ++r) outer[q][r] = comp[q][r] = 0.f;
-  float t_outer = 0.f, t_comp = 0.f;  // +-1 only: sum of the column's values
+    for (int r = 0; r < 4; ++r) outer[q][r] = 0.f;
   unsigned long long generated = 0;
 
   if (valid) {
@@ -86,89 +183,9 @@ __global__ void __launch_bounds__(kRegenWarps * 32, 2)
     const int32_t chunk = (len + split - 1) / split;
     const int32_t lo = p0 + min(len, sub * chunk);
     const int32_t hi = p0 + min(len, (sub + 1) * chunk);
-    const int rows_valid = min(TD, d - d0);
-
-    // bit masks of this lane's four rows inside its Philox word (+-1)
-    uint32_t mask[4];
-#pragma unroll
-    for (int r = 0; r < 4; ++r) mask[r] = 1u << (4 * (lane & 7) + r);
-
-    for (int32_t base = lo; base < hi; base += 32) {
-      const int cnt = min(32, hi - base);
-      int32_t j = 0;
-      float a = 0.f;
-      if (lane < cnt) {
-        j = rowidx[base + lane];
-        a = to_f32(vals[base + lane]);
-        if (static_cast<uint32_t>(j) >= static_cast<uint32_t>(m)) {
-          atomicOr(status, kStatusBadRow);
-          j = 0;
-          a = 0.f;
-        }
-      }
-      generated += static_cast<unsigned long long>(cnt) * rows_valid;
-      float inner[Q][4];
-#pragma unroll
-      for (int q = 0; q < Q; ++q)
-#pragma unroll
-        for (int r = 0; r < 4; ++r) inner[q][r] = 0.f;
-
-      if constexpr (DIST == kPM1) {
-        // lane t: Philox blocks of nonzero t for the Q 128-row blocks
-        if (lane < cnt) {
-#pragma unroll
-          for (int q = 0; q < Q; ++q) {
-            const uint4 x = philox_block(static_cast<uint32_t>((d0 >> 7) + q),
-                                         static_cast<uint32_t>(j), stream_id,
-                                         k0, k1);
-            *reinterpret_cast<uint4*>(&stage[warp][lane][4 * q]) = x;
-          }
-        }
-        __syncwarp();
-        float t_inner = 0.f;
-        const int wsel = lane >> 3;
-        for (int t = 0; t < cnt; ++t) {
-          const float at = __shfl_sync(0xffffffffu, a, t);
-          t_inner += at;
-#pragma unroll
-          for (int q = 0; q < Q; ++q) {
-            const uint32_t w = stage[warp][t][4 * q + wsel];
-#pragma unroll
-            for (int r = 0; r < 4; ++r)
-              if (w & mask[r]) inner[q][r] += at;
-          }
-        }
-        __syncwarp();
-        kahan_add(t_outer, t_comp, t_inner);
-      } else {
-        for (int t = 0; t < cnt; ++t) {
-          const int32_t jt = __shfl_sync(0xffffffffu, j, t);
-          const float at = __shfl_sync(0xffffffffu, a, t);
-#pragma unroll
-          for (int q = 0; q < Q; ++q) {
-            const uint4 x = philox_block(
-                static_cast<uint32_t>((d0 >> 2) + 32 * q + lane),
-                static_cast<uint32_t>(jt), stream_id, k0, k1);
-            const float4 s = four_entries<DIST>(x);
-            inner[q][0] = fmaf(at, s.x, inner[q][0]);
-            inner[q][1] = fmaf(at, s.y, inner[q][1]);
-            inner[q][2] = fmaf(at, s.z, inner[q][2]);
-            inner[q][3] = fmaf(at, s.w, inner[q][3]);
-          }
-        }
-      }
-#pragma unroll
-      for (int q = 0; q < Q; ++q)
-#pragma unroll
-        for (int r = 0; r < 4; ++r) kahan_add(outer[q][r], comp[q][r], inner[q][r]);
-    }
-    if constexpr (DIST == kPM1) {
-      // sum over +1 rows minus sum over -1 rows = T - 2 P
-#pragma unroll
-      for (int q = 0; q < Q; ++q)
-#pragma unroll
-        for (int r = 0; r < 4; ++r) outer[q][r] = t_outer - 2.f * outer[q][r];
-    }
+    generated = regen_accumulate<DIST, Q, VT>(lo, hi, m, d0, min(TD, d - d0), rowidx,
+                                             vals, k0, k1, stream_id, status,
+                                             stage[warp], outer);
   }
 
   if (split == 1) {
@@ -193,10 +210,10 @@ __global__ void __launch_bounds__(kRegenWarps * 32, 2)
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
           const int c = 128 * q + 4 * lane + r;
-          float s = red[warp][c];
-          for (int u = 1; u < split; ++u) s += red[warp + u][c];
+          float sum = red[warp][c];
+          for (int u = 1; u < split; ++u) sum += red[warp + u][c];
           const int32_t i = d0 + c;
-          if (i < d) Ahat[static_cast<int64_t>(k) * d + i] = s;
+          if (i < d) Ahat[static_cast<int64_t>(k) * d + i] = sum;
         }
     }
   }
@@ -204,6 +221,86 @@ __global__ void __launch_bounds__(kRegenWarps * 32, 2)
     // every lane holds the same warp-uniform count; lane 0 reports it
     if (lane == 0) atomicAdd(gen_count, generated);
   }
+}
+
+// ---------------------------------------------------------------------------
+// Batched REGEN: many uneven sketches in one persistent launch.  Items
+// (instance, column, tile of 128*Q rows of S) sit in a device work list
+// sorted by decreasing nonzero count; each warp claims the next item from a
+// counter (bounded: the loop ends when the counter passes the list), so the
+// launch is fair to uneven instances and can be replayed from a CUDA graph
+// once the counter is reset.
+// ---------------------------------------------------------------------------
+template <int DIST, int Q>
+__global__ void __launch_bounds__(kRegenWarps * 32, 2)
+    k_regen_batched(const BatchInstance* __restrict__ inst,
+                    const BatchItem* __restrict__ items, int64_t n_items,
+                    unsigned long long* __restrict__ counter, int* status) {
+  constexpr int TD = 128 * Q;
+  constexpr int SW = 4 * Q + 4;
+  __shared__ __align__(16) uint32_t stage[kRegenWarps][DIST == kPM1 ? 32 : 1][SW];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (;;) {
+    unsigned long long it = 0;
+    if (lane == 0) it = atomicAdd(counter, 1ULL);
+    it = __shfl_sync(0xffffffffu, it, 0);
+    if (it >= static_cast<unsigned long long>(n_items)) break;
+    const BatchItem w = items[it];
+    const BatchInstance& I = inst[w.instance];
+    const int32_t d0 = w.tile * TD;
+    const int32_t lo = I.colptr[w.column], hi = max(lo, I.colptr[w.column + 1]);
+    float outer[Q][4];
+    if (I.dtype == 0)
+      regen_accumulate<DIST, Q, float>(lo, hi, I.m, d0, min(TD, I.d - d0), I.rowidx,
+                                       static_cast<const float*>(I.values), I.k0, I.k1,
+                                       I.stream_id, status, stage[warp], outer);
+    else
+      regen_accumulate<DIST, Q, __nv_bfloat16>(
+          lo, hi, I.m, d0, min(TD, I.d - d0), I.rowidx,
+          static_cast<const __nv_bfloat16*>(I.values), I.k0, I.k1, I.stream_id, status,
+          stage[warp], outer);
+    float* col = I.Ahat + static_cast<int64_t>(w.column) * I.d;
+#pragma unroll
+    for (int q = 0; q < Q; ++q)
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const int32_t i = d0 + 128 * q + 4 * lane + r;
+        if (i < I.d) col[i] = outer[q][r];
+      }
+  }
+}
+
+cudaError_t launch_regen_batched(int dist, int q_tiles, const BatchInstance* inst,
+                                 const BatchItem* items, int64_t n_items,
+                                 unsigned long long* counter, int* status,
+                                 int blocks, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return e;
+  const dim3 grid(blocks), block(kRegenWarps * 32);
+#define SK_BATCH_CASE(DD, QQ)                                                  \
+  if (dist == DD && q_tiles == QQ) {                                           \
+    k_regen_batched<DD, QQ><<<grid, block, 0, s>>>(inst, items, n_items,      \
+                                                   counter, status);          \
+    return cudaGetLastError();                                                 \
+  }
+  SK_BATCH_CASE(kPM1, 1) SK_BATCH_CASE(kPM1, 2) SK_BATCH_CASE(kPM1, 4)
+  SK_BATCH_CASE(kUniform, 1) SK_BATCH_CASE(kUniform, 2) SK_BATCH_CASE(kUniform, 4)
+  SK_BATCH_CASE(kNormal, 1) SK_BATCH_CASE(kNormal, 2) SK_BATCH_CASE(kNormal, 4)
+#undef SK_BATCH_CASE
+  return cudaErrorInvalidValue;
+}
+
+int batched_blocks_per_sm(int dist, int q_tiles) {
+  int nb = 0;
+#define SK_OCC(DD, QQ)                                                          \
+  if (dist == DD && q_tiles == QQ)                                              \
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_regen_batched<DD, QQ>, \
+                                                  kRegenWarps * 32, 0);
+  SK_OCC(kPM1, 1) SK_OCC(kPM1, 2) SK_OCC(kPM1, 4)
+  SK_OCC(kUniform, 1) SK_OCC(kUniform, 2) SK_OCC(kUniform, 4)
+  SK_OCC(kNormal, 1) SK_OCC(kNormal, 2) SK_OCC(kNormal, 4)
+#undef SK_OCC
+  return nb > 0 ? nb : 1;
 }
 
 template <int DIST, typename VT>
