@@ -55,6 +55,12 @@ def parse():
                     default="auto", help="force one kernel family")
     ap.add_argument("--no-cpu", action="store_true",
                     help="skip the oracle's CPU baseline")
+    ap.add_argument("--extras", default="lsq,batched,serve",
+                    help="secondary workloads reported beside the headline")
+    ap.add_argument("--serve-seconds", type=float, default=2.0,
+                    help="length of the Poisson arrival trace of the serve run")
+    ap.add_argument("--serve-pool", type=int, default=24,
+                    help="distinct request matrices the arrival trace draws from")
     return ap.parse_args()
 
 
@@ -180,6 +186,120 @@ def cpu_baseline(A, d, seconds_budget, reps=1):
             "sample": "rows [0, %d) of the workload (%d nonzeros), all three "
                       "distributions, FP64 Alg. 4 order, %.1f s" %
                       (rows, nnz_rows, sec)}, sec
+
+
+def pct(xs, q):
+    return float(np.percentile(np.asarray(xs, dtype=np.float64), q)) if xs else None
+
+
+def bench_lsq(torch, capi, inputs, reps=10):
+    """lsq_mixed: m=1e6, n=500, density 0.2%, BF16 values, column scales
+    logU[1e-2, 1e2], b = A x* + 1e-6 noise, d = 2n, +-1 S, tol 1e-10.
+    Latency of sketch_lsq_solve (synchronous, inputs resident)."""
+    A, b, _ = inputs.lsq_mixed()
+    dA = capi.DeviceCSC(A)
+    bb = torch.from_numpy(b).cuda()
+    sk = capi.Sketch(A.m, A.n, 2 * A.n, "pm1", seed=1)
+    x, info = sk.lsq_solve(dA, bb)          # tunes the sketch plan
+    torch.cuda.synchronize()
+    lat, infos = [], []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        x, info = sk.lsq_solve(dA, bb)
+        torch.cuda.synchronize()
+        lat.append(1e3 * (time.perf_counter() - t0))
+        infos.append(info)
+    launches = sk.launch_count()
+    sk.close()
+    return {"workload": "lsq_mixed m=1,000,000 n=500 density 0.2% BF16, d=2n, +-1 S",
+            "solves_per_s": round(1e3 / statistics.mean(lat), 3),
+            "p50_ms": round(pct(lat, 50), 3), "p99_ms": round(pct(lat, 99), 3),
+            "iters": infos[-1]["iters"], "error": infos[-1]["error"],
+            "ms_sketch": round(infos[-1]["ms_sketch"], 3),
+            "ms_qr": round(infos[-1]["ms_qr"], 3),
+            "ms_lsqr": round(infos[-1]["ms_lsqr"], 3), "reps": reps,
+            "launches_total": launches}
+
+
+def bench_batched(torch, capi, inputs, steps=10):
+    """256 uneven instances (m ~ logU[1e4, 5e5], n ~ U[50, 1000], d = c n,
+    c ~ U[1.5, 4], density ~ logU[5e-4, 2e-2], N(0,1) values), +-1 S, one
+    persistent launch replayed from a captured CUDA graph."""
+    inst = inputs.batched()
+    sks = [capi.Sketch(A.m, A.n, d, "pm1", seed=1, stream_id=t)
+           for t, (A, d) in enumerate(inst)]
+    mats = [capi.DeviceCSC(A) for A, _ in inst]
+    flops = sum(2.0 * d * A.nnz for A, d in inst)
+    nnz = sum(A.nnz for A, _ in inst)
+    batch = capi.Batch(sks, mats)
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        batch.apply(stream=s)
+        torch.cuda.synchronize()
+        with torch.cuda.graph(g, stream=s):
+            batch.apply(stream=s)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    ms = []
+    for it in range(steps + 2):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        g.replay()
+        e1.record()
+        torch.cuda.synchronize()
+        if it >= 2:
+            ms.append(e0.elapsed_time(e1))
+    info = batch.info()
+    batch.close()
+    mean = statistics.mean(ms)
+    return {"workload": "256 uneven instances, sum nnz=%d, +-1 S, CUDA graph" % nnz,
+            "value": round(flops / (mean / 1e3) / 1e9, 3), "unit": UNIT,
+            "ms": round(mean, 4), "q_tiles": info["q_tiles"], "items": info["items"],
+            "l2": "flushed before every replay"}
+
+
+def bench_serve(capi, inputs, seconds, pool_size, rate=200.0):
+    """Poisson arrivals at `rate`/s of SAP-QR solves with m ~ logU[5e4, 2e6],
+    n ~ U[100, 2000], density ~ logU[5e-4, 1e-2], FP32 N(0,1) values, d = 2n,
+    +-1 S, tol 1e-10.  Requests draw their matrix from a pool of `pool_size`
+    such matrices (each request has its own b).  The continuous server (8
+    slots) and the one-at-a-time path (1 slot) replay the same trace."""
+    specs = inputs.serve_requests(duration_s=1e9, rate=rate)[:pool_size]
+    pool = []
+    for t, (_, m, n, dens) in enumerate(specs):
+        A, b, _ = inputs.lsq_problem(m, n, dens, seed=50_000 + t, noise=1e-3)
+        pool.append((A, b))
+    trace = [(t, i % pool_size) for i, (t, _, _, _) in
+             enumerate(inputs.serve_requests(seed=6, duration_s=seconds, rate=rate))]
+    out = {"workload": "Poisson %.0f req/s for %.1f s (%d requests), pool of %d "
+                       "serve matrices (mean nnz %.3g)" %
+                       (rate, seconds, len(trace), pool_size,
+                        statistics.mean(A.nnz for A, _ in pool))}
+    for name, slots in (("continuous", 8), ("one_at_a_time", 1)):
+        srv = capi.Server(slots=slots, mem_budget=64 << 30, dist="pm1", seed=1)
+        # warm the workers' workspaces with the largest pool matrix
+        big = max(range(pool_size), key=lambda i: pool[i][0].nnz)
+        srv.submit(*pool[big])
+        srv.drain()
+        srv.poll(8)
+        t0 = srv.now()
+        for (ta, i) in trace:
+            while srv.now() - t0 < ta:
+                time.sleep(min(0.002, max(0.0, ta - (srv.now() - t0))))
+            srv.submit(*pool[i])
+        srv.drain()
+        res = srv.poll(len(trace) + 8)
+        srv.close()
+        lat = [1e3 * (r["t_done"] - r["t_submit"]) for r in res]
+        span = max(r["t_done"] for r in res) - min(r["t_submit"] for r in res)
+        ok = sum(1 for r in res if r["status"] == 0)
+        out[name] = {"slots": slots, "solves_per_s": round(len(res) / span, 3),
+                     "p50_ms": round(pct(lat, 50), 2), "p99_ms": round(pct(lat, 99), 2),
+                     "ok": ok, "n": len(res),
+                     "max_error": max(r["error"] for r in res)}
+    return out
 
 
 def run_ours(args):
@@ -327,6 +447,23 @@ def run_ours(args):
             e2e_ms.append(e0.elapsed_time(e1))
     e2e_val = flops_step / (statistics.mean(e2e_ms) / 1e3) / 1e9 * world
 
+    # ---- secondary workloads (least squares, batched, serving)
+    extras = {}
+    if rank == 0:
+        for sketch in sketches.values():
+            sketch.close()
+        sketches = {}
+        del outs, dA
+        torch.cuda.empty_cache()
+        wanted = [w for w in args.extras.split(",") if w]
+        if "lsq" in wanted:
+            extras["lsq"] = bench_lsq(torch, capi, inputs)
+        if "batched" in wanted:
+            extras["batched"] = bench_batched(torch, capi, inputs)
+        if "serve" in wanted:
+            extras["serve"] = bench_serve(capi, inputs, args.serve_seconds,
+                                          args.serve_pool)
+
     # ---- CPU baseline: the oracle on a bounded row sample (rank 0, N = 1)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -350,9 +487,10 @@ def run_ours(args):
             "gpu_launches": int(launches),
             "clocks": clk,
         }
+        line.update(extras)
         print(json.dumps(line), flush=True)
-    for s in sketches.values():
-        s.close()
+    for sk_ in sketches.values():
+        sk_.close()
     if dist_pg:
         dist_pg.barrier()
         dist_pg.destroy_process_group()

@@ -116,6 +116,17 @@ int sketch_create(int64_t m, int64_t n, int64_t d, int32_t dist, uint64_t seed,
 /* Release the handle and its device workspace (synchronises the device). */
 int sketch_destroy(sketch_t h);
 
+/* Change the handle's problem shape (m, n, d) and keep its seed,
+ * distribution, stream id, options and device workspaces (which grow on
+ * demand), so a long-lived handle serves a stream of differently shaped
+ * problems without reallocating.  Same limits as sketch_create. */
+int sketch_reshape(sketch_t h, int64_t m, int64_t n, int64_t d);
+
+/* Autotuning on (1, default) or off (0).  Off, the planner uses its
+ * heuristic plan (deterministic, no timing runs); a server does this so every
+ * request of a given shape runs the same kernels alone or in a mix. */
+int sketch_set_autotune(sketch_t h, int32_t enable);
+
 /* Third Philox counter word ("stream", default 0).  Instances of a batch use
  * their index, so one seed yields independent S per instance. */
 int sketch_set_stream_id(sketch_t h, uint32_t stream_id);
@@ -234,6 +245,52 @@ typedef struct {
 int sketch_lsq_solve(sketch_t h, const sketch_csc* A, const double* b,
                      double* x, double tol, int32_t maxit,
                      sketch_lsq_info* info, sketch_stream_t stream);
+
+/* ---- continuous-batching solve server ---------------------------------- */
+typedef struct sketch_server_s* sketch_server_t;
+
+typedef struct {
+  int64_t id;        /* from sketch_server_submit                          */
+  int32_t status;    /* sketch_lsq_solve's status, or SKETCH_ERR_OOM when   */
+                     /* the request can never fit the memory budget         */
+  int32_t iters;     /* LSQR iterations                                      */
+  double error;      /* Error(x) of Sec. 5.4                                 */
+  double t_submit, t_start, t_done;  /* seconds on the server's clock       */
+} sketch_server_result;
+
+/* Start a server for SAP-QR least-squares requests (Sec. 5.4): `slots`
+ * worker threads, each with its own CUDA stream and a reusable sketch handle
+ * (autotuning off, so a request runs the same kernels alone or in a mix).
+ * A request is admitted, oldest first, as soon as a slot is free and its
+ * device footprint (A, b, x, the sketch, QR and LSQR workspaces) fits in
+ * `mem_budget_bytes` together with the requests already running; admitted
+ * requests overlap on the GPU.  d = ceil(d_over_n * n); S is keyed by
+ * (seed, stream id 0, i, j) for every request.  Errors: SKETCH_ERR_ARG,
+ * SKETCH_ERR_OOM. */
+int sketch_server_create(int32_t slots, int64_t mem_budget_bytes, int32_t dist,
+                         uint64_t seed, double d_over_n, double tol,
+                         int32_t maxit, sketch_server_t* out);
+
+/* Queue one request.  A's arrays, b (m) and x (n) are HOST pointers that the
+ * caller keeps valid until the request is returned by sketch_server_poll;
+ * x receives the solution.  Returns at once with the request id. */
+int sketch_server_submit(sketch_server_t srv, const sketch_csc* A,
+                         const double* b, double* x, int64_t* id);
+
+/* Move up to `max_results` completed requests into `out` (oldest first);
+ * waits up to `wait_ms` milliseconds for at least one.  *n_out = number
+ * returned. */
+int sketch_server_poll(sketch_server_t srv, sketch_server_result* out,
+                       int32_t max_results, int32_t* n_out, int32_t wait_ms);
+
+/* Block until every submitted request has completed (they stay pollable). */
+int sketch_server_drain(sketch_server_t srv);
+
+/* Seconds since the server started (the clock of the result timestamps). */
+double sketch_server_now(sketch_server_t srv);
+
+/* Stop accepting, finish queued requests, join the workers, free all. */
+int sketch_server_destroy(sketch_server_t srv);
 
 /* ---- test hooks: the generator and S itself --------------------------- */
 /* out[4t..4t+3] = Philox4x32-10(ctr[4t..4t+3], key = seed) for t < count.

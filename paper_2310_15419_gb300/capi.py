@@ -58,6 +58,16 @@ class sketch_plan(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class sketch_server_result(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_int64), ("status", ctypes.c_int32),
+                ("iters", ctypes.c_int32), ("error", ctypes.c_double),
+                ("t_submit", ctypes.c_double), ("t_start", ctypes.c_double),
+                ("t_done", ctypes.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 class sketch_lsq_info(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int32), ("status", ctypes.c_int32),
                 ("istop", ctypes.c_int32), ("reserved", ctypes.c_int32),
@@ -104,6 +114,16 @@ SIGNATURES = [
                                  ctypes.POINTER(_I64)]),
     ("sketch_batch_status", _I32, [_VP, _VP]),
     ("sketch_batch_destroy", _I32, [_VP]),
+    ("sketch_reshape", _I32, [_VP, _I64, _I64, _I64]),
+    ("sketch_set_autotune", _I32, [_VP, _I32]),
+    ("sketch_server_create", _I32, [_I32, _I64, _I32, _U64, _D, _D, _I32,
+                                    ctypes.POINTER(_VP)]),
+    ("sketch_server_submit", _I32, [_VP, _CSCP, _VP, _VP, ctypes.POINTER(_I64)]),
+    ("sketch_server_poll", _I32, [_VP, ctypes.POINTER(sketch_server_result), _I32,
+                                  ctypes.POINTER(_I32), _I32]),
+    ("sketch_server_drain", _I32, [_VP]),
+    ("sketch_server_now", _D, [_VP]),
+    ("sketch_server_destroy", _I32, [_VP]),
 ]
 
 
@@ -199,6 +219,13 @@ class Sketch:
             self.close()
         except Exception:
             pass
+
+    def set_autotune(self, on=True):
+        _check(load().sketch_set_autotune(self.h, 1 if on else 0), self.h)
+
+    def reshape(self, m, n, d):
+        _check(load().sketch_reshape(self.h, m, n, d), self.h)
+        self.m, self.n, self.d = int(m), int(n), int(d)
 
     def set_plan(self, mode=SKETCH_MODE_AUTO, q_tiles=0, split=0, n_block=0,
                  row_groups=0, panel_rows=0, cols_per_warp=0):
@@ -298,6 +325,75 @@ class Batch:
         if getattr(self, "b", None):
             load().sketch_batch_destroy(self.b)
             self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous-batching SAP-QR least-squares server (sketch_server_*).
+
+    submit() takes host arrays (an ``inputs.CSC`` and b); they are kept alive
+    here until the request is polled.  poll() returns result dicts with the
+    solution under "x"."""
+
+    def __init__(self, slots=4, mem_budget=32 << 30, dist="pm1", seed=1,
+                 d_over_n=2.0, tol=1e-10, maxit=1000):
+        lib = load()
+        self.dist = DIST_NAMES[dist] if isinstance(dist, str) else int(dist)
+        s = ctypes.c_void_p()
+        _check(lib.sketch_server_create(int(slots), int(mem_budget), self.dist,
+                                        ctypes.c_uint64(seed), float(d_over_n),
+                                        float(tol), int(maxit), ctypes.byref(s)))
+        self.s = s
+        self.live = {}
+
+    def submit(self, A, b):
+        lib = load()
+        colptr = np.ascontiguousarray(A.colptr, np.int32)
+        rowidx = np.ascontiguousarray(A.rowidx, np.int32)
+        if A.dtype == SKETCH_BF16:
+            vals = np.ascontiguousarray(A.values_bf16, np.uint16)
+        else:
+            vals = np.ascontiguousarray(A.values, np.float32)
+        bb = np.ascontiguousarray(b, np.float64)
+        x = np.zeros(A.n, dtype=np.float64)
+        desc = sketch_csc(A.m, A.n, int(colptr[-1]), colptr.ctypes.data,
+                          rowidx.ctypes.data, vals.ctypes.data, int(A.dtype))
+        rid = ctypes.c_int64()
+        _check(lib.sketch_server_submit(self.s, ctypes.byref(desc),
+                                        ctypes.c_void_p(bb.ctypes.data),
+                                        ctypes.c_void_p(x.ctypes.data),
+                                        ctypes.byref(rid)))
+        self.live[rid.value] = (colptr, rowidx, vals, bb, x, desc)
+        return rid.value
+
+    def poll(self, max_results=64, wait_ms=0):
+        arr = (sketch_server_result * max_results)()
+        n = ctypes.c_int32()
+        _check(load().sketch_server_poll(self.s, arr, max_results, ctypes.byref(n),
+                                         int(wait_ms)))
+        out = []
+        for t in range(n.value):
+            d = arr[t].as_dict()
+            keep = self.live.pop(d["id"])
+            d["x"] = keep[4]
+            out.append(d)
+        return out
+
+    def drain(self):
+        _check(load().sketch_server_drain(self.s))
+
+    def now(self):
+        return load().sketch_server_now(self.s)
+
+    def close(self):
+        if getattr(self, "s", None):
+            load().sketch_server_destroy(self.s)
+            self.s = None
 
     def __del__(self):
         try:

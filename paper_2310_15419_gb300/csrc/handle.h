@@ -28,6 +28,7 @@ struct sketch_s {
   size_t ws_bytes = 0;
   void* d_small = nullptr;       // 256 B: status word at 0, entry count at 64
   bool counting = false;
+  bool autotune = true;
   int64_t launches = 0;          // kernels launched so far
   bool capturing = false;        // the caller's stream is being captured
   sk::LsqState* lsq = nullptr;   // least-squares workspace (lazy)
@@ -50,5 +51,6 @@ int choose_plan(sketch_t h, const sketch_csc* A, float* Ahat, cudaStream_t s,
                 sketch_plan* out);
 int check_csc_args(sketch_t h, const sketch_csc* A);
 uint64_t shape_key(const sketch_s* h, const sketch_csc* A);
+size_t lsq_workspace_bytes(int64_t m, int64_t n, int64_t d, int64_t nnz);
 void destroy_lsq_state(sketch_t h);
 }  // namespace sk

@@ -534,6 +534,12 @@ void lsqr_iteration(const LsqLayout& L, const sketch_csc* A, const CsrView& csr,
 
 }  // namespace
 
+namespace sk {
+size_t lsq_workspace_bytes(int64_t m, int64_t n, int64_t d, int64_t nnz) {
+  return layout(nullptr, m, n, d, nnz).bytes + 256;
+}
+}  // namespace sk
+
 extern "C" int sketch_lsq_solve(sketch_t h, const sketch_csc* A,
                                 const double* b, double* x, double tol,
                                 int32_t maxit, sketch_lsq_info* info,

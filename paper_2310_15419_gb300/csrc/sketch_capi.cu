@@ -301,7 +301,8 @@ int choose_plan(sketch_t h, const sketch_csc* A, float* Ahat, cudaStream_t s,
     return SKETCH_OK;
   }
   const char* env = std::getenv("SKETCH_TUNE");
-  const bool tune = !(env && env[0] == '0') && !h->capturing && Ahat != nullptr;
+  const bool tune = h->autotune && !(env && env[0] == '0') && !h->capturing &&
+                    Ahat != nullptr;
   if (!tune) {
     *out = heuristic_plan(h, A);
     h->plans[key] = *out;
@@ -403,6 +404,24 @@ int sketch_destroy(sketch_t h) {
   if (h->d_small) cudaFree(h->d_small);
   destroy_lsq_state(h);
   delete h;
+  return SKETCH_OK;
+}
+
+int sketch_reshape(sketch_t h, int64_t m, int64_t n, int64_t d) {
+  if (!h) return fail(nullptr, SKETCH_ERR_ARG, "handle is null");
+  if (m < 1 || n < 1 || d < 1 || m >= (int64_t(1) << 31) ||
+      n >= (int64_t(1) << 31) || d >= (int64_t(1) << 31))
+    return fail(h, SKETCH_ERR_ARG, "need 1 <= m, n, d < 2^31");
+  if (n * d >= (int64_t(1) << 40)) return fail(h, SKETCH_ERR_UNSUPPORTED, "d * n too large");
+  h->m = m;
+  h->n = n;
+  h->d = d;
+  return SKETCH_OK;
+}
+
+int sketch_set_autotune(sketch_t h, int32_t enable) {
+  if (!h) return SKETCH_ERR_ARG;
+  h->autotune = enable != 0;
   return SKETCH_OK;
 }
 
