@@ -266,7 +266,7 @@ def bench_serve(capi, inputs, seconds, pool_size, rate=200.0):
     +-1 S, tol 1e-10.  Requests draw their matrix from a pool of `pool_size`
     such matrices (each request has its own b).  The continuous server (8
     slots) and the one-at-a-time path (1 slot) replay the same trace."""
-    specs = inputs.serve_requests(duration_s=1e9, rate=rate)[:pool_size]
+    specs = inputs.serve_requests(rate=rate, count=pool_size)
     pool = []
     for t, (_, m, n, dens) in enumerate(specs):
         A, b, _ = inputs.lsq_problem(m, n, dens, seed=50_000 + t, noise=1e-3)

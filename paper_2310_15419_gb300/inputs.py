@@ -94,20 +94,24 @@ def _csc_from_keys(keys: np.ndarray, m: int, n: int):
 def uniform_pattern(m: int, n: int, density: float, rng) -> tuple:
     """Each entry nonzero independently with probability `density`.
 
-    Column counts ~ Binomial(m, density); positions uniform without
-    replacement (drawn with replacement, de-duplicated, deficits re-drawn)."""
-    target = rng.binomial(m, density, size=n).astype(np.int64)
-    keys = np.zeros(0, dtype=np.int64)
-    need = target.copy()
-    for _ in range(64):
-        tot = int(need.sum())
-        if tot == 0:
+    Walks the m x n positions in column-major order with Geometric(density)
+    gaps between successive nonzeros -- exactly the iid Bernoulli pattern,
+    produced already sorted by (column, row)."""
+    total = int(m) * int(n)
+    if density <= 0.0 or total == 0:
+        return _csc_from_keys(np.zeros(0, dtype=np.int64), m, n)
+    if density >= 1.0:
+        return _csc_from_keys(np.arange(total, dtype=np.int64), m, n)
+    parts, last = [], -1
+    while True:
+        want = int((total - last) * density * 1.05) + 64
+        pos = last + np.cumsum(rng.geometric(density, size=want))
+        if pos[-1] >= total:
+            parts.append(pos[pos < total])
             break
-        cols = np.repeat(np.arange(n, dtype=np.int64), need)
-        rows = rng.integers(0, m, size=tot, dtype=np.int64)
-        keys = np.unique(np.concatenate([keys, cols * m + rows]))
-        have = np.bincount(keys // m, minlength=n)
-        need = np.maximum(target - have, 0)
+        parts.append(pos)
+        last = int(pos[-1])
+    keys = np.concatenate(parts).astype(np.int64)   # col * m + row
     return _csc_from_keys(keys, m, n)
 
 
@@ -303,13 +307,14 @@ def lsq_problem(m: int, n: int, density: float, seed: int, noise: float = 1e-6,
 
 def serve_requests(seed: int = 5, rate: float = 200.0, duration_s: float = 60.0,
                    m_range=(5e4, 2e6), n_range=(100, 2000),
-                   dens_range=(5e-4, 1e-2)):
-    """Poisson arrival times and (m, n, density) per request."""
+                   dens_range=(5e-4, 1e-2), count: int | None = None):
+    """Poisson arrival times and (m, n, density) per request: the arrivals
+    within `duration_s`, or the first `count` arrivals when count is given."""
     rng = _rng(seed)
     t, out = 0.0, []
     while True:
         t += rng.exponential(1.0 / rate)
-        if t > duration_s:
+        if (count is None and t > duration_s) or (count is not None and len(out) >= count):
             break
         m = int(np.exp(rng.uniform(math.log(m_range[0]), math.log(m_range[1]))))
         n = int(rng.integers(n_range[0], n_range[1] + 1))
