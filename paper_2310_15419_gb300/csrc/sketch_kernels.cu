@@ -806,6 +806,7 @@ __global__ void __launch_bounds__(kTileWarps * 32, 1)
            const int2* __restrict__ packed, const int32_t* __restrict__ off,
            float* __restrict__ out, uint32_t k0, uint32_t k1,
            uint32_t stream_id, unsigned long long* gen_count) {
+  static_assert(CPW % 4 == 0, "columns per warp come in quads");
   // shared memory: S tile [R][32] floats, then per-warp nonzero buffers
   extern __shared__ __align__(16) float smem[];
   float* S_tile = smem;
@@ -813,19 +814,24 @@ __global__ void __launch_bounds__(kTileWarps * 32, 1)
   const int tile = blockIdx.x;
   const int g = blockIdx.z;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  int2* ent = ent_all + warp * kTileWarpBuf;
+  // lane = (column group cg, rows 4*i4 .. 4*i4+3 of the tile): the warp works
+  // on four columns at a time, eight lanes (32 rows of S) per column
+  const int cg = lane >> 3, i4 = lane & 7;
+  int2* ent = ent_all + warp * (kTileWarpBuf + 1);
+  if (lane == 0) ent[kTileWarpBuf] = make_int2(0, 0);  // the zero entry
   // this warp's columns: kw0 .. kw0 + ncol - 1 (contiguous)
   const int32_t kw0 = blockIdx.y * (kTileWarps * CPW) + warp * CPW;
   const int32_t ncol = max(0, min(CPW, n - kw0));
   const int32_t pa = static_cast<int32_t>(static_cast<int64_t>(P) * g / G);
   const int32_t pb = static_cast<int32_t>(static_cast<int64_t>(P) * (g + 1) / G);
   const int rows_valid = min(32, d - tile * 32);
-  const float* S_lane = S_tile + lane;
+  const float* S_lane = S_tile + 4 * i4;
   constexpr int OFFR = (CPW + 32) / 32;  // registers holding CPW + 1 offsets
+  constexpr int NQ = CPW / 4;
 
-  float acc[CPW];
+  float4 acc[NQ];
 #pragma unroll
-  for (int c = 0; c < CPW; ++c) acc[c] = 0.f;
+  for (int q = 0; q < NQ; ++q) acc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
   unsigned long long generated = 0;
 
   for (int32_t p = pa; p < pb; ++p) {
@@ -840,10 +846,10 @@ __global__ void __launch_bounds__(kTileWarps * 32, 1)
       const int c = lane + 32 * u;
       offv[u] = (ncol > 0 && c <= ncol) ? offp[c] : 0;
     }
-    int32_t e_lo = 0, e_hi = 0;
+    int32_t e_lo = 0;
     if (ncol > 0) {
       e_lo = __shfl_sync(0xffffffffu, offv[0], 0);
-      e_hi = __shfl_sync(0xffffffffu, offv[ncol >> 5], ncol & 31);
+      const int32_t e_hi = __shfl_sync(0xffffffffu, offv[ncol >> 5], ncol & 31);
       const int32_t cnt = min(e_hi - e_lo, kTileWarpBuf);
       for (int32_t t = lane; t < cnt; t += 32) ent[t] = packed[e_lo + t];
     }
@@ -867,37 +873,72 @@ __global__ void __launch_bounds__(kTileWarps * 32, 1)
     }
     generated += static_cast<unsigned long long>(rows) * rows_valid;
     __syncthreads();
-    // ---- sweep the columns: entries (row * 32, value) broadcast from the
-    //      warp's buffer (or from global memory past its capacity)
+    // ---- sweep: four columns per step, one per group of eight lanes ------
     const int32_t buf_end = e_lo + kTileWarpBuf;
 #pragma unroll
-    for (int c = 0; c < CPW; ++c) {
-      if (c < ncol) {  // warp-uniform
-        const int32_t lo = __shfl_sync(0xffffffffu, offv[c >> 5], c & 31);
-        const int32_t hi = __shfl_sync(0xffffffffu, offv[(c + 1) >> 5], (c + 1) & 31);
-        float v = 0.f;
-        if (hi <= buf_end) {
+    for (int q = 0; q < NQ; ++q) {
+      if (4 * q < ncol) {  // warp-uniform
+        const int c = 4 * q + cg;  // this lane's column slot (differs by group)
+        // the register holding offset c is chosen by the receiving lane, so
+        // shuffle every offset register and select afterwards
+        int32_t lo = 0, hi = 0;
+#pragma unroll
+        for (int u = 0; u < OFFR; ++u) {
+          const int32_t a = __shfl_sync(0xffffffffu, offv[u], c & 31);
+          const int32_t b = __shfl_sync(0xffffffffu, offv[u], (c + 1) & 31);
+          if ((c >> 5) == u) lo = a;
+          if (((c + 1) >> 5) == u) hi = b;
+        }
+        const int32_t cnt = c < ncol ? hi - lo : 0;
+        const int32_t steps = __reduce_max_sync(0xffffffffu, cnt);
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (__all_sync(0xffffffffu, hi <= buf_end)) {
+          // fast path: every entry is staged; lanes past their column's end
+          // read the zero entry at ent[kTileWarpBuf] (no branch per step)
+          const int2* ep = ent + (lo - e_lo);
+          const int2* zero = ent + kTileWarpBuf;
 #pragma unroll 4
-          for (int32_t e = lo; e < hi; ++e) {
-            const int2 ja = ent[e - e_lo];
-            v = fmaf(__int_as_float(ja.y), S_lane[ja.x], v);
+          for (int32_t t = 0; t < steps; ++t) {
+            const int2 ja = *(t < cnt ? ep + t : zero);
+            const float a = __int_as_float(ja.y);
+            const float4 sv = *reinterpret_cast<const float4*>(S_lane + ja.x);
+            v.x = fmaf(a, sv.x, v.x);
+            v.y = fmaf(a, sv.y, v.y);
+            v.z = fmaf(a, sv.z, v.z);
+            v.w = fmaf(a, sv.w, v.w);
           }
         } else {
-          for (int32_t e = lo; e < hi; ++e) {
-            const int2 ja = packed[e];
-            v = fmaf(__int_as_float(ja.y), S_lane[ja.x], v);
+          for (int32_t t = 0; t < steps; ++t) {
+            if (t < cnt) {
+              const int2 ja = packed[lo + t];
+              const float a = __int_as_float(ja.y);
+              const float4 sv = *reinterpret_cast<const float4*>(S_lane + ja.x);
+              v.x = fmaf(a, sv.x, v.x);
+              v.y = fmaf(a, sv.y, v.y);
+              v.z = fmaf(a, sv.z, v.z);
+              v.w = fmaf(a, sv.w, v.w);
+            }
           }
         }
-        acc[c] += v;
+        acc[q].x += v.x;
+        acc[q].y += v.y;
+        acc[q].z += v.z;
+        acc[q].w += v.w;
       }
     }
     __syncthreads();
   }
   // ---- write this row group's partial sums -------------------------------
 #pragma unroll
-  for (int c = 0; c < CPW; ++c) {
-    if (c < ncol && lane < rows_valid)
-      out[(static_cast<int64_t>(g) * n + kw0 + c) * d + tile * 32 + lane] = acc[c];
+  for (int q = 0; q < NQ; ++q) {
+    const int c = 4 * q + cg;
+    if (c < ncol) {
+      float* o = out + (static_cast<int64_t>(g) * n + kw0 + c) * d + tile * 32 + 4 * i4;
+      if (4 * i4 + 0 < rows_valid) o[0] = acc[q].x;
+      if (4 * i4 + 1 < rows_valid) o[1] = acc[q].y;
+      if (4 * i4 + 2 < rows_valid) o[2] = acc[q].z;
+      if (4 * i4 + 3 < rows_valid) o[3] = acc[q].w;
+    }
   }
   if (gen_count && threadIdx.x == 0 && generated) atomicAdd(gen_count, generated);
 }
@@ -914,7 +955,8 @@ size_t tile_workspace_bytes(int64_t m, int64_t n, int64_t d, int64_t nnz,
 }
 
 size_t tile_smem_bytes(int32_t R) {
-  return static_cast<size_t>(R) * 32 * sizeof(float) + kTileWarps * kTileWarpBuf * sizeof(int2);
+  return static_cast<size_t>(R) * 32 * sizeof(float) +
+         kTileWarps * (kTileWarpBuf + 1) * sizeof(int2);
 }
 
 cudaError_t launch_tile(const TileArgs& a, void* ws, cudaStream_t s, int* launches) {
