@@ -55,7 +55,7 @@ def parse():
                     default="auto", help="force one kernel family")
     ap.add_argument("--no-cpu", action="store_true",
                     help="skip the oracle's CPU baseline")
-    ap.add_argument("--extras", default="lsq,batched,serve",
+    ap.add_argument("--extras", default="lsq,batched,dense,serve",
                     help="secondary workloads reported beside the headline")
     ap.add_argument("--serve-seconds", type=float, default=2.0,
                     help="length of the Poisson arrival trace of the serve run")
@@ -260,6 +260,57 @@ def bench_batched(torch, capi, inputs, steps=10):
             "l2": "flushed before every replay"}
 
 
+def bench_dense(torch, capi, inputs, peaks, steps=5):
+    """The paper's Abnormal_A pattern (m=100,000, n=10,000, every 1000th row
+    dense, density 1e-3, U(-1,1) values), d = 3n = 30,000, +-1 S: the
+    densified-panel plan (tensor cores, BF16 S, three exact BF16 terms of A,
+    FP32 accumulate) against the CUDA-core REGEN plan."""
+    A = inputs.abnormal("a")
+    d = 3 * A.n
+    dA = capi.DeviceCSC(A)
+    out = torch.empty((A.n, d), dtype=torch.float32, device="cuda")
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    res = {"workload": "abnormal_a m=100,000 n=10,000 every 1000th row dense, d=30,000, +-1 S"}
+    ref = None
+    for name, plan in (("tensor_core", dict(mode=capi.SKETCH_MODE_REGEN, q_tiles=4, split=8,
+                                            tc_min_row_nnz=A.n // 2)),
+                       ("cuda_core", dict(mode=capi.SKETCH_MODE_REGEN, q_tiles=4, split=8))):
+        sk = capi.Sketch(A.m, A.n, d, "pm1", seed=1)
+        sk.set_plan(**plan)
+        sk.apply(dA, out)
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            sk.apply(dA, out)
+            e1.record()
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        if ref is None:
+            ref = out.clone()
+        else:
+            res["max_abs_diff_vs_tensor_core"] = float((out - ref).abs().max().item())
+        sk.close()
+        mean = statistics.mean(ms)
+        res[name] = {"ms": round(mean, 4),
+                     "useful_tflops": round(2.0 * d * A.nnz / (mean / 1e3) / 1e12, 3)}
+    # tensor-core roofline of the panel product: 3 BF16 terms, K padded to 32
+    K = A.nnz // A.n
+    Kp = (K + 31) // 32 * 32
+    mma_flops = 2.0 * d * A.n * 3 * Kp
+    t = res["tensor_core"]["ms"] / 1e3
+    peak = float(peaks.get("bf16_tflops", 1900.0))
+    res["tensor_core"]["mma_tflops"] = round(mma_flops / t / 1e12, 3)
+    res["tensor_core"]["roofline"] = {"bound": "tensor", "achieved": round(mma_flops / t / 1e12, 3),
+                                      "peak": peak, "unit": "TFLOP/s",
+                                      "frac": round(mma_flops / t / 1e12 / peak, 4),
+                                      "note": "whole apply (panel build + sparse rest + MMA) "
+                                              "timed; peak = measured cuBLAS BF16 burst"}
+    return res
+
+
 def bench_serve(capi, inputs, seconds, pool_size, rate=200.0):
     """Poisson arrivals at `rate`/s of SAP-QR solves with m ~ logU[5e4, 2e6],
     n ~ U[100, 2000], density ~ logU[5e-4, 1e-2], FP32 N(0,1) values, d = 2n,
@@ -460,6 +511,8 @@ def run_ours(args):
             extras["lsq"] = bench_lsq(torch, capi, inputs)
         if "batched" in wanted:
             extras["batched"] = bench_batched(torch, capi, inputs)
+        if "dense" in wanted:
+            extras["dense_panel"] = bench_dense(torch, capi, inputs, measured_peaks()[0])
         if "serve" in wanted:
             extras["serve"] = bench_serve(capi, inputs, args.serve_seconds,
                                           args.serve_pool)

@@ -104,6 +104,12 @@ typedef struct {
   int32_t row_groups;    /* PANEL, TILE: number of row ranges of A         */
   int32_t panel_rows;    /* TILE: rows of A per panel, 8..1152 (m1)        */
   int32_t cols_per_warp; /* TILE: 4, 16 or 64                              */
+  int32_t tc_min_row_nnz;/* +-1 only: rows of A with at least this many     */
+                         /* nonzeros form a dense panel multiplied on the   */
+                         /* tensor cores (BF16 S, A split exactly into three */
+                         /* BF16 terms, FP32 accumulate); 0 = off.  Such a  */
+                         /* plan reads the panel height back to the host    */
+                         /* once per call (not capturable in a graph).      */
 } sketch_plan;
 
 /* Create a sketch handle for A (m x n) and S (d x m) with the distribution

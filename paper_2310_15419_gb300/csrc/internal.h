@@ -23,6 +23,7 @@ struct RegenArgs {
   int32_t split;    // 1, 2, 4, 8
   int* status;
   unsigned long long* gen_count;  // may be null
+  const int32_t* skip = nullptr;  // rows with skip[j] >= 0 are left out
 };
 cudaError_t launch_regen(const RegenArgs& a, cudaStream_t s);
 
@@ -88,6 +89,7 @@ struct TileArgs {
   int32_t cpw;  // columns per warp: 4, 16 or 64 (n1 = 16 * cpw per CTA)
   int* status;
   unsigned long long* gen_count;
+  const int32_t* skip = nullptr;  // rows with skip[j] >= 0 are left out
 };
 size_t tile_workspace_bytes(int64_t m, int64_t n, int64_t d, int64_t nnz,
                             int32_t R, int32_t G);
@@ -108,6 +110,41 @@ cudaError_t launch_debug_S(int dist, uint32_t k0, uint32_t k1,
 cudaError_t launch_bench_generator(int dist, uint32_t k0, uint32_t k1,
                                    int64_t threads, int64_t blocks_per_thread,
                                    float* sink, cudaStream_t s);
+
+// Tensor-core densified panels (dense_tc.cu).
+struct DenseArgs {
+  int32_t m, n, d;
+  int64_t nnz;
+  int32_t dtype;
+  const int32_t* colptr;
+  const int32_t* rowidx;
+  const void* values;
+  int32_t tau;   // rows with at least tau nonzeros go to the panel
+  int64_t kmax;  // capacity: nnz / tau bounds the number of such rows
+  uint32_t k0, k1, stream_id;
+  int* status;
+};
+struct DenseView {
+  const int32_t* didx;  // m: dense index of a row, or -1
+  const int32_t* rows;  // K: dense row ids
+  const int32_t* Kdev;  // device copy of K
+  const uint16_t* A3;   // n x 3Kp BF16 terms (column-major, K fastest)
+  int32_t Kp;
+};
+size_t dense_workspace_bytes(int64_t m, int64_t n, int64_t kmax);
+cudaError_t select_dense_rows(const DenseArgs& a, void* ws, DenseView* out, cudaStream_t s,
+                              int* launches);
+cudaError_t build_dense_panel(const DenseArgs& a, int32_t K, DenseView* v, cudaStream_t s,
+                              int* launches);
+cudaError_t launch_tc_gemm(const DenseArgs& a, const DenseView& v, float* Ahat,
+                           cudaStream_t s, int* launches);
+
+// Shared building blocks (sketch_kernels.cu).
+int64_t scan_bytes_for(int64_t len);
+cudaError_t scan_i32(const int32_t* in, int32_t* out, int64_t len, char* tmp,
+                     cudaStream_t s, int* launches);
+cudaError_t row_counts(int64_t nnz, int32_t m, const int32_t* rowidx, int32_t* cnt,
+                       int* status, cudaStream_t s);
 
 int num_sms();
 

@@ -126,8 +126,24 @@ int32_t default_row_groups(const sketch_s* h, const sketch_csc* A,
   return static_cast<int32_t>(g);
 }
 
+static int64_t dense_capacity(const sketch_csc* A, const sketch_plan& p) {
+  // every dense row holds at least tau nonzeros, so at most nnz / tau rows
+  return std::max<int64_t>(1, std::min<int64_t>(A->m, A->nnz / std::max(1, p.tc_min_row_nnz)));
+}
+
+static size_t sparse_workspace_bytes(const sketch_s* h, const sketch_csc* A,
+                                     const sketch_plan& p);
+
 size_t plan_workspace_bytes(const sketch_s* h, const sketch_csc* A,
                             const sketch_plan& p) {
+  size_t b = sparse_workspace_bytes(h, A, p);
+  if (p.tc_min_row_nnz > 0)
+    b = align256(b) + dense_workspace_bytes(A->m, A->n, dense_capacity(A, p));
+  return b;
+}
+
+static size_t sparse_workspace_bytes(const sketch_s* h, const sketch_csc* A,
+                                     const sketch_plan& p) {
   if (p.mode == SKETCH_MODE_TILE)
     return tile_workspace_bytes(A->m, A->n, h->d, A->nnz, p.panel_rows, p.row_groups);
   if (p.mode != SKETCH_MODE_PANEL) return 0;
@@ -138,6 +154,12 @@ size_t plan_workspace_bytes(const sketch_s* h, const sketch_csc* A,
 }
 
 int check_plan(sketch_t h, const sketch_plan& p) {
+  if (p.tc_min_row_nnz < 0) return fail(h, SKETCH_ERR_ARG, "tc_min_row_nnz < 0");
+  if (p.tc_min_row_nnz > 0 && h->dist != SKETCH_PM1)
+    return fail(h, SKETCH_ERR_UNSUPPORTED,
+                "tensor-core panels need +-1 S (exact in BF16)");
+  if (p.tc_min_row_nnz > 0 && p.mode == SKETCH_MODE_PANEL)
+    return fail(h, SKETCH_ERR_UNSUPPORTED, "tensor-core panels pair with REGEN or TILE");
   if (p.mode == SKETCH_MODE_REGEN) {
     if (p.q_tiles < 1 || p.q_tiles > 4)
       return fail(h, SKETCH_ERR_ARG, "q_tiles must be 1..4");
@@ -161,6 +183,10 @@ int check_plan(sketch_t h, const sketch_plan& p) {
   return SKETCH_OK;
 }
 
+int run_sparse(sketch_t h, const sketch_csc* A, float* Ahat, const sketch_plan& p,
+               void* ws, cudaStream_t s, int* status, unsigned long long* gen,
+               const int32_t* skip);
+
 // Run one plan.  `ws` must hold plan_workspace_bytes.
 int run_plan(sketch_t h, const sketch_csc* A, float* Ahat,
              const sketch_plan& p, void* ws, cudaStream_t s) {
@@ -178,6 +204,55 @@ int run_plan(sketch_t h, const sketch_csc* A, float* Ahat,
     cudaError_t e = cudaMemsetAsync(Ahat, 0, sizeof(float) * A->n * h->d, s);
     return e == cudaSuccess ? SKETCH_OK : cuda_fail(h, e, "cudaMemsetAsync");
   }
+  // tensor-core densified panel: pick its rows first (the sparse kernels
+  // then leave them out); the panel's product is added at the end
+  DenseArgs da{};
+  DenseView dv{};
+  int32_t K = 0;
+  if (p.tc_min_row_nnz > 0) {
+    if (h->capturing)
+      return fail(h, SKETCH_ERR_UNSUPPORTED, "a tensor-core plan cannot be captured");
+    da.m = static_cast<int32_t>(A->m);
+    da.n = static_cast<int32_t>(A->n);
+    da.d = static_cast<int32_t>(h->d);
+    da.nnz = A->nnz;
+    da.dtype = A->dtype;
+    da.colptr = A->colptr;
+    da.rowidx = A->rowidx;
+    da.values = A->values;
+    da.tau = p.tc_min_row_nnz;
+    da.kmax = dense_capacity(A, p);
+    da.k0 = h->k0;
+    da.k1 = h->k1;
+    da.stream_id = h->stream_id;
+    da.status = status;
+    void* dws = static_cast<char*>(ws) + align256(sparse_workspace_bytes(h, A, p));
+    int nl = 0;
+    cudaError_t e = select_dense_rows(da, dws, &dv, s, &nl);
+    h->launches += nl;
+    if (e != cudaSuccess) return cuda_fail(h, e, "dense row selection");
+    e = cudaMemcpyAsync(&K, dv.Kdev, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "dense row count");
+    if (K > 0) {
+      nl = 0;
+      e = build_dense_panel(da, K, &dv, s, &nl);
+      h->launches += nl;
+      if (e != cudaSuccess) return cuda_fail(h, e, "dense panel");
+    }
+  }
+  const int32_t* skip = K > 0 ? dv.didx : nullptr;
+  int rc_sparse = run_sparse(h, A, Ahat, p, ws, s, status, gen, skip);
+  if (rc_sparse != SKETCH_OK || K == 0) return rc_sparse;
+  int nl = 0;
+  cudaError_t e = launch_tc_gemm(da, dv, Ahat, s, &nl);
+  h->launches += nl;
+  return e == cudaSuccess ? SKETCH_OK : cuda_fail(h, e, "tensor-core panel");
+}
+
+int run_sparse(sketch_t h, const sketch_csc* A, float* Ahat, const sketch_plan& p,
+               void* ws, cudaStream_t s, int* status, unsigned long long* gen,
+               const int32_t* skip) {
   if (p.mode == SKETCH_MODE_REGEN) {
     RegenArgs a{};
     a.m = static_cast<int32_t>(A->m);
@@ -196,6 +271,7 @@ int run_plan(sketch_t h, const sketch_csc* A, float* Ahat,
     a.split = p.split;
     a.status = status;
     a.gen_count = gen;
+    a.skip = skip;
     cudaError_t e = launch_regen(a, s);
     h->launches += 1;
     return e == cudaSuccess ? SKETCH_OK : cuda_fail(h, e, "regen kernel");
@@ -221,6 +297,7 @@ int run_plan(sketch_t h, const sketch_csc* A, float* Ahat,
     a.cpw = p.cols_per_warp;
     a.status = status;
     a.gen_count = gen;
+    a.skip = skip;
     int nl = 0;
     cudaError_t e = launch_tile(a, ws, s, &nl);
     h->launches += nl;

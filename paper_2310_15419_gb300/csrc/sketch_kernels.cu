@@ -48,7 +48,8 @@ __device__ __forceinline__ unsigned long long regen_accumulate(
     int32_t lo, int32_t hi, int32_t m, int32_t d0, int rows_valid,
     const int32_t* __restrict__ rowidx, const VT* __restrict__ vals,
     uint32_t k0, uint32_t k1, uint32_t stream_id, int* status,
-    uint32_t (*stage)[4 * Q + 4], float (&outer)[Q][4]) {
+    uint32_t (*stage)[4 * Q + 4], float (&outer)[Q][4],
+    const int32_t* __restrict__ skip = nullptr) {
   const int lane = threadIdx.x & 31;
   // Two-level sums: a batch of 32 nonzeros accumulates in `inner`, batch
   // sums are added to `outer` with Kahan compensation (`comp`), so the FP32
@@ -76,6 +77,8 @@ __device__ __forceinline__ unsigned long long regen_accumulate(
         atomicOr(status, kStatusBadRow);
         j = 0;
         a = 0.f;
+      } else if (skip && skip[j] >= 0) {
+        a = 0.f;  // a densified row: the tensor-core panel covers it
       }
     }
     generated += static_cast<unsigned long long>(cnt) * rows_valid;
@@ -149,7 +152,7 @@ __global__ void __launch_bounds__(kRegenWarps * 32, 2)
             const int32_t* __restrict__ rowidx, const VT* __restrict__ vals,
             float* __restrict__ Ahat, uint32_t k0, uint32_t k1,
             uint32_t stream_id, int* status,
-            unsigned long long* gen_count) {
+            unsigned long long* gen_count, const int32_t* __restrict__ skip) {
   constexpr int TD = 128 * Q;          // rows of S per item
   constexpr int SW = 4 * Q + 4;        // staged words per nonzero (+pad)
   __shared__ float red[kRegenWarps][TD];
@@ -185,7 +188,7 @@ __global__ void __launch_bounds__(kRegenWarps * 32, 2)
     const int32_t hi = p0 + min(len, (sub + 1) * chunk);
     generated = regen_accumulate<DIST, Q, VT>(lo, hi, m, d0, min(TD, d - d0), rowidx,
                                              vals, k0, k1, stream_id, status,
-                                             stage[warp], outer);
+                                             stage[warp], outer, skip);
   }
 
   if (split == 1) {
@@ -318,7 +321,7 @@ static cudaError_t launch_regen_q(const RegenArgs& a, cudaStream_t s) {
   case QQ:                                                                  \
     k_regen<DIST, QQ, VT><<<grid, block, 0, s>>>(                           \
         a.m, a.n, a.d, a.split, a.colptr, a.rowidx, v, a.Ahat, a.k0, a.k1, \
-        a.stream_id, a.status, a.gen_count);                                \
+        a.stream_id, a.status, a.gen_count, a.skip);                        \
     break;
   switch (a.q_tiles) {
     SK_REGEN_CASE(1)
@@ -780,7 +783,8 @@ __global__ void k_panel_copy(int32_t n, int32_t P, int32_t R, int32_t m,
                              const VT* __restrict__ vals,
                              const int32_t* __restrict__ pp,
                              const int32_t* __restrict__ off,
-                             int2* __restrict__ packed, int* status) {
+                             int2* __restrict__ packed, int* status,
+                             const int32_t* __restrict__ skip) {
   const int64_t total = static_cast<int64_t>(P) * n;
   for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
        t < total; t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
@@ -791,7 +795,8 @@ __global__ void k_panel_copy(int32_t n, int32_t P, int32_t R, int32_t m,
     for (int32_t e = lo; e < hi; ++e, ++dst) {
       const int32_t jl = rowidx[e] - j0;
       if (static_cast<uint32_t>(jl) < static_cast<uint32_t>(R) && j0 + jl < m) {
-        packed[dst] = make_int2(jl * 32, __float_as_int(to_f32(vals[e])));
+        const float a = (skip && skip[j0 + jl] >= 0) ? 0.f : to_f32(vals[e]);
+        packed[dst] = make_int2(jl * 32, __float_as_int(a));
       } else {
         atomicOr(status, kStatusBadRow);
         packed[dst] = make_int2(0, 0);
@@ -992,11 +997,11 @@ cudaError_t launch_tile(const TileArgs& a, void* ws, cudaStream_t s, int* launch
     if (a.dtype == 0)
       k_panel_copy<float><<<grid_for(P * a.n), 256, 0, s>>>(
           a.n, static_cast<int32_t>(P), a.R, a.m, a.rowidx,
-          static_cast<const float*>(a.values), pp, off, packed, a.status);
+          static_cast<const float*>(a.values), pp, off, packed, a.status, a.skip);
     else
       k_panel_copy<__nv_bfloat16><<<grid_for(P * a.n), 256, 0, s>>>(
           a.n, static_cast<int32_t>(P), a.R, a.m, a.rowidx,
-          static_cast<const __nv_bfloat16*>(a.values), pp, off, packed, a.status);
+          static_cast<const __nv_bfloat16*>(a.values), pp, off, packed, a.status, a.skip);
     ++*launches;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
@@ -1163,6 +1168,21 @@ cudaError_t launch_bench_generator(int dist, uint32_t k0, uint32_t k1,
     default:
       return cudaErrorInvalidValue;
   }
+  return cudaGetLastError();
+}
+
+int64_t scan_bytes_for(int64_t len) { return scan_levels_bytes(len); }
+
+cudaError_t scan_i32(const int32_t* in, int32_t* out, int64_t len, char* tmp,
+                     cudaStream_t s, int* launches) {
+  return exclusive_scan(in, out, len, tmp, s, launches);
+}
+
+cudaError_t row_counts(int64_t nnz, int32_t m, const int32_t* rowidx, int32_t* cnt,
+                       int* status, cudaStream_t s) {
+  if (nnz <= 0) return cudaSuccess;
+  const int64_t blocks = std::min<int64_t>((nnz + 255) / 256, 32LL * num_sms());
+  k_row_count<<<static_cast<unsigned>(blocks), 256, 0, s>>>(nnz, m, rowidx, cnt, status);
   return cudaGetLastError();
 }
 

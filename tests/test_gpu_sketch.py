@@ -259,3 +259,53 @@ def test_skew_large_sampled_columns(skew_large, dist):
         ref = oracle_sketch(col, d, dist)[:, 0]
         assert rel_fro(got[k], ref) <= TOL, (dist, k)
     sk.close()
+
+
+# ------------------------------------------------ tensor-core dense panels
+def _dense_rows_matrix(m, n, every, dens, integer, seed):
+    """Every `every`-th row dense (the paper's Abnormal_A pattern) on top of a
+    uniformly sparse background."""
+    rng = np.random.default_rng(seed)
+    bg = inputs.integer_uniform(m, n, dens, seed=seed) if integer else \
+        inputs.float_uniform(m, n, dens, seed=seed)
+    S = bg.to_scipy().tolil()
+    for j in range(0, m, every):
+        vals = rng.integers(1, 4, size=n) * rng.choice([-1, 1], size=n) if integer \
+            else rng.uniform(-1, 1, size=n)
+        S[j, :] = vals
+    C = S.tocsc()
+    C.sort_indices()
+    return inputs.CSC(m, n, C.indptr.astype(np.int32), C.indices.astype(np.int32),
+                      C.data.astype(np.float32))
+
+
+TC_PLANS = [dict(mode=capi.SKETCH_MODE_REGEN, q_tiles=2, split=2, tc_min_row_nnz=64),
+            dict(mode=capi.SKETCH_MODE_TILE, panel_rows=512, row_groups=4,
+                 cols_per_warp=16, tc_min_row_nnz=40)]
+
+
+@pytest.mark.parametrize("plan", TC_PLANS)
+def test_tensor_core_panel_integer_bit_exact(plan):
+    A = _dense_rows_matrix(9000, 300, 97, 0.003, True, seed=31)   # 93 dense rows
+    for d in (300, 257):
+        ref = oracle_sketch(A, d, "pm1")
+        got = gpu_sketch(A, d, "pm1", plan=plan)
+        assert np.array_equal(got, ref), d
+
+
+@pytest.mark.parametrize("plan", TC_PLANS)
+def test_tensor_core_panel_float_tolerance(plan):
+    A = _dense_rows_matrix(9000, 300, 50, 0.003, False, seed=32)
+    ref = oracle_sketch(A, 301, "pm1")
+    got = gpu_sketch(A, 301, "pm1", plan=plan)
+    assert rel_fro(got, ref) <= TOL
+
+
+def test_tensor_core_panel_without_dense_rows_and_bad_dist():
+    A = inputs.integer_uniform(4000, 50, 0.01, seed=33)
+    got = gpu_sketch(A, 200, "pm1", plan=TC_PLANS[0])
+    assert np.array_equal(got, oracle_sketch(A, 200, "pm1"))
+    sk = capi.Sketch(A.m, A.n, 64, "uniform")
+    with pytest.raises(capi.SketchError) as e:
+        sk.set_plan(**TC_PLANS[0])
+    assert e.value.code == capi.SKETCH_ERR_UNSUPPORTED
