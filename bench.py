@@ -408,6 +408,9 @@ def run_ours(args):
     torch.cuda.synchronize()
 
     launches0 = sum(s.launch_count() for s in sketches.values())
+    # our kernels launched before the timed region: the generator probe
+    # (3 distributions x 6 launches) plus every sketch launch so far
+    launches_before = 6 * len(DISTS) + launches0
     per_dist = {dist: [] for dist in DISTS}
     step_ms = []
     clocks = ClockSampler(local)
@@ -538,6 +541,7 @@ def run_ours(args):
                     "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
             "cpu_baseline": cpu,
             "gpu_launches": int(launches),
+            "launches_before_timed": int(launches_before),
             "clocks": clk,
         }
         line.update(extras)

@@ -824,6 +824,9 @@ __global__ void __launch_bounds__(kTileWarps * 32, 1)
   const int cg = lane >> 3, i4 = lane & 7;
   int2* ent = ent_all + warp * (kTileWarpBuf + 1);
   if (lane == 0) ent[kTileWarpBuf] = make_int2(0, 0);  // the zero entry
+  // this warp's column offsets for the current panel (CPW + 1 values)
+  int32_t* offs = reinterpret_cast<int32_t*>(ent_all + kTileWarps * (kTileWarpBuf + 1)) +
+                  warp * (CPW + 4);
   // this warp's columns: kw0 .. kw0 + ncol - 1 (contiguous)
   const int32_t kw0 = blockIdx.y * (kTileWarps * CPW) + warp * CPW;
   const int32_t ncol = max(0, min(CPW, n - kw0));
@@ -857,6 +860,11 @@ __global__ void __launch_bounds__(kTileWarps * 32, 1)
       const int32_t e_hi = __shfl_sync(0xffffffffu, offv[ncol >> 5], ncol & 31);
       const int32_t cnt = min(e_hi - e_lo, kTileWarpBuf);
       for (int32_t t = lane; t < cnt; t += 32) ent[t] = packed[e_lo + t];
+#pragma unroll
+      for (int u = 0; u < OFFR; ++u) {
+        const int c = lane + 32 * u;
+        if (c <= ncol) offs[c] = offv[u];
+      }
     }
     // ---- S(tile, j0 .. j0 + rows) once into shared memory ---------------
     for (int idx = threadIdx.x; idx < rows * 8; idx += kTileWarps * 32) {
@@ -884,34 +892,47 @@ __global__ void __launch_bounds__(kTileWarps * 32, 1)
     for (int q = 0; q < NQ; ++q) {
       if (4 * q < ncol) {  // warp-uniform
         const int c = 4 * q + cg;  // this lane's column slot (differs by group)
-        // the register holding offset c is chosen by the receiving lane, so
-        // shuffle every offset register and select afterwards
-        int32_t lo = 0, hi = 0;
-#pragma unroll
-        for (int u = 0; u < OFFR; ++u) {
-          const int32_t a = __shfl_sync(0xffffffffu, offv[u], c & 31);
-          const int32_t b = __shfl_sync(0xffffffffu, offv[u], (c + 1) & 31);
-          if ((c >> 5) == u) lo = a;
-          if (((c + 1) >> 5) == u) hi = b;
-        }
+        const int32_t lo = offs[c], hi = offs[c + 1];
         const int32_t cnt = c < ncol ? hi - lo : 0;
         const int32_t steps = __reduce_max_sync(0xffffffffu, cnt);
         float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (__all_sync(0xffffffffu, hi <= buf_end)) {
+        if (__all_sync(0xffffffffu, c >= ncol || hi <= buf_end)) {
           // fast path: every entry is staged; lanes past their column's end
-          // read the zero entry at ent[kTileWarpBuf] (no branch per step)
+          // read the zero entry at ent[kTileWarpBuf] (no branch per step).
+          // Two steps per iteration with separate accumulators: both
+          // entries, then both S loads, then the FMAs (more loads in flight)
           const int2* ep = ent + (lo - e_lo);
           const int2* zero = ent + kTileWarpBuf;
-#pragma unroll 4
-          for (int32_t t = 0; t < steps; ++t) {
+          float4 w = make_float4(0.f, 0.f, 0.f, 0.f);
+          int32_t t = 0;
+          for (; t + 1 < steps; t += 2) {
             const int2 ja = *(t < cnt ? ep + t : zero);
-            const float a = __int_as_float(ja.y);
-            const float4 sv = *reinterpret_cast<const float4*>(S_lane + ja.x);
-            v.x = fmaf(a, sv.x, v.x);
-            v.y = fmaf(a, sv.y, v.y);
-            v.z = fmaf(a, sv.z, v.z);
-            v.w = fmaf(a, sv.w, v.w);
+            const int2 jb = *(t + 1 < cnt ? ep + t + 1 : zero);
+            const float4 sa = *reinterpret_cast<const float4*>(S_lane + ja.x);
+            const float4 sb = *reinterpret_cast<const float4*>(S_lane + jb.x);
+            const float a = __int_as_float(ja.y), b = __int_as_float(jb.y);
+            v.x = fmaf(a, sa.x, v.x);
+            v.y = fmaf(a, sa.y, v.y);
+            v.z = fmaf(a, sa.z, v.z);
+            v.w = fmaf(a, sa.w, v.w);
+            w.x = fmaf(b, sb.x, w.x);
+            w.y = fmaf(b, sb.y, w.y);
+            w.z = fmaf(b, sb.z, w.z);
+            w.w = fmaf(b, sb.w, w.w);
           }
+          if (t < steps) {
+            const int2 ja = *(t < cnt ? ep + t : zero);
+            const float4 sa = *reinterpret_cast<const float4*>(S_lane + ja.x);
+            const float a = __int_as_float(ja.y);
+            v.x = fmaf(a, sa.x, v.x);
+            v.y = fmaf(a, sa.y, v.y);
+            v.z = fmaf(a, sa.z, v.z);
+            v.w = fmaf(a, sa.w, v.w);
+          }
+          v.x += w.x;
+          v.y += w.y;
+          v.z += w.z;
+          v.w += w.w;
         } else {
           for (int32_t t = 0; t < steps; ++t) {
             if (t < cnt) {
@@ -961,7 +982,8 @@ size_t tile_workspace_bytes(int64_t m, int64_t n, int64_t d, int64_t nnz,
 
 size_t tile_smem_bytes(int32_t R) {
   return static_cast<size_t>(R) * 32 * sizeof(float) +
-         kTileWarps * (kTileWarpBuf + 1) * sizeof(int2);
+         kTileWarps * (kTileWarpBuf + 1) * sizeof(int2) +
+         kTileWarps * (64 + 4) * sizeof(int32_t);  // offsets, up to 64 columns per warp
 }
 
 cudaError_t launch_tile(const TileArgs& a, void* ws, cudaStream_t s, int* launches) {
