@@ -224,23 +224,23 @@ __global__ void __launch_bounds__(NT)
 }
 
 // out[k] = scale * sum_{e in column k} val[e] u[row[e]],  scale = inv_beta
-// (mode 0) or 1 (mode 1).
+// (mode 0) or 1 (mode 1).  One CTA per column (grid-stride), fixed-order
+// reduction, so even a few long columns keep the GPU busy.
 template <typename VT>
-__global__ void k_spmv_cols(int32_t n, const int32_t* __restrict__ colptr,
-                            const int32_t* __restrict__ rowidx,
-                            const VT* __restrict__ vals, const double* __restrict__ u,
-                            double* __restrict__ out, const Scalars* sc, int mode) {
+__global__ void __launch_bounds__(256)
+    k_spmv_cols(int32_t n, const int32_t* __restrict__ colptr,
+                const int32_t* __restrict__ rowidx, const VT* __restrict__ vals,
+                const double* __restrict__ u, double* __restrict__ out,
+                const Scalars* sc, int mode) {
+  __shared__ double red[33];
   if (mode == 0 && sc->done) return;
   const double scale = mode == 0 ? sc->inv_beta : 1.0;
-  const int lane = threadIdx.x & 31;
-  const int64_t warps = static_cast<int64_t>(gridDim.x) * (blockDim.x >> 5);
-  for (int64_t k = blockIdx.x * static_cast<int64_t>(blockDim.x >> 5) + (threadIdx.x >> 5);
-       k < n; k += warps) {
+  for (int64_t k = blockIdx.x; k < n; k += gridDim.x) {
     double s = 0.0;
-    for (int32_t e = colptr[k] + lane; e < colptr[k + 1]; e += 32)
+    for (int32_t e = colptr[k] + threadIdx.x; e < colptr[k + 1]; e += blockDim.x)
       s += val_at(vals, e) * u[rowidx[e]];
-    s = warp_sum(s);
-    if (lane == 0) out[k] = scale * s;
+    s = block_sum<256>(s, red);
+    if (threadIdx.x == 0) out[k] = scale * s;
   }
 }
 
@@ -431,6 +431,9 @@ struct LsqState {
   cudaEvent_t ev[6] = {};
   cudaGraphExec_t graph = nullptr;
   const void* graph_key[6] = {};  // what the captured iterations read/write
+  cudaGraphExec_t qr_graph = nullptr;  // the QR's n launches, per shape
+  int64_t qr_key[3] = {-1, -1, -1};     // (d, n, workspace address) of qr_graph
+  int64_t qr_seen[3] = {-1, -1, -1};    // shape of the previous solve
 };
 
 void destroy_lsq_state(sketch_t h) {
@@ -438,6 +441,7 @@ void destroy_lsq_state(sketch_t h) {
   LsqState* st = h->lsq;
   if (st->ls) cudaStreamSynchronize(st->ls);
   if (st->graph) cudaGraphExecDestroy(st->graph);
+  if (st->qr_graph) cudaGraphExecDestroy(st->qr_graph);
   for (auto& e : st->ev)
     if (e) cudaEventDestroy(e);
   if (st->ls) cudaStreamDestroy(st->ls);
@@ -500,7 +504,7 @@ LsqLayout layout(void* base, int64_t m, int64_t n, int64_t d, int64_t nnz) {
 template <typename VT>
 void launch_spmv_cols(const sketch_csc* A, const double* u, double* out,
                       const Scalars* sc, int mode, cudaStream_t s) {
-  const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((A->n + 7) / 8, 32LL * num_sms()));
+  const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>(A->n, 64LL * num_sms()));
   k_spmv_cols<VT><<<static_cast<unsigned>(blocks), 256, 0, s>>>(
       static_cast<int32_t>(A->n), A->colptr, A->rowidx,
       static_cast<const VT*>(A->values), u, out, sc, mode);
@@ -570,6 +574,10 @@ extern "C" int sketch_lsq_solve(sketch_t h, const sketch_csc* A,
       cudaGraphExecDestroy(st.graph);
       st.graph = nullptr;
     }
+    if (st.qr_graph) {
+      cudaGraphExecDestroy(st.qr_graph);
+      st.qr_graph = nullptr;
+    }
     st.ws = nullptr;
     st.ws_bytes = 0;
     if (cudaMalloc(&st.ws, need) != cudaSuccess) {
@@ -591,28 +599,63 @@ extern "C" int sketch_lsq_solve(sketch_t h, const sketch_csc* A,
   // ---- 1. sketch ------------------------------------------------------------
   if ((rc = sketch_apply(h, A, L.Ahat, reinterpret_cast<sketch_stream_t>(s))) != SKETCH_OK)
     return rc;
+  cudaError_t e = cudaSuccess;
   cudaEventRecord(st.ev[1], s);
 
   // ---- 2. FP64 Householder QR of the sketch, 3. R^{-1} ----------------------
   cudaMemsetAsync(L.status, 0, sizeof(int), s);
   const int64_t dn = d * n;
   const unsigned gb = static_cast<unsigned>(std::max<int64_t>(1, 16LL * num_sms()));
-  k_to_double<<<gb, 256, 0, s>>>(dn, L.Ahat, L.W);
-  k_qr_first<<<1, kQrThreads, 0, s>>>(L.W, d, L.tau);
-  for (int k = 0; k + 1 < n; ++k)
-    k_qr_step<<<static_cast<unsigned>(n - k - 1), kQrThreads, 0, s>>>(
-        L.W, d, static_cast<int>(n), k, L.tau);
-  k_extract_r<<<gb, 256, 0, s>>>(L.W, d, static_cast<int>(n), L.Rrow, L.status);
-  k_trtri<<<gemv_blocks(n), 256, 0, s>>>(L.Rrow, static_cast<int>(n), L.Rinv, L.RinvT);
+  {
+    // the QR is n dependent launches.  When a shape repeats (same d, n and
+    // workspace as the previous solve) they are captured once as a graph
+    // and replayed; a one-off shape launches them directly.
+    const int64_t qk[3] = {d, n, static_cast<int64_t>(reinterpret_cast<intptr_t>(st.ws))};
+    auto enqueue_qr = [&]() {
+      k_to_double<<<gb, 256, 0, s>>>(dn, L.Ahat, L.W);
+      k_qr_first<<<1, kQrThreads, 0, s>>>(L.W, d, L.tau);
+      for (int k = 0; k + 1 < n; ++k)
+        k_qr_step<<<static_cast<unsigned>(n - k - 1), kQrThreads, 0, s>>>(
+            L.W, d, static_cast<int>(n), k, L.tau);
+      k_extract_r<<<gb, 256, 0, s>>>(L.W, d, static_cast<int>(n), L.Rrow, L.status);
+      k_trtri<<<gemv_blocks(n), 256, 0, s>>>(L.Rrow, static_cast<int>(n), L.Rinv, L.RinvT);
+    };
+    const bool repeat = std::memcmp(qk, st.qr_seen, sizeof(qk)) == 0;
+    std::memcpy(st.qr_seen, qk, sizeof(qk));
+    if (st.qr_graph && std::memcmp(qk, st.qr_key, sizeof(qk)) != 0) {
+      cudaGraphExecDestroy(st.qr_graph);
+      st.qr_graph = nullptr;
+    }
+    if (!st.qr_graph && repeat) {
+      cudaGraph_t g = nullptr;
+      e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+      if (e != cudaSuccess) return cuda_fail(h, e, "begin QR capture");
+      enqueue_qr();
+      e = cudaStreamEndCapture(s, &g);
+      if (e != cudaSuccess) return cuda_fail(h, e, "end QR capture");
+      e = cudaGraphInstantiate(&st.qr_graph, g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) {
+        st.qr_graph = nullptr;
+        return cuda_fail(h, e, "QR graph instantiate");
+      }
+      std::memcpy(st.qr_key, qk, sizeof(qk));
+    }
+    if (st.qr_graph) {
+      e = cudaGraphLaunch(st.qr_graph, s);
+      if (e != cudaSuccess) return cuda_fail(h, e, "QR graph launch");
+    } else {
+      enqueue_qr();
+    }
+  }
   h->launches += 4 + (n - 1);
   cudaEventRecord(st.ev[2], s);
 
   // ---- 4. LSQR on A R^{-1} ---------------------------------------------------
   CsrView csr{};
   int nl = 0;
-  cudaError_t e = build_csr(static_cast<int32_t>(m), static_cast<int32_t>(n), nnz,
-                            A->colptr, A->rowidx, A->values, A->dtype, L.csr_ws,
-                            &csr, L.status, s, &nl);
+  e = build_csr(static_cast<int32_t>(m), static_cast<int32_t>(n), nnz, A->colptr,
+                A->rowidx, A->values, A->dtype, L.csr_ws, &csr, L.status, s, &nl);
   if (e != cudaSuccess) return cuda_fail(h, e, "csr build (lsq)");
   k_sort_rows<<<gb, 256, 0, s>>>(static_cast<int32_t>(m), csr.rowptr, csr.ccol, csr.cval,
                                  L.scol, L.sval);
