@@ -28,7 +28,7 @@ namespace sk {
 namespace {
 
 constexpr int kIterPerGraph = 8;
-constexpr int kRedBlocks = 512;  // partial sums of m-vector reductions
+constexpr int kRedBlocks = 2048;  // partial sums of m-vector reductions
 
 struct Scalars {
   double alpha, beta, inv_beta, rhobar, phibar, anorm2, bnorm;
@@ -143,26 +143,27 @@ __global__ void k_extract_r(const double* __restrict__ W, int64_t d, int n,
   }
 }
 
-// X = R^{-1} by back substitution, one warp per column j of X:
-// X[j][j] = 1/R[j][j];  X[i][j] = -(sum_{c=i+1..j} R[i][c] X[c][j]) / R[i][i].
-// Writes Xrow (row-major X) and XTrow (row-major X^T).
-__global__ void k_trtri(const double* __restrict__ Rrow, int n,
+// X = R^{-1} by back substitution, one warp per column j of X, in the
+// column (axpy) form: with s = e_j, for c = j, j-1, ..., 0:
+//   X[c][j] = s[c] / R[c][c];   s[0..c-1] -= R[0..c-1][c] * X[c][j].
+// R is read column-major from the QR workspace W (rows of a column are
+// contiguous); the running sums s live in X's own column.  Writes Xrow
+// (row-major X) and XTrow (row-major X^T).
+__global__ void k_trtri(const double* __restrict__ W, int64_t d, int n,
                         double* __restrict__ Xrow, double* __restrict__ XTrow) {
   const int lane = threadIdx.x & 31;
   const int64_t warps = static_cast<int64_t>(gridDim.x) * (blockDim.x >> 5);
   for (int64_t j = blockIdx.x * static_cast<int64_t>(blockDim.x >> 5) + (threadIdx.x >> 5);
        j < n; j += warps) {
     double* xt = XTrow + j * n;  // column j of X, contiguous
-    for (int c = lane; c < n; c += 32) xt[c] = 0.0;
+    for (int c = lane; c < n; c += 32) xt[c] = (c == j) ? 1.0 : 0.0;
     __syncwarp();
-    if (lane == 0) xt[j] = 1.0 / Rrow[j * static_cast<int64_t>(n) + j];
-    __syncwarp();
-    for (int64_t i = j - 1; i >= 0; --i) {
-      const double* ri = Rrow + i * n;
-      double s = 0.0;
-      for (int64_t c = i + 1 + lane; c <= j; c += 32) s += ri[c] * xt[c];
-      s = warp_sum(s);
-      if (lane == 0) xt[i] = -s / ri[i];
+    for (int64_t c = j; c >= 0; --c) {
+      const double* rc = W + c * d;  // column c of R: rows 0..c
+      const double xc = xt[c] / rc[c];
+      __syncwarp();
+      if (lane == 0) xt[c] = xc;
+      for (int64_t r = lane; r < c; r += 32) xt[r] -= rc[r] * xc;
       __syncwarp();
     }
     for (int64_t i = lane; i < n; i += 32) Xrow[i * n + j] = xt[i];
@@ -307,12 +308,13 @@ __global__ void __launch_bounds__(1024)
   const double phi = c * phibar;
   const double phibar_new = sn * phibar;
   double y2 = 0.0;
+  const double f_y = phi / rho, f_w = theta / rho;  // once, not per element
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     const double vi = vraw[i] * ia;
     v[i] = vi;
-    const double yi = y[i] + (phi / rho) * w[i];
+    const double yi = y[i] + f_y * w[i];
     y[i] = yi;
-    w[i] = vi - (theta / rho) * w[i];
+    w[i] = vi - f_w * w[i];
     y2 += yi * yi;
   }
   const double ynorm = sqrt(block_sum<1024>(y2, red));
@@ -618,7 +620,7 @@ extern "C" int sketch_lsq_solve(sketch_t h, const sketch_csc* A,
         k_qr_step<<<static_cast<unsigned>(n - k - 1), kQrThreads, 0, s>>>(
             L.W, d, static_cast<int>(n), k, L.tau);
       k_extract_r<<<gb, 256, 0, s>>>(L.W, d, static_cast<int>(n), L.Rrow, L.status);
-      k_trtri<<<gemv_blocks(n), 256, 0, s>>>(L.Rrow, static_cast<int>(n), L.Rinv, L.RinvT);
+      k_trtri<<<gemv_blocks(n), 256, 0, s>>>(L.W, d, static_cast<int>(n), L.Rinv, L.RinvT);
     };
     const bool repeat = std::memcmp(qk, st.qr_seen, sizeof(qk)) == 0;
     std::memcpy(st.qr_seen, qk, sizeof(qk));
@@ -799,7 +801,7 @@ extern "C" int sketch_debug_qr(int64_t d, int64_t n, const double* A, double* R,
     k_qr_step<<<static_cast<unsigned>(n - k - 1), kQrThreads, 0, s>>>(W, d, static_cast<int>(n), k, tau);
   const unsigned gb = static_cast<unsigned>(std::max<int64_t>(1, 16LL * num_sms()));
   k_extract_r<<<gb, 256, 0, s>>>(W, d, static_cast<int>(n), R, status);
-  k_trtri<<<gemv_blocks(n), 256, 0, s>>>(R, static_cast<int>(n), Rinv, RT);
+  k_trtri<<<gemv_blocks(n), 256, 0, s>>>(W, d, static_cast<int>(n), Rinv, RT);
   cudaError_t e = cudaStreamSynchronize(s);
   cudaFree(W); cudaFree(tau); cudaFree(RT); cudaFree(status);
   return e == cudaSuccess ? SKETCH_OK : cuda_fail(nullptr, e, "debug_qr");
