@@ -28,13 +28,16 @@ namespace sk {
 namespace {
 
 constexpr int kIterPerGraph = 8;
-constexpr int kRedBlocks = 2048;  // partial sums of m-vector reductions
 
 struct Scalars {
   double alpha, beta, inv_beta, rhobar, phibar, anorm2, bnorm;
   double test1, test2, ynorm, afro2, err_num2, err_res2;
   double tol;
+  double f_next;           // alpha_k / beta_k for the next rows pass
+  double usq;              // ||u_raw||^2 after the rows pass
+  double zsq;              // the part of usq from rows of A with no nonzero
   int iters, maxit, done, istop;
+  unsigned int counter;    // blocks of k_lsqr_step that have finished
 };
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -61,9 +64,27 @@ __device__ double block_sum(double v, double* red) {
   return red[32];
 }
 
+// float -> double, exactly, with integer operations for zeros and normal
+// numbers (IEEE 754 binary32 -> binary64: rebias the exponent by 1023 - 127,
+// widen the significand by 29 bits); subnormals, infinities and NaNs take
+// the conversion instruction.
+__device__ __forceinline__ double f64_of(float f) {
+  const uint32_t b = __float_as_uint(f);
+  const uint32_t e = (b >> 23) & 0xffu;
+  if (e == 0u || e == 0xffu) {
+    if ((b << 1) == 0u)
+      return __longlong_as_double(static_cast<long long>(static_cast<uint64_t>(b) << 32));
+    return static_cast<double>(f);
+  }
+  const uint64_t bits = (static_cast<uint64_t>(b & 0x80000000u) << 32) |
+                        (static_cast<uint64_t>(e + 896u) << 52) |
+                        (static_cast<uint64_t>(b & 0x7fffffu) << 29);
+  return __longlong_as_double(static_cast<long long>(bits));
+}
+
 template <typename VT>
 __device__ __forceinline__ double val_at(const VT* v, int64_t i) {
-  return static_cast<double>(to_f32(v[i]));
+  return f64_of(to_f32(v[i]));
 }
 
 // ---------------------------------------------------------------------------
@@ -76,55 +97,81 @@ __global__ void k_to_double(int64_t total, const float* __restrict__ a,
     w[i] = static_cast<double>(a[i]);
 }
 
-constexpr int kQrThreads = 256;
+constexpr int kQrThreads = 128;
 
-// Householder reflector of column k (rows k..d-1) of W, in place.
-__device__ void qr_reflector(double* W, int64_t d, int k, double* tau,
-                             double* red) {
+// Block-wide sum for the QR kernels (kQrThreads threads): warp sums, then
+// thread 0 adds the four in order; every thread gets the result.
+__device__ __forceinline__ double qr_block_sum(double v, double* red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  v = warp_sum(v);
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = red[0];
+#pragma unroll
+    for (int w = 1; w < kQrThreads / 32; ++w) t += red[w];
+    red[8] = t;
+  }
+  __syncthreads();
+  return red[8];
+}
+
+// Householder reflector of column k (rows k..d-1) of W, in place.  The
+// scalar chain (sqrt, two divides) runs in thread 0 only.
+__device__ void qr_reflector(double* W, int64_t d, int k, double* tau, double* red) {
   double* x = W + static_cast<int64_t>(k) * d;
-  double s = 0.0;
-  for (int64_t r = k + 1 + threadIdx.x; r < d; r += blockDim.x) s += x[r] * x[r];
-  const double sigma = block_sum<kQrThreads>(s, red);
-  const double alpha = x[k];
+  double s0 = 0.0, s1 = 0.0;
+  int64_t r = k + 1 + threadIdx.x;
+  for (; r + kQrThreads < d; r += 2 * kQrThreads) {
+    s0 = fma(x[r], x[r], s0);
+    s1 = fma(x[r + kQrThreads], x[r + kQrThreads], s1);
+  }
+  if (r < d) s0 = fma(x[r], x[r], s0);
+  const double sigma = qr_block_sum(s0 + s1, red);
   if (sigma == 0.0) {  // nothing below the diagonal: H = I
     if (threadIdx.x == 0) tau[k] = 0.0;
     return;
   }
-  const double norm = sqrt(alpha * alpha + sigma);
-  const double beta = alpha >= 0.0 ? -norm : norm;
-  const double scale = 1.0 / (alpha - beta);
-  for (int64_t r = k + 1 + threadIdx.x; r < d; r += blockDim.x) x[r] *= scale;
-  __syncthreads();
   if (threadIdx.x == 0) {
+    const double alpha = x[k];
+    const double norm = sqrt(fma(alpha, alpha, sigma));
+    const double beta = alpha >= 0.0 ? -norm : norm;
+    red[9] = 1.0 / (alpha - beta);
     tau[k] = (beta - alpha) / beta;
     x[k] = beta;
   }
+  __syncthreads();
+  const double scale = red[9];
+  for (int64_t q = k + 1 + threadIdx.x; q < d; q += kQrThreads) x[q] *= scale;
 }
 
 __global__ void __launch_bounds__(kQrThreads)
     k_qr_first(double* W, int64_t d, double* tau) {
-  __shared__ double red[33];
+  __shared__ double red[16];
   qr_reflector(W, d, 0, tau, red);
 }
 
-// Apply reflector k to columns k+1..n-1 (one CTA per column); the CTA of
+// Apply reflector k to columns k+1..n-1 (one block per column); the block of
 // column k+1 then forms reflector k+1.
 __global__ void __launch_bounds__(kQrThreads)
     k_qr_step(double* W, int64_t d, int n, int k, double* tau) {
-  __shared__ double red[33];
+  __shared__ double red[16];
   const int c = k + 1 + blockIdx.x;
   if (c >= n) return;
   const double t = tau[k];
   const double* v = W + static_cast<int64_t>(k) * d;
   double* y = W + static_cast<int64_t>(c) * d;
   if (t != 0.0) {
-    double s = 0.0;
-    for (int64_t r = k + 1 + threadIdx.x; r < d; r += blockDim.x) s += v[r] * y[r];
-    const double wsum = block_sum<kQrThreads>(s, red) + y[k];
-    const double f = t * wsum;
-    __syncthreads();
+    double s0 = 0.0, s1 = 0.0;
+    int64_t r = k + 1 + threadIdx.x;
+    for (; r + kQrThreads < d; r += 2 * kQrThreads) {
+      s0 = fma(v[r], y[r], s0);
+      s1 = fma(v[r + kQrThreads], y[r + kQrThreads], s1);
+    }
+    if (r < d) s0 = fma(v[r], y[r], s0);
+    const double f = t * (qr_block_sum(s0 + s1, red) + y[k]);
     if (threadIdx.x == 0) y[k] -= f;
-    for (int64_t r = k + 1 + threadIdx.x; r < d; r += blockDim.x) y[r] -= f * v[r];
+    for (int64_t q = k + 1 + threadIdx.x; q < d; q += kQrThreads) y[q] = fma(-f, v[q], y[q]);
     __syncthreads();
   }
   if (c == k + 1) qr_reflector(W, d, c, tau, red);
@@ -171,173 +218,394 @@ __global__ void k_trtri(const double* __restrict__ W, int64_t d, int n,
 }
 
 // ---------------------------------------------------------------------------
-// LSQR kernels (each returns at once once `done` is set)
+// LSQR kernels
+//
+// On this GPU a warp-wide FP64 instruction occupies its SM partition's FP64
+// pipe for about 80 cycles whatever the number of active lanes, and a
+// dependent FP64 add, sqrt or divide costs about 67, 720 and 460 cycles.  So
+// the kernels below keep FP64 scalar chains in one thread per block, reduce
+// per thread before reducing across lanes, convert float values to double
+// with integer operations, and let the scalar chain of one step overlap the
+// vector work of the next.  One iteration is four kernels:
+//   rows:  u_raw <- A t - (alpha/beta) u_raw and per-block sums of u_raw^2
+//   cols:  t2 <- A^T u_raw (unscaled)
+//   vraw:  beta <- ||u_raw|| (every block, same fixed order) while the warps
+//          form rows of R^{-T} t2; vraw = R^{-T} t2 / beta - beta v and
+//          per-block sums of vraw^2
+//   step:  alpha <- ||vraw||, the plane rotation, v = vraw/alpha,
+//          y += (phi/rho) w, w = v - (theta/rho) w, t = R^{-1} v for the next
+//          rows pass; the last block to finish forms the stopping tests.
+// Each kernel returns at once when `done` is set.
 // ---------------------------------------------------------------------------
-// out[i] = sum_c Mrow[i][c] x[c] - sub * prev[i] over the nonzero triangle:
-// c >= i (upper, lower = 0) or c <= i (lower = 1).  One warp per row.
+constexpr int kRows = 256;  // threads per block of the rows pass
+constexpr int kTriWarps = 8;  // rows of R^{-1} / R^{-T} per block
+
+// sum_{c in [lo, hi)} row[c] x[c] across one warp (every lane gets it).
+// Each round issues all sixteen loads of a lane before the first multiply,
+// so a row costs one memory latency per 256 entries.
+__device__ __forceinline__ double warp_row_dot(const double* __restrict__ row,
+                                               const double* __restrict__ x,
+                                               int64_t lo, int64_t hi, int lane) {
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+  for (int64_t c0 = lo + lane; c0 < hi; c0 += 256) {
+    double r[8], v[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int64_t c = c0 + 32 * q;
+      r[q] = c < hi ? row[c] : 0.0;
+      v[q] = c < hi ? x[c] : 0.0;
+    }
+    a0 = fma(r[0], v[0], a0); a1 = fma(r[1], v[1], a1);
+    a2 = fma(r[2], v[2], a2); a3 = fma(r[3], v[3], a3);
+    a0 = fma(r[4], v[4], a0); a1 = fma(r[5], v[5], a1);
+    a2 = fma(r[6], v[6], a2); a3 = fma(r[7], v[7], a3);
+  }
+  return warp_sum((a0 + a1) + (a2 + a3));
+}
+
+// Fixed-order sum of part[0..np) by one warp (every lane gets it); loads in
+// rounds of eight per lane.
+__device__ __forceinline__ double warp_sum_parts(const double* __restrict__ part,
+                                                 int np, int lane) {
+  double a0 = 0.0, a1 = 0.0;
+  for (int g0 = lane; g0 < np; g0 += 256) {
+    double v[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) v[q] = g0 + 32 * q < np ? part[g0 + 32 * q] : 0.0;
+    a0 += (v[0] + v[2]) + (v[4] + v[6]);
+    a1 += (v[1] + v[3]) + (v[5] + v[7]);
+  }
+  return warp_sum(a0 + a1);
+}
+
+// out[i] = sum_c Mrow[i][c] x[c] over the nonzero triangle (c >= i upper,
+// c <= i lower).  One warp per row.  Used for x = R^{-1} y.
 __global__ void k_gemv_tri(const double* __restrict__ Mrow, int n,
                            const double* __restrict__ x, double* __restrict__ out,
-                           const double* __restrict__ prev, const Scalars* sc,
-                           int use_beta, int ignore_done, int lower) {
-  if (!ignore_done && sc->done) return;
-  const double sub = use_beta ? sc->beta : 0.0;
+                           int lower) {
   const int lane = threadIdx.x & 31;
   const int64_t warps = static_cast<int64_t>(gridDim.x) * (blockDim.x >> 5);
   for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x >> 5) + (threadIdx.x >> 5);
        i < n; i += warps) {
-    const double* row = Mrow + i * n;
-    double s = 0.0;
-    if (lower) {
-      for (int64_t c = lane; c <= i; c += 32) s += row[c] * x[c];
-    } else {
-      for (int64_t c = (i & ~31LL) + lane; c < n; c += 32)
-        if (c >= i) s += row[c] * x[c];
-    }
-    s = warp_sum(s);
-    if (lane == 0) out[i] = s - (prev ? sub * prev[i] : 0.0);
+    const double s = lower ? warp_row_dot(Mrow + i * n, x, 0, i + 1, lane)
+                           : warp_row_dot(Mrow + i * n, x, i, n, lane);
+    if (lane == 0) out[i] = s;
   }
 }
 
-// u[j] <- sum_e val[e] t[col[e]] - alpha * inv_beta * u[j]  (u kept unscaled),
-// partial sums of u^2 per block.  mode 1: r = A x - b (error check).
+// Block-wide fixed-order sum for kernels of NT threads (thread 0 gets it).
 template <int NT>
-__global__ void __launch_bounds__(NT)
-    k_spmv_rows(int32_t m, const int32_t* __restrict__ rowptr,
-                const int32_t* __restrict__ ccol, const float* __restrict__ cval,
-                const double* __restrict__ t, double* __restrict__ u,
-                const double* __restrict__ b, double* __restrict__ partial,
-                const Scalars* sc, int mode) {
-  __shared__ double red[33];
-  if (mode == 0 && sc->done) return;
-  const double f = mode == 0 ? sc->alpha * sc->inv_beta : 0.0;
-  double s2 = 0.0;
-  for (int64_t j = blockIdx.x * static_cast<int64_t>(NT) + threadIdx.x; j < m;
-       j += static_cast<int64_t>(gridDim.x) * NT) {
-    double s = 0.0;
-    for (int32_t e = rowptr[j]; e < rowptr[j + 1]; ++e)
-      s += static_cast<double>(cval[e]) * t[ccol[e]];
-    const double nu = mode == 0 ? s - f * u[j] : s - b[j];
-    u[j] = nu;
-    s2 += nu * nu;
-  }
-  s2 = block_sum<NT>(s2, red);
-  if (threadIdx.x == 0) partial[blockIdx.x] = s2;
-}
-
-// out[k] = scale * sum_{e in column k} val[e] u[row[e]],  scale = inv_beta
-// (mode 0) or 1 (mode 1).  One CTA per column (grid-stride), fixed-order
-// reduction, so even a few long columns keep the GPU busy.
-template <typename VT>
-__global__ void __launch_bounds__(256)
-    k_spmv_cols(int32_t n, const int32_t* __restrict__ colptr,
-                const int32_t* __restrict__ rowidx, const VT* __restrict__ vals,
-                const double* __restrict__ u, double* __restrict__ out,
-                const Scalars* sc, int mode) {
-  __shared__ double red[33];
-  if (mode == 0 && sc->done) return;
-  const double scale = mode == 0 ? sc->inv_beta : 1.0;
-  for (int64_t k = blockIdx.x; k < n; k += gridDim.x) {
-    double s = 0.0;
-    for (int32_t e = colptr[k] + threadIdx.x; e < colptr[k + 1]; e += blockDim.x)
-      s += val_at(vals, e) * u[rowidx[e]];
-    s = block_sum<256>(s, red);
-    if (threadIdx.x == 0) out[k] = scale * s;
-  }
-}
-
-// Fixed-order sum of the m-vector partials; what = 0: beta (LSQR step),
-// 1: initial beta = ||b||, 2: ||Ax-b||^2 for the error check.
-__global__ void k_finish_beta(const double* __restrict__ partial, int nparts,
-                              Scalars* sc, int what) {
-  __shared__ double red[33];
-  if (what == 0 && sc->done) return;
-  double s = 0.0;
-  for (int i = threadIdx.x; i < nparts; i += blockDim.x) s += partial[i];
-  s = block_sum<1024>(s, red);
+__device__ __forceinline__ double block_sum0(double v, double* red) {
+  v = warp_sum(v);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double p = 0.0;
   if (threadIdx.x == 0) {
-    if (what == 2) {
-      sc->err_res2 = s;
-      return;
-    }
-    const double beta = sqrt(s);
-    sc->beta = beta;
-    sc->inv_beta = beta > 0.0 ? 1.0 / beta : 0.0;
-    if (what == 1) {
-      sc->bnorm = beta;
-      sc->phibar = beta;
+#pragma unroll
+    for (int w = 0; w < NT / 32; ++w) p += red[w];
+  }
+  __syncthreads();
+  return p;
+}
+
+// Rows pass over the CSR whose rows are ordered by decreasing length (row p
+// of it is row perm[p] of A; rows [0, *mnz) have nonzeros).
+// init: u_raw[p] = b[perm[p]] for every row; partial = sums of u_raw^2 over
+// the rows with nonzeros, partial_z over the others.
+// Otherwise, for p < *mnz: u_raw[p] = sum_e val t[col] - f u_raw[p] with
+// f = alpha_k / beta_k; partial as above.  Rows without nonzeros follow
+// u_raw <- -f u_raw, which only scales their sum of squares; the columns
+// pass applies that factor to it instead of touching them.
+__global__ void __launch_bounds__(kRows)
+    k_lsqr_rows(int32_t m, const int32_t* __restrict__ mnz_ptr,
+                const int32_t* __restrict__ rowptr, const int32_t* __restrict__ ccol,
+                const float* __restrict__ cval, const double* __restrict__ t,
+                double* __restrict__ u, const double* __restrict__ b,
+                const int32_t* __restrict__ perm, double* __restrict__ partial,
+                double* __restrict__ partial_z, const Scalars* __restrict__ sc, int init) {
+  __shared__ double red[kRows / 32];
+  if (sc->done) return;
+  const int32_t mnz = *mnz_ptr;
+  const double f = init ? 0.0 : sc->f_next;
+  const int64_t rows = init ? m : mnz;
+  double s2 = 0.0, sz = 0.0;
+  for (int64_t p = blockIdx.x * static_cast<int64_t>(kRows) + threadIdx.x; p < rows;
+       p += static_cast<int64_t>(gridDim.x) * kRows) {
+    if (init) {
+      const double nu = b[perm[p]];
+      u[p] = nu;
+      if (p < mnz)
+        s2 = fma(nu, nu, s2);
+      else
+        sz = fma(nu, nu, sz);
     } else {
-      sc->anorm2 += sc->alpha * sc->alpha + beta * beta;
+      double acc = 0.0;
+      const int32_t hi = rowptr[p + 1];
+      for (int32_t e = rowptr[p]; e < hi; ++e) acc = fma(f64_of(cval[e]), t[ccol[e]], acc);
+      const double nu = fma(-f, u[p], acc);
+      u[p] = nu;
+      s2 = fma(nu, nu, s2);
+    }
+  }
+  s2 = block_sum0<kRows>(s2, red);
+  if (threadIdx.x == 0) partial[blockIdx.x] = s2;
+  if (init) {
+    sz = block_sum0<kRows>(sz, red);
+    if (threadIdx.x == 0) partial_z[blockIdx.x] = sz;
+  }
+}
+
+// Columns pass: out[k] = sum_{e in column k} val[e] u[row[e]] (unscaled), one
+// block of 32*W threads per column, fixed-order reduction.  When np2 > 0,
+// block 0 first completes ||u_raw||^2 from the rows pass's partial sums:
+// usq = sum partial2 + z, with z = sum partial_z (init) or f^2 times the
+// previous z (rows without nonzeros), and stores usq and z.
+template <typename VT, int W>
+__global__ void __launch_bounds__(32 * W)
+    k_cols(int32_t n, const int32_t* __restrict__ colptr,
+           const int32_t* __restrict__ rowidx, const VT* __restrict__ vals,
+           const double* __restrict__ u, double* __restrict__ out, Scalars* sc,
+           int check_done, const double* __restrict__ partial2,
+           const double* __restrict__ partial_z, int np2, int init) {
+  __shared__ double red[W];
+  if (check_done && sc->done) return;
+  const int k = blockIdx.x;
+  if (k >= n) return;
+  if (k == 0 && np2 > 0) {
+    double a = 0.0, z = 0.0;
+    for (int g = threadIdx.x; g < np2; g += 32 * W) {
+      a += partial2[g];
+      if (init) z += partial_z[g];
+    }
+    a = block_sum0<32 * W>(a, red);
+    if (init) z = block_sum0<32 * W>(z, red);
+    if (threadIdx.x == 0) {
+      if (!init) {
+        const double f = sc->f_next;
+        z = f * f * sc->zsq;
+      }
+      sc->zsq = z;
+      sc->usq = a + z;
+    }
+  }
+  const int32_t lo = colptr[k], hi = colptr[k + 1];
+  double a0 = 0.0, a1 = 0.0;
+  for (int32_t e0 = lo + threadIdx.x; e0 < hi; e0 += 256 * W) {
+    int32_t row[8];
+    double val[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int32_t e = e0 + 32 * W * q;
+      row[q] = e < hi ? rowidx[e] : -1;
+      val[q] = e < hi ? val_at(vals, e) : 0.0;
+    }
+    double uu[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) uu[q] = row[q] >= 0 ? u[row[q]] : 0.0;
+#pragma unroll
+    for (int q = 0; q < 8; q += 2) {
+      a0 = fma(val[q], uu[q], a0);
+      a1 = fma(val[q + 1], uu[q + 1], a1);
+    }
+  }
+  const double s = block_sum0<32 * W>(a0 + a1, red);
+  if (threadIdx.x == 0) out[k] = s;
+}
+
+// vraw = R^{-T} t2 / beta - beta v  (init: without the beta v term), one warp
+// per row of the row-major lower-triangular R^{-T}.  Every block forms beta =
+// sqrt(usq) and 1/beta while its warps form their dot products; block 0
+// publishes them.  partial4[block]
+// = sum of vraw^2 over the block's rows.
+__global__ void __launch_bounds__(32 * kTriWarps)
+    k_lsqr_vraw(int n, const double* __restrict__ RinvT, const double* __restrict__ t2,
+                const double* __restrict__ v, double* __restrict__ vraw,
+                double* __restrict__ partial4, Scalars* sc, int init) {
+  __shared__ double sh[2 + kTriWarps];
+  if (sc->done) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t i = static_cast<int64_t>(blockIdx.x) * kTriWarps + warp;
+  if (threadIdx.x == 0) {
+    const double beta = sqrt(sc->usq);
+    sh[0] = beta;
+    sh[1] = beta > 0.0 ? 1.0 / beta : 0.0;
+  }
+  const double dot = i < n ? warp_row_dot(RinvT + i * n, t2, 0, i + 1, lane) : 0.0;
+  __syncthreads();
+  const double beta = sh[0], ib = sh[1];
+  if (lane == 0) {
+    double vr2 = 0.0;
+    if (i < n) {
+      const double vr = init ? ib * dot : fma(-beta, v[i], ib * dot);
+      vraw[i] = vr;
+      vr2 = vr * vr;
+    }
+    sh[2 + warp] = vr2;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double p = 0.0;
+#pragma unroll
+    for (int w = 0; w < kTriWarps; ++w) p += sh[2 + w];
+    partial4[blockIdx.x] = p;
+    if (blockIdx.x == 0) {
+      sc->beta = beta;
+      sc->inv_beta = ib;
     }
   }
 }
 
-// The n-sized part of an LSQR step (one CTA of 1024 threads).
-// init = 1: v = vraw / alpha, w = v, y = 0, rhobar = alpha (start-up).
-__global__ void __launch_bounds__(1024)
-    k_lsqr_update(int n, double* __restrict__ vraw, double* __restrict__ v,
-                  double* __restrict__ w, double* __restrict__ y, Scalars* sc,
-                  int init) {
-  __shared__ double red[33];
-  if (!init && sc->done) return;
-  double s = 0.0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) s += vraw[i] * vraw[i];
-  const double alpha = sqrt(block_sum<1024>(s, red));
-  const double ia = alpha > 0.0 ? 1.0 / alpha : 0.0;
+// One LSQR step after vraw: alpha = ||vraw|| (every block, same fixed
+// order), the plane rotation, v = vraw / alpha, y += (phi/rho) w,
+// w = v - (theta/rho) w, and t = R^{-1} v for the next rows pass (one warp
+// per row of the row-major upper-triangular R^{-1}; element i of v, w, y
+// belongs to the warp of row i).  The last block to finish sums ||y||^2 and
+// forms the stopping tests of Paige & Saunders: istop 1 when
+// ||r|| / ||b|| <= tol + tol ||A|| ||y|| / ||b||, istop 2 when
+// ||M^T r|| / (||M|| ||r||) <= tol.  init: start-up (v = w = vraw/alpha,
+// y = 0, rhobar = alpha, phibar = beta).
+__global__ void __launch_bounds__(32 * kTriWarps)
+    k_lsqr_step(int n, const double* __restrict__ Rinv, const double* __restrict__ vraw,
+                double* __restrict__ v, double* __restrict__ w, double* __restrict__ y,
+                double* __restrict__ t, const double* __restrict__ partial4, int np4,
+                double* __restrict__ party, Scalars* sc, int init) {
+  __shared__ double sh[8 + kTriWarps];
+  __shared__ int last;
+  if (sc->done) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t i = static_cast<int64_t>(blockIdx.x) * kTriWarps + warp;
+  if (warp == 0) {
+    const double s = warp_sum_parts(partial4, np4, lane);
+    if (lane == 0) {
+      const double alpha = sqrt(s);
+      const double beta = sc->beta;
+      double f_y = 0.0, f_w = 0.0, c = 0.0, rhobar = alpha, phibar = beta;
+      if (!init) {
+        const double rb = sc->rhobar, pb = sc->phibar;
+        const double rho = sqrt(fma(rb, rb, beta * beta));
+        const double irho = 1.0 / rho;
+        c = rb * irho;
+        const double sn = beta * irho;
+        f_y = c * pb * irho;
+        f_w = sn * alpha * irho;
+        rhobar = -c * alpha;
+        phibar = sn * pb;
+      }
+      sh[0] = alpha;
+      sh[1] = alpha > 0.0 ? 1.0 / alpha : 0.0;
+      sh[2] = f_y;
+      sh[3] = f_w;
+      sh[4] = c;
+      sh[5] = rhobar;
+      sh[6] = phibar;
+    }
+  }
+  const double dot = i < n ? warp_row_dot(Rinv + i * n, vraw, i, n, lane) : 0.0;
+  __syncthreads();
+  const double ia = sh[1];
+  if (lane == 0) {
+    double y2 = 0.0;
+    if (i < n) {
+      t[i] = ia * dot;
+      const double vi = ia * vraw[i];
+      v[i] = vi;
+      if (init) {
+        w[i] = vi;
+        y[i] = 0.0;
+      } else {
+        const double wi = w[i];
+        const double yi = fma(sh[2], wi, y[i]);
+        y[i] = yi;
+        w[i] = fma(-sh[3], wi, vi);
+        y2 = yi * yi;
+      }
+    }
+    sh[8 + warp] = y2;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double p = 0.0;
+#pragma unroll
+    for (int q = 0; q < kTriWarps; ++q) p += sh[8 + q];
+    party[blockIdx.x] = p;
+    __threadfence();
+    last = atomicAdd(&sc->counter, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last || warp != 0) return;
+  __threadfence();
+  const double y2 = warp_sum_parts(party, gridDim.x, lane);
+  if (lane != 0) return;
+  const double alpha = sh[0], beta = sc->beta;
+  sc->counter = 0u;
+  sc->f_next = alpha * sc->inv_beta;
   if (init) {
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-      v[i] = vraw[i] * ia;
-      w[i] = v[i];
-      y[i] = 0.0;
-    }
-    if (threadIdx.x == 0) {
-      sc->alpha = alpha;
-      sc->rhobar = alpha;
-      sc->anorm2 = 0.0;
-      sc->iters = 0;
-      sc->istop = 0;
-      sc->done = (alpha == 0.0 || sc->beta == 0.0) ? 1 : 0;
-      if (sc->done) sc->istop = 1;
-    }
+    sc->alpha = alpha;
+    sc->rhobar = alpha;
+    sc->phibar = beta;
+    sc->bnorm = beta;
+    sc->anorm2 = 0.0;
+    sc->iters = 0;
+    const int stop = alpha == 0.0 || beta == 0.0;
+    sc->istop = stop;
+    sc->done = stop;
     return;
   }
-  // plane rotation eliminating the subdiagonal beta (new alpha enters here)
-  const double rhobar = sc->rhobar, beta = sc->beta, phibar = sc->phibar;
-  const double rho = sqrt(rhobar * rhobar + beta * beta);
-  const double c = rhobar / rho, sn = beta / rho;
-  const double theta = sn * alpha;
-  const double phi = c * phibar;
-  const double phibar_new = sn * phibar;
-  double y2 = 0.0;
-  const double f_y = phi / rho, f_w = theta / rho;  // once, not per element
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    const double vi = vraw[i] * ia;
-    v[i] = vi;
-    const double yi = y[i] + f_y * w[i];
-    y[i] = yi;
-    w[i] = vi - f_w * w[i];
-    y2 += yi * yi;
+  const double alpha_k = sc->alpha;
+  const double anorm2 = sc->anorm2 + alpha_k * alpha_k + beta * beta;
+  const double phibar = sh[6];
+  sc->anorm2 = anorm2;
+  sc->alpha = alpha;
+  sc->rhobar = sh[5];
+  sc->phibar = phibar;
+  const int it = sc->iters + 1;
+  sc->iters = it;
+  const double ynorm = sqrt(y2);
+  const double anorm = sqrt(anorm2);
+  const double rnorm = phibar;
+  const double arnorm = phibar * alpha * fabs(sh[4]);
+  const double test1 = rnorm / sc->bnorm;
+  const double test2 = rnorm > 0.0 ? arnorm / (anorm * rnorm) : 0.0;
+  const double tol = sc->tol;
+  const double rtol = tol + tol * anorm * ynorm / sc->bnorm;
+  sc->test1 = test1;
+  sc->test2 = test2;
+  sc->ynorm = ynorm;
+  int istop = 0;
+  if (test2 <= tol) istop = 2;
+  if (test1 <= rtol) istop = 1;
+  sc->istop = istop;
+  if (istop || it >= sc->maxit) sc->done = 1;
+}
+
+// Error check: r = A x - b over the length-ordered CSR (row p is row perm[p]
+// of A) and per-block sums of r^2.
+__global__ void __launch_bounds__(kRows)
+    k_residual(int32_t m, const int32_t* __restrict__ rowptr,
+               const int32_t* __restrict__ ccol, const float* __restrict__ cval,
+               const double* __restrict__ x, const double* __restrict__ b,
+               const int32_t* __restrict__ perm, double* __restrict__ r,
+               double* __restrict__ partial) {
+  __shared__ double red[kRows / 32];
+  double s2 = 0.0;
+  for (int64_t j = blockIdx.x * static_cast<int64_t>(kRows) + threadIdx.x; j < m;
+       j += static_cast<int64_t>(gridDim.x) * kRows) {
+    double s = 0.0;
+    const int32_t hi = rowptr[j + 1];
+    for (int32_t e = rowptr[j]; e < hi; ++e) s = fma(f64_of(cval[e]), x[ccol[e]], s);
+    const double rj = s - b[perm[j]];
+    r[j] = rj;
+    s2 = fma(rj, rj, s2);
   }
-  const double ynorm = sqrt(block_sum<1024>(y2, red));
+  s2 = warp_sum(s2);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) red[warp] = s2;
+  __syncthreads();
   if (threadIdx.x == 0) {
-    sc->alpha = alpha;
-    sc->rhobar = -c * alpha;
-    sc->phibar = phibar_new;
-    const int it = sc->iters + 1;
-    sc->iters = it;
-    const double rnorm = phibar_new;
-    const double arnorm = phibar_new * alpha * fabs(c);
-    const double anorm = sqrt(sc->anorm2);
-    const double test1 = rnorm / sc->bnorm;
-    const double test2 = rnorm > 0.0 ? arnorm / (anorm * rnorm) : 0.0;
-    const double rtol = sc->tol + sc->tol * anorm * ynorm / sc->bnorm;
-    sc->test1 = test1;
-    sc->test2 = test2;
-    sc->ynorm = ynorm;
-    int istop = 0;
-    if (test2 <= sc->tol) istop = 2;
-    if (test1 <= rtol) istop = 1;
-    sc->istop = istop;
-    if (istop || it >= sc->maxit) sc->done = 1;
+    double p = 0.0;
+#pragma unroll
+    for (int w = 0; w < kRows / 32; ++w) p += red[w];
+    partial[blockIdx.x] = p;
   }
 }
 
@@ -349,44 +617,30 @@ __global__ void k_fro2(int64_t nnz, const VT* __restrict__ vals,
   for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
        e < nnz; e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
     const double v = val_at(vals, e);
-    s += v * v;
+    s = fma(v, v, s);
   }
   s = block_sum<256>(s, red);
   if (threadIdx.x == 0) partial[blockIdx.x] = s;
 }
 
-__global__ void k_finish_error(const double* __restrict__ partial, int nparts,
+// Error(x) pieces: ||A||_F^2, ||A x - b||^2 and ||A^T (A x - b)||^2, each a
+// fixed-order sum by one warp.
+__global__ void k_finish_error(const double* __restrict__ pfro, int nfro,
+                               const double* __restrict__ pres, int nres,
                                const double* __restrict__ g, int n, Scalars* sc) {
-  __shared__ double red[33];
-  double s = 0.0;
-  for (int i = threadIdx.x; i < nparts; i += blockDim.x) s += partial[i];
-  s = block_sum<1024>(s, red);
-  double g2 = 0.0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) g2 += g[i] * g[i];
-  g2 = block_sum<1024>(g2, red);
-  if (threadIdx.x == 0) {
-    sc->afro2 = s;
-    sc->err_num2 = g2;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (warp == 0) {
+    const double s = warp_sum_parts(pfro, nfro, lane);
+    if (lane == 0) sc->afro2 = s;
+  } else if (warp == 1) {
+    const double s = warp_sum_parts(pres, nres, lane);
+    if (lane == 0) sc->err_res2 = s;
+  } else if (warp == 2) {
+    double a0 = 0.0;
+    for (int i = lane; i < n; i += 32) a0 = fma(g[i], g[i], a0);
+    const double s = warp_sum(a0);
+    if (lane == 0) sc->err_num2 = s;
   }
-}
-
-// partial[block] = sum of x[i]^2 over the block's grid-stride share
-__global__ void k_sq_partials(int64_t len, const double* __restrict__ x,
-                              double* __restrict__ partial) {
-  __shared__ double red[33];
-  double s = 0.0;
-  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
-       i < len; i += static_cast<int64_t>(gridDim.x) * blockDim.x)
-    s += x[i] * x[i];
-  s = block_sum<256>(s, red);
-  if (threadIdx.x == 0) partial[blockIdx.x] = s;
-}
-
-__global__ void k_copy_d(int64_t len, const double* __restrict__ a,
-                         double* __restrict__ b) {
-  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
-       i < len; i += static_cast<int64_t>(gridDim.x) * blockDim.x)
-    b[i] = a[i];
 }
 
 // Deterministic CSR: each row's nonzeros placed in column order (the scatter
@@ -419,6 +673,99 @@ __global__ void k_tighten(Scalars* sc) {
   sc->tol *= 0.1;
   sc->done = 0;
   sc->istop = 0;
+}
+
+// ---- rows of A by decreasing nonzero count ------------------------------
+// A stable counting sort on the row lengths (lengths >= kLenBuckets - 1
+// share the first bucket), so that the 32 rows of a warp in the rows pass
+// have (nearly) the same length and rows without nonzeros come last.
+constexpr int kLenBuckets = 64;
+constexpr int kSortBlock = 1024;
+
+__device__ __forceinline__ int len_bucket(int32_t len) {
+  return kLenBuckets - 1 - min(len, kLenBuckets - 1);
+}
+
+// hist[b * nblk + blk] = rows of block blk (kSortBlock consecutive rows) in
+// bucket b.
+__global__ void __launch_bounds__(kSortBlock)
+    k_len_hist(int32_t m, const int32_t* __restrict__ rowptr, int32_t* __restrict__ hist,
+               int nblk) {
+  __shared__ int32_t cnt[kLenBuckets];
+  if (threadIdx.x < kLenBuckets) cnt[threadIdx.x] = 0;
+  __syncthreads();
+  const int64_t j = blockIdx.x * static_cast<int64_t>(kSortBlock) + threadIdx.x;
+  if (j < m) atomicAdd(&cnt[len_bucket(rowptr[j + 1] - rowptr[j])], 1);
+  __syncthreads();
+  if (threadIdx.x < kLenBuckets) hist[threadIdx.x * nblk + blockIdx.x] = cnt[threadIdx.x];
+}
+
+// perm[pos] = j, inv[j] = pos with pos = off[b * nblk + blk] + (rows of the
+// same bucket before j in its block).
+__global__ void __launch_bounds__(kSortBlock)
+    k_len_place(int32_t m, const int32_t* __restrict__ rowptr,
+                const int32_t* __restrict__ off, int nblk, int32_t* __restrict__ perm,
+                int32_t* __restrict__ inv) {
+  __shared__ int32_t wcnt[kSortBlock / 32][kLenBuckets];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int q = threadIdx.x; q < (kSortBlock / 32) * kLenBuckets; q += kSortBlock)
+    (&wcnt[0][0])[q] = 0;
+  __syncthreads();
+  const int64_t j = blockIdx.x * static_cast<int64_t>(kSortBlock) + threadIdx.x;
+  const bool ok = j < m;
+  const int b = ok ? len_bucket(rowptr[j + 1] - rowptr[j]) : kLenBuckets;
+  const unsigned same = __match_any_sync(0xffffffffu, b);
+  const int rank = __popc(same & ((1u << lane) - 1u));
+  if (ok && rank == 0) wcnt[warp][b] = __popc(same);
+  __syncthreads();
+  if (threadIdx.x < kLenBuckets) {
+    int32_t run = 0;
+    for (int w = 0; w < kSortBlock / 32; ++w) {
+      const int32_t c = wcnt[w][threadIdx.x];
+      wcnt[w][threadIdx.x] = run;
+      run += c;
+    }
+  }
+  __syncthreads();
+  if (ok) {
+    const int32_t pos = off[b * nblk + blockIdx.x] + wcnt[warp][b] + rank;
+    perm[pos] = static_cast<int32_t>(j);
+    inv[j] = pos;
+  }
+}
+
+// lenp[p] = length of row perm[p]; lenp[m] = 0 (so its exclusive scan ends
+// with nnz).
+__global__ void k_perm_len(int32_t m, const int32_t* __restrict__ rowptr,
+                           const int32_t* __restrict__ perm, int32_t* __restrict__ lenp) {
+  for (int64_t p = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; p <= m;
+       p += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    lenp[p] = p < m ? rowptr[perm[p] + 1] - rowptr[perm[p]] : 0;
+}
+
+// Row p of the ordered CSR = row perm[p] of the column-sorted CSR.
+__global__ void k_perm_copy(int32_t m, const int32_t* __restrict__ rowptr,
+                            const int32_t* __restrict__ scol, const float* __restrict__ sval,
+                            const int32_t* __restrict__ perm,
+                            const int32_t* __restrict__ rowptr_p, int32_t* __restrict__ ccol_p,
+                            float* __restrict__ cval_p) {
+  for (int64_t p = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; p < m;
+       p += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int32_t src = rowptr[perm[p]], len = rowptr[perm[p] + 1] - src;
+    const int32_t dst = rowptr_p[p];
+    for (int32_t k = 0; k < len; ++k) {
+      ccol_p[dst + k] = scol[src + k];
+      cval_p[dst + k] = sval[src + k];
+    }
+  }
+}
+
+// rowidx_p[e] = position of row rowidx[e] in the ordered CSR.
+__global__ void k_map_rows(int64_t nnz, const int32_t* __restrict__ rowidx,
+                           const int32_t* __restrict__ inv, int32_t* __restrict__ rowidx_p) {
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < nnz;
+       e += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    rowidx_p[e] = inv[rowidx[e]];
 }
 
 size_t al(size_t b) { return (b + 255) / 256 * 256; }
@@ -461,15 +808,31 @@ namespace {
 
 struct LsqLayout {
   float* Ahat;
-  double *W, *tau, *Rrow, *Rinv, *RinvT, *u, *t, *t2, *v, *vraw, *w, *y, *partial;
+  double *W, *tau, *Rrow, *Rinv, *RinvT, *u, *t, *t2, *v, *vraw, *w, *y;
+  double *p2, *p4, *py, *pfro, *pres;  // per-block partial sums
   double* r;  // A x - b for the error check (kept apart from LSQR's u)
   Scalars* sc;
   int32_t* scol;  // column-sorted CSR rows
   float* sval;
+  // rows ordered by decreasing length: perm[p] = row of A at position p,
+  // inv its inverse, the ordered CSR's rowptr, the CSC's rows mapped to
+  // positions, the counting sort's histogram and offsets, scan scratch
+  int32_t *perm, *inv, *lenp, *rowptr_p, *rowidx_p, *hist, *hoff;
+  double* pz;  // per-block sums of b^2 over rows without nonzeros
+  char* scan_tmp;
   void* csr_ws;
   int* status;
   size_t bytes;
 };
+
+constexpr int kFroBlocks = 512;
+
+int rows_blocks(int64_t m) {
+  return static_cast<int>(
+      std::max<int64_t>(1, std::min<int64_t>((m + kRows - 1) / kRows, 4LL * num_sms())));
+}
+
+int tri_blocks(int64_t n) { return static_cast<int>((n + kTriWarps - 1) / kTriWarps); }
 
 LsqLayout layout(void* base, int64_t m, int64_t n, int64_t d, int64_t nnz) {
   LsqLayout L{};
@@ -493,49 +856,87 @@ LsqLayout layout(void* base, int64_t m, int64_t n, int64_t d, int64_t nnz) {
   L.vraw = reinterpret_cast<double*>(take(sizeof(double) * n));
   L.w = reinterpret_cast<double*>(take(sizeof(double) * n));
   L.y = reinterpret_cast<double*>(take(sizeof(double) * n));
-  L.partial = reinterpret_cast<double*>(take(sizeof(double) * kRedBlocks));
+  L.p2 = reinterpret_cast<double*>(take(sizeof(double) * rows_blocks(m)));
+  L.pres = reinterpret_cast<double*>(take(sizeof(double) * rows_blocks(m)));
+  L.p4 = reinterpret_cast<double*>(take(sizeof(double) * tri_blocks(n)));
+  L.py = reinterpret_cast<double*>(take(sizeof(double) * tri_blocks(n)));
+  L.pfro = reinterpret_cast<double*>(take(sizeof(double) * kFroBlocks));
   L.sc = reinterpret_cast<Scalars*>(take(sizeof(Scalars)));
   L.status = reinterpret_cast<int*>(take(256));
   L.scol = reinterpret_cast<int32_t*>(take(sizeof(int32_t) * (nnz > 0 ? nnz : 1)));
   L.sval = reinterpret_cast<float*>(take(sizeof(float) * (nnz > 0 ? nnz : 1)));
+  const int64_t nblk = (m + kSortBlock - 1) / kSortBlock;
+  L.perm = reinterpret_cast<int32_t*>(take(sizeof(int32_t) * m));
+  L.inv = reinterpret_cast<int32_t*>(take(sizeof(int32_t) * m));
+  L.lenp = reinterpret_cast<int32_t*>(take(sizeof(int32_t) * (m + 1)));
+  L.rowptr_p = reinterpret_cast<int32_t*>(take(sizeof(int32_t) * (m + 1)));
+  L.rowidx_p = reinterpret_cast<int32_t*>(take(sizeof(int32_t) * (nnz > 0 ? nnz : 1)));
+  L.hist = reinterpret_cast<int32_t*>(take(sizeof(int32_t) * kLenBuckets * nblk));
+  L.hoff = reinterpret_cast<int32_t*>(take(sizeof(int32_t) * kLenBuckets * nblk));
+  L.pz = reinterpret_cast<double*>(take(sizeof(double) * rows_blocks(m)));
+  L.scan_tmp = take(static_cast<size_t>(
+      scan_bytes_for(std::max<int64_t>(m + 1, kLenBuckets * nblk))));
   L.csr_ws = take(csr_workspace_bytes(m, nnz));
   L.bytes = static_cast<size_t>(p - static_cast<char*>(base));
   return L;
 }
 
+// The CSC of A with its rows mapped to positions of the ordered CSR.
+struct CscView {
+  int32_t n;
+  int64_t nnz;
+  const int32_t* colptr;
+  const int32_t* rowidx;
+  const void* values;
+  int32_t dtype;
+};
+
 template <typename VT>
-void launch_spmv_cols(const sketch_csc* A, const double* u, double* out,
-                      const Scalars* sc, int mode, cudaStream_t s) {
-  const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>(A->n, 64LL * num_sms()));
-  k_spmv_cols<VT><<<static_cast<unsigned>(blocks), 256, 0, s>>>(
-      static_cast<int32_t>(A->n), A->colptr, A->rowidx,
-      static_cast<const VT*>(A->values), u, out, sc, mode);
+void launch_cols(const CscView& A, const double* u, double* out, Scalars* sc,
+                 int check_done, const double* p2, const double* pz, int np2, int init,
+                 cudaStream_t s) {
+  // warps per column from the mean column length: about 16 entries per
+  // thread (any choice is correct)
+  const int64_t avg = A.nnz / std::max<int64_t>(1, A.n);
+  int W = 1;
+  while (W < 8 && avg > 512LL * W) W *= 2;
+  const unsigned g = static_cast<unsigned>(A.n);
+  const VT* vals = static_cast<const VT*>(A.values);
+#define SK_COLS(WW)                                                              \
+  k_cols<VT, WW><<<g, 32 * WW, 0, s>>>(A.n, A.colptr, A.rowidx, vals, u, out, sc, \
+                                       check_done, p2, pz, np2, init)
+  switch (W) {
+    case 1: SK_COLS(1); break;
+    case 2: SK_COLS(2); break;
+    case 4: SK_COLS(4); break;
+    default: SK_COLS(8); break;
+  }
+#undef SK_COLS
 }
 
-void spmv_cols(const sketch_csc* A, const double* u, double* out,
-               const Scalars* sc, int mode, cudaStream_t s) {
-  if (A->dtype == SKETCH_F32)
-    launch_spmv_cols<float>(A, u, out, sc, mode, s);
+void cols(const CscView& A, const double* u, double* out, Scalars* sc, int check_done,
+          const double* p2, const double* pz, int np2, int init, cudaStream_t s) {
+  if (A.dtype == SKETCH_F32)
+    launch_cols<float>(A, u, out, sc, check_done, p2, pz, np2, init, s);
   else
-    launch_spmv_cols<__nv_bfloat16>(A, u, out, sc, mode, s);
+    launch_cols<__nv_bfloat16>(A, u, out, sc, check_done, p2, pz, np2, init, s);
 }
 
 unsigned gemv_blocks(int64_t n) {
   return static_cast<unsigned>(std::max<int64_t>(1, std::min<int64_t>((n + 7) / 8, 32LL * num_sms())));
 }
 
-// One LSQR iteration (6 kernels) on stream s.
-void lsqr_iteration(const LsqLayout& L, const sketch_csc* A, const CsrView& csr,
-                    cudaStream_t s) {
-  const int n = static_cast<int>(A->n);
-  const int32_t m = static_cast<int32_t>(A->m);
-  k_gemv_tri<<<gemv_blocks(n), 256, 0, s>>>(L.Rinv, n, L.v, L.t, nullptr, L.sc, 0, 0, 0);
-  k_spmv_rows<256><<<kRedBlocks, 256, 0, s>>>(m, csr.rowptr, csr.ccol, csr.cval,
-                                              L.t, L.u, nullptr, L.partial, L.sc, 0);
-  k_finish_beta<<<1, 1024, 0, s>>>(L.partial, kRedBlocks, L.sc, 0);
-  spmv_cols(A, L.u, L.t2, L.sc, 0, s);
-  k_gemv_tri<<<gemv_blocks(n), 256, 0, s>>>(L.RinvT, n, L.t2, L.vraw, L.v, L.sc, 1, 0, 1);
-  k_lsqr_update<<<1, 1024, 0, s>>>(n, L.vraw, L.v, L.w, L.y, L.sc, 0);
+// LSQR start-up (init = 1) or one iteration (init = 0): four kernels.
+void lsqr_kernels(const LsqLayout& L, const CscView& A, const CsrView& csr,
+                  const int32_t* mnz, const double* b, int32_t m, int init, cudaStream_t s) {
+  const int n = A.n;
+  const int g2 = rows_blocks(m), gt = tri_blocks(n);
+  k_lsqr_rows<<<g2, kRows, 0, s>>>(m, mnz, csr.rowptr, csr.ccol, csr.cval, L.t, L.u, b,
+                                   L.perm, L.p2, L.pz, L.sc, init);
+  cols(A, L.u, L.t2, L.sc, 1, L.p2, L.pz, g2, init, s);
+  k_lsqr_vraw<<<gt, 32 * kTriWarps, 0, s>>>(n, L.RinvT, L.t2, L.v, L.vraw, L.p4, L.sc, init);
+  k_lsqr_step<<<gt, 32 * kTriWarps, 0, s>>>(n, L.Rinv, L.vraw, L.v, L.w, L.y, L.t, L.p4, gt,
+                                            L.py, L.sc, init);
 }
 
 }  // namespace
@@ -661,23 +1062,34 @@ extern "C" int sketch_lsq_solve(sketch_t h, const sketch_csc* A,
   if (e != cudaSuccess) return cuda_fail(h, e, "csr build (lsq)");
   k_sort_rows<<<gb, 256, 0, s>>>(static_cast<int32_t>(m), csr.rowptr, csr.ccol, csr.cval,
                                  L.scol, L.sval);
-  csr.ccol = L.scol;
-  csr.cval = L.sval;
-  h->launches += nl + 1;
+  // rows by decreasing length; the ordered CSR reuses the unsorted arrays
+  {
+    const int32_t m32 = static_cast<int32_t>(m);
+    const int nblk = static_cast<int>((m + kSortBlock - 1) / kSortBlock);
+    k_len_hist<<<nblk, kSortBlock, 0, s>>>(m32, csr.rowptr, L.hist, nblk);
+    e = scan_i32(L.hist, L.hoff, static_cast<int64_t>(kLenBuckets) * nblk, L.scan_tmp, s, &nl);
+    if (e != cudaSuccess) return cuda_fail(h, e, "row order scan");
+    k_len_place<<<nblk, kSortBlock, 0, s>>>(m32, csr.rowptr, L.hoff, nblk, L.perm, L.inv);
+    k_perm_len<<<gb, 256, 0, s>>>(m32, csr.rowptr, L.perm, L.lenp);
+    e = scan_i32(L.lenp, L.rowptr_p, m + 1, L.scan_tmp, s, &nl);
+    if (e != cudaSuccess) return cuda_fail(h, e, "row order scan");
+    k_perm_copy<<<gb, 256, 0, s>>>(m32, csr.rowptr, L.scol, L.sval, L.perm, L.rowptr_p,
+                                   csr.ccol, csr.cval);
+    k_map_rows<<<gb, 256, 0, s>>>(nnz, A->rowidx, L.inv, L.rowidx_p);
+    csr.rowptr = L.rowptr_p;
+  }
+  const int32_t* mnz = L.hoff + static_cast<int64_t>(kLenBuckets - 1) *
+                                    ((m + kSortBlock - 1) / kSortBlock);
+  const CscView csc{static_cast<int32_t>(n), nnz, A->colptr, L.rowidx_p, A->values, A->dtype};
+  h->launches += nl + 7;
   Scalars init{};
   init.tol = tol;
   init.maxit = maxit;
   *st.host = init;
   cudaMemcpyAsync(L.sc, st.host, sizeof(Scalars), cudaMemcpyHostToDevice, s);
-  // u = b, beta = ||b||, v = R^{-T} A^T u / alpha, w = v, y = 0
-  k_copy_d<<<gb, 256, 0, s>>>(m, b, L.u);
-  k_sq_partials<<<kRedBlocks, 256, 0, s>>>(m, L.u, L.partial);
-  k_finish_beta<<<1, 1024, 0, s>>>(L.partial, kRedBlocks, L.sc, 1);
-  spmv_cols(A, L.u, L.t2, L.sc, 0, s);
-  k_gemv_tri<<<gemv_blocks(n), 256, 0, s>>>(L.RinvT, static_cast<int>(n), L.t2, L.vraw,
-                                            nullptr, L.sc, 0, 1, 1);
-  k_lsqr_update<<<1, 1024, 0, s>>>(static_cast<int>(n), L.vraw, L.v, L.w, L.y, L.sc, 1);
-  h->launches += 6;
+  // u = b, beta = ||b||, v = R^{-T} A^T u / (beta alpha), w = v, y = 0
+  lsqr_kernels(L, csc, csr, mnz, b, static_cast<int32_t>(m), 1, s);
+  h->launches += 4;
   // iterations: a cached graph of kIterPerGraph iterations, replayed until
   // the device sets `done`
   const void* key[6] = {A->colptr, A->rowidx, A->values, st.ws,
@@ -690,7 +1102,8 @@ extern "C" int sketch_lsq_solve(sketch_t h, const sketch_csc* A,
     cudaGraph_t g = nullptr;
     e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return cuda_fail(h, e, "begin capture");
-    for (int it = 0; it < kIterPerGraph; ++it) lsqr_iteration(L, A, csr, s);
+    for (int it = 0; it < kIterPerGraph; ++it)
+      lsqr_kernels(L, csc, csr, mnz, nullptr, static_cast<int32_t>(m), 0, s);
     e = cudaStreamEndCapture(s, &g);
     if (e != cudaSuccess) return cuda_fail(h, e, "end capture");
     e = cudaGraphInstantiate(&st.graph, g, 0);
@@ -711,28 +1124,28 @@ extern "C" int sketch_lsq_solve(sketch_t h, const sketch_csc* A,
     for (;; launched += kIterPerGraph) {
       e = cudaGraphLaunch(st.graph, s);
       if (e != cudaSuccess) return cuda_fail(h, e, "graph launch");
-      h->launches += 6 * kIterPerGraph;
+      h->launches += 4 * kIterPerGraph;
       cudaMemcpyAsync(st.host, L.sc, sizeof(Scalars), cudaMemcpyDeviceToHost, s);
       e = cudaStreamSynchronize(s);
       if (e != cudaSuccess) return cuda_fail(h, e, "lsqr iterations");
       if (st.host->done || launched >= maxit) break;
     }
     // x = R^{-1} y
-    k_gemv_tri<<<gemv_blocks(n), 256, 0, s>>>(L.Rinv, static_cast<int>(n), L.y, x,
-                                              nullptr, L.sc, 0, 1, 0);
+    k_gemv_tri<<<gemv_blocks(n), 256, 0, s>>>(L.Rinv, static_cast<int>(n), L.y, x, 0);
     cudaEventRecord(st.ev[3], s);
     // ---- 5. Error(x) = ||A^T (A x - b)|| / (||A||_F ||A x - b||) in FP64 ----
-    k_spmv_rows<256><<<kRedBlocks, 256, 0, s>>>(static_cast<int32_t>(m), csr.rowptr, csr.ccol,
-                                                csr.cval, x, L.r, b, L.partial, L.sc, 1);
-    k_finish_beta<<<1, 1024, 0, s>>>(L.partial, kRedBlocks, L.sc, 2);
-    spmv_cols(A, L.r, L.t2, L.sc, 1, s);
+    const int g2 = rows_blocks(m);
+    k_residual<<<g2, kRows, 0, s>>>(static_cast<int32_t>(m), csr.rowptr, csr.ccol, csr.cval,
+                                    x, b, L.perm, L.r, L.pres);
+    cols(csc, L.r, L.t2, L.sc, 0, nullptr, nullptr, 0, 0, s);
     if (A->dtype == SKETCH_F32)
-      k_fro2<float><<<kRedBlocks, 256, 0, s>>>(nnz, static_cast<const float*>(A->values), L.partial);
+      k_fro2<float><<<kFroBlocks, 256, 0, s>>>(nnz, static_cast<const float*>(A->values), L.pfro);
     else
-      k_fro2<__nv_bfloat16><<<kRedBlocks, 256, 0, s>>>(
-          nnz, static_cast<const __nv_bfloat16*>(A->values), L.partial);
-    k_finish_error<<<1, 1024, 0, s>>>(L.partial, kRedBlocks, L.t2, static_cast<int>(n), L.sc);
-    h->launches += 6;
+      k_fro2<__nv_bfloat16><<<kFroBlocks, 256, 0, s>>>(
+          nnz, static_cast<const __nv_bfloat16*>(A->values), L.pfro);
+    k_finish_error<<<1, 96, 0, s>>>(L.pfro, kFroBlocks, L.pres, g2, L.t2,
+                                    static_cast<int>(n), L.sc);
+    h->launches += 5;
     cudaMemcpyAsync(st.host, L.sc, sizeof(Scalars), cudaMemcpyDeviceToHost, s);
     cudaMemcpyAsync(&qr_status, L.status, sizeof(int), cudaMemcpyDeviceToHost, s);
     e = cudaStreamSynchronize(s);
