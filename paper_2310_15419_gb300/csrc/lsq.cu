@@ -29,15 +29,24 @@ namespace {
 
 constexpr int kIterPerGraph = 8;
 
+// LSQR state that one iteration reads and the next writes lives in two slots
+// indexed by the parity of the iteration inside a captured graph, so that no
+// kernel reads a slot it writes.
+struct Slot {
+  double alpha, rhobar, phibar, anorm2;  // alpha_k, rhobar_k, phibar_k, ||B_k||_F^2
+  double cabs;    // |c| of the last plane rotation
+  double f_next;  // alpha_k / beta_k for the next rows pass
+  int iters, pad;
+};
+
 struct Scalars {
-  double alpha, beta, inv_beta, rhobar, phibar, anorm2, bnorm;
-  double test1, test2, ynorm, afro2, err_num2, err_res2;
-  double tol;
-  double f_next;           // alpha_k / beta_k for the next rows pass
-  double usq;              // ||u_raw||^2 after the rows pass
-  double zsq;              // the part of usq from rows of A with no nonzero
-  int iters, maxit, done, istop;
-  unsigned int counter;    // blocks of k_lsqr_step that have finished
+  double beta, inv_beta, bnorm, tol;
+  double usq;   // ||u_raw||^2 after the rows pass
+  double zsq;   // the part of usq from rows of A with no nonzero
+  double ynorm2;
+  double afro2, err_num2, err_res2;
+  Slot slot[2];
+  int maxit, done, istop, latest;  // latest: slot of the last finished iteration
 };
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -238,16 +247,41 @@ __global__ void k_trtri(const double* __restrict__ W, int64_t d, int n,
 // Each kernel returns at once when `done` is set.
 // ---------------------------------------------------------------------------
 constexpr int kRows = 256;  // threads per block of the rows pass
-constexpr int kTriWarps = 8;  // rows of R^{-1} / R^{-T} per block
+constexpr int kTriWarps = 4;  // rows of R^{-1} / R^{-T} per block
 
-// sum_{c in [lo, hi)} row[c] x[c] across one warp (every lane gets it).
-// Each round issues all sixteen loads of a lane before the first multiply,
-// so a row costs one memory latency per 256 entries.
-__device__ __forceinline__ double warp_row_dot(const double* __restrict__ row,
-                                               const double* __restrict__ x,
-                                               int64_t lo, int64_t hi, int lane) {
+// The first 256 entries of a warp's row [lo, hi): lane l holds
+// row[lo + l + 32 q], q < 8 (0 beyond hi).
+__device__ __forceinline__ void row_chunk(const double* __restrict__ row, int64_t lo,
+                                          int64_t hi, int lane, double r[8]) {
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int64_t c = lo + lane + 32 * q;
+    r[q] = c < hi ? row[c] : 0.0;
+  }
+}
+
+// sum_{c in [lo, hi)} row[c] x[c] across one warp (every lane gets it), with
+// the first 256 row entries already in r0 (row_chunk).  Each later round
+// issues all sixteen loads of a lane before the first multiply, so a row
+// costs one memory latency per 256 entries.
+__device__ __forceinline__ double warp_row_dot_pre(const double* __restrict__ row,
+                                                   const double* __restrict__ x,
+                                                   int64_t lo, int64_t hi, int lane,
+                                                   const double r0[8]) {
   double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
-  for (int64_t c0 = lo + lane; c0 < hi; c0 += 256) {
+  {
+    double v[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int64_t c = lo + lane + 32 * q;
+      v[q] = c < hi ? x[c] : 0.0;
+    }
+    a0 = fma(r0[0], v[0], a0); a1 = fma(r0[1], v[1], a1);
+    a2 = fma(r0[2], v[2], a2); a3 = fma(r0[3], v[3], a3);
+    a0 = fma(r0[4], v[4], a0); a1 = fma(r0[5], v[5], a1);
+    a2 = fma(r0[6], v[6], a2); a3 = fma(r0[7], v[7], a3);
+  }
+  for (int64_t c0 = lo + lane + 256; c0 < hi; c0 += 256) {
     double r[8], v[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
@@ -261,6 +295,14 @@ __device__ __forceinline__ double warp_row_dot(const double* __restrict__ row,
     a2 = fma(r[6], v[6], a2); a3 = fma(r[7], v[7], a3);
   }
   return warp_sum((a0 + a1) + (a2 + a3));
+}
+
+__device__ __forceinline__ double warp_row_dot(const double* __restrict__ row,
+                                               const double* __restrict__ x,
+                                               int64_t lo, int64_t hi, int lane) {
+  double r0[8];
+  row_chunk(row, lo, hi, lane, r0);
+  return warp_row_dot_pre(row, x, lo, hi, lane, r0);
 }
 
 // Fixed-order sum of part[0..np) by one warp (every lane gets it); loads in
@@ -293,57 +335,80 @@ __global__ void k_gemv_tri(const double* __restrict__ Mrow, int n,
   }
 }
 
-// Block-wide fixed-order sum for kernels of NT threads (thread 0 gets it).
+// Block-wide fixed-order sum for kernels of NT threads (warp 0 gets it):
+// every thread stores its value, then lane l of warp 0 adds entries l,
+// l + 32, ... and the warp adds across lanes.  That is NT/32 + 5 FP64
+// instructions for the block instead of five per warp.  red holds NT
+// doubles.
 template <int NT>
 __device__ __forceinline__ double block_sum0(double v, double* red) {
-  v = warp_sum(v);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  red[threadIdx.x] = v;
   __syncthreads();
   double p = 0.0;
-  if (threadIdx.x == 0) {
+  if (threadIdx.x < 32) {
+    double a0 = 0.0, a1 = 0.0;
 #pragma unroll
-    for (int w = 0; w < NT / 32; ++w) p += red[w];
+    for (int q = 0; q < NT / 32; q += 2) {
+      a0 += red[threadIdx.x + 32 * q];
+      if (q + 1 < NT / 32) a1 += red[threadIdx.x + 32 * (q + 1)];
+    }
+    p = warp_sum(a0 + a1);
   }
   __syncthreads();
   return p;
 }
 
+// Programmatic dependent launch: a kernel launched with programmatic stream
+// serialization may start while its predecessor finishes; it reads only
+// data the predecessor does not write before pdl_wait(), which returns once
+// the predecessor has completed and its writes are visible.  Each kernel
+// lets its successor launch only after its own wait, so everything older
+// than the predecessor is complete when the successor starts.  Without the
+// launch attribute both are no-ops.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // Rows pass over the CSR whose rows are ordered by decreasing length (row p
-// of it is row perm[p] of A; rows [0, *mnz) have nonzeros).
-// init: u_raw[p] = b[perm[p]] for every row; partial = sums of u_raw^2 over
+// of it is row perm[p] of A; rows [0, *mnz) have nonzeros).  u_raw is double
+// buffered: the pass reads uin and writes uout.
+// init: uout[p] = b[perm[p]] for every row; partial = sums of uout^2 over
 // the rows with nonzeros, partial_z over the others.
-// Otherwise, for p < *mnz: u_raw[p] = sum_e val t[col] - f u_raw[p] with
+// Otherwise, for p < *mnz: uout[p] = sum_e val t[col] - f uin[p] with
 // f = alpha_k / beta_k; partial as above.  Rows without nonzeros follow
 // u_raw <- -f u_raw, which only scales their sum of squares; the columns
 // pass applies that factor to it instead of touching them.
-__global__ void __launch_bounds__(kRows)
+__global__ void __launch_bounds__(kRows, 8)
     k_lsqr_rows(int32_t m, const int32_t* __restrict__ mnz_ptr,
                 const int32_t* __restrict__ rowptr, const int32_t* __restrict__ ccol,
                 const float* __restrict__ cval, const double* __restrict__ t,
-                double* __restrict__ u, const double* __restrict__ b,
-                const int32_t* __restrict__ perm, double* __restrict__ partial,
-                double* __restrict__ partial_z, const Scalars* __restrict__ sc, int init) {
-  __shared__ double red[kRows / 32];
-  if (sc->done) return;
+                const double* __restrict__ uin, double* __restrict__ uout,
+                const double* __restrict__ b, const int32_t* __restrict__ perm,
+                double* __restrict__ partial, double* __restrict__ partial_z,
+                const Scalars* __restrict__ sc, int par, int init) {
+  __shared__ double red[kRows];
   const int32_t mnz = *mnz_ptr;
-  const double f = init ? 0.0 : sc->f_next;
+  pdl_wait();
+  pdl_launch();
+  if (sc->done) return;
+  const double f = init ? 0.0 : sc->slot[par].f_next;
   const int64_t rows = init ? m : mnz;
   double s2 = 0.0, sz = 0.0;
   for (int64_t p = blockIdx.x * static_cast<int64_t>(kRows) + threadIdx.x; p < rows;
        p += static_cast<int64_t>(gridDim.x) * kRows) {
     if (init) {
       const double nu = b[perm[p]];
-      u[p] = nu;
+      uout[p] = nu;
       if (p < mnz)
         s2 = fma(nu, nu, s2);
       else
         sz = fma(nu, nu, sz);
     } else {
+      const int32_t lo = rowptr[p], hi = rowptr[p + 1];
+      const double up = uin[p];
       double acc = 0.0;
-      const int32_t hi = rowptr[p + 1];
-      for (int32_t e = rowptr[p]; e < hi; ++e) acc = fma(f64_of(cval[e]), t[ccol[e]], acc);
-      const double nu = fma(-f, u[p], acc);
-      u[p] = nu;
+      for (int32_t e = lo; e < hi; ++e) acc = fma(f64_of(cval[e]), t[ccol[e]], acc);
+      const double nu = fma(-f, up, acc);
+      uout[p] = nu;
       s2 = fma(nu, nu, s2);
     }
   }
@@ -355,23 +420,70 @@ __global__ void __launch_bounds__(kRows)
   }
 }
 
+// Paige & Saunders' stopping rules for the iterate in slot S, without
+// divisions or square roots:  istop 1 when ||r|| <= tol ||b|| + tol ||A||
+// ||y|| (compatible system), istop 2 when ||M^T r|| <= tol ||M|| ||r||
+// (least-squares solution), with ||r|| = phibar, ||M^T r|| = phibar alpha |c|
+// and ||M||^2 estimated by anorm2.  Returns istop, or -1 at maxit.
+__device__ __forceinline__ int lsqr_test(const Slot& S, double bnorm, double tol, double y2,
+                                         int maxit) {
+  if (S.iters == 0) return (S.alpha == 0.0 || bnorm == 0.0) ? 1 : 0;
+  const double rnorm = S.phibar;
+  const double arnorm = rnorm * S.alpha * S.cabs;
+  const double tol2 = tol * tol;
+  int istop = 0;
+  if (rnorm == 0.0 || arnorm * arnorm <= tol2 * S.anorm2 * (rnorm * rnorm)) istop = 2;
+  const double lhs = rnorm - tol * bnorm;
+  if (lhs <= 0.0 || lhs * lhs <= tol2 * S.anorm2 * y2) istop = 1;
+  if (istop == 0 && S.iters >= maxit) return -1;
+  return istop;
+}
+
+// Records the outcome of lsqr_test (one thread).
+__device__ __forceinline__ bool lsqr_record(Scalars* sc, int istop, double y2) {
+  if (istop == 0) return false;
+  sc->istop = istop > 0 ? istop : 0;
+  sc->ynorm2 = y2;
+  sc->done = 1;
+  return true;
+}
+
 // Columns pass: out[k] = sum_{e in column k} val[e] u[row[e]] (unscaled), one
-// block of 32*W threads per column, fixed-order reduction.  When np2 > 0,
-// block 0 first completes ||u_raw||^2 from the rows pass's partial sums:
-// usq = sum partial2 + z, with z = sum partial_z (init) or f^2 times the
-// previous z (rows without nonzeros), and stores usq and z.
+// block of 32*W threads per column k < n, fixed-order reduction.  With
+// lsqr = 1 the grid has one more block, which first applies the stopping
+// test to the previous iteration (slot par, sums of y^2 in party; not at
+// start-up) and sets `done`, else completes ||u_raw||^2 = sum partial2 + z,
+// with z = sum partial_z (init) or f^2 times the previous z (rows without
+// nonzeros).
 template <typename VT, int W>
 __global__ void __launch_bounds__(32 * W)
     k_cols(int32_t n, const int32_t* __restrict__ colptr,
            const int32_t* __restrict__ rowidx, const VT* __restrict__ vals,
-           const double* __restrict__ u, double* __restrict__ out, Scalars* sc,
-           int check_done, const double* __restrict__ partial2,
-           const double* __restrict__ partial_z, int np2, int init) {
-  __shared__ double red[W];
-  if (check_done && sc->done) return;
+           const double* __restrict__ u, double* __restrict__ out, Scalars* sc, int lsqr,
+           const double* __restrict__ partial2, const double* __restrict__ partial_z,
+           int np2, const double* __restrict__ party, int npy, int par, int init) {
+  __shared__ double red[32 * W];
+  __shared__ int stop;
   const int k = blockIdx.x;
-  if (k >= n) return;
-  if (k == 0 && np2 > 0) {
+  if (k == n) {  // the scalar block
+    // the test reads only what the step kernel before the rows pass wrote
+    if (!init && !sc->done) {
+      double a = 0.0;
+      for (int g = threadIdx.x; g < npy; g += 32 * W) a += party[g];
+      const double y2 = block_sum0<32 * W>(a, red);
+      if (threadIdx.x == 0) {
+        const int istop = lsqr_test(sc->slot[par], sc->bnorm, sc->tol, y2, sc->maxit);
+        stop = lsqr_record(sc, istop, y2);
+      }
+      __syncthreads();
+      if (stop) {
+        pdl_launch();
+        return;
+      }
+    }
+    pdl_wait();
+    pdl_launch();
+    if (sc->done) return;
     double a = 0.0, z = 0.0;
     for (int g = threadIdx.x; g < np2; g += 32 * W) {
       a += partial2[g];
@@ -381,16 +493,18 @@ __global__ void __launch_bounds__(32 * W)
     if (init) z = block_sum0<32 * W>(z, red);
     if (threadIdx.x == 0) {
       if (!init) {
-        const double f = sc->f_next;
+        const double f = sc->slot[par].f_next;
         z = f * f * sc->zsq;
       }
       sc->zsq = z;
       sc->usq = a + z;
     }
+    return;
   }
   const int32_t lo = colptr[k], hi = colptr[k + 1];
   double a0 = 0.0, a1 = 0.0;
-  for (int32_t e0 = lo + threadIdx.x; e0 < hi; e0 += 256 * W) {
+  bool first = true;
+  for (int32_t e0 = lo + threadIdx.x; e0 < hi || first; e0 += 256 * W) {
     int32_t row[8];
     double val[8];
 #pragma unroll
@@ -398,6 +512,16 @@ __global__ void __launch_bounds__(32 * W)
       const int32_t e = e0 + 32 * W * q;
       row[q] = e < hi ? rowidx[e] : -1;
       val[q] = e < hi ? val_at(vals, e) : 0.0;
+    }
+    if (first) {  // the indices and values are the caller's: load them first
+      first = false;
+      pdl_wait();
+      pdl_launch();
+      if (lsqr) {  // the scalar block of this grid may set `done` meanwhile
+        if (threadIdx.x == 0) stop = sc->done;
+        __syncthreads();
+        if (stop) return;
+      }
     }
     double uu[8];
 #pragma unroll
@@ -412,31 +536,48 @@ __global__ void __launch_bounds__(32 * W)
   if (threadIdx.x == 0) out[k] = s;
 }
 
+// The stopping test alone (one warp), for the last iteration of a captured
+// graph.
+__global__ void k_lsqr_test(const double* __restrict__ party, int npy, Scalars* sc, int par) {
+  pdl_wait();
+  pdl_launch();
+  if (sc->done) return;
+  const double y2 = warp_sum_parts(party, npy, threadIdx.x & 31);
+  if (threadIdx.x == 0)
+    lsqr_record(sc, lsqr_test(sc->slot[par], sc->bnorm, sc->tol, y2, sc->maxit), y2);
+}
+
 // vraw = R^{-T} t2 / beta - beta v  (init: without the beta v term), one warp
-// per row of the row-major lower-triangular R^{-T}.  Every block forms beta =
-// sqrt(usq) and 1/beta while its warps form their dot products; block 0
-// publishes them.  partial4[block]
-// = sum of vraw^2 over the block's rows.
+// per row of the row-major lower-triangular R^{-T}.  Every block forms
+// 1/beta = rsqrt(usq) and beta while its warps form their dot products;
+// block 0 publishes them.  partial4[block] = sum of vraw^2 over its rows.
 __global__ void __launch_bounds__(32 * kTriWarps)
     k_lsqr_vraw(int n, const double* __restrict__ RinvT, const double* __restrict__ t2,
                 const double* __restrict__ v, double* __restrict__ vraw,
                 double* __restrict__ partial4, Scalars* sc, int init) {
   __shared__ double sh[2 + kTriWarps];
-  if (sc->done) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t i = static_cast<int64_t>(blockIdx.x) * kTriWarps + warp;
+  const bool has = i < n;
+  double r0[8];  // R^{-T} and v are not written by the columns pass
+  row_chunk(RinvT + (has ? i : 0) * n, 0, has ? i + 1 : 0, lane, r0);
+  const double vi = (!init && has && lane == 0) ? v[i] : 0.0;
+  pdl_wait();
+  pdl_launch();
+  if (sc->done) return;
   if (threadIdx.x == 0) {
-    const double beta = sqrt(sc->usq);
-    sh[0] = beta;
-    sh[1] = beta > 0.0 ? 1.0 / beta : 0.0;
+    const double usq = sc->usq;
+    const double ib = usq > 0.0 ? rsqrt(usq) : 0.0;
+    sh[0] = usq * ib;
+    sh[1] = ib;
   }
-  const double dot = i < n ? warp_row_dot(RinvT + i * n, t2, 0, i + 1, lane) : 0.0;
+  const double dot = has ? warp_row_dot_pre(RinvT + i * n, t2, 0, i + 1, lane, r0) : 0.0;
   __syncthreads();
   const double beta = sh[0], ib = sh[1];
   if (lane == 0) {
     double vr2 = 0.0;
     if (i < n) {
-      const double vr = init ? ib * dot : fma(-beta, v[i], ib * dot);
+      const double vr = fma(-beta, vi, ib * dot);
       vraw[i] = vr;
       vr2 = vr * vr;
     }
@@ -459,65 +600,84 @@ __global__ void __launch_bounds__(32 * kTriWarps)
 // order), the plane rotation, v = vraw / alpha, y += (phi/rho) w,
 // w = v - (theta/rho) w, and t = R^{-1} v for the next rows pass (one warp
 // per row of the row-major upper-triangular R^{-1}; element i of v, w, y
-// belongs to the warp of row i).  The last block to finish sums ||y||^2 and
-// forms the stopping tests of Paige & Saunders: istop 1 when
-// ||r|| / ||b|| <= tol + tol ||A|| ||y|| / ||b||, istop 2 when
-// ||M^T r|| / (||M|| ||r||) <= tol.  init: start-up (v = w = vraw/alpha,
-// y = 0, rhobar = alpha, phibar = beta).
+// belongs to the warp of row i).  Reads slot par, block 0 writes slot
+// par ^ 1; party[block] = sum of y^2 over its rows.  init: start-up
+// (v = w = vraw / alpha, y = 0, rhobar = alpha, phibar = beta).
 __global__ void __launch_bounds__(32 * kTriWarps)
     k_lsqr_step(int n, const double* __restrict__ Rinv, const double* __restrict__ vraw,
                 double* __restrict__ v, double* __restrict__ w, double* __restrict__ y,
                 double* __restrict__ t, const double* __restrict__ partial4, int np4,
-                double* __restrict__ party, Scalars* sc, int init) {
+                double* __restrict__ party, Scalars* sc, int par, int init) {
   __shared__ double sh[8 + kTriWarps];
-  __shared__ int last;
-  if (sc->done) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t i = static_cast<int64_t>(blockIdx.x) * kTriWarps + warp;
+  const bool has = i < n;
+  // R^{-1}, w, y and slot par are not written by the vraw kernel
+  double r0[8];
+  row_chunk(Rinv + (has ? i : 0) * n, has ? i : 0, has ? n : 0, lane, r0);
+  double wi = 0.0, yi = 0.0;
+  if (lane == 0 && has && !init) {
+    wi = w[i];
+    yi = y[i];
+  }
+  Slot S{};
+  if (threadIdx.x == 0 && !init) S = sc->slot[par];
+  pdl_wait();
+  pdl_launch();
+  if (sc->done) return;
+  const double vri = (lane == 0 && has) ? vraw[i] : 0.0;
   if (warp == 0) {
     const double s = warp_sum_parts(partial4, np4, lane);
     if (lane == 0) {
-      const double alpha = sqrt(s);
+      const double ia = s > 0.0 ? rsqrt(s) : 0.0;
+      const double alpha = s * ia;
       const double beta = sc->beta;
-      double f_y = 0.0, f_w = 0.0, c = 0.0, rhobar = alpha, phibar = beta;
-      if (!init) {
-        const double rb = sc->rhobar, pb = sc->phibar;
-        const double rho = sqrt(fma(rb, rb, beta * beta));
-        const double irho = 1.0 / rho;
-        c = rb * irho;
-        const double sn = beta * irho;
+      Slot o{};
+      o.alpha = alpha;
+      o.f_next = alpha * sc->inv_beta;
+      double f_y = 0.0, f_w = 0.0;
+      if (init) {
+        o.rhobar = alpha;
+        o.phibar = beta;
+      } else {
+        const double rb = S.rhobar, pb = S.phibar;
+        const double irho = rsqrt(fma(rb, rb, beta * beta));
+        const double c = rb * irho, sn = beta * irho;
         f_y = c * pb * irho;
         f_w = sn * alpha * irho;
-        rhobar = -c * alpha;
-        phibar = sn * pb;
+        o.rhobar = -c * alpha;
+        o.phibar = sn * pb;
+        o.cabs = fabs(c);
+        o.anorm2 = S.anorm2 + S.alpha * S.alpha + beta * beta;
+        o.iters = S.iters + 1;
       }
-      sh[0] = alpha;
-      sh[1] = alpha > 0.0 ? 1.0 / alpha : 0.0;
-      sh[2] = f_y;
-      sh[3] = f_w;
-      sh[4] = c;
-      sh[5] = rhobar;
-      sh[6] = phibar;
+      if (blockIdx.x == 0) {
+        sc->slot[par ^ 1] = o;
+        sc->latest = par ^ 1;
+        if (init) sc->bnorm = beta;
+      }
+      sh[0] = ia;
+      sh[1] = f_y;
+      sh[2] = f_w;
     }
   }
-  const double dot = i < n ? warp_row_dot(Rinv + i * n, vraw, i, n, lane) : 0.0;
+  const double dot = has ? warp_row_dot_pre(Rinv + i * n, vraw, i, n, lane, r0) : 0.0;
   __syncthreads();
-  const double ia = sh[1];
+  const double ia = sh[0];
   if (lane == 0) {
     double y2 = 0.0;
     if (i < n) {
       t[i] = ia * dot;
-      const double vi = ia * vraw[i];
+      const double vi = ia * vri;
       v[i] = vi;
       if (init) {
         w[i] = vi;
         y[i] = 0.0;
       } else {
-        const double wi = w[i];
-        const double yi = fma(sh[2], wi, y[i]);
-        y[i] = yi;
-        w[i] = fma(-sh[3], wi, vi);
-        y2 = yi * yi;
+        const double yn = fma(sh[1], wi, yi);
+        y[i] = yn;
+        w[i] = fma(-sh[2], wi, vi);
+        y2 = yn * yn;
       }
     }
     sh[8 + warp] = y2;
@@ -528,54 +688,7 @@ __global__ void __launch_bounds__(32 * kTriWarps)
 #pragma unroll
     for (int q = 0; q < kTriWarps; ++q) p += sh[8 + q];
     party[blockIdx.x] = p;
-    __threadfence();
-    last = atomicAdd(&sc->counter, 1u) == gridDim.x - 1;
   }
-  __syncthreads();
-  if (!last || warp != 0) return;
-  __threadfence();
-  const double y2 = warp_sum_parts(party, gridDim.x, lane);
-  if (lane != 0) return;
-  const double alpha = sh[0], beta = sc->beta;
-  sc->counter = 0u;
-  sc->f_next = alpha * sc->inv_beta;
-  if (init) {
-    sc->alpha = alpha;
-    sc->rhobar = alpha;
-    sc->phibar = beta;
-    sc->bnorm = beta;
-    sc->anorm2 = 0.0;
-    sc->iters = 0;
-    const int stop = alpha == 0.0 || beta == 0.0;
-    sc->istop = stop;
-    sc->done = stop;
-    return;
-  }
-  const double alpha_k = sc->alpha;
-  const double anorm2 = sc->anorm2 + alpha_k * alpha_k + beta * beta;
-  const double phibar = sh[6];
-  sc->anorm2 = anorm2;
-  sc->alpha = alpha;
-  sc->rhobar = sh[5];
-  sc->phibar = phibar;
-  const int it = sc->iters + 1;
-  sc->iters = it;
-  const double ynorm = sqrt(y2);
-  const double anorm = sqrt(anorm2);
-  const double rnorm = phibar;
-  const double arnorm = phibar * alpha * fabs(sh[4]);
-  const double test1 = rnorm / sc->bnorm;
-  const double test2 = rnorm > 0.0 ? arnorm / (anorm * rnorm) : 0.0;
-  const double tol = sc->tol;
-  const double rtol = tol + tol * anorm * ynorm / sc->bnorm;
-  sc->test1 = test1;
-  sc->test2 = test2;
-  sc->ynorm = ynorm;
-  int istop = 0;
-  if (test2 <= tol) istop = 2;
-  if (test1 <= rtol) istop = 1;
-  sc->istop = istop;
-  if (istop || it >= sc->maxit) sc->done = 1;
 }
 
 // Error check: r = A x - b over the length-ordered CSR (row p is row perm[p]
@@ -668,11 +781,25 @@ __global__ void k_sort_rows(int32_t m, const int32_t* __restrict__ rowptr,
 }
 
 // Continue LSQR with a 10x tighter internal tolerance (the true Error(x)
-// missed the requested one).
-__global__ void k_tighten(Scalars* sc) {
-  sc->tol *= 0.1;
-  sc->done = 0;
-  sc->istop = 0;
+// missed the requested one).  flip: the last iteration's state is in slot 1
+// and buffer 1 of u_raw; move it to slot 0 / buffer 0, where a captured
+// graph starts.
+__global__ void k_tighten(Scalars* sc, int flip, int64_t m, const double* __restrict__ u1,
+                          double* __restrict__ u0) {
+  if (flip) {
+    for (int64_t p = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; p < m;
+         p += static_cast<int64_t>(gridDim.x) * blockDim.x)
+      u0[p] = u1[p];
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    sc->tol *= 0.1;
+    sc->done = 0;
+    sc->istop = 0;
+    if (flip) {
+      sc->slot[0] = sc->slot[1];
+      sc->latest = 0;
+    }
+  }
 }
 
 // ---- rows of A by decreasing nonzero count ------------------------------
@@ -808,7 +935,8 @@ namespace {
 
 struct LsqLayout {
   float* Ahat;
-  double *W, *tau, *Rrow, *Rinv, *RinvT, *u, *t, *t2, *v, *vraw, *w, *y;
+  double *W, *tau, *Rrow, *Rinv, *RinvT, *t, *t2, *v, *vraw, *w, *y;
+  double* u[2];  // u_raw, double buffered by iteration parity
   double *p2, *p4, *py, *pfro, *pres;  // per-block partial sums
   double* r;  // A x - b for the error check (kept apart from LSQR's u)
   Scalars* sc;
@@ -829,7 +957,7 @@ constexpr int kFroBlocks = 512;
 
 int rows_blocks(int64_t m) {
   return static_cast<int>(
-      std::max<int64_t>(1, std::min<int64_t>((m + kRows - 1) / kRows, 4LL * num_sms())));
+      std::max<int64_t>(1, std::min<int64_t>((m + kRows - 1) / kRows, 8LL * num_sms())));
 }
 
 int tri_blocks(int64_t n) { return static_cast<int>((n + kTriWarps - 1) / kTriWarps); }
@@ -848,7 +976,8 @@ LsqLayout layout(void* base, int64_t m, int64_t n, int64_t d, int64_t nnz) {
   L.Rrow = reinterpret_cast<double*>(take(sizeof(double) * n * n));
   L.Rinv = reinterpret_cast<double*>(take(sizeof(double) * n * n));
   L.RinvT = reinterpret_cast<double*>(take(sizeof(double) * n * n));
-  L.u = reinterpret_cast<double*>(take(sizeof(double) * m));
+  L.u[0] = reinterpret_cast<double*>(take(sizeof(double) * m));
+  L.u[1] = reinterpret_cast<double*>(take(sizeof(double) * m));
   L.r = reinterpret_cast<double*>(take(sizeof(double) * m));
   L.t = reinterpret_cast<double*>(take(sizeof(double) * n));
   L.t2 = reinterpret_cast<double*>(take(sizeof(double) * n));
@@ -891,20 +1020,45 @@ struct CscView {
   int32_t dtype;
 };
 
+// Launch with programmatic stream serialization (pdl = 1): the kernel may
+// start while the previous kernel on the stream finishes (see pdl_wait).
+template <typename... KArgs, typename... Args>
+void launch(void (*kern)(KArgs...), unsigned grid, unsigned block, cudaStream_t s, int pdl,
+            Args... args) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl ? 1 : 0;
+  cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+
+// Columns pass launch.  lsqr = 1 adds the scalar block (stopping test and
+// ||u_raw||^2) of an LSQR iteration.
+struct ColsArgs {
+  int lsqr = 0;
+  const double *p2 = nullptr, *pz = nullptr, *py = nullptr;
+  int np2 = 0, npy = 0, par = 0, init = 0;
+};
+
 template <typename VT>
 void launch_cols(const CscView& A, const double* u, double* out, Scalars* sc,
-                 int check_done, const double* p2, const double* pz, int np2, int init,
-                 cudaStream_t s) {
+                 const ColsArgs& c, cudaStream_t s) {
   // warps per column from the mean column length: about 16 entries per
   // thread (any choice is correct)
   const int64_t avg = A.nnz / std::max<int64_t>(1, A.n);
   int W = 1;
   while (W < 8 && avg > 512LL * W) W *= 2;
-  const unsigned g = static_cast<unsigned>(A.n);
+  const unsigned g = static_cast<unsigned>(A.n + (c.lsqr ? 1 : 0));
   const VT* vals = static_cast<const VT*>(A.values);
-#define SK_COLS(WW)                                                              \
-  k_cols<VT, WW><<<g, 32 * WW, 0, s>>>(A.n, A.colptr, A.rowidx, vals, u, out, sc, \
-                                       check_done, p2, pz, np2, init)
+#define SK_COLS(WW)                                                                     \
+  launch(k_cols<VT, WW>, g, 32 * WW, s, c.lsqr, A.n, A.colptr, A.rowidx, vals, u, out, sc, \
+         c.lsqr, c.p2, c.pz, c.np2, c.py, c.npy, c.par, c.init)
   switch (W) {
     case 1: SK_COLS(1); break;
     case 2: SK_COLS(2); break;
@@ -914,29 +1068,42 @@ void launch_cols(const CscView& A, const double* u, double* out, Scalars* sc,
 #undef SK_COLS
 }
 
-void cols(const CscView& A, const double* u, double* out, Scalars* sc, int check_done,
-          const double* p2, const double* pz, int np2, int init, cudaStream_t s) {
+void cols(const CscView& A, const double* u, double* out, Scalars* sc, const ColsArgs& c,
+          cudaStream_t s) {
   if (A.dtype == SKETCH_F32)
-    launch_cols<float>(A, u, out, sc, check_done, p2, pz, np2, init, s);
+    launch_cols<float>(A, u, out, sc, c, s);
   else
-    launch_cols<__nv_bfloat16>(A, u, out, sc, check_done, p2, pz, np2, init, s);
+    launch_cols<__nv_bfloat16>(A, u, out, sc, c, s);
 }
 
 unsigned gemv_blocks(int64_t n) {
   return static_cast<unsigned>(std::max<int64_t>(1, std::min<int64_t>((n + 7) / 8, 32LL * num_sms())));
 }
 
-// LSQR start-up (init = 1) or one iteration (init = 0): four kernels.
+// LSQR start-up (init = 1, par = 1) or iteration j of a graph (par = j & 1):
+// four kernels.  The rows pass reads u_raw[par] and writes u_raw[par ^ 1];
+// the step reads slot par and writes slot par ^ 1.
 void lsqr_kernels(const LsqLayout& L, const CscView& A, const CsrView& csr,
-                  const int32_t* mnz, const double* b, int32_t m, int init, cudaStream_t s) {
+                  const int32_t* mnz, const double* b, int32_t m, int par, int init,
+                  cudaStream_t s) {
   const int n = A.n;
   const int g2 = rows_blocks(m), gt = tri_blocks(n);
-  k_lsqr_rows<<<g2, kRows, 0, s>>>(m, mnz, csr.rowptr, csr.ccol, csr.cval, L.t, L.u, b,
-                                   L.perm, L.p2, L.pz, L.sc, init);
-  cols(A, L.u, L.t2, L.sc, 1, L.p2, L.pz, g2, init, s);
-  k_lsqr_vraw<<<gt, 32 * kTriWarps, 0, s>>>(n, L.RinvT, L.t2, L.v, L.vraw, L.p4, L.sc, init);
-  k_lsqr_step<<<gt, 32 * kTriWarps, 0, s>>>(n, L.Rinv, L.vraw, L.v, L.w, L.y, L.t, L.p4, gt,
-                                            L.py, L.sc, init);
+  launch(k_lsqr_rows, g2, kRows, s, 1, m, mnz, csr.rowptr, csr.ccol, csr.cval, L.t, L.u[par],
+         L.u[par ^ 1], b, L.perm, L.p2, L.pz, L.sc, par, init);
+  ColsArgs c;
+  c.lsqr = 1;
+  c.p2 = L.p2;
+  c.pz = L.pz;
+  c.np2 = g2;
+  c.py = L.py;
+  c.npy = gt;
+  c.par = par;
+  c.init = init;
+  cols(A, L.u[par ^ 1], L.t2, L.sc, c, s);
+  launch(k_lsqr_vraw, gt, 32 * kTriWarps, s, 1, n, L.RinvT, L.t2, L.v, L.vraw, L.p4, L.sc,
+         init);
+  launch(k_lsqr_step, gt, 32 * kTriWarps, s, 1, n, L.Rinv, L.vraw, L.v, L.w, L.y, L.t, L.p4,
+         gt, L.py, L.sc, par, init);
 }
 
 }  // namespace
@@ -1088,7 +1255,7 @@ extern "C" int sketch_lsq_solve(sketch_t h, const sketch_csc* A,
   *st.host = init;
   cudaMemcpyAsync(L.sc, st.host, sizeof(Scalars), cudaMemcpyHostToDevice, s);
   // u = b, beta = ||b||, v = R^{-T} A^T u / (beta alpha), w = v, y = 0
-  lsqr_kernels(L, csc, csr, mnz, b, static_cast<int32_t>(m), 1, s);
+  lsqr_kernels(L, csc, csr, mnz, b, static_cast<int32_t>(m), 1, 1, s);
   h->launches += 4;
   // iterations: a cached graph of kIterPerGraph iterations, replayed until
   // the device sets `done`
@@ -1102,8 +1269,10 @@ extern "C" int sketch_lsq_solve(sketch_t h, const sketch_csc* A,
     cudaGraph_t g = nullptr;
     e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return cuda_fail(h, e, "begin capture");
+    static_assert(kIterPerGraph % 2 == 0, "a graph starts and ends on slot 0");
     for (int it = 0; it < kIterPerGraph; ++it)
-      lsqr_kernels(L, csc, csr, mnz, nullptr, static_cast<int32_t>(m), 0, s);
+      lsqr_kernels(L, csc, csr, mnz, nullptr, static_cast<int32_t>(m), it & 1, 0, s);
+    launch(k_lsqr_test, 1, 32, s, 1, L.py, tri_blocks(n), L.sc, 0);
     e = cudaStreamEndCapture(s, &g);
     if (e != cudaSuccess) return cuda_fail(h, e, "end capture");
     e = cudaGraphInstantiate(&st.graph, g, 0);
@@ -1124,7 +1293,7 @@ extern "C" int sketch_lsq_solve(sketch_t h, const sketch_csc* A,
     for (;; launched += kIterPerGraph) {
       e = cudaGraphLaunch(st.graph, s);
       if (e != cudaSuccess) return cuda_fail(h, e, "graph launch");
-      h->launches += 4 * kIterPerGraph;
+      h->launches += 4 * kIterPerGraph + 1;
       cudaMemcpyAsync(st.host, L.sc, sizeof(Scalars), cudaMemcpyDeviceToHost, s);
       e = cudaStreamSynchronize(s);
       if (e != cudaSuccess) return cuda_fail(h, e, "lsqr iterations");
@@ -1137,7 +1306,7 @@ extern "C" int sketch_lsq_solve(sketch_t h, const sketch_csc* A,
     const int g2 = rows_blocks(m);
     k_residual<<<g2, kRows, 0, s>>>(static_cast<int32_t>(m), csr.rowptr, csr.ccol, csr.cval,
                                     x, b, L.perm, L.r, L.pres);
-    cols(csc, L.r, L.t2, L.sc, 0, nullptr, nullptr, 0, 0, s);
+    cols(csc, L.r, L.t2, L.sc, ColsArgs{}, s);
     if (A->dtype == SKETCH_F32)
       k_fro2<float><<<kFroBlocks, 256, 0, s>>>(nnz, static_cast<const float*>(A->values), L.pfro);
     else
@@ -1155,11 +1324,11 @@ extern "C" int sketch_lsq_solve(sketch_t h, const sketch_csc* A,
     const double err = den > 0.0 ? std::sqrt(c.err_num2) / den : 0.0;
     // stop when the metric is met, LSQR ran out of iterations, or another
     // round gained less than 2x (the metric sits at its FP64 floor)
-    if (err <= tol || c.istop == 0 || qr_status != 0 || c.iters >= maxit ||
-        err > 0.5 * prev_err)
+    if (err <= tol || c.istop == 0 || qr_status != 0 ||
+        c.slot[c.latest & 1].iters >= maxit || err > 0.5 * prev_err)
       break;
     prev_err = err;
-    k_tighten<<<1, 1, 0, s>>>(L.sc);
+    k_tighten<<<gb, 256, 0, s>>>(L.sc, c.latest == 1, m, L.u[1], L.u[0]);
     h->launches += 1;
   }
   cudaEventRecord(st.ev[5], s);
@@ -1169,9 +1338,12 @@ extern "C" int sketch_lsq_solve(sketch_t h, const sketch_csc* A,
   const Scalars& sc = *st.host;
   if (info) {
     std::memset(info, 0, sizeof(*info));
-    info->iters = sc.iters;
+    const Slot& S = sc.slot[sc.latest & 1];
+    info->iters = S.iters;
     info->istop = sc.istop;
-    info->test2 = sc.test2;
+    const double arnorm = S.phibar * S.alpha * S.cabs;
+    const double anorm = std::sqrt(S.anorm2);
+    info->test2 = S.phibar > 0.0 && anorm > 0.0 ? arnorm / (anorm * S.phibar) : 0.0;
     const double den = std::sqrt(sc.afro2) * std::sqrt(sc.err_res2);
     info->error = den > 0.0 ? std::sqrt(sc.err_num2) / den : 0.0;
     float ms = 0.f;
