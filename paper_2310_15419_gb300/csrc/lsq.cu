@@ -91,6 +91,39 @@ __device__ __forceinline__ double f64_of(float f) {
   return __longlong_as_double(static_cast<long long>(bits));
 }
 
+// Block-wide fixed-order sum for kernels of NT threads (warp 0 gets it):
+// every thread stores its value, then lane l of warp 0 adds entries l,
+// l + 32, ... and the warp adds across lanes.  That is NT/32 + 5 FP64
+// instructions for the block instead of five per warp.  red holds NT
+// doubles.
+template <int NT>
+__device__ __forceinline__ double block_sum0(double v, double* red) {
+  red[threadIdx.x] = v;
+  __syncthreads();
+  double p = 0.0;
+  if (threadIdx.x < 32) {
+    double a0 = 0.0, a1 = 0.0;
+#pragma unroll
+    for (int q = 0; q < NT / 32; q += 2) {
+      a0 += red[threadIdx.x + 32 * q];
+      if (q + 1 < NT / 32) a1 += red[threadIdx.x + 32 * (q + 1)];
+    }
+    p = warp_sum(a0 + a1);
+  }
+  __syncthreads();
+  return p;
+}
+
+// Programmatic dependent launch: a kernel launched with programmatic stream
+// serialization may start while its predecessor finishes; it reads only
+// data the predecessor does not write before pdl_wait(), which returns once
+// the predecessor has completed and its writes are visible.  Each kernel
+// lets its successor launch only after its own wait, so everything older
+// than the predecessor is complete when the successor starts.  Without the
+// launch attribute both are no-ops.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 template <typename VT>
 __device__ __forceinline__ double val_at(const VT* v, int64_t i) {
   return f64_of(to_f32(v[i]));
@@ -107,123 +140,196 @@ __global__ void k_to_double(int64_t total, const float* __restrict__ a,
 }
 
 constexpr int kQrThreads = 128;
+constexpr int kQrRegs = 8;  // column entries a thread keeps in registers
 
-// Block-wide sum for the QR kernels (kQrThreads threads): warp sums, then
-// thread 0 adds the four in order; every thread gets the result.
-__device__ __forceinline__ double qr_block_sum(double v, double* red) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  v = warp_sum(v);
-  if (lane == 0) red[warp] = v;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double t = red[0];
+// Column c of W (column-major, leading dimension d): apply reflector k
+// (H = I - tau v v^T, v = column k below the diagonal with v_k = 1; k < 0:
+// none) and, when c == k + 1, form the reflector of column c (rows c..d-1)
+// in place: R(c,c) = beta = -sign(alpha) ||x||, v below the diagonal, tau[c]
+// (H = I, tau = 0, when the part below the diagonal is zero).  A thread keeps
+// rows r0 + tid + kQrThreads q, q < kQrRegs, in registers across the dot
+// product, the update with the squared norm, and the scaling; rows past
+// those are reloaded.  The scalar chain (sqrt, two divides) runs in thread 0.
+__device__ void qr_column(double* __restrict__ W, int64_t d, int k, int c,
+                          double* __restrict__ tau, double* red, double* bc) {
+  const int tid = threadIdx.x;
+  double* y = W + static_cast<int64_t>(c) * d;
+  const bool form = c == k + 1;
+  const int64_t r0 = k + 1;
+  const double t = k >= 0 ? tau[k] : 0.0;
+  const double* v = W + static_cast<int64_t>(k >= 0 ? k : 0) * d;
+  const int64_t rtail = r0 + static_cast<int64_t>(kQrThreads) * kQrRegs;
+  double yr[kQrRegs], vr[kQrRegs];
 #pragma unroll
-    for (int w = 1; w < kQrThreads / 32; ++w) t += red[w];
-    red[8] = t;
+  for (int q = 0; q < kQrRegs; ++q) {
+    const int64_t r = r0 + tid + kQrThreads * q;
+    yr[q] = r < d ? y[r] : 0.0;
+    vr[q] = (t != 0.0 && r < d) ? v[r] : 0.0;
+  }
+  if (t != 0.0) {
+    double s0 = 0.0, s1 = 0.0;
+#pragma unroll
+    for (int q = 0; q < kQrRegs; q += 2) {
+      s0 = fma(vr[q], yr[q], s0);
+      s1 = fma(vr[q + 1], yr[q + 1], s1);
+    }
+    for (int64_t r = rtail + tid; r < d; r += kQrThreads) s0 = fma(v[r], y[r], s0);
+    const double sum = block_sum0<kQrThreads>(s0 + s1, red);
+    if (tid == 0) {
+      const double yk = y[k];
+      const double f = t * (sum + yk);
+      y[k] = yk - f;
+      bc[0] = f;
+    }
+    __syncthreads();
+    const double f = bc[0];
+#pragma unroll
+    for (int q = 0; q < kQrRegs; ++q) yr[q] = fma(-f, vr[q], yr[q]);
+    for (int64_t r = rtail + tid; r < d; r += kQrThreads) y[r] = fma(-f, v[r], y[r]);
+    if (!form) {
+#pragma unroll
+      for (int q = 0; q < kQrRegs; ++q) {
+        const int64_t r = r0 + tid + kQrThreads * q;
+        if (r < d) y[r] = yr[q];
+      }
+      return;
+    }
+  }
+  if (!form) return;
+  // reflector of column c: alpha = row c (thread 0, q = 0), sigma = rows > c
+  double nrm = 0.0;
+#pragma unroll
+  for (int q = 0; q < kQrRegs; ++q) {
+    const int64_t r = r0 + tid + kQrThreads * q;
+    if (r > c) nrm = fma(yr[q], yr[q], nrm);
+  }
+  for (int64_t r = rtail + tid; r < d; r += kQrThreads) nrm = fma(y[r], y[r], nrm);
+  const double sigma = block_sum0<kQrThreads>(nrm, red);
+  if (tid == 0) {
+    if (sigma == 0.0) {
+      tau[c] = 0.0;
+      bc[1] = 1.0;
+    } else {
+      const double alpha = yr[0];
+      const double norm = sqrt(fma(alpha, alpha, sigma));
+      const double beta = alpha >= 0.0 ? -norm : norm;
+      bc[1] = 1.0 / (alpha - beta);
+      tau[c] = (beta - alpha) / beta;
+      yr[0] = beta;
+    }
   }
   __syncthreads();
-  return red[8];
-}
-
-// Householder reflector of column k (rows k..d-1) of W, in place.  The
-// scalar chain (sqrt, two divides) runs in thread 0 only.
-__device__ void qr_reflector(double* W, int64_t d, int k, double* tau, double* red) {
-  double* x = W + static_cast<int64_t>(k) * d;
-  double s0 = 0.0, s1 = 0.0;
-  int64_t r = k + 1 + threadIdx.x;
-  for (; r + kQrThreads < d; r += 2 * kQrThreads) {
-    s0 = fma(x[r], x[r], s0);
-    s1 = fma(x[r + kQrThreads], x[r + kQrThreads], s1);
+  const double scale = bc[1];
+#pragma unroll
+  for (int q = 0; q < kQrRegs; ++q) {
+    const int64_t r = r0 + tid + kQrThreads * q;
+    if (r < d) y[r] = r > c ? yr[q] * scale : yr[q];
   }
-  if (r < d) s0 = fma(x[r], x[r], s0);
-  const double sigma = qr_block_sum(s0 + s1, red);
-  if (sigma == 0.0) {  // nothing below the diagonal: H = I
-    if (threadIdx.x == 0) tau[k] = 0.0;
-    return;
-  }
-  if (threadIdx.x == 0) {
-    const double alpha = x[k];
-    const double norm = sqrt(fma(alpha, alpha, sigma));
-    const double beta = alpha >= 0.0 ? -norm : norm;
-    red[9] = 1.0 / (alpha - beta);
-    tau[k] = (beta - alpha) / beta;
-    x[k] = beta;
-  }
-  __syncthreads();
-  const double scale = red[9];
-  for (int64_t q = k + 1 + threadIdx.x; q < d; q += kQrThreads) x[q] *= scale;
+  for (int64_t r = rtail + tid; r < d; r += kQrThreads) y[r] *= scale;
 }
 
 __global__ void __launch_bounds__(kQrThreads)
     k_qr_first(double* W, int64_t d, double* tau) {
-  __shared__ double red[16];
-  qr_reflector(W, d, 0, tau, red);
+  __shared__ double red[kQrThreads];
+  __shared__ double bc[2];
+  qr_column(W, d, -1, 0, tau, red, bc);
 }
 
 // Apply reflector k to columns k+1..n-1 (one block per column); the block of
-// column k+1 then forms reflector k+1.
+// column k+1 then forms reflector k+1.  Launched with programmatic stream
+// serialization: every read depends on the previous step.
 __global__ void __launch_bounds__(kQrThreads)
     k_qr_step(double* W, int64_t d, int n, int k, double* tau) {
-  __shared__ double red[16];
+  __shared__ double red[kQrThreads];
+  __shared__ double bc[2];
+  pdl_wait();
+  pdl_launch();
   const int c = k + 1 + blockIdx.x;
   if (c >= n) return;
-  const double t = tau[k];
-  const double* v = W + static_cast<int64_t>(k) * d;
-  double* y = W + static_cast<int64_t>(c) * d;
-  if (t != 0.0) {
-    double s0 = 0.0, s1 = 0.0;
-    int64_t r = k + 1 + threadIdx.x;
-    for (; r + kQrThreads < d; r += 2 * kQrThreads) {
-      s0 = fma(v[r], y[r], s0);
-      s1 = fma(v[r + kQrThreads], y[r + kQrThreads], s1);
-    }
-    if (r < d) s0 = fma(v[r], y[r], s0);
-    const double f = t * (qr_block_sum(s0 + s1, red) + y[k]);
-    if (threadIdx.x == 0) y[k] -= f;
-    for (int64_t q = k + 1 + threadIdx.x; q < d; q += kQrThreads) y[q] = fma(-f, v[q], y[q]);
-    __syncthreads();
-  }
-  if (c == k + 1) qr_reflector(W, d, c, tau, red);
+  qr_column(W, d, k, c, tau, red, bc);
 }
 
-// Rrow = R (upper n x n of W) row-major; flags a zero diagonal.
+// Rrow = R (upper n x n of W) row-major, rdiag = 1 / diag(R); flags a zero
+// diagonal.
 __global__ void k_extract_r(const double* __restrict__ W, int64_t d, int n,
-                            double* __restrict__ Rrow, int* status) {
+                            double* __restrict__ Rrow, double* __restrict__ rdiag,
+                            int* status) {
   const int64_t total = static_cast<int64_t>(n) * n;
   for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
        t < total; t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
     const int i = static_cast<int>(t / n), c = static_cast<int>(t % n);
     const double v = c >= i ? W[static_cast<int64_t>(c) * d + i] : 0.0;
     Rrow[t] = v;
-    if (c == i && v == 0.0) atomicOr(status, 4);
+    if (c == i) {
+      rdiag[i] = v != 0.0 ? 1.0 / v : 0.0;
+      if (v == 0.0) atomicOr(status, 4);
+    }
   }
 }
 
-// X = R^{-1} by back substitution, one warp per column j of X, in the
-// column (axpy) form: with s = e_j, for c = j, j-1, ..., 0:
+// X = R^{-1} by back substitution, one block per column j of X (longest
+// first), in the column (axpy) form: with s = e_j, for c = j, j-1, ..., 0:
 //   X[c][j] = s[c] / R[c][c];   s[0..c-1] -= R[0..c-1][c] * X[c][j].
-// R is read column-major from the QR workspace W (rows of a column are
-// contiguous); the running sums s live in X's own column.  Writes Xrow
+// s lives in shared memory (n doubles); R is read column-major from the QR
+// workspace W, the next column while the current one is applied; rdiag =
+// 1 / diag(R).  Thread t owns rows t + blockDim.x q, q < NR.  Writes Xrow
 // (row-major X) and XTrow (row-major X^T).
+template <int NR>
 __global__ void k_trtri(const double* __restrict__ W, int64_t d, int n,
-                        double* __restrict__ Xrow, double* __restrict__ XTrow) {
-  const int lane = threadIdx.x & 31;
-  const int64_t warps = static_cast<int64_t>(gridDim.x) * (blockDim.x >> 5);
-  for (int64_t j = blockIdx.x * static_cast<int64_t>(blockDim.x >> 5) + (threadIdx.x >> 5);
-       j < n; j += warps) {
-    double* xt = XTrow + j * n;  // column j of X, contiguous
-    for (int c = lane; c < n; c += 32) xt[c] = (c == j) ? 1.0 : 0.0;
-    __syncwarp();
-    for (int64_t c = j; c >= 0; --c) {
-      const double* rc = W + c * d;  // column c of R: rows 0..c
-      const double xc = xt[c] / rc[c];
-      __syncwarp();
-      if (lane == 0) xt[c] = xc;
-      for (int64_t r = lane; r < c; r += 32) xt[r] -= rc[r] * xc;
-      __syncwarp();
-    }
-    for (int64_t i = lane; i < n; i += 32) Xrow[i * n + j] = xt[i];
+                        const double* __restrict__ rdiag, double* __restrict__ Xrow,
+                        double* __restrict__ XTrow) {
+  extern __shared__ double sx[];
+  const int T = blockDim.x, tid = threadIdx.x;
+  const int j = n - 1 - static_cast<int>(blockIdx.x);
+  for (int r = tid; r <= j; r += T) sx[r] = r == j ? 1.0 : 0.0;
+  double rc[NR], rn[NR];
+#pragma unroll
+  for (int q = 0; q < NR; ++q) {
+    const int r = tid + T * q;
+    rc[q] = r < j ? W[static_cast<int64_t>(j) * d + r] : 0.0;
   }
+  __syncthreads();
+  for (int c = j; c >= 0; --c) {
+#pragma unroll
+    for (int q = 0; q < NR; ++q) {
+      const int r = tid + T * q;
+      rn[q] = r < c - 1 ? W[static_cast<int64_t>(c - 1) * d + r] : 0.0;
+    }
+    const double xc = sx[c] * rdiag[c];
+#pragma unroll
+    for (int q = 0; q < NR; ++q) {
+      const int r = tid + T * q;
+      if (r < c) sx[r] = fma(-rc[q], xc, sx[r]);
+    }
+    __syncthreads();
+    if (tid == 0) sx[c] = xc;
+#pragma unroll
+    for (int q = 0; q < NR; ++q) rc[q] = rn[q];
+  }
+  __syncthreads();
+  for (int r = tid; r < n; r += T) {
+    const double x = r <= j ? sx[r] : 0.0;
+    Xrow[static_cast<int64_t>(r) * n + j] = x;
+    XTrow[static_cast<int64_t>(j) * n + r] = x;
+  }
+}
+
+// Launch of k_trtri: NR = 4 rows per thread up to n = 4096, else 8.
+cudaError_t launch_trtri(const double* W, int64_t d, int n, const double* rdiag,
+                         double* Xrow, double* XTrow, cudaStream_t s) {
+  const size_t smem = sizeof(double) * static_cast<size_t>(n);
+  if (n <= 4096) {
+    int T = 128;
+    while (T * 4 < n) T *= 2;
+    cudaFuncSetAttribute(k_trtri<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         static_cast<int>(smem));
+    k_trtri<4><<<n, T, smem, s>>>(W, d, n, rdiag, Xrow, XTrow);
+  } else {
+    cudaFuncSetAttribute(k_trtri<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         static_cast<int>(smem));
+    k_trtri<8><<<n, 1024, smem, s>>>(W, d, n, rdiag, Xrow, XTrow);
+  }
+  return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------
@@ -334,39 +440,6 @@ __global__ void k_gemv_tri(const double* __restrict__ Mrow, int n,
     if (lane == 0) out[i] = s;
   }
 }
-
-// Block-wide fixed-order sum for kernels of NT threads (warp 0 gets it):
-// every thread stores its value, then lane l of warp 0 adds entries l,
-// l + 32, ... and the warp adds across lanes.  That is NT/32 + 5 FP64
-// instructions for the block instead of five per warp.  red holds NT
-// doubles.
-template <int NT>
-__device__ __forceinline__ double block_sum0(double v, double* red) {
-  red[threadIdx.x] = v;
-  __syncthreads();
-  double p = 0.0;
-  if (threadIdx.x < 32) {
-    double a0 = 0.0, a1 = 0.0;
-#pragma unroll
-    for (int q = 0; q < NT / 32; q += 2) {
-      a0 += red[threadIdx.x + 32 * q];
-      if (q + 1 < NT / 32) a1 += red[threadIdx.x + 32 * (q + 1)];
-    }
-    p = warp_sum(a0 + a1);
-  }
-  __syncthreads();
-  return p;
-}
-
-// Programmatic dependent launch: a kernel launched with programmatic stream
-// serialization may start while its predecessor finishes; it reads only
-// data the predecessor does not write before pdl_wait(), which returns once
-// the predecessor has completed and its writes are visible.  Each kernel
-// lets its successor launch only after its own wait, so everything older
-// than the predecessor is complete when the successor starts.  Without the
-// launch attribute both are no-ops.
-__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-__device__ __forceinline__ void pdl_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
 // Rows pass over the CSR whose rows are ordered by decreasing length (row p
 // of it is row perm[p] of A; rows [0, *mnz) have nonzeros).  u_raw is double
@@ -935,7 +1008,7 @@ namespace {
 
 struct LsqLayout {
   float* Ahat;
-  double *W, *tau, *Rrow, *Rinv, *RinvT, *t, *t2, *v, *vraw, *w, *y;
+  double *W, *tau, *Rrow, *rdiag, *Rinv, *RinvT, *t, *t2, *v, *vraw, *w, *y;
   double* u[2];  // u_raw, double buffered by iteration parity
   double *p2, *p4, *py, *pfro, *pres;  // per-block partial sums
   double* r;  // A x - b for the error check (kept apart from LSQR's u)
@@ -974,6 +1047,7 @@ LsqLayout layout(void* base, int64_t m, int64_t n, int64_t d, int64_t nnz) {
   L.W = reinterpret_cast<double*>(take(sizeof(double) * d * n));
   L.tau = reinterpret_cast<double*>(take(sizeof(double) * n));
   L.Rrow = reinterpret_cast<double*>(take(sizeof(double) * n * n));
+  L.rdiag = reinterpret_cast<double*>(take(sizeof(double) * n));
   L.Rinv = reinterpret_cast<double*>(take(sizeof(double) * n * n));
   L.RinvT = reinterpret_cast<double*>(take(sizeof(double) * n * n));
   L.u[0] = reinterpret_cast<double*>(take(sizeof(double) * m));
@@ -1185,10 +1259,10 @@ extern "C" int sketch_lsq_solve(sketch_t h, const sketch_csc* A,
       k_to_double<<<gb, 256, 0, s>>>(dn, L.Ahat, L.W);
       k_qr_first<<<1, kQrThreads, 0, s>>>(L.W, d, L.tau);
       for (int k = 0; k + 1 < n; ++k)
-        k_qr_step<<<static_cast<unsigned>(n - k - 1), kQrThreads, 0, s>>>(
-            L.W, d, static_cast<int>(n), k, L.tau);
-      k_extract_r<<<gb, 256, 0, s>>>(L.W, d, static_cast<int>(n), L.Rrow, L.status);
-      k_trtri<<<gemv_blocks(n), 256, 0, s>>>(L.W, d, static_cast<int>(n), L.Rinv, L.RinvT);
+        launch(k_qr_step, static_cast<unsigned>(n - k - 1), kQrThreads, s, 1, L.W, d,
+               static_cast<int>(n), k, L.tau);
+      k_extract_r<<<gb, 256, 0, s>>>(L.W, d, static_cast<int>(n), L.Rrow, L.rdiag, L.status);
+      launch_trtri(L.W, d, static_cast<int>(n), L.rdiag, L.Rinv, L.RinvT, s);
     };
     const bool repeat = std::memcmp(qk, st.qr_seen, sizeof(qk)) == 0;
     std::memcpy(st.qr_seen, qk, sizeof(qk));
@@ -1369,13 +1443,14 @@ extern "C" int sketch_debug_qr(int64_t d, int64_t n, const double* A, double* R,
   if (d < 1 || n < 1 || d < n || n > 8192 || !A || !R || !Rinv)
     return fail(nullptr, SKETCH_ERR_ARG, "bad arguments");
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  double *W = nullptr, *tau = nullptr, *RT = nullptr;
+  double *W = nullptr, *tau = nullptr, *RT = nullptr, *rdiag = nullptr;
   int* status = nullptr;
   if (cudaMalloc(&W, sizeof(double) * d * n) != cudaSuccess ||
       cudaMalloc(&tau, sizeof(double) * n) != cudaSuccess ||
       cudaMalloc(&RT, sizeof(double) * n * n) != cudaSuccess ||
+      cudaMalloc(&rdiag, sizeof(double) * n) != cudaSuccess ||
       cudaMalloc(&status, sizeof(int)) != cudaSuccess) {
-    cudaFree(W); cudaFree(tau); cudaFree(RT); cudaFree(status);
+    cudaFree(W); cudaFree(tau); cudaFree(RT); cudaFree(rdiag); cudaFree(status);
     cudaGetLastError();
     return fail(nullptr, SKETCH_ERR_OOM, "cudaMalloc failed");
   }
@@ -1383,11 +1458,12 @@ extern "C" int sketch_debug_qr(int64_t d, int64_t n, const double* A, double* R,
   cudaMemsetAsync(status, 0, sizeof(int), s);
   k_qr_first<<<1, kQrThreads, 0, s>>>(W, d, tau);
   for (int k = 0; k + 1 < n; ++k)
-    k_qr_step<<<static_cast<unsigned>(n - k - 1), kQrThreads, 0, s>>>(W, d, static_cast<int>(n), k, tau);
+    launch(k_qr_step, static_cast<unsigned>(n - k - 1), kQrThreads, s, 1, W, d,
+           static_cast<int>(n), k, tau);
   const unsigned gb = static_cast<unsigned>(std::max<int64_t>(1, 16LL * num_sms()));
-  k_extract_r<<<gb, 256, 0, s>>>(W, d, static_cast<int>(n), R, status);
-  k_trtri<<<gemv_blocks(n), 256, 0, s>>>(W, d, static_cast<int>(n), Rinv, RT);
+  k_extract_r<<<gb, 256, 0, s>>>(W, d, static_cast<int>(n), R, rdiag, status);
+  launch_trtri(W, d, static_cast<int>(n), rdiag, Rinv, RT, s);
   cudaError_t e = cudaStreamSynchronize(s);
-  cudaFree(W); cudaFree(tau); cudaFree(RT); cudaFree(status);
+  cudaFree(W); cudaFree(tau); cudaFree(RT); cudaFree(rdiag); cudaFree(status);
   return e == cudaSuccess ? SKETCH_OK : cuda_fail(nullptr, e, "debug_qr");
 }
