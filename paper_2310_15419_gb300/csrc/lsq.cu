@@ -141,112 +141,213 @@ __global__ void k_to_double(int64_t total, const float* __restrict__ a,
 
 constexpr int kQrThreads = 128;
 constexpr int kQrRegs = 8;  // column entries a thread keeps in registers
+constexpr int kQrCols = 4;  // columns an update block carries at once
 
-// Column c of W (column-major, leading dimension d): apply reflector k
-// (H = I - tau v v^T, v = column k below the diagonal with v_k = 1; k < 0:
-// none) and, when c == k + 1, form the reflector of column c (rows c..d-1)
-// in place: R(c,c) = beta = -sign(alpha) ||x||, v below the diagonal, tau[c]
-// (H = I, tau = 0, when the part below the diagonal is zero).  A thread keeps
-// rows r0 + tid + kQrThreads q, q < kQrRegs, in registers across the dot
-// product, the update with the squared norm, and the scaling; rows past
-// those are reloaded.  The scalar chain (sqrt, two divides) runs in thread 0.
-__device__ void qr_column(double* __restrict__ W, int64_t d, int k, int c,
-                          double* __restrict__ tau, double* red, double* bc) {
+// Householder QR of W (d x n, column-major) with LAPACK's reflectors
+// H_k = I - tau_k v_k v_k^T, v_k(k) = 1, R(k,k) = beta = -sign(alpha) ||x||
+// (H = I, tau = 0, when the part below the diagonal is already zero).  Below
+// the diagonal column k keeps v_k unscaled: v_k(r) = vs[k] * W(r,k), r > k,
+// with vs[k] = 1 / (alpha - beta); consumers fold vs[k] into their scalars.
+//
+// Step k is one launch of min(n - k - 1, #SMs) blocks, so each block has an
+// SM to itself.  Block 0 carries the critical path: it applies H_k to
+// column k + 1 and forms reflector k + 1 (a dot product, an update fused
+// with the squared norm, two block sums and one sqrt / two divides in
+// thread 0).  The other blocks apply H_k to columns k + 2 .. n - 1, up to
+// kQrCols at a time, one warp reducing each column's dot product.
+
+// Column c = k + 1: apply H_k (k >= 0), then form reflector c.
+__device__ void qr_form(double* __restrict__ W, int64_t d, int k, double* __restrict__ tau,
+                        double* __restrict__ vs, double* red, double* bc) {
   const int tid = threadIdx.x;
+  const int c = k + 1;
   double* y = W + static_cast<int64_t>(c) * d;
-  const bool form = c == k + 1;
-  const int64_t r0 = k + 1;
-  const double t = k >= 0 ? tau[k] : 0.0;
-  const double* v = W + static_cast<int64_t>(k >= 0 ? k : 0) * d;
+  const int64_t r0 = c;  // rows r0.. are touched (row k separately)
   const int64_t rtail = r0 + static_cast<int64_t>(kQrThreads) * kQrRegs;
-  double yr[kQrRegs], vr[kQrRegs];
+  const double t = k >= 0 ? tau[k] : 0.0;
+  const double* w = W + static_cast<int64_t>(k >= 0 ? k : 0) * d;
+  double yr[kQrRegs], wr[kQrRegs];
 #pragma unroll
   for (int q = 0; q < kQrRegs; ++q) {
     const int64_t r = r0 + tid + kQrThreads * q;
     yr[q] = r < d ? y[r] : 0.0;
-    vr[q] = (t != 0.0 && r < d) ? v[r] : 0.0;
+    wr[q] = (t != 0.0 && r < d) ? w[r] : 0.0;
   }
+  double nrm = 0.0;
   if (t != 0.0) {
+    const double sk = vs[k];
     double s0 = 0.0, s1 = 0.0;
 #pragma unroll
     for (int q = 0; q < kQrRegs; q += 2) {
-      s0 = fma(vr[q], yr[q], s0);
-      s1 = fma(vr[q + 1], yr[q + 1], s1);
+      s0 = fma(wr[q], yr[q], s0);
+      s1 = fma(wr[q + 1], yr[q + 1], s1);
     }
-    for (int64_t r = rtail + tid; r < d; r += kQrThreads) s0 = fma(v[r], y[r], s0);
+    for (int64_t r = rtail + tid; r < d; r += kQrThreads) s0 = fma(w[r], y[r], s0);
     const double sum = block_sum0<kQrThreads>(s0 + s1, red);
     if (tid == 0) {
       const double yk = y[k];
-      const double f = t * (sum + yk);
+      const double f = t * fma(sk, sum, yk);
       y[k] = yk - f;
-      bc[0] = f;
+      bc[0] = f * sk;
     }
     __syncthreads();
-    const double f = bc[0];
+    const double g = bc[0];
 #pragma unroll
-    for (int q = 0; q < kQrRegs; ++q) yr[q] = fma(-f, vr[q], yr[q]);
-    for (int64_t r = rtail + tid; r < d; r += kQrThreads) y[r] = fma(-f, v[r], y[r]);
-    if (!form) {
-#pragma unroll
-      for (int q = 0; q < kQrRegs; ++q) {
-        const int64_t r = r0 + tid + kQrThreads * q;
-        if (r < d) y[r] = yr[q];
-      }
-      return;
+    for (int q = 0; q < kQrRegs; ++q) {
+      const int64_t r = r0 + tid + kQrThreads * q;
+      yr[q] = fma(-g, wr[q], yr[q]);
+      if (r > c) nrm = fma(yr[q], yr[q], nrm);
     }
-  }
-  if (!form) return;
-  // reflector of column c: alpha = row c (thread 0, q = 0), sigma = rows > c
-  double nrm = 0.0;
+    for (int64_t r = rtail + tid; r < d; r += kQrThreads) {
+      const double v = fma(-g, w[r], y[r]);
+      y[r] = v;
+      nrm = fma(v, v, nrm);
+    }
+  } else {
 #pragma unroll
-  for (int q = 0; q < kQrRegs; ++q) {
-    const int64_t r = r0 + tid + kQrThreads * q;
-    if (r > c) nrm = fma(yr[q], yr[q], nrm);
+    for (int q = 0; q < kQrRegs; ++q) {
+      const int64_t r = r0 + tid + kQrThreads * q;
+      if (r > c) nrm = fma(yr[q], yr[q], nrm);
+    }
+    for (int64_t r = rtail + tid; r < d; r += kQrThreads) nrm = fma(y[r], y[r], nrm);
   }
-  for (int64_t r = rtail + tid; r < d; r += kQrThreads) nrm = fma(y[r], y[r], nrm);
   const double sigma = block_sum0<kQrThreads>(nrm, red);
   if (tid == 0) {
     if (sigma == 0.0) {
       tau[c] = 0.0;
-      bc[1] = 1.0;
+      vs[c] = 1.0;
     } else {
-      const double alpha = yr[0];
+      const double alpha = yr[0];  // row c
       const double norm = sqrt(fma(alpha, alpha, sigma));
       const double beta = alpha >= 0.0 ? -norm : norm;
-      bc[1] = 1.0 / (alpha - beta);
+      vs[c] = 1.0 / (alpha - beta);
       tau[c] = (beta - alpha) / beta;
       yr[0] = beta;
     }
   }
-  __syncthreads();
-  const double scale = bc[1];
+  if (t != 0.0 || tid == 0) {
 #pragma unroll
-  for (int q = 0; q < kQrRegs; ++q) {
-    const int64_t r = r0 + tid + kQrThreads * q;
-    if (r < d) y[r] = r > c ? yr[q] * scale : yr[q];
+    for (int q = 0; q < kQrRegs; ++q) {
+      const int64_t r = r0 + tid + kQrThreads * q;
+      if (r < d) y[r] = yr[q];
+    }
   }
-  for (int64_t r = rtail + tid; r < d; r += kQrThreads) y[r] *= scale;
+}
+
+// Apply H_k to up to kQrCols columns cols[0..nc) (rows k..d-1).
+__device__ void qr_apply(double* __restrict__ W, int64_t d, int k, const int* cols, int nc,
+                         const double* __restrict__ wr, double t, double sk, double* red,
+                         double* bc) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t r0 = k + 1;
+  const int64_t rtail = r0 + static_cast<int64_t>(kQrThreads) * kQrRegs;
+  const double* w = W + static_cast<int64_t>(k) * d;
+  double yr[kQrCols][kQrRegs];
+#pragma unroll
+  for (int j = 0; j < kQrCols; ++j) {
+    const double* y = W + static_cast<int64_t>(j < nc ? cols[j] : cols[0]) * d;
+#pragma unroll
+    for (int q = 0; q < kQrRegs; ++q) {
+      const int64_t r = r0 + tid + kQrThreads * q;
+      yr[j][q] = (j < nc && r < d) ? y[r] : 0.0;
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < kQrCols; ++j) {
+    double s0 = 0.0, s1 = 0.0;
+#pragma unroll
+    for (int q = 0; q < kQrRegs; q += 2) {
+      s0 = fma(wr[q], yr[j][q], s0);
+      s1 = fma(wr[q + 1], yr[j][q + 1], s1);
+    }
+    if (j < nc) {
+      const double* y = W + static_cast<int64_t>(cols[j]) * d;
+      for (int64_t r = rtail + tid; r < d; r += kQrThreads) s0 = fma(w[r], y[r], s0);
+    }
+    red[j * kQrThreads + tid] = s0 + s1;
+  }
+  __syncthreads();
+  // warp j sums column j in a fixed order
+  if (warp < nc) {
+    double a0 = 0.0, a1 = 0.0;
+#pragma unroll
+    for (int q = 0; q < kQrThreads / 32; q += 2) {
+      a0 += red[warp * kQrThreads + lane + 32 * q];
+      a1 += red[warp * kQrThreads + lane + 32 * (q + 1)];
+    }
+    const double sum = warp_sum(a0 + a1);
+    if (lane == 0) {
+      double* y = W + static_cast<int64_t>(cols[warp]) * d;
+      const double yk = y[k];
+      const double f = t * fma(sk, sum, yk);
+      y[k] = yk - f;
+      bc[warp] = f * sk;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < kQrCols; ++j) {
+    if (j < nc) {
+      const double g = bc[j];
+      double* y = W + static_cast<int64_t>(cols[j]) * d;
+#pragma unroll
+      for (int q = 0; q < kQrRegs; ++q) {
+        const int64_t r = r0 + tid + kQrThreads * q;
+        if (r < d) y[r] = fma(-g, wr[q], yr[j][q]);
+      }
+      for (int64_t r = rtail + tid; r < d; r += kQrThreads) y[r] = fma(-g, w[r], y[r]);
+    }
+  }
+  __syncthreads();  // red and bc are reused by the next group of columns
 }
 
 __global__ void __launch_bounds__(kQrThreads)
-    k_qr_first(double* W, int64_t d, double* tau) {
+    k_qr_first(double* W, int64_t d, double* tau, double* vs) {
   __shared__ double red[kQrThreads];
-  __shared__ double bc[2];
-  qr_column(W, d, -1, 0, tau, red, bc);
+  __shared__ double bc[kQrCols];
+  qr_form(W, d, -1, tau, vs, red, bc);
 }
 
-// Apply reflector k to columns k+1..n-1 (one block per column); the block of
-// column k+1 then forms reflector k+1.  Launched with programmatic stream
-// serialization: every read depends on the previous step.
+// Step k (see above).  Launched with programmatic stream serialization:
+// every read depends on the previous step.
 __global__ void __launch_bounds__(kQrThreads)
-    k_qr_step(double* W, int64_t d, int n, int k, double* tau) {
-  __shared__ double red[kQrThreads];
-  __shared__ double bc[2];
+    k_qr_step(double* W, int64_t d, int n, int k, double* tau, double* vs) {
+  __shared__ double red[kQrThreads * kQrCols];
+  __shared__ double bc[kQrCols];
   pdl_wait();
   pdl_launch();
-  const int c = k + 1 + blockIdx.x;
-  if (c >= n) return;
-  qr_column(W, d, k, c, tau, red, bc);
+  if (blockIdx.x == 0) {
+    qr_form(W, d, k, tau, vs, red, bc);
+    return;
+  }
+  const double t = tau[k];
+  if (t == 0.0) return;
+  const double sk = vs[k];
+  const double* w = W + static_cast<int64_t>(k) * d;
+  double wr[kQrRegs];
+#pragma unroll
+  for (int q = 0; q < kQrRegs; ++q) {
+    const int64_t r = k + 1 + threadIdx.x + kQrThreads * q;
+    wr[q] = r < d ? w[r] : 0.0;
+  }
+  const int nb = gridDim.x - 1;
+  for (int c0 = k + 2 + static_cast<int>(blockIdx.x) - 1; c0 < n; c0 += nb * kQrCols) {
+    int cols[kQrCols];
+    int nc = 0;
+#pragma unroll
+    for (int j = 0; j < kQrCols; ++j) {
+      const int c = c0 + nb * j;
+      cols[j] = c < n ? c : c0;
+      nc += c < n;
+    }
+    qr_apply(W, d, k, cols, nc, wr, t, sk, red, bc);
+  }
+}
+
+// Blocks of step k: one for column k + 1, the rest for columns k + 2 ..
+unsigned qr_step_blocks(int64_t n, int k) {
+  return static_cast<unsigned>(
+      1 + std::min<int64_t>(std::max<int64_t>(n - k - 2, 0), num_sms() - 1));
 }
 
 // Rrow = R (upper n x n of W) row-major, rdiag = 1 / diag(R); flags a zero
@@ -1008,7 +1109,7 @@ namespace {
 
 struct LsqLayout {
   float* Ahat;
-  double *W, *tau, *Rrow, *rdiag, *Rinv, *RinvT, *t, *t2, *v, *vraw, *w, *y;
+  double *W, *tau, *vs, *Rrow, *rdiag, *Rinv, *RinvT, *t, *t2, *v, *vraw, *w, *y;
   double* u[2];  // u_raw, double buffered by iteration parity
   double *p2, *p4, *py, *pfro, *pres;  // per-block partial sums
   double* r;  // A x - b for the error check (kept apart from LSQR's u)
@@ -1046,6 +1147,7 @@ LsqLayout layout(void* base, int64_t m, int64_t n, int64_t d, int64_t nnz) {
   L.Ahat = reinterpret_cast<float*>(take(sizeof(float) * d * n));
   L.W = reinterpret_cast<double*>(take(sizeof(double) * d * n));
   L.tau = reinterpret_cast<double*>(take(sizeof(double) * n));
+  L.vs = reinterpret_cast<double*>(take(sizeof(double) * n));
   L.Rrow = reinterpret_cast<double*>(take(sizeof(double) * n * n));
   L.rdiag = reinterpret_cast<double*>(take(sizeof(double) * n));
   L.Rinv = reinterpret_cast<double*>(take(sizeof(double) * n * n));
@@ -1257,10 +1359,10 @@ extern "C" int sketch_lsq_solve(sketch_t h, const sketch_csc* A,
     const int64_t qk[3] = {d, n, static_cast<int64_t>(reinterpret_cast<intptr_t>(st.ws))};
     auto enqueue_qr = [&]() {
       k_to_double<<<gb, 256, 0, s>>>(dn, L.Ahat, L.W);
-      k_qr_first<<<1, kQrThreads, 0, s>>>(L.W, d, L.tau);
+      k_qr_first<<<1, kQrThreads, 0, s>>>(L.W, d, L.tau, L.vs);
       for (int k = 0; k + 1 < n; ++k)
-        launch(k_qr_step, static_cast<unsigned>(n - k - 1), kQrThreads, s, 1, L.W, d,
-               static_cast<int>(n), k, L.tau);
+        launch(k_qr_step, qr_step_blocks(n, k), kQrThreads, s, 1, L.W, d,
+               static_cast<int>(n), k, L.tau, L.vs);
       k_extract_r<<<gb, 256, 0, s>>>(L.W, d, static_cast<int>(n), L.Rrow, L.rdiag, L.status);
       launch_trtri(L.W, d, static_cast<int>(n), L.rdiag, L.Rinv, L.RinvT, s);
     };
@@ -1446,7 +1548,7 @@ extern "C" int sketch_debug_qr(int64_t d, int64_t n, const double* A, double* R,
   double *W = nullptr, *tau = nullptr, *RT = nullptr, *rdiag = nullptr;
   int* status = nullptr;
   if (cudaMalloc(&W, sizeof(double) * d * n) != cudaSuccess ||
-      cudaMalloc(&tau, sizeof(double) * n) != cudaSuccess ||
+      cudaMalloc(&tau, sizeof(double) * 2 * n) != cudaSuccess ||
       cudaMalloc(&RT, sizeof(double) * n * n) != cudaSuccess ||
       cudaMalloc(&rdiag, sizeof(double) * n) != cudaSuccess ||
       cudaMalloc(&status, sizeof(int)) != cudaSuccess) {
@@ -1456,10 +1558,11 @@ extern "C" int sketch_debug_qr(int64_t d, int64_t n, const double* A, double* R,
   }
   cudaMemcpyAsync(W, A, sizeof(double) * d * n, cudaMemcpyDeviceToDevice, s);
   cudaMemsetAsync(status, 0, sizeof(int), s);
-  k_qr_first<<<1, kQrThreads, 0, s>>>(W, d, tau);
+  double* vs = tau + n;
+  k_qr_first<<<1, kQrThreads, 0, s>>>(W, d, tau, vs);
   for (int k = 0; k + 1 < n; ++k)
-    launch(k_qr_step, static_cast<unsigned>(n - k - 1), kQrThreads, s, 1, W, d,
-           static_cast<int>(n), k, tau);
+    launch(k_qr_step, qr_step_blocks(n, k), kQrThreads, s, 1, W, d, static_cast<int>(n), k,
+           tau, vs);
   const unsigned gb = static_cast<unsigned>(std::max<int64_t>(1, 16LL * num_sms()));
   k_extract_r<<<gb, 256, 0, s>>>(W, d, static_cast<int>(n), R, rdiag, status);
   launch_trtri(W, d, static_cast<int>(n), rdiag, Rinv, RT, s);
