@@ -31,6 +31,10 @@ struct sketch_s {
   bool autotune = true;
   int64_t launches = 0;          // kernels launched so far
   bool capturing = false;        // the caller's stream is being captured
+  // least-squares kernels start while their predecessor finishes
+  // (programmatic dependent launch); off for handles whose solves share the
+  // GPU with other streams, where early-started blocks would hold SMs
+  bool dependent_launch = true;
   sk::LsqState* lsq = nullptr;   // least-squares workspace (lazy)
 };
 

@@ -1219,7 +1219,7 @@ void launch(void (*kern)(KArgs...), unsigned grid, unsigned block, cudaStream_t 
 struct ColsArgs {
   int lsqr = 0;
   const double *p2 = nullptr, *pz = nullptr, *py = nullptr;
-  int np2 = 0, npy = 0, par = 0, init = 0;
+  int np2 = 0, npy = 0, par = 0, init = 0, pdl = 0;
 };
 
 template <typename VT>
@@ -1233,7 +1233,7 @@ void launch_cols(const CscView& A, const double* u, double* out, Scalars* sc,
   const unsigned g = static_cast<unsigned>(A.n + (c.lsqr ? 1 : 0));
   const VT* vals = static_cast<const VT*>(A.values);
 #define SK_COLS(WW)                                                                     \
-  launch(k_cols<VT, WW>, g, 32 * WW, s, c.lsqr, A.n, A.colptr, A.rowidx, vals, u, out, sc, \
+  launch(k_cols<VT, WW>, g, 32 * WW, s, c.pdl, A.n, A.colptr, A.rowidx, vals, u, out, sc, \
          c.lsqr, c.p2, c.pz, c.np2, c.py, c.npy, c.par, c.init)
   switch (W) {
     case 1: SK_COLS(1); break;
@@ -1261,10 +1261,10 @@ unsigned gemv_blocks(int64_t n) {
 // the step reads slot par and writes slot par ^ 1.
 void lsqr_kernels(const LsqLayout& L, const CscView& A, const CsrView& csr,
                   const int32_t* mnz, const double* b, int32_t m, int par, int init,
-                  cudaStream_t s) {
+                  int pdl, cudaStream_t s) {
   const int n = A.n;
   const int g2 = rows_blocks(m), gt = tri_blocks(n);
-  launch(k_lsqr_rows, g2, kRows, s, 1, m, mnz, csr.rowptr, csr.ccol, csr.cval, L.t, L.u[par],
+  launch(k_lsqr_rows, g2, kRows, s, pdl, m, mnz, csr.rowptr, csr.ccol, csr.cval, L.t, L.u[par],
          L.u[par ^ 1], b, L.perm, L.p2, L.pz, L.sc, par, init);
   ColsArgs c;
   c.lsqr = 1;
@@ -1275,10 +1275,11 @@ void lsqr_kernels(const LsqLayout& L, const CscView& A, const CsrView& csr,
   c.npy = gt;
   c.par = par;
   c.init = init;
+  c.pdl = pdl;
   cols(A, L.u[par ^ 1], L.t2, L.sc, c, s);
-  launch(k_lsqr_vraw, gt, 32 * kTriWarps, s, 1, n, L.RinvT, L.t2, L.v, L.vraw, L.p4, L.sc,
+  launch(k_lsqr_vraw, gt, 32 * kTriWarps, s, pdl, n, L.RinvT, L.t2, L.v, L.vraw, L.p4, L.sc,
          init);
-  launch(k_lsqr_step, gt, 32 * kTriWarps, s, 1, n, L.Rinv, L.vraw, L.v, L.w, L.y, L.t, L.p4,
+  launch(k_lsqr_step, gt, 32 * kTriWarps, s, pdl, n, L.Rinv, L.vraw, L.v, L.w, L.y, L.t, L.p4,
          gt, L.py, L.sc, par, init);
 }
 
@@ -1350,6 +1351,7 @@ extern "C" int sketch_lsq_solve(sketch_t h, const sketch_csc* A,
 
   // ---- 2. FP64 Householder QR of the sketch, 3. R^{-1} ----------------------
   cudaMemsetAsync(L.status, 0, sizeof(int), s);
+  const int pdl = h->dependent_launch ? 1 : 0;
   const int64_t dn = d * n;
   const unsigned gb = static_cast<unsigned>(std::max<int64_t>(1, 16LL * num_sms()));
   {
@@ -1361,7 +1363,7 @@ extern "C" int sketch_lsq_solve(sketch_t h, const sketch_csc* A,
       k_to_double<<<gb, 256, 0, s>>>(dn, L.Ahat, L.W);
       k_qr_first<<<1, kQrThreads, 0, s>>>(L.W, d, L.tau, L.vs);
       for (int k = 0; k + 1 < n; ++k)
-        launch(k_qr_step, qr_step_blocks(n, k), kQrThreads, s, 1, L.W, d,
+        launch(k_qr_step, qr_step_blocks(n, k), kQrThreads, s, pdl, L.W, d,
                static_cast<int>(n), k, L.tau, L.vs);
       k_extract_r<<<gb, 256, 0, s>>>(L.W, d, static_cast<int>(n), L.Rrow, L.rdiag, L.status);
       launch_trtri(L.W, d, static_cast<int>(n), L.rdiag, L.Rinv, L.RinvT, s);
@@ -1431,7 +1433,7 @@ extern "C" int sketch_lsq_solve(sketch_t h, const sketch_csc* A,
   *st.host = init;
   cudaMemcpyAsync(L.sc, st.host, sizeof(Scalars), cudaMemcpyHostToDevice, s);
   // u = b, beta = ||b||, v = R^{-T} A^T u / (beta alpha), w = v, y = 0
-  lsqr_kernels(L, csc, csr, mnz, b, static_cast<int32_t>(m), 1, 1, s);
+  lsqr_kernels(L, csc, csr, mnz, b, static_cast<int32_t>(m), 1, 1, pdl, s);
   h->launches += 4;
   // iterations: a cached graph of kIterPerGraph iterations, replayed until
   // the device sets `done`
@@ -1447,8 +1449,8 @@ extern "C" int sketch_lsq_solve(sketch_t h, const sketch_csc* A,
     if (e != cudaSuccess) return cuda_fail(h, e, "begin capture");
     static_assert(kIterPerGraph % 2 == 0, "a graph starts and ends on slot 0");
     for (int it = 0; it < kIterPerGraph; ++it)
-      lsqr_kernels(L, csc, csr, mnz, nullptr, static_cast<int32_t>(m), it & 1, 0, s);
-    launch(k_lsqr_test, 1, 32, s, 1, L.py, tri_blocks(n), L.sc, 0);
+      lsqr_kernels(L, csc, csr, mnz, nullptr, static_cast<int32_t>(m), it & 1, 0, pdl, s);
+    launch(k_lsqr_test, 1, 32, s, pdl, L.py, tri_blocks(n), L.sc, 0);
     e = cudaStreamEndCapture(s, &g);
     if (e != cudaSuccess) return cuda_fail(h, e, "end capture");
     e = cudaGraphInstantiate(&st.graph, g, 0);

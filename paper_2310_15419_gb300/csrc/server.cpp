@@ -75,7 +75,10 @@ void worker(sketch_server_s* srv) {
   cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
   sketch_t h = nullptr;
   sketch_create(1, 1, 1, srv->dist, srv->seed, &h);
-  if (h) sketch_set_autotune(h, 0);
+  if (h) {
+    sketch_set_autotune(h, 0);
+    h->dependent_launch = false;  // requests overlap on separate streams
+  }
   for (;;) {
     Request* r = nullptr;
     {
