@@ -842,24 +842,36 @@ __global__ void __launch_bounds__(kTileWarps * 32, 1)
   for (int q = 0; q < NQ; ++q) acc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
   unsigned long long generated = 0;
 
-  for (int32_t p = pa; p < pb; ++p) {
-    const int32_t j0 = p * R;
-    const int32_t rows = min(R, m - j0);
-    // ---- this warp's column offsets and nonzeros (one contiguous range),
-    //      loaded before the S tile is generated so the loads overlap it
-    int32_t offv[OFFR];
+  // this warp's column offsets of panel p (CPW + 1 values over OFFR
+  // registers); the next panel's are loaded while the current one is swept
+  int32_t offv[OFFR];
+  auto load_offsets = [&](int32_t p) {
     const int32_t* offp = off + static_cast<int64_t>(p) * (n + 1) + kw0;
 #pragma unroll
     for (int u = 0; u < OFFR; ++u) {
       const int c = lane + 32 * u;
-      offv[u] = (ncol > 0 && c <= ncol) ? offp[c] : 0;
+      offv[u] = (ncol > 0 && c <= ncol && p < pb) ? offp[c] : 0;
     }
+  };
+  load_offsets(pa);
+
+  for (int32_t p = pa; p < pb; ++p) {
+    const int32_t j0 = p * R;
+    const int32_t rows = min(R, m - j0);
+    // ---- this warp's nonzeros (one contiguous range) copied global ->
+    //      shared asynchronously; the copies land while the S tile is
+    //      generated
     int32_t e_lo = 0;
     if (ncol > 0) {
       e_lo = __shfl_sync(0xffffffffu, offv[0], 0);
       const int32_t e_hi = __shfl_sync(0xffffffffu, offv[ncol >> 5], ncol & 31);
       const int32_t cnt = min(e_hi - e_lo, kTileWarpBuf);
-      for (int32_t t = lane; t < cnt; t += 32) ent[t] = packed[e_lo + t];
+      for (int32_t t = lane; t < cnt; t += 32) {
+        const unsigned dst = static_cast<unsigned>(__cvta_generic_to_shared(ent + t));
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst),
+                     "l"(packed + e_lo + t)
+                     : "memory");
+      }
 #pragma unroll
       for (int u = 0; u < OFFR; ++u) {
         const int c = lane + 32 * u;
@@ -885,7 +897,9 @@ __global__ void __launch_bounds__(kTileWarps * 32, 1)
       *reinterpret_cast<float4*>(&S_tile[jl * 32 + 4 * q]) = v;
     }
     generated += static_cast<unsigned long long>(rows) * rows_valid;
+    asm volatile("cp.async.wait_all;" ::: "memory");
     __syncthreads();
+    load_offsets(p + 1);  // used by the next panel; lands during the sweep
     // ---- sweep: four columns per step, one per group of eight lanes ------
     const int32_t buf_end = e_lo + kTileWarpBuf;
 #pragma unroll
