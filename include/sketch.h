@@ -304,6 +304,14 @@ int sketch_server_destroy(sketch_server_t srv);
 int sketch_debug_philox(const uint32_t* ctr, uint64_t seed, uint32_t* out,
                         int64_t count, sketch_stream_t stream);
 
+/* The N(0,1) transform alone: (out[2t], out[2t+1]) = Box-Muller of the word
+ * pair (words[2t] radius word, words[2t+1] angle word): u1 = ((w >> 8) + 1)
+ * 2^-24, u2 = (w >> 8) 2^-24, r = sqrt(-2 ln u1), (r cos 2 pi u2,
+ * r sin 2 pi u2) (Sec. 4.2).  words and out are device pointers.
+ * Asynchronous. */
+int sketch_debug_normal_pair(const uint32_t* words, float* out, int64_t count,
+                             sketch_stream_t stream);
+
 /* out[t] = S(i[t], j[t]) (FP32) for distribution `dist`, key `seed`, counter
  * word 2 = `stream_id`.  i, j, out are device pointers.  Asynchronous. */
 int sketch_debug_S(int32_t dist, uint64_t seed, uint32_t stream_id,

@@ -102,6 +102,7 @@ SIGNATURES = [
                                 ctypes.POINTER(sketch_lsq_info), _VP]),
     ("sketch_debug_philox", _I32, [_VP, _U64, _VP, _I64, _VP]),
     ("sketch_debug_S", _I32, [_I32, _U64, _U32, _VP, _VP, _VP, _I64, _VP]),
+    ("sketch_debug_normal_pair", _I32, [_VP, _VP, _I64, _VP]),
     ("sketch_set_counting", _I32, [_VP, _I32]),
     ("sketch_generated_entries", _I64, [_VP, _VP]),
     ("sketch_launch_count", _I64, [_VP]),
@@ -415,6 +416,18 @@ def debug_philox(ctr, seed, stream=None):
                                       ctypes.c_uint64(seed),
                                       ctypes.c_void_p(out.data_ptr()), count,
                                       _stream_ptr(stream)))
+    return out
+
+
+def debug_normal_pair(words, stream=None):
+    """words: int tensor (count, 2) of uint32 values on the GPU (as int32
+    bits), (radius word, angle word) per row; returns (count, 2) float32."""
+    import torch
+    count = words.shape[0]
+    out = torch.empty((count, 2), dtype=torch.float32, device=words.device)
+    _check(load().sketch_debug_normal_pair(ctypes.c_void_p(words.data_ptr()),
+                                           ctypes.c_void_p(out.data_ptr()), count,
+                                           _stream_ptr(stream)))
     return out
 
 

@@ -100,6 +100,8 @@ cudaError_t launch_tile(const TileArgs& a, void* ws, cudaStream_t s,
 cudaError_t launch_validate(int32_t m, int32_t n, int64_t nnz,
                             const int32_t* colptr, const int32_t* rowidx,
                             int* status, cudaStream_t s);
+cudaError_t launch_debug_normal_pair(const uint32_t* words, float* out, int64_t count,
+                                     cudaStream_t s);
 cudaError_t launch_debug_philox(const uint32_t* ctr, uint32_t k0, uint32_t k1,
                                 uint32_t* out, int64_t count, cudaStream_t s);
 cudaError_t launch_debug_S(int dist, uint32_t k0, uint32_t k1,

@@ -616,6 +616,15 @@ int sketch_debug_philox(const uint32_t* ctr, uint64_t seed, uint32_t* out,
   return e == cudaSuccess ? SKETCH_OK : cuda_fail(nullptr, e, "debug_philox");
 }
 
+int sketch_debug_normal_pair(const uint32_t* words, float* out, int64_t count,
+                             sketch_stream_t stream) {
+  if (count < 0 || (count > 0 && (!words || !out)))
+    return fail(nullptr, SKETCH_ERR_ARG, "bad arguments");
+  cudaError_t e = launch_debug_normal_pair(words, out, count,
+                                           reinterpret_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? SKETCH_OK : cuda_fail(nullptr, e, "debug_normal_pair");
+}
+
 int sketch_debug_S(int32_t dist, uint64_t seed, uint32_t stream_id,
                    const int64_t* i, const int64_t* j, float* out,
                    int64_t count, sketch_stream_t stream) {

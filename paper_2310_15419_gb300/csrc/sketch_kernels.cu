@@ -1140,6 +1140,24 @@ cudaError_t launch_debug_philox(const uint32_t* ctr, uint32_t k0, uint32_t k1,
   return cudaGetLastError();
 }
 
+__global__ void k_debug_normal_pair(const uint32_t* __restrict__ words,
+                                    float* __restrict__ out, int64_t count) {
+  for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+       t < count; t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const float2 z = normal_pair(words[2 * t], words[2 * t + 1]);
+    out[2 * t] = z.x;
+    out[2 * t + 1] = z.y;
+  }
+}
+
+cudaError_t launch_debug_normal_pair(const uint32_t* words, float* out, int64_t count,
+                                     cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  const int64_t blocks = std::min<int64_t>((count + 255) / 256, 4096);
+  k_debug_normal_pair<<<static_cast<unsigned>(blocks), 256, 0, s>>>(words, out, count);
+  return cudaGetLastError();
+}
+
 __global__ void k_debug_S(int dist, uint32_t k0, uint32_t k1,
                           uint32_t stream_id, const int64_t* __restrict__ ii,
                           const int64_t* __restrict__ jj,

@@ -88,6 +88,29 @@ def test_S_entries_match_oracle(dist):
         assert np.array_equal(got.astype(np.float64), ref)
 
 
+def test_normal_transform_matches_oracle_at_the_extremes():
+    """The N(0,1) transform on chosen word pairs: radius words at both ends
+    of u1 (u1 -> 1 gives a tiny r, u1 = 2^-24 the largest), every octant
+    boundary of the angle, and random pairs; each output within 4e-7
+    max(1, |z|) of the oracle's FP64 Box-Muller (Sec. 4.2)."""
+    rng = np.random.default_rng(11)
+    top = np.arange(2**24 - 4096, 2**24, dtype=np.uint64)        # u1 -> 1
+    low = np.arange(0, 4096, dtype=np.uint64)                     # u1 -> 0
+    ang = np.array([(o * 2**21 + d) % 2**24 for o in range(8) for d in (-2, -1, 0, 1, 2)])
+    rad_words = np.concatenate([top, low, np.repeat(rng.integers(0, 2**24, 8), ang.size),
+                                rng.integers(0, 2**24, 100_000)]).astype(np.uint64)
+    ang_words = np.concatenate([np.full(top.size, 12345), np.full(low.size, 2**22 + 7),
+                                np.tile(ang, 8), rng.integers(0, 2**24, 100_000)]).astype(np.uint64)
+    low_bits = rng.integers(0, 256, size=(rad_words.size, 2)).astype(np.uint64)
+    w = np.stack([(rad_words << 8) | low_bits[:, 0], (ang_words << 8) | low_bits[:, 1]], axis=1)
+    got = capi.debug_normal_pair(torch.from_numpy(w.astype(np.uint32).view(np.int32)).cuda())
+    got = got.cpu().numpy().astype(np.float64)
+    ref = np.array([[oracle.normal_from_words(int(a), int(b), 0),
+                     oracle.normal_from_words(int(a), int(b), 1)] for a, b in w])
+    err = np.abs(got - ref) / np.maximum(1.0, np.abs(ref))
+    assert err.max() <= 4e-7, (err.max(), w[np.unravel_index(err.argmax(), err.shape)[0]])
+
+
 # ------------------------------------------------------- exactness / tiling
 @pytest.mark.parametrize("plan", REGEN_PLANS + PANEL_PLANS + TILE_PLANS)
 def test_pm1_integer_bit_exact_every_plan(plan):
