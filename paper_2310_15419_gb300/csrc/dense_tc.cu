@@ -10,8 +10,9 @@
 //     rounding happens -- only the FP32 accumulation rounds;
 //   * S_D's signs come straight from Philox bits: one block per (128 rows of
 //     S, dense row), expanded to BF16 +-1 in registers (no S in memory).
-// The sparse kernels skip the dense rows (their value reads as 0), so
-// A_hat = S A_sparse + S_D A_D with the MMA adding into A_hat afterwards.
+// The sparse kernels run on the rest of A (a compacted CSC without the
+// panel's rows), so A_hat = S A_rest + S_D A_D with the MMA adding into A_hat
+// afterwards.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -195,20 +196,16 @@ size_t al256(size_t b) { return (b + 255) / 256 * 256; }
 
 }  // namespace
 
-size_t dense_workspace_bytes(int64_t m, int64_t n, int64_t kmax) {
-  const int64_t Kp = (kmax + kBK - 1) / kBK * kBK;
-  return 4 * al256((m + 1) * sizeof(int32_t)) + al256(sizeof(int32_t) * 64) +
-         al256(static_cast<size_t>(n) * 3 * Kp * sizeof(uint16_t)) +
-         al256(static_cast<size_t>(scan_bytes_for(m + 1)));
-}
-
 namespace {
 struct DenseLayout {
   int32_t *cnt, *flag, *pos, *didx, *Kdev;
   uint16_t* A3;
   char* scan_tmp;
+  int32_t *rcnt, *rcolptr, *rrowidx;  // the rest of A (CSC)
+  void* rvalues;
+  size_t bytes;
 };
-DenseLayout dense_layout(void* ws, int64_t m, int64_t n, int64_t kmax) {
+DenseLayout dense_layout(void* ws, int64_t m, int64_t n, int64_t kmax, int64_t nnz) {
   DenseLayout L{};
   char* p = static_cast<char*>(ws);
   auto take = [&](size_t b) {
@@ -223,16 +220,83 @@ DenseLayout dense_layout(void* ws, int64_t m, int64_t n, int64_t kmax) {
   L.Kdev = reinterpret_cast<int32_t*>(take(sizeof(int32_t) * 64));
   const int64_t Kp = (kmax + kBK - 1) / kBK * kBK;
   L.A3 = reinterpret_cast<uint16_t*>(take(static_cast<size_t>(n) * 3 * Kp * 2));
-  L.scan_tmp = take(static_cast<size_t>(scan_bytes_for(m + 1)));
+  L.scan_tmp = take(static_cast<size_t>(scan_bytes_for(std::max(m, n) + 1)));
+  L.rcnt = reinterpret_cast<int32_t*>(take((n + 1) * sizeof(int32_t)));
+  L.rcolptr = reinterpret_cast<int32_t*>(take((n + 1) * sizeof(int32_t)));
+  L.rrowidx = reinterpret_cast<int32_t*>(take(std::max<int64_t>(1, nnz) * sizeof(int32_t)));
+  L.rvalues = take(std::max<int64_t>(1, nnz) * sizeof(float));
+  L.bytes = static_cast<size_t>(p - static_cast<char*>(ws));
   return L;
+}
+
+// Entries of column k that stay in the sparse part: rows outside the panel
+// (and out-of-range rows, which the sparse kernels then flag).
+__device__ __forceinline__ bool rest_keeps(int32_t j, int32_t m, const int32_t* didx) {
+  return static_cast<uint32_t>(j) >= static_cast<uint32_t>(m) || didx[j] < 0;
+}
+
+// rcnt[k] = entries of column k outside the panel; rcnt[n] = 0.
+__global__ void k_rest_count(int32_t n, int32_t m, const int32_t* __restrict__ colptr,
+                             const int32_t* __restrict__ rowidx,
+                             const int32_t* __restrict__ didx, int32_t* __restrict__ rcnt) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = static_cast<int64_t>(gridDim.x) * (blockDim.x >> 5);
+  for (int64_t k = blockIdx.x * static_cast<int64_t>(blockDim.x >> 5) + (threadIdx.x >> 5);
+       k <= n; k += warps) {
+    int32_t c = 0;
+    if (k < n)
+      for (int32_t e = colptr[k] + lane; e < colptr[k + 1]; e += 32)
+        c += rest_keeps(rowidx[e], m, didx);
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if (lane == 0) rcnt[k] = c;
+  }
+}
+
+// The kept entries of column k, in their order, at rcolptr[k].. (one warp
+// per column, ballot compaction).
+template <typename VT>
+__global__ void k_rest_copy(int32_t n, int32_t m, const int32_t* __restrict__ colptr,
+                            const int32_t* __restrict__ rowidx, const VT* __restrict__ vals,
+                            const int32_t* __restrict__ didx,
+                            const int32_t* __restrict__ rcolptr,
+                            int32_t* __restrict__ rrowidx, VT* __restrict__ rvals) {
+  const int lane = threadIdx.x & 31;
+  const unsigned below = (1u << lane) - 1u;
+  const int64_t warps = static_cast<int64_t>(gridDim.x) * (blockDim.x >> 5);
+  for (int64_t k = blockIdx.x * static_cast<int64_t>(blockDim.x >> 5) + (threadIdx.x >> 5);
+       k < n; k += warps) {
+    int32_t out = rcolptr[k];
+    const int32_t hi = colptr[k + 1];
+    for (int32_t e0 = colptr[k]; e0 < hi; e0 += 32) {
+      const int32_t e = e0 + lane;
+      int32_t j = 0;
+      bool keep = false;
+      if (e < hi) {
+        j = rowidx[e];
+        keep = rest_keeps(j, m, didx);
+      }
+      const unsigned mask = __ballot_sync(0xffffffffu, keep);
+      if (keep) {
+        const int32_t pos = out + __popc(mask & below);
+        rrowidx[pos] = j;
+        rvals[pos] = vals[e];
+      }
+      out += __popc(mask);
+    }
+  }
 }
 }  // namespace
 
+size_t dense_workspace_bytes(int64_t m, int64_t n, int64_t kmax, int64_t nnz) {
+  return dense_layout(nullptr, m, n, kmax, nnz).bytes;
+}
+
 // Phase 1: choose the dense rows (at least tau nonzeros).  Writes didx,
-// rows and K to the workspace; the caller reads K (the panel height).
+// rows and K to the workspace, and the offsets of the rest of A; the caller
+// reads K (the panel height) and rest_colptr[n] (the rest's nonzeros).
 cudaError_t select_dense_rows(const DenseArgs& a, void* ws, DenseView* out, cudaStream_t s,
                               int* launches) {
-  const DenseLayout L = dense_layout(ws, a.m, a.n, a.kmax);
+  const DenseLayout L = dense_layout(ws, a.m, a.n, a.kmax, a.nnz);
   int32_t* rows = L.cnt;  // the counts are dead once the flags exist
   const int sms = num_sms();
   auto grid_for = [&](int64_t work) {
@@ -255,7 +319,18 @@ cudaError_t select_dense_rows(const DenseArgs& a, void* ws, DenseView* out, cuda
   out->Kdev = L.Kdev;
   out->A3 = L.A3;
   out->Kp = 0;
-  return cudaGetLastError();
+  out->rest_colptr = L.rcolptr;
+  out->rest_rowidx = L.rrowidx;
+  out->rest_values = L.rvalues;
+  out->rest_cnt = L.rcnt;
+  out->scan_tmp = L.scan_tmp;
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  // the rest of A: per-column counts and offsets (rest_colptr[n] = its nnz)
+  const int64_t wblocks = std::max<int64_t>(1, std::min<int64_t>((a.n + 8) / 8, 32LL * sms));
+  k_rest_count<<<static_cast<unsigned>(wblocks), 256, 0, s>>>(a.n, a.m, a.colptr, a.rowidx,
+                                                              L.didx, L.rcnt);
+  ++*launches;
+  return scan_i32(L.rcnt, L.rcolptr, a.n + 1, L.scan_tmp, s, launches);
 }
 
 // Phase 2: the panel's BF16 terms for K dense rows (K <= kmax).
@@ -275,6 +350,25 @@ cudaError_t build_dense_panel(const DenseArgs& a, int32_t K, DenseView* v, cudaS
     k_dense_scatter<__nv_bfloat16><<<static_cast<unsigned>(blocks), 256, 0, s>>>(
         a.n, a.m, static_cast<int32_t>(Kp), a.colptr, a.rowidx,
         static_cast<const __nv_bfloat16*>(a.values), v->didx, A3);
+  ++*launches;
+  return cudaGetLastError();
+}
+
+// Phase 3: the rest of A (entries outside the panel's rows) compacted into
+// its own CSC at the offsets phase 1 computed.
+cudaError_t build_dense_rest(const DenseArgs& a, const DenseView& v, cudaStream_t s,
+                             int* launches) {
+  const int64_t wblocks = std::max<int64_t>(1, std::min<int64_t>((a.n + 8) / 8, 32LL * num_sms()));
+  if (a.dtype == 0)
+    k_rest_copy<float><<<static_cast<unsigned>(wblocks), 256, 0, s>>>(
+        a.n, a.m, a.colptr, a.rowidx, static_cast<const float*>(a.values), v.didx,
+        v.rest_colptr, const_cast<int32_t*>(v.rest_rowidx),
+        static_cast<float*>(const_cast<void*>(v.rest_values)));
+  else
+    k_rest_copy<__nv_bfloat16><<<static_cast<unsigned>(wblocks), 256, 0, s>>>(
+        a.n, a.m, a.colptr, a.rowidx, static_cast<const __nv_bfloat16*>(a.values), v.didx,
+        v.rest_colptr, const_cast<int32_t*>(v.rest_rowidx),
+        static_cast<__nv_bfloat16*>(const_cast<void*>(v.rest_values)));
   ++*launches;
   return cudaGetLastError();
 }

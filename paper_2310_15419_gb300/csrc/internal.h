@@ -132,12 +132,22 @@ struct DenseView {
   const int32_t* Kdev;  // device copy of K
   const uint16_t* A3;   // n x 3Kp BF16 terms (column-major, K fastest)
   int32_t Kp;
+  // A without the panel's rows, in CSC (same dtype; rows stay sorted per
+  // column); rest_nnz is an upper bound (A's nnz), the exact count lives in
+  // rest_colptr[n]
+  const int32_t* rest_colptr;
+  const int32_t* rest_rowidx;
+  const void* rest_values;
+  int32_t* rest_cnt;  // workspace: per-column counts of the rest
+  char* scan_tmp;     // workspace: scan scratch
 };
-size_t dense_workspace_bytes(int64_t m, int64_t n, int64_t kmax);
+size_t dense_workspace_bytes(int64_t m, int64_t n, int64_t kmax, int64_t nnz);
 cudaError_t select_dense_rows(const DenseArgs& a, void* ws, DenseView* out, cudaStream_t s,
                               int* launches);
 cudaError_t build_dense_panel(const DenseArgs& a, int32_t K, DenseView* v, cudaStream_t s,
                               int* launches);
+cudaError_t build_dense_rest(const DenseArgs& a, const DenseView& v, cudaStream_t s,
+                             int* launches);
 cudaError_t launch_tc_gemm(const DenseArgs& a, const DenseView& v, float* Ahat,
                            cudaStream_t s, int* launches);
 

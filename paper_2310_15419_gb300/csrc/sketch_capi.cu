@@ -138,7 +138,7 @@ size_t plan_workspace_bytes(const sketch_s* h, const sketch_csc* A,
                             const sketch_plan& p) {
   size_t b = sparse_workspace_bytes(h, A, p);
   if (p.tc_min_row_nnz > 0)
-    b = align256(b) + dense_workspace_bytes(A->m, A->n, dense_capacity(A, p));
+    b = align256(b) + dense_workspace_bytes(A->m, A->n, dense_capacity(A, p), A->nnz);
   return b;
 }
 
@@ -208,7 +208,7 @@ int run_plan(sketch_t h, const sketch_csc* A, float* Ahat,
   // then leave them out); the panel's product is added at the end
   DenseArgs da{};
   DenseView dv{};
-  int32_t K = 0;
+  int32_t K = 0, rest_nnz = 0;
   if (p.tc_min_row_nnz > 0) {
     if (h->capturing)
       return fail(h, SKETCH_ERR_UNSUPPORTED, "a tensor-core plan cannot be captured");
@@ -232,17 +232,35 @@ int run_plan(sketch_t h, const sketch_csc* A, float* Ahat,
     h->launches += nl;
     if (e != cudaSuccess) return cuda_fail(h, e, "dense row selection");
     e = cudaMemcpyAsync(&K, dv.Kdev, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(&rest_nnz, dv.rest_colptr + A->n, sizeof(int32_t),
+                          cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(h, e, "dense row count");
     if (K > 0) {
       nl = 0;
       e = build_dense_panel(da, K, &dv, s, &nl);
+      if (e == cudaSuccess && rest_nnz > 0) e = build_dense_rest(da, dv, s, &nl);
       h->launches += nl;
       if (e != cudaSuccess) return cuda_fail(h, e, "dense panel");
     }
   }
-  const int32_t* skip = K > 0 ? dv.didx : nullptr;
-  int rc_sparse = run_sparse(h, A, Ahat, p, ws, s, status, gen, skip);
+  // the sparse kernels see A without the panel's rows; with nothing left
+  // A_hat starts from zero
+  sketch_csc rest = *A;
+  int rc_sparse = SKETCH_OK;
+  if (K > 0 && rest_nnz == 0) {
+    cudaError_t e = cudaMemsetAsync(Ahat, 0, sizeof(float) * A->n * h->d, s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemsetAsync");
+  } else {
+    if (K > 0) {
+      rest.colptr = dv.rest_colptr;
+      rest.rowidx = dv.rest_rowidx;
+      rest.values = dv.rest_values;
+      rest.nnz = rest_nnz;
+    }
+    rc_sparse = run_sparse(h, &rest, Ahat, p, ws, s, status, gen, nullptr);
+  }
   if (rc_sparse != SKETCH_OK || K == 0) return rc_sparse;
   int nl = 0;
   cudaError_t e = launch_tc_gemm(da, dv, Ahat, s, &nl);
