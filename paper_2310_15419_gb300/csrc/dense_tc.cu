@@ -105,18 +105,39 @@ __device__ __forceinline__ uint32_t pm1_pair(uint32_t b0, uint32_t b1) {
 
 // A_hat(rows d0.., cols n0..) += S3 A3 for a 128 x 128 tile; 8 warps as
 // 4 (rows) x 2 (cols), each warp 32 x 64 = 2 x 8 fragments of 16 x 8.
+// The contraction runs over the dense rows in steps of 32; each step's S
+// signs (one Philox block per dense row) and the warps' +-1 A fragments are
+// built once and serve the three BF16 terms of A.  The A3 tiles (128
+// columns x 32 values of one term) stream through two shared buffers
+// filled by cp.async one tile ahead of the MMAs.
+__device__ __forceinline__ void tc_load_tile(uint16_t (*dst)[kLdB], const uint16_t* A3,
+                                             int32_t n, int32_t n0, int64_t K3, int64_t koff) {
+  for (int t = threadIdx.x; t < kBN * 4; t += kTcThreads) {
+    const int c = t >> 2, part = t & 3;  // part: 8 values (16 bytes)
+    const int col = n0 + c;
+    const uint16_t* src = col < n ? A3 + col * K3 + koff + 8 * part : A3;
+    const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(&dst[c][8 * part]));
+    const int bytes = col < n ? 16 : 0;  // zero fill past the last column
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src), "r"(bytes)
+                 : "memory");
+  }
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
 __global__ void __launch_bounds__(kTcThreads)
     k_tc_gemm(int32_t d, int32_t n, int32_t Kp, const int32_t* __restrict__ rows,
               const int32_t* __restrict__ Kdev, const uint16_t* __restrict__ A3,
-              float* __restrict__ Ahat, uint32_t k0, uint32_t k1, uint32_t stream_id) {
-  __shared__ uint32_t sbits[kBK][4];                        // S signs, 128 rows
-  __shared__ __align__(16) uint16_t btile[kBN][kLdB];       // A3 tile, K fastest
+              float* __restrict__ Ahat, uint32_t k0, uint32_t k1, uint32_t stream_id,
+              int accumulate) {
+  __shared__ uint32_t sbits[kBK][4];                           // S signs, 128 rows
+  __shared__ __align__(16) uint16_t btile[2][kBN][kLdB];       // A3 tiles, K fastest
   const int K = *Kdev;
   const int d0 = blockIdx.x * kBM, n0 = blockIdx.y * kBN;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int wm = warp & 3, wn = warp >> 2;  // warp tile: rows wm*32, cols wn*64
   const int gid = lane >> 2, tig = lane & 3;
   const int64_t K3 = 3LL * Kp;
+  const int steps = Kp / kBK;  // 32 dense rows per step, three terms each
   float acc[2][8][4];
 #pragma unroll
   for (int a = 0; a < 2; ++a)
@@ -125,11 +146,13 @@ __global__ void __launch_bounds__(kTcThreads)
 #pragma unroll
       for (int c = 0; c < 4; ++c) acc[a][b][c] = 0.f;
 
-  for (int64_t kk = 0; kk < K3; kk += kBK) {
-    const int third_k = static_cast<int>(kk % Kp);  // position inside one term
-    // --- S signs for the 32 contraction rows of this step ------------------
+  // tile l = 3 * step + term holds A3 values [term * Kp + 32 step, +32)
+  auto koff = [&](int l) { return static_cast<int64_t>(l % 3) * Kp + (l / 3) * kBK; };
+  tc_load_tile(btile[0], A3, n, n0, K3, koff(0));
+  for (int st = 0; st < steps; ++st) {
+    // --- S signs for the 32 dense rows of this step --------------------------
     if (threadIdx.x < kBK) {
-      const int q = third_k + threadIdx.x;
+      const int q = st * kBK + threadIdx.x;
       const int32_t j = q < K ? rows[q] : 0;  // padding rows multiply zeros
       const uint4 x = philox_block(static_cast<uint32_t>(d0 >> 7), static_cast<uint32_t>(j),
                                    stream_id, k0, k1);
@@ -138,42 +161,50 @@ __global__ void __launch_bounds__(kTcThreads)
       sbits[threadIdx.x][2] = x.z;
       sbits[threadIdx.x][3] = x.w;
     }
-    // --- A3 tile: 128 columns x 32 values (64 bytes per column) -----------
-    for (int t = threadIdx.x; t < kBN * 4; t += kTcThreads) {
-      const int c = t >> 2, part = t & 3;  // part: 8 values (16 bytes)
-      const int col = n0 + c;
-      uint4 v = make_uint4(0, 0, 0, 0);
-      if (col < n) v = *reinterpret_cast<const uint4*>(A3 + col * K3 + kk + 8 * part);
-      *reinterpret_cast<uint4*>(&btile[c][8 * part]) = v;
-    }
     __syncthreads();
+    // A fragments (S, 16 x 16 row-major) for both k halves, from sign bits
+    uint32_t af[2][2][4];
 #pragma unroll
-    for (int ks = 0; ks < kBK; ks += 16) {
-      // A fragments (S, 16 x 16 row-major) from sign bits
-      uint32_t af[2][4];
+    for (int h = 0; h < 2; ++h)
 #pragma unroll
       for (int fm = 0; fm < 2; ++fm) {
         const int r0 = wm * 32 + fm * 16 + gid, r1 = r0 + 8;
-        const int c0 = ks + 2 * tig, c8 = c0 + 8;
+        const int c0 = 16 * h + 2 * tig, c8 = c0 + 8;
         auto bit = [&](int r, int c) { return (sbits[c][r >> 5] >> (r & 31)) & 1u; };
-        af[fm][0] = pm1_pair(bit(r0, c0), bit(r0, c0 + 1));
-        af[fm][1] = pm1_pair(bit(r1, c0), bit(r1, c0 + 1));
-        af[fm][2] = pm1_pair(bit(r0, c8), bit(r0, c8 + 1));
-        af[fm][3] = pm1_pair(bit(r1, c8), bit(r1, c8 + 1));
+        af[h][fm][0] = pm1_pair(bit(r0, c0), bit(r0, c0 + 1));
+        af[h][fm][1] = pm1_pair(bit(r1, c0), bit(r1, c0 + 1));
+        af[h][fm][2] = pm1_pair(bit(r0, c8), bit(r0, c8 + 1));
+        af[h][fm][3] = pm1_pair(bit(r1, c8), bit(r1, c8 + 1));
       }
 #pragma unroll
-      for (int fn = 0; fn < 8; ++fn) {
-        const int cn = wn * 64 + fn * 8 + gid;
-        uint32_t bf[2];
-        bf[0] = *reinterpret_cast<const uint32_t*>(&btile[cn][ks + 2 * tig]);
-        bf[1] = *reinterpret_cast<const uint32_t*>(&btile[cn][ks + 2 * tig + 8]);
-        mma_bf16_16816(acc[0][fn], af[0], bf);
-        mma_bf16_16816(acc[1][fn], af[1], bf);
+    for (int term = 0; term < 3; ++term) {
+      const int l = 3 * st + term;
+      // the next tile streams in while this one is multiplied
+      if (l + 1 < 3 * steps) {
+        tc_load_tile(btile[(l + 1) & 1], A3, n, n0, K3, koff(l + 1));
+        asm volatile("cp.async.wait_group 1;" ::: "memory");
+      } else {
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
       }
+      __syncthreads();
+      uint16_t (*bt)[kLdB] = btile[l & 1];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int ks = 16 * h;
+#pragma unroll
+        for (int fn = 0; fn < 8; ++fn) {
+          const int cn = wn * 64 + fn * 8 + gid;
+          uint32_t bf[2];
+          bf[0] = *reinterpret_cast<const uint32_t*>(&bt[cn][ks + 2 * tig]);
+          bf[1] = *reinterpret_cast<const uint32_t*>(&bt[cn][ks + 2 * tig + 8]);
+          mma_bf16_16816(acc[0][fn], af[h][0], bf);
+          mma_bf16_16816(acc[1][fn], af[h][1], bf);
+        }
+      }
+      __syncthreads();  // the buffer is refilled two tiles later
     }
-    __syncthreads();
   }
-  // --- add into A_hat (column-major, ld = d) -------------------------------
+  // --- add into (accumulate) or store to A_hat (column-major, ld = d) ------
 #pragma unroll
   for (int fm = 0; fm < 2; ++fm)
 #pragma unroll
@@ -186,7 +217,10 @@ __global__ void __launch_bounds__(kTcThreads)
 #pragma unroll
         for (int w = 0; w < 2; ++w) {
           const int c = c0 + w;
-          if (r < d && c < n) Ahat[static_cast<int64_t>(c) * d + r] += acc[fm][fn][2 * h + w];
+          if (r < d && c < n) {
+            float* o = Ahat + static_cast<int64_t>(c) * d + r;
+            *o = accumulate ? *o + acc[fm][fn][2 * h + w] : acc[fm][fn][2 * h + w];
+          }
         }
       }
     }
@@ -374,11 +408,11 @@ cudaError_t build_dense_rest(const DenseArgs& a, const DenseView& v, cudaStream_
 }
 
 cudaError_t launch_tc_gemm(const DenseArgs& a, const DenseView& v, float* Ahat,
-                           cudaStream_t s, int* launches) {
+                           int accumulate, cudaStream_t s, int* launches) {
   const dim3 grid((a.d + kBM - 1) / kBM, (a.n + kBN - 1) / kBN);
   if (grid.y > 65535) return cudaErrorInvalidValue;
   k_tc_gemm<<<grid, kTcThreads, 0, s>>>(a.d, a.n, v.Kp, v.rows, v.Kdev, v.A3, Ahat, a.k0,
-                                        a.k1, a.stream_id);
+                                        a.k1, a.stream_id, accumulate);
   ++*launches;
   return cudaGetLastError();
 }

@@ -149,7 +149,7 @@ cudaError_t build_dense_panel(const DenseArgs& a, int32_t K, DenseView* v, cudaS
 cudaError_t build_dense_rest(const DenseArgs& a, const DenseView& v, cudaStream_t s,
                              int* launches);
 cudaError_t launch_tc_gemm(const DenseArgs& a, const DenseView& v, float* Ahat,
-                           cudaStream_t s, int* launches);
+                           int accumulate, cudaStream_t s, int* launches);
 
 // Shared building blocks (sketch_kernels.cu).
 int64_t scan_bytes_for(int64_t len);

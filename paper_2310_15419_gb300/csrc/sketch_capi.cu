@@ -246,13 +246,11 @@ int run_plan(sketch_t h, const sketch_csc* A, float* Ahat,
     }
   }
   // the sparse kernels see A without the panel's rows; with nothing left
-  // A_hat starts from zero
+  // the panel's product is stored into A_hat directly
   sketch_csc rest = *A;
   int rc_sparse = SKETCH_OK;
-  if (K > 0 && rest_nnz == 0) {
-    cudaError_t e = cudaMemsetAsync(Ahat, 0, sizeof(float) * A->n * h->d, s);
-    if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemsetAsync");
-  } else {
+  const bool rest_empty = K > 0 && rest_nnz == 0;
+  if (!rest_empty) {
     if (K > 0) {
       rest.colptr = dv.rest_colptr;
       rest.rowidx = dv.rest_rowidx;
@@ -263,7 +261,7 @@ int run_plan(sketch_t h, const sketch_csc* A, float* Ahat,
   }
   if (rc_sparse != SKETCH_OK || K == 0) return rc_sparse;
   int nl = 0;
-  cudaError_t e = launch_tc_gemm(da, dv, Ahat, s, &nl);
+  cudaError_t e = launch_tc_gemm(da, dv, Ahat, rest_empty ? 0 : 1, s, &nl);
   h->launches += nl;
   return e == cudaSuccess ? SKETCH_OK : cuda_fail(h, e, "tensor-core panel");
 }
