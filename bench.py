@@ -18,6 +18,7 @@ work of all ranks.
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import statistics
@@ -27,6 +28,7 @@ import tempfile
 import time
 
 import numpy as np
+
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
@@ -71,6 +73,25 @@ def workload_config(rows=2_000_000):
                         "S swept over +-1, U(-1,1), N(0,1)" % format(rows, ","),
             "m": rows, "n": 1000, "d": inputs.SKEW_LARGE_D,
             "seed_A": 2, "seed_S": 1}
+
+
+def recorded_traffic(dist, plan):
+    """DRAM bytes per launch (read + write) of the dominant kernel from the
+    ncu capture recorded under profiles/, or None when that capture does not
+    describe the kernel as it is now: another distribution or plan, or a
+    kernel source that changed since (its SHA-256 no longer matches)."""
+    path = os.path.join(ROOT, "profiles", "k_tile_normal_skew_large_traffic.json")
+    if dist != "normal" or plan.get("mode") != 3 or plan.get("panel_rows") != 1024 \
+            or plan.get("row_groups") != 20 or plan.get("cols_per_warp") != 64:
+        return None
+    try:
+        rec = json.load(open(path))
+        h = hashlib.sha256()
+        for f in rec["source_files"]:
+            h.update(open(os.path.join(ROOT, f), "rb").read())
+        return rec["traffic_bytes"] if h.hexdigest() == rec["source_sha256"] else None
+    except (OSError, KeyError, ValueError):
+        return None
 
 
 def measured_peaks():
@@ -467,7 +488,7 @@ def run_ours(args):
     dom = max(DISTS, key=lambda x: roof[x]["ms"])
     roofline = {"bound": roof[dom]["bound"], "achieved": roof[dom]["achieved"],
                 "peak": roof[dom]["peak"], "unit": "TFLOP/s",
-                "frac": roof[dom]["frac"], "traffic": None,
+                "frac": roof[dom]["frac"], "traffic": recorded_traffic(dom, plans[dom]),
                 "kernel": "sketch_apply(%s)" % dom,
                 "peak_basis": "RNG at the measured generator rate for the "
                               "minimum d x nonempty-rows entries + d x nnz "

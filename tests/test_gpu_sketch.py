@@ -324,6 +324,25 @@ def test_tensor_core_panel_float_tolerance(plan):
     assert rel_fro(got, ref) <= TOL
 
 
+@pytest.mark.parametrize("plan", TC_PLANS)
+def test_tensor_core_panel_only_dense_rows(plan):
+    """Every nonzero in the panel (the Abnormal_A pattern): the sparse pass
+    has nothing left and the panel's product is stored into A_hat directly;
+    integer values keep it bit-exact, at ragged d and n."""
+    rng = np.random.default_rng(34)
+    m, n = 5000, 301
+    rows = np.arange(0, m, 97)
+    keys = np.sort((np.arange(n)[:, None] * m + rows[None, :]).ravel())
+    colptr = np.searchsorted(keys // m, np.arange(n + 1)).astype(np.int32)
+    rowidx = (keys % m).astype(np.int32)
+    vals = (rng.integers(1, 4, size=keys.size) * rng.choice([-1, 1], size=keys.size))
+    A = inputs.CSC(m, n, colptr, rowidx, vals.astype(np.float32))
+    for d in (256, 259):
+        ref = oracle_sketch(A, d, "pm1")
+        got = gpu_sketch(A, d, "pm1", plan=plan)
+        assert np.array_equal(got, ref), d
+
+
 def test_tensor_core_panel_without_dense_rows_and_bad_dist():
     A = inputs.integer_uniform(4000, 50, 0.01, seed=33)
     got = gpu_sketch(A, 200, "pm1", plan=TC_PLANS[0])
