@@ -94,6 +94,23 @@ def recorded_traffic(dist, plan):
         return None
 
 
+def reduce_max_ms(local_ms, pg, device):
+    """The largest of the ranks' timed totals (the job ends with its slowest
+    rank); `pg` is torch.distributed (any backend) or None for one rank."""
+    if pg is None:
+        return float(local_ms)
+    import torch
+    t = torch.tensor([float(local_ms)], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world, steps, units_per_step, max_ms):
+    """Whole-job throughput in G units/s: every rank processes `steps` steps
+    of `units_per_step` (replicas), the time is the slowest rank's."""
+    return world * steps * units_per_step / (max_ms / 1e3) / 1e9
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -458,13 +475,9 @@ def run_ours(args):
     clk = clocks.stop()
     launches = sum(s.launch_count() for s in sketches.values()) - launches0
 
-    total_ms = sum(step_ms)
-    if dist_pg:
-        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        dist_pg.all_reduce(t, op=dist_pg.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = reduce_max_ms(sum(step_ms), dist_pg, "cuda")
     flops_step = len(DISTS) * 2.0 * d * A.nnz
-    value = world * args.steps * flops_step / (total_ms / 1e3) / 1e9
+    value = job_value(world, args.steps, flops_step, total_ms)
 
     # ---- roofline of the dominant kernel (the distribution taking longest)
     peaks, peak_kind = measured_peaks()
@@ -520,7 +533,8 @@ def run_ours(args):
         torch.cuda.synchronize()
         if it > 0:
             e2e_ms.append(e0.elapsed_time(e1))
-    e2e_val = flops_step / (statistics.mean(e2e_ms) / 1e3) / 1e9 * world
+    e2e_val = job_value(world, 1, flops_step,
+                        reduce_max_ms(statistics.mean(e2e_ms), dist_pg, "cuda"))
 
     # ---- secondary workloads (least squares, batched, serving)
     extras = {}
