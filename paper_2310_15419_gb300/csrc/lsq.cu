@@ -643,7 +643,15 @@ __global__ void __launch_bounds__(32 * W)
     // the test reads only what the step kernel before the rows pass wrote
     if (!init && !sc->done) {
       double a = 0.0;
-      for (int g = threadIdx.x; g < npy; g += 32 * W) a += party[g];
+      for (int g0 = threadIdx.x; g0 < npy; g0 += 4 * 32 * W) {
+        double v[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int g = g0 + 32 * W * q;
+          v[q] = g < npy ? party[g] : 0.0;
+        }
+        a += (v[0] + v[1]) + (v[2] + v[3]);
+      }
       const double y2 = block_sum0<32 * W>(a, red);
       if (threadIdx.x == 0) {
         const int istop = lsqr_test(sc->slot[par], sc->bnorm, sc->tol, y2, sc->maxit);
@@ -658,10 +666,19 @@ __global__ void __launch_bounds__(32 * W)
     pdl_wait();
     pdl_launch();
     if (sc->done) return;
+    // fixed-order sums of the rows pass's partials, eight loads per thread
+    // in flight per round
     double a = 0.0, z = 0.0;
-    for (int g = threadIdx.x; g < np2; g += 32 * W) {
-      a += partial2[g];
-      if (init) z += partial_z[g];
+    for (int g0 = threadIdx.x; g0 < np2; g0 += 8 * 32 * W) {
+      double v[8], vz[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int g = g0 + 32 * W * q;
+        v[q] = g < np2 ? partial2[g] : 0.0;
+        vz[q] = (init && g < np2) ? partial_z[g] : 0.0;
+      }
+      a += ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7]));
+      if (init) z += ((vz[0] + vz[1]) + (vz[2] + vz[3])) + ((vz[4] + vz[5]) + (vz[6] + vz[7]));
     }
     a = block_sum0<32 * W>(a, red);
     if (init) z = block_sum0<32 * W>(z, red);
@@ -1225,11 +1242,12 @@ struct ColsArgs {
 template <typename VT>
 void launch_cols(const CscView& A, const double* u, double* out, Scalars* sc,
                  const ColsArgs& c, cudaStream_t s) {
-  // warps per column from the mean column length: about 16 entries per
-  // thread (any choice is correct)
+  // warps per column from the mean column length: about 8 entries per
+  // thread, one round of loads (any choice is correct; 16 warps measured
+  // slower on a 2000-entry column)
   const int64_t avg = A.nnz / std::max<int64_t>(1, A.n);
   int W = 1;
-  while (W < 8 && avg > 512LL * W) W *= 2;
+  while (W < 8 && avg > 256LL * W) W *= 2;
   const unsigned g = static_cast<unsigned>(A.n + (c.lsqr ? 1 : 0));
   const VT* vals = static_cast<const VT*>(A.values);
 #define SK_COLS(WW)                                                                     \
