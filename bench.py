@@ -312,10 +312,12 @@ def bench_dense(torch, capi, inputs, peaks, steps=5):
     ref = None
     for name, plan in (("tensor_core", dict(mode=capi.SKETCH_MODE_REGEN, q_tiles=4, split=8,
                                             tc_min_row_nnz=A.n // 2)),
-                       ("cuda_core", dict(mode=capi.SKETCH_MODE_REGEN, q_tiles=4, split=8))):
+                       ("cuda_core", dict(mode=capi.SKETCH_MODE_REGEN, q_tiles=4, split=8)),
+                       ("tuned", None)):
         sk = capi.Sketch(A.m, A.n, d, "pm1", seed=1)
-        sk.set_plan(**plan)
-        sk.apply(dA, out)
+        if plan is not None:
+            sk.set_plan(**plan)
+        sk.apply(dA, out)                   # the tuned entry picks its plan here
         torch.cuda.synchronize()
         ms = []
         for _ in range(steps):
@@ -328,12 +330,15 @@ def bench_dense(torch, capi, inputs, peaks, steps=5):
             ms.append(e0.elapsed_time(e1))
         if ref is None:
             ref = out.clone()
-        else:
+        elif name == "cuda_core":
             res["max_abs_diff_vs_tensor_core"] = float((out - ref).abs().max().item())
+        chosen = sk.get_plan(dA)
         sk.close()
         mean = statistics.mean(ms)
         res[name] = {"ms": round(mean, 4),
                      "useful_tflops": round(2.0 * d * A.nnz / (mean / 1e3) / 1e12, 3)}
+        if plan is None:
+            res[name]["plan"] = chosen
     # tensor-core roofline of the panel product: 3 BF16 terms, K padded to 32
     K = A.nnz // A.n
     Kp = (K + 31) // 32 * 32

@@ -369,6 +369,21 @@ static std::vector<sketch_plan> candidates(const sketch_s* h, const sketch_csc* 
         (size_t(8) << 30))
       c.push_back(p);
   }
+  // +-1 S: densified panels on the tensor cores for rows holding at least
+  // half, or a fifth, of the columns (REGEN for the rest).  With no such row
+  // a candidate costs its base plan plus the row count, so it only wins
+  // when there are dense-enough rows.
+  if (h->dist == SKETCH_PM1 && A->n >= 64) {
+    const double avg_col = A->n > 0 ? double(A->nnz) / double(A->n) : 0.0;
+    for (int32_t tau : {static_cast<int32_t>(A->n / 2), static_cast<int32_t>(A->n / 5)}) {
+      sketch_plan p{};
+      p.mode = SKETCH_MODE_REGEN;
+      p.q_tiles = qmax;
+      p.split = avg_col >= 4096 ? 8 : avg_col >= 1024 ? 4 : avg_col >= 256 ? 2 : 1;
+      p.tc_min_row_nnz = tau;
+      c.push_back(p);
+    }
+  }
   // PANEL (shared-memory atomics, order-dependent at the last bit) is not a
   // candidate: every plan the tuner picks is deterministic.
   return c;
@@ -391,6 +406,10 @@ int choose_plan(sketch_t h, const sketch_csc* A, float* Ahat, cudaStream_t s,
   auto it = h->plans.find(key);
   if (it != h->plans.end()) {
     *out = it->second;
+    // a tuned tensor-core panel needs a host read of its height, which a
+    // captured stream cannot do: under capture the same plan runs without
+    // the panel (same sketch, CUDA cores only)
+    if (h->capturing) out->tc_min_row_nnz = 0;
     return SKETCH_OK;
   }
   const char* env = std::getenv("SKETCH_TUNE");

@@ -343,6 +343,22 @@ def test_tensor_core_panel_only_dense_rows(plan):
         assert np.array_equal(got, ref), d
 
 
+def test_tuned_plan_on_dense_rows_is_exact():
+    """With tuning on, +-1 S on a matrix with dense rows: whichever plan the
+    tuner takes (tensor-core panels are candidates), the sketch is the
+    oracle's, bit for bit (integer values)."""
+    A = _dense_rows_matrix(9000, 300, 97, 0.003, True, seed=35)
+    sk = capi.Sketch(A.m, A.n, 300, "pm1", seed=1)
+    sk.set_autotune(True)
+    dA = capi.DeviceCSC(A)
+    out = sk.apply(dA)
+    plan = sk.get_plan(dA)
+    got = out.cpu().numpy().T
+    sk.close()
+    assert plan["mode"] in (capi.SKETCH_MODE_REGEN, capi.SKETCH_MODE_TILE)
+    assert np.array_equal(got, oracle_sketch(A, 300, "pm1"))
+
+
 def test_tensor_core_panel_without_dense_rows_and_bad_dist():
     A = inputs.integer_uniform(4000, 50, 0.01, seed=33)
     got = gpu_sketch(A, 200, "pm1", plan=TC_PLANS[0])
