@@ -181,7 +181,9 @@ int sketch_apply_noalloc(sketch_t h, const sketch_csc* A, float* Ahat,
 const char* sketch_last_error(sketch_t h);
 
 /* Read and clear the device status word of the handle (synchronous):
- * 0, or SKETCH_ERR_CSC if a kernel met a row index outside [0, m). */
+ * 0, SKETCH_ERR_TIMEOUT if a kernel's bounded wait on the tensor cores gave
+ * up (its output is then incomplete), or SKETCH_ERR_CSC if a kernel met a
+ * row index outside [0, m). */
 int sketch_device_status(sketch_t h, sketch_stream_t stream);
 
 /* Full CSC check on the device (synchronous): colptr[0] = 0, colptr

@@ -112,5 +112,6 @@ __device__ __forceinline__ float to_f32<__nv_bfloat16>(__nv_bfloat16 v) {
 // Device status bits written by kernels that meet bad input.
 constexpr int kStatusBadRow = 1;
 constexpr int kStatusBadColptr = 2;
+constexpr int kStatusTimeout = 4;  // a bounded wait inside a kernel gave up
 
 }  // namespace sk

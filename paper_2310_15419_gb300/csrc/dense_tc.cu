@@ -9,7 +9,10 @@
 //     A3 = [A1; A2; A3] (3K x n) against S3 = [S_D, S_D, S_D] and no input
 //     rounding happens -- only the FP32 accumulation rounds;
 //   * S_D's signs come straight from Philox bits: one block per (128 rows of
-//     S, dense row), expanded to BF16 +-1 in registers (no S in memory).
+//     S, dense row), expanded to a BF16 +-1 tile in shared memory (no S in
+//     global memory);
+//   * the MMA is tcgen05 (5th-generation tensor cores) with the accumulator
+//     in tensor memory.
 // The sparse kernels run on the rest of A (a compacted CSC without the
 // panel's rows), so A_hat = S A_rest + S_D A_D with the MMA adding into A_hat
 // afterwards.
@@ -28,7 +31,6 @@ namespace {
 constexpr int kBM = 128;   // rows of S (A_hat) per CTA
 constexpr int kBN = 128;   // columns of A per CTA
 constexpr int kBK = 32;    // contraction step
-constexpr int kLdB = 40;   // padded row length of the B tile (bf16)
 constexpr int kTcThreads = 256;
 
 __device__ __forceinline__ uint16_t bf16_bits(float v) {
@@ -89,141 +91,232 @@ __global__ void k_dense_scatter(int32_t n, int32_t m, int32_t Kp,
   }
 }
 
-__device__ __forceinline__ void mma_bf16_16816(float (&c)[4], const uint32_t (&a)[4],
-                                               const uint32_t (&b)[2]) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
-      "{%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, {%0, %1, %2, %3};\n"
-      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
-
 // +-1 in BF16 for sign bits b0 (low half) and b1 (high half): 0 -> +1, 1 -> -1
 __device__ __forceinline__ uint32_t pm1_pair(uint32_t b0, uint32_t b1) {
   return (0x3F80u | (b0 << 15)) | ((0x3F80u | (b1 << 15)) << 16);
 }
 
-// A_hat(rows d0.., cols n0..) += S3 A3 for a 128 x 128 tile; 8 warps as
-// 4 (rows) x 2 (cols), each warp 32 x 64 = 2 x 8 fragments of 16 x 8.
-// The contraction runs over the dense rows in steps of 32; each step's S
-// signs (one Philox block per dense row) and the warps' +-1 A fragments are
-// built once and serve the three BF16 terms of A.  The A3 tiles (128
-// columns x 32 values of one term) stream through two shared buffers
-// filled by cp.async one tile ahead of the MMAs.
-__device__ __forceinline__ void tc_load_tile(uint16_t (*dst)[kLdB], const uint16_t* A3,
-                                             int32_t n, int32_t n0, int64_t K3, int64_t koff) {
-  for (int t = threadIdx.x; t < kBN * 4; t += kTcThreads) {
-    const int c = t >> 2, part = t & 3;  // part: 8 values (16 bytes)
-    const int col = n0 + c;
-    const uint16_t* src = col < n ? A3 + col * K3 + koff + 8 * part : A3;
-    const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(&dst[c][8 * part]));
-    const int bytes = col < n ? 16 : 0;  // zero fill past the last column
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src), "r"(bytes)
-                 : "memory");
-  }
-  asm volatile("cp.async.commit_group;" ::: "memory");
+// ---------------------------------------------------------------------------
+// A_hat(rows d0.., cols n0..) (+)= S3 A3 for a 128 x 128 tile on the
+// 5th-generation tensor cores (tcgen05).  One thread issues `tcgen05.mma.cta_group::1.kind::f16` (M = N = 128, K = 16,
+// BF16 in, FP32 accumulate) with both operands in shared memory and the
+// 128 x 128 accumulator in tensor memory (128 columns, allocated per CTA).
+// Operand tiles (128 rows x 32 k, BF16) use the K-major layout without
+// swizzle: 8-row x 16-byte core matrices, the next one along K 128 bytes on,
+// along M/N 512 bytes on.  The A tile (+-1 S) is built from Philox sign bits,
+// One iteration per 32 dense rows: the A tile (+-1 S, built once) and the
+// three B tiles (the BF16 terms of A3, by cp.async one iteration ahead) form
+// a stage; six MMAs (3 terms x 2 k halves) and one tcgen05.commit per
+// iteration; a stage is reused once that commit has arrived on its
+// mbarrier.  Every wait has
+// an iteration limit: on expiry the CTA records kStatusTimeout, frees its
+// tensor memory and stops.
+constexpr uint32_t kUmmaLbo = 128, kUmmaSbo = 512;
+constexpr int kUmmaTile = 8192;  // bytes of one 128 x 32 BF16 operand tile
+// instruction descriptor: F32 accumulator, BF16 A and B, both K-major,
+// N = 128 (N >> 3 at bit 17), M = 128 (M >> 4 at bit 24)
+constexpr uint32_t kUmmaIdesc =
+    (1u << 4) | (1u << 7) | (1u << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
+constexpr int kUmmaStages = 2;  // stage = A tile + the three B terms of a step
+constexpr int kUmmaStageBytes = 4 * kUmmaTile;
+// two stages + alignment; at most three CTAs share an SM, so 3 x 128
+// tensor-memory columns never exceed the 512 there and tcgen05.alloc never
+// waits for another CTA
+constexpr size_t kUmmaSmem = kUmmaStages * kUmmaStageBytes + 1024;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
-__global__ void __launch_bounds__(kTcThreads)
-    k_tc_gemm(int32_t d, int32_t n, int32_t Kp, const int32_t* __restrict__ rows,
+// shared-memory matrix descriptor: start, leading (K) and stride (M/N)
+// byte offsets in 16-byte units, descriptor version 1, no swizzle
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr) {
+  return static_cast<uint64_t>((saddr >> 4) & 0x3FFFu) |
+         (static_cast<uint64_t>((kUmmaLbo >> 4) & 0x3FFFu) << 16) |
+         (static_cast<uint64_t>((kUmmaSbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// wait for the phase of parity `parity` of an mbarrier; false after the
+// iteration limit
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  for (int i = 0; i < (1 << 22); ++i) {
+    uint32_t ok;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+
+__global__ void __launch_bounds__(kTcThreads, 1)
+    k_tc_umma(int32_t d, int32_t n, int32_t Kp, const int32_t* __restrict__ rows,
               const int32_t* __restrict__ Kdev, const uint16_t* __restrict__ A3,
               float* __restrict__ Ahat, uint32_t k0, uint32_t k1, uint32_t stream_id,
-              int accumulate) {
-  __shared__ uint32_t sbits[kBK][4];                           // S signs, 128 rows
-  __shared__ __align__(16) uint16_t btile[2][kBN][kLdB];       // A3 tiles, K fastest
-  const int K = *Kdev;
+              int accumulate, int* status) {
+  extern __shared__ uint8_t sm_raw[];
+  __shared__ uint32_t sbits[kBK][4];
+  __shared__ __align__(8) uint64_t mbar[kUmmaStages];
+  __shared__ uint32_t tmem_base;
+  __shared__ int failed;
+  uint8_t* base = sm_raw + ((1024u - (smem_u32(sm_raw) & 1023u)) & 1023u);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int d0 = blockIdx.x * kBM, n0 = blockIdx.y * kBN;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int wm = warp & 3, wn = warp >> 2;  // warp tile: rows wm*32, cols wn*64
-  const int gid = lane >> 2, tig = lane & 3;
+  const int K = *Kdev;
   const int64_t K3 = 3LL * Kp;
-  const int steps = Kp / kBK;  // 32 dense rows per step, three terms each
-  float acc[2][8][4];
-#pragma unroll
-  for (int a = 0; a < 2; ++a)
-#pragma unroll
-    for (int b = 0; b < 8; ++b)
-#pragma unroll
-      for (int c = 0; c < 4; ++c) acc[a][b][c] = 0.f;
+  const int steps = Kp / kBK;
+  auto tileA = [&](int stg) { return base + stg * kUmmaStageBytes; };
+  auto tileB = [&](int stg, int term) { return base + stg * kUmmaStageBytes + (1 + term) * kUmmaTile; };
+  // the three B tiles of step st: terms of A3, dense rows 32 st .. + 31
+  auto load_B = [&](int st) {
+    for (int c = tid; c < 3 * kBN * 4; c += kTcThreads) {
+      const int term = c / (kBN * 4), cc = c % (kBN * 4);
+      const int nn = cc >> 2, part = cc & 3;
+      const int col = n0 + nn;
+      const int64_t koff = static_cast<int64_t>(term) * Kp + kBK * st;
+      const uint16_t* src = col < n ? A3 + col * K3 + koff + 8 * part : A3;
+      const uint32_t dst = smem_u32(tileB(st % kUmmaStages, term) + (nn >> 3) * kUmmaSbo +
+                                    part * kUmmaLbo + (nn & 7) * 16);
+      const int bytes = col < n ? 16 : 0;  // zero fill past the last column
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src),
+                   "r"(bytes)
+                   : "memory");
+    }
+  };
+  if (tid == 0) {
+    failed = 0;
+    for (int q = 0; q < kUmmaStages; ++q)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[q])) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;" ::"r"(
+                     smem_u32(&tmem_base))
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  load_B(0);
+  asm volatile("cp.async.commit_group;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_base;
 
-  // tile l = 3 * step + term holds A3 values [term * Kp + 32 step, +32)
-  auto koff = [&](int l) { return static_cast<int64_t>(l % 3) * Kp + (l / 3) * kBK; };
-  tc_load_tile(btile[0], A3, n, n0, K3, koff(0));
   for (int st = 0; st < steps; ++st) {
-    // --- S signs for the 32 dense rows of this step --------------------------
-    if (threadIdx.x < kBK) {
-      const int q = st * kBK + threadIdx.x;
+    const int sb = st % kUmmaStages;
+    // prefetch step st + 1 into the stage MMA(st - 1) read
+    if (st + 1 < steps && st >= 1 && tid == 0 &&
+        !mbar_wait(smem_u32(&mbar[(st - 1) % kUmmaStages]), ((st - 1) / kUmmaStages) & 1))
+      failed = 1;
+    if (tid < kBK) {  // S signs for the 32 dense rows of this step
+      const int q = st * kBK + tid;
       const int32_t j = q < K ? rows[q] : 0;  // padding rows multiply zeros
       const uint4 x = philox_block(static_cast<uint32_t>(d0 >> 7), static_cast<uint32_t>(j),
                                    stream_id, k0, k1);
-      sbits[threadIdx.x][0] = x.x;
-      sbits[threadIdx.x][1] = x.y;
-      sbits[threadIdx.x][2] = x.z;
-      sbits[threadIdx.x][3] = x.w;
+      sbits[tid][0] = x.x;
+      sbits[tid][1] = x.y;
+      sbits[tid][2] = x.z;
+      sbits[tid][3] = x.w;
     }
     __syncthreads();
-    // A fragments (S, 16 x 16 row-major) for both k halves, from sign bits
-    uint32_t af[2][2][4];
-#pragma unroll
-    for (int h = 0; h < 2; ++h)
-#pragma unroll
-      for (int fm = 0; fm < 2; ++fm) {
-        const int r0 = wm * 32 + fm * 16 + gid, r1 = r0 + 8;
-        const int c0 = 16 * h + 2 * tig, c8 = c0 + 8;
-        auto bit = [&](int r, int c) { return (sbits[c][r >> 5] >> (r & 31)) & 1u; };
-        af[h][fm][0] = pm1_pair(bit(r0, c0), bit(r0, c0 + 1));
-        af[h][fm][1] = pm1_pair(bit(r1, c0), bit(r1, c0 + 1));
-        af[h][fm][2] = pm1_pair(bit(r0, c8), bit(r0, c8 + 1));
-        af[h][fm][3] = pm1_pair(bit(r1, c8), bit(r1, c8 + 1));
-      }
-#pragma unroll
-    for (int term = 0; term < 3; ++term) {
-      const int l = 3 * st + term;
-      // the next tile streams in while this one is multiplied
-      if (l + 1 < 3 * steps) {
-        tc_load_tile(btile[(l + 1) & 1], A3, n, n0, K3, koff(l + 1));
-        asm volatile("cp.async.wait_group 1;" ::: "memory");
-      } else {
-        asm volatile("cp.async.wait_group 0;" ::: "memory");
-      }
-      __syncthreads();
-      uint16_t (*bt)[kLdB] = btile[l & 1];
+    if (failed) break;
+    if (st + 1 < steps) load_B(st + 1);
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    // A tile of step st: +-1 S (BF16), row r of the tile, k = dense row of
+    // the step (its stage was last read by MMA(st - 2), which the wait of
+    // iteration st - 1 covered)
+    {
+      uint8_t* smA = tileA(sb);
+      const int r = tid & 127;
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
-        const int ks = 16 * h;
+        const int kc = 2 * (tid >> 7) + h;
+        uint32_t w[4];
 #pragma unroll
-        for (int fn = 0; fn < 8; ++fn) {
-          const int cn = wn * 64 + fn * 8 + gid;
-          uint32_t bf[2];
-          bf[0] = *reinterpret_cast<const uint32_t*>(&bt[cn][ks + 2 * tig]);
-          bf[1] = *reinterpret_cast<const uint32_t*>(&bt[cn][ks + 2 * tig + 8]);
-          mma_bf16_16816(acc[0][fn], af[h][0], bf);
-          mma_bf16_16816(acc[1][fn], af[h][1], bf);
+        for (int u = 0; u < 4; ++u) {
+          const int ka = 8 * kc + 2 * u;
+          const uint32_t b0 = (sbits[ka][r >> 5] >> (r & 31)) & 1u;
+          const uint32_t b1 = (sbits[ka + 1][r >> 5] >> (r & 31)) & 1u;
+          w[u] = pm1_pair(b0, b1);
         }
+        *reinterpret_cast<uint4*>(smA + (r >> 3) * kUmmaSbo + kc * kUmmaLbo + (r & 7) * 16) =
+            make_uint4(w[0], w[1], w[2], w[3]);
       }
-      __syncthreads();  // the buffer is refilled two tiles later
+    }
+    // this step's B tiles have landed (at most one newer group)
+    asm volatile("cp.async.wait_group 1;" ::: "memory");
+    // generic-proxy writes (st.shared, cp.async) -> visible to the tensor core
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+      for (int term = 0; term < 3; ++term)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const uint64_t ad = umma_desc(smem_u32(tileA(sb)) + 256 * h);
+          const uint64_t bd = umma_desc(smem_u32(tileB(sb, term)) + 256 * h);
+          const uint32_t acc = (st > 0 || term > 0 || h > 0) ? 1u : 0u;
+          asm volatile(
+              "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+              "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+              "l"(ad), "l"(bd), "r"(kUmmaIdesc), "r"(acc)
+              : "memory");
+        }
+      asm volatile(
+          "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+              smem_u32(&mbar[sb]))
+          : "memory");
     }
   }
-  // --- add into (accumulate) or store to A_hat (column-major, ld = d) ------
+  asm volatile("cp.async.wait_all;" ::: "memory");
+  // the last commit completes after every MMA before it
+  if (!failed && tid == 0 &&
+      !mbar_wait(smem_u32(&mbar[(steps - 1) % kUmmaStages]), ((steps - 1) / kUmmaStages) & 1))
+    failed = 1;
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (!failed) {
+    // warp w: lanes (rows of S) 32 (w & 3) .. + 31, columns 64 (w >> 2) .. + 63
+    const int rq = warp & 3;
+    const int r = d0 + 32 * rq + lane;
 #pragma unroll
-  for (int fm = 0; fm < 2; ++fm)
+    for (int cc = 0; cc < 2; ++cc) {
+      const int c0 = 64 * (warp >> 2) + 32 * cc;
+      uint32_t v[32];
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, "
+          "%10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, "
+          "%26, %27, %28, %29, %30, %31}, [%32];"
+          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
+            "=r"(v[6]), "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]),
+            "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]),
+            "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+            "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]),
+            "=r"(v[30]), "=r"(v[31])
+          : "r"(tmem + (static_cast<uint32_t>(32 * rq) << 16) + static_cast<uint32_t>(c0)));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      if (r < d) {
 #pragma unroll
-    for (int fn = 0; fn < 8; ++fn) {
-      const int r0 = d0 + wm * 32 + fm * 16 + gid;
-      const int c0 = n0 + wn * 64 + fn * 8 + 2 * tig;
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int r = r0 + 8 * h;
-#pragma unroll
-        for (int w = 0; w < 2; ++w) {
-          const int c = c0 + w;
-          if (r < d && c < n) {
+        for (int j = 0; j < 32; ++j) {
+          const int c = n0 + c0 + j;
+          if (c < n) {
             float* o = Ahat + static_cast<int64_t>(c) * d + r;
-            *o = accumulate ? *o + acc[fm][fn][2 * h + w] : acc[fm][fn][2 * h + w];
+            const float x = __uint_as_float(v[j]);
+            *o = accumulate ? *o + x : x;
           }
         }
       }
     }
+  } else if (tid == 0) {
+    atomicOr(status, kStatusTimeout);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" ::"r"(tmem) : "memory");
 }
 
 size_t al256(size_t b) { return (b + 255) / 256 * 256; }
@@ -411,8 +504,11 @@ cudaError_t launch_tc_gemm(const DenseArgs& a, const DenseView& v, float* Ahat,
                            int accumulate, cudaStream_t s, int* launches) {
   const dim3 grid((a.d + kBM - 1) / kBM, (a.n + kBN - 1) / kBN);
   if (grid.y > 65535) return cudaErrorInvalidValue;
-  k_tc_gemm<<<grid, kTcThreads, 0, s>>>(a.d, a.n, v.Kp, v.rows, v.Kdev, v.A3, Ahat, a.k0,
-                                        a.k1, a.stream_id, accumulate);
+  cudaError_t e = cudaFuncSetAttribute(k_tc_umma, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(kUmmaSmem));
+  if (e != cudaSuccess) return e;
+  k_tc_umma<<<grid, kTcThreads, kUmmaSmem, s>>>(a.d, a.n, v.Kp, v.rows, v.Kdev, v.A3, Ahat,
+                                                a.k0, a.k1, a.stream_id, accumulate, a.status);
   ++*launches;
   return cudaGetLastError();
 }

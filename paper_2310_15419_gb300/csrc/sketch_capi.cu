@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "../../include/sketch.h"
+#include "common.cuh"
 #include "handle.h"
 #include "internal.h"
 
@@ -612,6 +613,8 @@ int sketch_device_status(sketch_t h, sketch_stream_t stream) {
   if (v) {
     cudaMemsetAsync(h->d_small, 0, sizeof(int), s);
     cudaStreamSynchronize(s);
+    if (v & kStatusTimeout)
+      return fail(h, SKETCH_ERR_TIMEOUT, "a kernel's bounded wait gave up");
     return fail(h, SKETCH_ERR_CSC, "a kernel met an out-of-range index");
   }
   return SKETCH_OK;
