@@ -314,6 +314,13 @@ int sketch_debug_philox(const uint32_t* ctr, uint64_t seed, uint32_t* out,
 int sketch_debug_normal_pair(const uint32_t* words, float* out, int64_t count,
                              sketch_stream_t stream);
 
+/* The timeout path of the kernels' bounded waits, on purpose: a kernel
+ * waits on an mbarrier phase that nothing completes, gives up after its
+ * iteration limit (well under a second) and records the timeout in the
+ * handle's device status word, so that sketch_device_status then returns
+ * SKETCH_ERR_TIMEOUT; the context stays usable.  Asynchronous. */
+int sketch_debug_wait_timeout(sketch_t h, sketch_stream_t stream);
+
 /* out[t] = S(i[t], j[t]) (FP32) for distribution `dist`, key `seed`, counter
  * word 2 = `stream_id`.  i, j, out are device pointers.  Asynchronous. */
 int sketch_debug_S(int32_t dist, uint64_t seed, uint32_t stream_id,

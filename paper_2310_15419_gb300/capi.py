@@ -103,6 +103,7 @@ SIGNATURES = [
     ("sketch_debug_philox", _I32, [_VP, _U64, _VP, _I64, _VP]),
     ("sketch_debug_S", _I32, [_I32, _U64, _U32, _VP, _VP, _VP, _I64, _VP]),
     ("sketch_debug_normal_pair", _I32, [_VP, _VP, _I64, _VP]),
+    ("sketch_debug_wait_timeout", _I32, [_VP, _VP]),
     ("sketch_set_counting", _I32, [_VP, _I32]),
     ("sketch_generated_entries", _I64, [_VP, _VP]),
     ("sketch_launch_count", _I64, [_VP]),
@@ -429,6 +430,11 @@ def debug_normal_pair(words, stream=None):
                                            ctypes.c_void_p(out.data_ptr()), count,
                                            _stream_ptr(stream)))
     return out
+
+
+def debug_wait_timeout(sketch, stream=None):
+    """Run the bounded-wait timeout path on purpose (see include/sketch.h)."""
+    _check(load().sketch_debug_wait_timeout(sketch.h, _stream_ptr(stream)), sketch.h)
 
 
 def bench_generator(dist, seed, threads, blocks_per_thread, sink, stream=None):

@@ -136,10 +136,10 @@ __device__ __forceinline__ uint64_t umma_desc(uint32_t saddr) {
          (static_cast<uint64_t>((kUmmaSbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
 }
 
-// wait for the phase of parity `parity` of an mbarrier; false after the
-// iteration limit
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-  for (int i = 0; i < (1 << 22); ++i) {
+// wait for the phase of parity `parity` of an mbarrier; false after `limit`
+// polls
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int limit = 1 << 22) {
+  for (int i = 0; i < limit; ++i) {
     uint32_t ok;
     asm volatile(
         "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
@@ -317,6 +317,17 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   __syncthreads();
   if (warp == 0)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" ::"r"(tmem) : "memory");
+}
+
+// The timeout path of mbar_wait on purpose: a fresh mbarrier whose phase
+// nothing completes; the bounded wait gives up and records kStatusTimeout.
+__global__ void k_debug_wait_timeout(int* status, int limit) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    if (!mbar_wait(smem_u32(&bar), 0, limit)) atomicOr(status, kStatusTimeout);
+  }
 }
 
 size_t al256(size_t b) { return (b + 255) / 256 * 256; }
@@ -497,6 +508,11 @@ cudaError_t build_dense_rest(const DenseArgs& a, const DenseView& v, cudaStream_
         v.rest_colptr, const_cast<int32_t*>(v.rest_rowidx),
         static_cast<__nv_bfloat16*>(const_cast<void*>(v.rest_values)));
   ++*launches;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_debug_wait_timeout(int* status, cudaStream_t s) {
+  k_debug_wait_timeout<<<1, 32, 0, s>>>(status, 1 << 14);
   return cudaGetLastError();
 }
 

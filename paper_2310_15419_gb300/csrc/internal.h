@@ -148,6 +148,7 @@ cudaError_t build_dense_panel(const DenseArgs& a, int32_t K, DenseView* v, cudaS
                               int* launches);
 cudaError_t build_dense_rest(const DenseArgs& a, const DenseView& v, cudaStream_t s,
                              int* launches);
+cudaError_t launch_debug_wait_timeout(int* status, cudaStream_t s);
 cudaError_t launch_tc_gemm(const DenseArgs& a, const DenseView& v, float* Ahat,
                            int accumulate, cudaStream_t s, int* launches);
 

@@ -663,6 +663,15 @@ int sketch_debug_normal_pair(const uint32_t* words, float* out, int64_t count,
   return e == cudaSuccess ? SKETCH_OK : cuda_fail(nullptr, e, "debug_normal_pair");
 }
 
+int sketch_debug_wait_timeout(sketch_t h, sketch_stream_t stream) {
+  if (!h) return fail(nullptr, SKETCH_ERR_ARG, "handle is null");
+  int rc = ensure_small(h);
+  if (rc != SKETCH_OK) return rc;
+  cudaError_t e = launch_debug_wait_timeout(reinterpret_cast<int*>(h->d_small),
+                                            reinterpret_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? SKETCH_OK : cuda_fail(h, e, "debug_wait_timeout");
+}
+
 int sketch_debug_S(int32_t dist, uint64_t seed, uint32_t stream_id,
                    const int64_t* i, const int64_t* j, float* out,
                    int64_t count, sketch_stream_t stream) {

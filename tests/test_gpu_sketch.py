@@ -359,6 +359,22 @@ def test_tuned_plan_on_dense_rows_is_exact():
     assert np.array_equal(got, oracle_sketch(A, 300, "pm1"))
 
 
+def test_bounded_wait_times_out_into_status_and_context_survives():
+    """A kernel waits on an mbarrier phase that nothing completes: the wait
+    gives up after its iteration limit, the host reads SKETCH_ERR_TIMEOUT
+    from the status word (once: reading clears it), and the context still
+    sketches correctly afterwards."""
+    A = inputs.integer_uniform(3000, 20, 0.01, seed=36)
+    sk = capi.Sketch(A.m, A.n, 128, "pm1", seed=1)
+    capi.debug_wait_timeout(sk)
+    torch.cuda.synchronize()
+    assert sk.device_status() == capi.SKETCH_ERR_TIMEOUT
+    assert sk.device_status() == capi.SKETCH_OK
+    got = sk.apply(capi.DeviceCSC(A)).cpu().numpy().T
+    sk.close()
+    assert np.array_equal(got, oracle_sketch(A, 128, "pm1"))
+
+
 def test_tensor_core_panel_without_dense_rows_and_bad_dist():
     A = inputs.integer_uniform(4000, 50, 0.01, seed=33)
     got = gpu_sketch(A, 200, "pm1", plan=TC_PLANS[0])
