@@ -98,19 +98,19 @@ __device__ __forceinline__ uint32_t pm1_pair(uint32_t b0, uint32_t b1) {
 
 // ---------------------------------------------------------------------------
 // A_hat(rows d0.., cols n0..) (+)= S3 A3 for a 128 x 128 tile on the
-// 5th-generation tensor cores (tcgen05).  One thread issues `tcgen05.mma.cta_group::1.kind::f16` (M = N = 128, K = 16,
-// BF16 in, FP32 accumulate) with both operands in shared memory and the
-// 128 x 128 accumulator in tensor memory (128 columns, allocated per CTA).
-// Operand tiles (128 rows x 32 k, BF16) use the K-major layout without
-// swizzle: 8-row x 16-byte core matrices, the next one along K 128 bytes on,
-// along M/N 512 bytes on.  The A tile (+-1 S) is built from Philox sign bits,
-// One iteration per 32 dense rows: the A tile (+-1 S, built once) and the
-// three B tiles (the BF16 terms of A3, by cp.async one iteration ahead) form
-// a stage; six MMAs (3 terms x 2 k halves) and one tcgen05.commit per
-// iteration; a stage is reused once that commit has arrived on its
-// mbarrier.  Every wait has
-// an iteration limit: on expiry the CTA records kStatusTimeout, frees its
-// tensor memory and stops.
+// 5th-generation tensor cores (tcgen05).  One thread issues
+// `tcgen05.mma.cta_group::1.kind::f16` (M = N = 128, K = 16, BF16 in, FP32
+// accumulate) with both operands in shared memory and the 128 x 128
+// accumulator in tensor memory (128 columns, allocated per CTA).  Operand
+// tiles (128 rows x 32 k, BF16) use the K-major layout without swizzle:
+// 8-row x 16-byte core matrices, the next one along K 128 bytes on, along
+// M/N 512 bytes on.  One iteration per 32 dense rows: the A tile (+-1 S,
+// built once from Philox sign bits) and the three B tiles (the BF16 terms of
+// A3, by cp.async one iteration ahead) form a stage; six MMAs (3 terms x 2 k
+// halves) and one tcgen05.commit per iteration; a stage is reused once that
+// commit has arrived on its mbarrier.  Every wait has an iteration limit: on
+// expiry the CTA records kStatusTimeout, frees its tensor memory and stops.
+// (N = 256 per CTA measured slower on Abnormal_A: 0.80 against 0.75 ms.)
 constexpr uint32_t kUmmaLbo = 128, kUmmaSbo = 512;
 constexpr int kUmmaTile = 8192;  // bytes of one 128 x 32 BF16 operand tile
 // instruction descriptor: F32 accumulator, BF16 A and B, both K-major,
