@@ -95,7 +95,10 @@ typedef struct {
  * warps share a column's nonzeros.  PANEL: a CTA owns 32 rows of S,
  * `n_block` columns and one of `row_groups` contiguous row ranges of A.
  * TILE: a CTA owns 32 rows of S (d1), 16*cols_per_warp columns (n1) and one
- * of `row_groups` ranges of panels of `panel_rows` rows of A (m1). */
+ * of `row_groups` ranges of panels of `panel_rows` rows of A (m1); its
+ * 32 x n1 running sums sit in registers (tile_acc = 0: 16 warps,
+ * n1 = 16*cols_per_warp) or in tensor memory (tile_acc = 1: 32 warps,
+ * cols_per_warp = 32, n1 = 1024).  Both give the same bits. */
 typedef struct {
   int32_t mode;          /* sketch_mode                                   */
   int32_t q_tiles;       /* REGEN: 1..4 blocks of 128 rows of S per warp  */
@@ -103,13 +106,14 @@ typedef struct {
   int32_t n_block;       /* PANEL: columns per CTA (<= 1536)               */
   int32_t row_groups;    /* PANEL, TILE: number of row ranges of A         */
   int32_t panel_rows;    /* TILE: rows of A per panel, 8..1152 (m1)        */
-  int32_t cols_per_warp; /* TILE: 4, 16 or 64                              */
+  int32_t cols_per_warp; /* TILE: 4, 16 or 64 (32 with tile_acc = 1)       */
   int32_t tc_min_row_nnz;/* +-1 only: rows of A with at least this many     */
                          /* nonzeros form a dense panel multiplied on the   */
                          /* tensor cores (BF16 S, A split exactly into three */
                          /* BF16 terms, FP32 accumulate); 0 = off.  Such a  */
                          /* plan reads the panel height back to the host    */
                          /* once per call (not capturable in a graph).      */
+  int32_t tile_acc;      /* TILE: 0 = register, 1 = tensor-memory sums     */
 } sketch_plan;
 
 /* Create a sketch handle for A (m x n) and S (d x m) with the distribution

@@ -52,7 +52,8 @@ class sketch_plan(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("q_tiles", ctypes.c_int32),
                 ("split", ctypes.c_int32), ("n_block", ctypes.c_int32),
                 ("row_groups", ctypes.c_int32), ("panel_rows", ctypes.c_int32),
-                ("cols_per_warp", ctypes.c_int32), ("tc_min_row_nnz", ctypes.c_int32)]
+                ("cols_per_warp", ctypes.c_int32), ("tc_min_row_nnz", ctypes.c_int32),
+                ("tile_acc", ctypes.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -230,9 +231,10 @@ class Sketch:
         self.m, self.n, self.d = int(m), int(n), int(d)
 
     def set_plan(self, mode=SKETCH_MODE_AUTO, q_tiles=0, split=0, n_block=0,
-                 row_groups=0, panel_rows=0, cols_per_warp=0, tc_min_row_nnz=0):
+                 row_groups=0, panel_rows=0, cols_per_warp=0, tc_min_row_nnz=0,
+                 tile_acc=0):
         p = sketch_plan(mode, q_tiles, split, n_block, row_groups, panel_rows,
-                        cols_per_warp, tc_min_row_nnz)
+                        cols_per_warp, tc_min_row_nnz, tile_acc)
         _check(load().sketch_set_plan(self.h, ctypes.byref(p)), self.h)
 
     def get_plan(self, A: DeviceCSC, stream=None) -> dict:

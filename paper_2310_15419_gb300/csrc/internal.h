@@ -23,7 +23,6 @@ struct RegenArgs {
   int32_t split;    // 1, 2, 4, 8
   int* status;
   unsigned long long* gen_count;  // may be null
-  const int32_t* skip = nullptr;  // rows with skip[j] >= 0 are left out
 };
 cudaError_t launch_regen(const RegenArgs& a, cudaStream_t s);
 
@@ -86,14 +85,14 @@ struct TileArgs {
   int32_t dist;
   int32_t R;    // rows of A per panel (m1)
   int32_t G;    // row groups (partial sums)
-  int32_t cpw;  // columns per warp: 4, 16 or 64 (n1 = 16 * cpw per CTA)
+  int32_t cpw;  // columns per warp: 4, 16 or 64; 32 with tacc (n1 = warps * cpw)
+  int32_t tacc;  // 1: accumulators in tensor memory (32 warps of cpw 32)
   int* status;
   unsigned long long* gen_count;
-  const int32_t* skip = nullptr;  // rows with skip[j] >= 0 are left out
 };
 size_t tile_workspace_bytes(int64_t m, int64_t n, int64_t d, int64_t nnz,
                             int32_t R, int32_t G);
-size_t tile_smem_bytes(int32_t R);
+size_t tile_smem_bytes(int32_t R, int32_t tacc);
 cudaError_t launch_tile(const TileArgs& a, void* ws, cudaStream_t s,
                         int* launches);
 

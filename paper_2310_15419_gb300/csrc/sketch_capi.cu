@@ -11,6 +11,7 @@
 #include <mutex>
 #include <string>
 #include <tuple>
+#include <utility>
 #include <vector>
 
 #include "../../include/sketch.h"
@@ -79,13 +80,18 @@ static size_t align256(size_t b) { return (b + 255) / 256 * 256; }
 // TILE plan for a panel height R: columns per warp covering n (up to 1024
 // per CTA), and row groups that fill the GPU and keep each column's partial
 // sums to ~512 terms.
-sketch_plan tile_plan(const sketch_s* h, const sketch_csc* A, int32_t R) {
+sketch_plan tile_plan(const sketch_s* h, const sketch_csc* A, int32_t R, int32_t tile_acc) {
   sketch_plan p{};
   p.mode = SKETCH_MODE_TILE;
   p.panel_rows = R;
   p.cols_per_warp = A->n <= 64 ? 4 : A->n <= 256 ? 16 : 64;
+  if (tile_acc && p.cols_per_warp == 64) {  // 32 warps of 32 columns
+    p.tile_acc = 1;
+    p.cols_per_warp = 32;
+  }
+  const int64_t n1 = (p.tile_acc ? 32 : 16) * p.cols_per_warp;
   const int64_t tiles = (h->d + 31) / 32;
-  const int64_t cblocks = (A->n + 16 * p.cols_per_warp - 1) / (16 * p.cols_per_warp);
+  const int64_t cblocks = (A->n + n1 - 1) / n1;
   const int64_t P = (A->m + R - 1) / R;
   const double avg_col = A->n > 0 ? double(A->nnz) / double(A->n) : 0.0;
   const int per_sm = 1;
@@ -107,7 +113,7 @@ sketch_plan heuristic_plan(const sketch_s* h, const sketch_csc* A) {
     p.q_tiles = std::max(1, q);
     p.split = avg_col >= 4096 ? 8 : avg_col >= 1024 ? 4 : avg_col >= 256 ? 2 : 1;
   } else {
-    p = tile_plan(h, A, 1024);
+    p = A->n > 256 ? tile_plan(h, A, 1152, 1) : tile_plan(h, A, 1024, 0);
   }
   return p;
 }
@@ -174,8 +180,13 @@ int check_plan(sketch_t h, const sketch_plan& p) {
   } else if (p.mode == SKETCH_MODE_TILE) {
     if (p.panel_rows < 8 || p.panel_rows > 1152)
       return fail(h, SKETCH_ERR_ARG, "panel_rows must be 8..1152");
-    if (p.cols_per_warp != 4 && p.cols_per_warp != 16 && p.cols_per_warp != 64)
+    if (p.tile_acc != 0 && p.tile_acc != 1)
+      return fail(h, SKETCH_ERR_ARG, "tile_acc must be 0 or 1");
+    if (p.tile_acc == 0 && p.cols_per_warp != 4 && p.cols_per_warp != 16 &&
+        p.cols_per_warp != 64)
       return fail(h, SKETCH_ERR_ARG, "cols_per_warp must be 4, 16 or 64");
+    if (p.tile_acc == 1 && p.cols_per_warp != 32)
+      return fail(h, SKETCH_ERR_ARG, "tile_acc = 1 needs cols_per_warp = 32");
     if (p.row_groups < 1 || p.row_groups > 65535)
       return fail(h, SKETCH_ERR_ARG, "row_groups must be 1..65535");
   } else if (p.mode != SKETCH_MODE_AUTO) {
@@ -185,8 +196,7 @@ int check_plan(sketch_t h, const sketch_plan& p) {
 }
 
 int run_sparse(sketch_t h, const sketch_csc* A, float* Ahat, const sketch_plan& p,
-               void* ws, cudaStream_t s, int* status, unsigned long long* gen,
-               const int32_t* skip);
+               void* ws, cudaStream_t s, int* status, unsigned long long* gen);
 
 // Run one plan.  `ws` must hold plan_workspace_bytes.
 int run_plan(sketch_t h, const sketch_csc* A, float* Ahat,
@@ -258,7 +268,7 @@ int run_plan(sketch_t h, const sketch_csc* A, float* Ahat,
       rest.values = dv.rest_values;
       rest.nnz = rest_nnz;
     }
-    rc_sparse = run_sparse(h, &rest, Ahat, p, ws, s, status, gen, nullptr);
+    rc_sparse = run_sparse(h, &rest, Ahat, p, ws, s, status, gen);
   }
   if (rc_sparse != SKETCH_OK || K == 0) return rc_sparse;
   int nl = 0;
@@ -268,8 +278,7 @@ int run_plan(sketch_t h, const sketch_csc* A, float* Ahat,
 }
 
 int run_sparse(sketch_t h, const sketch_csc* A, float* Ahat, const sketch_plan& p,
-               void* ws, cudaStream_t s, int* status, unsigned long long* gen,
-               const int32_t* skip) {
+               void* ws, cudaStream_t s, int* status, unsigned long long* gen) {
   if (p.mode == SKETCH_MODE_REGEN) {
     RegenArgs a{};
     a.m = static_cast<int32_t>(A->m);
@@ -288,7 +297,6 @@ int run_sparse(sketch_t h, const sketch_csc* A, float* Ahat, const sketch_plan& 
     a.split = p.split;
     a.status = status;
     a.gen_count = gen;
-    a.skip = skip;
     cudaError_t e = launch_regen(a, s);
     h->launches += 1;
     return e == cudaSuccess ? SKETCH_OK : cuda_fail(h, e, "regen kernel");
@@ -312,9 +320,9 @@ int run_sparse(sketch_t h, const sketch_csc* A, float* Ahat, const sketch_plan& 
     a.G = std::min<int32_t>(p.row_groups,
                             static_cast<int32_t>((A->m + p.panel_rows - 1) / p.panel_rows));
     a.cpw = p.cols_per_warp;
+    a.tacc = p.tile_acc;
     a.status = status;
     a.gen_count = gen;
-    a.skip = skip;
     int nl = 0;
     cudaError_t e = launch_tile(a, ws, s, &nl);
     h->launches += nl;
@@ -363,11 +371,13 @@ static std::vector<sketch_plan> candidates(const sketch_s* h, const sketch_csc* 
       if (!dup) c.push_back(p);
     }
   }
-  // TILE panel heights (the S tile takes R * 128 bytes of shared memory)
-  for (int32_t R : {1024, 512}) {
-    sketch_plan p = tile_plan(h, A, R);
-    if (tile_workspace_bytes(A->m, A->n, h->d, A->nnz, R, p.row_groups) <=
-        (size_t(8) << 30))
+  // TILE panel heights (the S tile takes R * 128 bytes of shared memory):
+  // register sums at 1024 and 512 rows, and for n > 256 the tensor-memory
+  // sums (32 warps per CTA) at 1152 and 1024
+  for (auto [R, tacc] : {std::pair<int32_t, int32_t>{1024, 0}, {512, 0}, {1152, 1}, {1024, 1}}) {
+    sketch_plan p = tile_plan(h, A, R, tacc);
+    if (p.tile_acc != tacc) continue;
+    if (tile_workspace_bytes(A->m, A->n, h->d, A->nnz, R, p.row_groups) <= (size_t(8) << 30))
       c.push_back(p);
   }
   // +-1 S: densified panels on the tensor cores for rows holding at least

@@ -48,8 +48,7 @@ __device__ __forceinline__ unsigned long long regen_accumulate(
     int32_t lo, int32_t hi, int32_t m, int32_t d0, int rows_valid,
     const int32_t* __restrict__ rowidx, const VT* __restrict__ vals,
     uint32_t k0, uint32_t k1, uint32_t stream_id, int* status,
-    uint32_t (*stage)[4 * Q + 4], float (&outer)[Q][4],
-    const int32_t* __restrict__ skip = nullptr) {
+    uint32_t (*stage)[4 * Q + 4], float (&outer)[Q][4]) {
   const int lane = threadIdx.x & 31;
   // Two-level sums: a batch of 32 nonzeros accumulates in `inner`, batch
   // sums are added to `outer` with Kahan compensation (`comp`), so the FP32
@@ -77,8 +76,6 @@ __device__ __forceinline__ unsigned long long regen_accumulate(
         atomicOr(status, kStatusBadRow);
         j = 0;
         a = 0.f;
-      } else if (skip && skip[j] >= 0) {
-        a = 0.f;  // a densified row: the tensor-core panel covers it
       }
     }
     generated += static_cast<unsigned long long>(cnt) * rows_valid;
@@ -152,7 +149,7 @@ __global__ void __launch_bounds__(kRegenWarps * 32, 2)
             const int32_t* __restrict__ rowidx, const VT* __restrict__ vals,
             float* __restrict__ Ahat, uint32_t k0, uint32_t k1,
             uint32_t stream_id, int* status,
-            unsigned long long* gen_count, const int32_t* __restrict__ skip) {
+            unsigned long long* gen_count) {
   constexpr int TD = 128 * Q;          // rows of S per item
   constexpr int SW = 4 * Q + 4;        // staged words per nonzero (+pad)
   __shared__ float red[kRegenWarps][TD];
@@ -188,7 +185,7 @@ __global__ void __launch_bounds__(kRegenWarps * 32, 2)
     const int32_t hi = p0 + min(len, (sub + 1) * chunk);
     generated = regen_accumulate<DIST, Q, VT>(lo, hi, m, d0, min(TD, d - d0), rowidx,
                                              vals, k0, k1, stream_id, status,
-                                             stage[warp], outer, skip);
+                                             stage[warp], outer);
   }
 
   if (split == 1) {
@@ -321,7 +318,7 @@ static cudaError_t launch_regen_q(const RegenArgs& a, cudaStream_t s) {
   case QQ:                                                                  \
     k_regen<DIST, QQ, VT><<<grid, block, 0, s>>>(                           \
         a.m, a.n, a.d, a.split, a.colptr, a.rowidx, v, a.Ahat, a.k0, a.k1, \
-        a.stream_id, a.status, a.gen_count, a.skip);                        \
+        a.stream_id, a.status, a.gen_count);                                \
     break;
   switch (a.q_tiles) {
     SK_REGEN_CASE(1)
@@ -733,8 +730,13 @@ cudaError_t launch_panel(const PanelArgs& a, cudaStream_t s, int* launches) {
 // accumulators (lane = row of S), reading S from shared memory.  No atomics;
 // each output is written once per row group, so results are deterministic.
 // ---------------------------------------------------------------------------
-constexpr int kTileWarps = 16;
-constexpr int kTileWarpBuf = 512;  // staged nonzeros per warp per panel
+// Warps per CTA: 16 with register sums (64 columns each), 32 with
+// tensor-memory sums (32 columns each); n1 = 1024 columns either way.
+__host__ __device__ constexpr int tile_warps(bool tacc) { return tacc ? 32 : 16; }
+// Staged nonzeros per warp and panel (a panel that holds more for a warp's
+// columns sweeps the rest from global memory): 512, or 256 for the warps of
+// half as many columns.
+__host__ __device__ constexpr int tile_warp_buf(bool tacc) { return tacc ? 256 : 512; }
 
 // Panel-major copy of A for TILE: nonzeros sorted by (panel, column, row),
 // each stored as (row within its panel, value bits).  For panel p and column
@@ -783,8 +785,7 @@ __global__ void k_panel_copy(int32_t n, int32_t P, int32_t R, int32_t m,
                              const VT* __restrict__ vals,
                              const int32_t* __restrict__ pp,
                              const int32_t* __restrict__ off,
-                             int2* __restrict__ packed, int* status,
-                             const int32_t* __restrict__ skip) {
+                             int2* __restrict__ packed, int* status) {
   const int64_t total = static_cast<int64_t>(P) * n;
   for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
        t < total; t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
@@ -795,8 +796,7 @@ __global__ void k_panel_copy(int32_t n, int32_t P, int32_t R, int32_t m,
     for (int32_t e = lo; e < hi; ++e, ++dst) {
       const int32_t jl = rowidx[e] - j0;
       if (static_cast<uint32_t>(jl) < static_cast<uint32_t>(R) && j0 + jl < m) {
-        const float a = (skip && skip[j0 + jl] >= 0) ? 0.f : to_f32(vals[e]);
-        packed[dst] = make_int2(jl * 32, __float_as_int(a));
+        packed[dst] = make_int2(jl * 32, __float_as_int(to_f32(vals[e])));
       } else {
         atomicOr(status, kStatusBadRow);
         packed[dst] = make_int2(0, 0);
@@ -805,14 +805,53 @@ __global__ void k_panel_copy(int32_t n, int32_t P, int32_t R, int32_t m,
   }
 }
 
-template <int DIST, int CPW>
-__global__ void __launch_bounds__(kTileWarps * 32, 1)
+// Tensor-memory accumulators for TILE (tcgen05.ld / tcgen05.st, shape
+// 32x32b: thread t of a warp reads or writes lane 32 * (warp % 4) + t, four
+// consecutive 32-bit columns).  The waits take the loaded registers as
+// operands so no use of them is scheduled before the data has landed.
+__device__ __forceinline__ void tmem_ld4(uint32_t taddr, uint32_t (&r)[4]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(taddr)
+               : "memory");
+}
+__device__ __forceinline__ void tmem_wait_ld4(uint32_t (&r)[4]) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3])
+               :
+               : "memory");
+}
+__device__ __forceinline__ void tmem_st4(uint32_t taddr, float4 v) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(taddr),
+               "r"(__float_as_uint(v.x)), "r"(__float_as_uint(v.y)),
+               "r"(__float_as_uint(v.z)), "r"(__float_as_uint(v.w))
+               : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() {
+  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
+// TACC = false: 16 warps; the CTA's 32 x (16 * CPW) accumulators live in
+// registers (64 per thread at CPW = 64), so one CTA fills an SM's register
+// file with 4 warps per scheduler.
+// TACC = true (CPW = 32 only): 32 warps, and the 32 x 1024 accumulators live
+// in tensor memory, 256 columns per CTA (warp w: lanes 32 (w % 4) ..,
+// columns 32 (w / 4) ..), each quad's float4 read, added to and written back
+// after its sweep; at <= 64 registers per thread the SM runs 8 warps per
+// scheduler with the same panel height.
+template <int DIST, int CPW, bool TACC>
+__global__ void __launch_bounds__(tile_warps(TACC) * 32, 1)
     k_tile(int32_t m, int32_t n, int32_t d, int32_t R, int32_t P, int32_t G,
            const int2* __restrict__ packed, const int32_t* __restrict__ off,
            float* __restrict__ out, uint32_t k0, uint32_t k1,
            uint32_t stream_id, unsigned long long* gen_count) {
   static_assert(CPW % 4 == 0, "columns per warp come in quads");
-  // shared memory: S tile [R][32] floats, then per-warp nonzero buffers
+  static_assert(!TACC || CPW == 32, "tensor-memory accumulators take 32 columns per warp");
+  constexpr int kWarps = tile_warps(TACC);
+  constexpr uint32_t kTmemCols = (kWarps / 4) * CPW;  // kWarps / 4 warps per lane quarter
+  constexpr int wbuf = tile_warp_buf(TACC);
+  // shared memory: S tile [R][32] floats, per-warp nonzero buffers (wbuf
+  // entries + a zero entry), per-warp column offsets, the tensor-memory base
   extern __shared__ __align__(16) float smem[];
   float* S_tile = smem;
   int2* ent_all = reinterpret_cast<int2*>(smem + static_cast<size_t>(R) * 32);
@@ -822,13 +861,14 @@ __global__ void __launch_bounds__(kTileWarps * 32, 1)
   // lane = (column group cg, rows 4*i4 .. 4*i4+3 of the tile): the warp works
   // on four columns at a time, eight lanes (32 rows of S) per column
   const int cg = lane >> 3, i4 = lane & 7;
-  int2* ent = ent_all + warp * (kTileWarpBuf + 1);
-  if (lane == 0) ent[kTileWarpBuf] = make_int2(0, 0);  // the zero entry
+  int2* ent = ent_all + warp * (wbuf + 1);
+  if (lane == 0) ent[wbuf] = make_int2(0, 0);  // the zero entry
   // this warp's column offsets for the current panel (CPW + 1 values)
-  int32_t* offs = reinterpret_cast<int32_t*>(ent_all + kTileWarps * (kTileWarpBuf + 1)) +
-                  warp * (CPW + 4);
+  int32_t* offs_all = reinterpret_cast<int32_t*>(ent_all + kWarps * (wbuf + 1));
+  int32_t* offs = offs_all + warp * (CPW + 4);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(offs_all + kWarps * (CPW + 4));
   // this warp's columns: kw0 .. kw0 + ncol - 1 (contiguous)
-  const int32_t kw0 = blockIdx.y * (kTileWarps * CPW) + warp * CPW;
+  const int32_t kw0 = blockIdx.y * (kWarps * CPW) + warp * CPW;
   const int32_t ncol = max(0, min(CPW, n - kw0));
   const int32_t pa = static_cast<int32_t>(static_cast<int64_t>(P) * g / G);
   const int32_t pb = static_cast<int32_t>(static_cast<int64_t>(P) * (g + 1) / G);
@@ -837,11 +877,27 @@ __global__ void __launch_bounds__(kTileWarps * 32, 1)
   constexpr int OFFR = (CPW + 32) / 32;  // registers holding CPW + 1 offsets
   constexpr int NQ = CPW / 4;
 
-  float4 acc[NQ];
+  float4 acc[TACC ? 1 : NQ];
+  uint32_t tacc = 0;  // this warp's first accumulator column in tensor memory
+  if constexpr (TACC) {
+    if (warp == 0) {
+      asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                       static_cast<uint32_t>(__cvta_generic_to_shared(tmem_slot))),
+                   "r"(kTmemCols)
+                   : "memory");
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    tacc = *tmem_slot + (static_cast<uint32_t>(32 * (warp & 3)) << 16) +
+           static_cast<uint32_t>(CPW * (warp >> 2));
 #pragma unroll
-  for (int q = 0; q < NQ; ++q) acc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
-  unsigned long long generated = 0;
-
+    for (int q = 0; q < NQ; ++q) tmem_st4(tacc + 4 * q, make_float4(0.f, 0.f, 0.f, 0.f));
+    tmem_wait_st();
+  } else {
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) acc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
   // this warp's column offsets of panel p (CPW + 1 values over OFFR
   // registers); the next panel's are loaded while the current one is swept
   int32_t offv[OFFR];
@@ -864,8 +920,12 @@ __global__ void __launch_bounds__(kTileWarps * 32, 1)
     int32_t e_lo = 0;
     if (ncol > 0) {
       e_lo = __shfl_sync(0xffffffffu, offv[0], 0);
-      const int32_t e_hi = __shfl_sync(0xffffffffu, offv[ncol >> 5], ncol & 31);
-      const int32_t cnt = min(e_hi - e_lo, kTileWarpBuf);
+      int32_t o_end = offv[0];  // offv[ncol >> 5] without a dynamic index
+#pragma unroll
+      for (int u = 1; u < OFFR; ++u)
+        if ((ncol >> 5) == u) o_end = offv[u];
+      const int32_t e_hi = __shfl_sync(0xffffffffu, o_end, ncol & 31);
+      const int32_t cnt = min(e_hi - e_lo, wbuf);
       for (int32_t t = lane; t < cnt; t += 32) {
         const unsigned dst = static_cast<unsigned>(__cvta_generic_to_shared(ent + t));
         asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst),
@@ -879,7 +939,7 @@ __global__ void __launch_bounds__(kTileWarps * 32, 1)
       }
     }
     // ---- S(tile, j0 .. j0 + rows) once into shared memory ---------------
-    for (int idx = threadIdx.x; idx < rows * 8; idx += kTileWarps * 32) {
+    for (int idx = threadIdx.x; idx < rows * 8; idx += kWarps * 32) {
       const int jl = idx >> 3, q = idx & 7;
       const uint32_t j = static_cast<uint32_t>(j0 + jl);
       float4 v;
@@ -896,13 +956,15 @@ __global__ void __launch_bounds__(kTileWarps * 32, 1)
       }
       *reinterpret_cast<float4*>(&S_tile[jl * 32 + 4 * q]) = v;
     }
-    generated += static_cast<unsigned long long>(rows) * rows_valid;
     asm volatile("cp.async.wait_all;" ::: "memory");
     __syncthreads();
     load_offsets(p + 1);  // used by the next panel; lands during the sweep
     // ---- sweep: four columns per step, one per group of eight lanes ------
-    const int32_t buf_end = e_lo + kTileWarpBuf;
-#pragma unroll
+    const int32_t buf_end = e_lo + wbuf;
+    // register sums need the quad index at compile time; tensor-memory sums
+    // do not, and a rolled loop keeps them within 64 registers
+    constexpr int kQuadUnroll = TACC ? 1 : NQ;
+#pragma unroll kQuadUnroll
     for (int q = 0; q < NQ; ++q) {
       if (4 * q < ncol) {  // warp-uniform
         const int c = 4 * q + cg;  // this lane's column slot (differs by group)
@@ -912,11 +974,11 @@ __global__ void __launch_bounds__(kTileWarps * 32, 1)
         float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
         if (__all_sync(0xffffffffu, c >= ncol || hi <= buf_end)) {
           // fast path: every entry is staged; lanes past their column's end
-          // read the zero entry at ent[kTileWarpBuf] (no branch per step).
+          // read the zero entry at ent[wbuf] (no branch per step).
           // Two steps per iteration with separate accumulators: both
           // entries, then both S loads, then the FMAs (more loads in flight)
           const int2* ep = ent + (lo - e_lo);
-          const int2* zero = ent + kTileWarpBuf;
+          const int2* zero = ent + wbuf;
           float4 w = make_float4(0.f, 0.f, 0.f, 0.f);
           int32_t t = 0;
           for (; t + 1 < steps; t += 2) {
@@ -948,7 +1010,11 @@ __global__ void __launch_bounds__(kTileWarps * 32, 1)
           v.z += w.z;
           v.w += w.w;
         } else {
-          for (int32_t t = 0; t < steps; ++t) {
+          // entries read from global memory; the same split of the sum
+          // (even steps into v, odd steps into w) as the fast path, so the
+          // bits do not depend on how much of the panel was staged
+          float4 w = make_float4(0.f, 0.f, 0.f, 0.f);
+          for (int32_t t = 0; t < steps; t += 2) {
             if (t < cnt) {
               const int2 ja = packed[lo + t];
               const float a = __int_as_float(ja.y);
@@ -958,29 +1024,78 @@ __global__ void __launch_bounds__(kTileWarps * 32, 1)
               v.z = fmaf(a, sv.z, v.z);
               v.w = fmaf(a, sv.w, v.w);
             }
+            if (t + 1 < cnt) {
+              const int2 jb = packed[lo + t + 1];
+              const float b = __int_as_float(jb.y);
+              const float4 sv = *reinterpret_cast<const float4*>(S_lane + jb.x);
+              w.x = fmaf(b, sv.x, w.x);
+              w.y = fmaf(b, sv.y, w.y);
+              w.z = fmaf(b, sv.z, w.z);
+              w.w = fmaf(b, sv.w, w.w);
+            }
           }
+          v.x += w.x;
+          v.y += w.y;
+          v.z += w.z;
+          v.w += w.w;
         }
-        acc[q].x += v.x;
-        acc[q].y += v.y;
-        acc[q].z += v.z;
-        acc[q].w += v.w;
+        if constexpr (TACC) {
+          uint32_t prev[4];  // the quad's running sums
+          tmem_ld4(tacc + 4 * q, prev);
+          tmem_wait_ld4(prev);
+          tmem_st4(tacc + 4 * q,
+                   make_float4(__uint_as_float(prev[0]) + v.x, __uint_as_float(prev[1]) + v.y,
+                               __uint_as_float(prev[2]) + v.z, __uint_as_float(prev[3]) + v.w));
+        } else {
+          acc[q].x += v.x;
+          acc[q].y += v.y;
+          acc[q].z += v.z;
+          acc[q].w += v.w;
+        }
       }
     }
+    // TACC: this panel's stores complete before the next panel reads them
+    if constexpr (TACC) tmem_wait_st();
     __syncthreads();
   }
   // ---- write this row group's partial sums -------------------------------
 #pragma unroll
   for (int q = 0; q < NQ; ++q) {
     const int c = 4 * q + cg;
-    if (c < ncol) {
-      float* o = out + (static_cast<int64_t>(g) * n + kw0 + c) * d + tile * 32 + 4 * i4;
-      if (4 * i4 + 0 < rows_valid) o[0] = acc[q].x;
-      if (4 * i4 + 1 < rows_valid) o[1] = acc[q].y;
-      if (4 * i4 + 2 < rows_valid) o[2] = acc[q].z;
-      if (4 * i4 + 3 < rows_valid) o[3] = acc[q].w;
+    if (4 * q < ncol) {  // warp-uniform
+      float4 r;
+      if constexpr (TACC) {
+        uint32_t t[4];
+        tmem_ld4(tacc + 4 * q, t);
+        tmem_wait_ld4(t);
+        r = make_float4(__uint_as_float(t[0]), __uint_as_float(t[1]), __uint_as_float(t[2]),
+                        __uint_as_float(t[3]));
+      } else {
+        r = acc[q];
+      }
+      if (c < ncol) {
+        float* o = out + (static_cast<int64_t>(g) * n + kw0 + c) * d + tile * 32 + 4 * i4;
+        if (4 * i4 + 0 < rows_valid) o[0] = r.x;
+        if (4 * i4 + 1 < rows_valid) o[1] = r.y;
+        if (4 * i4 + 2 < rows_valid) o[2] = r.z;
+        if (4 * i4 + 3 < rows_valid) o[3] = r.w;
+      }
     }
   }
-  if (gen_count && threadIdx.x == 0 && generated) atomicAdd(gen_count, generated);
+  if constexpr (TACC) {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(*tmem_slot),
+                   "r"(kTmemCols)
+                   : "memory");
+  }
+  // S entries generated: rows_valid for every row of the CTA's panels
+  if (gen_count && threadIdx.x == 0 && pb > pa) {
+    const int64_t rows_done =
+        min(static_cast<int64_t>(pb) * R, static_cast<int64_t>(m)) - static_cast<int64_t>(pa) * R;
+    atomicAdd(gen_count, static_cast<unsigned long long>(rows_done * rows_valid));
+  }
 }
 
 size_t tile_workspace_bytes(int64_t m, int64_t n, int64_t d, int64_t nnz,
@@ -994,10 +1109,11 @@ size_t tile_workspace_bytes(int64_t m, int64_t n, int64_t d, int64_t nnz,
   return b;
 }
 
-size_t tile_smem_bytes(int32_t R) {
+size_t tile_smem_bytes(int32_t R, int32_t tacc) {
   return static_cast<size_t>(R) * 32 * sizeof(float) +
-         kTileWarps * (kTileWarpBuf + 1) * sizeof(int2) +
-         kTileWarps * (64 + 4) * sizeof(int32_t);  // offsets, up to 64 columns per warp
+         tile_warps(tacc != 0) * (tile_warp_buf(tacc != 0) + 1) * sizeof(int2) +
+         tile_warps(tacc != 0) * ((tacc ? 32 : 64) + 4) * sizeof(int32_t) +  // offsets
+         16;                                         // tensor-memory base address
 }
 
 cudaError_t launch_tile(const TileArgs& a, void* ws, cudaStream_t s, int* launches) {
@@ -1033,38 +1149,42 @@ cudaError_t launch_tile(const TileArgs& a, void* ws, cudaStream_t s, int* launch
     if (a.dtype == 0)
       k_panel_copy<float><<<grid_for(P * a.n), 256, 0, s>>>(
           a.n, static_cast<int32_t>(P), a.R, a.m, a.rowidx,
-          static_cast<const float*>(a.values), pp, off, packed, a.status, a.skip);
+          static_cast<const float*>(a.values), pp, off, packed, a.status);
     else
       k_panel_copy<__nv_bfloat16><<<grid_for(P * a.n), 256, 0, s>>>(
           a.n, static_cast<int32_t>(P), a.R, a.m, a.rowidx,
-          static_cast<const __nv_bfloat16*>(a.values), pp, off, packed, a.status, a.skip);
+          static_cast<const __nv_bfloat16*>(a.values), pp, off, packed, a.status);
     ++*launches;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
-  const int cols_per_cta = kTileWarps * a.cpw;
+  const int cols_per_cta = tile_warps(a.tacc != 0) * a.cpw;
   const int tiles = (a.d + 31) / 32;
   const int cblocks = (a.n + cols_per_cta - 1) / cols_per_cta;
   if (cblocks > 65535 || a.G > 65535) return cudaErrorInvalidValue;
-  const dim3 grid(tiles, cblocks, a.G), block(kTileWarps * 32);
-  const size_t smem = tile_smem_bytes(a.R);
+  const dim3 grid(tiles, cblocks, a.G), block(tile_warps(a.tacc != 0) * 32);
+  const size_t smem = tile_smem_bytes(a.R, a.tacc);
   float* dst = a.G == 1 ? a.Ahat : partial;
-#define SK_TILE_CASE(DD, CC)                                                     \
-  if (a.dist == DD && a.cpw == CC) {                                             \
-    e = cudaFuncSetAttribute(k_tile<DD, CC>,                                     \
+  if (a.tacc && a.cpw != 32) return cudaErrorInvalidValue;
+#define SK_TILE_CASE(DD, CC, TT)                                                 \
+  if (a.dist == DD && a.cpw == CC && (a.tacc != 0) == TT) {                      \
+    e = cudaFuncSetAttribute(k_tile<DD, CC, TT>,                                 \
                              cudaFuncAttributeMaxDynamicSharedMemorySize,        \
                              static_cast<int>(smem));                            \
     if (e != cudaSuccess) return e;                                              \
-    k_tile<DD, CC><<<grid, block, smem, s>>>(a.m, a.n, a.d, a.R,                 \
-                                             static_cast<int32_t>(P), a.G,       \
-                                             packed, off, dst, a.k0, a.k1,       \
-                                             a.stream_id, a.gen_count);          \
+    k_tile<DD, CC, TT><<<grid, block, smem, s>>>(a.m, a.n, a.d, a.R,             \
+                                                 static_cast<int32_t>(P), a.G,   \
+                                                 packed, off, dst, a.k0, a.k1,   \
+                                                 a.stream_id, a.gen_count);      \
     ++*launches;                                                                 \
     launched = true;                                                             \
   }
   bool launched = false;
-  SK_TILE_CASE(kPM1, 4) SK_TILE_CASE(kPM1, 16) SK_TILE_CASE(kPM1, 64)
-  SK_TILE_CASE(kUniform, 4) SK_TILE_CASE(kUniform, 16) SK_TILE_CASE(kUniform, 64)
-  SK_TILE_CASE(kNormal, 4) SK_TILE_CASE(kNormal, 16) SK_TILE_CASE(kNormal, 64)
+  SK_TILE_CASE(kPM1, 4, false) SK_TILE_CASE(kPM1, 16, false) SK_TILE_CASE(kPM1, 64, false)
+  SK_TILE_CASE(kUniform, 4, false) SK_TILE_CASE(kUniform, 16, false)
+  SK_TILE_CASE(kUniform, 64, false)
+  SK_TILE_CASE(kNormal, 4, false) SK_TILE_CASE(kNormal, 16, false)
+  SK_TILE_CASE(kNormal, 64, false)
+  SK_TILE_CASE(kPM1, 32, true) SK_TILE_CASE(kUniform, 32, true) SK_TILE_CASE(kNormal, 32, true)
 #undef SK_TILE_CASE
   if (!launched) return cudaErrorInvalidValue;
   if ((e = cudaGetLastError()) != cudaSuccess) return e;

@@ -53,8 +53,9 @@ REGEN_PLANS = [dict(mode=capi.SKETCH_MODE_REGEN, q_tiles=q, split=s)
 PANEL_PLANS = [dict(mode=capi.SKETCH_MODE_PANEL, n_block=nb, row_groups=g)
                for nb, g in ((37, 1), (16, 3), (5, 7), (37, 64))]
 TILE_PLANS = [dict(mode=capi.SKETCH_MODE_TILE, panel_rows=r, row_groups=g,
-                   cols_per_warp=c)
-              for r, g, c in ((1024, 1, 4), (768, 3, 16), (100, 7, 64), (8, 50, 4))]
+                   cols_per_warp=c, tile_acc=t)
+              for r, g, c, t in ((1024, 1, 4, 0), (768, 3, 16, 0), (100, 7, 64, 0),
+                                 (8, 50, 4, 0), (512, 3, 32, 1), (8, 50, 32, 1))]
 
 
 # ---------------------------------------------------------------- generator
@@ -129,6 +130,38 @@ def test_float_within_tolerance_every_plan(dist, plan):
     ref = oracle_sketch(A, 301, dist)
     got = gpu_sketch(A, 301, dist, plan=plan)
     assert rel_fro(got, ref) <= TOL
+
+
+@pytest.mark.parametrize("dist", ["pm1", "uniform", "normal"])
+def test_tile_tensor_memory_sums_equal_register_sums(dist):
+    """TILE keeps a CTA's running sums in registers (16 warps x 64 columns)
+    or in tensor memory (32 warps x 32 columns); the additions are the same,
+    so the bits are.  n = 1100 spreads columns over every warp (all four
+    tensor-memory lane quarters) and two column blocks, the last one ragged;
+    d = 100 leaves a ragged row tile."""
+    A = inputs.float_uniform(3000, 1100, 0.01, seed=21)
+    d = 100
+    outs = []
+    for tacc, cpw in ((0, 64), (1, 32)):
+        for r, g in ((1024, 2), (136, 1)):
+            outs.append(gpu_sketch(A, d, dist, plan=dict(
+                mode=capi.SKETCH_MODE_TILE, panel_rows=r, row_groups=g, cols_per_warp=cpw,
+                tile_acc=tacc)))
+    assert np.array_equal(outs[0], outs[2]) and np.array_equal(outs[1], outs[3])
+    ref = oracle_sketch(A, d, dist)
+    assert rel_fro(outs[2], ref) <= TOL and rel_fro(outs[3], ref) <= TOL
+
+
+def test_tile_tensor_memory_plan_checks():
+    sk = capi.Sketch(1000, 100, 64, "uniform", seed=1)
+    for bad in (dict(panel_rows=1024, row_groups=1, cols_per_warp=64, tile_acc=1),
+                dict(panel_rows=512, row_groups=1, cols_per_warp=16, tile_acc=1),
+                dict(panel_rows=512, row_groups=1, cols_per_warp=32, tile_acc=0),
+                dict(panel_rows=512, row_groups=1, cols_per_warp=32, tile_acc=2)):
+        with pytest.raises(capi.SketchError) as e:
+            sk.set_plan(capi.SKETCH_MODE_TILE, **bad)
+        assert e.value.code == capi.SKETCH_ERR_ARG
+    sk.close()
 
 
 def test_uniform_integer_values_exact_in_integer_scale():
@@ -262,14 +295,22 @@ def skew_large():
     return inputs.skew_large()
 
 
-@pytest.mark.parametrize("dist", ["pm1", "uniform", "normal"])
-def test_skew_large_sampled_columns(skew_large, dist):
+SKEW_TACC = dict(mode=capi.SKETCH_MODE_TILE, panel_rows=1024, row_groups=20,
+                 cols_per_warp=32, tile_acc=1)
+
+
+@pytest.mark.parametrize("dist,plan", [("pm1", None), ("uniform", None), ("normal", None),
+                                       ("normal", SKEW_TACC)])
+def test_skew_large_sampled_columns(skew_large, dist, plan):
     """m=2e6, n=1000, d=3000, ~1e7 nnz, power-law rows: the tuned launch the
-    benchmark times, checked on sampled columns (columns of A_hat depend
-    only on the matching column of A, so the oracle computes them alone)."""
+    benchmark times (and TILE with tensor-memory sums), checked on sampled
+    columns (columns of A_hat depend only on the matching column of A, so the
+    oracle computes them alone)."""
     A = skew_large
     d = inputs.SKEW_LARGE_D
     sk = capi.Sketch(A.m, A.n, d, dist, seed=1)
+    if plan:
+        sk.set_plan(**plan)
     dA = capi.DeviceCSC(A)
     out = sk.apply(dA)
     torch.cuda.synchronize()
