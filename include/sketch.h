@@ -305,8 +305,11 @@ double sketch_server_now(sketch_server_t srv);
 int sketch_server_destroy(sketch_server_t srv);
 
 /* ---- test hooks: the generator and S itself --------------------------- */
-/* out[4t..4t+3] = Philox4x32-10(ctr[4t..4t+3], key = seed) for t < count.
- * ctr and out are device pointers.  Sec. 4.2.  Asynchronous. */
+/* out[4t..4t+3] = Philox4x32-10(ctr[4t..4t+3], key = seed) for t < count,
+ * computed with the key advanced round by round; out[4(count+t)..] holds
+ * the same blocks from the ten precomputed round keys (the form the TILE
+ * kernel and the generator benchmark use).  ctr (4 count words) and out
+ * (8 count words) are device pointers.  Sec. 4.2.  Asynchronous. */
 int sketch_debug_philox(const uint32_t* ctr, uint64_t seed, uint32_t* out,
                         int64_t count, sketch_stream_t stream);
 

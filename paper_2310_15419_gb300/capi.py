@@ -410,16 +410,18 @@ def validate_csc(A: DeviceCSC, stream=None) -> int:
     return load().sketch_validate_csc(ctypes.byref(A.desc), _stream_ptr(stream))
 
 
-def debug_philox(ctr, seed, stream=None):
-    """ctr: int tensor (count, 4) of uint32 values on the GPU (as int32 bits)."""
+def debug_philox(ctr, seed, stream=None, both=False):
+    """ctr: int tensor (count, 4) of uint32 values on the GPU (as int32 bits).
+    Returns the (count, 4) blocks; with both=True a pair (running-key form,
+    round-key form)."""
     import torch
     count = ctr.shape[0]
-    out = torch.empty((count, 4), dtype=torch.int32, device=ctr.device)
+    out = torch.empty((2 * count, 4), dtype=torch.int32, device=ctr.device)
     _check(load().sketch_debug_philox(ctypes.c_void_p(ctr.data_ptr()),
                                       ctypes.c_uint64(seed),
                                       ctypes.c_void_p(out.data_ptr()), count,
                                       _stream_ptr(stream)))
-    return out
+    return (out[:count], out[count:]) if both else out[:count]
 
 
 def debug_normal_pair(words, stream=None):

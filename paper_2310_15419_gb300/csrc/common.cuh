@@ -21,17 +21,21 @@ constexpr uint32_t kPhiloxW1 = 0xBB67AE85u;
 
 constexpr int kPM1 = 0, kUniform = 1, kNormal = 2;
 
-// Ten Philox rounds.  The round keys are warp-uniform; each round is two
-// 32x32->64 multiplies and two three-input xors.
+// One Philox round: two 32x32->64 multiplies (each one wide multiply,
+// both halves used) and two three-input xors with the round key.
+__device__ __forceinline__ uint4 philox_round(uint4 c, uint32_t k0, uint32_t k1) {
+  const uint64_t p0 = static_cast<uint64_t>(kPhiloxM0) * c.x;
+  const uint64_t p1 = static_cast<uint64_t>(kPhiloxM1) * c.z;
+  return make_uint4(static_cast<uint32_t>(p1 >> 32) ^ c.y ^ k0, static_cast<uint32_t>(p1),
+                    static_cast<uint32_t>(p0 >> 32) ^ c.w ^ k1, static_cast<uint32_t>(p0));
+}
+
+// Ten Philox rounds; the key advances by the Weyl increments after each.
 __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0,
                                                uint32_t k1) {
 #pragma unroll
   for (int r = 0; r < 10; ++r) {
-    const uint32_t hi0 = __umulhi(kPhiloxM0, c.x);
-    const uint32_t lo0 = kPhiloxM0 * c.x;
-    const uint32_t hi1 = __umulhi(kPhiloxM1, c.z);
-    const uint32_t lo1 = kPhiloxM1 * c.z;
-    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    c = philox_round(c, k0, k1);
     k0 += kPhiloxW0;
     k1 += kPhiloxW1;
   }
@@ -42,6 +46,30 @@ __device__ __forceinline__ uint4 philox_block(uint32_t i_blk, uint32_t j,
                                               uint32_t stream, uint32_t k0,
                                               uint32_t k1) {
   return philox4x32_10(make_uint4(i_blk, j, stream, 0u), k0, k1);
+}
+
+// The ten round keys of a seed, computed once on the host.  A kernel that
+// takes them as a __grid_constant__ parameter reads each from the constant
+// bank as an operand of its xor, with no key arithmetic per block.
+struct PhiloxKeys {
+  uint32_t k0[10], k1[10];
+};
+inline PhiloxKeys philox_keys(uint32_t k0, uint32_t k1) {
+  PhiloxKeys ks;
+  for (int r = 0; r < 10; ++r) {
+    ks.k0[r] = k0 + static_cast<uint32_t>(r) * kPhiloxW0;
+    ks.k1[r] = k1 + static_cast<uint32_t>(r) * kPhiloxW1;
+  }
+  return ks;
+}
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, const PhiloxKeys& ks) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) c = philox_round(c, ks.k0[r], ks.k1[r]);
+  return c;
+}
+__device__ __forceinline__ uint4 philox_block(uint32_t i_blk, uint32_t j, uint32_t stream,
+                                              const PhiloxKeys& ks) {
+  return philox4x32_10(make_uint4(i_blk, j, stream, 0u), ks);
 }
 
 // U(-1,1): top 24 bits as a signed integer u, S = (2u + 1) 2^-24.  The fma

@@ -843,7 +843,7 @@ template <int DIST, int CPW, bool TACC>
 __global__ void __launch_bounds__(tile_warps(TACC) * 32, 1)
     k_tile(int32_t m, int32_t n, int32_t d, int32_t R, int32_t P, int32_t G,
            const int2* __restrict__ packed, const int32_t* __restrict__ off,
-           float* __restrict__ out, uint32_t k0, uint32_t k1,
+           float* __restrict__ out, const __grid_constant__ PhiloxKeys keys,
            uint32_t stream_id, unsigned long long* gen_count) {
   static_assert(CPW % 4 == 0, "columns per warp come in quads");
   static_assert(!TACC || CPW == 32, "tensor-memory accumulators take 32 columns per warp");
@@ -944,15 +944,14 @@ __global__ void __launch_bounds__(tile_warps(TACC) * 32, 1)
       const uint32_t j = static_cast<uint32_t>(j0 + jl);
       float4 v;
       if constexpr (DIST == kPM1) {
-        const uint4 x = philox_block(static_cast<uint32_t>(tile >> 2), j,
-                                     stream_id, k0, k1);
+        const uint4 x = philox_block(static_cast<uint32_t>(tile >> 2), j, stream_id, keys);
         const int wsel = tile & 3;
         const uint32_t w = (wsel == 0 ? x.x : wsel == 1 ? x.y : wsel == 2 ? x.z : x.w) >> (4 * q);
         v = make_float4((w & 1u) ? -1.f : 1.f, (w & 2u) ? -1.f : 1.f,
                         (w & 4u) ? -1.f : 1.f, (w & 8u) ? -1.f : 1.f);
       } else {
-        v = four_entries<DIST>(philox_block(static_cast<uint32_t>(tile * 8 + q), j,
-                                            stream_id, k0, k1));
+        v = four_entries<DIST>(
+            philox_block(static_cast<uint32_t>(tile * 8 + q), j, stream_id, keys));
       }
       *reinterpret_cast<float4*>(&S_tile[jl * 32 + 4 * q]) = v;
     }
@@ -1163,6 +1162,7 @@ cudaError_t launch_tile(const TileArgs& a, void* ws, cudaStream_t s, int* launch
   if (cblocks > 65535 || a.G > 65535) return cudaErrorInvalidValue;
   const dim3 grid(tiles, cblocks, a.G), block(tile_warps(a.tacc != 0) * 32);
   const size_t smem = tile_smem_bytes(a.R, a.tacc);
+  const PhiloxKeys keys = philox_keys(a.k0, a.k1);
   float* dst = a.G == 1 ? a.Ahat : partial;
   if (a.tacc && a.cpw != 32) return cudaErrorInvalidValue;
 #define SK_TILE_CASE(DD, CC, TT)                                                 \
@@ -1173,7 +1173,7 @@ cudaError_t launch_tile(const TileArgs& a, void* ws, cudaStream_t s, int* launch
     if (e != cudaSuccess) return e;                                              \
     k_tile<DD, CC, TT><<<grid, block, smem, s>>>(a.m, a.n, a.d, a.R,             \
                                                  static_cast<int32_t>(P), a.G,   \
-                                                 packed, off, dst, a.k0, a.k1,   \
+                                                 packed, off, dst, keys,         \
                                                  a.stream_id, a.gen_count);      \
     ++*launches;                                                                 \
     launched = true;                                                             \
@@ -1236,18 +1236,19 @@ cudaError_t launch_validate(int32_t m, int32_t n, int64_t nnz,
   return cudaGetLastError();
 }
 
+// Both forms of the generator (running key, precomputed round keys) on the
+// same counters: slots [0, count) and [count, 2 count) of `out`.
 __global__ void k_debug_philox(const uint32_t* __restrict__ ctr, uint32_t k0,
-                               uint32_t k1, uint32_t* __restrict__ out,
-                               int64_t count) {
+                               uint32_t k1, const __grid_constant__ PhiloxKeys keys,
+                               uint32_t* __restrict__ out, int64_t count) {
   for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
        t < count; t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
     const uint4 c = make_uint4(ctr[4 * t], ctr[4 * t + 1], ctr[4 * t + 2],
                                ctr[4 * t + 3]);
     const uint4 x = philox4x32_10(c, k0, k1);
-    out[4 * t] = x.x;
-    out[4 * t + 1] = x.y;
-    out[4 * t + 2] = x.z;
-    out[4 * t + 3] = x.w;
+    const uint4 y = philox4x32_10(c, keys);
+    reinterpret_cast<uint4*>(out)[t] = x;
+    reinterpret_cast<uint4*>(out)[count + t] = y;
   }
 }
 
@@ -1255,8 +1256,8 @@ cudaError_t launch_debug_philox(const uint32_t* ctr, uint32_t k0, uint32_t k1,
                                 uint32_t* out, int64_t count, cudaStream_t s) {
   if (count <= 0) return cudaSuccess;
   const int64_t blocks = std::min<int64_t>((count + 255) / 256, 4096);
-  k_debug_philox<<<static_cast<unsigned>(blocks), 256, 0, s>>>(ctr, k0, k1, out,
-                                                               count);
+  k_debug_philox<<<static_cast<unsigned>(blocks), 256, 0, s>>>(
+      ctr, k0, k1, philox_keys(k0, k1), out, count);
   return cudaGetLastError();
 }
 
@@ -1300,7 +1301,7 @@ cudaError_t launch_debug_S(int dist, uint32_t k0, uint32_t k1,
 }
 
 template <int DIST>
-__global__ void k_bench_generator(uint32_t k0, uint32_t k1, int64_t threads,
+__global__ void k_bench_generator(const __grid_constant__ PhiloxKeys keys, int64_t threads,
                                   int64_t blocks_per_thread,
                                   float* __restrict__ sink) {
   const int64_t tid = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
@@ -1308,8 +1309,7 @@ __global__ void k_bench_generator(uint32_t k0, uint32_t k1, int64_t threads,
   float acc = 0.f;
   uint32_t bits = 0;
   for (int64_t b = 0; b < blocks_per_thread; ++b) {
-    const uint4 x = philox_block(static_cast<uint32_t>(b),
-                                 static_cast<uint32_t>(tid), 0u, k0, k1);
+    const uint4 x = philox_block(static_cast<uint32_t>(b), static_cast<uint32_t>(tid), 0u, keys);
     if constexpr (DIST == kPM1) {
       bits ^= x.x ^ x.y ^ x.z ^ x.w;
     } else {
@@ -1326,18 +1326,19 @@ cudaError_t launch_bench_generator(int dist, uint32_t k0, uint32_t k1,
   if (threads <= 0) return cudaSuccess;
   const int64_t blocks = (threads + 255) / 256;
   if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
+  const PhiloxKeys keys = philox_keys(k0, k1);
   switch (dist) {
     case kPM1:
       k_bench_generator<kPM1><<<static_cast<unsigned>(blocks), 256, 0, s>>>(
-          k0, k1, threads, blocks_per_thread, sink);
+          keys, threads, blocks_per_thread, sink);
       break;
     case kUniform:
       k_bench_generator<kUniform><<<static_cast<unsigned>(blocks), 256, 0, s>>>(
-          k0, k1, threads, blocks_per_thread, sink);
+          keys, threads, blocks_per_thread, sink);
       break;
     case kNormal:
       k_bench_generator<kNormal><<<static_cast<unsigned>(blocks), 256, 0, s>>>(
-          k0, k1, threads, blocks_per_thread, sink);
+          keys, threads, blocks_per_thread, sink);
       break;
     default:
       return cudaErrorInvalidValue;

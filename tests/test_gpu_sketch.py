@@ -65,8 +65,11 @@ def test_philox_matches_oracle():
     ctr[0] = 0
     ctr[1] = 2**32 - 1
     for seed in (0, 1, 0xFFFFFFFFFFFFFFFF, 0x0123456789ABCDEF):
-        dev = capi.debug_philox(torch.from_numpy(ctr.astype(np.uint32).view(np.int32)).cuda(),
-                                seed).cpu().numpy().view(np.uint32)
+        run, keyed = capi.debug_philox(
+            torch.from_numpy(ctr.astype(np.uint32).view(np.int32)).cuda(), seed, both=True)
+        dev = run.cpu().numpy().view(np.uint32)
+        # the precomputed-round-key form gives the same blocks everywhere
+        assert np.array_equal(dev, keyed.cpu().numpy().view(np.uint32))
         key = np.array([seed & 0xFFFFFFFF, seed >> 32], dtype=np.uint32)
         for t in list(range(50)) + [19999]:
             assert np.array_equal(dev[t], oracle.philox4x32_10(ctr[t].astype(np.uint32), key))
