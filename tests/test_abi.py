@@ -64,3 +64,25 @@ def test_host_side_argument_errors_need_no_gpu():
     bad = capi.sketch_plan(1, 9, 1, 0, 0)
     assert lib.sketch_set_plan(h, ctypes.byref(bad)) == capi.SKETCH_ERR_ARG
     assert lib.sketch_destroy(h) == capi.SKETCH_OK
+
+
+def test_tile_plan_checks_need_no_gpu():
+    """TILE plans: register sums take 4, 16 or 64 columns per warp, tensor-
+    memory sums (tile_acc = 1) exactly 32; both need panel_rows 8..1152."""
+    from paper_2310_15419_gb300 import capi
+    lib = capi.load()
+    h = ctypes.c_void_p()
+    assert lib.sketch_create(1000, 100, 64, 1, 1, ctypes.byref(h)) == capi.SKETCH_OK
+    T = capi.SKETCH_MODE_TILE
+    # mode, q_tiles, split, n_block, row_groups, panel_rows, cols_per_warp, tc, tile_acc
+    good = [(T, 0, 0, 0, 1, 1024, 64, 0, 0), (T, 0, 0, 0, 3, 8, 4, 0, 0),
+            (T, 0, 0, 0, 20, 1152, 32, 0, 1), (T, 0, 0, 0, 1, 8, 32, 0, 1)]
+    bad = [(T, 0, 0, 0, 1, 1024, 64, 0, 1), (T, 0, 0, 0, 1, 512, 16, 0, 1),
+           (T, 0, 0, 0, 1, 512, 32, 0, 0), (T, 0, 0, 0, 1, 512, 32, 0, 2),
+           (T, 0, 0, 0, 1, 1153, 32, 0, 1), (T, 0, 0, 0, 1, 7, 64, 0, 0),
+           (T, 0, 0, 0, 0, 1024, 64, 0, 0)]
+    for f in good:
+        assert lib.sketch_set_plan(h, ctypes.byref(capi.sketch_plan(*f))) == capi.SKETCH_OK, f
+    for f in bad:
+        assert lib.sketch_set_plan(h, ctypes.byref(capi.sketch_plan(*f))) == capi.SKETCH_ERR_ARG, f
+    assert lib.sketch_destroy(h) == capi.SKETCH_OK

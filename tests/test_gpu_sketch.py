@@ -155,18 +155,6 @@ def test_tile_tensor_memory_sums_equal_register_sums(dist):
     assert rel_fro(outs[2], ref) <= TOL and rel_fro(outs[3], ref) <= TOL
 
 
-def test_tile_tensor_memory_plan_checks():
-    sk = capi.Sketch(1000, 100, 64, "uniform", seed=1)
-    for bad in (dict(panel_rows=1024, row_groups=1, cols_per_warp=64, tile_acc=1),
-                dict(panel_rows=512, row_groups=1, cols_per_warp=16, tile_acc=1),
-                dict(panel_rows=512, row_groups=1, cols_per_warp=32, tile_acc=0),
-                dict(panel_rows=512, row_groups=1, cols_per_warp=32, tile_acc=2)):
-        with pytest.raises(capi.SketchError) as e:
-            sk.set_plan(capi.SKETCH_MODE_TILE, **bad)
-        assert e.value.code == capi.SKETCH_ERR_ARG
-    sk.close()
-
-
 def test_uniform_integer_values_exact_in_integer_scale():
     """U entries are odd multiples of 2^-24; with small integer A every
     partial sum of (2u+1) a is an integer below 2^24 only for tiny sums, so
