@@ -57,7 +57,7 @@ def parse():
                     default="auto", help="force one kernel family")
     ap.add_argument("--no-cpu", action="store_true",
                     help="skip the oracle's CPU baseline")
-    ap.add_argument("--extras", default="lsq,batched,dense,serve",
+    ap.add_argument("--extras", default="lsq,batched,dense,serve,density",
                     help="secondary workloads reported beside the headline")
     ap.add_argument("--serve-seconds", type=float, default=2.0,
                     help="length of the Poisson arrival trace of the serve run")
@@ -353,6 +353,73 @@ def bench_dense(torch, capi, inputs, peaks, steps=5):
     return res
 
 
+def bench_density(torch, capi, inputs, rates, r_fma, hbm, steps=3):
+    """Percent of roofline against nonzero density (the GPU counterpart of
+    Fig. percent_peak, Sec. 3.4): m = 10^6, n = 1000, d = 3n, uniform
+    sparsity, U(-1,1) values.  Methods: +-1, U(-1,1) and N(0,1) generated on
+    the fly (tuned plans), and U(-1,1) pre-generated in memory (S written once
+    by sketch_generate_S, 12 GB, not timed; the TILE kernel then copies S
+    tiles from HBM).  The "(-1,1) with scaling trick" variant is the U path
+    itself: its entries are odd multiples of 2^-24, so scaling is exact."""
+    m, n = 1_000_000, 1000
+    d = 3 * n
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    out = torch.empty((n, d), dtype=torch.float32, device="cuda")
+    S = None
+    res = {"workload": "m=1,000,000 n=1,000 d=3,000, uniform sparsity, U(-1,1) values",
+           "l2": "flushed before every timed call", "rows": []}
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return statistics.mean(ms)
+
+    for rho in (1e-4, 1e-3, 1e-2):
+        A = inputs.float_uniform(m, n, rho, seed=31)
+        dA = capi.DeviceCSC(A)
+        nonempty = int(np.count_nonzero(np.bincount(A.rowidx, minlength=m)))
+        a_bytes = A.nnz * 8 + 4 * (n + 1) + 4 * d * n
+        row = {"density": rho, "nnz": int(A.nnz)}
+        for method in ("pm1", "uniform", "normal", "pregen_uniform"):
+            dist = "uniform" if method == "pregen_uniform" else method
+            sk = capi.Sketch(m, n, d, dist, seed=1)
+            if method == "pregen_uniform":
+                if S is None:
+                    S = sk.generate_S()
+                    torch.cuda.synchronize()
+                ms = timed(lambda: sk.apply_pregen(dA, S, out))
+                t_mem = (4.0 * d * nonempty + a_bytes) / hbm
+                t_alu = d * A.nnz / r_fma
+                plan = "TILE from memory"
+            else:
+                ms = timed(lambda: sk.apply(dA, out))
+                t_alu = d * nonempty / rates[dist] + d * A.nnz / r_fma
+                t_mem = a_bytes / hbm
+                p = sk.get_plan(dA)
+                plan = {1: "REGEN", 2: "PANEL", 3: "TILE"}.get(p["mode"], str(p["mode"]))
+            assert sk.device_status() == capi.SKETCH_OK
+            sk.close()
+            t_star = max(t_alu, t_mem)
+            row[method] = {"ms": round(ms, 4),
+                           "tflops": round(2.0 * d * A.nnz / (ms / 1e3) / 1e12, 3),
+                           "frac": round(t_star / (ms / 1e3), 4),
+                           "bound": "alu" if t_alu >= t_mem else "hbm", "plan": plan}
+        res["rows"].append(row)
+        del dA
+    del S
+    torch.cuda.empty_cache()
+    return res
+
+
 def bench_serve(capi, inputs, seconds, pool_size, rate=200.0):
     """Poisson arrivals at `rate`/s of SAP-QR solves with m ~ logU[5e4, 2e6],
     n ~ U[100, 2000], density ~ logU[5e-4, 1e-2], FP32 N(0,1) values, d = 2n,
@@ -562,6 +629,8 @@ def run_ours(args):
         if "serve" in wanted:
             extras["serve"] = bench_serve(capi, inputs, args.serve_seconds,
                                           args.serve_pool)
+        if "density" in wanted:
+            extras["density"] = bench_density(torch, capi, inputs, rates, r_fma, hbm)
 
     # ---- CPU baseline: the oracle on a bounded row sample (rank 0, N = 1)
     cpu = None

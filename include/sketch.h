@@ -181,6 +181,25 @@ int sketch_apply(sketch_t h, const sketch_csc* A, float* Ahat,
 int sketch_apply_noalloc(sketch_t h, const sketch_csc* A, float* Ahat,
                          sketch_stream_t stream);
 
+/* The "pre-generated S" method of Sec. 3.4 (Fig. percent_peak): S stored in
+ * device memory instead of regenerated.  sketch_generate_S writes
+ * S[j * ld_s + i] = S(i, j) for i < d, j < m -- exactly the entries the
+ * sketch kernels regenerate, for the handle's distribution, seed and stream
+ * id.  S is a caller-owned device buffer of ld_s * m floats; ld_s >= d, a
+ * multiple of 4; S 16-byte aligned.  Asynchronous.
+ * Errors: SKETCH_ERR_ARG (null S, ld_s, alignment), SKETCH_ERR_CUDA. */
+int sketch_generate_S(sketch_t h, float* S, int64_t ld_s, sketch_stream_t stream);
+
+/* A_hat = S A with S read from such a buffer: the TILE kernel with
+ * tensor-memory sums, each 32-row x panel_rows tile of S copied from memory
+ * (cp.async, 16 bytes a thread) where the other paths generate it.  Same
+ * additions as the generated path, so the same bits.  Uses a forced TILE plan
+ * with tile_acc = 1 if one is set, else panels of 1152 rows.  Same
+ * requirements on S and ld_s as sketch_generate_S; same errors as
+ * sketch_apply.  Asynchronous. */
+int sketch_apply_pregen(sketch_t h, const sketch_csc* A, const float* S, int64_t ld_s,
+                        float* Ahat, sketch_stream_t stream);
+
 /* Message for the last error returned on this handle ("" if none). */
 const char* sketch_last_error(sketch_t h);
 

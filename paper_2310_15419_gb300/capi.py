@@ -96,6 +96,8 @@ SIGNATURES = [
     ("sketch_get_plan", _I32, [_VP, _CSCP, ctypes.POINTER(sketch_plan), _VP]),
     ("sketch_apply", _I32, [_VP, _CSCP, _VP, _VP]),
     ("sketch_apply_noalloc", _I32, [_VP, _CSCP, _VP, _VP]),
+    ("sketch_generate_S", _I32, [_VP, _VP, _I64, _VP]),
+    ("sketch_apply_pregen", _I32, [_VP, _CSCP, _VP, _I64, _VP, _VP]),
     ("sketch_last_error", ctypes.c_char_p, [_VP]),
     ("sketch_device_status", _I32, [_VP, _VP]),
     ("sketch_validate_csc", _I32, [_CSCP, _VP]),
@@ -260,6 +262,32 @@ class Sketch:
         _check(load().sketch_apply_noalloc(self.h, ctypes.byref(A.desc),
                                            ctypes.c_void_p(out.data_ptr()),
                                            _stream_ptr(stream)), self.h)
+        return out
+
+    def generate_S(self, ld_s=None, out=None, stream=None):
+        """sketch_generate_S: S materialised on the device as an (m, ld_s)
+        float32 tensor whose row j holds column j of S (rows 0..d-1 used);
+        ld_s defaults to d rounded up to a multiple of 4."""
+        import torch
+        if ld_s is None:
+            ld_s = (self.d + 3) // 4 * 4
+        if out is None:
+            out = torch.empty((self.m, ld_s), dtype=torch.float32, device="cuda")
+        _check(load().sketch_generate_S(self.h, ctypes.c_void_p(out.data_ptr()), int(ld_s),
+                                        _stream_ptr(stream)), self.h)
+        return out
+
+    def apply_pregen(self, A: DeviceCSC, S, out=None, stream=None):
+        """sketch_apply_pregen: A_hat = S A with S read from `S` (as written by
+        generate_S, leading dimension S.shape[1])."""
+        import torch
+        if out is None:
+            out = torch.empty((self.n, self.d), dtype=torch.float32,
+                              device=A.colptr.device)
+        _check(load().sketch_apply_pregen(self.h, ctypes.byref(A.desc),
+                                          ctypes.c_void_p(S.data_ptr()), int(S.stride(0)),
+                                          ctypes.c_void_p(out.data_ptr()),
+                                          _stream_ptr(stream)), self.h)
         return out
 
     def device_status(self, stream=None):

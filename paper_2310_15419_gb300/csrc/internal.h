@@ -87,6 +87,10 @@ struct TileArgs {
   int32_t G;    // row groups (partial sums)
   int32_t cpw;  // columns per warp: 4, 16 or 64; 32 with tacc (n1 = warps * cpw)
   int32_t tacc;  // 1: accumulators in tensor memory (32 warps of cpw 32)
+  // dist 3: S read from S_mem (d x m, column j at S_mem + j * ld_s; ld_s a
+  // multiple of 4 and >= d, S_mem 16-byte aligned) instead of generated
+  const float* S_mem = nullptr;
+  int64_t ld_s = 0;
   int* status;
   unsigned long long* gen_count;
 };
@@ -103,6 +107,11 @@ cudaError_t launch_debug_normal_pair(const uint32_t* words, float* out, int64_t 
                                      cudaStream_t s);
 cudaError_t launch_debug_philox(const uint32_t* ctr, uint32_t k0, uint32_t k1,
                                 uint32_t* out, int64_t count, cudaStream_t s);
+// S_mem[j * ld_s + i] = S(i, j), i < d, j < m (ld_s >= d, a multiple of 4;
+// S_mem 16-byte aligned).
+cudaError_t launch_generate_S(int dist, uint32_t k0, uint32_t k1, uint32_t stream_id,
+                              int32_t d, int32_t m, float* S_mem, int64_t ld_s,
+                              cudaStream_t s);
 cudaError_t launch_debug_S(int dist, uint32_t k0, uint32_t k1,
                            uint32_t stream_id, const int64_t* i,
                            const int64_t* j, float* out, int64_t count,

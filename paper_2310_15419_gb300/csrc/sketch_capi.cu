@@ -607,6 +607,80 @@ int sketch_apply(sketch_t h, const sketch_csc* A, float* Ahat,
   return run_plan(h, A, Ahat, p, h->ws, s);
 }
 
+static int check_S_mem(sketch_t h, const float* S, int64_t ld_s) {
+  if (!S) return fail(h, SKETCH_ERR_ARG, "S is null");
+  if (ld_s < h->d || ld_s % 4 != 0)
+    return fail(h, SKETCH_ERR_ARG, "ld_s must be >= d and a multiple of 4");
+  if (reinterpret_cast<uintptr_t>(S) % 16 != 0)
+    return fail(h, SKETCH_ERR_ARG, "S must be 16-byte aligned");
+  return SKETCH_OK;
+}
+
+int sketch_generate_S(sketch_t h, float* S, int64_t ld_s, sketch_stream_t stream) {
+  if (!h) return fail(nullptr, SKETCH_ERR_ARG, "handle is null");
+  int rc = check_S_mem(h, S, ld_s);
+  if (rc != SKETCH_OK) return rc;
+  cudaError_t e = launch_generate_S(h->dist, h->k0, h->k1, h->stream_id,
+                                    static_cast<int32_t>(h->d), static_cast<int32_t>(h->m), S,
+                                    ld_s, reinterpret_cast<cudaStream_t>(stream));
+  if (e == cudaSuccess) h->launches += 1;
+  return e == cudaSuccess ? SKETCH_OK : cuda_fail(h, e, "generate_S");
+}
+
+int sketch_apply_pregen(sketch_t h, const sketch_csc* A, const float* S, int64_t ld_s,
+                        float* Ahat, sketch_stream_t stream) {
+  if (!h) return fail(nullptr, SKETCH_ERR_ARG, "handle is null");
+  if (!Ahat) return fail(h, SKETCH_ERR_ARG, "Ahat is null");
+  int rc = check_csc_args(h, A);
+  if (rc != SKETCH_OK) return rc;
+  if ((rc = check_S_mem(h, S, ld_s)) != SKETCH_OK) return rc;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if ((rc = ensure_small(h)) != SKETCH_OK) return rc;
+  if (A->n == 0) return SKETCH_OK;
+  if (A->nnz == 0) {
+    cudaError_t e = cudaMemsetAsync(Ahat, 0, sizeof(float) * A->n * h->d, s);
+    return e == cudaSuccess ? SKETCH_OK : cuda_fail(h, e, "cudaMemsetAsync");
+  }
+  // a forced TILE plan with tensor-memory sums sets R and the row groups;
+  // otherwise panels of 1152 rows
+  sketch_plan p{};
+  if (h->has_forced && h->forced.mode == SKETCH_MODE_TILE && h->forced.tile_acc == 1) {
+    p = h->forced;
+  } else {
+    p = tile_plan(h, A, 1152, 1);
+    p.tile_acc = 1;
+    p.cols_per_warp = 32;
+  }
+  if ((rc = ensure_workspace(h, plan_workspace_bytes(h, A, p))) != SKETCH_OK) return rc;
+  TileArgs a{};
+  a.m = static_cast<int32_t>(A->m);
+  a.n = static_cast<int32_t>(A->n);
+  a.d = static_cast<int32_t>(h->d);
+  a.nnz = A->nnz;
+  a.dtype = A->dtype;
+  a.colptr = A->colptr;
+  a.rowidx = A->rowidx;
+  a.values = A->values;
+  a.Ahat = Ahat;
+  a.k0 = h->k0;
+  a.k1 = h->k1;
+  a.stream_id = h->stream_id;
+  a.dist = 3;  // S from memory
+  a.R = p.panel_rows;
+  a.G = std::min<int32_t>(p.row_groups,
+                          static_cast<int32_t>((A->m + p.panel_rows - 1) / p.panel_rows));
+  a.cpw = 32;
+  a.tacc = 1;
+  a.status = reinterpret_cast<int*>(h->d_small);
+  a.gen_count = nullptr;
+  a.S_mem = S;
+  a.ld_s = ld_s;
+  int nl = 0;
+  cudaError_t e = launch_tile(a, h->ws, s, &nl);
+  h->launches += nl;
+  return e == cudaSuccess ? SKETCH_OK : cuda_fail(h, e, "tile kernel (S from memory)");
+}
+
 const char* sketch_last_error(sketch_t h) {
   return h ? h->last_error.c_str() : sk::g_global_error.c_str();
 }

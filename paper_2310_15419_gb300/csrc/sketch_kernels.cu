@@ -730,6 +730,9 @@ cudaError_t launch_panel(const PanelArgs& a, cudaStream_t s, int* launches) {
 // accumulators (lane = row of S), reading S from shared memory.  No atomics;
 // each output is written once per row group, so results are deterministic.
 // ---------------------------------------------------------------------------
+// TILE's S source besides the three distributions: S read from memory, as
+// written by k_generate_S (the "pre-generated S" of Fig. percent_peak).
+constexpr int kFromMemory = 3;
 // Warps per CTA: 16 with register sums (64 columns each), 32 with
 // tensor-memory sums (32 columns each); n1 = 1024 columns either way.
 __host__ __device__ constexpr int tile_warps(bool tacc) { return tacc ? 32 : 16; }
@@ -844,7 +847,8 @@ __global__ void __launch_bounds__(tile_warps(TACC) * 32, 1)
     k_tile(int32_t m, int32_t n, int32_t d, int32_t R, int32_t P, int32_t G,
            const int2* __restrict__ packed, const int32_t* __restrict__ off,
            float* __restrict__ out, const __grid_constant__ PhiloxKeys keys,
-           uint32_t stream_id, unsigned long long* gen_count) {
+           uint32_t stream_id, unsigned long long* gen_count,
+           const float* __restrict__ S_mem, int64_t ld_s) {
   static_assert(CPW % 4 == 0, "columns per warp come in quads");
   static_assert(!TACC || CPW == 32, "tensor-memory accumulators take 32 columns per warp");
   constexpr int kWarps = tile_warps(TACC);
@@ -942,18 +946,32 @@ __global__ void __launch_bounds__(tile_warps(TACC) * 32, 1)
     for (int idx = threadIdx.x; idx < rows * 8; idx += kWarps * 32) {
       const int jl = idx >> 3, q = idx & 7;
       const uint32_t j = static_cast<uint32_t>(j0 + jl);
-      float4 v;
-      if constexpr (DIST == kPM1) {
-        const uint4 x = philox_block(static_cast<uint32_t>(tile >> 2), j, stream_id, keys);
-        const int wsel = tile & 3;
-        const uint32_t w = (wsel == 0 ? x.x : wsel == 1 ? x.y : wsel == 2 ? x.z : x.w) >> (4 * q);
-        v = make_float4((w & 1u) ? -1.f : 1.f, (w & 2u) ? -1.f : 1.f,
-                        (w & 4u) ? -1.f : 1.f, (w & 8u) ? -1.f : 1.f);
+      if constexpr (DIST == kFromMemory) {
+        // S read from memory: 16 bytes (rows 4q .. 4q+3 of the tile) by
+        // cp.async; rows past d are zero-filled (src-size below 16)
+        const int valid = min(4, max(0, rows_valid - 4 * q));
+        const float* src = valid > 0 ? S_mem + static_cast<int64_t>(j) * ld_s + tile * 32 + 4 * q
+                                     : S_mem;
+        const unsigned dst =
+            static_cast<unsigned>(__cvta_generic_to_shared(&S_tile[jl * 32 + 4 * q]));
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src),
+                     "r"(4 * valid)
+                     : "memory");
       } else {
-        v = four_entries<DIST>(
-            philox_block(static_cast<uint32_t>(tile * 8 + q), j, stream_id, keys));
+        float4 v;
+        if constexpr (DIST == kPM1) {
+          const uint4 x = philox_block(static_cast<uint32_t>(tile >> 2), j, stream_id, keys);
+          const int wsel = tile & 3;
+          const uint32_t w =
+              (wsel == 0 ? x.x : wsel == 1 ? x.y : wsel == 2 ? x.z : x.w) >> (4 * q);
+          v = make_float4((w & 1u) ? -1.f : 1.f, (w & 2u) ? -1.f : 1.f,
+                          (w & 4u) ? -1.f : 1.f, (w & 8u) ? -1.f : 1.f);
+        } else {
+          v = four_entries<DIST>(
+              philox_block(static_cast<uint32_t>(tile * 8 + q), j, stream_id, keys));
+        }
+        *reinterpret_cast<float4*>(&S_tile[jl * 32 + 4 * q]) = v;
       }
-      *reinterpret_cast<float4*>(&S_tile[jl * 32 + 4 * q]) = v;
     }
     asm volatile("cp.async.wait_all;" ::: "memory");
     __syncthreads();
@@ -1165,6 +1183,10 @@ cudaError_t launch_tile(const TileArgs& a, void* ws, cudaStream_t s, int* launch
   const PhiloxKeys keys = philox_keys(a.k0, a.k1);
   float* dst = a.G == 1 ? a.Ahat : partial;
   if (a.tacc && a.cpw != 32) return cudaErrorInvalidValue;
+  if (a.dist == kFromMemory &&
+      (!a.tacc || !a.S_mem || a.ld_s < a.d || a.ld_s % 4 != 0 ||
+       reinterpret_cast<uintptr_t>(a.S_mem) % 16 != 0))
+    return cudaErrorInvalidValue;
 #define SK_TILE_CASE(DD, CC, TT)                                                 \
   if (a.dist == DD && a.cpw == CC && (a.tacc != 0) == TT) {                      \
     e = cudaFuncSetAttribute(k_tile<DD, CC, TT>,                                 \
@@ -1174,7 +1196,8 @@ cudaError_t launch_tile(const TileArgs& a, void* ws, cudaStream_t s, int* launch
     k_tile<DD, CC, TT><<<grid, block, smem, s>>>(a.m, a.n, a.d, a.R,             \
                                                  static_cast<int32_t>(P), a.G,   \
                                                  packed, off, dst, keys,         \
-                                                 a.stream_id, a.gen_count);      \
+                                                 a.stream_id, a.gen_count,       \
+                                                 a.S_mem, a.ld_s);               \
     ++*launches;                                                                 \
     launched = true;                                                             \
   }
@@ -1185,6 +1208,7 @@ cudaError_t launch_tile(const TileArgs& a, void* ws, cudaStream_t s, int* launch
   SK_TILE_CASE(kNormal, 4, false) SK_TILE_CASE(kNormal, 16, false)
   SK_TILE_CASE(kNormal, 64, false)
   SK_TILE_CASE(kPM1, 32, true) SK_TILE_CASE(kUniform, 32, true) SK_TILE_CASE(kNormal, 32, true)
+  SK_TILE_CASE(kFromMemory, 32, true)
 #undef SK_TILE_CASE
   if (!launched) return cudaErrorInvalidValue;
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -1276,6 +1300,65 @@ cudaError_t launch_debug_normal_pair(const uint32_t* words, float* out, int64_t 
   if (count <= 0) return cudaSuccess;
   const int64_t blocks = std::min<int64_t>((count + 255) / 256, 4096);
   k_debug_normal_pair<<<static_cast<unsigned>(blocks), 256, 0, s>>>(words, out, count);
+  return cudaGetLastError();
+}
+
+// S itself: S_mem[j * ld_s + i] = S(i, j) for i < d, j < m, the entries the
+// sketch kernels regenerate.  One item = four rows of a column: one
+// generator block (U, N: its four entries; +-1: four of its 128 signs).
+template <int DIST>
+__global__ void k_generate_S(const __grid_constant__ PhiloxKeys keys, uint32_t stream_id,
+                             int32_t d, int32_t m, float* __restrict__ S_mem, int64_t ld_s) {
+  const int32_t g4 = (d + 3) / 4;
+  const int64_t items = static_cast<int64_t>(m) * g4;
+  for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; t < items;
+       t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const uint32_t j = static_cast<uint32_t>(t / g4);
+    const int32_t g = static_cast<int32_t>(t % g4);
+    float4 v;
+    if constexpr (DIST == kPM1) {
+      const uint4 x = philox_block(static_cast<uint32_t>(g >> 5), j, stream_id, keys);
+      const int b = (4 * g) & 127;  // rows 4g .. 4g+3 are bits b .. b+3 of the block
+      const uint32_t w = ((b < 32) ? x.x : (b < 64) ? x.y : (b < 96) ? x.z : x.w) >> (b & 31);
+      v = make_float4((w & 1u) ? -1.f : 1.f, (w & 2u) ? -1.f : 1.f, (w & 4u) ? -1.f : 1.f,
+                      (w & 8u) ? -1.f : 1.f);
+    } else {
+      v = four_entries<DIST>(philox_block(static_cast<uint32_t>(g), j, stream_id, keys));
+    }
+    float* o = S_mem + static_cast<int64_t>(j) * ld_s + 4 * g;
+    if (4 * g + 4 <= d) {
+      *reinterpret_cast<float4*>(o) = v;  // ld_s % 4 == 0 and S_mem 16-byte aligned
+    } else {
+      o[0] = v.x;
+      if (4 * g + 1 < d) o[1] = v.y;
+      if (4 * g + 2 < d) o[2] = v.z;
+    }
+  }
+}
+
+cudaError_t launch_generate_S(int dist, uint32_t k0, uint32_t k1, uint32_t stream_id,
+                              int32_t d, int32_t m, float* S_mem, int64_t ld_s,
+                              cudaStream_t s) {
+  if (d <= 0 || m <= 0) return cudaSuccess;
+  if (!S_mem || ld_s < d || ld_s % 4 != 0 || reinterpret_cast<uintptr_t>(S_mem) % 16 != 0)
+    return cudaErrorInvalidValue;
+  const int64_t items = static_cast<int64_t>(m) * ((d + 3) / 4);
+  const unsigned blocks =
+      static_cast<unsigned>(std::min<int64_t>((items + 255) / 256, 32LL * num_sms()));
+  const PhiloxKeys keys = philox_keys(k0, k1);
+  switch (dist) {
+    case kPM1:
+      k_generate_S<kPM1><<<blocks, 256, 0, s>>>(keys, stream_id, d, m, S_mem, ld_s);
+      break;
+    case kUniform:
+      k_generate_S<kUniform><<<blocks, 256, 0, s>>>(keys, stream_id, d, m, S_mem, ld_s);
+      break;
+    case kNormal:
+      k_generate_S<kNormal><<<blocks, 256, 0, s>>>(keys, stream_id, d, m, S_mem, ld_s);
+      break;
+    default:
+      return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
 

@@ -86,3 +86,26 @@ def test_tile_plan_checks_need_no_gpu():
     for f in bad:
         assert lib.sketch_set_plan(h, ctypes.byref(capi.sketch_plan(*f))) == capi.SKETCH_ERR_ARG, f
     assert lib.sketch_destroy(h) == capi.SKETCH_OK
+
+
+def test_pregenerated_S_argument_errors_need_no_gpu():
+    from paper_2310_15419_gb300 import capi
+    lib = capi.load()
+    h = ctypes.c_void_p()
+    assert lib.sketch_create(1000, 10, 30, 1, 1, ctypes.byref(h)) == capi.SKETCH_OK
+    E = capi.SKETCH_ERR_ARG
+    assert lib.sketch_generate_S(h, None, 32, None) == E           # null S
+    assert lib.sketch_generate_S(h, ctypes.c_void_p(4096), 28, None) == E  # ld_s < d
+    assert lib.sketch_generate_S(h, ctypes.c_void_p(4096), 34, None) == E  # not a multiple of 4
+    assert lib.sketch_generate_S(h, ctypes.c_void_p(4104), 32, None) == E  # not 16-byte aligned
+    A = capi.sketch_csc(1000, 10, 3, 8, 8, 8, 0)
+    out = ctypes.c_void_p(8192)
+    assert lib.sketch_apply_pregen(h, ctypes.byref(A), None, 32, out, None) == E
+    assert lib.sketch_apply_pregen(h, ctypes.byref(A), ctypes.c_void_p(4096), 30, out,
+                                   None) == E
+    assert lib.sketch_apply_pregen(h, ctypes.byref(A), ctypes.c_void_p(4096), 32, None,
+                                   None) == E
+    B = capi.sketch_csc(999, 10, 3, 8, 8, 8, 0)
+    assert lib.sketch_apply_pregen(h, ctypes.byref(B), ctypes.c_void_p(4096), 32, out,
+                                   None) == E
+    assert lib.sketch_destroy(h) == capi.SKETCH_OK

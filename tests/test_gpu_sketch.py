@@ -155,6 +155,51 @@ def test_tile_tensor_memory_sums_equal_register_sums(dist):
     assert rel_fro(outs[2], ref) <= TOL and rel_fro(outs[3], ref) <= TOL
 
 
+@pytest.mark.parametrize("dist", ["pm1", "uniform", "normal"])
+@pytest.mark.parametrize("d,ld", [(100, 100), (98, 100), (61, 64), (300, 304)])
+def test_pregenerated_S_gives_the_generated_bits(dist, d, ld):
+    """Sec. 3.4's pre-generated S: S written to memory, then the TILE kernel
+    reading it, equals the TILE kernel generating it bit for bit; the stored
+    S matches the oracle's entries (ragged d, padded leading dimension)."""
+    A = inputs.float_uniform(3000, 300, 0.02, seed=23)
+    sk = capi.Sketch(A.m, A.n, d, dist, seed=5, stream_id=2)
+    sk.set_plan(capi.SKETCH_MODE_TILE, panel_rows=512, row_groups=3, cols_per_warp=32,
+                tile_acc=1)
+    dA = capi.DeviceCSC(A)
+    fly = sk.apply(dA).clone()
+    S = sk.generate_S(ld_s=ld)
+    mem = sk.apply_pregen(dA, S)
+    torch.cuda.synchronize()
+    assert sk.device_status() == capi.SKETCH_OK
+    assert torch.equal(fly, mem)
+    Sh = S.cpu().numpy()
+    rng = np.random.default_rng(3)
+    for i, j in list(zip(rng.integers(0, d, 300), rng.integers(0, A.m, 300))) + \
+            [(0, 0), (d - 1, A.m - 1), (d - 1, 0)]:
+        ref = oracle.S_entry(DISTS[dist], 5, 2, int(i), int(j))
+        if dist == "normal":
+            assert abs(Sh[j, i] - ref) <= 4e-7 * max(1.0, abs(ref))
+        else:
+            assert Sh[j, i] == ref
+    sk.close()
+
+
+def test_pregenerated_S_default_plan_and_tolerance():
+    """Without a forced plan the S-from-memory path picks its own panels;
+    result within the FP32 tolerance of the oracle, n > 1024 (two column
+    blocks)."""
+    A = inputs.float_uniform(2000, 1100, 0.01, seed=24)
+    d = 64
+    sk = capi.Sketch(A.m, A.n, d, "uniform", seed=1)
+    S = sk.generate_S()
+    got = sk.apply_pregen(capi.DeviceCSC(A), S)
+    torch.cuda.synchronize()
+    assert sk.device_status() == capi.SKETCH_OK
+    ref = oracle_sketch(A, d, "uniform")
+    assert rel_fro(got.cpu().numpy().astype(np.float64).T, ref) <= TOL
+    sk.close()
+
+
 def test_uniform_integer_values_exact_in_integer_scale():
     """U entries are odd multiples of 2^-24; with small integer A every
     partial sum of (2u+1) a is an integer below 2^24 only for tiny sums, so
