@@ -356,7 +356,8 @@ int sketch_debug_S(int32_t dist, uint64_t seed, uint32_t stream_id,
 /* Generator throughput probe: `threads` threads each evaluate
  * `blocks_per_thread` Philox blocks at distinct counters and apply the
  * distribution's transform (4 entries per block for U and N, 128 signs for
- * +-1), folding the entries into one float per thread written to sink
+ * +-1), folding the entries' bits together with xors (no floating-point
+ * work beyond the transform) into one word per thread written to sink
  * (device, `threads` floats) so nothing is optimised away.  Asynchronous.
  * Entries generated = threads * blocks_per_thread * (dist == +-1 ? 128 : 4).
  * Used to measure the RNG leg of the ALU roofline (Sec. 3.1's cost h of
