@@ -182,7 +182,8 @@ def generator_rates(torch, capi, sms):
     out = {}
     for dist in DISTS:
         code = capi.DIST_NAMES[dist]
-        bpt = 64 if dist == "pm1" else 32
+        bpt = 512 if dist == "pm1" else 256   # launches of 0.2-0.6 ms: ramp and
+                                              # tail stay near 1% of the time
         per_block = 128 if dist == "pm1" else 4
         capi.bench_generator(code, 7, threads, bpt, sink)
         torch.cuda.synchronize()

@@ -1392,15 +1392,26 @@ __global__ void k_bench_generator(const __grid_constant__ PhiloxKeys keys, int64
   // every entry is consumed by two three-input xors per block (the
   // cheapest use that still forces each value to be computed), so the rate
   // is the generator's own and not that of an add chain
+  // Two independent blocks per iteration (counters b and b + half) give
+  // each thread two dependency chains to interleave.
   uint32_t bits = 0;
-  for (int64_t b = 0; b < blocks_per_thread; ++b) {
+  const int64_t half = (blocks_per_thread + 1) / 2;
+  for (int64_t b = 0; b < half; ++b) {
+    const bool second = b + half < blocks_per_thread;
     const uint4 x = philox_block(static_cast<uint32_t>(b), static_cast<uint32_t>(tid), 0u, keys);
+    const uint4 y = philox_block(static_cast<uint32_t>(b + half), static_cast<uint32_t>(tid), 0u,
+                                 keys);
     if constexpr (DIST == kPM1) {
       bits ^= x.x ^ x.y ^ x.z ^ x.w;
+      if (second) bits ^= y.x ^ y.y ^ y.z ^ y.w;
     } else {
       const float4 v = four_entries<DIST>(x);
+      const float4 u = four_entries<DIST>(y);
       bits ^= __float_as_uint(v.x) ^ __float_as_uint(v.y) ^ __float_as_uint(v.z) ^
               __float_as_uint(v.w);
+      if (second)
+        bits ^= __float_as_uint(u.x) ^ __float_as_uint(u.y) ^ __float_as_uint(u.z) ^
+                __float_as_uint(u.w);
     }
   }
   sink[tid] = __uint_as_float(bits & 0x007fffffu);
