@@ -85,12 +85,26 @@ def recorded_traffic(dist, plan):
         rec = json.load(open(path))
         if dist != rec["dist"] or any(plan.get(k) != v for k, v in rec["plan"].items()):
             return None
-        h = hashlib.sha256()
-        for f in rec["source_files"]:
-            h.update(open(os.path.join(ROOT, f), "rb").read())
-        return rec["traffic_bytes"] if h.hexdigest() == rec["source_sha256"] else None
-    except (OSError, KeyError, ValueError):
+        return rec["traffic_bytes"] if source_digest(rec["sources"]) == rec["source_sha256"] \
+            else None
+    except (OSError, KeyError, ValueError, StopIteration):
         return None
+
+
+def source_digest(sources):
+    """SHA-256 over source regions: each {"file": path} (whole file) or
+    {"file", "from", "to"} (the lines from the first one starting with
+    `from` up to the first later one starting with `to`)."""
+    h = hashlib.sha256()
+    for src in sources:
+        text = open(os.path.join(ROOT, src["file"]), encoding="utf-8").read()
+        if "from" in src:
+            lines = text.splitlines(keepends=True)
+            i = next(k for k, l in enumerate(lines) if l.startswith(src["from"]))
+            j = next(k for k in range(i + 1, len(lines)) if lines[k].startswith(src["to"]))
+            text = "".join(lines[i:j])
+        h.update(text.encode("utf-8"))
+    return h.hexdigest()
 
 
 def reduce_max_ms(local_ms, pg, device):
