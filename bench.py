@@ -370,7 +370,7 @@ def bench_dense(torch, capi, inputs, peaks, steps=5):
 
 def bench_density(torch, capi, inputs, rates, r_fma, hbm, steps=3):
     """Percent of roofline against nonzero density (the GPU counterpart of
-    Fig. percent_peak, Sec. 3.4): m = 10^6, n = 1000, d = 3n, uniform
+    Fig. percent_peak, Sec. 3.3): m = 10^6, n = 1000, d = 3n, uniform
     sparsity, U(-1,1) values.  Methods: +-1, U(-1,1) and N(0,1) generated on
     the fly (tuned plans), and U(-1,1) pre-generated in memory (S written once
     by sketch_generate_S, 12 GB, not timed; the TILE kernel then copies S

@@ -10,7 +10,7 @@
  * Philox4x32-10) keyed by (seed, stream, i, j), so S is the same under any
  * tiling, launch shape or kernel choice (the reproducibility policy of
  * Sec. 4.3).  On top of the sketch it provides the sketch-and-precondition
- * least-squares solver of Sec. 5.4 (Householder QR of A_hat in FP64, LSQR on
+ * least-squares solver of Sec. 5.3 (Householder QR of A_hat in FP64, LSQR on
  * A R^{-1} with FP64 vector arithmetic), a batched launch for many uneven
  * sketches, and a continuous-batching solve server.
  *
@@ -181,7 +181,7 @@ int sketch_apply(sketch_t h, const sketch_csc* A, float* Ahat,
 int sketch_apply_noalloc(sketch_t h, const sketch_csc* A, float* Ahat,
                          sketch_stream_t stream);
 
-/* The "pre-generated S" method of Sec. 3.4 (Fig. percent_peak): S stored in
+/* The "pre-generated S" method of Sec. 3.3 (Fig. percent_peak): S stored in
  * device memory instead of regenerated.  sketch_generate_S writes
  * S[j * ld_s + i] = S(i, j) for i < d, j < m -- exactly the entries the
  * sketch kernels regenerate, for the handle's distribution, seed and stream
@@ -247,7 +247,7 @@ int sketch_batch_status(sketch_batch_t b, sketch_stream_t stream);
 
 int sketch_batch_destroy(sketch_batch_t b);
 
-/* ---- least squares (Sec. 5.4, sketch-and-precondition with QR) -------- */
+/* ---- least squares (Sec. 5.3, sketch-and-precondition with QR) -------- */
 typedef struct {
   int32_t iters;        /* LSQR iterations                                 */
   int32_t status;       /* SKETCH_OK or SKETCH_ERR_NO_CONVERGENCE          */
@@ -262,7 +262,7 @@ typedef struct {
  * (d = the handle's d, normally 2n), FP64 Householder QR of A_hat -> R,
  * LSQR on A R^{-1} with FP64 residual and norm updates until LSQR's own
  * estimate for the preconditioned system falls below `tol` (the stopping
- * rule of Sec. 5.4), then x = R^{-1} y and Error(x) = ||A^T(Ax-b)|| /
+ * rule of Sec. 5.3), then x = R^{-1} y and Error(x) = ||A^T(Ax-b)|| /
  * (||A||_F ||Ax-b||) in FP64.  If Error(x) is still above `tol`, LSQR
  * continues from the same state with a 10x tighter internal tolerance, for
  * as long as each round at least halves Error(x) (up to 6 rounds); the
@@ -285,11 +285,11 @@ typedef struct {
   int32_t status;    /* sketch_lsq_solve's status, or SKETCH_ERR_OOM when   */
                      /* the request can never fit the memory budget         */
   int32_t iters;     /* LSQR iterations                                      */
-  double error;      /* Error(x) of Sec. 5.4                                 */
+  double error;      /* Error(x) of Sec. 5.3                                 */
   double t_submit, t_start, t_done;  /* seconds on the server's clock       */
 } sketch_server_result;
 
-/* Start a server for SAP-QR least-squares requests (Sec. 5.4): `slots`
+/* Start a server for SAP-QR least-squares requests (Sec. 5.3): `slots`
  * worker threads, each with its own CUDA stream and a reusable sketch handle
  * (autotuning off, so a request runs the same kernels alone or in a mix).
  * A request is admitted, oldest first, as soon as a slot is free and its
@@ -367,7 +367,7 @@ int sketch_bench_generator(int32_t dist, uint64_t seed, int64_t threads,
                            sketch_stream_t stream);
 
 /* Householder QR of a dense d x n FP64 matrix A (device, column-major,
- * d >= n) with the kernels sketch_lsq_solve uses (Sec. 5.4): writes R
+ * d >= n) with the kernels sketch_lsq_solve uses (Sec. 5.3): writes R
  * (n x n, ROW-major, upper triangular; R(k,k) = -sign(x_0)||x||, or x_0 when
  * the column below the diagonal is already zero) and R^{-1} (n x n,
  * row-major).  Synchronous; allocates temporary device memory. */

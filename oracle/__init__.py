@@ -11,10 +11,10 @@ Functions follow the paper (arXiv 2310.15419):
   * ``S_entry`` / ``S_column`` / ``S_dense``  S(i, j), Sec. 1.1 + Sec. 3.3
   * ``sketch_kji``               Alg. 3 (regenerate S(:, j) per nonzero)
   * ``sketch_jki``               Alg. 4 (generate S(:, j) once per nonempty row)
-  * ``householder_qr``           QR of the sketch, Sec. 5.4
-  * ``lsqr``                     LSQR on A R^{-1}, Sec. 5.4
-  * ``ls_error``                 Error(x) of Sec. 5.4
-  * ``sap_qr_solve``             the whole SAP-QR pipeline of Sec. 5.4
+  * ``householder_qr``           QR of the sketch, Sec. 5.3
+  * ``lsqr``                     LSQR on A R^{-1}, Sec. 5.3
+  * ``ls_error``                 Error(x) of Sec. 5.3
+  * ``sap_qr_solve``             the whole SAP-QR pipeline of Sec. 5.3
 
 Parity status: every function above is pinned by a ``-m "not gpu"`` test
 against something other than itself (torch's Philox engine, closed forms,
@@ -223,7 +223,7 @@ def lsqr(m, n, colptr, rowidx, values, b, R=None, tol=1e-10, maxit=1000):
 
 def sap_qr_solve(m, n, d, dist, seed, stream, colptr, rowidx, values, b,
                  tol=1e-10, maxit=1000):
-    """Sec. 5.4 SAP-QR.  Returns (x, info dict with 'error' = Error(x))."""
+    """Sec. 5.3 SAP-QR.  Returns (x, info dict with 'error' = Error(x))."""
     cp, ri, va = _i32(colptr), _i32(rowidx), _f64(values)
     bb = _f64(b)
     x = np.zeros(n, dtype=np.float64)

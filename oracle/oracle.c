@@ -21,7 +21,7 @@
  *   - Alg. 3 (variant kji, regenerate S[:, j] for every nonzero) and Alg. 4
  *     (variant jki, generate S[:, j] once per nonempty row), both with one
  *     block covering all of d and n (Alg. 1 with b_d = d, b_n = n).
- *   - Sec. 5.4: SAP least squares -- Householder QR of A_hat, LSQR (Paige &
+ *   - Sec. 5.3: SAP least squares -- Householder QR of A_hat, LSQR (Paige &
  *     Saunders 1982) on the preconditioned operator A R^{-1}, and the error
  *     metric Error(x) = ||A^T (A x - b)||_2 / (||A||_F ||A x - b||_2).
  *
@@ -246,7 +246,7 @@ int64_t oracle_sketch_jki_rows(int64_t m, int64_t n, int64_t d, int dist,
 
 /* ------------------------------------------------------------------------ */
 /* Householder QR of a dense d x n matrix (column-major, d >= n), FP64.      */
-/* Sec. 5.4: the decomposition of the sketch that gives the preconditioner.  */
+/* Sec. 5.3: the decomposition of the sketch that gives the preconditioner.  */
 /* Convention: for column x, alpha = -sign(x_0) ||x||, v = x - alpha e_1,    */
 /* H = I - 2 v v^T / (v^T v); R(k,k) = alpha; when x(1:) is already zero the */
 /* reflector is the identity and R(k,k) = x_0.  Writes R (n x n, col-major  */
@@ -335,7 +335,7 @@ static void trsv_upper_t(int64_t n, const double* R, double* y) {
   }
 }
 
-/* Sec. 5.4 error metric: ||A^T (A x - b)|| / (||A||_F ||A x - b||). */
+/* Sec. 5.3 error metric: ||A^T (A x - b)|| / (||A||_F ||A x - b||). */
 double oracle_ls_error(int64_t m, int64_t n, const int32_t* colptr,
                        const int32_t* rowidx, const double* values,
                        const double* b, const double* x) {
@@ -354,7 +354,7 @@ double oracle_ls_error(int64_t m, int64_t n, const int32_t* colptr,
 
 /* ------------------------------------------------------------------------ */
 /* LSQR (Paige & Saunders, ACM TOMS 1982) on min || M y - b ||,              */
-/* M = A R^{-1} (or M = A when R is NULL), then x = R^{-1} y.  Sec. 5.4.     */
+/* M = A R^{-1} (or M = A when R is NULL), then x = R^{-1} y.  Sec. 5.3.     */
 /* Stopping rule (the solver's own estimates for the preconditioned system): */
 /*   test1 = ||r|| / ||b||                         <= tol + tol*||M||*||y||/||b|| */
 /*   test2 = ||M^T r|| / (||M||_F ||r||)           <= tol                     */
@@ -444,7 +444,7 @@ int oracle_lsqr(int64_t m, int64_t n, const int32_t* colptr,
   return istop ? 0 : 1;
 }
 
-/* Full SAP-QR pipeline (Sec. 5.4): A_hat = S A (Alg. 4 order, FP64),
+/* Full SAP-QR pipeline (Sec. 5.3): A_hat = S A (Alg. 4 order, FP64),
  * Householder QR of A_hat -> R, LSQR on A R^{-1}, x = R^{-1} y.
  * info as for oracle_lsqr, plus info[4] = Error(x). */
 int oracle_sap_qr_solve(int64_t m, int64_t n, int64_t d, int dist,

@@ -1,4 +1,4 @@
-// lsq.cu -- sketch-and-precondition least squares (Sec. 5.4) on the GPU.
+// lsq.cu -- sketch-and-precondition least squares (Sec. 5.3) on the GPU.
 //
 //   1. A_hat = S A (FP32, the sketch kernels; d = the handle's d, normally 2n)
 //   2. Householder QR of A_hat in FP64 -> R  (LAPACK-style reflectors

@@ -1,5 +1,5 @@
 // server.cpp -- continuous-batching server for sketch-and-precondition
-// least-squares requests (Sec. 5.4), host-side C++.
+// least-squares requests (Sec. 5.3), host-side C++.
 //
 // Worker threads (the "slots") each own a CUDA stream and one long-lived
 // sketch handle that is reshaped per request, so its workspaces are reused.

@@ -1,4 +1,4 @@
-"""Sketch-and-precondition least squares on the GPU (Sec. 5.4) against the
+"""Sketch-and-precondition least squares on the GPU (Sec. 5.3) against the
 FP64 oracle and LAPACK, through the C ABI.
 
 Gates: the device QR equals LAPACK's R (same Householder sign convention)

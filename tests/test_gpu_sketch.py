@@ -158,7 +158,7 @@ def test_tile_tensor_memory_sums_equal_register_sums(dist):
 @pytest.mark.parametrize("dist", ["pm1", "uniform", "normal"])
 @pytest.mark.parametrize("d,ld", [(100, 100), (98, 100), (61, 64), (300, 304)])
 def test_pregenerated_S_gives_the_generated_bits(dist, d, ld):
-    """Sec. 3.4's pre-generated S: S written to memory, then the TILE kernel
+    """Sec. 3.3's pre-generated S: S written to memory, then the TILE kernel
     reading it, equals the TILE kernel generating it bit for bit; the stored
     S matches the oracle's entries (ragged d, padded leading dimension)."""
     A = inputs.float_uniform(3000, 300, 0.02, seed=23)

@@ -1,4 +1,4 @@
-"""Pins for the oracle's SAP least-squares pieces (Sec. 5.4); CPU only.
+"""Pins for the oracle's SAP least-squares pieces (Sec. 5.3); CPU only.
 
 Householder QR is pinned to LAPACK (numpy.linalg.qr uses the same sign
 convention R(k,k) = -sign(x_0) ||x||); LSQR to SciPy's independent LSQR and
