@@ -109,3 +109,34 @@ def test_pregenerated_S_argument_errors_need_no_gpu():
     assert lib.sketch_apply_pregen(h, ctypes.byref(B), ctypes.c_void_p(4096), 32, out,
                                    None) == E
     assert lib.sketch_destroy(h) == capi.SKETCH_OK
+
+
+def test_heuristic_plans_need_no_gpu():
+    """With tuning off the plan is the heuristic's, chosen on the host:
+    +-1 -> REGEN; U and N -> TILE, with tensor-memory sums (32 warps x 32
+    columns, panels of 1152 rows) when n > 256; very sparse input -> REGEN."""
+    from paper_2310_15419_gb300 import capi
+    lib = capi.load()
+
+    def plan(m, n, d, dist, nnz):
+        h = ctypes.c_void_p()
+        assert lib.sketch_create(m, n, d, dist, 1, ctypes.byref(h)) == capi.SKETCH_OK
+        assert lib.sketch_set_autotune(h, 0) == capi.SKETCH_OK
+        A = capi.sketch_csc(m, n, nnz, 8, 8, 8, 0)
+        p = capi.sketch_plan()
+        assert lib.sketch_get_plan(h, ctypes.byref(A), ctypes.byref(p), None) == capi.SKETCH_OK
+        assert lib.sketch_destroy(h) == capi.SKETCH_OK
+        return p.as_dict()
+
+    p = plan(2_000_000, 1000, 3000, 0, 10_000_000)
+    assert (p["mode"], p["q_tiles"], p["split"]) == (capi.SKETCH_MODE_REGEN, 4, 8)
+    for dist in (1, 2):
+        p = plan(2_000_000, 1000, 3000, dist, 10_000_000)
+        assert (p["mode"], p["panel_rows"], p["cols_per_warp"], p["tile_acc"]) == \
+            (capi.SKETCH_MODE_TILE, 1152, 32, 1)
+        assert p["row_groups"] >= 20          # <= 512 terms of a column per group
+        p = plan(100_000, 200, 400, dist, 1_000_000)
+        assert (p["mode"], p["panel_rows"], p["cols_per_warp"], p["tile_acc"]) == \
+            (capi.SKETCH_MODE_TILE, 1024, 16, 0)
+        p = plan(100_000, 200, 400, dist, 500)
+        assert p["mode"] == capi.SKETCH_MODE_REGEN
