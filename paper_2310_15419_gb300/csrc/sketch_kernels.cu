@@ -724,11 +724,12 @@ cudaError_t launch_panel(const PanelArgs& a, cudaStream_t s, int* launches) {
 // ---------------------------------------------------------------------------
 // TILE: the three-level blocking of Sec. 3.1 (S_sub d1 x m1, A_sub m1 x n1).
 // A CTA owns a tile of 32 rows of S (d1 = 32) and a range of row panels of A
-// (m1 = R rows each) for a block of columns (n1 = 16 * CPW).  Per panel it
+// (m1 = R rows each) for a block of columns (n1 = warps * CPW).  Per panel it
 // generates S(tile, panel) ONCE into shared memory -- d1 * m1 entries, the
-// minimum -- then every warp sweeps its columns in CSC order with register
-// accumulators (lane = row of S), reading S from shared memory.  No atomics;
-// each output is written once per row group, so results are deterministic.
+// minimum -- then every warp sweeps its columns in CSC order, reading S from
+// shared memory, with its running sums in registers or in tensor memory.  No
+// atomics; each output is written once per row group, so results are
+// deterministic.
 // ---------------------------------------------------------------------------
 // TILE's S source besides the three distributions: S read from memory, as
 // written by k_generate_S (the "pre-generated S" of Fig. percent_peak).
