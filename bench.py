@@ -213,31 +213,47 @@ def generator_rates(torch, capi, sms):
     return out
 
 
-def cpu_baseline(A, d, seconds_budget, reps=1):
-    """The oracle as it stands, single thread, on a row sample of A."""
+def cpu_baseline(A, d, seconds_budget, reps=1, threads=1):
+    """The oracle as it stands on a row sample of A: the serial oracle
+    (threads = 1) or its OpenMP form on `threads` host cores (bit-identical
+    results, the rows of A_hat split between the threads)."""
     import oracle
     codes = {"pm1": oracle.PM1, "uniform": oracle.UNIFORM, "normal": oracle.NORMAL}
+
+    def run(dist, rows):
+        if threads == 1:
+            oracle.sketch_jki(A.m, A.n, d, codes[dist], 1, 0, A.colptr, A.rowidx,
+                              A.values, 0, rows)
+        else:
+            oracle.sketch_jki_omp(A.m, A.n, d, codes[dist], 1, 0, A.colptr, A.rowidx,
+                                  A.values, 0, rows, threads=threads)
     # calibrate on a small sample, then size the sample to the budget
-    rows = 2000
+    rows = 2000 * threads
     t0 = time.perf_counter()
     for dist in DISTS:
-        oracle.sketch_jki(A.m, A.n, d, codes[dist], 1, 0, A.colptr, A.rowidx,
-                          A.values, 0, rows)
+        run(dist, rows)
     per_row = (time.perf_counter() - t0) / rows
     rows = int(max(2000, min(A.m, seconds_budget / max(per_row, 1e-9))))
     nnz_rows = int(np.count_nonzero(A.rowidx < rows))
     t0 = time.perf_counter()
     for _ in range(reps):
         for dist in DISTS:
-            oracle.sketch_jki(A.m, A.n, d, codes[dist], 1, 0, A.colptr,
-                              A.rowidx, A.values, 0, rows)
+            run(dist, rows)
     sec = time.perf_counter() - t0
     flops = reps * len(DISTS) * 2.0 * d * nnz_rows
-    return {"value": flops / sec / 1e9, "unit": UNIT, "cores": 1,
-            "kind": "oracle",
+    return {"value": flops / sec / 1e9, "unit": UNIT, "cores": int(threads),
+            "kind": "oracle" if threads == 1 else "oracle-omp",
             "sample": "rows [0, %d) of the workload (%d nonzeros), all three "
-                      "distributions, FP64 Alg. 4 order, %.1f s" %
-                      (rows, nnz_rows, sec)}, sec
+                      "distributions, FP64 Alg. 4 order, %d thread%s, %.1f s" %
+                      (rows, nnz_rows, threads, "" if threads == 1 else "s", sec)}, sec
+
+
+def host_cores():
+    """Host cores this process may run on (the oracle's OpenMP threads)."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        return os.cpu_count() or 1
 
 
 def pct(xs, q):
@@ -648,9 +664,11 @@ def run_ours(args):
             extras["density"] = bench_density(torch, capi, inputs, rates, r_fma, hbm)
 
     # ---- CPU baseline: the oracle on a bounded row sample (rank 0, N = 1)
-    cpu = None
+    cpu = cpu1 = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        cpu, _ = cpu_baseline(A, d, args.cpu_seconds / len(DISTS))
+        cpu, _ = cpu_baseline(A, d, args.cpu_seconds / len(DISTS), threads=host_cores())
+        cpu["nproc"] = host_cores()
+        cpu1, _ = cpu_baseline(A, d, args.cpu_seconds / 2 / len(DISTS), threads=1)
 
     if rank == 0:
         line = {
@@ -667,6 +685,7 @@ def run_ours(args):
             "e2e": {"value": round(e2e_val, 3), "unit": UNIT,
                     "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
             "cpu_baseline": cpu,
+            "cpu_baseline_1core": cpu1,
             "gpu_launches": int(launches),
             "launches_before_timed": int(launches_before),
             "clocks": clk,
@@ -682,8 +701,8 @@ def run_ours(args):
 
 # -------------------------------------------------------- reference arm
 def run_reference(args):
-    """The oracle as it stands on the host cores: each step is a bounded row
-    sample of the same workload, all three distributions."""
+    """The oracle as it stands on all host cores (its OpenMP form): each step
+    is a bounded row sample of the same workload, all three distributions."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
@@ -691,11 +710,12 @@ def run_reference(args):
     cfg = workload_config(args.rows)
     A = inputs.skew_large(seed=cfg["seed_A"], m=args.rows)
     budget = max(0.3, 150.0 / max(1, args.steps + args.warmup))
+    cores = host_cores()
     for _ in range(args.warmup):
-        cpu_baseline(A, cfg["d"], budget / 3)
+        cpu_baseline(A, cfg["d"], budget / 3, threads=cores)
     vals, secs = [], []
     for _ in range(args.steps):
-        cb, sec = cpu_baseline(A, cfg["d"], budget / 3)
+        cb, sec = cpu_baseline(A, cfg["d"], budget / 3, threads=cores)
         vals.append(cb["value"])
         secs.append(sec)
     value = statistics.mean(vals)
@@ -705,7 +725,7 @@ def run_reference(args):
             "ms_per_step": round(1e3 * statistics.mean(secs), 3),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": dict(cfg, parallelism="single host thread"),
+            "config": dict(cfg, parallelism="%d host threads (OpenMP)" % cores),
             "cpu_baseline": cb,
             "e2e": {"value": round(value, 5), "unit": UNIT,
                     "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}

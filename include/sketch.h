@@ -168,7 +168,12 @@ int sketch_apply(sketch_t h, const sketch_csc* A, float* Ahat,
  * It always runs the PANEL kernel with a single row group (A_hat written
  * directly), and its scratch -- the device CSR copy of A -- is a fixed
  * array of about 10 MiB inside the library that every GPU loading the
- * library keeps until the process exits.
+ * library keeps until the process exits.  Each column is summed in one
+ * piece with compensated shared-memory atomics (the sum plus the exact
+ * rounding error of every addition), which keeps the 1e-6 relative error
+ * bound at the row limit; the hardware picks the order of the additions, so
+ * float results may differ in the last bit from call to call (+-1 S with
+ * integer-valued A is exact).
  *   Limits: A->m <= 262,144 and A->nnz <= 1,048,576, otherwise
  *   SKETCH_ERR_UNSUPPORTED.
  *   Sharing: every call uses the same array and finds the previous call's
@@ -206,7 +211,13 @@ const char* sketch_last_error(sketch_t h);
 /* Read and clear the device status word of the handle (synchronous):
  * 0, SKETCH_ERR_TIMEOUT if a kernel's bounded wait on the tensor cores gave
  * up (its output is then incomplete), or SKETCH_ERR_CSC if a kernel met a
- * row index outside [0, m). */
+ * row index outside [0, m) or a malformed colptr (decreasing, negative or past
+ * nnz; the kernels clamp every column range to [0, nnz] and never read or
+ * write outside A's arrays or their workspace, but A_hat is then not
+ * meaningful).  A timeout of a tensor-core plan drains the MMAs that CTA
+ * issued before it frees its tensor memory; if that drain also times out,
+ * the tensor cores did not finish work in time and the caller should treat
+ * the CUDA context as unreliable (destroy the handle, restart the process). */
 int sketch_device_status(sketch_t h, sketch_stream_t stream);
 
 /* Full CSC check on the device (synchronous): colptr[0] = 0, colptr
@@ -226,7 +237,8 @@ typedef struct sketch_batch_s* sketch_batch_t;
  * Alg. 1's outer blocking spread over instances.  Pointers in As / Ahats are
  * device pointers that must stay valid for the life of the batch.
  * Errors: SKETCH_ERR_ARG, SKETCH_ERR_UNSUPPORTED (mixed distributions),
- * SKETCH_ERR_OOM, SKETCH_ERR_CUDA. */
+ * SKETCH_ERR_CSC (a colptr that does not start at 0, decreases or does not
+ * end at nnz), SKETCH_ERR_OOM, SKETCH_ERR_CUDA. */
 int sketch_batch_create(int32_t count, const sketch_t* handles,
                         const sketch_csc* As, float* const* Ahats,
                         sketch_stream_t stream, sketch_batch_t* out);
@@ -269,10 +281,12 @@ typedef struct {
  * achieved Error(x) is returned in info->error either way (it can sit at
  * the FP64 floor of the metric for badly scaled, nearly consistent data).
  * b (m) and x (n) are FP64 device pointers.  Synchronous: returns when x
- * and *info are final.  Errors: SKETCH_ERR_ARG (d < n, tol <= 0),
+ * and *info are final.  A is checked on the device first (the checks of
+ * sketch_validate_csc); a malformed A returns SKETCH_ERR_CSC before any other
+ * kernel runs.  Errors: SKETCH_ERR_ARG (d < n, tol <= 0),
  * SKETCH_ERR_NO_CONVERGENCE (maxit reached; x holds the last iterate),
- * SKETCH_ERR_CSC (a zero column makes R singular), SKETCH_ERR_OOM,
- * SKETCH_ERR_CUDA. */
+ * SKETCH_ERR_CSC (malformed A, or a zero column makes R singular),
+ * SKETCH_ERR_OOM, SKETCH_ERR_CUDA. */
 int sketch_lsq_solve(sketch_t h, const sketch_csc* A, const double* b,
                      double* x, double tol, int32_t maxit,
                      sketch_lsq_info* info, sketch_stream_t stream);

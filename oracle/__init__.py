@@ -46,7 +46,7 @@ def build(force: bool = False) -> str:
             and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
         return _LIB
     tmp = _LIB + ".tmp.%d" % os.getpid()
-    cmd = ["gcc", "-O2", "-std=c11", "-Wall", "-shared", "-fPIC", "-o", tmp,
+    cmd = ["gcc", "-O2", "-std=c11", "-Wall", "-fopenmp", "-shared", "-fPIC", "-o", tmp,
            _SRC, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB)
@@ -82,6 +82,11 @@ def _load():
         lib.oracle_sketch_jki_rows.argtypes = [i64, i64, i64, i32, u64, u32, ip,
                                                ip, dp, dp, i64, i64]
         lib.oracle_sketch_jki_rows.restype = i64
+        lib.oracle_sketch_jki_omp.argtypes = [i64, i64, i64, i32, u64, u32, ip,
+                                              ip, dp, dp, i64, i64, i32]
+        lib.oracle_sketch_jki_omp.restype = i64
+        lib.oracle_max_threads.argtypes = []
+        lib.oracle_max_threads.restype = i32
         lib.oracle_householder_qr.argtypes = [i64, i64, dp, dp]
         lib.oracle_householder_qr.restype = i32
         lib.oracle_ls_error.argtypes = [i64, i64, ip, ip, dp, dp, dp]
@@ -155,6 +160,30 @@ def sketch_kji(m, n, d, dist, seed, stream, colptr, rowidx, values):
                                     _ptr(va, ctypes.c_double),
                                     _ptr(out, ctypes.c_double))
     return out.T, int(gen)
+
+
+def sketch_jki_omp(m, n, d, dist, seed, stream, colptr, rowidx, values,
+                   row_lo: int = 0, row_hi: int = -1, threads: int = 0):
+    """Alg. 4 order on all host cores (OpenMP; `threads` <= 0: the default
+    count), bit-identical to ``sketch_jki``: the rows of A_hat are split
+    between the threads, so each element's additions keep the serial order.
+    Returns (A_hat (d x n float64), S entries generated)."""
+    cp, ri, va = _i32(colptr), _i32(rowidx), _f64(values)
+    out = np.zeros((n, d), dtype=np.float64)
+    gen = _load().oracle_sketch_jki_omp(m, n, d, dist, seed, stream,
+                                        _ptr(cp, ctypes.c_int32),
+                                        _ptr(ri, ctypes.c_int32),
+                                        _ptr(va, ctypes.c_double),
+                                        _ptr(out, ctypes.c_double),
+                                        row_lo, row_hi, int(threads))
+    if gen < 0:
+        raise MemoryError("oracle_sketch_jki_omp: allocation failed")
+    return out.T, int(gen)
+
+
+def max_threads() -> int:
+    """Threads the oracle's OpenMP regions use by default."""
+    return int(_load().oracle_max_threads())
 
 
 def sketch_jki(m, n, d, dist, seed, stream, colptr, rowidx, values,

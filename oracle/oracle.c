@@ -43,6 +43,7 @@
  */
 #define _GNU_SOURCE
 #include <math.h>
+#include <omp.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -243,6 +244,102 @@ int64_t oracle_sketch_jki_rows(int64_t m, int64_t n, int64_t d, int dist,
   free(rowptr); free(cursor); free(csr_col); free(csr_val); free(v);
   return generated;
 }
+
+/* Entries S(i0:i1, j) into out[0 .. i1-i0): the same values as
+ * oracle_S_column, computed only for the rows asked for (the blocks that
+ * hold them). */
+static void S_rows(int dist, uint64_t seed, uint32_t stream, int64_t i0, int64_t i1,
+                   int64_t j, double* out) {
+  uint32_t x[4];
+  const int64_t per = (dist == ORACLE_PM1) ? 128 : 4;
+  for (int64_t b0 = (i0 / per) * per; b0 < i1; b0 += per) {
+    philox_block(seed, stream, (uint32_t)(b0 / per), (uint32_t)j, x);
+    for (int64_t i = (b0 > i0 ? b0 : i0); i < b0 + per && i < i1; ++i) {
+      const int q = (int)(i - b0);
+      double v;
+      if (dist == ORACLE_PM1)
+        v = ((x[q >> 5] >> (q & 31)) & 1u) ? -1.0 : 1.0;
+      else if (dist == ORACLE_UNIFORM)
+        v = oracle_uniform_from_word(x[q]);
+      else
+        v = oracle_normal_from_words(x[2 * (q >> 1)], x[2 * (q >> 1) + 1], q & 1);
+      out[i - i0] = v;
+    }
+  }
+}
+
+/* Alg. 4 (variant jki) on all host cores: the same CSR transpose and row
+ * order as oracle_sketch_jki_rows, with the rows of A_hat (rows of S) split
+ * into `threads` contiguous slices on Philox block boundaries.  A thread
+ * walks every nonempty row j in order, generates only its slice of S(:, j)
+ * and adds it into its slice of A_hat, so every element of A_hat receives
+ * exactly the serial oracle's additions in the serial oracle's order: the
+ * result is bit-identical to oracle_sketch_jki_rows, with no reduction.
+ * The total RNG work is the serial oracle's too (each block is generated by
+ * the one thread whose slice holds it).  threads <= 0: OpenMP's default.
+ * Returns the entries generated, or -1 on allocation failure. */
+int64_t oracle_sketch_jki_omp(int64_t m, int64_t n, int64_t d, int dist,
+                              uint64_t seed, uint32_t stream,
+                              const int32_t* colptr, const int32_t* rowidx,
+                              const double* values, double* Ahat,
+                              int64_t row_lo, int64_t row_hi, int threads) {
+  int64_t nnz = colptr[n];
+  int64_t* rowptr = (int64_t*)calloc((size_t)(m + 1), sizeof(int64_t));
+  int64_t* cursor = (int64_t*)malloc(sizeof(int64_t) * (size_t)(m + 1));
+  int64_t* csr_col = (int64_t*)malloc(sizeof(int64_t) * (size_t)(nnz > 0 ? nnz : 1));
+  double* csr_val = (double*)malloc(sizeof(double) * (size_t)(nnz > 0 ? nnz : 1));
+  if (!rowptr || !cursor || !csr_col || !csr_val) {
+    free(rowptr); free(cursor); free(csr_col); free(csr_val);
+    return -1;
+  }
+  for (int64_t p = 0; p < nnz; ++p) rowptr[rowidx[p] + 1]++;
+  for (int64_t j = 0; j < m; ++j) rowptr[j + 1] += rowptr[j];
+  memcpy(cursor, rowptr, sizeof(int64_t) * (size_t)(m + 1));
+  for (int64_t k = 0; k < n; ++k)
+    for (int64_t p = colptr[k]; p < colptr[k + 1]; ++p) {
+      int64_t q = cursor[rowidx[p]]++;
+      csr_col[q] = k;
+      csr_val[q] = values[p];
+    }
+  memset(Ahat, 0, sizeof(double) * (size_t)(d * n));
+  if (row_lo < 0) row_lo = 0;
+  if (row_hi > m || row_hi < 0) row_hi = m;
+  int64_t nonempty = 0;
+  for (int64_t j = row_lo; j < row_hi; ++j) nonempty += rowptr[j] != rowptr[j + 1];
+  const int64_t per = (dist == ORACLE_PM1) ? 128 : 4;
+  const int64_t blocks = (d + per - 1) / per;
+  int T = threads > 0 ? threads : omp_get_max_threads();
+  if (T > blocks) T = (int)blocks;
+  if (T < 1) T = 1;
+  int failed = 0;
+#pragma omp parallel for num_threads(T) schedule(static, 1) reduction(|| : failed)
+  for (int t = 0; t < T; ++t) {
+    const int64_t i0 = per * (blocks * t / T);
+    const int64_t i1t = per * (blocks * (t + 1) / T);
+    const int64_t i1 = i1t < d ? i1t : d;
+    if (i1 <= i0) continue;
+    double* v = (double*)malloc(sizeof(double) * (size_t)(i1 - i0));
+    if (!v) {
+      failed = 1;
+      continue;
+    }
+    for (int64_t j = row_lo; j < row_hi; ++j) {
+      if (rowptr[j] == rowptr[j + 1]) continue;
+      S_rows(dist, seed, stream, i0, i1, j, v);
+      for (int64_t q = rowptr[j]; q < rowptr[j + 1]; ++q) {
+        double a = csr_val[q];
+        double* col = Ahat + csr_col[q] * d;
+        for (int64_t i = i0; i < i1; ++i) col[i] += a * v[i - i0];
+      }
+    }
+    free(v);
+  }
+  free(rowptr); free(cursor); free(csr_col); free(csr_val);
+  return failed ? -1 : nonempty * d;
+}
+
+/* Threads an OpenMP region of this library would use by default. */
+int oracle_max_threads(void) { return omp_get_max_threads(); }
 
 /* ------------------------------------------------------------------------ */
 /* Householder QR of a dense d x n matrix (column-major, d >= n), FP64.      */

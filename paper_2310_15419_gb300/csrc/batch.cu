@@ -101,6 +101,14 @@ int sketch_batch_create(int32_t count, const sketch_t* handles,
   }
   if (cudaStreamSynchronize(s) != cudaSuccess)
     return sk::fail(nullptr, SKETCH_ERR_CUDA, "reading colptr");
+  // the work list and the persistent kernel walk these column ranges: they
+  // must start at 0, never decrease and end at nnz
+  for (int32_t i = 0; i < count; ++i) {
+    const std::vector<int32_t>& cp = colptrs[i];
+    bool ok = cp[0] == 0 && cp[As[i].n] == As[i].nnz;
+    for (int64_t k = 0; ok && k < As[i].n; ++k) ok = cp[k] <= cp[k + 1];
+    if (!ok) return sk::fail(nullptr, SKETCH_ERR_CSC, "malformed colptr in batch instance");
+  }
 
   sketch_batch_t b = new (std::nothrow) sketch_batch_s();
   if (!b) return sk::fail(nullptr, SKETCH_ERR_OOM, "host allocation failed");

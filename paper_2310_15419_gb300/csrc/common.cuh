@@ -142,4 +142,19 @@ constexpr int kStatusBadRow = 1;
 constexpr int kStatusBadColptr = 2;
 constexpr int kStatusTimeout = 4;  // a bounded wait inside a kernel gave up
 
+// Column k's nonzeros [lo, hi) of a CSC with nnz entries, clamped so that
+// 0 <= lo <= hi <= nnz whatever colptr holds: a malformed colptr (decreasing,
+// negative or past nnz) is recorded in *status and never turns into an
+// out-of-range read.  (Overlapping column ranges stay in bounds too; the
+// kernels that scatter by such ranges check their write positions.)
+__device__ __forceinline__ int2 column_range(const int32_t* __restrict__ colptr, int64_t k,
+                                             int64_t nnz, int* status) {
+  const int64_t p0 = colptr[k], p1 = colptr[k + 1];
+  const int64_t lo64 = p0 < 0 ? 0 : (p0 > nnz ? nnz : p0);
+  const int64_t hi64 = p1 < lo64 ? lo64 : (p1 > nnz ? nnz : p1);
+  const int32_t lo = static_cast<int32_t>(lo64), hi = static_cast<int32_t>(hi64);
+  if ((lo64 != p0 || hi64 != p1) && status) atomicOr(status, kStatusBadColptr);
+  return make_int2(lo, hi);
+}
+
 }  // namespace sk

@@ -62,7 +62,7 @@ __global__ void k_dense_index(int32_t m, const int32_t* __restrict__ flag,
 
 // A3[k * K3 + t * Kp + didx[j]] = t-th BF16 term of A(j, k) for dense rows.
 template <typename VT>
-__global__ void k_dense_scatter(int32_t n, int32_t m, int32_t Kp,
+__global__ void k_dense_scatter(int32_t n, int32_t m, int32_t Kp, int64_t nnz,
                                 const int32_t* __restrict__ colptr,
                                 const int32_t* __restrict__ rowidx,
                                 const VT* __restrict__ vals,
@@ -73,7 +73,8 @@ __global__ void k_dense_scatter(int32_t n, int32_t m, int32_t Kp,
   const int64_t K3 = 3LL * Kp;
   for (int64_t k = blockIdx.x * static_cast<int64_t>(blockDim.x >> 5) + (threadIdx.x >> 5);
        k < n; k += warps) {
-    for (int32_t e = colptr[k] + lane; e < colptr[k + 1]; e += 32) {
+    const int2 range = column_range(colptr, k, nnz, nullptr);
+    for (int32_t e = range.x + lane; e < range.y; e += 32) {
       const int32_t j = rowidx[e];
       if (static_cast<uint32_t>(j) >= static_cast<uint32_t>(m)) continue;
       const int32_t q = didx[j];
@@ -159,7 +160,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
               int accumulate, int* status) {
   extern __shared__ uint8_t sm_raw[];
   __shared__ uint32_t sbits[kBK][4];
-  __shared__ __align__(8) uint64_t mbar[kUmmaStages];
+  // one mbarrier per stage, plus one that only the drain commit of the
+  // failure path arrives on
+  __shared__ __align__(8) uint64_t mbar[kUmmaStages + 1];
   __shared__ uint32_t tmem_base;
   __shared__ int failed;
   uint8_t* base = sm_raw + ((1024u - (smem_u32(sm_raw) & 1023u)) & 1023u);
@@ -188,7 +191,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   };
   if (tid == 0) {
     failed = 0;
-    for (int q = 0; q < kUmmaStages; ++q)
+    for (int q = 0; q <= kUmmaStages; ++q)
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[q])) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -276,6 +279,19 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   if (!failed && tid == 0 &&
       !mbar_wait(smem_u32(&mbar[(steps - 1) % kUmmaStages]), ((steps - 1) / kUmmaStages) & 1))
     failed = 1;
+  // After a timeout, MMAs issued earlier may still be running and writing
+  // tensor memory: one more commit (it arrives once every MMA this thread
+  // issued has completed) drains them before the memory is freed.  If even
+  // that wait runs out, kStatusTimeout still goes to the host, and the
+  // tensor-memory columns are freed with work possibly in flight (the error
+  // documentation tells the caller to treat the context as unreliable).
+  if (failed && tid == 0) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_u32(&mbar[kUmmaStages]))
+        : "memory");
+    mbar_wait(smem_u32(&mbar[kUmmaStages]), 0);
+  }
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (!failed) {
@@ -373,18 +389,23 @@ __device__ __forceinline__ bool rest_keeps(int32_t j, int32_t m, const int32_t* 
   return static_cast<uint32_t>(j) >= static_cast<uint32_t>(m) || didx[j] < 0;
 }
 
-// rcnt[k] = entries of column k outside the panel; rcnt[n] = 0.
-__global__ void k_rest_count(int32_t n, int32_t m, const int32_t* __restrict__ colptr,
+// rcnt[k] = entries of column k outside the panel; rcnt[n] = 0.  A malformed
+// colptr is recorded in *status (its column ranges are clamped to [0, nnz]).
+__global__ void k_rest_count(int32_t n, int32_t m, int64_t nnz,
+                             const int32_t* __restrict__ colptr,
                              const int32_t* __restrict__ rowidx,
-                             const int32_t* __restrict__ didx, int32_t* __restrict__ rcnt) {
+                             const int32_t* __restrict__ didx, int32_t* __restrict__ rcnt,
+                             int* status) {
   const int lane = threadIdx.x & 31;
   const int64_t warps = static_cast<int64_t>(gridDim.x) * (blockDim.x >> 5);
   for (int64_t k = blockIdx.x * static_cast<int64_t>(blockDim.x >> 5) + (threadIdx.x >> 5);
        k <= n; k += warps) {
     int32_t c = 0;
-    if (k < n)
-      for (int32_t e = colptr[k] + lane; e < colptr[k + 1]; e += 32)
+    if (k < n) {
+      const int2 range = column_range(colptr, k, nnz, lane == 0 ? status : nullptr);
+      for (int32_t e = range.x + lane; e < range.y; e += 32)
         c += rest_keeps(rowidx[e], m, didx);
+    }
     for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
     if (lane == 0) rcnt[k] = c;
   }
@@ -392,8 +413,11 @@ __global__ void k_rest_count(int32_t n, int32_t m, const int32_t* __restrict__ c
 
 // The kept entries of column k, in their order, at rcolptr[k].. (one warp
 // per column, ballot compaction).
+// (Write positions stay below nnz: overlapping column ranges of a malformed
+// colptr could otherwise count more kept entries than A holds.)
 template <typename VT>
-__global__ void k_rest_copy(int32_t n, int32_t m, const int32_t* __restrict__ colptr,
+__global__ void k_rest_copy(int32_t n, int32_t m, int64_t nnz,
+                            const int32_t* __restrict__ colptr,
                             const int32_t* __restrict__ rowidx, const VT* __restrict__ vals,
                             const int32_t* __restrict__ didx,
                             const int32_t* __restrict__ rcolptr,
@@ -404,8 +428,9 @@ __global__ void k_rest_copy(int32_t n, int32_t m, const int32_t* __restrict__ co
   for (int64_t k = blockIdx.x * static_cast<int64_t>(blockDim.x >> 5) + (threadIdx.x >> 5);
        k < n; k += warps) {
     int32_t out = rcolptr[k];
-    const int32_t hi = colptr[k + 1];
-    for (int32_t e0 = colptr[k]; e0 < hi; e0 += 32) {
+    const int2 range = column_range(colptr, k, nnz, nullptr);
+    const int32_t hi = range.y;
+    for (int32_t e0 = range.x; e0 < hi; e0 += 32) {
       const int32_t e = e0 + lane;
       int32_t j = 0;
       bool keep = false;
@@ -416,8 +441,10 @@ __global__ void k_rest_copy(int32_t n, int32_t m, const int32_t* __restrict__ co
       const unsigned mask = __ballot_sync(0xffffffffu, keep);
       if (keep) {
         const int32_t pos = out + __popc(mask & below);
-        rrowidx[pos] = j;
-        rvals[pos] = vals[e];
+        if (static_cast<uint32_t>(pos) < static_cast<uint64_t>(nnz)) {
+          rrowidx[pos] = j;
+          rvals[pos] = vals[e];
+        }
       }
       out += __popc(mask);
     }
@@ -465,8 +492,9 @@ cudaError_t select_dense_rows(const DenseArgs& a, void* ws, DenseView* out, cuda
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   // the rest of A: per-column counts and offsets (rest_colptr[n] = its nnz)
   const int64_t wblocks = std::max<int64_t>(1, std::min<int64_t>((a.n + 8) / 8, 32LL * sms));
-  k_rest_count<<<static_cast<unsigned>(wblocks), 256, 0, s>>>(a.n, a.m, a.colptr, a.rowidx,
-                                                              L.didx, L.rcnt);
+  k_rest_count<<<static_cast<unsigned>(wblocks), 256, 0, s>>>(a.n, a.m, a.nnz, a.colptr,
+                                                              a.rowidx, L.didx, L.rcnt,
+                                                              a.status);
   ++*launches;
   return scan_i32(L.rcnt, L.rcolptr, a.n + 1, L.scan_tmp, s, launches);
 }
@@ -482,11 +510,11 @@ cudaError_t build_dense_panel(const DenseArgs& a, int32_t K, DenseView* v, cudaS
   const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((a.n + 7) / 8, 32LL * num_sms()));
   if (a.dtype == 0)
     k_dense_scatter<float><<<static_cast<unsigned>(blocks), 256, 0, s>>>(
-        a.n, a.m, static_cast<int32_t>(Kp), a.colptr, a.rowidx,
+        a.n, a.m, static_cast<int32_t>(Kp), a.nnz, a.colptr, a.rowidx,
         static_cast<const float*>(a.values), v->didx, A3);
   else
     k_dense_scatter<__nv_bfloat16><<<static_cast<unsigned>(blocks), 256, 0, s>>>(
-        a.n, a.m, static_cast<int32_t>(Kp), a.colptr, a.rowidx,
+        a.n, a.m, static_cast<int32_t>(Kp), a.nnz, a.colptr, a.rowidx,
         static_cast<const __nv_bfloat16*>(a.values), v->didx, A3);
   ++*launches;
   return cudaGetLastError();
@@ -499,12 +527,12 @@ cudaError_t build_dense_rest(const DenseArgs& a, const DenseView& v, cudaStream_
   const int64_t wblocks = std::max<int64_t>(1, std::min<int64_t>((a.n + 8) / 8, 32LL * num_sms()));
   if (a.dtype == 0)
     k_rest_copy<float><<<static_cast<unsigned>(wblocks), 256, 0, s>>>(
-        a.n, a.m, a.colptr, a.rowidx, static_cast<const float*>(a.values), v.didx,
+        a.n, a.m, a.nnz, a.colptr, a.rowidx, static_cast<const float*>(a.values), v.didx,
         v.rest_colptr, const_cast<int32_t*>(v.rest_rowidx),
         static_cast<float*>(const_cast<void*>(v.rest_values)));
   else
     k_rest_copy<__nv_bfloat16><<<static_cast<unsigned>(wblocks), 256, 0, s>>>(
-        a.n, a.m, a.colptr, a.rowidx, static_cast<const __nv_bfloat16*>(a.values), v.didx,
+        a.n, a.m, a.nnz, a.colptr, a.rowidx, static_cast<const __nv_bfloat16*>(a.values), v.didx,
         v.rest_colptr, const_cast<int32_t*>(v.rest_rowidx),
         static_cast<__nv_bfloat16*>(const_cast<void*>(v.rest_values)));
   ++*launches;

@@ -13,6 +13,7 @@ namespace sk {
 struct RegenArgs {
   int32_t m, n, d;
   int32_t dtype;  // 0 = f32, 1 = bf16
+  int64_t nnz;
   const int32_t* colptr;
   const int32_t* rowidx;
   const void* values;
@@ -68,9 +69,10 @@ struct PanelArgs {
   int32_t dist;
   int32_t n_block;
   int32_t row_groups;
+  int32_t compensated;  // 1: compensated shared-memory sums (k_panel COMP)
   unsigned long long* gen_count;
 };
-size_t panel_smem_bytes(int32_t n_block);
+size_t panel_smem_bytes(int32_t n_block, bool compensated);
 cudaError_t launch_panel(const PanelArgs& a, cudaStream_t s, int* launches);
 
 struct TileArgs {

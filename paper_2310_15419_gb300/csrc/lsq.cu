@@ -1361,6 +1361,21 @@ extern "C" int sketch_lsq_solve(sketch_t h, const sketch_csc* A,
   cudaStreamWaitEvent(s, st.ev[4], 0);
   cudaEventRecord(st.ev[0], s);
 
+  // ---- 0. a malformed CSC is refused before any kernel walks its columns ---
+  {
+    int bad = 0;
+    cudaError_t ve = cudaMemsetAsync(L.status, 0, sizeof(int), s);
+    if (ve == cudaSuccess)
+      ve = launch_validate(static_cast<int32_t>(m), static_cast<int32_t>(n), nnz, A->colptr,
+                           A->rowidx, L.status, s);
+    if (ve == cudaSuccess)
+      ve = cudaMemcpyAsync(&bad, L.status, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (ve == cudaSuccess) ve = cudaStreamSynchronize(s);
+    if (ve != cudaSuccess) return cuda_fail(h, ve, "CSC check (lsq)");
+    h->launches += 1;
+    if (bad) return fail(h, SKETCH_ERR_CSC, "malformed CSC (colptr or row indices)");
+  }
+
   // ---- 1. sketch ------------------------------------------------------------
   if ((rc = sketch_apply(h, A, L.Ahat, reinterpret_cast<sketch_stream_t>(s))) != SKETCH_OK)
     return rc;

@@ -1,6 +1,11 @@
 // noalloc.cu -- sketch_apply_noalloc: the PANEL sketch (one row group, so it
 // writes A_hat directly) with its scratch in a fixed device array instead of
-// a cudaMalloc'd workspace.
+// a cudaMalloc'd workspace.  Its shared-memory sums are compensated (every
+// atomic add also adds its own rounding error into a second array), so a
+// column summed in one piece -- up to the whole row limit -- stays within
+// about one rounding of the exact result.  The atomics leave the order of the
+// additions to the hardware, so the last bit of a float result can differ
+// between calls; +-1 S with integer-valued A is exact in any order.
 //
 // Why it exists: some callers cannot let a library allocate device memory
 // while they run -- e.g. a process whose device memory is entirely handed out
@@ -113,8 +118,10 @@ extern "C" int sketch_apply_noalloc(sketch_t h, const sketch_csc* A,
   a.k1 = h->k1;
   a.stream_id = h->stream_id;
   a.dist = h->dist;
-  a.n_block = static_cast<int32_t>(A->n < 1024 ? A->n : 1024);
+  // two shared-memory arrays (sums, compensation) of 32 x n_block floats
+  a.n_block = static_cast<int32_t>(A->n < 768 ? A->n : 768);
   a.row_groups = 1;
+  a.compensated = 1;
   a.gen_count = nullptr;
   e = launch_panel(a, s, &launches);
   h->launches += launches;

@@ -248,6 +248,9 @@ int run_plan(sketch_t h, const sketch_csc* A, float* Ahat,
                           cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(h, e, "dense row count");
+    // overlapping column ranges of a malformed colptr (flagged on the
+    // device) can count more kept entries than A holds
+    if (rest_nnz < 0 || rest_nnz > A->nnz) rest_nnz = static_cast<int32_t>(A->nnz);
     if (K > 0) {
       nl = 0;
       e = build_dense_panel(da, K, &dv, s, &nl);
@@ -285,6 +288,7 @@ int run_sparse(sketch_t h, const sketch_csc* A, float* Ahat, const sketch_plan& 
     a.n = static_cast<int32_t>(A->n);
     a.d = static_cast<int32_t>(h->d);
     a.dtype = A->dtype;
+    a.nnz = A->nnz;
     a.colptr = A->colptr;
     a.rowidx = A->rowidx;
     a.values = A->values;

@@ -144,7 +144,7 @@ __device__ __forceinline__ unsigned long long regen_accumulate(
 
 template <int DIST, int Q, typename VT>
 __global__ void __launch_bounds__(kRegenWarps * 32, 2)
-    k_regen(int32_t m, int32_t n, int32_t d, int32_t split,
+    k_regen(int32_t m, int32_t n, int32_t d, int32_t split, int64_t nnz,
             const int32_t* __restrict__ colptr,
             const int32_t* __restrict__ rowidx, const VT* __restrict__ vals,
             float* __restrict__ Ahat, uint32_t k0, uint32_t k1,
@@ -174,12 +174,9 @@ __global__ void __launch_bounds__(kRegenWarps * 32, 2)
   unsigned long long generated = 0;
 
   if (valid) {
-    int32_t p0 = colptr[k], p1 = colptr[k + 1];
-    if (p1 < p0) {
-      atomicOr(status, kStatusBadColptr);
-      p1 = p0;
-    }
-    const int32_t len = p1 - p0;
+    const int2 range = column_range(colptr, k, nnz, status);
+    const int32_t p0 = range.x;
+    const int32_t len = range.y - range.x;
     const int32_t chunk = (len + split - 1) / split;
     const int32_t lo = p0 + min(len, sub * chunk);
     const int32_t hi = p0 + min(len, (sub + 1) * chunk);
@@ -317,7 +314,7 @@ static cudaError_t launch_regen_q(const RegenArgs& a, cudaStream_t s) {
 #define SK_REGEN_CASE(QQ)                                                   \
   case QQ:                                                                  \
     k_regen<DIST, QQ, VT><<<grid, block, 0, s>>>(                           \
-        a.m, a.n, a.d, a.split, a.colptr, a.rowidx, v, a.Ahat, a.k0, a.k1, \
+        a.m, a.n, a.d, a.split, a.nnz, a.colptr, a.rowidx, v, a.Ahat, a.k0, a.k1, \
         a.stream_id, a.status, a.gen_count);                                \
     break;
   switch (a.q_tiles) {
@@ -455,25 +452,32 @@ static cudaError_t exclusive_scan(const int32_t* in, int32_t* out, int64_t len,
   return cudaGetLastError();
 }
 
+// Each column's nonzeros go to their rows' next free slots.  A slot past the
+// row's end (only possible when colptr's column ranges overlap) is not
+// written; the malformed colptr is recorded instead.
 template <typename VT>
-__global__ void k_csr_scatter(int32_t n, int32_t m,
+__global__ void k_csr_scatter(int32_t n, int32_t m, int64_t nnz,
                               const int32_t* __restrict__ colptr,
                               const int32_t* __restrict__ rowidx,
                               const VT* __restrict__ vals,
                               const int32_t* __restrict__ rowptr,
                               int32_t* __restrict__ cursor,
                               int32_t* __restrict__ ccol,
-                              float* __restrict__ cval) {
+                              float* __restrict__ cval, int* status) {
   const int lane = threadIdx.x & 31;
   const int64_t warps = static_cast<int64_t>(gridDim.x) * (blockDim.x >> 5);
   for (int64_t k = blockIdx.x * static_cast<int64_t>(blockDim.x >> 5) +
                    (threadIdx.x >> 5);
        k < n; k += warps) {
-    const int32_t p0 = colptr[k], p1 = colptr[k + 1];
-    for (int32_t p = p0 + lane; p < p1; p += 32) {
+    const int2 range = column_range(colptr, k, nnz, status);
+    for (int32_t p = range.x + lane; p < range.y; p += 32) {
       const int32_t j = rowidx[p];
       if (static_cast<uint32_t>(j) >= static_cast<uint32_t>(m)) continue;
       const int32_t pos = rowptr[j] + atomicAdd(&cursor[j], 1);
+      if (pos >= rowptr[j + 1]) {
+        atomicOr(status, kStatusBadColptr);
+        continue;
+      }
       ccol[pos] = static_cast<int32_t>(k);
       cval[pos] = to_f32(vals[p]);
     }
@@ -524,13 +528,13 @@ cudaError_t build_csr(int32_t m, int32_t n, int64_t nnz, const int32_t* colptr,
     const int64_t blocks = std::min<int64_t>((n + 7) / 8, 32LL * sms);
     if (dtype == 0)
       k_csr_scatter<float><<<static_cast<unsigned>(blocks), 256, 0, s>>>(
-          n, m, colptr, rowidx, static_cast<const float*>(values), rowptr, cnt,
-          ccol, cval);
+          n, m, nnz, colptr, rowidx, static_cast<const float*>(values), rowptr, cnt,
+          ccol, cval, status);
     else
       k_csr_scatter<__nv_bfloat16><<<static_cast<unsigned>(blocks), 256, 0,
                                      s>>>(
-          n, m, colptr, rowidx, static_cast<const __nv_bfloat16*>(values),
-          rowptr, cnt, ccol, cval);
+          n, m, nnz, colptr, rowidx, static_cast<const __nv_bfloat16*>(values),
+          rowptr, cnt, ccol, cval, status);
     ++*launches;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
@@ -547,12 +551,26 @@ constexpr int kPanelWarps = 16;
 constexpr int kPanelRows = 32;  // rows of S per CTA
 constexpr int kBatchRows = 8;   // rows of A a warp takes at a time
 
-size_t panel_smem_bytes(int32_t n_block) {
-  return static_cast<size_t>(n_block) * kPanelRows * sizeof(float) +
+size_t panel_smem_bytes(int32_t n_block, bool compensated) {
+  return static_cast<size_t>(n_block) * kPanelRows * sizeof(float) * (compensated ? 2 : 1) +
          kPanelWarps * kBatchRows * 32 * sizeof(float);
 }
 
-template <int DIST>
+// old + x as the atomic add stored it (round to nearest even), and the exact
+// rounding error of that addition (Knuth's TwoSum), so that
+// old + x = fl(old + x) + err holds exactly.
+__device__ __forceinline__ float two_sum_err(float old, float x) {
+  const float s = __fadd_rn(old, x);
+  const float bb = __fsub_rn(s, old);
+  return __fadd_rn(__fsub_rn(old, __fsub_rn(s, bb)), __fsub_rn(x, bb));
+}
+
+// COMP = true: every shared-memory atomic add also adds its own rounding
+// error (two_sum_err of the value it replaced and the addend) into a second
+// array, and the output is sum + compensation.  A column's whole nonzero list
+// can then be summed in one row group (no partial buffers) and still keep
+// the error near one rounding of the result, however long the column is.
+template <int DIST, bool COMP>
 __global__ void __launch_bounds__(kPanelWarps * 32, 1)
     k_panel(int32_t m, int32_t n, int32_t d, int32_t nb, int32_t G,
             const int32_t* __restrict__ rowptr,
@@ -565,8 +583,12 @@ __global__ void __launch_bounds__(kPanelWarps * 32, 1)
   const int g = blockIdx.z;
   const int32_t nbw = min(nb, n - kb0);
   float* acc = smem;                                // [nbw][32]
-  float* stage_all = smem + static_cast<size_t>(nb) * kPanelRows;
-  for (int t = threadIdx.x; t < nbw * kPanelRows; t += blockDim.x) acc[t] = 0.f;
+  float* comp = smem + static_cast<size_t>(nb) * kPanelRows;  // [nbw][32] (COMP)
+  float* stage_all = smem + static_cast<size_t>(nb) * kPanelRows * (COMP ? 2 : 1);
+  for (int t = threadIdx.x; t < nbw * kPanelRows; t += blockDim.x) {
+    acc[t] = 0.f;
+    if constexpr (COMP) comp[t] = 0.f;
+  }
   __syncthreads();
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -646,8 +668,11 @@ __global__ void __launch_bounds__(kPanelWarps * 32, 1)
         }
         const int32_t kt = __shfl_sync(0xffffffffu, kk, e - chunk);
         const float at = __shfl_sync(0xffffffffu, aa, e - chunk);
-        if (static_cast<uint32_t>(kt) < static_cast<uint32_t>(nbw))
-          atomicAdd(&acc[kt * kPanelRows + lane], at * sv[rr]);
+        if (static_cast<uint32_t>(kt) < static_cast<uint32_t>(nbw)) {
+          const float x = at * sv[rr];
+          const float old = atomicAdd(&acc[kt * kPanelRows + lane], x);
+          if constexpr (COMP) atomicAdd(&comp[kt * kPanelRows + lane], two_sum_err(old, x));
+        }
       }
     }
   }
@@ -656,7 +681,11 @@ __global__ void __launch_bounds__(kPanelWarps * 32, 1)
                static_cast<int64_t>(tile) * kPanelRows;
   for (int t = threadIdx.x; t < nbw * kPanelRows; t += blockDim.x) {
     const int kk2 = t >> 5, i = t & 31;
-    if (i < rows_valid) out[static_cast<int64_t>(kk2) * d + i] = acc[t];
+    if (i < rows_valid) {
+      float v = acc[t];
+      if constexpr (COMP) v += comp[t];
+      out[static_cast<int64_t>(kk2) * d + i] = v;
+    }
   }
   if (gen_count) {
     // lanes 0, 8, 16, 24 counted different rows: sum over the warp
@@ -681,7 +710,7 @@ __global__ void k_reduce_partials(int64_t total, int32_t G,
 
 cudaError_t launch_panel(const PanelArgs& a, cudaStream_t s, int* launches) {
   if (a.n_block <= 0 || a.row_groups <= 0) return cudaErrorInvalidValue;
-  const size_t smem = panel_smem_bytes(a.n_block);
+  const size_t smem = panel_smem_bytes(a.n_block, a.compensated != 0);
   const int tiles = (a.d + kPanelRows - 1) / kPanelRows;
   const int cblocks = (a.n + a.n_block - 1) / a.n_block;
   if (cblocks > 65535 || a.row_groups > 65535) return cudaErrorInvalidValue;
@@ -689,25 +718,23 @@ cudaError_t launch_panel(const PanelArgs& a, cudaStream_t s, int* launches) {
   cudaError_t e;
   // a single row group writes straight into A_hat
   float* dst = a.row_groups == 1 ? a.Ahat : a.partial;
-#define SK_PANEL_CASE(DD)                                                    \
-  case DD:                                                                   \
-    e = cudaFuncSetAttribute(k_panel<DD>,                                    \
+#define SK_PANEL_CASE(DD, CC)                                                \
+  if (a.dist == DD && (a.compensated != 0) == CC) {                          \
+    e = cudaFuncSetAttribute(k_panel<DD, CC>,                                \
                              cudaFuncAttributeMaxDynamicSharedMemorySize,    \
                              static_cast<int>(smem));                        \
     if (e != cudaSuccess) return e;                                          \
-    k_panel<DD><<<grid, block, smem, s>>>(                                   \
+    k_panel<DD, CC><<<grid, block, smem, s>>>(                               \
         a.m, a.n, a.d, a.n_block, a.row_groups, a.csr.rowptr, a.csr.ccol,    \
         a.csr.cval, dst, a.k0, a.k1, a.stream_id, a.gen_count);              \
     ++*launches;                                                             \
-    break;
-  switch (a.dist) {
-    SK_PANEL_CASE(kPM1)
-    SK_PANEL_CASE(kUniform)
-    SK_PANEL_CASE(kNormal)
-    default:
-      return cudaErrorInvalidValue;
+    launched = true;                                                         \
   }
+  bool launched = false;
+  SK_PANEL_CASE(kPM1, false) SK_PANEL_CASE(kUniform, false) SK_PANEL_CASE(kNormal, false)
+  SK_PANEL_CASE(kPM1, true) SK_PANEL_CASE(kUniform, true) SK_PANEL_CASE(kNormal, true)
 #undef SK_PANEL_CASE
+  if (!launched) return cudaErrorInvalidValue;
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (a.row_groups > 1) {
     const int64_t total = static_cast<int64_t>(a.n) * a.d;
@@ -749,15 +776,16 @@ __host__ __device__ constexpr int tile_warp_buf(bool tacc) { return tacc ? 256 :
 
 // pp[p * n + k] = first position of column k whose row is >= p * R
 // (p = 0..P): a binary search over the column's sorted rows.
-__global__ void k_panel_pointers(int32_t n, int32_t P, int32_t R,
+__global__ void k_panel_pointers(int32_t n, int32_t P, int32_t R, int64_t nnz,
                                  const int32_t* __restrict__ colptr,
                                  const int32_t* __restrict__ rowidx,
-                                 int32_t* __restrict__ pp) {
+                                 int32_t* __restrict__ pp, int* status) {
   const int64_t total = static_cast<int64_t>(P + 1) * n;
   for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
        t < total; t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
     const int32_t p = static_cast<int32_t>(t / n), k = static_cast<int32_t>(t % n);
-    int32_t lo = colptr[k], hi = colptr[k + 1];
+    const int2 range = column_range(colptr, k, nnz, p == 0 ? status : nullptr);
+    int32_t lo = range.x, hi = range.y;
     const int64_t key = static_cast<int64_t>(p) * R;
     while (lo < hi) {
       const int32_t mid = lo + ((hi - lo) >> 1);
@@ -775,7 +803,8 @@ __global__ void k_panel_counts(int32_t n, int32_t P, const int32_t* __restrict__
   for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
        t < cells; t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
     const int64_t p = t / (n + 1), k = t % (n + 1);
-    cnt[t] = (p < P && k < n) ? pp[(p + 1) * n + k] - pp[p * n + k] : 0;
+    // negative only for rows not sorted within a column (malformed input)
+    cnt[t] = (p < P && k < n) ? max(0, pp[(p + 1) * n + k] - pp[p * n + k]) : 0;
   }
 }
 
@@ -784,7 +813,7 @@ __global__ void k_panel_counts(int32_t n, int32_t P, const int32_t* __restrict__
 // offset in the [R][32] S tile.  A row outside the panel (unsorted
 // or out-of-range input) becomes (0, 0.0) and is flagged.
 template <typename VT>
-__global__ void k_panel_copy(int32_t n, int32_t P, int32_t R, int32_t m,
+__global__ void k_panel_copy(int32_t n, int32_t P, int32_t R, int32_t m, int64_t nnz,
                              const int32_t* __restrict__ rowidx,
                              const VT* __restrict__ vals,
                              const int32_t* __restrict__ pp,
@@ -798,6 +827,10 @@ __global__ void k_panel_copy(int32_t n, int32_t P, int32_t R, int32_t m,
     int32_t dst = off[p * (n + 1) + k];
     const int32_t j0 = static_cast<int32_t>(p * R);
     for (int32_t e = lo; e < hi; ++e, ++dst) {
+      if (dst >= nnz) {  // only for rows not sorted within a column
+        atomicOr(status, kStatusBadRow);
+        break;
+      }
       const int32_t jl = rowidx[e] - j0;
       if (static_cast<uint32_t>(jl) < static_cast<uint32_t>(R) && j0 + jl < m) {
         packed[dst] = make_int2(jl * 32, __float_as_int(to_f32(vals[e])));
@@ -846,7 +879,7 @@ __device__ __forceinline__ void tmem_wait_st() {
 template <int DIST, int CPW, bool TACC>
 __global__ void __launch_bounds__(tile_warps(TACC) * 32, 1)
     k_tile(int32_t m, int32_t n, int32_t d, int32_t R, int32_t P, int32_t G,
-           const int2* __restrict__ packed, const int32_t* __restrict__ off,
+           const int2* __restrict__ packed, const int32_t* __restrict__ off, int32_t nnz,
            float* __restrict__ out, const __grid_constant__ PhiloxKeys keys,
            uint32_t stream_id, unsigned long long* gen_count,
            const float* __restrict__ S_mem, int64_t ld_s) {
@@ -911,7 +944,8 @@ __global__ void __launch_bounds__(tile_warps(TACC) * 32, 1)
 #pragma unroll
     for (int u = 0; u < OFFR; ++u) {
       const int c = lane + 32 * u;
-      offv[u] = (ncol > 0 && c <= ncol && p < pb) ? offp[c] : 0;
+      // at most nnz (malformed input can push the scanned offsets past it)
+      offv[u] = (ncol > 0 && c <= ncol && p < pb) ? min(offp[c], nnz) : 0;
     }
   };
   load_offsets(pa);
@@ -1157,7 +1191,7 @@ cudaError_t launch_tile(const TileArgs& a, void* ws, cudaStream_t s, int* launch
       return static_cast<unsigned>(std::max<int64_t>(1, std::min<int64_t>((work + 255) / 256, 32LL * sms)));
     };
     k_panel_pointers<<<grid_for((P + 1) * a.n), 256, 0, s>>>(
-        a.n, static_cast<int32_t>(P), a.R, a.colptr, a.rowidx, pp);
+        a.n, static_cast<int32_t>(P), a.R, a.nnz, a.colptr, a.rowidx, pp, a.status);
     ++*launches;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     k_panel_counts<<<grid_for(cells), 256, 0, s>>>(a.n, static_cast<int32_t>(P), pp, cnt);
@@ -1166,11 +1200,11 @@ cudaError_t launch_tile(const TileArgs& a, void* ws, cudaStream_t s, int* launch
     if ((e = exclusive_scan(cnt, off, cells, scan_tmp, s, launches)) != cudaSuccess) return e;
     if (a.dtype == 0)
       k_panel_copy<float><<<grid_for(P * a.n), 256, 0, s>>>(
-          a.n, static_cast<int32_t>(P), a.R, a.m, a.rowidx,
+          a.n, static_cast<int32_t>(P), a.R, a.m, a.nnz, a.rowidx,
           static_cast<const float*>(a.values), pp, off, packed, a.status);
     else
       k_panel_copy<__nv_bfloat16><<<grid_for(P * a.n), 256, 0, s>>>(
-          a.n, static_cast<int32_t>(P), a.R, a.m, a.rowidx,
+          a.n, static_cast<int32_t>(P), a.R, a.m, a.nnz, a.rowidx,
           static_cast<const __nv_bfloat16*>(a.values), pp, off, packed, a.status);
     ++*launches;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -1196,7 +1230,8 @@ cudaError_t launch_tile(const TileArgs& a, void* ws, cudaStream_t s, int* launch
     if (e != cudaSuccess) return e;                                              \
     k_tile<DD, CC, TT><<<grid, block, smem, s>>>(a.m, a.n, a.d, a.R,             \
                                                  static_cast<int32_t>(P), a.G,   \
-                                                 packed, off, dst, keys,         \
+                                                 packed, off,                    \
+                                                 static_cast<int32_t>(a.nnz), dst, keys, \
                                                  a.stream_id, a.gen_count,       \
                                                  a.S_mem, a.ld_s);               \
     ++*launches;                                                                 \

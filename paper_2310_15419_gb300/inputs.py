@@ -69,6 +69,20 @@ class CSC:
                    self.rowidx[keep].copy(), self.values[keep].copy(),
                    self.dtype, vb)
 
+    def columns(self, cols) -> "CSC":
+        """The submatrix of the given columns (same m, columns in the given
+        order), as a new CSC: column t of the result is column cols[t]."""
+        cols = np.asarray(cols, dtype=np.int64)
+        lens = (self.colptr[cols + 1] - self.colptr[cols]).astype(np.int64)
+        colptr = np.zeros(cols.size + 1, dtype=np.int64)
+        np.cumsum(lens, out=colptr[1:])
+        take = np.concatenate([np.arange(self.colptr[k], self.colptr[k + 1])
+                               for k in cols]) if cols.size else np.zeros(0, np.int64)
+        take = take.astype(np.int64)
+        vb = None if self.values_bf16 is None else self.values_bf16[take]
+        return CSC(self.m, int(cols.size), colptr.astype(np.int32),
+                   self.rowidx[take].copy(), self.values[take].copy(), self.dtype, vb)
+
     def to_scipy(self):
         import scipy.sparse as sp
         return sp.csc_matrix((self.values.astype(np.float64), self.rowidx,
@@ -235,6 +249,23 @@ def float_uniform(m: int, n: int, density: float, seed: int,
     else:
         v = rng.standard_normal(size=rowidx.size)
     return CSC(m, n, colptr, rowidx, v.astype(np.float32))
+
+
+def heavy_column(m: int, n: int, heavy_nnz: int, density: float, seed: int,
+                 heavy_col: int = 0) -> CSC:
+    """A uniform pattern of the given density whose column `heavy_col` is
+    replaced by `heavy_nnz` distinct rows chosen uniformly; values U(-1,1)."""
+    rng = _rng(seed)
+    colptr, rowidx = uniform_pattern(m, n, density, rng)
+    heavy = np.sort(rng.choice(m, size=heavy_nnz, replace=False)).astype(np.int32)
+    lens = np.diff(colptr).astype(np.int64)
+    parts = [rowidx[colptr[k]:colptr[k + 1]] if k != heavy_col else heavy for k in range(n)]
+    lens[heavy_col] = heavy_nnz
+    cp = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(lens, out=cp[1:])
+    rows = np.concatenate(parts).astype(np.int32)
+    v = rng.uniform(-1.0, 1.0, size=rows.size).astype(np.float32)
+    return CSC(m, n, cp.astype(np.int32), rows, v)
 
 
 def skew_large(seed: int = 2, m: int = 2_000_000, n: int = 1000,

@@ -90,6 +90,57 @@ def test_batch_graph_replay():
     batch.close()
 
 
+def test_full_size_batch_sampled_columns_match_oracle():
+    """The benchmark's batch at full size (256 instances, about 9e7 nonzeros,
+    +-1 S, N(0,1) values, one persistent launch): 64 columns over 32
+    instances -- each instance's heaviest column and a random one -- against
+    the oracle within 1e-6 (columns of A_hat depend only on the matching
+    column of A, so the oracle computes them alone)."""
+    inst = inputs.batched()
+    sks = [capi.Sketch(A.m, A.n, d, "pm1", seed=1, stream_id=t)
+           for t, (A, d) in enumerate(inst)]
+    mats = [capi.DeviceCSC(A) for A, _ in inst]
+    batch = capi.Batch(sks, mats)
+    outs = batch.apply()
+    torch.cuda.synchronize()
+    assert batch.status() == capi.SKETCH_OK
+    rng = np.random.default_rng(15)
+    # the largest instances by nonzeros, plus random ones: 32 in all
+    by_nnz = sorted(range(len(inst)), key=lambda t: -inst[t][0].nnz)
+    chosen = set(by_nnz[:12])
+    while len(chosen) < 32:
+        chosen.add(int(rng.integers(0, len(inst))))
+    for t in sorted(chosen):
+        A, d = inst[t]
+        lens = np.diff(A.colptr)
+        cols = sorted({int(np.argmax(lens)), int(rng.integers(0, A.n))})
+        ref, _ = oracle.sketch_jki(A.m, len(cols), d, oracle.PM1, 1, t,
+                                   *_cols(A, cols))
+        got = outs[t][cols].cpu().numpy().astype(np.float64)
+        for c in range(len(cols)):
+            r = ref[:, c]
+            assert np.linalg.norm(got[c] - r) <= 1e-6 * np.linalg.norm(r), (t, cols[c])
+    batch.close()
+    for sk in sks:
+        sk.close()
+
+
+def _cols(A, cols):
+    sub = A.columns(cols)
+    return sub.colptr, sub.rowidx, sub.values
+
+
+def test_batch_rejects_malformed_colptr():
+    A = inputs.integer_uniform(800, 6, 0.05, seed=2)
+    B = inputs.CSC(A.m, A.n, A.colptr.copy(), A.rowidx, A.values)
+    B.colptr[3] = B.colptr[2] - 1            # stays inside [0, nnz]
+    sks = [capi.Sketch(800, 6, 32, "pm1"), capi.Sketch(800, 6, 32, "pm1", stream_id=1)]
+    mats = [capi.DeviceCSC(A), capi.DeviceCSC(B)]
+    with pytest.raises(capi.SketchError) as e:
+        capi.Batch(sks, mats)
+    assert e.value.code == capi.SKETCH_ERR_CSC
+
+
 def test_batch_rejects_mixed_distributions():
     A = inputs.integer_uniform(500, 5, 0.05, seed=1)
     sks = [capi.Sketch(500, 5, 16, "pm1"), capi.Sketch(500, 5, 16, "uniform")]

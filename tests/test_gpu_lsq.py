@@ -108,6 +108,13 @@ def test_zero_rhs_and_errors():
     with pytest.raises(capi.SketchError) as e:
         sk.lsq_solve(capi.DeviceCSC(B), torch.from_numpy(b).cuda())
     assert e.value.code == capi.SKETCH_ERR_CSC
+    # a malformed colptr (decreasing, inside [0, nnz]) is refused up front
+    B = inputs.CSC(A.m, A.n, A.colptr.copy(), A.rowidx, A.values)
+    B.colptr[5] = B.colptr[4] - 1
+    sk = capi.Sketch(B.m, B.n, 2 * B.n, "uniform")
+    with pytest.raises(capi.SketchError) as e:
+        sk.lsq_solve(capi.DeviceCSC(B), torch.from_numpy(b).cuda())
+    assert e.value.code == capi.SKETCH_ERR_CSC
     # d < n is refused
     sk = capi.Sketch(A.m, A.n, A.n - 1, "uniform")
     with pytest.raises(capi.SketchError) as e:

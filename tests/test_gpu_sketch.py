@@ -308,6 +308,34 @@ def test_bad_row_index_is_reported_not_faulted():
         sk.close()
 
 
+def _decreasing_colptr(A, k):
+    """colptr[k + 1] set one below colptr[k]: column k's range decreases and
+    column k + 1's range reaches one entry back into column k - 1.  Every
+    index stays inside [0, nnz], so even a kernel without the clamps would
+    address only A's own arrays."""
+    B = inputs.CSC(A.m, A.n, A.colptr.copy(), A.rowidx, A.values)
+    assert B.colptr[k] > 0 and B.colptr[k + 2] > B.colptr[k]
+    B.colptr[k + 1] = B.colptr[k] - 1
+    return B
+
+
+def test_decreasing_colptr_is_reported_by_every_plan():
+    """A malformed colptr is clamped column by column inside the kernels and
+    reported as SKETCH_ERR_CSC through the device status word."""
+    A = _decreasing_colptr(inputs.integer_uniform(3000, 12, 0.02, seed=12), 4)
+    dA = capi.DeviceCSC(A)
+    assert capi.validate_csc(dA) == capi.SKETCH_ERR_CSC
+    for plan in (REGEN_PLANS[0], PANEL_PLANS[0], TILE_PLANS[0], TILE_PLANS[4],
+                 dict(mode=capi.SKETCH_MODE_REGEN, q_tiles=1, split=1, tc_min_row_nnz=2)):
+        sk = capi.Sketch(A.m, A.n, 64, "pm1", seed=1)
+        sk.set_plan(**plan)
+        sk.apply(dA)
+        torch.cuda.synchronize()
+        assert sk.device_status() == capi.SKETCH_ERR_CSC, plan
+        assert sk.device_status() == capi.SKETCH_OK  # reading clears it
+        sk.close()
+
+
 def test_validator_accepts_good_and_rejects_unsorted():
     A = inputs.integer_uniform(1000, 5, 0.02, seed=10)
     assert capi.validate_csc(capi.DeviceCSC(A)) == capi.SKETCH_OK
@@ -352,13 +380,18 @@ def test_skew_large_sampled_columns(skew_large, dist, plan):
     torch.cuda.synchronize()
     assert sk.device_status() == capi.SKETCH_OK
     got = out.cpu().numpy().astype(np.float64)  # n x d
-    for k in (0, 1, 499, 998, 999):
-        p0, p1 = A.colptr[k], A.colptr[k + 1]
-        col = inputs.CSC(A.m, 1, np.array([0, p1 - p0], np.int32),
-                         A.rowidx[p0:p1], A.values[p0:p1])
-        ref = oracle_sketch(col, d, dist)[:, 0]
-        assert rel_fro(got[k], ref) <= TOL, (dist, k)
     sk.close()
+    # 60 columns: the three heaviest, the ends and middle, and random ones
+    lens = np.diff(A.colptr)
+    cols = set(np.argsort(lens)[-3:].tolist()) | {0, 1, 499, 998, 999}
+    rng = np.random.default_rng(13)
+    while len(cols) < 60:
+        cols.add(int(rng.integers(0, A.n)))
+    cols = sorted(cols)
+    ref = oracle_sketch(A.columns(cols), d, dist).T  # len(cols) x d
+    for t, k in enumerate(cols):
+        assert rel_fro(got[k], ref[t]) <= TOL, (dist, k)
+    assert rel_fro(got[cols], ref) <= TOL
 
 
 # ------------------------------------------------ tensor-core dense panels
@@ -434,6 +467,35 @@ def test_tuned_plan_on_dense_rows_is_exact():
     sk.close()
     assert plan["mode"] in (capi.SKETCH_MODE_REGEN, capi.SKETCH_MODE_TILE)
     assert np.array_equal(got, oracle_sketch(A, 300, "pm1"))
+
+
+def test_abnormal_a_full_size_tensor_core_plan_sampled_columns():
+    """The benchmark's Abnormal_A case at full size (m = 100,000, n = 10,000,
+    every 1000th row dense, d = 30,000): the tensor-core panel plan and the
+    tuned plan, 64 sampled columns (including both ends of the column range
+    and the CTA tile edges) against the oracle within 1e-6."""
+    A = inputs.abnormal("a")
+    d = 3 * A.n
+    dA = capi.DeviceCSC(A)
+    rng = np.random.default_rng(14)
+    cols = sorted({0, 1, 127, 128, 255, 256, A.n - 2, A.n - 1} |
+                  set(rng.choice(A.n, size=56, replace=False).tolist()))
+    ref = oracle_sketch(A.columns(cols), d, "pm1").T
+    for plan in (dict(mode=capi.SKETCH_MODE_REGEN, q_tiles=4, split=8,
+                      tc_min_row_nnz=A.n // 2), None):
+        sk = capi.Sketch(A.m, A.n, d, "pm1", seed=1)
+        if plan:
+            sk.set_plan(**plan)
+        out = sk.apply(dA)
+        torch.cuda.synchronize()
+        assert sk.device_status() == capi.SKETCH_OK
+        if plan is None:
+            assert sk.get_plan(dA)["tc_min_row_nnz"] > 0  # the tuner takes a panel
+        got = out[cols].cpu().numpy().astype(np.float64)
+        sk.close()
+        for t, k in enumerate(cols):
+            assert rel_fro(got[t], ref[t]) <= TOL, (plan, k)
+        del out
 
 
 def test_bounded_wait_times_out_into_status_and_context_survives():

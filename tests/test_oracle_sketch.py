@@ -128,3 +128,33 @@ def test_paper_gflops_definition():
             continue
         d, nnz, t, gf = int(r[2]), int(r[3]), float(r[4]), float(r[5])
         assert abs(2 * d * nnz / t / 1e9 - gf) < 0.01 * gf
+
+
+@pytest.mark.parametrize("dist", [oracle.PM1, oracle.UNIFORM, oracle.NORMAL])
+@pytest.mark.parametrize("threads", [1, 2, 3, 8])
+def test_all_core_oracle_is_bit_identical_to_the_serial_one(dist, threads):
+    """The OpenMP oracle splits the rows of A_hat between threads, so each
+    element's additions keep the serial order: equal bits for float values,
+    ragged d (not a multiple of the Philox block), dense-ish and empty rows,
+    and a row sample."""
+    A = inputs.float_uniform(3000, 37, 0.03, seed=41)
+    for d in (1, 131, 517):
+        ref, g1 = oracle.sketch_jki(A.m, A.n, d, dist, 9, 4, A.colptr, A.rowidx, A.values)
+        got, g2 = oracle.sketch_jki_omp(A.m, A.n, d, dist, 9, 4, A.colptr, A.rowidx,
+                                        A.values, threads=threads)
+        assert g1 == g2 and np.array_equal(got, ref), d
+    ref, _ = oracle.sketch_jki(A.m, A.n, 300, dist, 9, 0, A.colptr, A.rowidx, A.values,
+                               700, 2100)
+    got, _ = oracle.sketch_jki_omp(A.m, A.n, 300, dist, 9, 0, A.colptr, A.rowidx,
+                                   A.values, 700, 2100, threads=threads)
+    assert np.array_equal(got, ref)
+
+
+def test_all_core_oracle_matches_brute_force():
+    """Pinned on its own too: the materialised S times the dense A."""
+    A = inputs.integer_uniform(200, 11, 0.1, seed=42)
+    S = oracle.S_dense(oracle.PM1, 3, 1, 300, A.m)
+    got, _ = oracle.sketch_jki_omp(A.m, A.n, 300, oracle.PM1, 3, 1, A.colptr, A.rowidx,
+                                   A.values, threads=4)
+    assert np.array_equal(got, S @ _dense(A))
+    assert oracle.max_threads() >= 1
