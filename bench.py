@@ -63,6 +63,8 @@ def parse():
                     help="length of the Poisson arrival trace of the serve run")
     ap.add_argument("--serve-pool", type=int, default=24,
                     help="distinct request matrices the arrival trace draws from")
+    ap.add_argument("--probe-only", action="store_true",
+                    help="launch each generator probe and the FMA probe once, then exit")
     return ap.parse_args()
 
 
@@ -211,6 +213,41 @@ def generator_rates(torch, capi, sms):
         sec = e0.elapsed_time(e1) / 1e3 / reps
         out[dist] = threads * bpt * per_block / sec
     return out
+
+
+def fma_rate(torch, capi, sms, reps=5):
+    """FP32 FMAs/s of the library's FMA probe (eight independent chains per
+    thread), the measured counterpart of the FMA leg's unit-count peak."""
+    threads, iters = sms * 2048, 4096
+    sink = torch.empty(threads, dtype=torch.float32, device="cuda")
+    capi.bench_fma(threads, iters, sink)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        capi.bench_fma(threads, iters, sink)
+    e1.record()
+    torch.cuda.synchronize()
+    return threads * iters * 8 / (e0.elapsed_time(e1) / 1e3 / reps)
+
+
+def run_probes(args):
+    """--probe-only: one launch of each generator probe and of the FMA probe
+    (the launches an ncu capture of the ALU roofline's rates looks at)."""
+    import torch
+
+    from paper_2310_15419_gb300 import capi
+    torch.cuda.set_device(0)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    threads = sms * 2048
+    sink = torch.empty(threads, dtype=torch.float32, device="cuda")
+    for dist in DISTS:
+        capi.bench_generator(capi.DIST_NAMES[dist], 7, threads, 512 if dist == "pm1" else 256,
+                             sink)
+    capi.bench_fma(threads, 4096, sink)
+    torch.cuda.synchronize()
+    print(json.dumps({"probes": ["k_bench_generator<%s>" % d for d in DISTS] + ["k_bench_fma"],
+                      "threads": threads}))
 
 
 def cpu_baseline(A, d, seconds_budget, reps=1, threads=1):
@@ -516,6 +553,7 @@ def run_ours(args):
     dA = capi.DeviceCSC(A)
     sms = torch.cuda.get_device_properties(local).multi_processor_count
     rates = generator_rates(torch, capi, sms)
+    fma_probe = fma_rate(torch, capi, sms)
 
     sketches = {dist: capi.Sketch(A.m, A.n, d, dist, seed=cfg["seed_S"]) for dist in DISTS}
     if args.mode != "auto":
@@ -553,8 +591,9 @@ def run_ours(args):
 
     launches0 = sum(s.launch_count() for s in sketches.values())
     # our kernels launched before the timed region: the generator probe
-    # (3 distributions x 6 launches) plus every sketch launch so far
-    launches_before = 6 * len(DISTS) + launches0
+    # (3 distributions x 6 launches), the FMA probe (6) and every sketch
+    # launch so far
+    launches_before = 6 * len(DISTS) + 6 + launches0
     per_dist = {dist: [] for dist in DISTS}
     step_ms = []
     clocks = ClockSampler(local)
@@ -682,6 +721,8 @@ def run_ours(args):
             "roofline": roofline,
             "sweep": roof,
             "generator_entries_per_s": {k: float("%.4g" % v) for k, v in rates.items()},
+            "fma_probe": {"fma_per_s": float("%.4g" % fma_probe),
+                          "frac_of_unit_count_peak": round(fma_probe / r_fma, 4)},
             "e2e": {"value": round(e2e_val, 3), "unit": UNIT,
                     "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
             "cpu_baseline": cpu,
@@ -734,7 +775,9 @@ def run_reference(args):
 
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.probe_only:
+        run_probes(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

@@ -380,6 +380,14 @@ int sketch_bench_generator(int32_t dist, uint64_t seed, int64_t threads,
                            int64_t blocks_per_thread, float* sink,
                            sketch_stream_t stream);
 
+/* FP32 FMA throughput probe: `threads` threads each run `iters` rounds of
+ * eight independent FMAs (x = x * a + c) and write one float to sink
+ * (device, `threads` floats).  FMAs executed = threads * iters * 8.  Used to
+ * show that the FMA leg of the ALU roofline (d * nnz FMAs at 128 FP32 lanes
+ * per SM per clock, Sec. 3.1's cost of one multiply-add) is reachable on
+ * this part.  Asynchronous. */
+int sketch_bench_fma(int64_t threads, int64_t iters, float* sink, sketch_stream_t stream);
+
 /* Householder QR of a dense d x n FP64 matrix A (device, column-major,
  * d >= n) with the kernels sketch_lsq_solve uses (Sec. 5.3): writes R
  * (n x n, ROW-major, upper triangular; R(k,k) = -sign(x_0)||x||, or x_0 when

@@ -111,6 +111,7 @@ SIGNATURES = [
     ("sketch_generated_entries", _I64, [_VP, _VP]),
     ("sketch_launch_count", _I64, [_VP]),
     ("sketch_bench_generator", _I32, [_I32, _U64, _I64, _I64, _VP, _VP]),
+    ("sketch_bench_fma", _I32, [_I64, _I64, _VP, _VP]),
     ("sketch_debug_qr", _I32, [_I64, _I64, _VP, _VP, _VP, _VP]),
     ("sketch_batch_create", _I32, [_I32, ctypes.POINTER(_VP), _CSCP,
                                    ctypes.POINTER(_VP), _VP, ctypes.POINTER(_VP)]),
@@ -475,6 +476,12 @@ def bench_generator(dist, seed, threads, blocks_per_thread, sink, stream=None):
                                          int(threads), int(blocks_per_thread),
                                          ctypes.c_void_p(sink.data_ptr()),
                                          _stream_ptr(stream)))
+
+
+def bench_fma(threads, iters, sink, stream=None):
+    """Launch the FP32 FMA throughput probe (see include/sketch.h)."""
+    _check(load().sketch_bench_fma(int(threads), int(iters),
+                                   ctypes.c_void_p(sink.data_ptr()), _stream_ptr(stream)))
 
 
 def debug_qr(A, stream=None):

@@ -119,6 +119,7 @@ cudaError_t launch_debug_S(int dist, uint32_t k0, uint32_t k1,
                            const int64_t* j, float* out, int64_t count,
                            cudaStream_t s);
 
+cudaError_t launch_bench_fma(int64_t threads, int64_t iters, float* sink, cudaStream_t s);
 cudaError_t launch_bench_generator(int dist, uint32_t k0, uint32_t k1,
                                    int64_t threads, int64_t blocks_per_thread,
                                    float* sink, cudaStream_t s);

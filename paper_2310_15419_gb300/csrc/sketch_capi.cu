@@ -785,6 +785,13 @@ int sketch_bench_generator(int32_t dist, uint64_t seed, int64_t threads,
   return e == cudaSuccess ? SKETCH_OK : cuda_fail(nullptr, e, "bench_generator");
 }
 
+int sketch_bench_fma(int64_t threads, int64_t iters, float* sink, sketch_stream_t stream) {
+  if (threads < 0 || iters < 0 || (threads > 0 && !sink))
+    return fail(nullptr, SKETCH_ERR_ARG, "bad arguments");
+  cudaError_t e = launch_bench_fma(threads, iters, sink, reinterpret_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? SKETCH_OK : cuda_fail(nullptr, e, "bench_fma");
+}
+
 int sketch_set_counting(sketch_t h, int32_t enable) {
   if (!h) return SKETCH_ERR_ARG;
   h->counting = enable != 0;

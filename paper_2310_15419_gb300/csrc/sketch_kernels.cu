@@ -1479,6 +1479,32 @@ cudaError_t launch_bench_generator(int dist, uint32_t k0, uint32_t k1,
   return cudaGetLastError();
 }
 
+// FP32 FMA throughput probe: every thread runs eight independent FMA chains
+// (x <- x * a + c), so the rate is the FMA pipe's and not a chain's latency.
+__global__ void k_bench_fma(int64_t threads, int64_t iters, float a, float* __restrict__ sink) {
+  const int64_t tid = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (tid >= threads) return;
+  float x[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) x[i] = static_cast<float>(tid & 1023) * 1e-3f + static_cast<float>(i);
+  for (int64_t it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) x[i] = fmaf(x[i], a, 0.5f);
+  }
+  float t = 0.f;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) t += x[i];
+  sink[tid] = t;
+}
+
+cudaError_t launch_bench_fma(int64_t threads, int64_t iters, float* sink, cudaStream_t s) {
+  if (threads <= 0) return cudaSuccess;
+  const int64_t blocks = (threads + 255) / 256;
+  if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
+  k_bench_fma<<<static_cast<unsigned>(blocks), 256, 0, s>>>(threads, iters, 0.999f, sink);
+  return cudaGetLastError();
+}
+
 int64_t scan_bytes_for(int64_t len) { return scan_levels_bytes(len); }
 
 cudaError_t scan_i32(const int32_t* in, int32_t* out, int64_t len, char* tmp,
