@@ -380,6 +380,13 @@ int sketch_bench_generator(int32_t dist, uint64_t seed, int64_t threads,
                            int64_t blocks_per_thread, float* sink,
                            sketch_stream_t stream);
 
+/* The tuner's candidate plans for A on this handle (the plans sketch_apply
+ * times when it tunes), so a test can time each one itself: up to
+ * `max_plans` are written to `out` (host), *count = how many there are.
+ * No device work.  Errors: SKETCH_ERR_ARG. */
+int sketch_debug_candidates(sketch_t h, const sketch_csc* A, sketch_plan* out,
+                            int32_t max_plans, int32_t* count);
+
 /* FP32 FMA throughput probe: `threads` threads each run `iters` rounds of
  * eight independent FMAs (x = x * a + c) and write one float to sink
  * (device, `threads` floats).  FMAs executed = threads * iters * 8.  Used to

@@ -15,6 +15,13 @@ Functions follow the paper (arXiv 2310.15419):
   * ``lsqr``                     LSQR on A R^{-1}, Sec. 5.3
   * ``ls_error``                 Error(x) of Sec. 5.3
   * ``sap_qr_solve``             the whole SAP-QR pipeline of Sec. 5.3
+  * ``jacobi_svd``               one-sided Jacobi SVD of the sketch, Sec. 5.3
+  * ``sap_svd_solve``            SAP-SVD (singular values below sigma_max / 1e12
+                                 dropped), Sec. 5.3
+  * ``lsqr_d_solve``             LSQR-D, the diagonal-preconditioned LSQR that
+                                 Sec. 5.3 compares against
+  * ``sketch_jki_omp``           Alg. 4 order on all host cores (bit-identical
+                                 to ``sketch_jki``)
 
 Parity status: every function above is pinned by a ``-m "not gpu"`` test
 against something other than itself (torch's Philox engine, closed forms,
@@ -98,6 +105,15 @@ def _load():
                                             ip, dp, dp, ctypes.c_double, i64,
                                             dp, dp]
         lib.oracle_sap_qr_solve.restype = i32
+        lib.oracle_jacobi_svd.argtypes = [i64, i64, dp, dp, dp]
+        lib.oracle_jacobi_svd.restype = i32
+        lib.oracle_sap_svd_solve.argtypes = [i64, i64, i64, i32, u64, u32, ip,
+                                             ip, dp, dp, ctypes.c_double, i64,
+                                             dp, dp]
+        lib.oracle_sap_svd_solve.restype = i32
+        lib.oracle_lsqr_d_solve.argtypes = [i64, i64, ip, ip, dp, dp,
+                                            ctypes.c_double, i64, dp, dp]
+        lib.oracle_lsqr_d_solve.restype = i32
         _lib = lib
         return lib
 
@@ -269,3 +285,56 @@ def sap_qr_solve(m, n, d, dist, seed, stream, colptr, rowidx, values, b,
     return x, {"iters": int(info[0]), "istop": int(info[1]),
                "test2": float(info[2]), "anorm": float(info[3]),
                "error": float(info[4]), "converged": st == 0}
+
+
+def jacobi_svd(A):
+    """One-sided Jacobi SVD of a dense d x n array (d >= n): (sigma
+    decreasing, V n x n, sweeps).  Sec. 5.3's SVD of the sketch."""
+    A = np.asarray(A, dtype=np.float64)
+    d, n = A.shape
+    a = np.ascontiguousarray(A.T)          # column-major d x n
+    sigma = np.zeros(n, dtype=np.float64)
+    V = np.zeros((n, n), dtype=np.float64)  # row j = column j of V
+    sw = _load().oracle_jacobi_svd(d, n, _ptr(a, ctypes.c_double),
+                                   _ptr(sigma, ctypes.c_double), _ptr(V, ctypes.c_double))
+    if sw == -2:
+        raise MemoryError("oracle_jacobi_svd: allocation failed")
+    return sigma, V.T.copy(), int(sw)
+
+
+def sap_svd_solve(m, n, d, dist, seed, stream, colptr, rowidx, values, b,
+                  tol=1e-10, maxit=1000):
+    """Sec. 5.3 SAP-SVD.  Returns (x, info) with 'error' = Error(x), 'rank'
+    = singular values kept (>= sigma_max / 1e12) and the Jacobi 'sweeps'."""
+    cp, ri, va = _i32(colptr), _i32(rowidx), _f64(values)
+    bb = _f64(b)
+    x = np.zeros(n, dtype=np.float64)
+    info = np.zeros(8, dtype=np.float64)
+    st = _load().oracle_sap_svd_solve(m, n, d, dist, seed, stream,
+                                      _ptr(cp, ctypes.c_int32), _ptr(ri, ctypes.c_int32),
+                                      _ptr(va, ctypes.c_double), _ptr(bb, ctypes.c_double),
+                                      tol, maxit, _ptr(x, ctypes.c_double),
+                                      _ptr(info, ctypes.c_double))
+    if st == -2:
+        raise MemoryError("oracle_sap_svd_solve: allocation failed")
+    if st == -1:
+        raise RuntimeError("oracle_sap_svd_solve: the Jacobi SVD did not converge")
+    return x, {"iters": int(info[0]), "istop": int(info[1]), "test2": float(info[2]),
+               "anorm": float(info[3]), "error": float(info[4]), "rank": int(info[5]),
+               "sweeps": int(info[6]), "converged": st == 0}
+
+
+def lsqr_d_solve(m, n, colptr, rowidx, values, b, tol=1e-10, maxit=1000):
+    """Sec. 5.3 LSQR-D (LSQR with D_ii = 1 / ||A_i||).  Returns (x, info)."""
+    cp, ri, va = _i32(colptr), _i32(rowidx), _f64(values)
+    bb = _f64(b)
+    x = np.zeros(n, dtype=np.float64)
+    info = np.zeros(8, dtype=np.float64)
+    st = _load().oracle_lsqr_d_solve(m, n, _ptr(cp, ctypes.c_int32), _ptr(ri, ctypes.c_int32),
+                                     _ptr(va, ctypes.c_double), _ptr(bb, ctypes.c_double),
+                                     tol, maxit, _ptr(x, ctypes.c_double),
+                                     _ptr(info, ctypes.c_double))
+    if st == -2:
+        raise MemoryError("oracle_lsqr_d_solve: allocation failed")
+    return x, {"iters": int(info[0]), "istop": int(info[1]), "test2": float(info[2]),
+               "anorm": float(info[3]), "error": float(info[4]), "converged": st == 0}

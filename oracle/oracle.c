@@ -450,29 +450,78 @@ double oracle_ls_error(int64_t m, int64_t n, const int32_t* colptr,
 }
 
 /* ------------------------------------------------------------------------ */
-/* LSQR (Paige & Saunders, ACM TOMS 1982) on min || M y - b ||,              */
-/* M = A R^{-1} (or M = A when R is NULL), then x = R^{-1} y.  Sec. 5.3.     */
+/* Preconditioners M of Sec. 5.3's LSQR on min || A M y - b || (x = M y):     */
+/*   PC_TRI   M = R^{-1}, R upper triangular n x n (SAP-QR)                  */
+/*   PC_DENSE M = P, a dense n x k matrix (SAP-SVD: P = V_k Sigma_k^{-1})    */
+/*   PC_DIAG  M = diag(D) (LSQR-D: D_ii = 1 / ||A_i||)                       */
+/*   PC_NONE  M = I                                                          */
+/* ------------------------------------------------------------------------ */
+enum { PC_NONE = 0, PC_TRI = 1, PC_DENSE = 2, PC_DIAG = 3 };
+typedef struct {
+  int kind;
+  int64_t k;        /* columns of A M (unknowns of the preconditioned system) */
+  const double* R;  /* PC_TRI: n x n column-major, upper triangle used */
+  const double* P;  /* PC_DENSE: n x k column-major */
+  const double* D;  /* PC_DIAG: n */
+} precond;
+
+/* out (n) = M y (y has k entries) */
+static void pc_apply(const precond* pc, int64_t n, const double* y, double* out) {
+  if (pc->kind == PC_DENSE) {
+    for (int64_t i = 0; i < n; ++i) out[i] = 0.0;
+    for (int64_t j = 0; j < pc->k; ++j)
+      for (int64_t i = 0; i < n; ++i) out[i] += pc->P[j * n + i] * y[j];
+    return;
+  }
+  for (int64_t i = 0; i < n; ++i) out[i] = y[i];
+  if (pc->kind == PC_TRI) trsv_upper(n, pc->R, out);
+  if (pc->kind == PC_DIAG)
+    for (int64_t i = 0; i < n; ++i) out[i] *= pc->D[i];
+}
+
+/* out (k) = M^T z (z has n entries) */
+static void pc_apply_t(const precond* pc, int64_t n, const double* z, double* out) {
+  if (pc->kind == PC_DENSE) {
+    for (int64_t j = 0; j < pc->k; ++j) {
+      double s = 0.0;
+      for (int64_t i = 0; i < n; ++i) s += pc->P[j * n + i] * z[i];
+      out[j] = s;
+    }
+    return;
+  }
+  for (int64_t i = 0; i < n; ++i) out[i] = z[i];
+  if (pc->kind == PC_TRI) trsv_upper_t(n, pc->R, out);
+  if (pc->kind == PC_DIAG)
+    for (int64_t i = 0; i < n; ++i) out[i] *= pc->D[i];
+}
+
+/* ------------------------------------------------------------------------ */
+/* LSQR (Paige & Saunders, ACM TOMS 1982) on min || A M y - b ||, then       */
+/* x = M y.  Sec. 5.3.                                                       */
 /* Stopping rule (the solver's own estimates for the preconditioned system): */
 /*   test1 = ||r|| / ||b||                         <= tol + tol*||M||*||y||/||b|| */
 /*   test2 = ||M^T r|| / (||M||_F ||r||)           <= tol                     */
 /* info[0] = iterations, info[1] = istop (1 = test1, 2 = test2, 0 = maxit),  */
-/* info[2] = final test2 estimate, info[3] = ||M||_F estimate.              */
+/* info[2] = final test2 estimate, info[3] = ||A M||_F estimate.            */
 /* ------------------------------------------------------------------------ */
-int oracle_lsqr(int64_t m, int64_t n, const int32_t* colptr,
-                const int32_t* rowidx, const double* values, const double* b,
-                const double* R, double tol, int64_t maxit, double* x,
-                double* info) {
+static int lsqr_core(int64_t m, int64_t n, const int32_t* colptr,
+                     const int32_t* rowidx, const double* values, const double* b,
+                     const precond* pc, double tol, int64_t maxit, double* x,
+                     double* info) {
+  const int64_t k = pc->k;
+  const int64_t kk = k > 0 ? k : 1;
   double* u = (double*)malloc(sizeof(double) * (size_t)(m > 0 ? m : 1));
   double* Mv = (double*)malloc(sizeof(double) * (size_t)(m > 0 ? m : 1));
-  double* v = (double*)malloc(sizeof(double) * (size_t)n);
-  double* w = (double*)malloc(sizeof(double) * (size_t)n);
-  double* y = (double*)malloc(sizeof(double) * (size_t)n);
-  double* t = (double*)malloc(sizeof(double) * (size_t)n);
-  if (!u || !Mv || !v || !w || !y || !t) {
-    free(u); free(Mv); free(v); free(w); free(y); free(t);
+  double* v = (double*)malloc(sizeof(double) * (size_t)kk);
+  double* w = (double*)malloc(sizeof(double) * (size_t)kk);
+  double* y = (double*)malloc(sizeof(double) * (size_t)kk);
+  double* t = (double*)malloc(sizeof(double) * (size_t)(n > kk ? n : kk));
+  double* t2 = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+  if (!u || !Mv || !v || !w || !y || !t || !t2) {
+    free(u); free(Mv); free(v); free(w); free(y); free(t); free(t2);
     return -2;
   }
-  for (int64_t k = 0; k < n; ++k) y[k] = 0.0;
+  for (int64_t q = 0; q < k; ++q) y[q] = 0.0;
   for (int64_t j = 0; j < m; ++j) u[j] = b[j];
   double bnorm = vnorm(m, u);
   double beta = bnorm, alpha = 0.0;
@@ -481,33 +530,32 @@ int oracle_lsqr(int64_t m, int64_t n, const int32_t* colptr,
   double anorm2 = 0.0, test2 = 0.0;
   if (beta > 0.0) {
     for (int64_t j = 0; j < m; ++j) u[j] /= beta;
-    csc_rmatvec(n, colptr, rowidx, values, u, v); /* v = M^T u = R^{-T} A^T u */
-    if (R) trsv_upper_t(n, R, v);
-    alpha = vnorm(n, v);
+    csc_rmatvec(n, colptr, rowidx, values, u, t2); /* v = M^T A^T u */
+    pc_apply_t(pc, n, t2, v);
+    alpha = vnorm(k, v);
   }
   if (alpha > 0.0)
-    for (int64_t k = 0; k < n; ++k) v[k] /= alpha;
-  for (int64_t k = 0; k < n; ++k) w[k] = v[k];
+    for (int64_t q = 0; q < k; ++q) v[q] /= alpha;
+  for (int64_t q = 0; q < k; ++q) w[q] = v[q];
   double phibar = beta, rhobar = alpha;
   if (alpha == 0.0 || beta == 0.0) istop = 1; /* x = 0 is already exact */
   while (!istop && it < maxit) {
     ++it;
-    /* Golub-Kahan bidiagonalisation: beta u = M v - alpha u */
-    for (int64_t k = 0; k < n; ++k) t[k] = v[k];
-    if (R) trsv_upper(n, R, t);
+    /* Golub-Kahan bidiagonalisation: beta u = A M v - alpha u */
+    pc_apply(pc, n, v, t);
     csc_matvec(m, n, colptr, rowidx, values, t, Mv);
     for (int64_t j = 0; j < m; ++j) u[j] = Mv[j] - alpha * u[j];
     beta = vnorm(m, u);
     if (beta > 0.0)
       for (int64_t j = 0; j < m; ++j) u[j] /= beta;
     anorm2 += alpha * alpha + beta * beta;
-    /* alpha v = M^T u - beta v */
-    csc_rmatvec(n, colptr, rowidx, values, u, t);
-    if (R) trsv_upper_t(n, R, t);
-    for (int64_t k = 0; k < n; ++k) v[k] = t[k] - beta * v[k];
-    alpha = vnorm(n, v);
+    /* alpha v = M^T A^T u - beta v */
+    csc_rmatvec(n, colptr, rowidx, values, u, t2);
+    pc_apply_t(pc, n, t2, t);
+    for (int64_t q = 0; q < k; ++q) v[q] = t[q] - beta * v[q];
+    alpha = vnorm(k, v);
     if (alpha > 0.0)
-      for (int64_t k = 0; k < n; ++k) v[k] /= alpha;
+      for (int64_t q = 0; q < k; ++q) v[q] /= alpha;
     /* plane rotation eliminating the subdiagonal beta */
     double rho = sqrt(rhobar * rhobar + beta * beta);
     double c = rhobar / rho, s = beta / rho;
@@ -516,29 +564,38 @@ int oracle_lsqr(int64_t m, int64_t n, const int32_t* colptr,
     double phi = c * phibar;
     phibar = s * phibar;
     /* solution and search-direction updates */
-    for (int64_t k = 0; k < n; ++k) {
-      y[k] += (phi / rho) * w[k];
-      w[k] = v[k] - (theta / rho) * w[k];
+    for (int64_t q = 0; q < k; ++q) {
+      y[q] += (phi / rho) * w[q];
+      w[q] = v[q] - (theta / rho) * w[q];
     }
     /* the solver's estimates for the preconditioned system */
     double rnorm = phibar;
     double arnorm = phibar * alpha * fabs(c);
     double anorm = sqrt(anorm2);
-    double ynorm = vnorm(n, y);
+    double ynorm = vnorm(k, y);
     double test1 = rnorm / bnorm;
     test2 = (rnorm > 0.0) ? arnorm / (anorm * rnorm) : 0.0;
     double rtol = tol + tol * anorm * ynorm / bnorm;
     if (test2 <= tol) istop = 2;
     if (test1 <= rtol) istop = 1;
   }
-  for (int64_t k = 0; k < n; ++k) x[k] = y[k];
-  if (R) trsv_upper(n, R, x); /* x = R^{-1} y */
-  free(u); free(Mv); free(v); free(w); free(y); free(t);
+  pc_apply(pc, n, y, x); /* x = M y */
+  free(u); free(Mv); free(v); free(w); free(y); free(t); free(t2);
   info[0] = (double)it;
   info[1] = (double)istop;
   info[2] = test2;
   info[3] = sqrt(anorm2);
   return istop ? 0 : 1;
+}
+
+/* LSQR with M = R^{-1} (R upper triangular, column-major n x n), or M = I
+ * when R is NULL.  Returns 0 (converged), 1 (maxit) or -2 (allocation). */
+int oracle_lsqr(int64_t m, int64_t n, const int32_t* colptr,
+                const int32_t* rowidx, const double* values, const double* b,
+                const double* R, double tol, int64_t maxit, double* x,
+                double* info) {
+  precond pc = {R ? PC_TRI : PC_NONE, n, R, NULL, NULL};
+  return lsqr_core(m, n, colptr, rowidx, values, b, &pc, tol, maxit, x, info);
 }
 
 /* Full SAP-QR pipeline (Sec. 5.3): A_hat = S A (Alg. 4 order, FP64),
@@ -560,5 +617,144 @@ int oracle_sap_qr_solve(int64_t m, int64_t n, int64_t d, int dist,
                      : -1;
   if (qs == 0) info[4] = oracle_ls_error(m, n, colptr, rowidx, values, b, x);
   free(Ahat); free(R);
+  return ls;
+}
+
+/* ------------------------------------------------------------------------ */
+/* One-sided (Hestenes) Jacobi SVD of a dense d x n matrix (column-major,    */
+/* d >= n), FP64.  Sec. 5.3's SVD of the sketch.  Sweeps over all column     */
+/* pairs (p < q) in order; a pair whose columns are not orthogonal to        */
+/* working precision (|a_p . a_q| > 1e-15 sqrt(||a_p||^2 ||a_q||^2)) is      */
+/* rotated by the 2 x 2 symmetric Schur rotation of its Gram matrix          */
+/* (Golub & Van Loan, Alg. 8.4.1), which makes the two columns orthogonal;   */
+/* V accumulates the rotations.  At convergence A V = U diag(sigma) with     */
+/* sigma_j = ||column j||.  sigma (n) is returned in decreasing order with   */
+/* the columns of V (n x n, column-major) permuted to match.  Returns the    */
+/* number of sweeps, -1 if 80 sweeps did not converge, -2 on allocation      */
+/* failure.                                                                  */
+/* ------------------------------------------------------------------------ */
+int oracle_jacobi_svd(int64_t d, int64_t n, const double* A, double* sigma, double* V) {
+  double* W = (double*)malloc(sizeof(double) * (size_t)(d * n));
+  double* Vw = (double*)malloc(sizeof(double) * (size_t)(n * n));
+  if (!W || !Vw) { free(W); free(Vw); return -2; }
+  memcpy(W, A, sizeof(double) * (size_t)(d * n));
+  for (int64_t j = 0; j < n; ++j)
+    for (int64_t i = 0; i < n; ++i) Vw[j * n + i] = (i == j) ? 1.0 : 0.0;
+  int sweeps = 0, converged = 0;
+  while (!converged && sweeps < 80) {
+    ++sweeps;
+    int64_t rotations = 0;
+    for (int64_t p = 0; p + 1 < n; ++p)
+      for (int64_t q = p + 1; q < n; ++q) {
+        double* ap = W + p * d;
+        double* aq = W + q * d;
+        double alpha = 0.0, beta = 0.0, gamma = 0.0;
+        for (int64_t i = 0; i < d; ++i) {
+          alpha += ap[i] * ap[i];
+          beta += aq[i] * aq[i];
+          gamma += ap[i] * aq[i];
+        }
+        if (gamma == 0.0 || fabs(gamma) <= 1e-15 * sqrt(alpha * beta)) continue;
+        ++rotations;
+        double zeta = (beta - alpha) / (2.0 * gamma);
+        double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+        double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
+        for (int64_t i = 0; i < d; ++i) {
+          double x0 = ap[i], x1 = aq[i];
+          ap[i] = c * x0 - s * x1;
+          aq[i] = s * x0 + c * x1;
+        }
+        double* vp = Vw + p * n;
+        double* vq = Vw + q * n;
+        for (int64_t i = 0; i < n; ++i) {
+          double x0 = vp[i], x1 = vq[i];
+          vp[i] = c * x0 - s * x1;
+          vq[i] = s * x0 + c * x1;
+        }
+      }
+    if (rotations == 0) converged = 1;
+  }
+  /* sigma_j = ||column j||, then sort decreasing (selection sort) */
+  int64_t* order = (int64_t*)malloc(sizeof(int64_t) * (size_t)n);
+  double* sv = (double*)malloc(sizeof(double) * (size_t)n);
+  if (!order || !sv) { free(W); free(Vw); free(order); free(sv); return -2; }
+  for (int64_t j = 0; j < n; ++j) {
+    sv[j] = vnorm(d, W + j * d);
+    order[j] = j;
+  }
+  for (int64_t a = 0; a < n; ++a) {
+    int64_t best = a;
+    for (int64_t c = a + 1; c < n; ++c)
+      if (sv[order[c]] > sv[order[best]]) best = c;
+    int64_t tmp = order[a]; order[a] = order[best]; order[best] = tmp;
+  }
+  for (int64_t a = 0; a < n; ++a) {
+    sigma[a] = sv[order[a]];
+    memcpy(V + a * n, Vw + order[a] * n, sizeof(double) * (size_t)n);
+  }
+  free(W); free(Vw); free(order); free(sv);
+  return converged ? sweeps : -1;
+}
+
+/* SAP-SVD (Sec. 5.3): A_hat = S A (Alg. 4 order, FP64), A_hat = U Sigma V^T
+ * by the Jacobi SVD above, singular values below sigma_max / 10^12 dropped
+ * (k kept), LSQR on A P with P = V_k Sigma_k^{-1} (n x k), x = P y.
+ * info as for oracle_lsqr, plus info[4] = Error(x), info[5] = k,
+ * info[6] = Jacobi sweeps.  Returns 0, 1 (maxit), -1 (SVD did not
+ * converge) or -2 (allocation). */
+int oracle_sap_svd_solve(int64_t m, int64_t n, int64_t d, int dist,
+                         uint64_t seed, uint32_t stream, const int32_t* colptr,
+                         const int32_t* rowidx, const double* values,
+                         const double* b, double tol, int64_t maxit, double* x,
+                         double* info) {
+  double* Ahat = (double*)malloc(sizeof(double) * (size_t)(d * n));
+  double* sigma = (double*)malloc(sizeof(double) * (size_t)n);
+  double* V = (double*)malloc(sizeof(double) * (size_t)(n * n));
+  if (!Ahat || !sigma || !V) { free(Ahat); free(sigma); free(V); return -2; }
+  oracle_sketch_jki_rows(m, n, d, dist, seed, stream, colptr, rowidx, values, Ahat, 0, m);
+  int sweeps = oracle_jacobi_svd(d, n, Ahat, sigma, V);
+  free(Ahat);
+  if (sweeps < 0) { free(sigma); free(V); return sweeps == -2 ? -2 : -1; }
+  int64_t k = 0;
+  while (k < n && sigma[k] > 0.0 && sigma[k] >= sigma[0] / 1e12) ++k;
+  /* P = V_k Sigma_k^{-1}: column j of V divided by sigma_j */
+  for (int64_t j = 0; j < k; ++j)
+    for (int64_t i = 0; i < n; ++i) V[j * n + i] /= sigma[j];
+  precond pc = {PC_DENSE, k, NULL, V, NULL};
+  int ls = lsqr_core(m, n, colptr, rowidx, values, b, &pc, tol, maxit, x, info);
+  if (ls >= 0) {
+    info[4] = oracle_ls_error(m, n, colptr, rowidx, values, b, x);
+    info[5] = (double)k;
+    info[6] = (double)sweeps;
+  }
+  free(sigma); free(V);
+  return ls;
+}
+
+/* LSQR-D (Sec. 5.3's first comparator): LSQR with the diagonal
+ * preconditioner D_ii = 1 / ||A_i||_2 (A_i the i-th column), except that
+ * D_ii = 1 when ||A_i||_2 <= eps sqrt(n) max_i ||A_i||_2 (eps = 2^-52, the
+ * FP64 machine epsilon); x = D y.  info as for oracle_lsqr, plus info[4] =
+ * Error(x).  Returns 0, 1 (maxit) or -2 (allocation). */
+int oracle_lsqr_d_solve(int64_t m, int64_t n, const int32_t* colptr,
+                        const int32_t* rowidx, const double* values,
+                        const double* b, double tol, int64_t maxit, double* x,
+                        double* info) {
+  double* D = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+  if (!D) return -2;
+  double nmax = 0.0;
+  for (int64_t k = 0; k < n; ++k) {
+    double s = 0.0;
+    for (int64_t p = colptr[k]; p < colptr[k + 1]; ++p) s += values[p] * values[p];
+    D[k] = sqrt(s);
+    if (D[k] > nmax) nmax = D[k];
+  }
+  const double eps = ldexp(1.0, -52);
+  for (int64_t k = 0; k < n; ++k)
+    D[k] = (D[k] <= eps * sqrt((double)n) * nmax) ? 1.0 : 1.0 / D[k];
+  precond pc = {PC_DIAG, n, NULL, NULL, D};
+  int ls = lsqr_core(m, n, colptr, rowidx, values, b, &pc, tol, maxit, x, info);
+  if (ls >= 0) info[4] = oracle_ls_error(m, n, colptr, rowidx, values, b, x);
+  free(D);
   return ls;
 }

@@ -112,6 +112,8 @@ SIGNATURES = [
     ("sketch_launch_count", _I64, [_VP]),
     ("sketch_bench_generator", _I32, [_I32, _U64, _I64, _I64, _VP, _VP]),
     ("sketch_bench_fma", _I32, [_I64, _I64, _VP, _VP]),
+    ("sketch_debug_candidates", _I32, [_VP, _CSCP, ctypes.POINTER(sketch_plan), _I32,
+                                       ctypes.POINTER(_I32)]),
     ("sketch_debug_qr", _I32, [_I64, _I64, _VP, _VP, _VP, _VP]),
     ("sketch_batch_create", _I32, [_I32, ctypes.POINTER(_VP), _CSCP,
                                    ctypes.POINTER(_VP), _VP, ctypes.POINTER(_VP)]),
@@ -245,6 +247,14 @@ class Sketch:
         _check(load().sketch_get_plan(self.h, ctypes.byref(A.desc),
                                       ctypes.byref(p), _stream_ptr(stream)), self.h)
         return p.as_dict()
+
+    def candidates(self, A: DeviceCSC) -> list:
+        """The tuner's candidate plans for A (sketch_debug_candidates)."""
+        arr = (sketch_plan * 64)()
+        cnt = ctypes.c_int32()
+        _check(load().sketch_debug_candidates(self.h, ctypes.byref(A.desc), arr, 64,
+                                              ctypes.byref(cnt)), self.h)
+        return [arr[t].as_dict() for t in range(min(cnt.value, 64))]
 
     def apply(self, A: DeviceCSC, out=None, stream=None):
         import torch

@@ -1,0 +1,86 @@
+"""The autotuner on the paper's abnormal sparsity patterns (Table
+"extreme_examples": m = 100,000, n = 10,000, density about 1e-3), with
+U(-1,1) S as the paper ran them, d = 3n (GPU, through the C ABI).
+
+For each pattern the tuned plan must be within 10% of the fastest of the
+tuner's own candidates, each candidate timed here on its own (median of
+three runs), and the tuned sketch must match the oracle on sampled columns.
+  a: every 1000th row dense, all other rows empty
+  b: 2998/3000 of the nonzeros in the middle third of the columns
+  c: every 1000th column dense, all other columns empty
+"""
+import statistics
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2310_15419_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2310_15419_gb300 import capi  # noqa: E402
+
+TOL = 1e-6
+
+
+def _median_ms(sk, dA, out, reps=3):
+    sk.apply(dA, out)
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        sk.apply(dA, out)
+        e1.record()
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    return statistics.median(ms)
+
+
+@pytest.mark.parametrize("kind", ["a", "b", "c"])
+def test_tuned_plan_within_10_percent_of_best_candidate(kind):
+    A = inputs.abnormal(kind)
+    d = 3 * A.n
+    dA = capi.DeviceCSC(A)
+    out = torch.empty((A.n, d), dtype=torch.float32, device="cuda")
+    tuned = capi.Sketch(A.m, A.n, d, "uniform", seed=1)
+    tuned.set_autotune(True)
+    tuned.apply(dA, out)
+    torch.cuda.synchronize()
+    plan = tuned.get_plan(dA)
+    cands = tuned.candidates(dA)
+    assert cands and plan in cands
+    times = []
+    for c in cands:
+        sk = capi.Sketch(A.m, A.n, d, "uniform", seed=1)
+        sk.set_plan(**c)
+        times.append(_median_ms(sk, dA, out))
+        sk.close()
+    t_tuned = _median_ms(tuned, dA, out)
+    best = min(times)
+    assert t_tuned <= 1.10 * best, (kind, plan, t_tuned, best, cands[times.index(best)])
+    # the tuned sketch against the oracle on sampled columns (the heaviest
+    # two, both ends, and random ones)
+    got = out.cpu().numpy().astype(np.float64)
+    assert tuned.device_status() == capi.SKETCH_OK
+    tuned.close()
+    lens = np.diff(A.colptr)
+    rng = np.random.default_rng(16)
+    cols = sorted(set(np.argsort(lens)[-2:].tolist()) | {0, A.n - 1} |
+                  set(rng.choice(A.n, size=8, replace=False).tolist()))
+    ref, _ = oracle.sketch_jki_omp(A.m, len(cols), d, oracle.UNIFORM, 1, 0,
+                                   *_cols(A, cols))
+    for t, k in enumerate(cols):
+        r = ref[:, t]
+        den = np.linalg.norm(r)
+        assert np.linalg.norm(got[k] - r) <= TOL * (den if den > 0 else 1.0), (kind, k)
+
+
+def _cols(A, cols):
+    sub = A.columns(cols)
+    return sub.colptr, sub.rowidx, sub.values

@@ -106,3 +106,96 @@ def test_sap_iterations_comparable_to_paper():
                                   A.rowidx, A.values, b, tol=1e-14, maxit=500)
     assert 0.5 * min(iters) <= info["iters"] <= 1.5 * max(iters)
     assert info["error"] <= 100 * max(errs)
+
+
+# ------------------------------------------------------------ SAP-SVD, LSQR-D
+def test_jacobi_svd_matches_lapack():
+    """Singular values and right singular vectors against numpy's LAPACK SVD
+    (vectors up to sign), at several shapes including a graded matrix."""
+    rng = np.random.default_rng(3)
+    for d, n, grade in [(10, 10, 0), (40, 7, 0), (120, 60, 6), (5, 1, 0)]:
+        A = rng.standard_normal((d, n)) * 10.0 ** np.linspace(0, -grade, n)[None, :]
+        s, V, sweeps = oracle.jacobi_svd(A)
+        _, sl, Vt = np.linalg.svd(A)
+        assert sweeps > 0
+        assert np.allclose(s, sl, rtol=1e-12, atol=0)
+        # A V = U diag(s) with orthonormal U, and |V^T V_lapack| = I
+        U = (A @ V) / s
+        assert np.allclose(U.T @ U, np.eye(n), atol=1e-10)
+        assert np.allclose(np.abs(V.T @ Vt.T), np.eye(n), atol=1e-8)
+
+
+def test_jacobi_svd_rank_deficient():
+    """A duplicated (scaled) column and a zero column: two singular values
+    at the FP64 noise level, the rest equal to LAPACK's."""
+    rng = np.random.default_rng(4)
+    A = rng.standard_normal((50, 12))
+    A[:, 5] = 3.0 * A[:, 2]
+    A[:, 9] = 0.0
+    s, V, _ = oracle.jacobi_svd(A)
+    sl = np.linalg.svd(A, compute_uv=False)
+    assert np.allclose(s[:10], sl[:10], rtol=1e-12)
+    assert np.all(s[10:] <= 1e-13 * s[0])
+
+
+def _dense(A):
+    return A.to_scipy().toarray()
+
+
+@pytest.mark.parametrize("dist", [oracle.PM1, oracle.UNIFORM, oracle.NORMAL])
+def test_sap_svd_full_rank_matches_lstsq(dist):
+    A, b, _ = inputs.lsq_problem(3000, 40, 0.05, seed=21, noise=1e-2,
+                                 col_scale_decades=2.0)
+    x, info = oracle.sap_svd_solve(A.m, A.n, 2 * A.n, dist, 1, 0, A.colptr, A.rowidx,
+                                   A.values, b, tol=1e-12, maxit=500)
+    xl = np.linalg.lstsq(_dense(A), b, rcond=None)[0]
+    assert info["converged"] and info["rank"] == A.n
+    assert np.linalg.norm(x - xl) <= 1e-9 * np.linalg.norm(xl)
+    assert info["error"] <= 1e-11
+    # the sketch preconditions as well as the QR one: few iterations
+    assert info["iters"] <= 80
+
+
+def test_sap_svd_rank_deficient_gives_the_minimum_norm_solution():
+    """With a duplicated column and a zero column, the kept singular
+    directions span the row space of A, so x = P y is the minimum-norm
+    least-squares solution, numpy's pinv(A) b."""
+    A, b, _ = inputs.lsq_problem(2000, 30, 0.08, seed=22, noise=1e-1)
+    Ad = _dense(A)
+    Ad[:, 7] = -2.0 * Ad[:, 3]
+    Ad[:, 20] = 0.0
+    import scipy.sparse as sp
+    C = sp.csc_matrix(Ad)
+    C.sort_indices()
+    B = inputs.CSC(A.m, A.n, C.indptr.astype(np.int32), C.indices.astype(np.int32),
+                   C.data.astype(np.float32))
+    Ad = B.to_scipy().toarray()
+    x, info = oracle.sap_svd_solve(B.m, B.n, 2 * B.n, oracle.UNIFORM, 3, 0, B.colptr,
+                                   B.rowidx, B.values, b, tol=1e-12, maxit=500)
+    xp = np.linalg.pinv(Ad, rcond=1e-12) @ b
+    assert info["rank"] == B.n - 2
+    assert np.linalg.norm(x - xp) <= 1e-8 * np.linalg.norm(xp)
+    assert abs(x[20]) <= 1e-12 * np.linalg.norm(xp)
+
+
+def test_lsqr_d_matches_lstsq_and_scales_columns():
+    """LSQR-D reaches lstsq's solution; on columns scaled over four decades
+    it needs far fewer iterations than unpreconditioned LSQR (so D_ii is
+    1 / ||A_i||, not ||A_i||), and a zero column takes D_ii = 1."""
+    A, b, _ = inputs.lsq_problem(4000, 30, 0.05, seed=23, noise=1e-2,
+                                 col_scale_decades=2.0)
+    xl = np.linalg.lstsq(_dense(A), b, rcond=None)[0]
+    x, info = oracle.lsqr_d_solve(A.m, A.n, A.colptr, A.rowidx, A.values, b,
+                                  tol=1e-12, maxit=5000)
+    assert info["converged"]
+    assert np.linalg.norm(x - xl) <= 1e-8 * np.linalg.norm(xl)
+    x0, i0 = oracle.lsqr(A.m, A.n, A.colptr, A.rowidx, A.values, b, None,
+                         tol=1e-12, maxit=5000)
+    assert info["iters"] * 3 < i0["iters"]
+    # a zero column: D = 1 there and its solution entry stays 0
+    cp = np.concatenate([A.colptr, A.colptr[-1:]])
+    Z = inputs.CSC(A.m, A.n + 1, cp, A.rowidx, A.values)
+    xz, iz = oracle.lsqr_d_solve(Z.m, Z.n, Z.colptr, Z.rowidx, Z.values, b,
+                                 tol=1e-12, maxit=5000)
+    assert np.isfinite(xz).all() and xz[-1] == 0.0
+    assert np.linalg.norm(xz[:-1] - xl) <= 1e-8 * np.linalg.norm(xl)
