@@ -260,11 +260,24 @@ int sketch_batch_status(sketch_batch_t b, sketch_stream_t stream);
 int sketch_batch_destroy(sketch_batch_t b);
 
 /* ---- least squares (Sec. 5.3, sketch-and-precondition with QR) -------- */
+/* Least-squares methods of Sec. 5.3: SAP with a QR of the sketch
+ * (preconditioner R^{-1}), SAP with an SVD of the sketch (singular values
+ * below sigma_max(S A) / 10^12 dropped; preconditioner V_k Sigma_k^{-1}, for
+ * problems with singular values near zero), and the paper's comparator
+ * LSQR-D (no sketch; D_ii = 1 / ||A_i||_2, or 1 when ||A_i||_2 <= eps
+ * sqrt(n) max_i ||A_i||_2 with eps = 2^-52). */
+enum sketch_lsq_method {
+  SKETCH_LSQ_SAP_QR = 0,
+  SKETCH_LSQ_SAP_SVD = 1,
+  SKETCH_LSQ_LSQR_D = 2
+};
+
 typedef struct {
   int32_t iters;        /* LSQR iterations                                 */
   int32_t status;       /* SKETCH_OK or SKETCH_ERR_NO_CONVERGENCE          */
   int32_t istop;        /* 1: ||r|| test, 2: ||M^T r|| test, 0: max iters  */
-  int32_t reserved;
+  int32_t rank;         /* columns of the preconditioner: the singular     */
+                        /* values kept (SAP-SVD), else n                   */
   double error;         /* Error(x) = ||A^T(Ax-b)|| / (||A||_F ||Ax-b||)   */
   double test2;         /* LSQR's own estimate for the preconditioned system*/
   double ms_sketch, ms_qr, ms_lsqr;  /* stage times (CUDA events)          */
@@ -290,6 +303,25 @@ typedef struct {
 int sketch_lsq_solve(sketch_t h, const sketch_csc* A, const double* b,
                      double* x, double tol, int32_t maxit,
                      sketch_lsq_info* info, sketch_stream_t stream);
+
+/* sketch_lsq_solve with a choice of method (sketch_lsq_method), Sec. 5.3.
+ *   SKETCH_LSQ_SAP_QR: exactly sketch_lsq_solve.
+ *   SKETCH_LSQ_SAP_SVD: the same sketch and QR, then the SVD of R (= the
+ *     SVD of the sketch up to the left factor) by one-sided Jacobi in FP64
+ *     (sweeps of round-robin column-pair rotations until a sweep rotates
+ *     nothing, at most 40); singular values below sigma_max / 10^12 are
+ *     dropped (info->rank = the number kept) and LSQR runs on A V_k
+ *     Sigma_k^{-1}, so a rank-deficient A gives its minimum-norm
+ *     least-squares solution instead of SKETCH_ERR_CSC.  n <= 4096; extra
+ *     workspace 2 n^2 doubles.
+ *   SKETCH_LSQ_LSQR_D: no sketch; LSQR on A D with the diagonal D above
+ *     (ms_sketch = 0, ms_qr = the column norms).
+ * Same arguments, synchronisation and errors as sketch_lsq_solve, plus
+ * SKETCH_ERR_ARG for an unknown method and SKETCH_ERR_UNSUPPORTED for
+ * SAP-SVD with n > 4096. */
+int sketch_lsq_solve_method(sketch_t h, const sketch_csc* A, const double* b,
+                            double* x, double tol, int32_t maxit, int32_t method,
+                            sketch_lsq_info* info, sketch_stream_t stream);
 
 /* ---- continuous-batching solve server ---------------------------------- */
 typedef struct sketch_server_s* sketch_server_t;

@@ -30,6 +30,9 @@ SKETCH_ERR_UNSUPPORTED = -7
 SKETCH_PM1, SKETCH_UNIFORM, SKETCH_NORMAL = 0, 1, 2
 SKETCH_F32, SKETCH_BF16 = 0, 1
 SKETCH_MODE_AUTO, SKETCH_MODE_REGEN, SKETCH_MODE_PANEL, SKETCH_MODE_TILE = 0, 1, 2, 3
+SKETCH_LSQ_SAP_QR, SKETCH_LSQ_SAP_SVD, SKETCH_LSQ_LSQR_D = 0, 1, 2
+LSQ_METHODS = {"sap_qr": SKETCH_LSQ_SAP_QR, "sap_svd": SKETCH_LSQ_SAP_SVD,
+               "lsqr_d": SKETCH_LSQ_LSQR_D}
 
 DIST_NAMES = {"pm1": SKETCH_PM1, "uniform": SKETCH_UNIFORM,
               "normal": SKETCH_NORMAL}
@@ -71,13 +74,13 @@ class sketch_server_result(ctypes.Structure):
 
 class sketch_lsq_info(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int32), ("status", ctypes.c_int32),
-                ("istop", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("istop", ctypes.c_int32), ("rank", ctypes.c_int32),
                 ("error", ctypes.c_double), ("test2", ctypes.c_double),
                 ("ms_sketch", ctypes.c_double), ("ms_qr", ctypes.c_double),
                 ("ms_lsqr", ctypes.c_double)]
 
     def as_dict(self):
-        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+        return {f: getattr(self, f) for f, _ in self._fields_}
 
 
 _lock = threading.Lock()
@@ -103,6 +106,8 @@ SIGNATURES = [
     ("sketch_validate_csc", _I32, [_CSCP, _VP]),
     ("sketch_lsq_solve", _I32, [_VP, _CSCP, _VP, _VP, _D, _I32,
                                 ctypes.POINTER(sketch_lsq_info), _VP]),
+    ("sketch_lsq_solve_method", _I32, [_VP, _CSCP, _VP, _VP, _D, _I32, _I32,
+                                       ctypes.POINTER(sketch_lsq_info), _VP]),
     ("sketch_debug_philox", _I32, [_VP, _U64, _VP, _I64, _VP]),
     ("sketch_debug_S", _I32, [_I32, _U64, _U32, _VP, _VP, _VP, _I64, _VP]),
     ("sketch_debug_normal_pair", _I32, [_VP, _VP, _I64, _VP]),
@@ -314,16 +319,26 @@ class Sketch:
         return int(load().sketch_generated_entries(self.h, _stream_ptr(stream)))
 
     def lsq_solve(self, A: DeviceCSC, b, x=None, tol=1e-10, maxit=1000,
-                  stream=None, check=True):
+                  stream=None, check=True, method=None):
+        """sketch_lsq_solve, or sketch_lsq_solve_method when `method` is given
+        ("sap_qr", "sap_svd", "lsqr_d" or the enum value)."""
         import torch
         if x is None:
             x = torch.zeros(self.n, dtype=torch.float64, device=b.device)
         info = sketch_lsq_info()
-        rc = load().sketch_lsq_solve(self.h, ctypes.byref(A.desc),
-                                     ctypes.c_void_p(b.data_ptr()),
-                                     ctypes.c_void_p(x.data_ptr()), float(tol),
-                                     int(maxit), ctypes.byref(info),
-                                     _stream_ptr(stream))
+        if method is None:
+            rc = load().sketch_lsq_solve(self.h, ctypes.byref(A.desc),
+                                         ctypes.c_void_p(b.data_ptr()),
+                                         ctypes.c_void_p(x.data_ptr()), float(tol),
+                                         int(maxit), ctypes.byref(info),
+                                         _stream_ptr(stream))
+        else:
+            code = LSQ_METHODS[method] if isinstance(method, str) else int(method)
+            rc = load().sketch_lsq_solve_method(self.h, ctypes.byref(A.desc),
+                                                ctypes.c_void_p(b.data_ptr()),
+                                                ctypes.c_void_p(x.data_ptr()), float(tol),
+                                                int(maxit), code, ctypes.byref(info),
+                                                _stream_ptr(stream))
         if check and rc not in (SKETCH_OK, SKETCH_ERR_NO_CONVERGENCE):
             _check(rc, self.h)
         d = info.as_dict()

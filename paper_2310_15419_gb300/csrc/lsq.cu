@@ -527,17 +527,41 @@ __device__ __forceinline__ double warp_sum_parts(const double* __restrict__ part
   return warp_sum(a0 + a1);
 }
 
-// out[i] = sum_c Mrow[i][c] x[c] over the nonzero triangle (c >= i upper,
-// c <= i lower).  One warp per row.  Used for x = R^{-1} y.
+// The preconditioner M of LSQR on A M (x = M y), kept as two row-major n x n
+// matrices, M and M^T:
+//   kPcTri   M = R^{-1} (SAP-QR): M upper triangular, M^T lower triangular
+//   kPcDense M = V_k Sigma_k^{-1} padded with zero columns (SAP-SVD): full
+//   kPcDiag  M = diag(D) (LSQR-D): only the diagonal is read
+constexpr int kPcTri = 0, kPcDense = 1, kPcDiag = 2;
+
+// Columns [lo, hi) of row i that can be nonzero, for M (lower = 0) or M^T
+// (lower = 1).
+__device__ __forceinline__ void pc_range(int pk, int lower, int64_t i, int n, int64_t& lo,
+                                         int64_t& hi) {
+  if (pk == kPcDense) {
+    lo = 0;
+    hi = n;
+  } else if (pk == kPcDiag) {
+    lo = i;
+    hi = i + 1;
+  } else {
+    lo = lower ? 0 : i;
+    hi = lower ? i + 1 : n;
+  }
+}
+
+// out[i] = sum_c Mrow[i][c] x[c] over the columns pc_range allows.  One warp
+// per row.  Used for x = M y.
 __global__ void k_gemv_tri(const double* __restrict__ Mrow, int n,
                            const double* __restrict__ x, double* __restrict__ out,
-                           int lower) {
+                           int lower, int pk) {
   const int lane = threadIdx.x & 31;
   const int64_t warps = static_cast<int64_t>(gridDim.x) * (blockDim.x >> 5);
   for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x >> 5) + (threadIdx.x >> 5);
        i < n; i += warps) {
-    const double s = lower ? warp_row_dot(Mrow + i * n, x, 0, i + 1, lane)
-                           : warp_row_dot(Mrow + i * n, x, i, n, lane);
+    int64_t lo, hi;
+    pc_range(pk, lower, i, n, lo, hi);
+    const double s = warp_row_dot(Mrow + i * n, x, lo, hi, lane);
     if (lane == 0) out[i] = s;
   }
 }
@@ -745,13 +769,15 @@ __global__ void k_lsqr_test(const double* __restrict__ party, int npy, Scalars* 
 __global__ void __launch_bounds__(32 * kTriWarps)
     k_lsqr_vraw(int n, const double* __restrict__ RinvT, const double* __restrict__ t2,
                 const double* __restrict__ v, double* __restrict__ vraw,
-                double* __restrict__ partial4, Scalars* sc, int init) {
+                double* __restrict__ partial4, Scalars* sc, int init, int pk) {
   __shared__ double sh[2 + kTriWarps];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t i = static_cast<int64_t>(blockIdx.x) * kTriWarps + warp;
   const bool has = i < n;
-  double r0[8];  // R^{-T} and v are not written by the columns pass
-  row_chunk(RinvT + (has ? i : 0) * n, 0, has ? i + 1 : 0, lane, r0);
+  int64_t lo = 0, hi = 0;
+  if (has) pc_range(pk, 1, i, n, lo, hi);
+  double r0[8];  // M^T and v are not written by the columns pass
+  row_chunk(RinvT + (has ? i : 0) * n, lo, hi, lane, r0);
   const double vi = (!init && has && lane == 0) ? v[i] : 0.0;
   pdl_wait();
   pdl_launch();
@@ -762,7 +788,7 @@ __global__ void __launch_bounds__(32 * kTriWarps)
     sh[0] = usq * ib;
     sh[1] = ib;
   }
-  const double dot = has ? warp_row_dot_pre(RinvT + i * n, t2, 0, i + 1, lane, r0) : 0.0;
+  const double dot = has ? warp_row_dot_pre(RinvT + i * n, t2, lo, hi, lane, r0) : 0.0;
   __syncthreads();
   const double beta = sh[0], ib = sh[1];
   if (lane == 0) {
@@ -798,14 +824,16 @@ __global__ void __launch_bounds__(32 * kTriWarps)
     k_lsqr_step(int n, const double* __restrict__ Rinv, const double* __restrict__ vraw,
                 double* __restrict__ v, double* __restrict__ w, double* __restrict__ y,
                 double* __restrict__ t, const double* __restrict__ partial4, int np4,
-                double* __restrict__ party, Scalars* sc, int par, int init) {
+                double* __restrict__ party, Scalars* sc, int par, int init, int pk) {
   __shared__ double sh[8 + kTriWarps];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t i = static_cast<int64_t>(blockIdx.x) * kTriWarps + warp;
   const bool has = i < n;
-  // R^{-1}, w, y and slot par are not written by the vraw kernel
+  int64_t lo = 0, hi = 0;
+  if (has) pc_range(pk, 0, i, n, lo, hi);
+  // M, w, y and slot par are not written by the vraw kernel
   double r0[8];
-  row_chunk(Rinv + (has ? i : 0) * n, has ? i : 0, has ? n : 0, lane, r0);
+  row_chunk(Rinv + (has ? i : 0) * n, lo, hi, lane, r0);
   double wi = 0.0, yi = 0.0;
   if (lane == 0 && has && !init) {
     wi = w[i];
@@ -852,7 +880,7 @@ __global__ void __launch_bounds__(32 * kTriWarps)
       sh[2] = f_w;
     }
   }
-  const double dot = has ? warp_row_dot_pre(Rinv + i * n, vraw, i, n, lane, r0) : 0.0;
+  const double dot = has ? warp_row_dot_pre(Rinv + i * n, vraw, lo, hi, lane, r0) : 0.0;
   __syncthreads();
   const double ia = sh[0];
   if (lane == 0) {
@@ -1090,6 +1118,227 @@ size_t al(size_t b) { return (b + 255) / 256 * 256; }
 
 }  // namespace
 
+// ---------------------------------------------------------------------------
+// SAP-SVD (Sec. 5.3): the SVD of the sketch from its R (A_hat = Q R, so A_hat
+// and R have the same singular values and right singular vectors), by the
+// one-sided (Hestenes) Jacobi method in FP64: rotate pairs of columns of R
+// until all are orthogonal; then R V = U Sigma with sigma_j the column norms
+// and V the accumulated rotations.  A sweep visits every pair once in
+// n' - 1 rounds of n'/2 disjoint pairs (n' = n rounded up to even, the
+// round-robin "circle" order); one kernel per round, one block per pair.
+// ---------------------------------------------------------------------------
+constexpr int kJacobiThreads = 256;
+
+// Rc = R column-major (n x n) from the QR workspace W (d x n, R in its upper
+// triangle), V = I.
+__global__ void k_svd_init(const double* __restrict__ W, int64_t d, int n,
+                           double* __restrict__ Rc, double* __restrict__ V) {
+  const int64_t total = static_cast<int64_t>(n) * n;
+  for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; t < total;
+       t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t c = t / n, r = t % n;
+    Rc[t] = r <= c ? W[c * d + r] : 0.0;
+    V[t] = r == c ? 1.0 : 0.0;
+  }
+}
+
+// Pair `p` of round `r` of the circle order on n2 (even) slots: slot 0 stays,
+// slots 1 .. n2 - 1 turn by one position per round.
+__device__ __forceinline__ void jacobi_pair(int n2, int r, int p, int& a, int& b) {
+  const int m1 = n2 - 1;
+  if (p == 0) {
+    a = 0;
+    b = 1 + r % m1;
+  } else {
+    a = 1 + (r + p) % m1;
+    b = 1 + (r + m1 - p) % m1;
+  }
+  if (a > b) {
+    const int t = a;
+    a = b;
+    b = t;
+  }
+}
+
+// One round: block p rotates its pair of columns of Rc (and V) when they are
+// not orthogonal to working precision (|a.b| > 1e-15 sqrt(|a|^2 |b|^2)), by
+// the 2 x 2 symmetric Schur rotation of their Gram matrix; counts rotations.
+__global__ void __launch_bounds__(kJacobiThreads)
+    k_jacobi_round(int n, int n2, int r, double* __restrict__ Rc, double* __restrict__ V,
+                   unsigned long long* __restrict__ rotations) {
+  __shared__ double red[3][kJacobiThreads / 32];
+  __shared__ double cs[2];
+  int a, b;
+  jacobi_pair(n2, r, blockIdx.x, a, b);
+  if (b >= n) return;  // the padding slot of an odd n
+  double* ca = Rc + static_cast<int64_t>(a) * n;
+  double* cb = Rc + static_cast<int64_t>(b) * n;
+  double al = 0.0, be = 0.0, ga = 0.0;
+  for (int i = threadIdx.x; i < n; i += kJacobiThreads) {
+    const double x = ca[i], y = cb[i];
+    al = fma(x, x, al);
+    be = fma(y, y, be);
+    ga = fma(x, y, ga);
+  }
+  al = warp_sum(al);
+  be = warp_sum(be);
+  ga = warp_sum(ga);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) {
+    red[0][warp] = al;
+    red[1][warp] = be;
+    red[2][warp] = ga;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double A = 0.0, B = 0.0, G = 0.0;
+    for (int w = 0; w < kJacobiThreads / 32; ++w) {
+      A += red[0][w];
+      B += red[1][w];
+      G += red[2][w];
+    }
+    double c = 1.0, sn = 0.0;
+    if (G != 0.0 && fabs(G) > 1e-15 * sqrt(A * B)) {
+      const double zeta = (B - A) / (2.0 * G);
+      const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+      c = 1.0 / sqrt(1.0 + t * t);
+      sn = c * t;
+      atomicAdd(rotations, 1ULL);
+    }
+    cs[0] = c;
+    cs[1] = sn;
+  }
+  __syncthreads();
+  const double c = cs[0], sn = cs[1];
+  if (sn == 0.0) return;
+  double* va = V + static_cast<int64_t>(a) * n;
+  double* vb = V + static_cast<int64_t>(b) * n;
+  for (int i = threadIdx.x; i < n; i += kJacobiThreads) {
+    const double x = ca[i], y = cb[i];
+    ca[i] = c * x - sn * y;
+    cb[i] = sn * x + c * y;
+    const double p = va[i], q = vb[i];
+    va[i] = c * p - sn * q;
+    vb[i] = sn * p + c * q;
+  }
+}
+
+// sigma_j = ||column j of Rc|| (one warp per column); then (one block) the
+// cutoff sigma_max / 1e12 and the rank: keep[j] = 1 / sigma_j for kept j,
+// else 0; rank[0] = number kept.
+__global__ void k_svd_sigma(const double* __restrict__ Rc, int n, double* __restrict__ sig) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = static_cast<int64_t>(gridDim.x) * (blockDim.x >> 5);
+  for (int64_t j = blockIdx.x * static_cast<int64_t>(blockDim.x >> 5) + (threadIdx.x >> 5);
+       j < n; j += warps) {
+    double a = 0.0;
+    for (int i = lane; i < n; i += 32) {
+      const double x = Rc[j * n + i];
+      a = fma(x, x, a);
+    }
+    a = warp_sum(a);
+    if (lane == 0) sig[j] = sqrt(a);
+  }
+}
+
+__global__ void __launch_bounds__(1024)
+    k_svd_cutoff(int n, const double* __restrict__ sig, double* __restrict__ keep,
+                 int* __restrict__ rank) {
+  __shared__ double red[32];
+  __shared__ int cnt[32];
+  double mx = 0.0;
+  for (int j = threadIdx.x; j < n; j += blockDim.x) mx = fmax(mx, sig[j]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) red[warp] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double m = 0.0;
+    for (int w = 0; w < (blockDim.x + 31) / 32; ++w) m = fmax(m, red[w]);
+    red[0] = m;
+  }
+  __syncthreads();
+  const double smax = red[0];
+  int k = 0;
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    const bool kept = sig[j] > 0.0 && sig[j] >= smax / 1e12;
+    keep[j] = kept ? 1.0 / sig[j] : 0.0;
+    k += kept;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) k += __shfl_xor_sync(0xffffffffu, k, o);
+  __syncthreads();
+  if (lane == 0) cnt[warp] = k;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int t = 0;
+    for (int w = 0; w < (blockDim.x + 31) / 32; ++w) t += cnt[w];
+    rank[0] = t;
+  }
+}
+
+// P = V diag(keep) (row-major n x n: P[i][j] = V[j][i] keep[j], V
+// column-major) and P^T (row-major).
+__global__ void k_svd_precond(const double* __restrict__ V, const double* __restrict__ keep,
+                              int n, double* __restrict__ P, double* __restrict__ PT) {
+  const int64_t total = static_cast<int64_t>(n) * n;
+  for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; t < total;
+       t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t i = t / n, j = t % n;
+    P[t] = V[j * n + i] * keep[j];   // row i, column j
+    PT[t] = V[i * n + j] * keep[i];  // row i of P^T = column i of P
+  }
+}
+
+// ---------------------------------------------------------------------------
+// LSQR-D (Sec. 5.3's diagonal preconditioner): colnorm[k] = ||A_k||_2 in FP64
+// (one warp per column), then D_k = 1 / ||A_k|| or 1 when ||A_k|| <= eps
+// sqrt(n) max ||A_k|| (eps = 2^-52), written on the diagonals of the two
+// row-major preconditioner matrices (the diagonal kind reads nothing else).
+// ---------------------------------------------------------------------------
+template <typename VT>
+__global__ void k_colnorm(int32_t n, int64_t nnz, const int32_t* __restrict__ colptr,
+                          const VT* __restrict__ vals, double* __restrict__ norm) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = static_cast<int64_t>(gridDim.x) * (blockDim.x >> 5);
+  for (int64_t k = blockIdx.x * static_cast<int64_t>(blockDim.x >> 5) + (threadIdx.x >> 5);
+       k < n; k += warps) {
+    const int2 range = column_range(colptr, k, nnz, nullptr);
+    double a = 0.0;
+    for (int32_t e = range.x + lane; e < range.y; e += 32) {
+      const double v = static_cast<double>(to_f32(vals[e]));
+      a = fma(v, v, a);
+    }
+    a = warp_sum(a);
+    if (lane == 0) norm[k] = sqrt(a);
+  }
+}
+
+__global__ void __launch_bounds__(1024)
+    k_diag_precond(int n, const double* __restrict__ norm, double* __restrict__ P,
+                   double* __restrict__ PT) {
+  __shared__ double red[32];
+  double mx = 0.0;
+  for (int j = threadIdx.x; j < n; j += blockDim.x) mx = fmax(mx, norm[j]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double m = 0.0;
+    for (int w = 0; w < (blockDim.x + 31) / 32; ++w) m = fmax(m, red[w]);
+    red[0] = m;
+  }
+  __syncthreads();
+  const double thr = 0x1p-52 * sqrt(static_cast<double>(n)) * red[0];
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    const double dj = norm[j] <= thr ? 1.0 : 1.0 / norm[j];
+    P[static_cast<int64_t>(j) * n + j] = dj;
+    PT[static_cast<int64_t>(j) * n + j] = dj;
+  }
+}
+
 struct LsqState {
   void* ws = nullptr;
   size_t ws_bytes = 0;
@@ -1097,10 +1346,13 @@ struct LsqState {
   cudaStream_t ls = nullptr;     // internal stream (capturable)
   cudaEvent_t ev[6] = {};
   cudaGraphExec_t graph = nullptr;
-  const void* graph_key[6] = {};  // what the captured iterations read/write
+  const void* graph_key[8] = {};  // what the captured iterations read/write
   cudaGraphExec_t qr_graph = nullptr;  // the QR's n launches, per shape
   int64_t qr_key[3] = {-1, -1, -1};     // (d, n, workspace address) of qr_graph
   int64_t qr_seen[3] = {-1, -1, -1};    // shape of the previous solve
+  cudaGraphExec_t jacobi_graph = nullptr;  // one Jacobi sweep, per shape
+  const void* jacobi_key[3] = {};
+  int svd_sweeps = 0;                    // sweeps of the last SAP-SVD solve
 };
 
 void destroy_lsq_state(sketch_t h) {
@@ -1109,6 +1361,7 @@ void destroy_lsq_state(sketch_t h) {
   if (st->ls) cudaStreamSynchronize(st->ls);
   if (st->graph) cudaGraphExecDestroy(st->graph);
   if (st->qr_graph) cudaGraphExecDestroy(st->qr_graph);
+  if (st->jacobi_graph) cudaGraphExecDestroy(st->jacobi_graph);
   for (auto& e : st->ev)
     if (e) cudaEventDestroy(e);
   if (st->ls) cudaStreamDestroy(st->ls);
@@ -1141,6 +1394,11 @@ struct LsqLayout {
   char* scan_tmp;
   void* csr_ws;
   int* status;
+  // SAP-SVD: R column-major, V, sigma, 1/sigma of the kept values, rank and
+  // the rotation counter (sized only for that method); LSQR-D: column norms
+  double *Rc, *Vj, *sig, *keep, *colnorm;
+  int* rank;
+  unsigned long long* rotations;
   size_t bytes;
 };
 
@@ -1153,7 +1411,7 @@ int rows_blocks(int64_t m) {
 
 int tri_blocks(int64_t n) { return static_cast<int>((n + kTriWarps - 1) / kTriWarps); }
 
-LsqLayout layout(void* base, int64_t m, int64_t n, int64_t d, int64_t nnz) {
+LsqLayout layout(void* base, int64_t m, int64_t n, int64_t d, int64_t nnz, int method = 0) {
   LsqLayout L{};
   char* p = static_cast<char*>(base);
   auto take = [&](size_t b) {
@@ -1199,6 +1457,14 @@ LsqLayout layout(void* base, int64_t m, int64_t n, int64_t d, int64_t nnz) {
   L.scan_tmp = take(static_cast<size_t>(
       scan_bytes_for(std::max<int64_t>(m + 1, kLenBuckets * nblk))));
   L.csr_ws = take(csr_workspace_bytes(m, nnz));
+  const int64_t nsvd = method == 1 ? n : 0;
+  L.Rc = reinterpret_cast<double*>(take(sizeof(double) * nsvd * nsvd));
+  L.Vj = reinterpret_cast<double*>(take(sizeof(double) * nsvd * nsvd));
+  L.sig = reinterpret_cast<double*>(take(sizeof(double) * n));
+  L.keep = reinterpret_cast<double*>(take(sizeof(double) * n));
+  L.colnorm = reinterpret_cast<double*>(take(sizeof(double) * n));
+  L.rank = reinterpret_cast<int*>(take(256));
+  L.rotations = reinterpret_cast<unsigned long long*>(take(256));
   L.bytes = static_cast<size_t>(p - static_cast<char*>(base));
   return L;
 }
@@ -1279,7 +1545,7 @@ unsigned gemv_blocks(int64_t n) {
 // the step reads slot par and writes slot par ^ 1.
 void lsqr_kernels(const LsqLayout& L, const CscView& A, const CsrView& csr,
                   const int32_t* mnz, const double* b, int32_t m, int par, int init,
-                  int pdl, cudaStream_t s) {
+                  int pdl, int pk, cudaStream_t s) {
   const int n = A.n;
   const int g2 = rows_blocks(m), gt = tri_blocks(n);
   launch(k_lsqr_rows, g2, kRows, s, pdl, m, mnz, csr.rowptr, csr.ccol, csr.cval, L.t, L.u[par],
@@ -1296,9 +1562,9 @@ void lsqr_kernels(const LsqLayout& L, const CscView& A, const CsrView& csr,
   c.pdl = pdl;
   cols(A, L.u[par ^ 1], L.t2, L.sc, c, s);
   launch(k_lsqr_vraw, gt, 32 * kTriWarps, s, pdl, n, L.RinvT, L.t2, L.v, L.vraw, L.p4, L.sc,
-         init);
+         init, pk);
   launch(k_lsqr_step, gt, 32 * kTriWarps, s, pdl, n, L.Rinv, L.vraw, L.v, L.w, L.y, L.t, L.p4,
-         gt, L.py, L.sc, par, init);
+         gt, L.py, L.sc, par, init, pk);
 }
 
 }  // namespace
@@ -1309,18 +1575,29 @@ size_t lsq_workspace_bytes(int64_t m, int64_t n, int64_t d, int64_t nnz) {
 }
 }  // namespace sk
 
-extern "C" int sketch_lsq_solve(sketch_t h, const sketch_csc* A,
-                                const double* b, double* x, double tol,
-                                int32_t maxit, sketch_lsq_info* info,
-                                sketch_stream_t stream) {
+namespace {
+
+// The solve of sketch_lsq_solve / sketch_lsq_solve_method.  method:
+// SKETCH_LSQ_SAP_QR (preconditioner R^{-1}), SKETCH_LSQ_SAP_SVD (V_k
+// Sigma_k^{-1} from the Jacobi SVD of R) or SKETCH_LSQ_LSQR_D (diagonal, no
+// sketch).
+int lsq_solve(sketch_t h, const sketch_csc* A, const double* b, double* x, double tol,
+              int32_t maxit, int method, sketch_lsq_info* info, sketch_stream_t stream) {
   if (!h) return fail(nullptr, SKETCH_ERR_ARG, "handle is null");
   int rc = check_csc_args(h, A);
   if (rc != SKETCH_OK) return rc;
   if (!b || !x) return fail(h, SKETCH_ERR_ARG, "b or x is null");
   if (!(tol > 0.0)) return fail(h, SKETCH_ERR_ARG, "tol must be > 0");
   if (maxit < 1) return fail(h, SKETCH_ERR_ARG, "maxit must be >= 1");
-  if (h->d < h->n) return fail(h, SKETCH_ERR_ARG, "sketch size d must be >= n");
+  if (method < SKETCH_LSQ_SAP_QR || method > SKETCH_LSQ_LSQR_D)
+    return fail(h, SKETCH_ERR_ARG, "unknown least-squares method");
+  const bool sketched = method != SKETCH_LSQ_LSQR_D;
+  if (sketched && h->d < h->n) return fail(h, SKETCH_ERR_ARG, "sketch size d must be >= n");
   if (h->n > 8192) return fail(h, SKETCH_ERR_UNSUPPORTED, "n > 8192");
+  if (method == SKETCH_LSQ_SAP_SVD && h->n > 4096)
+    return fail(h, SKETCH_ERR_UNSUPPORTED, "SAP-SVD takes n <= 4096");
+  const int pk = method == SKETCH_LSQ_SAP_QR ? kPcTri
+                 : method == SKETCH_LSQ_SAP_SVD ? kPcDense : kPcDiag;
   cudaStream_t user = reinterpret_cast<cudaStream_t>(stream);
   const int64_t m = A->m, n = A->n, d = h->d, nnz = A->nnz;
   if (!h->lsq) h->lsq = new (std::nothrow) LsqState();
@@ -1331,7 +1608,7 @@ extern "C" int sketch_lsq_solve(sketch_t h, const sketch_csc* A,
       return fail(h, SKETCH_ERR_CUDA, "cudaStreamCreate failed");
     for (auto& e : st.ev) cudaEventCreate(&e);
   }
-  const size_t need = layout(nullptr, m, n, d, nnz).bytes + 256;
+  const size_t need = layout(nullptr, m, n, d, nnz, method).bytes + 256;
   if (st.ws_bytes < need) {
     cudaStreamSynchronize(st.ls);
     if (st.ws) cudaFree(st.ws);
@@ -1342,6 +1619,10 @@ extern "C" int sketch_lsq_solve(sketch_t h, const sketch_csc* A,
     if (st.qr_graph) {
       cudaGraphExecDestroy(st.qr_graph);
       st.qr_graph = nullptr;
+    }
+    if (st.jacobi_graph) {
+      cudaGraphExecDestroy(st.jacobi_graph);
+      st.jacobi_graph = nullptr;
     }
     st.ws = nullptr;
     st.ws_bytes = 0;
@@ -1355,7 +1636,7 @@ extern "C" int sketch_lsq_solve(sketch_t h, const sketch_csc* A,
     st.host = nullptr;
     return fail(h, SKETCH_ERR_OOM, "cudaMallocHost failed");
   }
-  const LsqLayout L = layout(st.ws, m, n, d, nnz);
+  const LsqLayout L = layout(st.ws, m, n, d, nnz, method);
   cudaStream_t s = st.ls;
   cudaEventRecord(st.ev[4], user);  // the solve starts after the caller's work
   cudaStreamWaitEvent(s, st.ev[4], 0);
@@ -1376,8 +1657,9 @@ extern "C" int sketch_lsq_solve(sketch_t h, const sketch_csc* A,
     if (bad) return fail(h, SKETCH_ERR_CSC, "malformed CSC (colptr or row indices)");
   }
 
-  // ---- 1. sketch ------------------------------------------------------------
-  if ((rc = sketch_apply(h, A, L.Ahat, reinterpret_cast<sketch_stream_t>(s))) != SKETCH_OK)
+  // ---- 1. sketch (not for LSQR-D) -------------------------------------------
+  if (sketched &&
+      (rc = sketch_apply(h, A, L.Ahat, reinterpret_cast<sketch_stream_t>(s))) != SKETCH_OK)
     return rc;
   cudaError_t e = cudaSuccess;
   cudaEventRecord(st.ev[1], s);
@@ -1387,7 +1669,7 @@ extern "C" int sketch_lsq_solve(sketch_t h, const sketch_csc* A,
   const int pdl = h->dependent_launch ? 1 : 0;
   const int64_t dn = d * n;
   const unsigned gb = static_cast<unsigned>(std::max<int64_t>(1, 16LL * num_sms()));
-  {
+  if (sketched) {
     // the QR is n dependent launches.  When a shape repeats (same d, n and
     // workspace as the previous solve) they are captured once as a graph
     // and replayed; a one-off shape launches them directly.
@@ -1429,7 +1711,66 @@ extern "C" int sketch_lsq_solve(sketch_t h, const sketch_csc* A,
       enqueue_qr();
     }
   }
-  h->launches += 4 + (n - 1);
+  if (sketched) h->launches += 4 + (n - 1);
+  int rank = static_cast<int>(n);
+  if (method == SKETCH_LSQ_SAP_SVD) {
+    // one-sided Jacobi on R: sweeps of n' - 1 rounds (a graph per sweep, per
+    // shape), until a sweep rotates nothing or 40 sweeps have run
+    const int n32 = static_cast<int>(n), n2 = n32 + (n32 & 1);
+    k_svd_init<<<gb, 256, 0, s>>>(L.W, d, n32, L.Rc, L.Vj);
+    h->launches += 1;
+    const void* jkey[3] = {L.Rc, L.Vj, L.rotations};
+    if (st.jacobi_graph && std::memcmp(jkey, st.jacobi_key, sizeof(jkey)) != 0) {
+      cudaGraphExecDestroy(st.jacobi_graph);
+      st.jacobi_graph = nullptr;
+    }
+    if (!st.jacobi_graph) {
+      cudaGraph_t g = nullptr;
+      e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+      if (e != cudaSuccess) return cuda_fail(h, e, "begin Jacobi capture");
+      for (int r = 0; r < n2 - 1; ++r)
+        k_jacobi_round<<<n2 / 2, kJacobiThreads, 0, s>>>(n32, n2, r, L.Rc, L.Vj, L.rotations);
+      e = cudaStreamEndCapture(s, &g);
+      if (e != cudaSuccess) return cuda_fail(h, e, "end Jacobi capture");
+      e = cudaGraphInstantiate(&st.jacobi_graph, g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) {
+        st.jacobi_graph = nullptr;
+        return cuda_fail(h, e, "Jacobi graph instantiate");
+      }
+      std::memcpy(st.jacobi_key, jkey, sizeof(jkey));
+    }
+    unsigned long long rot = 1;
+    int sweeps = 0;
+    for (; sweeps < 40 && rot != 0; ++sweeps) {
+      cudaMemsetAsync(L.rotations, 0, sizeof(unsigned long long), s);
+      e = cudaGraphLaunch(st.jacobi_graph, s);
+      if (e != cudaSuccess) return cuda_fail(h, e, "Jacobi sweep");
+      h->launches += n2 - 1;
+      cudaMemcpyAsync(&rot, L.rotations, sizeof(rot), cudaMemcpyDeviceToHost, s);
+      e = cudaStreamSynchronize(s);
+      if (e != cudaSuccess) return cuda_fail(h, e, "Jacobi sweep");
+    }
+    st.svd_sweeps = sweeps;
+    k_svd_sigma<<<gemv_blocks(n), 256, 0, s>>>(L.Rc, n32, L.sig);
+    k_svd_cutoff<<<1, 1024, 0, s>>>(n32, L.sig, L.keep, L.rank);
+    k_svd_precond<<<gb, 256, 0, s>>>(L.Vj, L.keep, n32, L.Rinv, L.RinvT);
+    h->launches += 3;
+    e = cudaMemcpyAsync(&rank, L.rank, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "SVD rank");
+  } else if (method == SKETCH_LSQ_LSQR_D) {
+    if (A->dtype == SKETCH_F32)
+      k_colnorm<float><<<gemv_blocks(n), 256, 0, s>>>(
+          static_cast<int32_t>(n), nnz, A->colptr, static_cast<const float*>(A->values),
+          L.colnorm);
+    else
+      k_colnorm<__nv_bfloat16><<<gemv_blocks(n), 256, 0, s>>>(
+          static_cast<int32_t>(n), nnz, A->colptr,
+          static_cast<const __nv_bfloat16*>(A->values), L.colnorm);
+    k_diag_precond<<<1, 1024, 0, s>>>(static_cast<int>(n), L.colnorm, L.Rinv, L.RinvT);
+    h->launches += 2;
+  }
   cudaEventRecord(st.ev[2], s);
 
   // ---- 4. LSQR on A R^{-1} ---------------------------------------------------
@@ -1466,12 +1807,14 @@ extern "C" int sketch_lsq_solve(sketch_t h, const sketch_csc* A,
   *st.host = init;
   cudaMemcpyAsync(L.sc, st.host, sizeof(Scalars), cudaMemcpyHostToDevice, s);
   // u = b, beta = ||b||, v = R^{-T} A^T u / (beta alpha), w = v, y = 0
-  lsqr_kernels(L, csc, csr, mnz, b, static_cast<int32_t>(m), 1, 1, pdl, s);
+  lsqr_kernels(L, csc, csr, mnz, b, static_cast<int32_t>(m), 1, 1, pdl, pk, s);
   h->launches += 4;
   // iterations: a cached graph of kIterPerGraph iterations, replayed until
   // the device sets `done`
-  const void* key[6] = {A->colptr, A->rowidx, A->values, st.ws,
-                        reinterpret_cast<const void*>(n), reinterpret_cast<const void*>(m)};
+  const void* key[8] = {A->colptr, A->rowidx, A->values, st.ws,
+                        reinterpret_cast<const void*>(n), reinterpret_cast<const void*>(m),
+                        reinterpret_cast<const void*>(static_cast<intptr_t>(pk)),
+                        reinterpret_cast<const void*>(d)};
   if (st.graph && std::memcmp(key, st.graph_key, sizeof(key)) != 0) {
     cudaGraphExecDestroy(st.graph);
     st.graph = nullptr;
@@ -1482,7 +1825,7 @@ extern "C" int sketch_lsq_solve(sketch_t h, const sketch_csc* A,
     if (e != cudaSuccess) return cuda_fail(h, e, "begin capture");
     static_assert(kIterPerGraph % 2 == 0, "a graph starts and ends on slot 0");
     for (int it = 0; it < kIterPerGraph; ++it)
-      lsqr_kernels(L, csc, csr, mnz, nullptr, static_cast<int32_t>(m), it & 1, 0, pdl, s);
+      lsqr_kernels(L, csc, csr, mnz, nullptr, static_cast<int32_t>(m), it & 1, 0, pdl, pk, s);
     launch(k_lsqr_test, 1, 32, s, pdl, L.py, tri_blocks(n), L.sc, 0);
     e = cudaStreamEndCapture(s, &g);
     if (e != cudaSuccess) return cuda_fail(h, e, "end capture");
@@ -1510,8 +1853,8 @@ extern "C" int sketch_lsq_solve(sketch_t h, const sketch_csc* A,
       if (e != cudaSuccess) return cuda_fail(h, e, "lsqr iterations");
       if (st.host->done || launched >= maxit) break;
     }
-    // x = R^{-1} y
-    k_gemv_tri<<<gemv_blocks(n), 256, 0, s>>>(L.Rinv, static_cast<int>(n), L.y, x, 0);
+    // x = M y
+    k_gemv_tri<<<gemv_blocks(n), 256, 0, s>>>(L.Rinv, static_cast<int>(n), L.y, x, 0, pk);
     cudaEventRecord(st.ev[3], s);
     // ---- 5. Error(x) = ||A^T (A x - b)|| / (||A||_F ||A x - b||) in FP64 ----
     const int g2 = rows_blocks(m);
@@ -1564,8 +1907,11 @@ extern "C" int sketch_lsq_solve(sketch_t h, const sketch_csc* A,
     info->ms_qr = ms;
     cudaEventElapsedTime(&ms, st.ev[2], st.ev[3]);
     info->ms_lsqr = ms;
+    info->rank = rank;
   }
-  if (qr_status & 4)
+  // a zero diagonal of R is an error of SAP-QR only (SAP-SVD drops the
+  // small singular values instead)
+  if ((qr_status & 4) && method == SKETCH_LSQ_SAP_QR)
     return fail(h, SKETCH_ERR_CSC, "R has a zero diagonal entry (rank-deficient A)");
   if (qr_status & (kStatusBadRow | kStatusBadColptr))
     return fail(h, SKETCH_ERR_CSC, "a kernel met an out-of-range index");
@@ -1573,6 +1919,20 @@ extern "C" int sketch_lsq_solve(sketch_t h, const sketch_csc* A,
   if (info) info->status = status;
   if (status != SKETCH_OK) fail(h, status, "LSQR reached maxit");
   return status;
+}
+
+}  // namespace
+
+extern "C" int sketch_lsq_solve(sketch_t h, const sketch_csc* A, const double* b, double* x,
+                                double tol, int32_t maxit, sketch_lsq_info* info,
+                                sketch_stream_t stream) {
+  return lsq_solve(h, A, b, x, tol, maxit, SKETCH_LSQ_SAP_QR, info, stream);
+}
+
+extern "C" int sketch_lsq_solve_method(sketch_t h, const sketch_csc* A, const double* b,
+                                       double* x, double tol, int32_t maxit, int32_t method,
+                                       sketch_lsq_info* info, sketch_stream_t stream) {
+  return lsq_solve(h, A, b, x, tol, maxit, method, info, stream);
 }
 
 extern "C" int sketch_debug_qr(int64_t d, int64_t n, const double* A, double* R,

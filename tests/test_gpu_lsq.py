@@ -130,3 +130,97 @@ def test_repeat_solves_reuse_state_and_agree():
     x1, i1 = sk.lsq_solve(dA, bb)
     x2, i2 = sk.lsq_solve(dA, bb)
     assert torch.equal(x1, x2) and i1["iters"] == i2["iters"]
+
+
+# ------------------------------------------------- SAP-SVD and LSQR-D (Sec. 5.3)
+def _solve_m(A, b, d, method, dist="uniform", seed=1, tol=1e-10, maxit=2000):
+    dA = capi.DeviceCSC(A)
+    sk = capi.Sketch(A.m, A.n, d, dist, seed=seed)
+    bb = torch.from_numpy(np.ascontiguousarray(b, np.float64)).cuda()
+    x, info = sk.lsq_solve(dA, bb, tol=tol, maxit=maxit, method=method)
+    torch.cuda.synchronize()
+    sk.close()
+    return x.cpu().numpy(), info
+
+
+@pytest.mark.parametrize("dist", ["pm1", "normal"])
+def test_sap_svd_full_rank_matches_oracle_and_lstsq(dist):
+    m, n = 20_000, 90
+    A, b, _ = inputs.lsq_problem(m, n, 0.01, seed=17, noise=1e-2, col_scale_decades=2.0)
+    x, info = _solve_m(A, b, 2 * n, "sap_svd", dist)
+    assert info["rc"] == capi.SKETCH_OK and info["rank"] == n
+    assert info["error"] <= 1e-10
+    xo, io = oracle.sap_svd_solve(m, n, 2 * n, DISTS[dist], 1, 0, A.colptr, A.rowidx,
+                                  A.values, b, tol=1e-10, maxit=500)
+    Ad = A.to_scipy().toarray()
+    xl = np.linalg.lstsq(Ad, b, rcond=None)[0]
+    cond = np.linalg.cond(Ad)
+    assert np.linalg.norm(x - xl) <= 1e-9 * cond * np.linalg.norm(xl)
+    assert np.linalg.norm(x - xo) <= 1e-9 * cond * np.linalg.norm(xo)
+    assert abs(info["iters"] - io["iters"]) <= 5
+    e_cpu = oracle.ls_error(m, n, A.colptr, A.rowidx, A.values, b, x)
+    assert abs(info["error"] - e_cpu) <= 0.05 * e_cpu + 1e-16
+
+
+def test_sap_svd_rank_deficient_gives_minimum_norm_solution():
+    """A scaled duplicate column and a zero column: SAP-QR refuses (zero
+    diagonal of R) or cannot be trusted, SAP-SVD drops the two null
+    directions (rank n - 2) and returns pinv(A) b, as the oracle does."""
+    m, n = 8000, 40
+    A, b, _ = inputs.lsq_problem(m, n, 0.03, seed=18, noise=1e-1)
+    import scipy.sparse as sp
+    Ad = A.to_scipy().toarray()
+    Ad[:, 11] = 2.0 * Ad[:, 4]
+    Ad[:, 30] = 0.0
+    C = sp.csc_matrix(Ad)
+    C.sort_indices()
+    B = inputs.CSC(m, n, C.indptr.astype(np.int32), C.indices.astype(np.int32),
+                   C.data.astype(np.float32))
+    Ad = B.to_scipy().toarray()
+    x, info = _solve_m(B, b, 2 * n, "sap_svd", "uniform", seed=3, tol=1e-12)
+    assert info["rc"] == capi.SKETCH_OK and info["rank"] == n - 2
+    xp = np.linalg.pinv(Ad, rcond=1e-12) @ b
+    assert np.linalg.norm(x - xp) <= 1e-8 * np.linalg.norm(xp)
+    xo, io = oracle.sap_svd_solve(m, n, 2 * n, oracle.UNIFORM, 3, 0, B.colptr, B.rowidx,
+                                  B.values, b, tol=1e-12, maxit=500)
+    assert io["rank"] == n - 2
+    assert np.linalg.norm(x - xo) <= 1e-8 * np.linalg.norm(xo)
+
+
+def test_lsqr_d_matches_oracle_and_lstsq():
+    m, n = 20_000, 60
+    A, b, _ = inputs.lsq_problem(m, n, 0.01, seed=19, noise=1e-2, col_scale_decades=2.0)
+    x, info = _solve_m(A, b, 2 * n, "lsqr_d")
+    assert info["rc"] == capi.SKETCH_OK and info["error"] <= 1e-10
+    assert info["ms_sketch"] < 0.05  # no sketch on this path
+    xo, io = oracle.lsqr_d_solve(m, n, A.colptr, A.rowidx, A.values, b, tol=1e-10,
+                                 maxit=2000)
+    Ad = A.to_scipy().toarray()
+    xl = np.linalg.lstsq(Ad, b, rcond=None)[0]
+    cond = np.linalg.cond(Ad)
+    assert np.linalg.norm(x - xl) <= 1e-9 * cond * np.linalg.norm(xl)
+    assert np.linalg.norm(x - xo) <= 1e-9 * cond * np.linalg.norm(xo)
+    assert abs(info["iters"] - io["iters"]) <= max(5, io["iters"] // 20)
+
+
+def test_three_methods_on_lsq_mixed_full_size():
+    """lsq_mixed (m = 10^6, n = 500, BF16, column scales over four decades):
+    SAP-QR, SAP-SVD and LSQR-D reach the same solution; Error(x) of each is
+    re-checked in FP64 on the host."""
+    A, b, _ = inputs.lsq_mixed()
+    dA = capi.DeviceCSC(A)
+    bb = torch.from_numpy(b).cuda()
+    xs = {}
+    for method in ("sap_qr", "sap_svd", "lsqr_d"):
+        sk = capi.Sketch(A.m, A.n, 2 * A.n, "pm1", seed=1)
+        x, info = sk.lsq_solve(dA, bb, tol=1e-10, maxit=5000, method=method)
+        torch.cuda.synchronize()
+        sk.close()
+        x = x.cpu().numpy()
+        e_cpu = oracle.ls_error(A.m, A.n, A.colptr, A.rowidx, A.values, b, x)
+        assert abs(info["error"] - e_cpu) <= 0.05 * e_cpu + 1e-16, method
+        assert e_cpu <= 1e-8, (method, e_cpu)
+        xs[method] = x
+    ref = xs["sap_qr"]
+    for method in ("sap_svd", "lsqr_d"):
+        assert np.linalg.norm(xs[method] - ref) <= 1e-8 * np.linalg.norm(ref), method
