@@ -1876,10 +1876,17 @@ int lsq_solve(sketch_t h, const sketch_csc* A, const double* b, double* x, doubl
     const Scalars& c = *st.host;
     const double den = std::sqrt(c.afro2) * std::sqrt(c.err_res2);
     const double err = den > 0.0 ? std::sqrt(c.err_num2) / den : 0.0;
-    // stop when the metric is met, LSQR ran out of iterations, or another
-    // round gained less than 2x (the metric sits at its FP64 floor)
+    // The FP64 floor of the metric: r = A x - b carries the rounding of b,
+    // about eps ||b||, and A^T moves that by at most ||A||_2 eps ||b|| <=
+    // ||A||_F eps ||b||, so Error(x) cannot be resolved below about
+    // eps ||b|| / ||r||.  Within 2x of that, more LSQR rounds are wasted.
+    const double rnorm = std::sqrt(c.err_res2);
+    const double floor_est = rnorm > 0.0 ? 0x1p-52 * c.bnorm / rnorm : 0.0;
+    // stop when the metric is met, LSQR ran out of iterations, the metric
+    // is at its FP64 floor, or another round gained less than 2x
     if (err <= tol || c.istop == 0 || qr_status != 0 ||
-        c.slot[c.latest & 1].iters >= maxit || err > 0.5 * prev_err)
+        c.slot[c.latest & 1].iters >= maxit || err <= 2.0 * floor_est ||
+        err > 0.5 * prev_err)
       break;
     prev_err = err;
     k_tighten<<<gb, 256, 0, s>>>(L.sc, c.latest == 1, m, L.u[1], L.u[0]);
