@@ -60,35 +60,58 @@ __global__ void k_dense_index(int32_t m, const int32_t* __restrict__ flag,
   }
 }
 
-// A3[k * K3 + t * Kp + didx[j]] = t-th BF16 term of A(j, k) for dense rows.
+// Column of entry e of a CSC: the k with colptr[k] <= e < colptr[k + 1]
+// (binary search; entries outside every column range give -1).
+__device__ __forceinline__ int32_t column_of(const int32_t* __restrict__ colptr, int32_t n,
+                                             int64_t e) {
+  int32_t lo = 0, hi = n;  // colptr[lo] <= e < colptr[hi] if e is in range
+  if (e < colptr[0] || e >= colptr[n]) return -1;
+  while (hi - lo > 1) {
+    const int32_t mid = lo + ((hi - lo) >> 1);
+    if (colptr[mid] <= e) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+// The t-th BF16 term of A(j, k) for dense rows j (q = didx[j]), one thread
+// per entry (its column by binary search), so the build runs at memory speed
+// however long the columns are.  Two layouts of A3:
+//   tiled = 0: A3[k * 3 Kp + t * Kp + q] (column k's terms, K fastest);
+//   tiled = 1: for the pipelined kernel, each step's three 128-column B
+//     tiles contiguous (24 KB) in the operand layout the MMA reads: tile
+//     (k >> 7, step q >> 5), term t, k-chunk (q >> 3) & 3, column k & 127,
+//     8 consecutive q -- one bulk copy per step.
+__device__ __forceinline__ int64_t a3_offset(int tiled, int32_t k, int32_t q, int t,
+                                             int64_t Kp) {
+  if (!tiled) return static_cast<int64_t>(k) * 3 * Kp + t * Kp + q;
+  const int64_t steps = Kp >> 5;
+  const int64_t tile_step = (static_cast<int64_t>(k >> 7) * steps + (q >> 5)) * 3 + t;
+  return ((tile_step * 4 + ((q >> 3) & 3)) * 128 + (k & 127)) * 8 + (q & 7);
+}
+
 template <typename VT>
-__global__ void k_dense_scatter(int32_t n, int32_t m, int32_t Kp, int64_t nnz,
+__global__ void k_dense_scatter(int32_t n, int32_t m, int32_t Kp, int64_t nnz, int tiled,
                                 const int32_t* __restrict__ colptr,
                                 const int32_t* __restrict__ rowidx,
                                 const VT* __restrict__ vals,
                                 const int32_t* __restrict__ didx,
                                 uint16_t* __restrict__ A3) {
-  const int lane = threadIdx.x & 31;
-  const int64_t warps = static_cast<int64_t>(gridDim.x) * (blockDim.x >> 5);
-  const int64_t K3 = 3LL * Kp;
-  for (int64_t k = blockIdx.x * static_cast<int64_t>(blockDim.x >> 5) + (threadIdx.x >> 5);
-       k < n; k += warps) {
-    const int2 range = column_range(colptr, k, nnz, nullptr);
-    for (int32_t e = range.x + lane; e < range.y; e += 32) {
-      const int32_t j = rowidx[e];
-      if (static_cast<uint32_t>(j) >= static_cast<uint32_t>(m)) continue;
-      const int32_t q = didx[j];
-      if (q < 0) continue;
-      const float a = to_f32(vals[e]);
-      const float a1 = __bfloat162float(__float2bfloat16_rn(a));
-      const float r1 = a - a1;  // exact
-      const float a2 = __bfloat162float(__float2bfloat16_rn(r1));
-      const float a3 = r1 - a2;  // exact, fits BF16
-      uint16_t* col = A3 + k * K3;
-      col[q] = bf16_bits(a1);
-      col[Kp + q] = bf16_bits(a2);
-      col[2 * Kp + q] = bf16_bits(a3);
-    }
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < nnz;
+       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int32_t j = rowidx[e];
+    if (static_cast<uint32_t>(j) >= static_cast<uint32_t>(m)) continue;
+    const int32_t q = didx[j];
+    if (q < 0) continue;
+    const int32_t k = column_of(colptr, n, e);
+    if (k < 0) continue;
+    const float a = to_f32(vals[e]);
+    const float a1 = __bfloat162float(__float2bfloat16_rn(a));
+    const float r1 = a - a1;  // exact
+    const float a2 = __bfloat162float(__float2bfloat16_rn(r1));
+    const float a3 = r1 - a2;  // exact, fits BF16
+    A3[a3_offset(tiled, k, q, 0, Kp)] = bf16_bits(a1);
+    A3[a3_offset(tiled, k, q, 1, Kp)] = bf16_bits(a2);
+    A3[a3_offset(tiled, k, q, 2, Kp)] = bf16_bits(a3);
   }
 }
 
@@ -335,6 +358,368 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" ::"r"(tmem) : "memory");
 }
 
+// ---------------------------------------------------------------------------
+// k_tc_panel: the same product for long panels (many dense rows), warp
+// specialised and pipelined.  A CTA owns a 128 x 128 tile of A_hat (rows of
+// S x columns of A) and one of `splits` slices of the dense rows (split-K:
+// enough CTAs for every SM; the slices' partial tiles are added in a fixed
+// order afterwards).  Per step of 32 dense rows, in a ring of kPanStages
+// shared-memory stages:
+//   warp 0 (one thread): the three B tiles (the BF16 terms of A3, 128
+//     columns x 32 k each) by TMA, twelve 16-byte-wide boxes into the
+//     no-swizzle K-major layout (row i of a box at 16 i, k-chunks 2048 B
+//     apart), completion counted on the stage's full barrier;
+//   warps 4-11: the +-1 S tile (128 rows x 32 k, BF16, same layout), warps
+//     4-7 for even steps and 8-11 for odd ones, 32 rows each with no barrier
+//     between them: lane k computes the Philox block of
+//     dense row k and keeps the warp's word, a five-stage shuffle transpose
+//     gives each lane its row's 32 signs, which become BF16 +-1; then a proxy
+//     fence and one arrival per warp on the stage's full barrier;
+//   warp 1 (one thread): six MMAs (3 terms x 2 k halves, M = N = 128,
+//     K = 16) into one of two tensor-memory accumulators, which it switches
+//     every two steps, and a commit that frees the stage.
+// Warps 12-15 promote: each finished two-step accumulator is added, with
+// CUDA-core round-to-nearest FP32 additions, into running sums kept in
+// tensor memory.  The tensor core's own accumulation then covers only twelve
+// products per output at a time, so its rounding cannot build up along a
+// panel of thousands of rows.  The same warps finally store the sums.
+// Every mbarrier wait has an iteration limit; on a timeout the CTA records
+// kStatusTimeout, drains the MMAs it issued and frees its tensor memory.
+// ---------------------------------------------------------------------------
+constexpr int kPanStages = 4;
+constexpr int kPanThreads = 512;
+constexpr uint32_t kPanLbo = 2048;       // K-direction core-matrix stride
+constexpr uint32_t kPanSbo = 128;        // M/N-direction 8-row-group stride
+constexpr int kPanTileBytes = 8192;      // one 128 x 32 BF16 operand tile
+constexpr int kPanStageBytes = 4 * kPanTileBytes;  // the S tile + three B tiles
+constexpr uint32_t kPanTxBytes = 3 * kPanTileBytes;
+constexpr size_t kPanSmem = kPanStages * kPanStageBytes + 1024;  // + the slice's row ids
+constexpr uint32_t kPanSums = 256;       // tensor-memory column of the running sums
+// Panels of at least this many padded dense rows take the pipelined kernel.
+constexpr int kPanMinKp = 512;
+constexpr int kPanMaxSliceSteps = 384;  // steps of one split-K slice (row ids in smem)
+
+__device__ __forceinline__ uint64_t pan_desc(uint32_t saddr) {
+  return static_cast<uint64_t>((saddr >> 4) & 0x3FFFu) |
+         (static_cast<uint64_t>((kPanLbo >> 4) & 0x3FFFu) << 16) |
+         (static_cast<uint64_t>((kPanSbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("{\n.reg .b64 st;\nmbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(bar)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile(
+      "{\n.reg .b64 st;\nmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}\n" ::"r"(
+          bar),
+      "r"(bytes)
+      : "memory");
+}
+// Bulk copy (TMA, untiled) of `bytes` contiguous bytes into shared memory,
+// completing them on the mbarrier (both addresses 16-byte aligned, bytes a
+// multiple of 16).
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes,
+                                          uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, "
+      "[%3];" ::"r"(dst),
+      "l"(src), "r"(bytes), "r"(bar)
+      : "memory");
+}
+
+#define SK_TMEM_X32_REGS(v)                                                              \
+  "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),     \
+      "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),         \
+      "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]),      \
+      "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),      \
+      "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]),      \
+      "=r"(v[31])
+#define SK_TMEM_X32_ARGS(v)                                                              \
+  "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), \
+      "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]),  \
+      "r"(v[15]), "r"(v[16]), "r"(v[17]), "r"(v[18]), "r"(v[19]), "r"(v[20]), "r"(v[21]), \
+      "r"(v[22]), "r"(v[23]), "r"(v[24]), "r"(v[25]), "r"(v[26]), "r"(v[27]), "r"(v[28]), \
+      "r"(v[29]), "r"(v[30]), "r"(v[31])
+#define SK_X32_LIST                                                                       \
+  "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, " \
+  "%19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}"
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 " SK_X32_LIST ", [%32];"
+               : SK_TMEM_X32_REGS(v)
+               : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_ld32_nowait(uint32_t taddr, uint32_t (&v)[32]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 " SK_X32_LIST ", [%32];"
+               : SK_TMEM_X32_REGS(v)
+               : "r"(taddr));
+}
+// Wait for the loads in flight; the registers are operands so no use of
+// them is scheduled before the data has landed.
+__device__ __forceinline__ void tmem_wait_ld32(uint32_t (&a)[32], uint32_t (&b)[32]) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(a[0]), "+r"(a[1]), "+r"(a[2]), "+r"(a[3]), "+r"(a[4]), "+r"(a[5]),
+                 "+r"(a[6]), "+r"(a[7]), "+r"(a[8]), "+r"(a[9]), "+r"(a[10]), "+r"(a[11]),
+                 "+r"(a[12]), "+r"(a[13]), "+r"(a[14]), "+r"(a[15]), "+r"(a[16]), "+r"(a[17]),
+                 "+r"(a[18]), "+r"(a[19]), "+r"(a[20]), "+r"(a[21]), "+r"(a[22]), "+r"(a[23]),
+                 "+r"(a[24]), "+r"(a[25]), "+r"(a[26]), "+r"(a[27]), "+r"(a[28]), "+r"(a[29]),
+                 "+r"(a[30]), "+r"(a[31])
+               :
+               : "memory");
+  asm volatile(""
+               : "+r"(b[0]), "+r"(b[1]), "+r"(b[2]), "+r"(b[3]), "+r"(b[4]), "+r"(b[5]),
+                 "+r"(b[6]), "+r"(b[7]), "+r"(b[8]), "+r"(b[9]), "+r"(b[10]), "+r"(b[11]),
+                 "+r"(b[12]), "+r"(b[13]), "+r"(b[14]), "+r"(b[15]), "+r"(b[16]), "+r"(b[17]),
+                 "+r"(b[18]), "+r"(b[19]), "+r"(b[20]), "+r"(b[21]), "+r"(b[22]), "+r"(b[23]),
+                 "+r"(b[24]), "+r"(b[25]), "+r"(b[26]), "+r"(b[27]), "+r"(b[28]), "+r"(b[29]),
+                 "+r"(b[30]), "+r"(b[31])
+               :
+               : "memory");
+}
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&v)[32]) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], "
+               "{%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, "
+               "%18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};" ::"r"(
+                   taddr),
+               SK_TMEM_X32_ARGS(v)
+               : "memory");
+}
+
+__global__ void __launch_bounds__(kPanThreads, 1)
+    k_tc_panel(int32_t d, int32_t n, int32_t Kp, int32_t steps_per_split,
+               const int32_t* __restrict__ rows, const int32_t* __restrict__ Kdev,
+               const uint16_t* __restrict__ A3, float* __restrict__ out,
+               int64_t split_stride, int accumulate, uint32_t k0, uint32_t k1,
+               uint32_t stream_id, int* status) {
+  extern __shared__ uint8_t sm_raw[];
+  __shared__ __align__(8) uint64_t full[kPanStages], empty[kPanStages], acc_full[2],
+      acc_empty[2], drain_bar;
+  __shared__ uint32_t tmem_base;
+  __shared__ volatile int failed;  // set by any role whose bounded wait gave up
+  uint8_t* base = sm_raw + ((1024u - (smem_u32(sm_raw) & 1023u)) & 1023u);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int d0 = blockIdx.x * 128, n0 = blockIdx.y * 128;
+  const int K = *Kdev;
+  const int st0 = blockIdx.z * steps_per_split;
+  const int nsteps = max(0, min(Kp / kBK, st0 + steps_per_split) - st0);
+  const int npairs = (nsteps + 1) / 2;
+  float* dst = out + blockIdx.z * split_stride;
+  auto tileS = [&](int stg) { return base + stg * kPanStageBytes; };
+  auto tileB = [&](int stg, int t) { return base + stg * kPanStageBytes + (1 + t) * kPanTileBytes; };
+  if (tid == 0) {
+    failed = 0;
+    for (int q = 0; q < kPanStages; ++q) {
+      mbar_init(smem_u32(&full[q]), 5);   // the TMA arrival (with its bytes) + 4 builder warps
+      mbar_init(smem_u32(&empty[q]), 1);  // the MMA commit
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(smem_u32(&acc_full[b]), 1);   // the MMA commit of a two-step accumulator
+      mbar_init(smem_u32(&acc_empty[b]), 4);  // one arrival per promoting warp
+    }
+    mbar_init(smem_u32(&drain_bar), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(
+                     smem_u32(&tmem_base))
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_base;
+  // the dense-row ids of this CTA's slice, staged once (the builders read
+  // them every step)
+  int32_t* srows = reinterpret_cast<int32_t*>(base + kPanStages * kPanStageBytes);
+  for (int t = tid; t < nsteps * kBK; t += kPanThreads) {
+    const int q = st0 * kBK + t;
+    srows[t] = q < K ? rows[q] : 0;  // padding rows multiply zeros
+  }
+  __syncthreads();
+
+  if (warp == 0) {
+    if (lane == 0) {  // TMA producer of the A-panel (B operand) tiles
+      for (int i = 0; i < nsteps; ++i) {
+        const int sg = i % kPanStages, round = i / kPanStages, st = st0 + i;
+        if (i >= kPanStages && !mbar_wait(smem_u32(&empty[sg]), (round - 1) & 1)) {
+          failed = 1;
+          break;
+        }
+        if (failed) break;
+        mbar_arrive_tx(smem_u32(&full[sg]), kPanTxBytes);
+        // the step's three B tiles are one contiguous 24 KB block of A3
+        const uint16_t* src = A3 + (static_cast<int64_t>(blockIdx.y) * (Kp / kBK) + st) * 3 *
+                                       (kPanTileBytes / 2);
+        bulk_load(smem_u32(tileB(sg, 0)), src, kPanTxBytes, smem_u32(&full[sg]));
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {  // MMA issuer
+      bool ok = true;
+      for (int i = 0; i < nsteps && ok; ++i) {
+        const int sg = i % kPanStages, round = i / kPanStages, pr = i >> 1, b = pr & 1;
+        if ((i & 1) == 0 && pr >= 2 &&
+            !mbar_wait(smem_u32(&acc_empty[b]), ((pr >> 1) - 1) & 1)) {
+          ok = false;
+          break;
+        }
+        if (!mbar_wait(smem_u32(&full[sg]), round & 1)) {
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+        for (int t = 0; t < 3; ++t)
+#pragma unroll
+          for (int kh = 0; kh < 2; ++kh) {
+            const uint64_t ad = pan_desc(smem_u32(tileS(sg)) + kh * 2 * kPanLbo);
+            const uint64_t bd = pan_desc(smem_u32(tileB(sg, t)) + kh * 2 * kPanLbo);
+            const uint32_t acc = ((i & 1) || t > 0 || kh > 0) ? 1u : 0u;
+            asm volatile(
+                "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+                    tmem + static_cast<uint32_t>(128 * b)),
+                "l"(ad), "l"(bd), "r"(kUmmaIdesc), "r"(acc)
+                : "memory");
+          }
+        asm volatile(
+            "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                smem_u32(&empty[sg]))
+            : "memory");
+        if ((i & 1) || i == nsteps - 1)
+          asm volatile(
+              "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                  smem_u32(&acc_full[b]))
+              : "memory");
+      }
+      if (!ok) {  // drain the MMAs issued so far before the memory is freed
+        failed = 1;
+        asm volatile(
+            "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                smem_u32(&drain_bar))
+            : "memory");
+        mbar_wait(smem_u32(&drain_bar), 0);
+      }
+    }
+  } else if (warp >= 4 && warp < 12) {  // S-tile builders: rows 32 w'.., steps of one parity
+    const int wq = (warp - 4) & 3, parity = (warp - 4) >> 2;
+    const int r = 32 * wq + lane;
+    for (int i = parity; i < nsteps; i += 2) {
+      const int sg = i % kPanStages, round = i / kPanStages;
+      int ok = 1;
+      if (lane == 0 && i >= kPanStages && !mbar_wait(smem_u32(&empty[sg]), (round - 1) & 1))
+        ok = 0;
+      ok = __shfl_sync(0xffffffffu, ok, 0);
+      if (!ok) failed = 1;
+      if (failed) break;
+      // lane L: the Philox block of dense row k = L, word wq (the signs of
+      // rows 32 wq .. 32 wq + 31); transposed, lane L holds the 32 signs of
+      // row 32 wq + L over the step's dense rows (bit k)
+      const int32_t j = srows[i * kBK + lane];
+      const uint4 x = philox_block(static_cast<uint32_t>(d0 >> 7), static_cast<uint32_t>(j),
+                                   stream_id, k0, k1);
+      uint32_t v = wq == 0 ? x.x : wq == 1 ? x.y : wq == 2 ? x.z : x.w;
+#pragma unroll
+      for (int sh = 16; sh > 0; sh >>= 1) {
+        const uint32_t m = sh == 16 ? 0x0000FFFFu : sh == 8 ? 0x00FF00FFu
+                         : sh == 4 ? 0x0F0F0F0Fu : sh == 2 ? 0x33333333u : 0x55555555u;
+        const uint32_t o = __shfl_xor_sync(0xffffffffu, v, sh);
+        v = (lane & sh) ? ((v & ~m) | ((o >> sh) & m)) : ((v & m) | ((o & m) << sh));
+      }
+      uint8_t* dstS = tileS(sg) + r * 16;
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {  // k-chunk c: dense rows 8c .. 8c + 7
+        uint32_t wv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int ka = 8 * c + 2 * u;
+          wv[u] = pm1_pair((v >> ka) & 1u, (v >> (ka + 1)) & 1u);
+        }
+        *reinterpret_cast<uint4*>(dstS + c * kPanLbo) = make_uint4(wv[0], wv[1], wv[2], wv[3]);
+      }
+      // generic-proxy writes -> visible to the tensor core, then one arrival
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&full[sg]));
+    }
+  } else if (warp >= 12) {  // promoters: lanes 32 (warp & 3) .. of the tile
+    const int rq = warp & 3;
+    const uint32_t lanes = static_cast<uint32_t>(32 * rq) << 16;
+    bool ok = true;
+    for (int pr = 0; pr < npairs; ++pr) {
+      const int b = pr & 1;
+      int got = 1;
+      if (lane == 0) got = mbar_wait(smem_u32(&acc_full[b]), (pr >> 1) & 1) ? 1 : 0;
+      got = __shfl_sync(0xffffffffu, got, 0);
+      if (!got || failed) {
+        ok = false;
+        failed = 1;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll 1
+      for (int cc = 0; cc < 4; ++cc) {
+        uint32_t v[32], sm[32];
+        // both loads in flight before one wait
+        tmem_ld32_nowait(tmem + lanes + static_cast<uint32_t>(128 * b + 32 * cc), v);
+        if (pr > 0) tmem_ld32_nowait(tmem + lanes + kPanSums + static_cast<uint32_t>(32 * cc), sm);
+        tmem_wait_ld32(v, sm);
+        if (pr > 0) {
+#pragma unroll
+          for (int jj = 0; jj < 32; ++jj)
+            v[jj] = __float_as_uint(__fadd_rn(__uint_as_float(sm[jj]), __uint_as_float(v[jj])));
+        }
+        tmem_st32(tmem + lanes + kPanSums + static_cast<uint32_t>(32 * cc), v);
+      }
+      asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&acc_empty[b]));
+    }
+    if (ok && npairs > 0) {
+      const int r = d0 + 32 * rq + lane;
+#pragma unroll 1
+      for (int cc = 0; cc < 4; ++cc) {
+        uint32_t v[32];
+        tmem_ld32(tmem + lanes + kPanSums + static_cast<uint32_t>(32 * cc), v);
+        if (r < d) {
+#pragma unroll
+          for (int jj = 0; jj < 32; ++jj) {
+            const int c = n0 + 32 * cc + jj;
+            if (c < n) {
+              float* o = dst + static_cast<int64_t>(c) * d + r;
+              const float x = __uint_as_float(v[jj]);
+              *o = accumulate ? *o + x : x;
+            }
+          }
+        }
+      }
+    }
+  }
+  __syncthreads();
+  if (tid == 0 && failed) atomicOr(status, kStatusTimeout);
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
+}
+
+// A_hat (+)= the splits' partial tiles, added in the fixed order 0, 1, ...
+__global__ void k_panel_reduce(int64_t total, int splits, const float* __restrict__ partial,
+                               float* __restrict__ Ahat, int accumulate) {
+  for (int64_t idx = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; idx < total;
+       idx += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    float v = partial[idx];
+    for (int z = 1; z < splits; ++z) v += partial[static_cast<int64_t>(z) * total + idx];
+    Ahat[idx] = accumulate ? Ahat[idx] + v : v;
+  }
+}
+
 // The timeout path of mbar_wait on purpose: a fresh mbarrier whose phase
 // nothing completes; the bounded wait gives up and records kStatusTimeout.
 __global__ void k_debug_wait_timeout(int* status, int limit) {
@@ -355,11 +740,23 @@ struct DenseLayout {
   int32_t *cnt, *flag, *pos, *didx, *Kdev;
   uint16_t* A3;
   char* scan_tmp;
-  int32_t *rcnt, *rcolptr, *rrowidx;  // the rest of A (CSC)
+  int32_t *rpos, *rcolptr, *rrowidx;  // the rest of A (CSC); rpos: nnz + 1 positions
+  float* partial;                      // split-K partial copies of A_hat (panel kernel)
+  int32_t max_splits;
   void* rvalues;
   size_t bytes;
 };
-DenseLayout dense_layout(void* ws, int64_t m, int64_t n, int64_t kmax, int64_t nnz) {
+// Split-K copies of A_hat the pipelined panel kernel may use: up to four,
+// and at most 1 GiB of them (none when the panel cannot reach its length).
+int64_t panel_max_splits(int64_t n, int64_t d, int64_t kmax) {
+  const int64_t Kp = (kmax + kBK - 1) / kBK * kBK;
+  if (Kp < kPanMinKp) return 0;
+  const int64_t one = n * d * static_cast<int64_t>(sizeof(float));
+  return std::min<int64_t>(4, (int64_t(1) << 30) / std::max<int64_t>(one, 1));
+}
+
+DenseLayout dense_layout(void* ws, int64_t m, int64_t n, int64_t d, int64_t kmax,
+                         int64_t nnz) {
   DenseLayout L{};
   char* p = static_cast<char*>(ws);
   auto take = [&](size_t b) {
@@ -373,12 +770,15 @@ DenseLayout dense_layout(void* ws, int64_t m, int64_t n, int64_t kmax, int64_t n
   L.didx = reinterpret_cast<int32_t*>(take((m + 1) * sizeof(int32_t)));
   L.Kdev = reinterpret_cast<int32_t*>(take(sizeof(int32_t) * 64));
   const int64_t Kp = (kmax + kBK - 1) / kBK * kBK;
-  L.A3 = reinterpret_cast<uint16_t*>(take(static_cast<size_t>(n) * 3 * Kp * 2));
-  L.scan_tmp = take(static_cast<size_t>(scan_bytes_for(std::max(m, n) + 1)));
-  L.rcnt = reinterpret_cast<int32_t*>(take((n + 1) * sizeof(int32_t)));
+  L.A3 = reinterpret_cast<uint16_t*>(take(static_cast<size_t>((n + 127) / 128 * 128) * 3 * Kp * 2));
+  L.scan_tmp = take(static_cast<size_t>(scan_bytes_for(std::max(std::max(m, n), nnz) + 1)));
+  L.rpos = reinterpret_cast<int32_t*>(take((std::max<int64_t>(1, nnz) + 1) * sizeof(int32_t)));
   L.rcolptr = reinterpret_cast<int32_t*>(take((n + 1) * sizeof(int32_t)));
   L.rrowidx = reinterpret_cast<int32_t*>(take(std::max<int64_t>(1, nnz) * sizeof(int32_t)));
   L.rvalues = take(std::max<int64_t>(1, nnz) * sizeof(float));
+  L.max_splits = static_cast<int32_t>(panel_max_splits(n, d, kmax));
+  L.partial = reinterpret_cast<float*>(
+      take(static_cast<size_t>(L.max_splits > 1 ? L.max_splits : 0) * n * d * sizeof(float)));
   L.bytes = static_cast<size_t>(p - static_cast<char*>(ws));
   return L;
 }
@@ -389,71 +789,53 @@ __device__ __forceinline__ bool rest_keeps(int32_t j, int32_t m, const int32_t* 
   return static_cast<uint32_t>(j) >= static_cast<uint32_t>(m) || didx[j] < 0;
 }
 
-// rcnt[k] = entries of column k outside the panel; rcnt[n] = 0.  A malformed
-// colptr is recorded in *status (its column ranges are clamped to [0, nnz]).
-__global__ void k_rest_count(int32_t n, int32_t m, int64_t nnz,
-                             const int32_t* __restrict__ colptr,
-                             const int32_t* __restrict__ rowidx,
-                             const int32_t* __restrict__ didx, int32_t* __restrict__ rcnt,
-                             int* status) {
-  const int lane = threadIdx.x & 31;
-  const int64_t warps = static_cast<int64_t>(gridDim.x) * (blockDim.x >> 5);
-  for (int64_t k = blockIdx.x * static_cast<int64_t>(blockDim.x >> 5) + (threadIdx.x >> 5);
-       k <= n; k += warps) {
-    int32_t c = 0;
-    if (k < n) {
-      const int2 range = column_range(colptr, k, nnz, lane == 0 ? status : nullptr);
-      for (int32_t e = range.x + lane; e < range.y; e += 32)
-        c += rest_keeps(rowidx[e], m, didx);
-    }
-    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-    if (lane == 0) rcnt[k] = c;
+// The rest of A (entries outside the panel's rows) as a stream compaction
+// over all entries: rpos[e] = 1 for kept entries (rows outside the panel,
+// and out-of-range rows, which the sparse kernels then flag), 0 otherwise,
+// and rpos[nnz] = 0; an exclusive scan turns the flags into output
+// positions.  One thread per entry throughout.
+__global__ void k_rest_flags(int64_t nnz, int32_t m, const int32_t* __restrict__ rowidx,
+                             const int32_t* __restrict__ didx, int32_t* __restrict__ rpos) {
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e <= nnz;
+       e += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    rpos[e] = e < nnz ? (rest_keeps(rowidx[e], m, didx) ? 1 : 0) : 0;
+}
+
+// rest_colptr[k] = kept entries before column k's first entry (column
+// ranges clamped to [0, nnz]; a malformed colptr is recorded in *status).
+__global__ void k_rest_colptr(int32_t n, int64_t nnz, const int32_t* __restrict__ colptr,
+                              const int32_t* __restrict__ rpos, int32_t* __restrict__ rcolptr,
+                              int* status) {
+  for (int64_t k = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; k <= n;
+       k += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t p = colptr[k];
+    const int64_t c = p < 0 ? 0 : (p > nnz ? nnz : p);
+    if (c != p || (k < n && colptr[k + 1] < p)) atomicOr(status, kStatusBadColptr);
+    rcolptr[k] = rpos[c];
   }
 }
 
-// The kept entries of column k, in their order, at rcolptr[k].. (one warp
-// per column, ballot compaction).
-// (Write positions stay below nnz: overlapping column ranges of a malformed
-// colptr could otherwise count more kept entries than A holds.)
+// Kept entry e goes to position rpos[e] (positions stay below nnz).
 template <typename VT>
-__global__ void k_rest_copy(int32_t n, int32_t m, int64_t nnz,
-                            const int32_t* __restrict__ colptr,
-                            const int32_t* __restrict__ rowidx, const VT* __restrict__ vals,
-                            const int32_t* __restrict__ didx,
-                            const int32_t* __restrict__ rcolptr,
-                            int32_t* __restrict__ rrowidx, VT* __restrict__ rvals) {
-  const int lane = threadIdx.x & 31;
-  const unsigned below = (1u << lane) - 1u;
-  const int64_t warps = static_cast<int64_t>(gridDim.x) * (blockDim.x >> 5);
-  for (int64_t k = blockIdx.x * static_cast<int64_t>(blockDim.x >> 5) + (threadIdx.x >> 5);
-       k < n; k += warps) {
-    int32_t out = rcolptr[k];
-    const int2 range = column_range(colptr, k, nnz, nullptr);
-    const int32_t hi = range.y;
-    for (int32_t e0 = range.x; e0 < hi; e0 += 32) {
-      const int32_t e = e0 + lane;
-      int32_t j = 0;
-      bool keep = false;
-      if (e < hi) {
-        j = rowidx[e];
-        keep = rest_keeps(j, m, didx);
-      }
-      const unsigned mask = __ballot_sync(0xffffffffu, keep);
-      if (keep) {
-        const int32_t pos = out + __popc(mask & below);
-        if (static_cast<uint32_t>(pos) < static_cast<uint64_t>(nnz)) {
-          rrowidx[pos] = j;
-          rvals[pos] = vals[e];
-        }
-      }
-      out += __popc(mask);
+__global__ void k_rest_scatter(int64_t nnz, int32_t m, const int32_t* __restrict__ rowidx,
+                               const VT* __restrict__ vals, const int32_t* __restrict__ didx,
+                               const int32_t* __restrict__ rpos, int32_t* __restrict__ rrowidx,
+                               VT* __restrict__ rvals) {
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < nnz;
+       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int32_t j = rowidx[e];
+    if (!rest_keeps(j, m, didx)) continue;
+    const int32_t pos = rpos[e];
+    if (static_cast<uint64_t>(pos) < static_cast<uint64_t>(nnz)) {
+      rrowidx[pos] = j;
+      rvals[pos] = vals[e];
     }
   }
 }
 }  // namespace
 
-size_t dense_workspace_bytes(int64_t m, int64_t n, int64_t kmax, int64_t nnz) {
-  return dense_layout(nullptr, m, n, kmax, nnz).bytes;
+size_t dense_workspace_bytes(int64_t m, int64_t n, int64_t d, int64_t kmax, int64_t nnz) {
+  return dense_layout(nullptr, m, n, d, kmax, nnz).bytes;
 }
 
 // Phase 1: choose the dense rows (at least tau nonzeros).  Writes didx,
@@ -461,7 +843,7 @@ size_t dense_workspace_bytes(int64_t m, int64_t n, int64_t kmax, int64_t nnz) {
 // reads K (the panel height) and rest_colptr[n] (the rest's nonzeros).
 cudaError_t select_dense_rows(const DenseArgs& a, void* ws, DenseView* out, cudaStream_t s,
                               int* launches) {
-  const DenseLayout L = dense_layout(ws, a.m, a.n, a.kmax, a.nnz);
+  const DenseLayout L = dense_layout(ws, a.m, a.n, a.d, a.kmax, a.nnz);
   int32_t* rows = L.cnt;  // the counts are dead once the flags exist
   const int sms = num_sms();
   auto grid_for = [&](int64_t work) {
@@ -487,16 +869,31 @@ cudaError_t select_dense_rows(const DenseArgs& a, void* ws, DenseView* out, cuda
   out->rest_colptr = L.rcolptr;
   out->rest_rowidx = L.rrowidx;
   out->rest_values = L.rvalues;
-  out->rest_cnt = L.rcnt;
+  out->rest_pos = L.rpos;
+  out->partial = L.partial;
+  out->max_splits = L.max_splits;
   out->scan_tmp = L.scan_tmp;
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  // the rest of A: per-column counts and offsets (rest_colptr[n] = its nnz)
-  const int64_t wblocks = std::max<int64_t>(1, std::min<int64_t>((a.n + 8) / 8, 32LL * sms));
-  k_rest_count<<<static_cast<unsigned>(wblocks), 256, 0, s>>>(a.n, a.m, a.nnz, a.colptr,
-                                                              a.rowidx, L.didx, L.rcnt,
-                                                              a.status);
+  // the rest of A: each kept entry's output position (an exclusive scan of
+  // keep flags over all entries) and the column offsets (rest_colptr[n] =
+  // its nnz)
+  k_rest_flags<<<grid_for(a.nnz + 1), 256, 0, s>>>(a.nnz, a.m, a.rowidx, L.didx, L.rpos);
   ++*launches;
-  return scan_i32(L.rcnt, L.rcolptr, a.n + 1, L.scan_tmp, s, launches);
+  if ((e = scan_i32(L.rpos, L.rpos, a.nnz + 1, L.scan_tmp, s, launches)) != cudaSuccess)
+    return e;
+  k_rest_colptr<<<grid_for(a.n + 1), 256, 0, s>>>(a.n, a.nnz, a.colptr, L.rpos, L.rcolptr,
+                                                  a.status);
+  ++*launches;
+  return cudaGetLastError();
+}
+
+// Long panels (and a workspace holding the split-K copies) take the
+// pipelined kernel and the tiled A3 layout.
+static bool panel_kernel_takes(int64_t Kp, const DenseView& v) {
+  // a slice holds at most kPanMaxSliceSteps steps (its row ids sit in
+  // shared memory) and the workspace at most max_splits partial copies
+  return Kp >= kPanMinKp && v.max_splits >= 1 &&
+         (Kp / kBK + kPanMaxSliceSteps - 1) / kPanMaxSliceSteps <= v.max_splits;
 }
 
 // Phase 2: the panel's BF16 terms for K dense rows (K <= kmax).
@@ -505,16 +902,19 @@ cudaError_t build_dense_panel(const DenseArgs& a, int32_t K, DenseView* v, cudaS
   const int64_t Kp = (static_cast<int64_t>(K) + kBK - 1) / kBK * kBK;
   v->Kp = static_cast<int32_t>(Kp);
   uint16_t* A3 = const_cast<uint16_t*>(v->A3);
-  cudaError_t e = cudaMemsetAsync(A3, 0, static_cast<size_t>(a.n) * 3 * Kp * 2, s);
+  const int tiled = panel_kernel_takes(Kp, *v) ? 1 : 0;
+  cudaError_t e = cudaMemsetAsync(
+      A3, 0, static_cast<size_t>(tiled ? (a.n + 127) / 128 * 128 : a.n) * 3 * Kp * 2, s);
   if (e != cudaSuccess) return e;
-  const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((a.n + 7) / 8, 32LL * num_sms()));
+  const int64_t blocks =
+      std::max<int64_t>(1, std::min<int64_t>((a.nnz + 255) / 256, 32LL * num_sms()));
   if (a.dtype == 0)
     k_dense_scatter<float><<<static_cast<unsigned>(blocks), 256, 0, s>>>(
-        a.n, a.m, static_cast<int32_t>(Kp), a.nnz, a.colptr, a.rowidx,
+        a.n, a.m, static_cast<int32_t>(Kp), a.nnz, tiled, a.colptr, a.rowidx,
         static_cast<const float*>(a.values), v->didx, A3);
   else
     k_dense_scatter<__nv_bfloat16><<<static_cast<unsigned>(blocks), 256, 0, s>>>(
-        a.n, a.m, static_cast<int32_t>(Kp), a.nnz, a.colptr, a.rowidx,
+        a.n, a.m, static_cast<int32_t>(Kp), a.nnz, tiled, a.colptr, a.rowidx,
         static_cast<const __nv_bfloat16*>(a.values), v->didx, A3);
   ++*launches;
   return cudaGetLastError();
@@ -524,16 +924,16 @@ cudaError_t build_dense_panel(const DenseArgs& a, int32_t K, DenseView* v, cudaS
 // its own CSC at the offsets phase 1 computed.
 cudaError_t build_dense_rest(const DenseArgs& a, const DenseView& v, cudaStream_t s,
                              int* launches) {
-  const int64_t wblocks = std::max<int64_t>(1, std::min<int64_t>((a.n + 8) / 8, 32LL * num_sms()));
+  const int64_t blocks =
+      std::max<int64_t>(1, std::min<int64_t>((a.nnz + 255) / 256, 32LL * num_sms()));
   if (a.dtype == 0)
-    k_rest_copy<float><<<static_cast<unsigned>(wblocks), 256, 0, s>>>(
-        a.n, a.m, a.nnz, a.colptr, a.rowidx, static_cast<const float*>(a.values), v.didx,
-        v.rest_colptr, const_cast<int32_t*>(v.rest_rowidx),
-        static_cast<float*>(const_cast<void*>(v.rest_values)));
+    k_rest_scatter<float><<<static_cast<unsigned>(blocks), 256, 0, s>>>(
+        a.nnz, a.m, a.rowidx, static_cast<const float*>(a.values), v.didx, v.rest_pos,
+        const_cast<int32_t*>(v.rest_rowidx), static_cast<float*>(const_cast<void*>(v.rest_values)));
   else
-    k_rest_copy<__nv_bfloat16><<<static_cast<unsigned>(wblocks), 256, 0, s>>>(
-        a.n, a.m, a.nnz, a.colptr, a.rowidx, static_cast<const __nv_bfloat16*>(a.values), v.didx,
-        v.rest_colptr, const_cast<int32_t*>(v.rest_rowidx),
+    k_rest_scatter<__nv_bfloat16><<<static_cast<unsigned>(blocks), 256, 0, s>>>(
+        a.nnz, a.m, a.rowidx, static_cast<const __nv_bfloat16*>(a.values), v.didx, v.rest_pos,
+        const_cast<int32_t*>(v.rest_rowidx),
         static_cast<__nv_bfloat16*>(const_cast<void*>(v.rest_values)));
   ++*launches;
   return cudaGetLastError();
@@ -546,6 +946,42 @@ cudaError_t launch_debug_wait_timeout(int* status, cudaStream_t s) {
 
 cudaError_t launch_tc_gemm(const DenseArgs& a, const DenseView& v, float* Ahat,
                            int accumulate, cudaStream_t s, int* launches) {
+  if (panel_kernel_takes(v.Kp, v)) {
+    {
+      cudaError_t e;
+      // split-K: about two CTAs per SM, at least four steps per slice
+      const int64_t tiles = static_cast<int64_t>((a.d + 127) / 128) * ((a.n + 127) / 128);
+      const int64_t steps = v.Kp / kBK;
+      const int64_t min_splits = (steps + kPanMaxSliceSteps - 1) / kPanMaxSliceSteps;
+      int64_t splits = (2LL * num_sms() + tiles - 1) / tiles;
+      splits = std::min<int64_t>({splits, v.max_splits, std::max<int64_t>(1, steps / 4)});
+      splits = std::max<int64_t>(splits, min_splits);  // <= max_splits (panel_kernel_takes)
+      const int64_t sps = (steps + splits - 1) / splits;
+      splits = (steps + sps - 1) / sps;  // no empty slice
+      const dim3 grid((a.d + 127) / 128, (a.n + 127) / 128, static_cast<unsigned>(splits));
+      if (grid.y > 65535) return cudaErrorInvalidValue;
+      const size_t smem = kPanSmem + static_cast<size_t>(sps) * kBK * sizeof(int32_t);
+      e = cudaFuncSetAttribute(k_tc_panel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               static_cast<int>(smem));
+      if (e != cudaSuccess) return e;
+      const int64_t total = static_cast<int64_t>(a.n) * a.d;
+      float* out = splits > 1 ? v.partial : Ahat;
+      k_tc_panel<<<grid, kPanThreads, smem, s>>>(
+          a.d, a.n, v.Kp, static_cast<int32_t>(sps), v.rows, v.Kdev, v.A3, out,
+          splits > 1 ? total : 0, splits > 1 ? 0 : accumulate, a.k0, a.k1, a.stream_id,
+          a.status);
+      ++*launches;
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+      if (splits > 1) {
+        const int64_t blocks = std::min<int64_t>((total + 255) / 256, 16LL * num_sms());
+        k_panel_reduce<<<static_cast<unsigned>(blocks), 256, 0, s>>>(
+            total, static_cast<int>(splits), v.partial, Ahat, accumulate);
+        ++*launches;
+        e = cudaGetLastError();
+      }
+      return e;
+    }
+  }
   const dim3 grid((a.d + kBM - 1) / kBM, (a.n + kBN - 1) / kBN);
   if (grid.y > 65535) return cudaErrorInvalidValue;
   cudaError_t e = cudaFuncSetAttribute(k_tc_umma, cudaFuncAttributeMaxDynamicSharedMemorySize,

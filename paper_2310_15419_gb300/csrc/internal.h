@@ -149,10 +149,12 @@ struct DenseView {
   const int32_t* rest_colptr;
   const int32_t* rest_rowidx;
   const void* rest_values;
-  int32_t* rest_cnt;  // workspace: per-column counts of the rest
+  const int32_t* rest_pos;  // output position of each kept entry (scan of keep flags)
+  float* partial;           // split-K partial copies of A_hat (pipelined panel kernel)
+  int32_t max_splits;       // how many of them the workspace holds (0: none)
   char* scan_tmp;     // workspace: scan scratch
 };
-size_t dense_workspace_bytes(int64_t m, int64_t n, int64_t kmax, int64_t nnz);
+size_t dense_workspace_bytes(int64_t m, int64_t n, int64_t d, int64_t kmax, int64_t nnz);
 cudaError_t select_dense_rows(const DenseArgs& a, void* ws, DenseView* out, cudaStream_t s,
                               int* launches);
 cudaError_t build_dense_panel(const DenseArgs& a, int32_t K, DenseView* v, cudaStream_t s,

@@ -145,7 +145,7 @@ size_t plan_workspace_bytes(const sketch_s* h, const sketch_csc* A,
                             const sketch_plan& p) {
   size_t b = sparse_workspace_bytes(h, A, p);
   if (p.tc_min_row_nnz > 0)
-    b = align256(b) + dense_workspace_bytes(A->m, A->n, dense_capacity(A, p), A->nnz);
+    b = align256(b) + dense_workspace_bytes(A->m, A->n, h->d, dense_capacity(A, p), A->nnz);
   return b;
 }
 
@@ -385,12 +385,17 @@ static std::vector<sketch_plan> candidates(const sketch_s* h, const sketch_csc* 
       c.push_back(p);
   }
   // +-1 S: densified panels on the tensor cores for rows holding at least
-  // half, or a fifth, of the columns (REGEN for the rest).  With no such row
-  // a candidate costs its base plan plus the row count, so it only wins
-  // when there are dense-enough rows.
+  // half, a fifth, a tenth or a sixteenth of the columns, or 32 nonzeros
+  // (REGEN for the rest): the heavy rows of a skewed matrix (Sec. 3.1's
+  // large-density case).  With no such row a candidate costs its base plan
+  // plus the row count, so it only wins when there are dense-enough rows.
   if (h->dist == SKETCH_PM1 && A->n >= 64) {
     const double avg_col = A->n > 0 ? double(A->nnz) / double(A->n) : 0.0;
-    for (int32_t tau : {static_cast<int32_t>(A->n / 2), static_cast<int32_t>(A->n / 5)}) {
+    std::vector<int32_t> taus;
+    for (int64_t t : {A->n / 2, A->n / 5, A->n / 10, A->n / 16, int64_t(32)})
+      if (t >= 16 && std::find(taus.begin(), taus.end(), static_cast<int32_t>(t)) == taus.end())
+        taus.push_back(static_cast<int32_t>(t));
+    for (int32_t tau : taus) {
       sketch_plan p{};
       p.mode = SKETCH_MODE_REGEN;
       p.q_tiles = qmax;

@@ -453,6 +453,25 @@ def test_tensor_core_panel_only_dense_rows(plan):
         assert np.array_equal(got, ref), d
 
 
+@pytest.mark.parametrize("d", [256, 300, 611])
+def test_tensor_core_long_panel_integer_bit_exact(d):
+    """Panels of at least 512 dense rows take the pipelined kernel (TMA A
+    tiles, 256 rows of S per CTA): 760 dense rows, ragged d and n = 301 (the
+    last column tile is mostly past n), integer values: bit-exact."""
+    A = _dense_rows_matrix(30_400, 301, 40, 0.002, True, seed=37)
+    plan = dict(mode=capi.SKETCH_MODE_REGEN, q_tiles=2, split=2, tc_min_row_nnz=100)
+    got = gpu_sketch(A, d, "pm1", plan=plan)
+    assert np.array_equal(got, oracle_sketch(A, d, "pm1"))
+
+
+def test_tensor_core_long_panel_float_tolerance():
+    A = _dense_rows_matrix(30_400, 300, 40, 0.002, False, seed=38)
+    plan = dict(mode=capi.SKETCH_MODE_TILE, panel_rows=512, row_groups=4,
+                cols_per_warp=16, tc_min_row_nnz=100)
+    got = gpu_sketch(A, 513, "pm1", plan=plan)
+    assert rel_fro(got, oracle_sketch(A, 513, "pm1")) <= TOL
+
+
 def test_tuned_plan_on_dense_rows_is_exact():
     """With tuning on, +-1 S on a matrix with dense rows: whichever plan the
     tuner takes (tensor-core panels are candidates), the sketch is the
