@@ -134,7 +134,19 @@ int sketch_reshape(sketch_t h, int64_t m, int64_t n, int64_t d);
 
 /* Autotuning on (1, default) or off (0).  Off, the planner uses its
  * heuristic plan (deterministic, no timing runs); a server does this so every
- * request of a given shape runs the same kernels alone or in a mix. */
+ * request of a given shape runs the same kernels alone or in a mix.  Either
+ * way the handle's plan cache is cleared.
+ * Tuning (the first apply of a matrix): one device pass measures A's pattern
+ * (nonempty rows, longest row and column, nonzeros in rows of >= 32
+ * entries); a cost model after Sec. 3.1 (S entries drawn: d * nnz for
+ * Alg. 3, d * nonempty rows generate-once; multiply-adds d * nnz) orders the
+ * candidate plans and drops those predicted four times slower than the best
+ * prediction; the rest are timed on A and the fastest is kept, keyed by the
+ * shape and the addresses of A's arrays (a caller that rewrites A in place
+ * with another pattern calls this function to re-plan).  With the
+ * environment variable SKETCH_PLAN_CACHE naming a file, tuned plans are also
+ * appended there keyed by shape and quantised pattern features, and a later
+ * process (or handle) with a matching entry uses it without timing. */
 int sketch_set_autotune(sketch_t h, int32_t enable);
 
 /* Third Philox counter word ("stream", default 0).  Instances of a batch use

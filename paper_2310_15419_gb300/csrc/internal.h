@@ -172,6 +172,13 @@ cudaError_t scan_i32(const int32_t* in, int32_t* out, int64_t len, char* tmp,
 cudaError_t row_counts(int64_t nnz, int32_t m, const int32_t* rowidx, int32_t* cnt,
                        int* status, cudaStream_t s);
 
+// Pattern features of A for the plan tuner (see k_pattern_features): f[0]
+// nonempty rows, f[1] longest row, f[2] nonzeros in rows of >= 32 entries,
+// f[3] longest column.  cnt: m ints of scratch.
+cudaError_t pattern_features(int32_t m, int32_t n, int64_t nnz, const int32_t* colptr,
+                             const int32_t* rowidx, int32_t* cnt, unsigned long long* f,
+                             int* status, cudaStream_t s);
+
 int num_sms();
 
 }  // namespace sk

@@ -409,11 +409,137 @@ static std::vector<sketch_plan> candidates(const sketch_s* h, const sketch_csc* 
   return c;
 }
 
+// The in-memory plan cache key: the shape and the addresses of A's arrays,
+// so two matrices of one shape but different patterns tune separately (a
+// caller that rewrites A in place with another pattern resets the cache
+// with sketch_set_autotune).
 uint64_t shape_key(const sketch_s* h, const sketch_csc* A) {
   uint64_t k = 1469598103934665603ULL;
   auto mix = [&](uint64_t v) { k = (k ^ v) * 1099511628211ULL; };
   mix(A->m); mix(A->n); mix(A->nnz); mix(h->d); mix(h->dist); mix(A->dtype);
+  mix(reinterpret_cast<uintptr_t>(A->colptr));
+  mix(reinterpret_cast<uintptr_t>(A->rowidx));
+  mix(reinterpret_cast<uintptr_t>(A->values));
   return k;
+}
+
+// Pattern features measured on the device when a plan is tuned.
+struct Features {
+  int64_t nonempty = 0, max_row = 0, heavy_nnz = 0, max_col = 0;
+};
+
+static bool measure_features(sketch_t h, const sketch_csc* A, cudaStream_t s, Features* f) {
+  int32_t* cnt = nullptr;
+  unsigned long long* dev = nullptr;
+  if (cudaMalloc(&cnt, sizeof(int32_t) * std::max<int64_t>(1, A->m)) != cudaSuccess ||
+      cudaMalloc(&dev, 4 * sizeof(unsigned long long)) != cudaSuccess) {
+    cudaFree(cnt);
+    cudaGetLastError();
+    return false;
+  }
+  unsigned long long host[4] = {};
+  cudaError_t e = pattern_features(static_cast<int32_t>(A->m), static_cast<int32_t>(A->n),
+                                   A->nnz, A->colptr, A->rowidx, cnt, dev,
+                                   reinterpret_cast<int*>(h->d_small), s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(host, dev, sizeof(host), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(cnt);
+  cudaFree(dev);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  h->launches += 3;
+  f->nonempty = static_cast<int64_t>(host[0]);
+  f->max_row = static_cast<int64_t>(host[1]);
+  f->heavy_nnz = static_cast<int64_t>(host[2]);
+  f->max_col = static_cast<int64_t>(host[3]);
+  return true;
+}
+
+// The persisted plan cache key: shape plus quantised pattern features
+// (nonempty-row share and heavy-row share in 1/32 steps, longest row and
+// column in powers of two), valid across processes.
+static uint64_t feature_key(const sketch_s* h, const sketch_csc* A, const Features& f) {
+  uint64_t k = 0x9E3779B97F4A7C15ULL;
+  auto mix = [&](uint64_t v) { k = (k ^ v) * 1099511628211ULL; };
+  auto lg = [](int64_t v) { int b = 0; while (v > 1) { v >>= 1; ++b; } return b; };
+  mix(A->m); mix(A->n); mix(A->nnz); mix(h->d); mix(h->dist); mix(A->dtype);
+  mix(static_cast<uint64_t>(32 * f.nonempty / std::max<int64_t>(1, A->m)));
+  mix(static_cast<uint64_t>(32 * f.heavy_nnz / std::max<int64_t>(1, A->nnz)));
+  mix(static_cast<uint64_t>(lg(f.max_row)));
+  mix(static_cast<uint64_t>(lg(f.max_col)));
+  mix(2);  // version of the plan set
+  return k;
+}
+
+// Persisted plans (the file named by SKETCH_PLAN_CACHE, one plan per line:
+// key in hex, then the nine plan fields), loaded once per process.
+static std::mutex g_cache_mu;
+static std::map<uint64_t, sketch_plan> g_cache;
+static bool g_cache_loaded = false;
+
+static const char* cache_path() {
+  const char* p = std::getenv("SKETCH_PLAN_CACHE");
+  return (p && p[0]) ? p : nullptr;
+}
+
+static bool cache_lookup(uint64_t key, sketch_plan* out) {
+  const char* path = cache_path();
+  if (!path) return false;
+  std::lock_guard<std::mutex> lock(g_cache_mu);
+  if (!g_cache_loaded) {
+    g_cache_loaded = true;
+    if (FILE* f = std::fopen(path, "r")) {
+      unsigned long long k = 0;
+      sketch_plan p{};
+      while (std::fscanf(f, "%llx %d %d %d %d %d %d %d %d %d", &k, &p.mode, &p.q_tiles, &p.split,
+                         &p.n_block, &p.row_groups, &p.panel_rows, &p.cols_per_warp,
+                         &p.tc_min_row_nnz, &p.tile_acc) == 10)
+        g_cache[k] = p;
+      std::fclose(f);
+    }
+  }
+  auto it = g_cache.find(key);
+  if (it == g_cache.end()) return false;
+  *out = it->second;
+  return true;
+}
+
+static void cache_store(uint64_t key, const sketch_plan& p) {
+  const char* path = cache_path();
+  if (!path) return;
+  std::lock_guard<std::mutex> lock(g_cache_mu);
+  g_cache[key] = p;
+  if (FILE* f = std::fopen(path, "a")) {
+    std::fprintf(f, "%llx %d %d %d %d %d %d %d %d %d\n", static_cast<unsigned long long>(key),
+                 p.mode, p.q_tiles, p.split, p.n_block, p.row_groups, p.panel_rows,
+                 p.cols_per_warp, p.tc_min_row_nnz, p.tile_acc);
+    std::fclose(f);
+  }
+}
+
+// A cost model in the spirit of Sec. 3.1, used to order and prune the
+// tuner's candidates (every kept candidate is still timed): generation at
+// the generator rate of the distribution for the S entries a plan draws --
+// d * nnz for Alg. 3 (REGEN), d * nonempty rows for the generate-once TILE
+// -- plus d * nnz multiply-adds at the rate each kernel family reaches.
+static double model_seconds(const sketch_s* h, const sketch_csc* A, const Features& f,
+                            const sketch_plan& p) {
+  const double gen = h->dist == SKETCH_PM1 ? 5.5e13 : h->dist == SKETCH_UNIFORM ? 1.5e12 : 6.2e11;
+  const double d = static_cast<double>(h->d);
+  const double nnz = static_cast<double>(A->nnz);
+  double dense_share = 0.0;
+  if (p.tc_min_row_nnz > 0)
+    dense_share = f.max_row >= p.tc_min_row_nnz
+                      ? std::min(1.0, static_cast<double>(f.heavy_nnz) / std::max(1.0, nnz))
+                      : 0.0;
+  const double sparse = nnz * (1.0 - dense_share);
+  if (p.mode == SKETCH_MODE_TILE)
+    return d * static_cast<double>(f.nonempty) / gen + d * sparse / 3.5e12;
+  // REGEN: each nonzero regenerates its S column (+-1: 128 signs a block)
+  const double regen = h->dist == SKETCH_PM1 ? 9.6e12 : gen;
+  return d * sparse / regen + (dense_share > 0.0 ? d * nnz * dense_share / 4e13 : 0.0);
 }
 
 int choose_plan(sketch_t h, const sketch_csc* A, float* Ahat, cudaStream_t s,
@@ -440,10 +566,34 @@ int choose_plan(sketch_t h, const sketch_csc* A, float* Ahat, cudaStream_t s,
     h->plans[key] = *out;
     return SKETCH_OK;
   }
-  // Empirical tuning: run every candidate once on the real input (warm-up:
-  // workspace, caches), then time it twice and keep its faster run; the
-  // fastest candidate wins.
+  // Pattern features (one device pass), then the persisted cache.
+  Features feat{};
+  const bool have_feat = measure_features(h, A, s, &feat);
+  const uint64_t fkey = have_feat ? feature_key(h, A, feat) : 0;
+  sketch_plan cached{};
+  if (have_feat && cache_lookup(fkey, &cached) && check_plan(h, cached) == SKETCH_OK) {
+    h->plans[key] = cached;
+    *out = cached;
+    return SKETCH_OK;
+  }
+  // Empirical tuning, seeded by the cost model: candidates whose predicted
+  // time is more than four times the best prediction are dropped, panel
+  // candidates whose threshold no row reaches are dropped, and the rest run
+  // once on the real input (warm-up: workspace, caches), then twice timed,
+  // keeping the faster run; the fastest candidate wins.
   auto cands = candidates(h, A);
+  if (have_feat) {
+    std::vector<std::pair<double, sketch_plan>> ranked;
+    for (const auto& p : cands) {
+      if (p.tc_min_row_nnz > 0 && feat.max_row < p.tc_min_row_nnz) continue;
+      ranked.emplace_back(model_seconds(h, A, feat, p), p);
+    }
+    std::stable_sort(ranked.begin(), ranked.end(),
+                     [](const auto& a, const auto& b) { return a.first < b.first; });
+    cands.clear();
+    for (const auto& r : ranked)
+      if (r.first <= 4.0 * ranked.front().first) cands.push_back(r.second);
+  }
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
@@ -489,6 +639,7 @@ int choose_plan(sketch_t h, const sketch_csc* A, float* Ahat, cudaStream_t s,
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   h->plans[key] = best_p;
+  if (have_feat && best < 1e29f) cache_store(fkey, best_p);
   *out = best_p;
   return SKETCH_OK;
 }
@@ -564,6 +715,7 @@ int sketch_reshape(sketch_t h, int64_t m, int64_t n, int64_t d) {
 int sketch_set_autotune(sketch_t h, int32_t enable) {
   if (!h) return SKETCH_ERR_ARG;
   h->autotune = enable != 0;
+  h->plans.clear();  // the next apply plans (and, when on, tunes) afresh
   return SKETCH_OK;
 }
 

@@ -1505,6 +1505,58 @@ cudaError_t launch_bench_fma(int64_t threads, int64_t iters, float* sink, cudaSt
   return cudaGetLastError();
 }
 
+// Pattern features of A for the plan tuner, from row counts cnt[0..m):
+// f[0] = nonempty rows, f[1] = the longest row, f[2] = nonzeros in rows of
+// at least 32 entries, f[3] = the longest column (from colptr, clamped).
+__global__ void k_pattern_features(int32_t m, int32_t n, int64_t nnz,
+                                   const int32_t* __restrict__ cnt,
+                                   const int32_t* __restrict__ colptr,
+                                   unsigned long long* __restrict__ f) {
+  unsigned long long ne = 0, heavy = 0, mx = 0, mc = 0;
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  for (int64_t j = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; j < m;
+       j += stride) {
+    const unsigned long long c = static_cast<unsigned long long>(max(cnt[j], 0));
+    ne += c > 0;
+    heavy += c >= 32 ? c : 0;
+    mx = c > mx ? c : mx;
+  }
+  for (int64_t k = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; k < n;
+       k += stride) {
+    const int2 r = column_range(colptr, k, nnz, nullptr);
+    const unsigned long long c = static_cast<unsigned long long>(r.y - r.x);
+    mc = c > mc ? c : mc;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    ne += __shfl_xor_sync(0xffffffffu, ne, o);
+    heavy += __shfl_xor_sync(0xffffffffu, heavy, o);
+    const unsigned long long a = __shfl_xor_sync(0xffffffffu, mx, o);
+    const unsigned long long b = __shfl_xor_sync(0xffffffffu, mc, o);
+    mx = a > mx ? a : mx;
+    mc = b > mc ? b : mc;
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(&f[0], ne);
+    atomicMax(&f[1], mx);
+    atomicAdd(&f[2], heavy);
+    atomicMax(&f[3], mc);
+  }
+}
+
+cudaError_t pattern_features(int32_t m, int32_t n, int64_t nnz, const int32_t* colptr,
+                             const int32_t* rowidx, int32_t* cnt, unsigned long long* f,
+                             int* status, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(cnt, 0, static_cast<size_t>(m) * sizeof(int32_t), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(f, 0, 4 * sizeof(unsigned long long), s);
+  if (e == cudaSuccess) e = row_counts(nnz, m, rowidx, cnt, status, s);
+  if (e != cudaSuccess) return e;
+  const int64_t work = std::max<int64_t>(m, n);
+  const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((work + 255) / 256, 8LL * num_sms()));
+  k_pattern_features<<<static_cast<unsigned>(blocks), 256, 0, s>>>(m, n, nnz, cnt, colptr, f);
+  return cudaGetLastError();
+}
+
 int64_t scan_bytes_for(int64_t len) { return scan_levels_bytes(len); }
 
 cudaError_t scan_i32(const int32_t* in, int32_t* out, int64_t len, char* tmp,

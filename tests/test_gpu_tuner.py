@@ -84,3 +84,31 @@ def test_tuned_plan_within_10_percent_of_best_candidate(kind):
 def _cols(A, cols):
     sub = A.columns(cols)
     return sub.colptr, sub.rowidx, sub.values
+
+
+def test_persisted_plan_cache_skips_timing(tmp_path, monkeypatch):
+    """With SKETCH_PLAN_CACHE set, the first handle tunes and appends its
+    plan (keyed by shape and quantised pattern features); a second handle on
+    a copy of the same matrix (other addresses, same pattern) reads it back:
+    same plan, same sketch, and only the feature pass plus the sketch itself
+    launched (no candidate timing runs)."""
+    path = tmp_path / "plans.txt"
+    monkeypatch.setenv("SKETCH_PLAN_CACHE", str(path))
+    A = inputs.float_uniform(150_000, 300, 0.004, seed=17)
+    d = 600
+    first = capi.Sketch(A.m, A.n, d, "uniform", seed=3)
+    out1 = first.apply(capi.DeviceCSC(A))
+    torch.cuda.synchronize()
+    plan1 = first.get_plan(capi.DeviceCSC(A))
+    tuning_launches = first.launch_count()
+    first.close()
+    lines = path.read_text().split("\n")
+    assert any(line.strip() for line in lines)
+    second = capi.Sketch(A.m, A.n, d, "uniform", seed=3)
+    dA2 = capi.DeviceCSC(A)
+    out2 = second.apply(dA2)
+    torch.cuda.synchronize()
+    assert second.get_plan(dA2) == plan1
+    assert second.launch_count() < tuning_launches
+    assert torch.equal(out1, out2)
+    second.close()
