@@ -307,15 +307,32 @@ def bench_lsq(torch, capi, inputs, reps=10):
     dA = capi.DeviceCSC(A)
     bb = torch.from_numpy(b).cuda()
     out = {"workload": "lsq_mixed m=1,000,000 n=500 density 0.2% BF16, d=2n, +-1 S"}
+    fp8_plan = dict(mode=capi.SKETCH_MODE_REGEN, q_tiles=4, split=1, tc_min_row_nnz=1,
+                    tc_fp8=1)
     for method, nrep in (("sap_qr", reps), ("sap_svd", max(2, reps // 3)),
-                         ("lsqr_d", max(2, reps // 3))):
+                         ("lsqr_d", max(2, reps // 3)), ("sap_qr_fp8_panels", max(2, reps // 3))):
         sk = capi.Sketch(A.m, A.n, 2 * A.n, "pm1", seed=1)
-        x, info = sk.lsq_solve(dA, bb, maxit=5000, method=method)   # tunes the sketch plan
+        sketch_err = None
+        if method == "sap_qr_fp8_panels":
+            # config 4's sketch on FP8 tensor-core panels (every nonempty row
+            # in the panel: this matrix has no dense rows); its error against
+            # the exact FP32 sketch (itself within 1e-6 of FP64)
+            exact = capi.Sketch(A.m, A.n, 2 * A.n, "pm1", seed=1)
+            ref = exact.apply(dA)
+            exact.close()
+            sk.set_plan(**fp8_plan)
+            got = sk.apply(dA)
+            torch.cuda.synchronize()
+            sketch_err = float(torch.linalg.norm(got.double() - ref.double()) /
+                               torch.linalg.norm(ref.double()))
+            del got, ref
+        run = "sap_qr" if method == "sap_qr_fp8_panels" else method
+        x, info = sk.lsq_solve(dA, bb, maxit=5000, method=run)   # tunes the sketch plan
         torch.cuda.synchronize()
         lat, infos = [], []
         for _ in range(nrep):
             t0 = time.perf_counter()
-            x, info = sk.lsq_solve(dA, bb, maxit=5000, method=method)
+            x, info = sk.lsq_solve(dA, bb, maxit=5000, method=run)
             torch.cuda.synchronize()
             lat.append(1e3 * (time.perf_counter() - t0))
             infos.append(info)
@@ -329,6 +346,8 @@ def bench_lsq(torch, capi, inputs, reps=10):
              "ms_factor": round(infos[-1]["ms_qr"], 3),
              "ms_lsqr": round(infos[-1]["ms_lsqr"], 3), "reps": nrep,
              "launches_total": launches}
+        if sketch_err is not None:
+            r["sketch_rel_error_vs_fp32"] = sketch_err
         if method == "sap_qr":
             out.update(r)          # the headline keys stay where they were
         else:

@@ -114,6 +114,16 @@ typedef struct {
                          /* plan reads the panel height back to the host    */
                          /* once per call (not capturable in a graph).      */
   int32_t tile_acc;      /* TILE: 0 = register, 1 = tensor-memory sums     */
+  int32_t tc_fp8;        /* tensor-core panels in FP8 (1) instead of BF16   */
+                         /* (0): +-1 S in E4M3 (exact) times A split into  */
+                         /* two E4M3 terms after a power-of-two scale per  */
+                         /* column (undone exactly on output), FP32        */
+                         /* accumulate; about 2^-8 relative error per      */
+                         /* value of A (integer values up to 16 in         */
+                         /* magnitude stay exact), so it suits the         */
+                         /* preconditioner sketch of sketch_lsq_solve      */
+                         /* (Sec. 5.3) rather than the 1e-6 sketch.  The   */
+                         /* tuner never picks it; a forced plan does.      */
 } sketch_plan;
 
 /* Create a sketch handle for A (m x n) and S (d x m) with the distribution

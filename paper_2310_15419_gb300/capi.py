@@ -56,7 +56,7 @@ class sketch_plan(ctypes.Structure):
                 ("split", ctypes.c_int32), ("n_block", ctypes.c_int32),
                 ("row_groups", ctypes.c_int32), ("panel_rows", ctypes.c_int32),
                 ("cols_per_warp", ctypes.c_int32), ("tc_min_row_nnz", ctypes.c_int32),
-                ("tile_acc", ctypes.c_int32)]
+                ("tile_acc", ctypes.c_int32), ("tc_fp8", ctypes.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -242,9 +242,9 @@ class Sketch:
 
     def set_plan(self, mode=SKETCH_MODE_AUTO, q_tiles=0, split=0, n_block=0,
                  row_groups=0, panel_rows=0, cols_per_warp=0, tc_min_row_nnz=0,
-                 tile_acc=0):
+                 tile_acc=0, tc_fp8=0):
         p = sketch_plan(mode, q_tiles, split, n_block, row_groups, panel_rows,
-                        cols_per_warp, tc_min_row_nnz, tile_acc)
+                        cols_per_warp, tc_min_row_nnz, tile_acc, tc_fp8)
         _check(load().sketch_set_plan(self.h, ctypes.byref(p)), self.h)
 
     def get_plan(self, A: DeviceCSC, stream=None) -> dict:

@@ -17,6 +17,7 @@
 // panel's rows), so A_hat = S A_rest + S_D A_D with the MMA adding into A_hat
 // afterwards.
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -87,6 +88,70 @@ __device__ __forceinline__ int64_t a3_offset(int tiled, int32_t k, int32_t q, in
   const int64_t steps = Kp >> 5;
   const int64_t tile_step = (static_cast<int64_t>(k >> 7) * steps + (q >> 5)) * 3 + t;
   return ((tile_step * 4 + ((q >> 3) & 3)) * 128 + (k & 127)) * 8 + (q & 7);
+}
+
+// FP8 panels: colinv[k] = 2^(x - 8) for the largest |A(j, k)| over the
+// panel's rows, f 2^x with f in [0.5, 1) (so A(j, k) / colinv[k] <= 256 <
+// 448, the E4M3 maximum); 1 for a column without panel entries.  cmax holds
+// the bits of the largest magnitude (non-negative floats order as integers).
+template <typename VT>
+__global__ void k_panel_colmax(int32_t n, int32_t m, int64_t nnz,
+                               const int32_t* __restrict__ colptr,
+                               const int32_t* __restrict__ rowidx, const VT* __restrict__ vals,
+                               const int32_t* __restrict__ didx, uint32_t* __restrict__ cmax) {
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < nnz;
+       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int32_t j = rowidx[e];
+    if (static_cast<uint32_t>(j) >= static_cast<uint32_t>(m) || didx[j] < 0) continue;
+    const int32_t k = column_of(colptr, n, e);
+    if (k < 0) continue;
+    atomicMax(&cmax[k], __float_as_uint(fabsf(to_f32(vals[e]))));
+  }
+}
+
+__global__ void k_panel_colscale(int32_t n, const uint32_t* __restrict__ cmax,
+                                 float* __restrict__ colinv) {
+  for (int64_t k = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; k < n;
+       k += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const float mx = __uint_as_float(cmax[k]);
+    int x = 0;
+    frexpf(mx, &x);
+    colinv[k] = mx > 0.0f ? ldexpf(1.0f, x - 8) : 1.0f;
+  }
+}
+
+// The FP8 panel in the pipelined kernel's tiled layout: for tile k >> 7 and
+// step q >> 5 an 8 KB block of two terms x two 16-byte k-chunks x 128
+// columns; term t of A(j, k) / colinv[k] (E4M3, round to nearest): t = 0 the
+// value, t = 1 its remainder.
+__device__ __forceinline__ int64_t a3_offset_fp8(int32_t k, int32_t q, int t, int64_t Kp) {
+  const int64_t steps = Kp >> 5;
+  const int64_t tile_step = (static_cast<int64_t>(k >> 7) * steps + (q >> 5)) * 2 + t;
+  return ((tile_step * 2 + ((q >> 4) & 1)) * 128 + (k & 127)) * 16 + (q & 15);
+}
+
+template <typename VT>
+__global__ void k_dense_scatter_fp8(int32_t n, int32_t m, int32_t Kp, int64_t nnz,
+                                    const int32_t* __restrict__ colptr,
+                                    const int32_t* __restrict__ rowidx,
+                                    const VT* __restrict__ vals,
+                                    const int32_t* __restrict__ didx,
+                                    const float* __restrict__ colinv,
+                                    uint8_t* __restrict__ A8) {
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < nnz;
+       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int32_t j = rowidx[e];
+    if (static_cast<uint32_t>(j) >= static_cast<uint32_t>(m)) continue;
+    const int32_t q = didx[j];
+    if (q < 0) continue;
+    const int32_t k = column_of(colptr, n, e);
+    if (k < 0) continue;
+    const float a = to_f32(vals[e]) / colinv[k];  // exact: a power of two
+    const __nv_fp8_e4m3 t1(a);
+    const __nv_fp8_e4m3 t2(a - static_cast<float>(t1));
+    A8[a3_offset_fp8(k, q, 0, Kp)] = t1.__x;
+    A8[a3_offset_fp8(k, q, 1, Kp)] = t2.__x;
+  }
 }
 
 template <typename VT>
@@ -490,12 +555,24 @@ __device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&v)[32
                : "memory");
 }
 
+// FP8 = true: E4M3 operands (kind::f8f6f4, K = 32 per MMA): the S tile is
+// 128 rows x 32 bytes, the A panel two terms of 4 KB per step (one 8 KB bulk
+// copy), two MMAs per step, and the output is multiplied by the column scale
+// colinv.  Same layout rules: 16-byte core-matrix rows, k-chunks 2048 B apart.
+// Instruction descriptor of kind::f8f6f4: F32 accumulator, E4M3 A and B
+// (format code 0), both K-major, N = 128, M = 128.
+constexpr uint32_t kUmmaIdescFp8 = (1u << 4) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
+
+template <bool FP8>
 __global__ void __launch_bounds__(kPanThreads, 1)
     k_tc_panel(int32_t d, int32_t n, int32_t Kp, int32_t steps_per_split,
                const int32_t* __restrict__ rows, const int32_t* __restrict__ Kdev,
-               const uint16_t* __restrict__ A3, float* __restrict__ out,
-               int64_t split_stride, int accumulate, uint32_t k0, uint32_t k1,
-               uint32_t stream_id, int* status) {
+               const uint8_t* __restrict__ A3, const float* __restrict__ colinv,
+               float* __restrict__ out, int64_t split_stride, int accumulate, uint32_t k0,
+               uint32_t k1, uint32_t stream_id, int* status) {
+  constexpr int kTerms = FP8 ? 2 : 3;
+  constexpr int kTermBytes = FP8 ? kPanTileBytes / 2 : kPanTileBytes;
+  constexpr uint32_t kTx = kTerms * kTermBytes;
   extern __shared__ uint8_t sm_raw[];
   __shared__ __align__(8) uint64_t full[kPanStages], empty[kPanStages], acc_full[2],
       acc_empty[2], drain_bar;
@@ -510,7 +587,9 @@ __global__ void __launch_bounds__(kPanThreads, 1)
   const int npairs = (nsteps + 1) / 2;
   float* dst = out + blockIdx.z * split_stride;
   auto tileS = [&](int stg) { return base + stg * kPanStageBytes; };
-  auto tileB = [&](int stg, int t) { return base + stg * kPanStageBytes + (1 + t) * kPanTileBytes; };
+  auto tileB = [&](int stg, int t) {
+    return base + stg * kPanStageBytes + kPanTileBytes + t * kTermBytes;
+  };
   if (tid == 0) {
     failed = 0;
     for (int q = 0; q < kPanStages; ++q) {
@@ -551,11 +630,10 @@ __global__ void __launch_bounds__(kPanThreads, 1)
           break;
         }
         if (failed) break;
-        mbar_arrive_tx(smem_u32(&full[sg]), kPanTxBytes);
-        // the step's three B tiles are one contiguous 24 KB block of A3
-        const uint16_t* src = A3 + (static_cast<int64_t>(blockIdx.y) * (Kp / kBK) + st) * 3 *
-                                       (kPanTileBytes / 2);
-        bulk_load(smem_u32(tileB(sg, 0)), src, kPanTxBytes, smem_u32(&full[sg]));
+        mbar_arrive_tx(smem_u32(&full[sg]), kTx);
+        // the step's B tiles (all terms) are one contiguous block of A3
+        const uint8_t* src = A3 + (static_cast<int64_t>(blockIdx.y) * (Kp / kBK) + st) * kTx;
+        bulk_load(smem_u32(tileB(sg, 0)), src, kTx, smem_u32(&full[sg]));
       }
     }
   } else if (warp == 1) {
@@ -573,20 +651,35 @@ __global__ void __launch_bounds__(kPanThreads, 1)
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if constexpr (FP8) {
 #pragma unroll
-        for (int t = 0; t < 3; ++t)
-#pragma unroll
-          for (int kh = 0; kh < 2; ++kh) {
-            const uint64_t ad = pan_desc(smem_u32(tileS(sg)) + kh * 2 * kPanLbo);
-            const uint64_t bd = pan_desc(smem_u32(tileB(sg, t)) + kh * 2 * kPanLbo);
-            const uint32_t acc = ((i & 1) || t > 0 || kh > 0) ? 1u : 0u;
+          for (int t = 0; t < 2; ++t) {  // K = 32: the whole step
+            const uint64_t ad = pan_desc(smem_u32(tileS(sg)));
+            const uint64_t bd = pan_desc(smem_u32(tileB(sg, t)));
+            const uint32_t acc = ((i & 1) || t > 0) ? 1u : 0u;
             asm volatile(
                 "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+                "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(
                     tmem + static_cast<uint32_t>(128 * b)),
-                "l"(ad), "l"(bd), "r"(kUmmaIdesc), "r"(acc)
+                "l"(ad), "l"(bd), "r"(kUmmaIdescFp8), "r"(acc)
                 : "memory");
           }
+        } else {
+#pragma unroll
+          for (int t = 0; t < 3; ++t)
+#pragma unroll
+            for (int kh = 0; kh < 2; ++kh) {
+              const uint64_t ad = pan_desc(smem_u32(tileS(sg)) + kh * 2 * kPanLbo);
+              const uint64_t bd = pan_desc(smem_u32(tileB(sg, t)) + kh * 2 * kPanLbo);
+              const uint32_t acc = ((i & 1) || t > 0 || kh > 0) ? 1u : 0u;
+              asm volatile(
+                  "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                  "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+                      tmem + static_cast<uint32_t>(128 * b)),
+                  "l"(ad), "l"(bd), "r"(kUmmaIdesc), "r"(acc)
+                  : "memory");
+            }
+        }
         asm volatile(
             "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                 smem_u32(&empty[sg]))
@@ -632,15 +725,29 @@ __global__ void __launch_bounds__(kPanThreads, 1)
         v = (lane & sh) ? ((v & ~m) | ((o >> sh) & m)) : ((v & m) | ((o & m) << sh));
       }
       uint8_t* dstS = tileS(sg) + r * 16;
+      if constexpr (FP8) {
 #pragma unroll
-      for (int c = 0; c < 4; ++c) {  // k-chunk c: dense rows 8c .. 8c + 7
-        uint32_t wv[4];
+        for (int c = 0; c < 2; ++c) {  // k-chunk c: dense rows 16c .. 16c + 15
+          uint32_t wv[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int ka = 8 * c + 2 * u;
-          wv[u] = pm1_pair((v >> ka) & 1u, (v >> (ka + 1)) & 1u);
+          for (int u = 0; u < 4; ++u) {  // E4M3 +1 = 0x38, -1 = 0xB8
+            const uint32_t b4 = v >> (16 * c + 4 * u);
+            wv[u] = 0x38383838u | ((b4 & 1u) << 7) | ((b4 & 2u) << 14) | ((b4 & 4u) << 21) |
+                    ((b4 & 8u) << 28);
+          }
+          *reinterpret_cast<uint4*>(dstS + c * kPanLbo) = make_uint4(wv[0], wv[1], wv[2], wv[3]);
         }
-        *reinterpret_cast<uint4*>(dstS + c * kPanLbo) = make_uint4(wv[0], wv[1], wv[2], wv[3]);
+      } else {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {  // k-chunk c: dense rows 8c .. 8c + 7
+          uint32_t wv[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int ka = 8 * c + 2 * u;
+            wv[u] = pm1_pair((v >> ka) & 1u, (v >> (ka + 1)) & 1u);
+          }
+          *reinterpret_cast<uint4*>(dstS + c * kPanLbo) = make_uint4(wv[0], wv[1], wv[2], wv[3]);
+        }
       }
       // generic-proxy writes -> visible to the tensor core, then one arrival
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -693,7 +800,8 @@ __global__ void __launch_bounds__(kPanThreads, 1)
             const int c = n0 + 32 * cc + jj;
             if (c < n) {
               float* o = dst + static_cast<int64_t>(c) * d + r;
-              const float x = __uint_as_float(v[jj]);
+              float x = __uint_as_float(v[jj]);
+              if constexpr (FP8) x *= colinv[c];  // exact: a power of two
               *o = accumulate ? *o + x : x;
             }
           }
@@ -742,17 +850,19 @@ struct DenseLayout {
   char* scan_tmp;
   int32_t *rpos, *rcolptr, *rrowidx;  // the rest of A (CSC); rpos: nnz + 1 positions
   float* partial;                      // split-K partial copies of A_hat (panel kernel)
+  float* colinv;                       // FP8: the per-column scale undone on output
+  uint32_t* cmax;                      // FP8: largest panel magnitude per column (bits)
   int32_t max_splits;
   void* rvalues;
   size_t bytes;
 };
-// Split-K copies of A_hat the pipelined panel kernel may use: up to four,
-// and at most 1 GiB of them (none when the panel cannot reach its length).
+// Split-K copies of A_hat the pipelined panel kernel may use: up to 64, and
+// at most 1 GiB of them (none when the panel cannot reach a useful length).
 int64_t panel_max_splits(int64_t n, int64_t d, int64_t kmax) {
   const int64_t Kp = (kmax + kBK - 1) / kBK * kBK;
-  if (Kp < kPanMinKp) return 0;
+  if (Kp < kBK) return 0;
   const int64_t one = n * d * static_cast<int64_t>(sizeof(float));
-  return std::min<int64_t>(4, (int64_t(1) << 30) / std::max<int64_t>(one, 1));
+  return std::min<int64_t>(64, (int64_t(1) << 30) / std::max<int64_t>(one, 1));
 }
 
 DenseLayout dense_layout(void* ws, int64_t m, int64_t n, int64_t d, int64_t kmax,
@@ -776,6 +886,8 @@ DenseLayout dense_layout(void* ws, int64_t m, int64_t n, int64_t d, int64_t kmax
   L.rcolptr = reinterpret_cast<int32_t*>(take((n + 1) * sizeof(int32_t)));
   L.rrowidx = reinterpret_cast<int32_t*>(take(std::max<int64_t>(1, nnz) * sizeof(int32_t)));
   L.rvalues = take(std::max<int64_t>(1, nnz) * sizeof(float));
+  L.colinv = reinterpret_cast<float*>(take(std::max<int64_t>(1, n) * sizeof(float)));
+  L.cmax = reinterpret_cast<uint32_t*>(take(std::max<int64_t>(1, n) * sizeof(uint32_t)));
   L.max_splits = static_cast<int32_t>(panel_max_splits(n, d, kmax));
   L.partial = reinterpret_cast<float*>(
       take(static_cast<size_t>(L.max_splits > 1 ? L.max_splits : 0) * n * d * sizeof(float)));
@@ -871,6 +983,8 @@ cudaError_t select_dense_rows(const DenseArgs& a, void* ws, DenseView* out, cuda
   out->rest_values = L.rvalues;
   out->rest_pos = L.rpos;
   out->partial = L.partial;
+  out->colscale = L.colinv;
+  out->cmax = L.cmax;
   out->max_splits = L.max_splits;
   out->scan_tmp = L.scan_tmp;
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -889,10 +1003,11 @@ cudaError_t select_dense_rows(const DenseArgs& a, void* ws, DenseView* out, cuda
 
 // Long panels (and a workspace holding the split-K copies) take the
 // pipelined kernel and the tiled A3 layout.
-static bool panel_kernel_takes(int64_t Kp, const DenseView& v) {
+static bool panel_kernel_takes(int64_t Kp, const DenseView& v, bool fp8) {
   // a slice holds at most kPanMaxSliceSteps steps (its row ids sit in
-  // shared memory) and the workspace at most max_splits partial copies
-  return Kp >= kPanMinKp && v.max_splits >= 1 &&
+  // shared memory) and the workspace at most max_splits partial copies;
+  // FP8 panels always take this kernel, BF16 ones from kPanMinKp rows
+  return (fp8 || Kp >= kPanMinKp) && v.max_splits >= 1 &&
          (Kp / kBK + kPanMaxSliceSteps - 1) / kPanMaxSliceSteps <= v.max_splits;
 }
 
@@ -902,7 +1017,41 @@ cudaError_t build_dense_panel(const DenseArgs& a, int32_t K, DenseView* v, cudaS
   const int64_t Kp = (static_cast<int64_t>(K) + kBK - 1) / kBK * kBK;
   v->Kp = static_cast<int32_t>(Kp);
   uint16_t* A3 = const_cast<uint16_t*>(v->A3);
-  const int tiled = panel_kernel_takes(Kp, *v) ? 1 : 0;
+  if (a.fp8) {
+    // E4M3 panel: per-column scales from the panel's largest magnitudes,
+    // then the two terms in the tiled layout (n padded to 128, 2 bytes per
+    // entry)
+    if (!panel_kernel_takes(Kp, *v, true)) return cudaErrorNotSupported;
+    const unsigned gb = static_cast<unsigned>(
+        std::max<int64_t>(1, std::min<int64_t>((a.nnz + 255) / 256, 32LL * num_sms())));
+    const unsigned gn = static_cast<unsigned>(
+        std::max<int64_t>(1, std::min<int64_t>((a.n + 255) / 256, 32LL * num_sms())));
+    cudaError_t e = cudaMemsetAsync(v->cmax, 0, static_cast<size_t>(a.n) * sizeof(uint32_t), s);
+    if (e == cudaSuccess)
+      e = cudaMemsetAsync(A3, 0, static_cast<size_t>((a.n + 127) / 128 * 128) * Kp * 2, s);
+    if (e != cudaSuccess) return e;
+    if (a.dtype == 0)
+      k_panel_colmax<float><<<gb, 256, 0, s>>>(a.n, a.m, a.nnz, a.colptr, a.rowidx,
+                                               static_cast<const float*>(a.values), v->didx,
+                                               v->cmax);
+    else
+      k_panel_colmax<__nv_bfloat16><<<gb, 256, 0, s>>>(
+          a.n, a.m, a.nnz, a.colptr, a.rowidx, static_cast<const __nv_bfloat16*>(a.values),
+          v->didx, v->cmax);
+    k_panel_colscale<<<gn, 256, 0, s>>>(a.n, v->cmax, v->colscale);
+    uint8_t* A8 = reinterpret_cast<uint8_t*>(A3);
+    if (a.dtype == 0)
+      k_dense_scatter_fp8<float><<<gb, 256, 0, s>>>(
+          a.n, a.m, static_cast<int32_t>(Kp), a.nnz, a.colptr, a.rowidx,
+          static_cast<const float*>(a.values), v->didx, v->colscale, A8);
+    else
+      k_dense_scatter_fp8<__nv_bfloat16><<<gb, 256, 0, s>>>(
+          a.n, a.m, static_cast<int32_t>(Kp), a.nnz, a.colptr, a.rowidx,
+          static_cast<const __nv_bfloat16*>(a.values), v->didx, v->colscale, A8);
+    *launches += 3;
+    return cudaGetLastError();
+  }
+  const int tiled = panel_kernel_takes(Kp, *v, false) ? 1 : 0;
   cudaError_t e = cudaMemsetAsync(
       A3, 0, static_cast<size_t>(tiled ? (a.n + 127) / 128 * 128 : a.n) * 3 * Kp * 2, s);
   if (e != cudaSuccess) return e;
@@ -946,7 +1095,7 @@ cudaError_t launch_debug_wait_timeout(int* status, cudaStream_t s) {
 
 cudaError_t launch_tc_gemm(const DenseArgs& a, const DenseView& v, float* Ahat,
                            int accumulate, cudaStream_t s, int* launches) {
-  if (panel_kernel_takes(v.Kp, v)) {
+  if (panel_kernel_takes(v.Kp, v, a.fp8 != 0)) {
     {
       cudaError_t e;
       // split-K: about two CTAs per SM, at least four steps per slice
@@ -961,15 +1110,16 @@ cudaError_t launch_tc_gemm(const DenseArgs& a, const DenseView& v, float* Ahat,
       const dim3 grid((a.d + 127) / 128, (a.n + 127) / 128, static_cast<unsigned>(splits));
       if (grid.y > 65535) return cudaErrorInvalidValue;
       const size_t smem = kPanSmem + static_cast<size_t>(sps) * kBK * sizeof(int32_t);
-      e = cudaFuncSetAttribute(k_tc_panel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      auto kern = a.fp8 ? k_tc_panel<true> : k_tc_panel<false>;
+      e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                static_cast<int>(smem));
       if (e != cudaSuccess) return e;
       const int64_t total = static_cast<int64_t>(a.n) * a.d;
       float* out = splits > 1 ? v.partial : Ahat;
-      k_tc_panel<<<grid, kPanThreads, smem, s>>>(
-          a.d, a.n, v.Kp, static_cast<int32_t>(sps), v.rows, v.Kdev, v.A3, out,
-          splits > 1 ? total : 0, splits > 1 ? 0 : accumulate, a.k0, a.k1, a.stream_id,
-          a.status);
+      kern<<<grid, kPanThreads, smem, s>>>(
+          a.d, a.n, v.Kp, static_cast<int32_t>(sps), v.rows, v.Kdev,
+          reinterpret_cast<const uint8_t*>(v.A3), v.colscale, out, splits > 1 ? total : 0,
+          splits > 1 ? 0 : accumulate, a.k0, a.k1, a.stream_id, a.status);
       ++*launches;
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
       if (splits > 1) {
@@ -982,6 +1132,7 @@ cudaError_t launch_tc_gemm(const DenseArgs& a, const DenseView& v, float* Ahat,
       return e;
     }
   }
+  if (a.fp8) return cudaErrorNotSupported;  // FP8 panels exist only in the pipelined kernel
   const dim3 grid((a.d + kBM - 1) / kBM, (a.n + kBN - 1) / kBN);
   if (grid.y > 65535) return cudaErrorInvalidValue;
   cudaError_t e = cudaFuncSetAttribute(k_tc_umma, cudaFuncAttributeMaxDynamicSharedMemorySize,

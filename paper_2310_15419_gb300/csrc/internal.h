@@ -133,6 +133,7 @@ struct DenseArgs {
   const int32_t* rowidx;
   const void* values;
   int32_t tau;   // rows with at least tau nonzeros go to the panel
+  int32_t fp8;   // 1: E4M3 operands (two terms of A, per-column scales)
   int64_t kmax;  // capacity: nnz / tau bounds the number of such rows
   uint32_t k0, k1, stream_id;
   int* status;
@@ -151,6 +152,8 @@ struct DenseView {
   const void* rest_values;
   const int32_t* rest_pos;  // output position of each kept entry (scan of keep flags)
   float* partial;           // split-K partial copies of A_hat (pipelined panel kernel)
+  float* colscale;          // FP8: 2^e per column of A, undone on output
+  uint32_t* cmax;           // FP8: workspace, largest panel magnitude per column
   int32_t max_splits;       // how many of them the workspace holds (0: none)
   char* scan_tmp;     // workspace: scan scratch
 };

@@ -167,6 +167,9 @@ int check_plan(sketch_t h, const sketch_plan& p) {
                 "tensor-core panels need +-1 S (exact in BF16)");
   if (p.tc_min_row_nnz > 0 && p.mode == SKETCH_MODE_PANEL)
     return fail(h, SKETCH_ERR_UNSUPPORTED, "tensor-core panels pair with REGEN or TILE");
+  if (p.tc_fp8 != 0 && p.tc_fp8 != 1) return fail(h, SKETCH_ERR_ARG, "tc_fp8 must be 0 or 1");
+  if (p.tc_fp8 && p.tc_min_row_nnz <= 0)
+    return fail(h, SKETCH_ERR_ARG, "tc_fp8 needs tensor-core panels (tc_min_row_nnz > 0)");
   if (p.mode == SKETCH_MODE_REGEN) {
     if (p.q_tiles < 1 || p.q_tiles > 4)
       return fail(h, SKETCH_ERR_ARG, "q_tiles must be 1..4");
@@ -232,6 +235,7 @@ int run_plan(sketch_t h, const sketch_csc* A, float* Ahat,
     da.rowidx = A->rowidx;
     da.values = A->values;
     da.tau = p.tc_min_row_nnz;
+    da.fp8 = p.tc_fp8;
     da.kmax = dense_capacity(A, p);
     da.k0 = h->k0;
     da.k1 = h->k1;
@@ -469,12 +473,12 @@ static uint64_t feature_key(const sketch_s* h, const sketch_csc* A, const Featur
   mix(static_cast<uint64_t>(32 * f.heavy_nnz / std::max<int64_t>(1, A->nnz)));
   mix(static_cast<uint64_t>(lg(f.max_row)));
   mix(static_cast<uint64_t>(lg(f.max_col)));
-  mix(2);  // version of the plan set
+  mix(3);  // version of the plan set
   return k;
 }
 
 // Persisted plans (the file named by SKETCH_PLAN_CACHE, one plan per line:
-// key in hex, then the nine plan fields), loaded once per process.
+// key in hex, then the ten plan fields), loaded once per process.
 static std::mutex g_cache_mu;
 static std::map<uint64_t, sketch_plan> g_cache;
 static bool g_cache_loaded = false;
@@ -493,9 +497,9 @@ static bool cache_lookup(uint64_t key, sketch_plan* out) {
     if (FILE* f = std::fopen(path, "r")) {
       unsigned long long k = 0;
       sketch_plan p{};
-      while (std::fscanf(f, "%llx %d %d %d %d %d %d %d %d %d", &k, &p.mode, &p.q_tiles, &p.split,
-                         &p.n_block, &p.row_groups, &p.panel_rows, &p.cols_per_warp,
-                         &p.tc_min_row_nnz, &p.tile_acc) == 10)
+      while (std::fscanf(f, "%llx %d %d %d %d %d %d %d %d %d %d", &k, &p.mode, &p.q_tiles,
+                         &p.split, &p.n_block, &p.row_groups, &p.panel_rows, &p.cols_per_warp,
+                         &p.tc_min_row_nnz, &p.tile_acc, &p.tc_fp8) == 11)
         g_cache[k] = p;
       std::fclose(f);
     }
@@ -512,9 +516,10 @@ static void cache_store(uint64_t key, const sketch_plan& p) {
   std::lock_guard<std::mutex> lock(g_cache_mu);
   g_cache[key] = p;
   if (FILE* f = std::fopen(path, "a")) {
-    std::fprintf(f, "%llx %d %d %d %d %d %d %d %d %d\n", static_cast<unsigned long long>(key),
-                 p.mode, p.q_tiles, p.split, p.n_block, p.row_groups, p.panel_rows,
-                 p.cols_per_warp, p.tc_min_row_nnz, p.tile_acc);
+    std::fprintf(f, "%llx %d %d %d %d %d %d %d %d %d %d\n",
+                 static_cast<unsigned long long>(key), p.mode, p.q_tiles, p.split, p.n_block,
+                 p.row_groups, p.panel_rows, p.cols_per_warp, p.tc_min_row_nnz, p.tile_acc,
+                 p.tc_fp8);
     std::fclose(f);
   }
 }
@@ -561,9 +566,8 @@ int choose_plan(sketch_t h, const sketch_csc* A, float* Ahat, cudaStream_t s,
   const char* env = std::getenv("SKETCH_TUNE");
   const bool tune = h->autotune && !(env && env[0] == '0') && !h->capturing &&
                     Ahat != nullptr;
-  if (!tune) {
+  if (!tune) {  // the heuristic is cheap: planned on every call, not cached
     *out = heuristic_plan(h, A);
-    h->plans[key] = *out;
     return SKETCH_OK;
   }
   // Pattern features (one device pass), then the persisted cache.

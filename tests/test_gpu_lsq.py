@@ -224,3 +224,33 @@ def test_three_methods_on_lsq_mixed_full_size():
     ref = xs["sap_qr"]
     for method in ("sap_svd", "lsqr_d"):
         assert np.linalg.norm(xs[method] - ref) <= 1e-8 * np.linalg.norm(ref), method
+
+
+def test_lsq_with_fp8_panel_sketch():
+    """Sec. 5.3 with the sketch on FP8 tensor-core panels (every nonempty row
+    in the panel, BF16 values over four decades of column scale): the sketch
+    is within 2e-2 of FP64, and since LSQR runs on the true A, the solve
+    still reaches the same solution as the exact-sketch solve."""
+    m, n = 60_000, 80
+    A, b, _ = inputs.lsq_problem(m, n, 0.02, seed=20, noise=1e-3, col_scale_decades=2.0)
+    A.dtype = inputs.DTYPE_BF16
+    A.values_bf16 = inputs.to_bf16_bits(A.values)
+    A.values = inputs.bf16_bits_to_f32(A.values_bf16)
+    b = A.to_scipy() @ np.ones(n) + 1e-3 * np.random.default_rng(2).standard_normal(m)
+    dA = capi.DeviceCSC(A)
+    fp8 = dict(mode=capi.SKETCH_MODE_REGEN, q_tiles=2, split=1, tc_min_row_nnz=1, tc_fp8=1)
+    sk = capi.Sketch(m, n, 2 * n, "pm1", seed=1)
+    sk.set_plan(**fp8)
+    Ahat = sk.apply(dA).cpu().numpy().astype(np.float64).T
+    ref, _ = oracle.sketch_jki(m, n, 2 * n, oracle.PM1, 1, 0, A.colptr, A.rowidx, A.values)
+    err = np.linalg.norm(Ahat - ref) / np.linalg.norm(ref)
+    assert 0 < err <= 2e-2, err
+    bb = torch.from_numpy(b).cuda()
+    x, info = sk.lsq_solve(dA, bb, tol=1e-10, maxit=2000)
+    sk.close()
+    x = x.cpu().numpy()
+    assert info["rc"] == capi.SKETCH_OK
+    xe, ie = _solve(A, b, 2 * n, "pm1", tol=1e-10, maxit=2000)
+    assert np.linalg.norm(x - xe) <= 1e-8 * np.linalg.norm(xe)
+    e_cpu = oracle.ls_error(m, n, A.colptr, A.rowidx, A.values, b, x)
+    assert e_cpu <= max(1e-10, 2 * ie["error"])

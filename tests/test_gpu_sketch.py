@@ -472,6 +472,40 @@ def test_tensor_core_long_panel_float_tolerance():
     assert rel_fro(got, oracle_sketch(A, 513, "pm1")) <= TOL
 
 
+FP8_PLANS = [dict(mode=capi.SKETCH_MODE_REGEN, q_tiles=2, split=2, tc_min_row_nnz=40, tc_fp8=1),
+             dict(mode=capi.SKETCH_MODE_TILE, panel_rows=512, row_groups=4, cols_per_warp=16,
+                  tc_min_row_nnz=100, tc_fp8=1)]
+
+
+@pytest.mark.parametrize("plan", FP8_PLANS)
+@pytest.mark.parametrize("every", [97, 40])
+def test_fp8_panel_integer_bit_exact(plan, every):
+    """FP8 panels: +-1 is exact in E4M3 and integers up to 3 in magnitude
+    survive the per-column power-of-two scale and the two-term split, so the
+    sketch stays bit-exact (short panels, and long ones past 512 rows)."""
+    A = _dense_rows_matrix(30_400 if every == 40 else 9000, 300, every, 0.002, True, seed=39)
+    for d in (256, 301):
+        got = gpu_sketch(A, d, "pm1", plan=plan)
+        assert np.array_equal(got, oracle_sketch(A, d, "pm1")), d
+
+
+@pytest.mark.parametrize("plan", FP8_PLANS)
+def test_fp8_panel_float_within_2e_2(plan):
+    """U(-1,1) values: each value is carried by two E4M3 terms (about 2^-8
+    relative), so the sketch meets the FP8 gate of 2e-2 against FP64."""
+    A = _dense_rows_matrix(30_400, 300, 40, 0.002, False, seed=40)
+    ref = oracle_sketch(A, 513, "pm1")
+    err = rel_fro(gpu_sketch(A, 513, "pm1", plan=plan), ref)
+    assert err <= 2e-2, err
+
+
+def test_fp8_panel_needs_a_panel():
+    sk = capi.Sketch(1000, 10, 64, "pm1")
+    with pytest.raises(capi.SketchError) as e:
+        sk.set_plan(mode=capi.SKETCH_MODE_REGEN, q_tiles=1, split=1, tc_fp8=1)
+    assert e.value.code == capi.SKETCH_ERR_ARG
+
+
 def test_tuned_plan_on_dense_rows_is_exact():
     """With tuning on, +-1 S on a matrix with dense rows: whichever plan the
     tuner takes (tensor-core panels are candidates), the sketch is the

@@ -97,9 +97,10 @@ def test_persisted_plan_cache_skips_timing(tmp_path, monkeypatch):
     A = inputs.float_uniform(150_000, 300, 0.004, seed=17)
     d = 600
     first = capi.Sketch(A.m, A.n, d, "uniform", seed=3)
-    out1 = first.apply(capi.DeviceCSC(A))
+    dA1 = capi.DeviceCSC(A)
+    out1 = first.apply(dA1)
     torch.cuda.synchronize()
-    plan1 = first.get_plan(capi.DeviceCSC(A))
+    plan1 = first.get_plan(dA1)
     tuning_launches = first.launch_count()
     first.close()
     lines = path.read_text().split("\n")
