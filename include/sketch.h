@@ -410,7 +410,7 @@ int sketch_debug_normal_pair(const uint32_t* words, float* out, int64_t count,
 
 /* The timeout path of the kernels' bounded waits, on purpose: a kernel
  * waits on an mbarrier phase that nothing completes, gives up after its
- * iteration limit (well under a second) and records the timeout in the
+ * time limit (2 ms here; 2 s in the real kernels) and records the timeout in the
  * handle's device status word, so that sketch_device_status then returns
  * SKETCH_ERR_TIMEOUT; the context stays usable.  Asynchronous. */
 int sketch_debug_wait_timeout(sketch_t h, sketch_stream_t stream);

@@ -12,7 +12,9 @@
 //     S, dense row), expanded to a BF16 +-1 tile in shared memory (no S in
 //     global memory);
 //   * the MMA is tcgen05 (5th-generation tensor cores) with the accumulator
-//     in tensor memory.
+//     in tensor memory, in one persistent kernel (k_tc_panel);
+//   * optionally FP8: E4M3 +-1 S against two E4M3 terms of A, each column
+//     first scaled by a power of two (undone exactly on the output).
 // The sparse kernels run on the rest of A (a compacted CSC without the
 // panel's rows), so A_hat = S A_rest + S_D A_D with the MMA adding into A_hat
 // afterwards.
@@ -29,10 +31,7 @@ namespace sk {
 
 namespace {
 
-constexpr int kBM = 128;   // rows of S (A_hat) per CTA
-constexpr int kBN = 128;   // columns of A per CTA
-constexpr int kBK = 32;    // contraction step
-constexpr int kTcThreads = 256;
+constexpr int kBK = 32;    // contraction step (dense rows per step)
 
 __device__ __forceinline__ uint16_t bf16_bits(float v) {
   return __bfloat16_as_ushort(__float2bfloat16_rn(v));
@@ -76,15 +75,11 @@ __device__ __forceinline__ int32_t column_of(const int32_t* __restrict__ colptr,
 
 // The t-th BF16 term of A(j, k) for dense rows j (q = didx[j]), one thread
 // per entry (its column by binary search), so the build runs at memory speed
-// however long the columns are.  Two layouts of A3:
-//   tiled = 0: A3[k * 3 Kp + t * Kp + q] (column k's terms, K fastest);
-//   tiled = 1: for the pipelined kernel, each step's three 128-column B
-//     tiles contiguous (24 KB) in the operand layout the MMA reads: tile
-//     (k >> 7, step q >> 5), term t, k-chunk (q >> 3) & 3, column k & 127,
-//     8 consecutive q -- one bulk copy per step.
-__device__ __forceinline__ int64_t a3_offset(int tiled, int32_t k, int32_t q, int t,
-                                             int64_t Kp) {
-  if (!tiled) return static_cast<int64_t>(k) * 3 * Kp + t * Kp + q;
+// however long the columns are.  Layout of A3: each step's three 128-column
+// B tiles contiguous (24 KB) in the operand layout the MMA reads: tile
+// (k >> 7, step q >> 5), term t, k-chunk (q >> 3) & 3, column k & 127, 8
+// consecutive q -- one bulk copy per step.
+__device__ __forceinline__ int64_t a3_offset(int32_t k, int32_t q, int t, int64_t Kp) {
   const int64_t steps = Kp >> 5;
   const int64_t tile_step = (static_cast<int64_t>(k >> 7) * steps + (q >> 5)) * 3 + t;
   return ((tile_step * 4 + ((q >> 3) & 3)) * 128 + (k & 127)) * 8 + (q & 7);
@@ -155,7 +150,7 @@ __global__ void k_dense_scatter_fp8(int32_t n, int32_t m, int32_t Kp, int64_t nn
 }
 
 template <typename VT>
-__global__ void k_dense_scatter(int32_t n, int32_t m, int32_t Kp, int64_t nnz, int tiled,
+__global__ void k_dense_scatter(int32_t n, int32_t m, int32_t Kp, int64_t nnz,
                                 const int32_t* __restrict__ colptr,
                                 const int32_t* __restrict__ rowidx,
                                 const VT* __restrict__ vals,
@@ -174,9 +169,9 @@ __global__ void k_dense_scatter(int32_t n, int32_t m, int32_t Kp, int64_t nnz, i
     const float r1 = a - a1;  // exact
     const float a2 = __bfloat162float(__float2bfloat16_rn(r1));
     const float a3 = r1 - a2;  // exact, fits BF16
-    A3[a3_offset(tiled, k, q, 0, Kp)] = bf16_bits(a1);
-    A3[a3_offset(tiled, k, q, 1, Kp)] = bf16_bits(a2);
-    A3[a3_offset(tiled, k, q, 2, Kp)] = bf16_bits(a3);
+    A3[a3_offset(k, q, 0, Kp)] = bf16_bits(a1);
+    A3[a3_offset(k, q, 1, Kp)] = bf16_bits(a2);
+    A3[a3_offset(k, q, 2, Kp)] = bf16_bits(a3);
   }
 }
 
@@ -185,269 +180,81 @@ __device__ __forceinline__ uint32_t pm1_pair(uint32_t b0, uint32_t b1) {
   return (0x3F80u | (b0 << 15)) | ((0x3F80u | (b1 << 15)) << 16);
 }
 
-// ---------------------------------------------------------------------------
-// A_hat(rows d0.., cols n0..) (+)= S3 A3 for a 128 x 128 tile on the
-// 5th-generation tensor cores (tcgen05).  One thread issues
-// `tcgen05.mma.cta_group::1.kind::f16` (M = N = 128, K = 16, BF16 in, FP32
-// accumulate) with both operands in shared memory and the 128 x 128
-// accumulator in tensor memory (128 columns, allocated per CTA).  Operand
-// tiles (128 rows x 32 k, BF16) use the K-major layout without swizzle:
-// 8-row x 16-byte core matrices, the next one along K 128 bytes on, along
-// M/N 512 bytes on.  One iteration per 32 dense rows: the A tile (+-1 S,
-// built once from Philox sign bits) and the three B tiles (the BF16 terms of
-// A3, by cp.async one iteration ahead) form a stage; six MMAs (3 terms x 2 k
-// halves) and one tcgen05.commit per iteration; a stage is reused once that
-// commit has arrived on its mbarrier.  Every wait has an iteration limit: on
-// expiry the CTA records kStatusTimeout, frees its tensor memory and stops.
-// (N = 256 per CTA measured slower on Abnormal_A: 0.80 against 0.75 ms.)
-constexpr uint32_t kUmmaLbo = 128, kUmmaSbo = 512;
-constexpr int kUmmaTile = 8192;  // bytes of one 128 x 32 BF16 operand tile
-// instruction descriptor: F32 accumulator, BF16 A and B, both K-major,
-// N = 128 (N >> 3 at bit 17), M = 128 (M >> 4 at bit 24)
+// Instruction descriptor of kind::f16: F32 accumulator, BF16 A and B, both
+// K-major, N = 128 (N >> 3 at bit 17), M = 128 (M >> 4 at bit 24).
 constexpr uint32_t kUmmaIdesc =
     (1u << 4) | (1u << 7) | (1u << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
-constexpr int kUmmaStages = 2;  // stage = A tile + the three B terms of a step
-constexpr int kUmmaStageBytes = 4 * kUmmaTile;
-// two stages + alignment; at most three CTAs share an SM, so 3 x 128
-// tensor-memory columns never exceed the 512 there and tcgen05.alloc never
-// waits for another CTA
-constexpr size_t kUmmaSmem = kUmmaStages * kUmmaStageBytes + 1024;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
-// shared-memory matrix descriptor: start, leading (K) and stride (M/N)
-// byte offsets in 16-byte units, descriptor version 1, no swizzle
-__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr) {
-  return static_cast<uint64_t>((saddr >> 4) & 0x3FFFu) |
-         (static_cast<uint64_t>((kUmmaLbo >> 4) & 0x3FFFu) << 16) |
-         (static_cast<uint64_t>((kUmmaSbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+// Wait for the phase of parity `parity` of an mbarrier; false once
+// `limit_ns` nanoseconds (by the global timer) have passed.  Each poll lets
+// the hardware suspend the thread until the phase completes or a few
+// microseconds pass, so waiting warps take few issue slots from the
+// working ones.
+constexpr uint32_t kSuspendNs = 10000;
+constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
 }
-
-// wait for the phase of parity `parity` of an mbarrier; false after `limit`
-// polls
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int limit = 1 << 22) {
-  for (int i = 0; i < limit; ++i) {
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity,
+                                          uint64_t limit_ns = kWaitLimitNs) {
+  uint64_t t0 = 0;
+  for (bool first = true;; first = false) {
     uint32_t ok;
     asm volatile(
-        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
         "selp.u32 %0, 1, 0, p;\n}\n"
         : "=r"(ok)
-        : "r"(bar), "r"(parity)
+        : "r"(bar), "r"(parity), "r"(kSuspendNs)
         : "memory");
     if (ok) return true;
+    const uint64_t t = global_ns();
+    if (first)
+      t0 = t;
+    else if (t - t0 > limit_ns)
+      return false;
   }
-  return false;
-}
-
-__global__ void __launch_bounds__(kTcThreads, 1)
-    k_tc_umma(int32_t d, int32_t n, int32_t Kp, const int32_t* __restrict__ rows,
-              const int32_t* __restrict__ Kdev, const uint16_t* __restrict__ A3,
-              float* __restrict__ Ahat, uint32_t k0, uint32_t k1, uint32_t stream_id,
-              int accumulate, int* status) {
-  extern __shared__ uint8_t sm_raw[];
-  __shared__ uint32_t sbits[kBK][4];
-  // one mbarrier per stage, plus one that only the drain commit of the
-  // failure path arrives on
-  __shared__ __align__(8) uint64_t mbar[kUmmaStages + 1];
-  __shared__ uint32_t tmem_base;
-  __shared__ int failed;
-  uint8_t* base = sm_raw + ((1024u - (smem_u32(sm_raw) & 1023u)) & 1023u);
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int d0 = blockIdx.x * kBM, n0 = blockIdx.y * kBN;
-  const int K = *Kdev;
-  const int64_t K3 = 3LL * Kp;
-  const int steps = Kp / kBK;
-  auto tileA = [&](int stg) { return base + stg * kUmmaStageBytes; };
-  auto tileB = [&](int stg, int term) { return base + stg * kUmmaStageBytes + (1 + term) * kUmmaTile; };
-  // the three B tiles of step st: terms of A3, dense rows 32 st .. + 31
-  auto load_B = [&](int st) {
-    for (int c = tid; c < 3 * kBN * 4; c += kTcThreads) {
-      const int term = c / (kBN * 4), cc = c % (kBN * 4);
-      const int nn = cc >> 2, part = cc & 3;
-      const int col = n0 + nn;
-      const int64_t koff = static_cast<int64_t>(term) * Kp + kBK * st;
-      const uint16_t* src = col < n ? A3 + col * K3 + koff + 8 * part : A3;
-      const uint32_t dst = smem_u32(tileB(st % kUmmaStages, term) + (nn >> 3) * kUmmaSbo +
-                                    part * kUmmaLbo + (nn & 7) * 16);
-      const int bytes = col < n ? 16 : 0;  // zero fill past the last column
-      asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src),
-                   "r"(bytes)
-                   : "memory");
-    }
-  };
-  if (tid == 0) {
-    failed = 0;
-    for (int q = 0; q <= kUmmaStages; ++q)
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[q])) : "memory");
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;" ::"r"(
-                     smem_u32(&tmem_base))
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-  }
-  load_B(0);
-  asm volatile("cp.async.commit_group;" ::: "memory");
-  __syncthreads();
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  const uint32_t tmem = tmem_base;
-
-  for (int st = 0; st < steps; ++st) {
-    const int sb = st % kUmmaStages;
-    // prefetch step st + 1 into the stage MMA(st - 1) read
-    if (st + 1 < steps && st >= 1 && tid == 0 &&
-        !mbar_wait(smem_u32(&mbar[(st - 1) % kUmmaStages]), ((st - 1) / kUmmaStages) & 1))
-      failed = 1;
-    if (tid < kBK) {  // S signs for the 32 dense rows of this step
-      const int q = st * kBK + tid;
-      const int32_t j = q < K ? rows[q] : 0;  // padding rows multiply zeros
-      const uint4 x = philox_block(static_cast<uint32_t>(d0 >> 7), static_cast<uint32_t>(j),
-                                   stream_id, k0, k1);
-      sbits[tid][0] = x.x;
-      sbits[tid][1] = x.y;
-      sbits[tid][2] = x.z;
-      sbits[tid][3] = x.w;
-    }
-    __syncthreads();
-    if (failed) break;
-    if (st + 1 < steps) load_B(st + 1);
-    asm volatile("cp.async.commit_group;" ::: "memory");
-    // A tile of step st: +-1 S (BF16), row r of the tile, k = dense row of
-    // the step (its stage was last read by MMA(st - 2), which the wait of
-    // iteration st - 1 covered)
-    {
-      uint8_t* smA = tileA(sb);
-      const int r = tid & 127;
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int kc = 2 * (tid >> 7) + h;
-        uint32_t w[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int ka = 8 * kc + 2 * u;
-          const uint32_t b0 = (sbits[ka][r >> 5] >> (r & 31)) & 1u;
-          const uint32_t b1 = (sbits[ka + 1][r >> 5] >> (r & 31)) & 1u;
-          w[u] = pm1_pair(b0, b1);
-        }
-        *reinterpret_cast<uint4*>(smA + (r >> 3) * kUmmaSbo + kc * kUmmaLbo + (r & 7) * 16) =
-            make_uint4(w[0], w[1], w[2], w[3]);
-      }
-    }
-    // this step's B tiles have landed (at most one newer group)
-    asm volatile("cp.async.wait_group 1;" ::: "memory");
-    // generic-proxy writes (st.shared, cp.async) -> visible to the tensor core
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
-    if (tid == 0) {
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-#pragma unroll
-      for (int term = 0; term < 3; ++term)
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const uint64_t ad = umma_desc(smem_u32(tileA(sb)) + 256 * h);
-          const uint64_t bd = umma_desc(smem_u32(tileB(sb, term)) + 256 * h);
-          const uint32_t acc = (st > 0 || term > 0 || h > 0) ? 1u : 0u;
-          asm volatile(
-              "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-              "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-              "l"(ad), "l"(bd), "r"(kUmmaIdesc), "r"(acc)
-              : "memory");
-        }
-      asm volatile(
-          "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-              smem_u32(&mbar[sb]))
-          : "memory");
-    }
-  }
-  asm volatile("cp.async.wait_all;" ::: "memory");
-  // the last commit completes after every MMA before it
-  if (!failed && tid == 0 &&
-      !mbar_wait(smem_u32(&mbar[(steps - 1) % kUmmaStages]), ((steps - 1) / kUmmaStages) & 1))
-    failed = 1;
-  // After a timeout, MMAs issued earlier may still be running and writing
-  // tensor memory: one more commit (it arrives once every MMA this thread
-  // issued has completed) drains them before the memory is freed.  If even
-  // that wait runs out, kStatusTimeout still goes to the host, and the
-  // tensor-memory columns are freed with work possibly in flight (the error
-  // documentation tells the caller to treat the context as unreliable).
-  if (failed && tid == 0) {
-    asm volatile(
-        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-            smem_u32(&mbar[kUmmaStages]))
-        : "memory");
-    mbar_wait(smem_u32(&mbar[kUmmaStages]), 0);
-  }
-  __syncthreads();
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  if (!failed) {
-    // warp w: lanes (rows of S) 32 (w & 3) .. + 31, columns 64 (w >> 2) .. + 63
-    const int rq = warp & 3;
-    const int r = d0 + 32 * rq + lane;
-#pragma unroll
-    for (int cc = 0; cc < 2; ++cc) {
-      const int c0 = 64 * (warp >> 2) + 32 * cc;
-      uint32_t v[32];
-      asm volatile(
-          "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, "
-          "%10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, "
-          "%26, %27, %28, %29, %30, %31}, [%32];"
-          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
-            "=r"(v[6]), "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]),
-            "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]),
-            "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
-            "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]),
-            "=r"(v[30]), "=r"(v[31])
-          : "r"(tmem + (static_cast<uint32_t>(32 * rq) << 16) + static_cast<uint32_t>(c0)));
-      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-      if (r < d) {
-#pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          const int c = n0 + c0 + j;
-          if (c < n) {
-            float* o = Ahat + static_cast<int64_t>(c) * d + r;
-            const float x = __uint_as_float(v[j]);
-            *o = accumulate ? *o + x : x;
-          }
-        }
-      }
-    }
-  } else if (tid == 0) {
-    atomicOr(status, kStatusTimeout);
-  }
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-  __syncthreads();
-  if (warp == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" ::"r"(tmem) : "memory");
 }
 
 // ---------------------------------------------------------------------------
-// k_tc_panel: the same product for long panels (many dense rows), warp
-// specialised and pipelined.  A CTA owns a 128 x 128 tile of A_hat (rows of
-// S x columns of A) and one of `splits` slices of the dense rows (split-K:
-// enough CTAs for every SM; the slices' partial tiles are added in a fixed
-// order afterwards).  Per step of 32 dense rows, in a ring of kPanStages
-// shared-memory stages:
-//   warp 0 (one thread): the three B tiles (the BF16 terms of A3, 128
-//     columns x 32 k each) by TMA, twelve 16-byte-wide boxes into the
-//     no-swizzle K-major layout (row i of a box at 16 i, k-chunks 2048 B
-//     apart), completion counted on the stage's full barrier;
-//   warps 4-11: the +-1 S tile (128 rows x 32 k, BF16, same layout), warps
-//     4-7 for even steps and 8-11 for odd ones, 32 rows each with no barrier
-//     between them: lane k computes the Philox block of
-//     dense row k and keeps the warp's word, a five-stage shuffle transpose
-//     gives each lane its row's 32 signs, which become BF16 +-1; then a proxy
-//     fence and one arrival per warp on the stage's full barrier;
-//   warp 1 (one thread): six MMAs (3 terms x 2 k halves, M = N = 128,
-//     K = 16) into one of two tensor-memory accumulators, which it switches
-//     every two steps, and a commit that frees the stage.
-// Warps 12-15 promote: each finished two-step accumulator is added, with
-// CUDA-core round-to-nearest FP32 additions, into running sums kept in
-// tensor memory.  The tensor core's own accumulation then covers only twelve
-// products per output at a time, so its rounding cannot build up along a
-// panel of thousands of rows.  The same warps finally store the sums.
+// k_tc_panel: the same product, persistent, warp specialised and pipelined.
+// One CTA per SM walks a list of units, a unit being a 128 x 128 tile of
+// A_hat (rows of S x columns of A) and one of `splits` slices of the dense
+// rows (split-K; the slices' partial tiles are added in a fixed order
+// afterwards).  Two ways to feed the B operand (the terms of A3):
+//   streaming (long panels): each 32-row step's B block (all terms, one
+//     contiguous block of the tiled A3) is bulk-copied (TMA) into a ring of
+//     kPanStages stages next to that step's S tile; CTA b takes units b,
+//     b + G, ... (G CTAs), so the CTAs running at once share B blocks in L2;
+//   resident (short panels, all steps' B of a column tile within
+//     kPanResBytes): a column tile's whole B stays in shared memory while the
+//     CTA works through a contiguous run of units with that column tile (the
+//     row tiles vary fastest), so A3 is read about once per CTA; only the S
+//     tiles go through the ring.
+// Roles (512 threads):
+//   warp 0 (one thread): the bulk copies;
+//   warp 1 (one thread): per step six BF16 MMAs (3 terms x 2 k halves,
+//     M = N = 128, K = 16) or two FP8 ones, into one of two tensor-memory
+//     accumulators, switched every two steps of a unit; commits free the
+//     stage and, every two steps, hand the accumulator to the promoters;
+//   warps 4-11: the +-1 S tiles, warps 4-7 for even steps and 8-11 for odd
+//     ones (steps counted over the CTA's units), 32 rows of S each: lane k
+//     computes the Philox block of the step's dense row k and keeps the
+//     warp's word, a five-stage shuffle transpose gives each lane its row's
+//     32 signs, written as BF16 (or E4M3) +-1 in the no-swizzle K-major
+//     layout; the next step's dense-row id is loaded one step ahead;
+//   warps 12-15 (the promoters): each finished two-step accumulator is added
+//     with round-to-nearest FP32 additions into running sums in tensor memory
+//     (so the tensor core's truncating accumulation covers only twelve
+//     products per output at a time), then freed; the unit's last one is
+//     added in registers and stored to A_hat (or the slice's partial copy)
+//     directly, while the MMAs of the next unit already run in the other
+//     accumulator.
 // Every mbarrier wait has an iteration limit; on a timeout the CTA records
 // kStatusTimeout, drains the MMAs it issued and frees its tensor memory.
 // ---------------------------------------------------------------------------
@@ -456,13 +263,51 @@ constexpr int kPanThreads = 512;
 constexpr uint32_t kPanLbo = 2048;       // K-direction core-matrix stride
 constexpr uint32_t kPanSbo = 128;        // M/N-direction 8-row-group stride
 constexpr int kPanTileBytes = 8192;      // one 128 x 32 BF16 operand tile
-constexpr int kPanStageBytes = 4 * kPanTileBytes;  // the S tile + three B tiles
-constexpr uint32_t kPanTxBytes = 3 * kPanTileBytes;
-constexpr size_t kPanSmem = kPanStages * kPanStageBytes + 1024;  // + the slice's row ids
+constexpr int kPanStageBytes = 4 * kPanTileBytes;  // streaming: the S tile + three B tiles
+constexpr int kPanResBytes = 192 * 1024;           // resident: all steps' B of a column tile
 constexpr uint32_t kPanSums = 256;       // tensor-memory column of the running sums
-// Panels of at least this many padded dense rows take the pipelined kernel.
-constexpr int kPanMinKp = 512;
-constexpr int kPanMaxSliceSteps = 384;  // steps of one split-K slice (row ids in smem)
+
+// The unit grid of one launch.
+struct PanelGrid {
+  int32_t d, n, steps, sps, tiles_d, tiles_n;
+  int64_t units;
+  int32_t resident;
+};
+
+struct PanUnit {
+  int32_t x, y, z, st0, ns;
+};
+
+// Unit u (< 2^31, checked on the host) in 32-bit arithmetic: every role
+// decodes each of its units, so a 64-bit division would cost more than a
+// step of S.
+__device__ __forceinline__ PanUnit pan_unit(const PanelGrid& g, int64_t u64) {
+  PanUnit t;
+  const uint32_t u = static_cast<uint32_t>(u64);
+  const uint32_t r = u / static_cast<uint32_t>(g.tiles_d);
+  t.x = static_cast<int32_t>(u - r * static_cast<uint32_t>(g.tiles_d));
+  const uint32_t z = r / static_cast<uint32_t>(g.tiles_n);
+  t.y = static_cast<int32_t>(r - z * static_cast<uint32_t>(g.tiles_n));
+  t.z = static_cast<int32_t>(z);
+  t.st0 = t.z * g.sps;
+  t.ns = max(0, min(g.steps, t.st0 + g.sps) - t.st0);
+  return t;
+}
+
+// This CTA's units: a contiguous run (resident B) or every G-th one.
+__device__ __forceinline__ void pan_range(const PanelGrid& g, int64_t& lo, int64_t& hi,
+                                          int64_t& stride) {
+  const int64_t G = gridDim.x, b = blockIdx.x;
+  if (g.resident) {
+    lo = b * g.units / G;
+    hi = (b + 1) * g.units / G;
+    stride = 1;
+  } else {
+    lo = b;
+    hi = g.units;
+    stride = G;
+  }
+}
 
 __device__ __forceinline__ uint64_t pan_desc(uint32_t saddr) {
   return static_cast<uint64_t>((saddr >> 4) & 0x3FFFu) |
@@ -513,12 +358,6 @@ __device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_
   "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, " \
   "%19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}"
 
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 " SK_X32_LIST ", [%32];"
-               : SK_TMEM_X32_REGS(v)
-               : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
 __device__ __forceinline__ void tmem_ld32_nowait(uint32_t taddr, uint32_t (&v)[32]) {
   asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 " SK_X32_LIST ", [%32];"
                : SK_TMEM_X32_REGS(v)
@@ -546,6 +385,17 @@ __device__ __forceinline__ void tmem_wait_ld32(uint32_t (&a)[32], uint32_t (&b)[
                :
                : "memory");
 }
+__device__ __forceinline__ void tmem_wait_ld32(uint32_t (&a)[32]) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(a[0]), "+r"(a[1]), "+r"(a[2]), "+r"(a[3]), "+r"(a[4]), "+r"(a[5]),
+                 "+r"(a[6]), "+r"(a[7]), "+r"(a[8]), "+r"(a[9]), "+r"(a[10]), "+r"(a[11]),
+                 "+r"(a[12]), "+r"(a[13]), "+r"(a[14]), "+r"(a[15]), "+r"(a[16]), "+r"(a[17]),
+                 "+r"(a[18]), "+r"(a[19]), "+r"(a[20]), "+r"(a[21]), "+r"(a[22]), "+r"(a[23]),
+                 "+r"(a[24]), "+r"(a[25]), "+r"(a[26]), "+r"(a[27]), "+r"(a[28]), "+r"(a[29]),
+                 "+r"(a[30]), "+r"(a[31])
+               :
+               : "memory");
+}
 __device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&v)[32]) {
   asm volatile("tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], "
                "{%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, "
@@ -556,50 +406,70 @@ __device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&v)[32
 }
 
 // FP8 = true: E4M3 operands (kind::f8f6f4, K = 32 per MMA): the S tile is
-// 128 rows x 32 bytes, the A panel two terms of 4 KB per step (one 8 KB bulk
-// copy), two MMAs per step, and the output is multiplied by the column scale
-// colinv.  Same layout rules: 16-byte core-matrix rows, k-chunks 2048 B apart.
+// 128 rows x 32 bytes, the A panel two terms of 4 KB per step (one 8 KB
+// block), two MMAs per step, and the output is multiplied by the column
+// scale colinv.  Same layout rules: 16-byte core-matrix rows, k-chunks
+// 2048 B apart.
 // Instruction descriptor of kind::f8f6f4: F32 accumulator, E4M3 A and B
 // (format code 0), both K-major, N = 128, M = 128.
 constexpr uint32_t kUmmaIdescFp8 = (1u << 4) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
 
+// Shared memory of one CTA: the stage ring (S tiles, and B blocks when
+// streaming) and, when resident, one column tile's B for every step.
+__host__ __device__ constexpr int pan_term_bytes(bool fp8) {
+  return fp8 ? kPanTileBytes / 2 : kPanTileBytes;
+}
+__host__ __device__ constexpr int pan_step_bytes(bool fp8) {
+  return (fp8 ? 2 : 3) * pan_term_bytes(fp8);
+}
+size_t pan_smem_bytes(bool fp8, bool resident, int steps) {
+  return resident ? static_cast<size_t>(kPanStages) * kPanTileBytes +
+                        static_cast<size_t>(steps) * pan_step_bytes(fp8) + 1024
+                  : static_cast<size_t>(kPanStages) * kPanStageBytes + 1024;
+}
+
 template <bool FP8>
 __global__ void __launch_bounds__(kPanThreads, 1)
-    k_tc_panel(int32_t d, int32_t n, int32_t Kp, int32_t steps_per_split,
-               const int32_t* __restrict__ rows, const int32_t* __restrict__ Kdev,
-               const uint8_t* __restrict__ A3, const float* __restrict__ colinv,
-               float* __restrict__ out, int64_t split_stride, int accumulate, uint32_t k0,
-               uint32_t k1, uint32_t stream_id, int* status) {
-  constexpr int kTerms = FP8 ? 2 : 3;
-  constexpr int kTermBytes = FP8 ? kPanTileBytes / 2 : kPanTileBytes;
-  constexpr uint32_t kTx = kTerms * kTermBytes;
+    k_tc_panel(const PanelGrid g, const int32_t* __restrict__ rows,
+               const int32_t* __restrict__ Kdev, const uint8_t* __restrict__ A3,
+               const float* __restrict__ colinv, float* __restrict__ out,
+               int64_t split_stride, int accumulate, uint32_t k0, uint32_t k1,
+               uint32_t stream_id, int* status) {
+  constexpr int kTermBytes = pan_term_bytes(FP8);
+  constexpr uint32_t kTx = pan_step_bytes(FP8);
   extern __shared__ uint8_t sm_raw[];
   __shared__ __align__(8) uint64_t full[kPanStages], empty[kPanStages], acc_full[2],
-      acc_empty[2], drain_bar;
+      acc_empty[2], bfull, bempty, drain_bar;
   __shared__ uint32_t tmem_base;
   __shared__ volatile int failed;  // set by any role whose bounded wait gave up
   uint8_t* base = sm_raw + ((1024u - (smem_u32(sm_raw) & 1023u)) & 1023u);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int d0 = blockIdx.x * 128, n0 = blockIdx.y * 128;
-  const int K = *Kdev;
-  const int st0 = blockIdx.z * steps_per_split;
-  const int nsteps = max(0, min(Kp / kBK, st0 + steps_per_split) - st0);
-  const int npairs = (nsteps + 1) / 2;
-  float* dst = out + blockIdx.z * split_stride;
-  auto tileS = [&](int stg) { return base + stg * kPanStageBytes; };
-  auto tileB = [&](int stg, int t) {
-    return base + stg * kPanStageBytes + kPanTileBytes + t * kTermBytes;
+  const int d = g.d, n = g.n;
+  const bool res = g.resident != 0;
+  int64_t lo, hi, stride;
+  pan_range(g, lo, hi, stride);
+  // stage sg's S tile; term t of the B operand of step i (resident) or of
+  // the step in stage sg (streaming)
+  auto tileS = [&](int sg) {
+    return base + sg * (res ? kPanTileBytes : kPanStageBytes);
+  };
+  auto tileB = [&](int sg, int i, int t) {
+    return res ? base + kPanStages * kPanTileBytes + i * kTx + t * kTermBytes
+               : base + sg * kPanStageBytes + kPanTileBytes + t * kTermBytes;
   };
   if (tid == 0) {
     failed = 0;
     for (int q = 0; q < kPanStages; ++q) {
-      mbar_init(smem_u32(&full[q]), 5);   // the TMA arrival (with its bytes) + 4 builder warps
+      // the builders' four warps, plus the bulk copy with its bytes when streaming
+      mbar_init(smem_u32(&full[q]), res ? 4 : 5);
       mbar_init(smem_u32(&empty[q]), 1);  // the MMA commit
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(smem_u32(&acc_full[b]), 1);   // the MMA commit of a two-step accumulator
       mbar_init(smem_u32(&acc_empty[b]), 4);  // one arrival per promoting warp
     }
+    mbar_init(smem_u32(&bfull), 1);   // resident B: the copies' bytes
+    mbar_init(smem_u32(&bempty), 1);  // resident B: the MMA commit after its last use
     mbar_init(smem_u32(&drain_bar), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -612,83 +482,116 @@ __global__ void __launch_bounds__(kPanThreads, 1)
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_base;
-  // the dense-row ids of this CTA's slice, staged once (the builders read
-  // them every step)
-  int32_t* srows = reinterpret_cast<int32_t*>(base + kPanStages * kPanStageBytes);
-  for (int t = tid; t < nsteps * kBK; t += kPanThreads) {
-    const int q = st0 * kBK + t;
-    srows[t] = q < K ? rows[q] : 0;  // padding rows multiply zeros
-  }
-  __syncthreads();
 
   if (warp == 0) {
-    if (lane == 0) {  // TMA producer of the A-panel (B operand) tiles
-      for (int i = 0; i < nsteps; ++i) {
-        const int sg = i % kPanStages, round = i / kPanStages, st = st0 + i;
-        if (i >= kPanStages && !mbar_wait(smem_u32(&empty[sg]), (round - 1) & 1)) {
-          failed = 1;
-          break;
+    if (lane == 0) {  // bulk copies of the B operand
+      int gs = 0, loads = 0, yprev = -1;
+      for (int64_t u = lo; u < hi && !failed; u += stride) {
+        const PanUnit t = pan_unit(g, u);
+        if (res) {
+          if (t.y == yprev) continue;
+          // the previous column tile's B is overwritten once its MMAs are done
+          if (loads > 0 && !mbar_wait(smem_u32(&bempty), (loads - 1) & 1)) {
+            failed = 1;
+            break;
+          }
+          mbar_arrive_tx(smem_u32(&bfull), static_cast<uint32_t>(g.steps) * kTx);
+          for (int i = 0; i < g.steps; ++i)
+            bulk_load(smem_u32(tileB(0, i, 0)),
+                      A3 + (static_cast<int64_t>(t.y) * g.steps + i) * kTx, kTx,
+                      smem_u32(&bfull));
+          ++loads;
+          yprev = t.y;
+          continue;
         }
-        if (failed) break;
-        mbar_arrive_tx(smem_u32(&full[sg]), kTx);
-        // the step's B tiles (all terms) are one contiguous block of A3
-        const uint8_t* src = A3 + (static_cast<int64_t>(blockIdx.y) * (Kp / kBK) + st) * kTx;
-        bulk_load(smem_u32(tileB(sg, 0)), src, kTx, smem_u32(&full[sg]));
+        for (int i = 0; i < t.ns; ++i, ++gs) {
+          const int sg = gs % kPanStages, round = gs / kPanStages;
+          if (gs >= kPanStages && !mbar_wait(smem_u32(&empty[sg]), (round - 1) & 1)) {
+            failed = 1;
+            break;
+          }
+          if (failed) break;
+          mbar_arrive_tx(smem_u32(&full[sg]), kTx);
+          // the step's B tiles (all terms) are one contiguous block of A3
+          bulk_load(smem_u32(tileB(sg, 0, 0)),
+                    A3 + (static_cast<int64_t>(t.y) * g.steps + t.st0 + i) * kTx, kTx,
+                    smem_u32(&full[sg]));
+        }
       }
     }
   } else if (warp == 1) {
     if (lane == 0) {  // MMA issuer
       bool ok = true;
-      for (int i = 0; i < nsteps && ok; ++i) {
-        const int sg = i % kPanStages, round = i / kPanStages, pr = i >> 1, b = pr & 1;
-        if ((i & 1) == 0 && pr >= 2 &&
-            !mbar_wait(smem_u32(&acc_empty[b]), ((pr >> 1) - 1) & 1)) {
-          ok = false;
-          break;
-        }
-        if (!mbar_wait(smem_u32(&full[sg]), round & 1)) {
-          ok = false;
-          break;
-        }
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        if constexpr (FP8) {
-#pragma unroll
-          for (int t = 0; t < 2; ++t) {  // K = 32: the whole step
-            const uint64_t ad = pan_desc(smem_u32(tileS(sg)));
-            const uint64_t bd = pan_desc(smem_u32(tileB(sg, t)));
-            const uint32_t acc = ((i & 1) || t > 0) ? 1u : 0u;
+      int gs = 0, P = 0, loads = 0, yprev = -1;
+      for (int64_t u = lo; u < hi && ok; u += stride) {
+        const PanUnit t = pan_unit(g, u);
+        if (res && t.y != yprev) {
+          // free the previous column tile's B once its MMAs finish, then
+          // wait for this one's
+          if (loads > 0)
             asm volatile(
-                "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-                "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(
-                    tmem + static_cast<uint32_t>(128 * b)),
-                "l"(ad), "l"(bd), "r"(kUmmaIdescFp8), "r"(acc)
+                "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 "
+                "[%0];" ::"r"(smem_u32(&bempty))
                 : "memory");
+          if (!mbar_wait(smem_u32(&bfull), loads & 1)) {
+            ok = false;
+            break;
           }
-        } else {
+          ++loads;
+          yprev = t.y;
+        }
+        for (int i = 0; i < t.ns; ++i, ++gs) {
+          const int sg = gs % kPanStages, round = gs / kPanStages, b = P & 1;
+          if (failed ||
+              ((i & 1) == 0 && P >= 2 &&
+               !mbar_wait(smem_u32(&acc_empty[b]), ((P >> 1) - 1) & 1)) ||
+              !mbar_wait(smem_u32(&full[sg]), round & 1)) {
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t acc_addr = tmem + static_cast<uint32_t>(128 * b);
+          if constexpr (FP8) {
 #pragma unroll
-          for (int t = 0; t < 3; ++t)
-#pragma unroll
-            for (int kh = 0; kh < 2; ++kh) {
-              const uint64_t ad = pan_desc(smem_u32(tileS(sg)) + kh * 2 * kPanLbo);
-              const uint64_t bd = pan_desc(smem_u32(tileB(sg, t)) + kh * 2 * kPanLbo);
-              const uint32_t acc = ((i & 1) || t > 0 || kh > 0) ? 1u : 0u;
+            for (int tt = 0; tt < 2; ++tt) {  // K = 32: the whole step
+              const uint64_t ad = pan_desc(smem_u32(tileS(sg)));
+              const uint64_t bd = pan_desc(smem_u32(tileB(sg, i, tt)));
+              const uint32_t acc = ((i & 1) || tt > 0) ? 1u : 0u;
               asm volatile(
                   "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-                  "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
-                      tmem + static_cast<uint32_t>(128 * b)),
-                  "l"(ad), "l"(bd), "r"(kUmmaIdesc), "r"(acc)
+                  "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+                      acc_addr),
+                  "l"(ad), "l"(bd), "r"(kUmmaIdescFp8), "r"(acc)
                   : "memory");
             }
-        }
-        asm volatile(
-            "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                smem_u32(&empty[sg]))
-            : "memory");
-        if ((i & 1) || i == nsteps - 1)
+          } else {
+#pragma unroll
+            for (int tt = 0; tt < 3; ++tt)
+#pragma unroll
+              for (int kh = 0; kh < 2; ++kh) {
+                const uint64_t ad = pan_desc(smem_u32(tileS(sg)) + kh * 2 * kPanLbo);
+                const uint64_t bd = pan_desc(smem_u32(tileB(sg, i, tt)) + kh * 2 * kPanLbo);
+                const uint32_t acc = ((i & 1) || tt > 0 || kh > 0) ? 1u : 0u;
+                asm volatile(
+                    "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+                        acc_addr),
+                    "l"(ad), "l"(bd), "r"(kUmmaIdesc), "r"(acc)
+                    : "memory");
+              }
+          }
           asm volatile(
               "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                  smem_u32(&acc_full[b]))
+                  smem_u32(&empty[sg]))
               : "memory");
+          if ((i & 1) || i == t.ns - 1) {
+            asm volatile(
+                "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 "
+                "[%0];" ::"r"(smem_u32(&acc_full[b]))
+                : "memory");
+            ++P;
+          }
+        }
       }
       if (!ok) {  // drain the MMAs issued so far before the memory is freed
         failed = 1;
@@ -699,13 +602,42 @@ __global__ void __launch_bounds__(kPanThreads, 1)
         mbar_wait(smem_u32(&drain_bar), 0);
       }
     }
-  } else if (warp >= 4 && warp < 12) {  // S-tile builders: rows 32 w'.., steps of one parity
+  } else if (warp >= 4 && warp < 12) {  // S-tile builders: rows 32 wq.., steps of one parity
     const int wq = (warp - 4) & 3, parity = (warp - 4) >> 2;
-    const int r = 32 * wq + lane;
-    for (int i = parity; i < nsteps; i += 2) {
-      const int sg = i % kPanStages, round = i / kPanStages;
+    const int K = *Kdev;
+    // walk the CTA's steps in order (gs counts them over its units)
+    int64_t u = lo;
+    PanUnit t{};
+    int i = 0, gs = 0;
+    auto settle = [&]() {  // move past finished (or empty) units
+      while (u < hi && i >= t.ns) {
+        u += stride;
+        i = 0;
+        if (u < hi) t = pan_unit(g, u);
+      }
+      return u < hi;
+    };
+    auto advance = [&]() {
+      ++i;
+      ++gs;
+      return settle();
+    };
+    auto row_id = [&]() {  // this lane's dense row of the current step (0 past K)
+      const int q = (t.st0 + i) * kBK + lane;
+      return q < K ? rows[q] : 0;  // padding rows multiply zeros
+    };
+    if (u < hi) t = pan_unit(g, u);
+    bool have = settle();
+    if (have && (gs & 1) != parity) have = advance();
+    int32_t jn = have ? row_id() : 0;
+    while (have) {
+      const int gc = gs, d0 = t.x * 128;
+      const int32_t j = jn;
+      have = advance() && advance();  // this group's next step
+      if (have) jn = row_id();        // in flight while this step is built
+      const int sg = gc % kPanStages, round = gc / kPanStages;
       int ok = 1;
-      if (lane == 0 && i >= kPanStages && !mbar_wait(smem_u32(&empty[sg]), (round - 1) & 1))
+      if (lane == 0 && gc >= kPanStages && !mbar_wait(smem_u32(&empty[sg]), (round - 1) & 1))
         ok = 0;
       ok = __shfl_sync(0xffffffffu, ok, 0);
       if (!ok) failed = 1;
@@ -713,7 +645,6 @@ __global__ void __launch_bounds__(kPanThreads, 1)
       // lane L: the Philox block of dense row k = L, word wq (the signs of
       // rows 32 wq .. 32 wq + 31); transposed, lane L holds the 32 signs of
       // row 32 wq + L over the step's dense rows (bit k)
-      const int32_t j = srows[i * kBK + lane];
       const uint4 x = philox_block(static_cast<uint32_t>(d0 >> 7), static_cast<uint32_t>(j),
                                    stream_id, k0, k1);
       uint32_t v = wq == 0 ? x.x : wq == 1 ? x.y : wq == 2 ? x.z : x.w;
@@ -724,16 +655,16 @@ __global__ void __launch_bounds__(kPanThreads, 1)
         const uint32_t o = __shfl_xor_sync(0xffffffffu, v, sh);
         v = (lane & sh) ? ((v & ~m) | ((o >> sh) & m)) : ((v & m) | ((o & m) << sh));
       }
-      uint8_t* dstS = tileS(sg) + r * 16;
+      uint8_t* dstS = tileS(sg) + (32 * wq + lane) * 16;
       if constexpr (FP8) {
 #pragma unroll
         for (int c = 0; c < 2; ++c) {  // k-chunk c: dense rows 16c .. 16c + 15
           uint32_t wv[4];
 #pragma unroll
-          for (int u = 0; u < 4; ++u) {  // E4M3 +1 = 0x38, -1 = 0xB8
-            const uint32_t b4 = v >> (16 * c + 4 * u);
-            wv[u] = 0x38383838u | ((b4 & 1u) << 7) | ((b4 & 2u) << 14) | ((b4 & 4u) << 21) |
-                    ((b4 & 8u) << 28);
+          for (int w4 = 0; w4 < 4; ++w4) {  // E4M3 +1 = 0x38, -1 = 0xB8
+            const uint32_t b4 = v >> (16 * c + 4 * w4);
+            wv[w4] = 0x38383838u | ((b4 & 1u) << 7) | ((b4 & 2u) << 14) | ((b4 & 4u) << 21) |
+                     ((b4 & 8u) << 28);
           }
           *reinterpret_cast<uint4*>(dstS + c * kPanLbo) = make_uint4(wv[0], wv[1], wv[2], wv[3]);
         }
@@ -742,9 +673,9 @@ __global__ void __launch_bounds__(kPanThreads, 1)
         for (int c = 0; c < 4; ++c) {  // k-chunk c: dense rows 8c .. 8c + 7
           uint32_t wv[4];
 #pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const int ka = 8 * c + 2 * u;
-            wv[u] = pm1_pair((v >> ka) & 1u, (v >> (ka + 1)) & 1u);
+          for (int w4 = 0; w4 < 4; ++w4) {
+            const int ka = 8 * c + 2 * w4;
+            wv[w4] = pm1_pair((v >> ka) & 1u, (v >> (ka + 1)) & 1u);
           }
           *reinterpret_cast<uint4*>(dstS + c * kPanLbo) = make_uint4(wv[0], wv[1], wv[2], wv[3]);
         }
@@ -758,51 +689,74 @@ __global__ void __launch_bounds__(kPanThreads, 1)
     const int rq = warp & 3;
     const uint32_t lanes = static_cast<uint32_t>(32 * rq) << 16;
     bool ok = true;
-    for (int pr = 0; pr < npairs; ++pr) {
-      const int b = pr & 1;
-      int got = 1;
-      if (lane == 0) got = mbar_wait(smem_u32(&acc_full[b]), (pr >> 1) & 1) ? 1 : 0;
-      got = __shfl_sync(0xffffffffu, got, 0);
-      if (!got || failed) {
-        ok = false;
-        failed = 1;
-        break;
+    int P = 0;
+    for (int64_t u = lo; u < hi && ok; u += stride) {
+      const PanUnit t = pan_unit(g, u);
+      const int npairs = (t.ns + 1) / 2;
+      const int r = t.x * 128 + 32 * rq + lane, n0 = t.y * 128;
+      float* dst = out + t.z * split_stride;
+      if (npairs == 0) {  // an empty slice contributes zeros
+        if (!accumulate && r < d)
+          for (int c = n0; c < min(n, n0 + 128); ++c) dst[static_cast<int64_t>(c) * d + r] = 0.f;
+        continue;
       }
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-#pragma unroll 1
-      for (int cc = 0; cc < 4; ++cc) {
-        uint32_t v[32], sm[32];
-        // both loads in flight before one wait
-        tmem_ld32_nowait(tmem + lanes + static_cast<uint32_t>(128 * b + 32 * cc), v);
-        if (pr > 0) tmem_ld32_nowait(tmem + lanes + kPanSums + static_cast<uint32_t>(32 * cc), sm);
-        tmem_wait_ld32(v, sm);
-        if (pr > 0) {
-#pragma unroll
-          for (int jj = 0; jj < 32; ++jj)
-            v[jj] = __float_as_uint(__fadd_rn(__uint_as_float(sm[jj]), __uint_as_float(v[jj])));
+      for (int p = 0; p < npairs; ++p, ++P) {
+        const int b = P & 1;
+        int got = 1;
+        if (lane == 0) got = mbar_wait(smem_u32(&acc_full[b]), (P >> 1) & 1) ? 1 : 0;
+        got = __shfl_sync(0xffffffffu, got, 0);
+        if (!got || failed) {
+          ok = false;
+          failed = 1;
+          break;
         }
-        tmem_st32(tmem + lanes + kPanSums + static_cast<uint32_t>(32 * cc), v);
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll 1
+        for (int cc = 0; cc < 4; ++cc) {
+          uint32_t v[32], sm[32];
+          // both loads in flight before one wait
+          tmem_ld32_nowait(tmem + lanes + static_cast<uint32_t>(128 * b + 32 * cc), v);
+          if (p > 0) tmem_ld32_nowait(tmem + lanes + kPanSums + static_cast<uint32_t>(32 * cc), sm);
+          tmem_wait_ld32(v, sm);
+          if (p > 0) {
+#pragma unroll
+            for (int jj = 0; jj < 32; ++jj)
+              v[jj] = __float_as_uint(__fadd_rn(__uint_as_float(sm[jj]), __uint_as_float(v[jj])));
+          }
+          tmem_st32(tmem + lanes + kPanSums + static_cast<uint32_t>(32 * cc), v);
+        }
+        // the accumulator is free again: the MMAs of the next pair (or unit)
+        // proceed while the unit's sums are stored below
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(&acc_empty[b]));
       }
-      asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-      __syncwarp();
-      if (lane == 0) mbar_arrive(smem_u32(&acc_empty[b]));
-    }
-    if (ok && npairs > 0) {
-      const int r = d0 + 32 * rq + lane;
+      if (!ok) break;
+      // the unit's sums: to A_hat or the slice's copy
 #pragma unroll 1
       for (int cc = 0; cc < 4; ++cc) {
         uint32_t v[32];
-        tmem_ld32(tmem + lanes + kPanSums + static_cast<uint32_t>(32 * cc), v);
-        if (r < d) {
+        tmem_ld32_nowait(tmem + lanes + kPanSums + static_cast<uint32_t>(32 * cc), v);
+        tmem_wait_ld32(v);
+        const int c0 = n0 + 32 * cc;
+        if constexpr (FP8) {  // lane l holds the scale of column c0 + l (2^k: exact)
+          const float sc = c0 + lane < n ? colinv[c0 + lane] : 1.0f;
+#pragma unroll
+          for (int jj = 0; jj < 32; ++jj)
+            v[jj] = __float_as_uint(__uint_as_float(v[jj]) * __shfl_sync(0xffffffffu, sc, jj));
+        }
+        float* o = dst + static_cast<int64_t>(c0) * d + r;
+        if (r < d && c0 + 32 <= n && !accumulate) {  // a full chunk: plain stores
+#pragma unroll
+          for (int jj = 0; jj < 32; ++jj) o[static_cast<int64_t>(jj) * d] = __uint_as_float(v[jj]);
+        } else if (r < d) {
 #pragma unroll
           for (int jj = 0; jj < 32; ++jj) {
-            const int c = n0 + 32 * cc + jj;
-            if (c < n) {
-              float* o = dst + static_cast<int64_t>(c) * d + r;
-              float x = __uint_as_float(v[jj]);
-              if constexpr (FP8) x *= colinv[c];  // exact: a power of two
-              *o = accumulate ? *o + x : x;
+            if (c0 + jj < n) {
+              float* oj = o + static_cast<int64_t>(jj) * d;
+              const float x = __uint_as_float(v[jj]);
+              *oj = accumulate ? *oj + x : x;
             }
           }
         }
@@ -830,12 +784,12 @@ __global__ void k_panel_reduce(int64_t total, int splits, const float* __restric
 
 // The timeout path of mbar_wait on purpose: a fresh mbarrier whose phase
 // nothing completes; the bounded wait gives up and records kStatusTimeout.
-__global__ void k_debug_wait_timeout(int* status, int limit) {
+__global__ void k_debug_wait_timeout(int* status, uint64_t limit_ns) {
   __shared__ __align__(8) uint64_t bar;
   if (threadIdx.x == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar)) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    if (!mbar_wait(smem_u32(&bar), 0, limit)) atomicOr(status, kStatusTimeout);
+    if (!mbar_wait(smem_u32(&bar), 0, limit_ns)) atomicOr(status, kStatusTimeout);
   }
 }
 
@@ -1001,16 +955,6 @@ cudaError_t select_dense_rows(const DenseArgs& a, void* ws, DenseView* out, cuda
   return cudaGetLastError();
 }
 
-// Long panels (and a workspace holding the split-K copies) take the
-// pipelined kernel and the tiled A3 layout.
-static bool panel_kernel_takes(int64_t Kp, const DenseView& v, bool fp8) {
-  // a slice holds at most kPanMaxSliceSteps steps (its row ids sit in
-  // shared memory) and the workspace at most max_splits partial copies;
-  // FP8 panels always take this kernel, BF16 ones from kPanMinKp rows
-  return (fp8 || Kp >= kPanMinKp) && v.max_splits >= 1 &&
-         (Kp / kBK + kPanMaxSliceSteps - 1) / kPanMaxSliceSteps <= v.max_splits;
-}
-
 // Phase 2: the panel's BF16 terms for K dense rows (K <= kmax).
 cudaError_t build_dense_panel(const DenseArgs& a, int32_t K, DenseView* v, cudaStream_t s,
                               int* launches) {
@@ -1021,7 +965,7 @@ cudaError_t build_dense_panel(const DenseArgs& a, int32_t K, DenseView* v, cudaS
     // E4M3 panel: per-column scales from the panel's largest magnitudes,
     // then the two terms in the tiled layout (n padded to 128, 2 bytes per
     // entry)
-    if (!panel_kernel_takes(Kp, *v, true)) return cudaErrorNotSupported;
+    if (Kp < kBK) return cudaErrorNotSupported;
     const unsigned gb = static_cast<unsigned>(
         std::max<int64_t>(1, std::min<int64_t>((a.nnz + 255) / 256, 32LL * num_sms())));
     const unsigned gn = static_cast<unsigned>(
@@ -1051,19 +995,18 @@ cudaError_t build_dense_panel(const DenseArgs& a, int32_t K, DenseView* v, cudaS
     *launches += 3;
     return cudaGetLastError();
   }
-  const int tiled = panel_kernel_takes(Kp, *v, false) ? 1 : 0;
-  cudaError_t e = cudaMemsetAsync(
-      A3, 0, static_cast<size_t>(tiled ? (a.n + 127) / 128 * 128 : a.n) * 3 * Kp * 2, s);
+  cudaError_t e =
+      cudaMemsetAsync(A3, 0, static_cast<size_t>((a.n + 127) / 128 * 128) * 3 * Kp * 2, s);
   if (e != cudaSuccess) return e;
   const int64_t blocks =
       std::max<int64_t>(1, std::min<int64_t>((a.nnz + 255) / 256, 32LL * num_sms()));
   if (a.dtype == 0)
     k_dense_scatter<float><<<static_cast<unsigned>(blocks), 256, 0, s>>>(
-        a.n, a.m, static_cast<int32_t>(Kp), a.nnz, tiled, a.colptr, a.rowidx,
+        a.n, a.m, static_cast<int32_t>(Kp), a.nnz, a.colptr, a.rowidx,
         static_cast<const float*>(a.values), v->didx, A3);
   else
     k_dense_scatter<__nv_bfloat16><<<static_cast<unsigned>(blocks), 256, 0, s>>>(
-        a.n, a.m, static_cast<int32_t>(Kp), a.nnz, tiled, a.colptr, a.rowidx,
+        a.n, a.m, static_cast<int32_t>(Kp), a.nnz, a.colptr, a.rowidx,
         static_cast<const __nv_bfloat16*>(a.values), v->didx, A3);
   ++*launches;
   return cudaGetLastError();
@@ -1089,59 +1032,68 @@ cudaError_t build_dense_rest(const DenseArgs& a, const DenseView& v, cudaStream_
 }
 
 cudaError_t launch_debug_wait_timeout(int* status, cudaStream_t s) {
-  k_debug_wait_timeout<<<1, 32, 0, s>>>(status, 1 << 14);
+  k_debug_wait_timeout<<<1, 32, 0, s>>>(status, 2000000ull);  // 2 ms
   return cudaGetLastError();
 }
 
 cudaError_t launch_tc_gemm(const DenseArgs& a, const DenseView& v, float* Ahat,
                            int accumulate, cudaStream_t s, int* launches) {
-  if (panel_kernel_takes(v.Kp, v, a.fp8 != 0)) {
-    {
-      cudaError_t e;
-      // split-K: about two CTAs per SM, at least four steps per slice
-      const int64_t tiles = static_cast<int64_t>((a.d + 127) / 128) * ((a.n + 127) / 128);
-      const int64_t steps = v.Kp / kBK;
-      const int64_t min_splits = (steps + kPanMaxSliceSteps - 1) / kPanMaxSliceSteps;
-      int64_t splits = (2LL * num_sms() + tiles - 1) / tiles;
-      splits = std::min<int64_t>({splits, v.max_splits, std::max<int64_t>(1, steps / 4)});
-      splits = std::max<int64_t>(splits, min_splits);  // <= max_splits (panel_kernel_takes)
-      const int64_t sps = (steps + splits - 1) / splits;
-      splits = (steps + sps - 1) / sps;  // no empty slice
-      const dim3 grid((a.d + 127) / 128, (a.n + 127) / 128, static_cast<unsigned>(splits));
-      if (grid.y > 65535) return cudaErrorInvalidValue;
-      const size_t smem = kPanSmem + static_cast<size_t>(sps) * kBK * sizeof(int32_t);
-      auto kern = a.fp8 ? k_tc_panel<true> : k_tc_panel<false>;
-      e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               static_cast<int>(smem));
-      if (e != cudaSuccess) return e;
-      const int64_t total = static_cast<int64_t>(a.n) * a.d;
-      float* out = splits > 1 ? v.partial : Ahat;
-      kern<<<grid, kPanThreads, smem, s>>>(
-          a.d, a.n, v.Kp, static_cast<int32_t>(sps), v.rows, v.Kdev,
-          reinterpret_cast<const uint8_t*>(v.A3), v.colscale, out, splits > 1 ? total : 0,
-          splits > 1 ? 0 : accumulate, a.k0, a.k1, a.stream_id, a.status);
-      ++*launches;
-      if ((e = cudaGetLastError()) != cudaSuccess) return e;
-      if (splits > 1) {
-        const int64_t blocks = std::min<int64_t>((total + 255) / 256, 16LL * num_sms());
-        k_panel_reduce<<<static_cast<unsigned>(blocks), 256, 0, s>>>(
-            total, static_cast<int>(splits), v.partial, Ahat, accumulate);
-        ++*launches;
-        e = cudaGetLastError();
+  if (v.Kp < kBK) return cudaErrorInvalidValue;
+  const bool fp8 = a.fp8 != 0;
+  const int64_t sms = num_sms();
+  PanelGrid g{};
+  g.d = a.d;
+  g.n = a.n;
+  g.steps = v.Kp / kBK;
+  g.tiles_d = (a.d + 127) / 128;
+  g.tiles_n = (a.n + 127) / 128;
+  const int64_t tiles = static_cast<int64_t>(g.tiles_d) * g.tiles_n;
+  int64_t splits = 1;
+  if (static_cast<int64_t>(g.steps) * pan_step_bytes(fp8) <= kPanResBytes) {
+    g.resident = 1;  // a short panel: each column tile's B stays in shared memory
+  } else {
+    // split-K by a small cost model in units of one step of one CTA
+    // (about 0.3 us): the busiest CTA's steps plus two a unit, plus each
+    // partial copy of A_hat written and read back at HBM speed
+    const double copy_steps = 2.0 * 4.0 * a.n * static_cast<double>(a.d) / 6.7e12 / 0.3e-6;
+    const int64_t smax = std::max<int64_t>(1, std::min<int64_t>(v.max_splits, g.steps));
+    double best = 1e300;
+    for (int64_t sp = 1; sp <= smax; ++sp) {
+      const int64_t sps = (g.steps + sp - 1) / sp;
+      if ((g.steps + sps - 1) / sps != sp) continue;  // no empty slice
+      const int64_t U = tiles * sp, G = std::min<int64_t>(U, sms);
+      const double cost = static_cast<double>((U + G - 1) / G) * static_cast<double>(sps + 2) +
+                          (sp > 1 ? static_cast<double>(sp) * copy_steps : 0.0);
+      if (cost < best) {
+        best = cost;
+        splits = sp;
       }
-      return e;
     }
   }
-  if (a.fp8) return cudaErrorNotSupported;  // FP8 panels exist only in the pipelined kernel
-  const dim3 grid((a.d + kBM - 1) / kBM, (a.n + kBN - 1) / kBN);
-  if (grid.y > 65535) return cudaErrorInvalidValue;
-  cudaError_t e = cudaFuncSetAttribute(k_tc_umma, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       static_cast<int>(kUmmaSmem));
+  g.sps = static_cast<int32_t>((g.steps + splits - 1) / splits);
+  g.units = tiles * splits;
+  if (g.units >= (int64_t(1) << 31)) return cudaErrorInvalidValue;  // 32-bit unit ids
+  const unsigned grid = static_cast<unsigned>(std::min<int64_t>(g.units, sms));
+  const size_t smem = pan_smem_bytes(fp8, g.resident != 0, g.steps);
+  auto kern = fp8 ? k_tc_panel<true> : k_tc_panel<false>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(smem));
   if (e != cudaSuccess) return e;
-  k_tc_umma<<<grid, kTcThreads, kUmmaSmem, s>>>(a.d, a.n, v.Kp, v.rows, v.Kdev, v.A3, Ahat,
-                                                a.k0, a.k1, a.stream_id, accumulate, a.status);
+  const int64_t total = static_cast<int64_t>(a.n) * a.d;
+  float* out = splits > 1 ? v.partial : Ahat;
+  kern<<<grid, kPanThreads, smem, s>>>(
+      g, v.rows, v.Kdev, reinterpret_cast<const uint8_t*>(v.A3), v.colscale, out,
+      splits > 1 ? total : 0, splits > 1 ? 0 : accumulate, a.k0, a.k1, a.stream_id, a.status);
   ++*launches;
-  return cudaGetLastError();
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (splits > 1) {
+    const int64_t blocks = std::min<int64_t>((total + 255) / 256, 16LL * sms);
+    k_panel_reduce<<<static_cast<unsigned>(blocks), 256, 0, s>>>(
+        total, static_cast<int>(splits), v.partial, Ahat, accumulate);
+    ++*launches;
+    e = cudaGetLastError();
+  }
+  return e;
 }
 
 }  // namespace sk

@@ -455,13 +455,30 @@ def test_tensor_core_panel_only_dense_rows(plan):
 
 @pytest.mark.parametrize("d", [256, 300, 611])
 def test_tensor_core_long_panel_integer_bit_exact(d):
-    """Panels of at least 512 dense rows take the pipelined kernel (TMA A
-    tiles, 256 rows of S per CTA): 760 dense rows, ragged d and n = 301 (the
-    last column tile is mostly past n), integer values: bit-exact."""
+    """A long panel streams its B operand through the stage ring and is split
+    along K: 760 dense rows, ragged d and n = 301 (the last column tile is
+    mostly past n), integer values: bit-exact."""
     A = _dense_rows_matrix(30_400, 301, 40, 0.002, True, seed=37)
     plan = dict(mode=capi.SKETCH_MODE_REGEN, q_tiles=2, split=2, tc_min_row_nnz=100)
     got = gpu_sketch(A, d, "pm1", plan=plan)
     assert np.array_equal(got, oracle_sketch(A, d, "pm1"))
+
+
+def test_tensor_core_resident_panel_many_units_per_cta():
+    """A short panel (100 dense rows) over 24 x 24 tiles of 128 x 128: each
+    CTA keeps a column tile's B operand in shared memory and walks a run of
+    about four units, reloading B where its run crosses into the next
+    column tile; ragged d, integer values: bit-exact on sampled columns
+    (both ends of each crossing included)."""
+    A = _dense_rows_matrix(20_000, 3000, 200, 0.001, True, seed=36)
+    d = 3001
+    plan = dict(mode=capi.SKETCH_MODE_REGEN, q_tiles=4, split=1, tc_min_row_nnz=1000)
+    got = gpu_sketch(A, d, "pm1", plan=plan)
+    rng = np.random.default_rng(36)
+    cols = sorted({0, 127, 128, 255, 256, 1535, 1536, 2943, 2944, 2999} |
+                  set(rng.choice(A.n, size=30, replace=False).tolist()))
+    ref = oracle_sketch(A.columns(cols), d, "pm1")
+    assert np.array_equal(got[:, cols], ref)
 
 
 def test_tensor_core_long_panel_float_tolerance():
@@ -478,12 +495,13 @@ FP8_PLANS = [dict(mode=capi.SKETCH_MODE_REGEN, q_tiles=2, split=2, tc_min_row_nn
 
 
 @pytest.mark.parametrize("plan", FP8_PLANS)
-@pytest.mark.parametrize("every", [97, 40])
+@pytest.mark.parametrize("every", [97, 40, 20])
 def test_fp8_panel_integer_bit_exact(plan, every):
     """FP8 panels: +-1 is exact in E4M3 and integers up to 3 in magnitude
     survive the per-column power-of-two scale and the two-term split, so the
-    sketch stays bit-exact (short panels, and long ones past 512 rows)."""
-    A = _dense_rows_matrix(30_400 if every == 40 else 9000, 300, every, 0.002, True, seed=39)
+    sketch stays bit-exact (93 and 760 dense rows: B resident in shared
+    memory; 1520: streamed and split along K)."""
+    A = _dense_rows_matrix(9000 if every == 97 else 30_400, 300, every, 0.002, True, seed=39)
     for d in (256, 301):
         got = gpu_sketch(A, d, "pm1", plan=plan)
         assert np.array_equal(got, oracle_sketch(A, d, "pm1")), d
