@@ -175,15 +175,14 @@ __global__ void k_dense_scatter(int32_t n, int32_t m, int32_t Kp, int64_t nnz,
   }
 }
 
-// +-1 in BF16 for sign bits b0 (low half) and b1 (high half): 0 -> +1, 1 -> -1
-__device__ __forceinline__ uint32_t pm1_pair(uint32_t b0, uint32_t b1) {
-  return (0x3F80u | (b0 << 15)) | ((0x3F80u | (b1 << 15)) << 16);
-}
-
-// Instruction descriptor of kind::f16: F32 accumulator, BF16 A and B, both
-// K-major, N = 128 (N >> 3 at bit 17), M = 128 (M >> 4 at bit 24).
-constexpr uint32_t kUmmaIdesc =
-    (1u << 4) | (1u << 7) | (1u << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
+// Instruction descriptor of kind::f16: F32 accumulator, BF16 A and B, A (the
+// S tile) MN-major (bit 15), B K-major, N = 128 (N >> 3 at bit 17), M = 128
+// (M >> 4 at bit 24).  The MN-major no-swizzle S tile: 8 (rows of S) x 8
+// (dense rows) core matrices of 8 x 16 B, dense row k's 8 values 16 B, the
+// next group of 8 rows of S 128 B on (the SBO field), the next group of 8
+// dense rows 2048 B on (the LBO field).
+constexpr uint32_t kUmmaIdesc = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) |
+                                ((128u >> 3) << 17) | ((128u >> 4) << 24);
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -226,46 +225,50 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity,
 // One CTA per SM walks a list of units, a unit being a 128 x 128 tile of
 // A_hat (rows of S x columns of A) and one of `splits` slices of the dense
 // rows (split-K; the slices' partial tiles are added in a fixed order
-// afterwards).  Two ways to feed the B operand (the terms of A3):
-//   streaming (long panels): each 32-row step's B block (all terms, one
-//     contiguous block of the tiled A3) is bulk-copied (TMA) into a ring of
-//     kPanStages stages next to that step's S tile; CTA b takes units b,
-//     b + G, ... (G CTAs), so the CTAs running at once share B blocks in L2;
+// afterwards).  Steps of 32 dense rows are counted over the CTA's units.
+// Two rings of shared-memory stages: kPanSStages S tiles, and for long
+// panels kPanBStages B blocks.  Two ways to feed the B operand (the terms of
+// A3):
+//   streaming (long panels): each step's B block (all terms, one contiguous
+//     block of the tiled A3) is bulk-copied (TMA) into the B ring; CTA b
+//     takes units b, b + G, ... (G CTAs), so the CTAs running at once share
+//     B blocks in L2;
 //   resident (short panels, all steps' B of a column tile within
 //     kPanResBytes): a column tile's whole B stays in shared memory while the
 //     CTA works through a contiguous run of units with that column tile (the
-//     row tiles vary fastest), so A3 is read about once per CTA; only the S
-//     tiles go through the ring.
+//     row tiles vary fastest), so A3 is read about once per CTA.
 // Roles (512 threads):
 //   warp 0 (one thread): the bulk copies;
 //   warp 1 (one thread): per step six BF16 MMAs (3 terms x 2 k halves,
 //     M = N = 128, K = 16) or two FP8 ones, into one of two tensor-memory
 //     accumulators, switched every two steps of a unit; commits free the
-//     stage and, every two steps, hand the accumulator to the promoters;
-//   warps 4-11: the +-1 S tiles, warps 4-7 for even steps and 8-11 for odd
-//     ones (steps counted over the CTA's units), 32 rows of S each: lane k
-//     computes the Philox block of the step's dense row k and keeps the
-//     warp's word, a five-stage shuffle transpose gives each lane its row's
-//     32 signs, written as BF16 (or E4M3) +-1 in the no-swizzle K-major
-//     layout; the next step's dense-row id is loaded one step ahead;
+//     stages and, every two steps, hand the accumulator to the promoters;
+//   warps 4-11 (the builders): builder w builds the S tile of every step
+//     s = w (mod 8) into S stage w: lane k computes the Philox block of the
+//     step's dense row k (the signs of all 128 rows of S), four five-stage
+//     shuffle transposes give lane L the 32 signs of rows L, 32 + L, 64 + L
+//     and 96 + L, and a multiply spreads each pair (BF16) or nibble (E4M3)
+//     of signs into +-1 values, written in the no-swizzle K-major layout;
+//     the dense-row id of the builder's next step is loaded a step ahead;
 //   warps 12-15 (the promoters): each finished two-step accumulator is added
 //     with round-to-nearest FP32 additions into running sums in tensor memory
 //     (so the tensor core's truncating accumulation covers only twelve
-//     products per output at a time), then freed; the unit's last one is
-//     added in registers and stored to A_hat (or the slice's partial copy)
-//     directly, while the MMAs of the next unit already run in the other
-//     accumulator.
-// Every mbarrier wait has an iteration limit; on a timeout the CTA records
+//     products per output at a time) and freed; after a unit's last pair the
+//     sums are stored to A_hat (or the slice's partial copy) while the MMAs
+//     of the next unit already run.
+// Every mbarrier wait has a time limit; on a timeout the CTA records
 // kStatusTimeout, drains the MMAs it issued and frees its tensor memory.
 // ---------------------------------------------------------------------------
-constexpr int kPanStages = 4;
+constexpr int kPanSStages = 8;           // one per builder warp
+constexpr int kPanBStages = 4;
+constexpr int kPanBuilders = 8;
 constexpr int kPanThreads = 512;
 constexpr uint32_t kPanLbo = 2048;       // K-direction core-matrix stride
 constexpr uint32_t kPanSbo = 128;        // M/N-direction 8-row-group stride
 constexpr int kPanTileBytes = 8192;      // one 128 x 32 BF16 operand tile
-constexpr int kPanStageBytes = 4 * kPanTileBytes;  // streaming: the S tile + three B tiles
-constexpr int kPanResBytes = 192 * 1024;           // resident: all steps' B of a column tile
+constexpr int kPanResBytes = 160 * 1024; // resident: all steps' B of a column tile
 constexpr uint32_t kPanSums = 256;       // tensor-memory column of the running sums
+constexpr int kPanGroup = 4;             // steps accumulated by the tensor core between promotions
 
 // The unit grid of one launch.
 struct PanelGrid {
@@ -385,17 +388,6 @@ __device__ __forceinline__ void tmem_wait_ld32(uint32_t (&a)[32], uint32_t (&b)[
                :
                : "memory");
 }
-__device__ __forceinline__ void tmem_wait_ld32(uint32_t (&a)[32]) {
-  asm volatile("tcgen05.wait::ld.sync.aligned;"
-               : "+r"(a[0]), "+r"(a[1]), "+r"(a[2]), "+r"(a[3]), "+r"(a[4]), "+r"(a[5]),
-                 "+r"(a[6]), "+r"(a[7]), "+r"(a[8]), "+r"(a[9]), "+r"(a[10]), "+r"(a[11]),
-                 "+r"(a[12]), "+r"(a[13]), "+r"(a[14]), "+r"(a[15]), "+r"(a[16]), "+r"(a[17]),
-                 "+r"(a[18]), "+r"(a[19]), "+r"(a[20]), "+r"(a[21]), "+r"(a[22]), "+r"(a[23]),
-                 "+r"(a[24]), "+r"(a[25]), "+r"(a[26]), "+r"(a[27]), "+r"(a[28]), "+r"(a[29]),
-                 "+r"(a[30]), "+r"(a[31])
-               :
-               : "memory");
-}
 __device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&v)[32]) {
   asm volatile("tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], "
                "{%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, "
@@ -414,8 +406,8 @@ __device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&v)[32
 // (format code 0), both K-major, N = 128, M = 128.
 constexpr uint32_t kUmmaIdescFp8 = (1u << 4) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
 
-// Shared memory of one CTA: the stage ring (S tiles, and B blocks when
-// streaming) and, when resident, one column tile's B for every step.
+// Shared memory of one CTA: the S ring, then the B ring (streaming) or one
+// column tile's B for every step (resident).
 __host__ __device__ constexpr int pan_term_bytes(bool fp8) {
   return fp8 ? kPanTileBytes / 2 : kPanTileBytes;
 }
@@ -423,9 +415,21 @@ __host__ __device__ constexpr int pan_step_bytes(bool fp8) {
   return (fp8 ? 2 : 3) * pan_term_bytes(fp8);
 }
 size_t pan_smem_bytes(bool fp8, bool resident, int steps) {
-  return resident ? static_cast<size_t>(kPanStages) * kPanTileBytes +
-                        static_cast<size_t>(steps) * pan_step_bytes(fp8) + 1024
-                  : static_cast<size_t>(kPanStages) * kPanStageBytes + 1024;
+  const size_t b = resident ? static_cast<size_t>(steps) * pan_step_bytes(fp8)
+                            : static_cast<size_t>(kPanBStages) * pan_step_bytes(fp8);
+  return static_cast<size_t>(kPanSStages) * kPanTileBytes + b + 1024;
+}
+
+// +-1 S words from sign bits (bit set = -1): BF16, the two signs in bits 0
+// and 1 of t go to bits 15 and 31 over 0x3F80 (+1) halves; E4M3, the four
+// signs in bits 0..3 go to bit 7 of each byte over 0x38 (+1) bytes.  The
+// multiplies place every other product bit away from the kept ones, so no
+// carry reaches them.
+__device__ __forceinline__ uint32_t pm1_bf16x2(uint32_t t) {
+  return (((t & 3u) * 0x40008000u) & 0x80008000u) | 0x3F803F80u;
+}
+__device__ __forceinline__ uint32_t pm1_e4m3x4(uint32_t t) {
+  return (((t & 15u) * 0x10204080u) & 0x80808080u) | 0x38383838u;
 }
 
 template <bool FP8>
@@ -438,8 +442,9 @@ __global__ void __launch_bounds__(kPanThreads, 1)
   constexpr int kTermBytes = pan_term_bytes(FP8);
   constexpr uint32_t kTx = pan_step_bytes(FP8);
   extern __shared__ uint8_t sm_raw[];
-  __shared__ __align__(8) uint64_t full[kPanStages], empty[kPanStages], acc_full[2],
-      acc_empty[2], bfull, bempty, drain_bar;
+  __shared__ __align__(8) uint64_t sfull[kPanSStages], sempty[kPanSStages],
+      bfull[kPanBStages], bempty[kPanBStages], acc_full[2], acc_empty[2], rfull, rempty,
+      drain_bar[2];
   __shared__ uint32_t tmem_base;
   __shared__ volatile int failed;  // set by any role whose bounded wait gave up
   uint8_t* base = sm_raw + ((1024u - (smem_u32(sm_raw) & 1023u)) & 1023u);
@@ -448,29 +453,30 @@ __global__ void __launch_bounds__(kPanThreads, 1)
   const bool res = g.resident != 0;
   int64_t lo, hi, stride;
   pan_range(g, lo, hi, stride);
-  // stage sg's S tile; term t of the B operand of step i (resident) or of
-  // the step in stage sg (streaming)
-  auto tileS = [&](int sg) {
-    return base + sg * (res ? kPanTileBytes : kPanStageBytes);
-  };
-  auto tileB = [&](int sg, int i, int t) {
-    return res ? base + kPanStages * kPanTileBytes + i * kTx + t * kTermBytes
-               : base + sg * kPanStageBytes + kPanTileBytes + t * kTermBytes;
+  // S stage sg; term t of the B operand of step i of a unit (resident) or of
+  // the step in B stage bs (streaming)
+  auto tileS = [&](int sg) { return base + sg * kPanTileBytes; };
+  uint8_t* const bbase = base + kPanSStages * kPanTileBytes;
+  auto tileB = [&](int bs, int i, int t) {
+    return bbase + (res ? i : bs) * kTx + t * kTermBytes;
   };
   if (tid == 0) {
     failed = 0;
-    for (int q = 0; q < kPanStages; ++q) {
-      // the builders' four warps, plus the bulk copy with its bytes when streaming
-      mbar_init(smem_u32(&full[q]), res ? 4 : 5);
-      mbar_init(smem_u32(&empty[q]), 1);  // the MMA commit
+    for (int q = 0; q < kPanSStages; ++q) {
+      mbar_init(smem_u32(&sfull[q]), 1);   // the builder warp
+      mbar_init(smem_u32(&sempty[q]), 1);  // the MMA commit
+    }
+    for (int q = 0; q < kPanBStages; ++q) {
+      mbar_init(smem_u32(&bfull[q]), 1);   // the bulk copy with its bytes
+      mbar_init(smem_u32(&bempty[q]), 1);  // the MMA commit
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(smem_u32(&acc_full[b]), 1);   // the MMA commit of a two-step accumulator
       mbar_init(smem_u32(&acc_empty[b]), 4);  // one arrival per promoting warp
     }
-    mbar_init(smem_u32(&bfull), 1);   // resident B: the copies' bytes
-    mbar_init(smem_u32(&bempty), 1);  // resident B: the MMA commit after its last use
-    mbar_init(smem_u32(&drain_bar), 1);
+    mbar_init(smem_u32(&rfull), 1);   // resident B: the copies' bytes
+    mbar_init(smem_u32(&rempty), 2);  // resident B: both MMA threads' commits after its last use
+    for (int b = 0; b < 2; ++b) mbar_init(smem_u32(&drain_bar[b]), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
@@ -491,49 +497,54 @@ __global__ void __launch_bounds__(kPanThreads, 1)
         if (res) {
           if (t.y == yprev) continue;
           // the previous column tile's B is overwritten once its MMAs are done
-          if (loads > 0 && !mbar_wait(smem_u32(&bempty), (loads - 1) & 1)) {
+          if (loads > 0 && !mbar_wait(smem_u32(&rempty), (loads - 1) & 1)) {
             failed = 1;
             break;
           }
-          mbar_arrive_tx(smem_u32(&bfull), static_cast<uint32_t>(g.steps) * kTx);
+          mbar_arrive_tx(smem_u32(&rfull), static_cast<uint32_t>(g.steps) * kTx);
           for (int i = 0; i < g.steps; ++i)
             bulk_load(smem_u32(tileB(0, i, 0)),
                       A3 + (static_cast<int64_t>(t.y) * g.steps + i) * kTx, kTx,
-                      smem_u32(&bfull));
+                      smem_u32(&rfull));
           ++loads;
           yprev = t.y;
           continue;
         }
         for (int i = 0; i < t.ns; ++i, ++gs) {
-          const int sg = gs % kPanStages, round = gs / kPanStages;
-          if (gs >= kPanStages && !mbar_wait(smem_u32(&empty[sg]), (round - 1) & 1)) {
+          const int bs = gs % kPanBStages, round = gs / kPanBStages;
+          if (gs >= kPanBStages && !mbar_wait(smem_u32(&bempty[bs]), (round - 1) & 1)) {
             failed = 1;
             break;
           }
           if (failed) break;
-          mbar_arrive_tx(smem_u32(&full[sg]), kTx);
+          mbar_arrive_tx(smem_u32(&bfull[bs]), kTx);
           // the step's B tiles (all terms) are one contiguous block of A3
-          bulk_load(smem_u32(tileB(sg, 0, 0)),
+          bulk_load(smem_u32(tileB(bs, 0, 0)),
                     A3 + (static_cast<int64_t>(t.y) * g.steps + t.st0 + i) * kTx, kTx,
-                    smem_u32(&full[sg]));
+                    smem_u32(&bfull[bs]));
         }
       }
     }
-  } else if (warp == 1) {
-    if (lane == 0) {  // MMA issuer
+  } else if (warp == 1 || warp == 2) {
+    if (lane == 0) {  // MMA issuers: thread `me` takes the groups P with P % 2 == me
+      const int me = warp - 1;
       bool ok = true;
       int gs = 0, P = 0, loads = 0, yprev = -1;
       for (int64_t u = lo; u < hi && ok; u += stride) {
         const PanUnit t = pan_unit(g, u);
+        if (failed) {
+          ok = false;
+          break;
+        }
         if (res && t.y != yprev) {
-          // free the previous column tile's B once its MMAs finish, then
-          // wait for this one's
+          // free the previous column tile's B once this thread's MMAs on it
+          // finish (both threads commit), then wait for this one's
           if (loads > 0)
             asm volatile(
                 "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 "
-                "[%0];" ::"r"(smem_u32(&bempty))
+                "[%0];" ::"r"(smem_u32(&rempty))
                 : "memory");
-          if (!mbar_wait(smem_u32(&bfull), loads & 1)) {
+          if (!mbar_wait(smem_u32(&rfull), loads & 1)) {
             ok = false;
             break;
           }
@@ -541,22 +552,24 @@ __global__ void __launch_bounds__(kPanThreads, 1)
           yprev = t.y;
         }
         for (int i = 0; i < t.ns; ++i, ++gs) {
-          const int sg = gs % kPanStages, round = gs / kPanStages, b = P & 1;
-          if (failed ||
-              ((i & 1) == 0 && P >= 2 &&
-               !mbar_wait(smem_u32(&acc_empty[b]), ((P >> 1) - 1) & 1)) ||
-              !mbar_wait(smem_u32(&full[sg]), round & 1)) {
+          const int Pi = P + i / kPanGroup;  // the step's group
+          if ((Pi & 1) != me) continue;
+          const int sg = gs % kPanSStages, bs = gs % kPanBStages;
+          if ((i % kPanGroup == 0 && Pi >= 2 &&
+               !mbar_wait(smem_u32(&acc_empty[me]), ((Pi >> 1) - 1) & 1)) ||
+              !mbar_wait(smem_u32(&sfull[sg]), (gs / kPanSStages) & 1) ||
+              (!res && !mbar_wait(smem_u32(&bfull[bs]), (gs / kPanBStages) & 1))) {
             ok = false;
             break;
           }
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-          const uint32_t acc_addr = tmem + static_cast<uint32_t>(128 * b);
+          const uint32_t acc_addr = tmem + static_cast<uint32_t>(128 * me);
           if constexpr (FP8) {
 #pragma unroll
             for (int tt = 0; tt < 2; ++tt) {  // K = 32: the whole step
               const uint64_t ad = pan_desc(smem_u32(tileS(sg)));
-              const uint64_t bd = pan_desc(smem_u32(tileB(sg, i, tt)));
-              const uint32_t acc = ((i & 1) || tt > 0) ? 1u : 0u;
+              const uint64_t bd = pan_desc(smem_u32(tileB(bs, i, tt)));
+              const uint32_t acc = (i % kPanGroup || tt > 0) ? 1u : 0u;
               asm volatile(
                   "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
                   "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(
@@ -570,8 +583,8 @@ __global__ void __launch_bounds__(kPanThreads, 1)
 #pragma unroll
               for (int kh = 0; kh < 2; ++kh) {
                 const uint64_t ad = pan_desc(smem_u32(tileS(sg)) + kh * 2 * kPanLbo);
-                const uint64_t bd = pan_desc(smem_u32(tileB(sg, i, tt)) + kh * 2 * kPanLbo);
-                const uint32_t acc = ((i & 1) || tt > 0 || kh > 0) ? 1u : 0u;
+                const uint64_t bd = pan_desc(smem_u32(tileB(bs, i, tt)) + kh * 2 * kPanLbo);
+                const uint32_t acc = (i % kPanGroup || tt > 0 || kh > 0) ? 1u : 0u;
                 asm volatile(
                     "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
                     "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
@@ -582,108 +595,105 @@ __global__ void __launch_bounds__(kPanThreads, 1)
           }
           asm volatile(
               "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                  smem_u32(&empty[sg]))
+                  smem_u32(&sempty[sg]))
               : "memory");
-          if ((i & 1) || i == t.ns - 1) {
+          if (!res)
             asm volatile(
                 "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 "
-                "[%0];" ::"r"(smem_u32(&acc_full[b]))
+                "[%0];" ::"r"(smem_u32(&bempty[bs]))
                 : "memory");
-            ++P;
-          }
+          if (i % kPanGroup == kPanGroup - 1 || i == t.ns - 1)
+            asm volatile(
+                "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 "
+                "[%0];" ::"r"(smem_u32(&acc_full[me]))
+                : "memory");
         }
+        P += (t.ns + kPanGroup - 1) / kPanGroup;
       }
-      if (!ok) {  // drain the MMAs issued so far before the memory is freed
+      if (!ok) {  // drain the MMAs this thread issued before the memory is freed
         failed = 1;
         asm volatile(
             "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                smem_u32(&drain_bar))
+                smem_u32(&drain_bar[me]))
             : "memory");
-        mbar_wait(smem_u32(&drain_bar), 0);
+        mbar_wait(smem_u32(&drain_bar[me]), 0);
       }
     }
-  } else if (warp >= 4 && warp < 12) {  // S-tile builders: rows 32 wq.., steps of one parity
-    const int wq = (warp - 4) & 3, parity = (warp - 4) >> 2;
+  } else if (warp >= 4 && warp < 4 + kPanBuilders) {  // S-tile builders
+    const int bw = warp - 4;  // builds steps bw, bw + 8, ... into S stage bw
     const int K = *Kdev;
     // walk the CTA's steps in order (gs counts them over its units)
     int64_t u = lo;
     PanUnit t{};
     int i = 0, gs = 0;
-    auto settle = [&]() {  // move past finished (or empty) units
+    auto advance_by = [&](int k) {  // k steps on, past finished (or empty) units
+      i += k;
+      gs += k;
       while (u < hi && i >= t.ns) {
+        i -= t.ns;
         u += stride;
-        i = 0;
         if (u < hi) t = pan_unit(g, u);
       }
       return u < hi;
-    };
-    auto advance = [&]() {
-      ++i;
-      ++gs;
-      return settle();
     };
     auto row_id = [&]() {  // this lane's dense row of the current step (0 past K)
       const int q = (t.st0 + i) * kBK + lane;
       return q < K ? rows[q] : 0;  // padding rows multiply zeros
     };
     if (u < hi) t = pan_unit(g, u);
-    bool have = settle();
-    if (have && (gs & 1) != parity) have = advance();
+    bool have = advance_by(bw);
     int32_t jn = have ? row_id() : 0;
     while (have) {
       const int gc = gs, d0 = t.x * 128;
       const int32_t j = jn;
-      have = advance() && advance();  // this group's next step
-      if (have) jn = row_id();        // in flight while this step is built
-      const int sg = gc % kPanStages, round = gc / kPanStages;
+      have = advance_by(kPanBuilders);  // this builder's next step
+      if (have) jn = row_id();          // in flight while this step is built
+      const int round = gc / kPanSStages;
       int ok = 1;
-      if (lane == 0 && gc >= kPanStages && !mbar_wait(smem_u32(&empty[sg]), (round - 1) & 1))
-        ok = 0;
+      if (lane == 0 && round > 0 && !mbar_wait(smem_u32(&sempty[bw]), (round - 1) & 1)) ok = 0;
       ok = __shfl_sync(0xffffffffu, ok, 0);
       if (!ok) failed = 1;
       if (failed) break;
-      // lane L: the Philox block of dense row k = L, word wq (the signs of
-      // rows 32 wq .. 32 wq + 31); transposed, lane L holds the 32 signs of
-      // row 32 wq + L over the step's dense rows (bit k)
+      // lane k: the Philox block of dense row k, the signs of all 128 rows
       const uint4 x = philox_block(static_cast<uint32_t>(d0 >> 7), static_cast<uint32_t>(j),
                                    stream_id, k0, k1);
-      uint32_t v = wq == 0 ? x.x : wq == 1 ? x.y : wq == 2 ? x.z : x.w;
-#pragma unroll
-      for (int sh = 16; sh > 0; sh >>= 1) {
-        const uint32_t m = sh == 16 ? 0x0000FFFFu : sh == 8 ? 0x00FF00FFu
-                         : sh == 4 ? 0x0F0F0F0Fu : sh == 2 ? 0x33333333u : 0x55555555u;
-        const uint32_t o = __shfl_xor_sync(0xffffffffu, v, sh);
-        v = (lane & sh) ? ((v & ~m) | ((o >> sh) & m)) : ((v & m) | ((o & m) << sh));
-      }
-      uint8_t* dstS = tileS(sg) + (32 * wq + lane) * 16;
       if constexpr (FP8) {
+        // K-major E4M3 tile: four shuffle transposes give lane L the signs
+        // of rows L, 32 + L, 64 + L, 96 + L over the step's dense rows
 #pragma unroll
-        for (int c = 0; c < 2; ++c) {  // k-chunk c: dense rows 16c .. 16c + 15
-          uint32_t wv[4];
+        for (int wq = 0; wq < 4; ++wq) {
+          uint32_t v = wq == 0 ? x.x : wq == 1 ? x.y : wq == 2 ? x.z : x.w;
 #pragma unroll
-          for (int w4 = 0; w4 < 4; ++w4) {  // E4M3 +1 = 0x38, -1 = 0xB8
-            const uint32_t b4 = v >> (16 * c + 4 * w4);
-            wv[w4] = 0x38383838u | ((b4 & 1u) << 7) | ((b4 & 2u) << 14) | ((b4 & 4u) << 21) |
-                     ((b4 & 8u) << 28);
+          for (int sh = 16; sh > 0; sh >>= 1) {
+            const uint32_t m = sh == 16 ? 0x0000FFFFu : sh == 8 ? 0x00FF00FFu
+                             : sh == 4 ? 0x0F0F0F0Fu : sh == 2 ? 0x33333333u : 0x55555555u;
+            const uint32_t o = __shfl_xor_sync(0xffffffffu, v, sh);
+            v = (lane & sh) ? ((v & ~m) | ((o >> sh) & m)) : ((v & m) | ((o & m) << sh));
           }
-          *reinterpret_cast<uint4*>(dstS + c * kPanLbo) = make_uint4(wv[0], wv[1], wv[2], wv[3]);
+          uint8_t* dstS = tileS(bw) + (32 * wq + lane) * 16;
+#pragma unroll
+          for (int c = 0; c < 2; ++c)  // k-chunk c: dense rows 16c .. 16c + 15
+            *reinterpret_cast<uint4*>(dstS + c * kPanLbo) =
+                make_uint4(pm1_e4m3x4(v >> (16 * c)), pm1_e4m3x4(v >> (16 * c + 4)),
+                           pm1_e4m3x4(v >> (16 * c + 8)), pm1_e4m3x4(v >> (16 * c + 12)));
         }
       } else {
+        // MN-major BF16 tile: lane k writes column k (its dense row), 16 B
+        // (8 rows of S) per group of 8 rows, straight from its own block
+        uint8_t* col = tileS(bw) + (lane >> 3) * kPanLbo + (lane & 7) * 16;
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {  // k-chunk c: dense rows 8c .. 8c + 7
-          uint32_t wv[4];
-#pragma unroll
-          for (int w4 = 0; w4 < 4; ++w4) {
-            const int ka = 8 * c + 2 * w4;
-            wv[w4] = pm1_pair((v >> ka) & 1u, (v >> (ka + 1)) & 1u);
-          }
-          *reinterpret_cast<uint4*>(dstS + c * kPanLbo) = make_uint4(wv[0], wv[1], wv[2], wv[3]);
+        for (int mg = 0; mg < 16; ++mg) {
+          const uint32_t w = (mg >> 2) == 0 ? x.x : (mg >> 2) == 1 ? x.y : (mg >> 2) == 2 ? x.z : x.w;
+          const uint32_t s8 = w >> (8 * (mg & 3));  // the signs of rows 8 mg .. 8 mg + 7
+          *reinterpret_cast<uint4*>(col + mg * kPanSbo) =
+              make_uint4(pm1_bf16x2(s8), pm1_bf16x2(s8 >> 2), pm1_bf16x2(s8 >> 4),
+                         pm1_bf16x2(s8 >> 6));
         }
       }
       // generic-proxy writes -> visible to the tensor core, then one arrival
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncwarp();
-      if (lane == 0) mbar_arrive(smem_u32(&full[sg]));
+      if (lane == 0) mbar_arrive(smem_u32(&sfull[bw]));
     }
   } else if (warp >= 12) {  // promoters: lanes 32 (warp & 3) .. of the tile
     const int rq = warp & 3;
@@ -692,15 +702,15 @@ __global__ void __launch_bounds__(kPanThreads, 1)
     int P = 0;
     for (int64_t u = lo; u < hi && ok; u += stride) {
       const PanUnit t = pan_unit(g, u);
-      const int npairs = (t.ns + 1) / 2;
+      const int ngroups = (t.ns + kPanGroup - 1) / kPanGroup;
       const int r = t.x * 128 + 32 * rq + lane, n0 = t.y * 128;
       float* dst = out + t.z * split_stride;
-      if (npairs == 0) {  // an empty slice contributes zeros
+      if (ngroups == 0) {  // an empty slice contributes zeros
         if (!accumulate && r < d)
           for (int c = n0; c < min(n, n0 + 128); ++c) dst[static_cast<int64_t>(c) * d + r] = 0.f;
         continue;
       }
-      for (int p = 0; p < npairs; ++p, ++P) {
+      for (int p = 0; p < ngroups; ++p, ++P) {
         const int b = P & 1;
         int got = 1;
         if (lane == 0) got = mbar_wait(smem_u32(&acc_full[b]), (P >> 1) & 1) ? 1 : 0;
@@ -711,6 +721,7 @@ __global__ void __launch_bounds__(kPanThreads, 1)
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const bool last = p == ngroups - 1;
 #pragma unroll 1
         for (int cc = 0; cc < 4; ++cc) {
           uint32_t v[32], sm[32];
@@ -723,43 +734,37 @@ __global__ void __launch_bounds__(kPanThreads, 1)
             for (int jj = 0; jj < 32; ++jj)
               v[jj] = __float_as_uint(__fadd_rn(__uint_as_float(sm[jj]), __uint_as_float(v[jj])));
           }
-          tmem_st32(tmem + lanes + kPanSums + static_cast<uint32_t>(32 * cc), v);
-        }
-        // the accumulator is free again: the MMAs of the next pair (or unit)
-        // proceed while the unit's sums are stored below
-        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncwarp();
-        if (lane == 0) mbar_arrive(smem_u32(&acc_empty[b]));
-      }
-      if (!ok) break;
-      // the unit's sums: to A_hat or the slice's copy
-#pragma unroll 1
-      for (int cc = 0; cc < 4; ++cc) {
-        uint32_t v[32];
-        tmem_ld32_nowait(tmem + lanes + kPanSums + static_cast<uint32_t>(32 * cc), v);
-        tmem_wait_ld32(v);
-        const int c0 = n0 + 32 * cc;
-        if constexpr (FP8) {  // lane l holds the scale of column c0 + l (2^k: exact)
-          const float sc = c0 + lane < n ? colinv[c0 + lane] : 1.0f;
+          if (!last) {
+            tmem_st32(tmem + lanes + kPanSums + static_cast<uint32_t>(32 * cc), v);
+            continue;
+          }
+          // the unit's sums: to A_hat or the slice's copy
+          const int c0 = n0 + 32 * cc;
+          if constexpr (FP8) {  // lane l holds the scale of column c0 + l (2^k: exact)
+            const float sc = c0 + lane < n ? colinv[c0 + lane] : 1.0f;
 #pragma unroll
-          for (int jj = 0; jj < 32; ++jj)
-            v[jj] = __float_as_uint(__uint_as_float(v[jj]) * __shfl_sync(0xffffffffu, sc, jj));
-        }
-        float* o = dst + static_cast<int64_t>(c0) * d + r;
-        if (r < d && c0 + 32 <= n && !accumulate) {  // a full chunk: plain stores
+            for (int jj = 0; jj < 32; ++jj)
+              v[jj] = __float_as_uint(__uint_as_float(v[jj]) * __shfl_sync(0xffffffffu, sc, jj));
+          }
+          float* o = dst + static_cast<int64_t>(c0) * d + r;
+          if (r < d && c0 + 32 <= n && !accumulate) {  // a full chunk: plain stores
 #pragma unroll
-          for (int jj = 0; jj < 32; ++jj) o[static_cast<int64_t>(jj) * d] = __uint_as_float(v[jj]);
-        } else if (r < d) {
+            for (int jj = 0; jj < 32; ++jj) o[static_cast<int64_t>(jj) * d] = __uint_as_float(v[jj]);
+          } else if (r < d) {
 #pragma unroll
-          for (int jj = 0; jj < 32; ++jj) {
-            if (c0 + jj < n) {
-              float* oj = o + static_cast<int64_t>(jj) * d;
-              const float x = __uint_as_float(v[jj]);
-              *oj = accumulate ? *oj + x : x;
+            for (int jj = 0; jj < 32; ++jj) {
+              if (c0 + jj < n) {
+                float* oj = o + static_cast<int64_t>(jj) * d;
+                const float x = __uint_as_float(v[jj]);
+                *oj = accumulate ? *oj + x : x;
+              }
             }
           }
         }
+        if (!last) asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(&acc_empty[b]));
       }
     }
   }
