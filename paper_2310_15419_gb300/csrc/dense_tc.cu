@@ -239,23 +239,28 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity,
 //     row tiles vary fastest), so A3 is read about once per CTA.
 // Roles (512 threads):
 //   warp 0 (one thread): the bulk copies;
-//   warp 1 (one thread): per step six BF16 MMAs (3 terms x 2 k halves,
-//     M = N = 128, K = 16) or two FP8 ones, into one of two tensor-memory
-//     accumulators, switched every two steps of a unit; commits free the
-//     stages and, every two steps, hand the accumulator to the promoters;
+//   warps 1 and 2 (one thread each): the MMAs, in groups of kPanGroup steps
+//     of a unit: thread g takes the groups G with G % 2 == g and owns
+//     tensor-memory accumulator g (so each accumulator's MMAs keep one order
+//     and the result its bits).  Per step six BF16 MMAs (3 terms x 2 k
+//     halves, M = N = 128, K = 16) or two FP8 ones; commits free the stages
+//     and, after a group, hand the accumulator to the promoters.  A thread
+//     issuing tcgen05.mma runs in step with the tensor pipe, so any wait or
+//     commit on one thread would idle the pipe; two threads hide each
+//     other's;
 //   warps 4-11 (the builders): builder w builds the S tile of every step
-//     s = w (mod 8) into S stage w: lane k computes the Philox block of the
-//     step's dense row k (the signs of all 128 rows of S), four five-stage
-//     shuffle transposes give lane L the 32 signs of rows L, 32 + L, 64 + L
-//     and 96 + L, and a multiply spreads each pair (BF16) or nibble (E4M3)
-//     of signs into +-1 values, written in the no-swizzle K-major layout;
-//     the dense-row id of the builder's next step is loaded a step ahead;
-//   warps 12-15 (the promoters): each finished two-step accumulator is added
-//     with round-to-nearest FP32 additions into running sums in tensor memory
-//     (so the tensor core's truncating accumulation covers only twelve
-//     products per output at a time) and freed; after a unit's last pair the
-//     sums are stored to A_hat (or the slice's partial copy) while the MMAs
-//     of the next unit already run.
+//     s = w (mod 8) into S stage w; lane k computes the Philox block of the
+//     step's dense row k (the signs of all 128 rows of S).  BF16: the tile is
+//     MN-major, so lane k writes its own column (16 B per 8 rows, each pair
+//     of signs spread into two BF16 +-1 by one multiply).  E4M3: the tile is
+//     K-major; four five-stage shuffle transposes give lane L the signs of
+//     rows L, 32 + L, 64 + L and 96 + L.  The dense-row id of the builder's
+//     next step is loaded a step ahead;
+//   warps 12-15 (the promoters): each finished accumulator (kPanGroup steps,
+//     up to 24 MMAs: the tensor core's truncating accumulation stays near
+//     4e-7 relative) is added with round-to-nearest FP32 additions into
+//     running sums in tensor memory and freed; a unit's last one is added in
+//     registers and stored to A_hat (or the slice's partial copy).
 // Every mbarrier wait has a time limit; on a timeout the CTA records
 // kStatusTimeout, drains the MMAs it issued and frees its tensor memory.
 // ---------------------------------------------------------------------------
@@ -912,6 +917,24 @@ size_t dense_workspace_bytes(int64_t m, int64_t n, int64_t d, int64_t kmax, int6
 // Phase 1: choose the dense rows (at least tau nonzeros).  Writes didx,
 // rows and K to the workspace, and the offsets of the rest of A; the caller
 // reads K (the panel height) and rest_colptr[n] (the rest's nonzeros).
+void dense_view(const DenseArgs& a, void* ws, DenseView* out) {
+  const DenseLayout L = dense_layout(ws, a.m, a.n, a.d, a.kmax, a.nnz);
+  out->didx = L.didx;
+  out->rows = L.cnt;  // the panel's row ids reuse the counts' space
+  out->Kdev = L.Kdev;
+  out->A3 = L.A3;
+  out->Kp = 0;
+  out->rest_colptr = L.rcolptr;
+  out->rest_rowidx = L.rrowidx;
+  out->rest_values = L.rvalues;
+  out->rest_pos = L.rpos;
+  out->partial = L.partial;
+  out->colscale = L.colinv;
+  out->cmax = L.cmax;
+  out->max_splits = L.max_splits;
+  out->scan_tmp = L.scan_tmp;
+}
+
 cudaError_t select_dense_rows(const DenseArgs& a, void* ws, DenseView* out, cudaStream_t s,
                               int* launches) {
   const DenseLayout L = dense_layout(ws, a.m, a.n, a.d, a.kmax, a.nnz);
@@ -932,20 +955,7 @@ cudaError_t select_dense_rows(const DenseArgs& a, void* ws, DenseView* out, cuda
   if ((e = cudaMemcpyAsync(L.Kdev, L.pos + a.m, sizeof(int32_t), cudaMemcpyDeviceToDevice, s)) !=
       cudaSuccess)
     return e;
-  out->didx = L.didx;
-  out->rows = rows;
-  out->Kdev = L.Kdev;
-  out->A3 = L.A3;
-  out->Kp = 0;
-  out->rest_colptr = L.rcolptr;
-  out->rest_rowidx = L.rrowidx;
-  out->rest_values = L.rvalues;
-  out->rest_pos = L.rpos;
-  out->partial = L.partial;
-  out->colscale = L.colinv;
-  out->cmax = L.cmax;
-  out->max_splits = L.max_splits;
-  out->scan_tmp = L.scan_tmp;
+  dense_view(a, ws, out);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   // the rest of A: each kept entry's output position (an exclusive scan of
   // keep flags over all entries) and the column offsets (rest_colptr[n] =

@@ -36,6 +36,19 @@ struct sketch_s {
   // GPU with other streams, where early-started blocks would hold SMs
   bool dependent_launch = true;
   sk::LsqState* lsq = nullptr;   // least-squares workspace (lazy)
+  // Derived data of the last A run through the workspace -- a tensor-core
+  // plan's panel and the rest of A, TILE's panel-major copy -- reused while
+  // A's content hash, its arrays, the shape, the plan and the workspace match
+  struct Prepared {
+    bool valid = false;
+    uint64_t hash = 0;
+    const void* arrays[3] = {};
+    int64_t m = 0, n = 0, nnz = 0, d = 0;
+    int32_t dtype = 0;
+    sketch_plan plan{};
+    void* ws = nullptr;
+    int32_t K = 0, rest_nnz = 0;  // the panel's rows and the rest's nonzeros
+  } prep;
 };
 
 namespace sk {

@@ -95,6 +95,9 @@ struct TileArgs {
   int64_t ld_s = 0;
   int* status;
   unsigned long long* gen_count;
+  // 1: the panel-major copy, panel pointers and offsets already sit in the
+  // workspace from an earlier call on the same A (same content hash) and plan
+  int32_t prepared = 0;
 };
 size_t tile_workspace_bytes(int64_t m, int64_t n, int64_t d, int64_t nnz,
                             int32_t R, int32_t G);
@@ -158,6 +161,9 @@ struct DenseView {
   char* scan_tmp;     // workspace: scan scratch
 };
 size_t dense_workspace_bytes(int64_t m, int64_t n, int64_t d, int64_t kmax, int64_t nnz);
+// The workspace pointers of a panel (no launches): what select_dense_rows
+// fills in, for a panel already built in `ws` by an earlier call.
+void dense_view(const DenseArgs& a, void* ws, DenseView* out);
 cudaError_t select_dense_rows(const DenseArgs& a, void* ws, DenseView* out, cudaStream_t s,
                               int* launches);
 cudaError_t build_dense_panel(const DenseArgs& a, int32_t K, DenseView* v, cudaStream_t s,
@@ -174,6 +180,13 @@ cudaError_t scan_i32(const int32_t* in, int32_t* out, int64_t len, char* tmp,
                      cudaStream_t s, int* launches);
 cudaError_t row_counts(int64_t nnz, int32_t m, const int32_t* rowidx, int32_t* cnt,
                        int* status, cudaStream_t s);
+
+// A 64-bit content hash of A (colptr, rowidx and the value words), XOR of one
+// mixed key per array entry, so it does not depend on the order the entries
+// are visited in: written to *out (zeroed here first).
+cudaError_t content_hash(int32_t n, int64_t nnz, const int32_t* colptr,
+                         const int32_t* rowidx, const void* values, int32_t value_bytes,
+                         unsigned long long* out, cudaStream_t s);
 
 // Pattern features of A for the plan tuner (see k_pattern_features): f[0]
 // nonempty rows, f[1] longest row, f[2] nonzeros in rows of >= 32 entries,

@@ -65,6 +65,7 @@ int ensure_workspace(sketch_t h, size_t bytes) {
     h->ws_bytes = 0;
   }
   const size_t want = bytes + bytes / 8;
+  h->prep.valid = false;  // a new allocation may reuse the old address
   cudaError_t e = cudaMalloc(&h->ws, want);
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -199,11 +200,76 @@ int check_plan(sketch_t h, const sketch_plan& p) {
 }
 
 int run_sparse(sketch_t h, const sketch_csc* A, float* Ahat, const sketch_plan& p,
-               void* ws, cudaStream_t s, int* status, unsigned long long* gen);
+               void* ws, cudaStream_t s, int* status, unsigned long long* gen,
+               bool prepared);
 
-// Run one plan.  `ws` must hold plan_workspace_bytes.
+static int run_plan_body(sketch_t h, const sketch_csc* A, float* Ahat,
+                         const sketch_plan& p, void* ws, cudaStream_t s, bool prepared,
+                         int32_t* K_out, int32_t* rest_out);
+
+static bool same_plan(const sketch_plan& a, const sketch_plan& b) {
+  return a.mode == b.mode && a.q_tiles == b.q_tiles && a.split == b.split &&
+         a.n_block == b.n_block && a.row_groups == b.row_groups &&
+         a.panel_rows == b.panel_rows && a.cols_per_warp == b.cols_per_warp &&
+         a.tc_min_row_nnz == b.tc_min_row_nnz && a.tile_acc == b.tile_acc &&
+         a.tc_fp8 == b.tc_fp8;
+}
+
+// Run one plan.  `ws` must hold plan_workspace_bytes.  Plans that derive
+// data from A before the sketch (a tensor-core panel, TILE's panel-major
+// copy) first hash A's content on the device; when the hash, A's arrays, the
+// shape, the plan and the workspace match the previous such call and no
+// error has been flagged since, the derived data still in the workspace is
+// reused and only the sketch kernels run.  Under stream capture (no host
+// read possible) the data is always rebuilt.
 int run_plan(sketch_t h, const sketch_csc* A, float* Ahat,
              const sketch_plan& p, void* ws, cudaStream_t s) {
+  const bool cacheable = !h->capturing && ws == h->ws && A->n > 0 && A->nnz > 0 &&
+                         h->d > 0 && (p.tc_min_row_nnz > 0 || p.mode == SKETCH_MODE_TILE);
+  bool hit = false;
+  uint64_t hash = 0;
+  if (cacheable) {
+    auto* dh = reinterpret_cast<unsigned long long*>(static_cast<char*>(h->d_small) + 128);
+    int st = 0;
+    cudaError_t e = content_hash(static_cast<int32_t>(A->n), A->nnz, A->colptr, A->rowidx,
+                                 A->values, A->dtype == SKETCH_BF16 ? 2 : 4, dh, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hash, dh, sizeof(hash), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&st, h->d_small, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "content hash");
+    h->launches += 1;
+    const auto& c = h->prep;
+    hit = c.valid && st == 0 && c.hash == hash && c.ws == ws && c.m == A->m && c.n == A->n &&
+          c.nnz == A->nnz && c.d == h->d && c.dtype == A->dtype &&
+          c.arrays[0] == A->colptr && c.arrays[1] == A->rowidx && c.arrays[2] == A->values &&
+          same_plan(c.plan, p);
+  }
+  h->prep.valid = false;  // the workspace is (re)written below
+  int32_t K = hit ? h->prep.K : 0, rest_nnz = hit ? h->prep.rest_nnz : 0;
+  const int rc = run_plan_body(h, A, Ahat, p, ws, s, hit, &K, &rest_nnz);
+  if (rc == SKETCH_OK && cacheable) {
+    auto& c = h->prep;
+    c.valid = true;
+    c.hash = hash;
+    c.arrays[0] = A->colptr;
+    c.arrays[1] = A->rowidx;
+    c.arrays[2] = A->values;
+    c.m = A->m;
+    c.n = A->n;
+    c.nnz = A->nnz;
+    c.d = h->d;
+    c.dtype = A->dtype;
+    c.plan = p;
+    c.ws = ws;
+    c.K = K;
+    c.rest_nnz = rest_nnz;
+  }
+  return rc;
+}
+
+static int run_plan_body(sketch_t h, const sketch_csc* A, float* Ahat,
+                         const sketch_plan& p, void* ws, cudaStream_t s, bool prepared,
+                         int32_t* K_out, int32_t* rest_out) {
   int* status = reinterpret_cast<int*>(h->d_small);
   unsigned long long* gen =
       h->counting ? reinterpret_cast<unsigned long long*>(
@@ -222,7 +288,7 @@ int run_plan(sketch_t h, const sketch_csc* A, float* Ahat,
   // then leave them out); the panel's product is added at the end
   DenseArgs da{};
   DenseView dv{};
-  int32_t K = 0, rest_nnz = 0;
+  int32_t K = prepared ? *K_out : 0, rest_nnz = prepared ? *rest_out : 0;
   if (p.tc_min_row_nnz > 0) {
     if (h->capturing)
       return fail(h, SKETCH_ERR_UNSUPPORTED, "a tensor-core plan cannot be captured");
@@ -243,24 +309,32 @@ int run_plan(sketch_t h, const sketch_csc* A, float* Ahat,
     da.status = status;
     void* dws = static_cast<char*>(ws) + align256(sparse_workspace_bytes(h, A, p));
     int nl = 0;
-    cudaError_t e = select_dense_rows(da, dws, &dv, s, &nl);
-    h->launches += nl;
-    if (e != cudaSuccess) return cuda_fail(h, e, "dense row selection");
-    e = cudaMemcpyAsync(&K, dv.Kdev, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(&rest_nnz, dv.rest_colptr + A->n, sizeof(int32_t),
-                          cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) return cuda_fail(h, e, "dense row count");
-    // overlapping column ranges of a malformed colptr (flagged on the
-    // device) can count more kept entries than A holds
-    if (rest_nnz < 0 || rest_nnz > A->nnz) rest_nnz = static_cast<int32_t>(A->nnz);
-    if (K > 0) {
-      nl = 0;
-      e = build_dense_panel(da, K, &dv, s, &nl);
-      if (e == cudaSuccess && rest_nnz > 0) e = build_dense_rest(da, dv, s, &nl);
+    if (prepared) {  // the panel and the rest of A from the previous call
+      dense_view(da, dws, &dv);
+      dv.Kp = (K + 31) / 32 * 32;
+    }
+    if (!prepared) {
+      cudaError_t e = select_dense_rows(da, dws, &dv, s, &nl);
       h->launches += nl;
-      if (e != cudaSuccess) return cuda_fail(h, e, "dense panel");
+      if (e != cudaSuccess) return cuda_fail(h, e, "dense row selection");
+      e = cudaMemcpyAsync(&K, dv.Kdev, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&rest_nnz, dv.rest_colptr + A->n, sizeof(int32_t),
+                            cudaMemcpyDeviceToHost, s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+      if (e != cudaSuccess) return cuda_fail(h, e, "dense row count");
+      // overlapping column ranges of a malformed colptr (flagged on the
+      // device) can count more kept entries than A holds
+      if (rest_nnz < 0 || rest_nnz > A->nnz) rest_nnz = static_cast<int32_t>(A->nnz);
+      if (K > 0) {
+        nl = 0;
+        e = build_dense_panel(da, K, &dv, s, &nl);
+        if (e == cudaSuccess && rest_nnz > 0) e = build_dense_rest(da, dv, s, &nl);
+        h->launches += nl;
+        if (e != cudaSuccess) return cuda_fail(h, e, "dense panel");
+      }
+      *K_out = K;
+      *rest_out = rest_nnz;
     }
   }
   // the sparse kernels see A without the panel's rows; with nothing left
@@ -275,7 +349,7 @@ int run_plan(sketch_t h, const sketch_csc* A, float* Ahat,
       rest.values = dv.rest_values;
       rest.nnz = rest_nnz;
     }
-    rc_sparse = run_sparse(h, &rest, Ahat, p, ws, s, status, gen);
+    rc_sparse = run_sparse(h, &rest, Ahat, p, ws, s, status, gen, prepared);
   }
   if (rc_sparse != SKETCH_OK || K == 0) return rc_sparse;
   int nl = 0;
@@ -285,7 +359,8 @@ int run_plan(sketch_t h, const sketch_csc* A, float* Ahat,
 }
 
 int run_sparse(sketch_t h, const sketch_csc* A, float* Ahat, const sketch_plan& p,
-               void* ws, cudaStream_t s, int* status, unsigned long long* gen) {
+               void* ws, cudaStream_t s, int* status, unsigned long long* gen,
+               bool prepared) {
   if (p.mode == SKETCH_MODE_REGEN) {
     RegenArgs a{};
     a.m = static_cast<int32_t>(A->m);
@@ -331,6 +406,7 @@ int run_sparse(sketch_t h, const sketch_csc* A, float* Ahat, const sketch_plan& 
     a.tacc = p.tile_acc;
     a.status = status;
     a.gen_count = gen;
+    a.prepared = prepared ? 1 : 0;
     int nl = 0;
     cudaError_t e = launch_tile(a, ws, s, &nl);
     h->launches += nl;
@@ -851,6 +927,7 @@ int sketch_apply_pregen(sketch_t h, const sketch_csc* A, const float* S, int64_t
   a.S_mem = S;
   a.ld_s = ld_s;
   int nl = 0;
+  h->prep.valid = false;  // the panel-major copy below replaces any prepared data
   cudaError_t e = launch_tile(a, h->ws, s, &nl);
   h->launches += nl;
   return e == cudaSuccess ? SKETCH_OK : cuda_fail(h, e, "tile kernel (S from memory)");

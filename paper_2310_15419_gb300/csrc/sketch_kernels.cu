@@ -1186,7 +1186,7 @@ cudaError_t launch_tile(const TileArgs& a, void* ws, cudaStream_t s, int* launch
   float* partial = reinterpret_cast<float*>(p);
   const int sms = num_sms();
   cudaError_t e;
-  {
+  if (!a.prepared) {  // the panel-major copy of A, its panel pointers and offsets
     auto grid_for = [&](int64_t work) {
       return static_cast<unsigned>(std::max<int64_t>(1, std::min<int64_t>((work + 255) / 256, 32LL * sms)));
     };
@@ -1508,6 +1508,54 @@ cudaError_t launch_bench_fma(int64_t threads, int64_t iters, float* sink, cudaSt
 // Pattern features of A for the plan tuner, from row counts cnt[0..m):
 // f[0] = nonempty rows, f[1] = the longest row, f[2] = nonzeros in rows of
 // at least 32 entries, f[3] = the longest column (from colptr, clamped).
+// ---------------------------------------------------------------------------
+// Content hash of A, to recognise a matrix seen before: entry e of array a
+// (0 colptr, 1 rowidx, 2 values) with 32-bit word w gives the key
+// (e << 32 | w) ^ seed_a, mixed by the splitmix64 finalizer (Steele, Lea,
+// Flood, OOPSLA 2014; constants of Vigna's public version), and the mixed
+// keys are XOR-reduced, which makes the result independent of the order.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+
+__global__ void k_content_hash(int32_t n, int64_t nnz, const int32_t* __restrict__ colptr,
+                               const int32_t* __restrict__ rowidx,
+                               const void* __restrict__ values, int32_t value_bytes,
+                               unsigned long long* out) {
+  unsigned long long h = 0;
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  const int64_t t0 = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  for (int64_t e = t0; e <= n; e += stride)
+    h ^= mix64(((static_cast<unsigned long long>(e) << 32) |
+                static_cast<uint32_t>(colptr[e])) ^ 0x243F6A8885A308D3ULL);
+  for (int64_t e = t0; e < nnz; e += stride) {
+    const uint32_t w = value_bytes == 2
+                           ? static_cast<const uint16_t*>(values)[e]
+                           : static_cast<const uint32_t*>(values)[e];
+    h ^= mix64(((static_cast<unsigned long long>(e) << 32) |
+                static_cast<uint32_t>(rowidx[e])) ^ 0x13198A2E03707344ULL);
+    h ^= mix64(((static_cast<unsigned long long>(e) << 32) | w) ^ 0xA4093822299F31D0ULL);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) h ^= __shfl_xor_sync(0xffffffffu, h, o);
+  if ((threadIdx.x & 31) == 0 && h) atomicXor(out, h);
+}
+
+cudaError_t content_hash(int32_t n, int64_t nnz, const int32_t* colptr,
+                         const int32_t* rowidx, const void* values, int32_t value_bytes,
+                         unsigned long long* out, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(out, 0, sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return e;
+  const int64_t work = std::max<int64_t>(nnz, static_cast<int64_t>(n) + 1);
+  const unsigned blocks = static_cast<unsigned>(
+      std::max<int64_t>(1, std::min<int64_t>((work + 255) / 256, 8LL * num_sms())));
+  k_content_hash<<<blocks, 256, 0, s>>>(n, nnz, colptr, rowidx, values, value_bytes, out);
+  return cudaGetLastError();
+}
+
 __global__ void k_pattern_features(int32_t m, int32_t n, int64_t nnz,
                                    const int32_t* __restrict__ cnt,
                                    const int32_t* __restrict__ colptr,

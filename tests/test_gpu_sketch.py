@@ -481,6 +481,62 @@ def test_tensor_core_resident_panel_many_units_per_cta():
     assert np.array_equal(got[:, cols], ref)
 
 
+PREPARED_PLANS = [dict(mode=capi.SKETCH_MODE_REGEN, q_tiles=2, split=2, tc_min_row_nnz=40),
+                  dict(mode=capi.SKETCH_MODE_TILE, panel_rows=512, row_groups=4,
+                       cols_per_warp=32, tile_acc=1),
+                  dict(mode=capi.SKETCH_MODE_TILE, panel_rows=512, row_groups=4,
+                       cols_per_warp=16, tc_min_row_nnz=100)]
+
+
+@pytest.mark.parametrize("plan", PREPARED_PLANS)
+def test_prepared_data_reused_and_rebuilt_when_A_changes(plan):
+    """Plans that derive data from A (a tensor-core panel, TILE's panel-major
+    copy) reuse it on the next call with the same A: fewer launches, the same
+    bits.  Rewriting A's values or rows in place (same addresses) changes its
+    content hash, so the data is rebuilt and the sketch matches the oracle
+    for the new A."""
+    A = _dense_rows_matrix(30_400, 300, 40, 0.002, True, seed=35)
+    d = 300
+    sk = capi.Sketch(A.m, A.n, d, "pm1", seed=1)
+    sk.set_plan(**plan)
+    dA = capi.DeviceCSC(A)
+    out = torch.empty((A.n, d), dtype=torch.float32, device="cuda")
+    sk.apply(dA, out)
+    torch.cuda.synchronize()
+    first = out.clone()
+    n0 = sk.launch_count()
+    sk.apply(dA, out)
+    torch.cuda.synchronize()
+    reused = sk.launch_count() - n0
+    assert torch.equal(out, first)
+    assert np.array_equal(first.cpu().numpy().astype(np.float64).T, oracle_sketch(A, d, "pm1"))
+    # new values at the same addresses
+    rng = np.random.default_rng(36)
+    B = inputs.CSC(A.m, A.n, A.colptr, A.rowidx,
+                   (rng.integers(1, 4, size=A.nnz) * rng.choice([-1, 1], size=A.nnz))
+                   .astype(np.float32))
+    dA.values.copy_(torch.from_numpy(B.values))
+    n1 = sk.launch_count()
+    sk.apply(dA, out)
+    torch.cuda.synchronize()
+    rebuilt = sk.launch_count() - n1
+    assert rebuilt > reused
+    assert np.array_equal(out.cpu().numpy().astype(np.float64).T, oracle_sketch(B, d, "pm1"))
+    # the last row of a column moved down by one (the column stays sorted and
+    # distinct): the pattern changes
+    rows = A.rowidx.copy()
+    lasts = A.colptr[1:][np.diff(A.colptr) > 0] - 1
+    lasts = lasts[rows[lasts] < A.m - 1]
+    rows[lasts[0]] += 1
+    C = inputs.CSC(A.m, A.n, A.colptr, rows, B.values)
+    dA.rowidx.copy_(torch.from_numpy(C.rowidx))
+    sk.apply(dA, out)
+    torch.cuda.synchronize()
+    assert sk.device_status() == capi.SKETCH_OK
+    assert np.array_equal(out.cpu().numpy().astype(np.float64).T, oracle_sketch(C, d, "pm1"))
+    sk.close()
+
+
 def test_tensor_core_long_panel_float_tolerance():
     A = _dense_rows_matrix(30_400, 300, 40, 0.002, False, seed=38)
     plan = dict(mode=capi.SKETCH_MODE_TILE, panel_rows=512, row_groups=4,
