@@ -174,8 +174,14 @@ int sketch_get_plan(sketch_t h, const sketch_csc* A, sketch_plan* out,
 
 /* A_hat (device, d x n, ld = d, FP32) = S A.  Eq. (1); kernels follow Alg. 3
  * (REGEN) or Alg. 4 (PANEL) with Alg. 1's outer blocking mapped to the CTA
- * grid.  Asynchronous on `stream`.  The first call for a new shape may tune
- * (synchronously) and may grow the handle's device workspace.
+ * grid.  Asynchronous on `stream`, except that plans deriving data from A (a
+ * tensor-core panel, TILE's panel-major copy) first read a 64-bit content
+ * hash of A back to the host: when it, A's array addresses, the shape, the
+ * plan and the workspace equal those of the handle's previous such call and
+ * no error has been flagged since, the derived data still in the workspace
+ * is reused (A changed in place is recognised by its hash and rebuilt).  The
+ * first call for a new shape may tune (synchronously) and may grow the
+ * handle's device workspace.
  * Errors: SKETCH_ERR_ARG (null pointers, A->m/n differ from the handle,
  * dtype), SKETCH_ERR_UNSUPPORTED (nnz >= 2^31), SKETCH_ERR_OOM,
  * SKETCH_ERR_CUDA. */
