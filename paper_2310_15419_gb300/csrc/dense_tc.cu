@@ -75,14 +75,16 @@ __device__ __forceinline__ int32_t column_of(const int32_t* __restrict__ colptr,
 
 // The t-th BF16 term of A(j, k) for dense rows j (q = didx[j]), one thread
 // per entry (its column by binary search), so the build runs at memory speed
-// however long the columns are.  Layout of A3: each step's three 128-column
-// B tiles contiguous (24 KB) in the operand layout the MMA reads: tile
-// (k >> 7, step q >> 5), term t, k-chunk (q >> 3) & 3, column k & 127, 8
+// however long the columns are.  Layout of A3, for column tiles of
+// 2^lg columns (128, or 256 for short panels): each step's three B tiles
+// contiguous in the operand layout the MMA reads -- tile k >> lg, step
+// q >> 5, term t, k-chunk (q >> 3) & 3, column k within the tile, 8
 // consecutive q -- one bulk copy per step.
-__device__ __forceinline__ int64_t a3_offset(int32_t k, int32_t q, int t, int64_t Kp) {
+__device__ __forceinline__ int64_t a3_offset(int32_t k, int32_t q, int t, int64_t Kp, int lg) {
   const int64_t steps = Kp >> 5;
-  const int64_t tile_step = (static_cast<int64_t>(k >> 7) * steps + (q >> 5)) * 3 + t;
-  return ((tile_step * 4 + ((q >> 3) & 3)) * 128 + (k & 127)) * 8 + (q & 7);
+  const int64_t tile_step = (static_cast<int64_t>(k >> lg) * steps + (q >> 5)) * 3 + t;
+  return ((tile_step * 4 + ((q >> 3) & 3)) * (int64_t(1) << lg) + (k & ((1 << lg) - 1))) * 8 +
+         (q & 7);
 }
 
 // FP8 panels: colinv[k] = 2^(x - 8) for the largest |A(j, k)| over the
@@ -115,18 +117,20 @@ __global__ void k_panel_colscale(int32_t n, const uint32_t* __restrict__ cmax,
   }
 }
 
-// The FP8 panel in the pipelined kernel's tiled layout: for tile k >> 7 and
-// step q >> 5 an 8 KB block of two terms x two 16-byte k-chunks x 128
-// columns; term t of A(j, k) / colinv[k] (E4M3, round to nearest): t = 0 the
-// value, t = 1 its remainder.
-__device__ __forceinline__ int64_t a3_offset_fp8(int32_t k, int32_t q, int t, int64_t Kp) {
+// The FP8 panel in the same tiled layout: for tile k >> lg and step q >> 5
+// a block of two terms x two 16-byte k-chunks x 2^lg columns; term t of
+// A(j, k) / colinv[k] (E4M3, round to nearest): t = 0 the value, t = 1 its
+// remainder.
+__device__ __forceinline__ int64_t a3_offset_fp8(int32_t k, int32_t q, int t, int64_t Kp,
+                                                 int lg) {
   const int64_t steps = Kp >> 5;
-  const int64_t tile_step = (static_cast<int64_t>(k >> 7) * steps + (q >> 5)) * 2 + t;
-  return ((tile_step * 2 + ((q >> 4) & 1)) * 128 + (k & 127)) * 16 + (q & 15);
+  const int64_t tile_step = (static_cast<int64_t>(k >> lg) * steps + (q >> 5)) * 2 + t;
+  return ((tile_step * 2 + ((q >> 4) & 1)) * (int64_t(1) << lg) + (k & ((1 << lg) - 1))) * 16 +
+         (q & 15);
 }
 
 template <typename VT>
-__global__ void k_dense_scatter_fp8(int32_t n, int32_t m, int32_t Kp, int64_t nnz,
+__global__ void k_dense_scatter_fp8(int32_t n, int32_t m, int32_t Kp, int lg, int64_t nnz,
                                     const int32_t* __restrict__ colptr,
                                     const int32_t* __restrict__ rowidx,
                                     const VT* __restrict__ vals,
@@ -144,13 +148,13 @@ __global__ void k_dense_scatter_fp8(int32_t n, int32_t m, int32_t Kp, int64_t nn
     const float a = to_f32(vals[e]) / colinv[k];  // exact: a power of two
     const __nv_fp8_e4m3 t1(a);
     const __nv_fp8_e4m3 t2(a - static_cast<float>(t1));
-    A8[a3_offset_fp8(k, q, 0, Kp)] = t1.__x;
-    A8[a3_offset_fp8(k, q, 1, Kp)] = t2.__x;
+    A8[a3_offset_fp8(k, q, 0, Kp, lg)] = t1.__x;
+    A8[a3_offset_fp8(k, q, 1, Kp, lg)] = t2.__x;
   }
 }
 
 template <typename VT>
-__global__ void k_dense_scatter(int32_t n, int32_t m, int32_t Kp, int64_t nnz,
+__global__ void k_dense_scatter(int32_t n, int32_t m, int32_t Kp, int lg, int64_t nnz,
                                 const int32_t* __restrict__ colptr,
                                 const int32_t* __restrict__ rowidx,
                                 const VT* __restrict__ vals,
@@ -169,20 +173,12 @@ __global__ void k_dense_scatter(int32_t n, int32_t m, int32_t Kp, int64_t nnz,
     const float r1 = a - a1;  // exact
     const float a2 = __bfloat162float(__float2bfloat16_rn(r1));
     const float a3 = r1 - a2;  // exact, fits BF16
-    A3[a3_offset(k, q, 0, Kp)] = bf16_bits(a1);
-    A3[a3_offset(k, q, 1, Kp)] = bf16_bits(a2);
-    A3[a3_offset(k, q, 2, Kp)] = bf16_bits(a3);
+    A3[a3_offset(k, q, 0, Kp, lg)] = bf16_bits(a1);
+    A3[a3_offset(k, q, 1, Kp, lg)] = bf16_bits(a2);
+    A3[a3_offset(k, q, 2, Kp, lg)] = bf16_bits(a3);
   }
 }
 
-// Instruction descriptor of kind::f16: F32 accumulator, BF16 A and B, A (the
-// S tile) MN-major (bit 15), B K-major, N = 128 (N >> 3 at bit 17), M = 128
-// (M >> 4 at bit 24).  The MN-major no-swizzle S tile: 8 (rows of S) x 8
-// (dense rows) core matrices of 8 x 16 B, dense row k's 8 values 16 B, the
-// next group of 8 rows of S 128 B on (the SBO field), the next group of 8
-// dense rows 2048 B on (the LBO field).
-constexpr uint32_t kUmmaIdesc = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) |
-                                ((128u >> 3) << 17) | ((128u >> 4) << 24);
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -226,7 +222,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity,
 // A_hat (rows of S x columns of A) and one of `splits` slices of the dense
 // rows (split-K; the slices' partial tiles are added in a fixed order
 // afterwards).  Steps of 32 dense rows are counted over the CTA's units.
-// Two rings of shared-memory stages: kPanSStages S tiles, and for long
+// Two rings of shared-memory stages: one S tile per builder, and for long
 // panels kPanBStages B blocks.  Two ways to feed the B operand (the terms of
 // A3):
 //   streaming (long panels): each step's B block (all terms, one contiguous
@@ -264,9 +260,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity,
 // Every mbarrier wait has a time limit; on a timeout the CTA records
 // kStatusTimeout, drains the MMAs it issued and frees its tensor memory.
 // ---------------------------------------------------------------------------
-constexpr int kPanSStages = 8;           // one per builder warp
 constexpr int kPanBStages = 4;
-constexpr int kPanBuilders = 8;
 constexpr int kPanThreads = 512;
 constexpr uint32_t kPanLbo = 2048;       // K-direction core-matrix stride
 constexpr uint32_t kPanSbo = 128;        // M/N-direction 8-row-group stride
@@ -274,6 +268,11 @@ constexpr int kPanTileBytes = 8192;      // one 128 x 32 BF16 operand tile
 constexpr int kPanResBytes = 160 * 1024; // resident: all steps' B of a column tile
 constexpr uint32_t kPanSums = 256;       // tensor-memory column of the running sums
 constexpr int kPanGroup = 4;             // steps accumulated by the tensor core between promotions
+// Short panels (at most one group of steps) take 128 x 256 units: the whole
+// unit stays in one accumulator, so two 256-column accumulators fill the
+// tensor memory with no promotion sums needed, and an N = 256 MMA costs what
+// an N = 128 one does.
+__host__ __device__ constexpr bool pan_wide(int64_t Kp) { return Kp / kBK <= kPanGroup; }
 
 // The unit grid of one launch.
 struct PanelGrid {
@@ -317,9 +316,12 @@ __device__ __forceinline__ void pan_range(const PanelGrid& g, int64_t& lo, int64
   }
 }
 
-__device__ __forceinline__ uint64_t pan_desc(uint32_t saddr) {
+// Shared-memory matrix descriptor (no swizzle): `lbo` the K-direction stride
+// between 8-element core-matrix chunks (the rows of an operand tile times
+// 16 B), kPanSbo between 8-row groups.
+__device__ __forceinline__ uint64_t pan_desc(uint32_t saddr, uint32_t lbo = kPanLbo) {
   return static_cast<uint64_t>((saddr >> 4) & 0x3FFFu) |
-         (static_cast<uint64_t>((kPanLbo >> 4) & 0x3FFFu) << 16) |
+         (static_cast<uint64_t>((lbo >> 4) & 0x3FFFu) << 16) |
          (static_cast<uint64_t>((kPanSbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
 }
 
@@ -408,21 +410,39 @@ __device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&v)[32
 // scale colinv.  Same layout rules: 16-byte core-matrix rows, k-chunks
 // 2048 B apart.
 // Instruction descriptor of kind::f8f6f4: F32 accumulator, E4M3 A and B
-// (format code 0), both K-major, N = 128, M = 128.
-constexpr uint32_t kUmmaIdescFp8 = (1u << 4) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
+// (format code 0), both K-major, N = kN, M = 128.
+__host__ __device__ constexpr uint32_t idesc_fp8(uint32_t kN) {
+  return (1u << 4) | ((kN >> 3) << 17) | ((128u >> 4) << 24);
+}
+// Instruction descriptor of kind::f16: F32 accumulator, BF16 A and B, A (the
+// S tile) MN-major (bit 15), B K-major, N = kN (N >> 3 at bit 17), M = 128
+// (M >> 4 at bit 24).  The MN-major no-swizzle S tile: 8 (rows of S) x 8
+// (dense rows) core matrices of 8 x 16 B, dense row k's 8 values 16 B, the
+// next group of 8 rows of S 128 B on (the SBO field), the next group of 8
+// dense rows 2048 B on (the LBO field).
+__host__ __device__ constexpr uint32_t idesc_bf16(uint32_t kN) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | ((kN >> 3) << 17) | ((128u >> 4) << 24);
+}
+
+// Per mode: columns per unit, S stages (= builder warps), promoter warps.
+// Wide units (short panels): 256 columns, 4 builders, 8 promoters (two per
+// tensor-memory lane quarter, 128 columns each); else 128, 8 and 4.
+__host__ __device__ constexpr int pan_cols(bool wide) { return wide ? 256 : 128; }
+__host__ __device__ constexpr int pan_sstages(bool wide) { return wide ? 4 : 8; }
+__host__ __device__ constexpr int pan_promoters(bool wide) { return wide ? 8 : 4; }
 
 // Shared memory of one CTA: the S ring, then the B ring (streaming) or one
 // column tile's B for every step (resident).
-__host__ __device__ constexpr int pan_term_bytes(bool fp8) {
-  return fp8 ? kPanTileBytes / 2 : kPanTileBytes;
+__host__ __device__ constexpr int pan_term_bytes(bool fp8, bool wide) {
+  return (fp8 ? 32 : 64) * pan_cols(wide);
 }
-__host__ __device__ constexpr int pan_step_bytes(bool fp8) {
-  return (fp8 ? 2 : 3) * pan_term_bytes(fp8);
+__host__ __device__ constexpr int pan_step_bytes(bool fp8, bool wide) {
+  return (fp8 ? 2 : 3) * pan_term_bytes(fp8, wide);
 }
-size_t pan_smem_bytes(bool fp8, bool resident, int steps) {
-  const size_t b = resident ? static_cast<size_t>(steps) * pan_step_bytes(fp8)
-                            : static_cast<size_t>(kPanBStages) * pan_step_bytes(fp8);
-  return static_cast<size_t>(kPanSStages) * kPanTileBytes + b + 1024;
+size_t pan_smem_bytes(bool fp8, bool wide, bool resident, int steps) {
+  const size_t b = resident ? static_cast<size_t>(steps) * pan_step_bytes(fp8, wide)
+                            : static_cast<size_t>(kPanBStages) * pan_step_bytes(fp8, wide);
+  return static_cast<size_t>(pan_sstages(wide)) * kPanTileBytes + b + 1024;
 }
 
 // +-1 S words from sign bits (bit set = -1): BF16, the two signs in bits 0
@@ -437,17 +457,23 @@ __device__ __forceinline__ uint32_t pm1_e4m3x4(uint32_t t) {
   return (((t & 15u) * 0x10204080u) & 0x80808080u) | 0x38383838u;
 }
 
-template <bool FP8>
+template <bool FP8, bool WIDE>
 __global__ void __launch_bounds__(kPanThreads, 1)
     k_tc_panel(const PanelGrid g, const int32_t* __restrict__ rows,
                const int32_t* __restrict__ Kdev, const uint8_t* __restrict__ A3,
                const float* __restrict__ colinv, float* __restrict__ out,
                int64_t split_stride, int accumulate, uint32_t k0, uint32_t k1,
                uint32_t stream_id, int* status) {
-  constexpr int kTermBytes = pan_term_bytes(FP8);
-  constexpr uint32_t kTx = pan_step_bytes(FP8);
+  constexpr int kN = pan_cols(WIDE);               // columns of A per unit
+  constexpr int kSSt = pan_sstages(WIDE);          // S stages = builder warps
+  constexpr int kProm = pan_promoters(WIDE);       // promoter warps: the last kProm
+  constexpr int kTermBytes = pan_term_bytes(FP8, WIDE);
+  constexpr uint32_t kTx = pan_step_bytes(FP8, WIDE);
+  constexpr uint32_t kBLbo = 16u * kN;             // B tile: K-direction chunk stride
+  constexpr uint32_t kIdesc = FP8 ? idesc_fp8(kN) : idesc_bf16(kN);
+  static_assert(4 + kSSt <= 16 - kProm, "builders and promoters overlap");
   extern __shared__ uint8_t sm_raw[];
-  __shared__ __align__(8) uint64_t sfull[kPanSStages], sempty[kPanSStages],
+  __shared__ __align__(8) uint64_t sfull[kSSt], sempty[kSSt],
       bfull[kPanBStages], bempty[kPanBStages], acc_full[2], acc_empty[2], rfull, rempty,
       drain_bar[2];
   __shared__ uint32_t tmem_base;
@@ -461,13 +487,13 @@ __global__ void __launch_bounds__(kPanThreads, 1)
   // S stage sg; term t of the B operand of step i of a unit (resident) or of
   // the step in B stage bs (streaming)
   auto tileS = [&](int sg) { return base + sg * kPanTileBytes; };
-  uint8_t* const bbase = base + kPanSStages * kPanTileBytes;
+  uint8_t* const bbase = base + kSSt * kPanTileBytes;
   auto tileB = [&](int bs, int i, int t) {
     return bbase + (res ? i : bs) * kTx + t * kTermBytes;
   };
   if (tid == 0) {
     failed = 0;
-    for (int q = 0; q < kPanSStages; ++q) {
+    for (int q = 0; q < kSSt; ++q) {
       mbar_init(smem_u32(&sfull[q]), 1);   // the builder warp
       mbar_init(smem_u32(&sempty[q]), 1);  // the MMA commit
     }
@@ -477,7 +503,7 @@ __global__ void __launch_bounds__(kPanThreads, 1)
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(smem_u32(&acc_full[b]), 1);   // the MMA commit of a two-step accumulator
-      mbar_init(smem_u32(&acc_empty[b]), 4);  // one arrival per promoting warp
+      mbar_init(smem_u32(&acc_empty[b]), kProm);  // one arrival per promoting warp
     }
     mbar_init(smem_u32(&rfull), 1);   // resident B: the copies' bytes
     mbar_init(smem_u32(&rempty), 2);  // resident B: both MMA threads' commits after its last use
@@ -559,27 +585,27 @@ __global__ void __launch_bounds__(kPanThreads, 1)
         for (int i = 0; i < t.ns; ++i, ++gs) {
           const int Pi = P + i / kPanGroup;  // the step's group
           if ((Pi & 1) != me) continue;
-          const int sg = gs % kPanSStages, bs = gs % kPanBStages;
+          const int sg = gs % kSSt, bs = gs % kPanBStages;
           if ((i % kPanGroup == 0 && Pi >= 2 &&
                !mbar_wait(smem_u32(&acc_empty[me]), ((Pi >> 1) - 1) & 1)) ||
-              !mbar_wait(smem_u32(&sfull[sg]), (gs / kPanSStages) & 1) ||
+              !mbar_wait(smem_u32(&sfull[sg]), (gs / kSSt) & 1) ||
               (!res && !mbar_wait(smem_u32(&bfull[bs]), (gs / kPanBStages) & 1))) {
             ok = false;
             break;
           }
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-          const uint32_t acc_addr = tmem + static_cast<uint32_t>(128 * me);
+          const uint32_t acc_addr = tmem + static_cast<uint32_t>(kN * me);
           if constexpr (FP8) {
 #pragma unroll
             for (int tt = 0; tt < 2; ++tt) {  // K = 32: the whole step
               const uint64_t ad = pan_desc(smem_u32(tileS(sg)));
-              const uint64_t bd = pan_desc(smem_u32(tileB(bs, i, tt)));
+              const uint64_t bd = pan_desc(smem_u32(tileB(bs, i, tt)), kBLbo);
               const uint32_t acc = (i % kPanGroup || tt > 0) ? 1u : 0u;
               asm volatile(
                   "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
                   "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(
                       acc_addr),
-                  "l"(ad), "l"(bd), "r"(kUmmaIdescFp8), "r"(acc)
+                  "l"(ad), "l"(bd), "r"(kIdesc), "r"(acc)
                   : "memory");
             }
           } else {
@@ -588,13 +614,13 @@ __global__ void __launch_bounds__(kPanThreads, 1)
 #pragma unroll
               for (int kh = 0; kh < 2; ++kh) {
                 const uint64_t ad = pan_desc(smem_u32(tileS(sg)) + kh * 2 * kPanLbo);
-                const uint64_t bd = pan_desc(smem_u32(tileB(bs, i, tt)) + kh * 2 * kPanLbo);
+                const uint64_t bd = pan_desc(smem_u32(tileB(bs, i, tt)) + kh * 2 * kBLbo, kBLbo);
                 const uint32_t acc = (i % kPanGroup || tt > 0 || kh > 0) ? 1u : 0u;
                 asm volatile(
                     "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
                     "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
                         acc_addr),
-                    "l"(ad), "l"(bd), "r"(kUmmaIdesc), "r"(acc)
+                    "l"(ad), "l"(bd), "r"(kIdesc), "r"(acc)
                     : "memory");
               }
           }
@@ -624,8 +650,8 @@ __global__ void __launch_bounds__(kPanThreads, 1)
         mbar_wait(smem_u32(&drain_bar[me]), 0);
       }
     }
-  } else if (warp >= 4 && warp < 4 + kPanBuilders) {  // S-tile builders
-    const int bw = warp - 4;  // builds steps bw, bw + 8, ... into S stage bw
+  } else if (warp >= 4 && warp < 4 + kSSt) {  // S-tile builders
+    const int bw = warp - 4;  // builds steps bw, bw + kSSt, ... into S stage bw
     const int K = *Kdev;
     // walk the CTA's steps in order (gs counts them over its units)
     int64_t u = lo;
@@ -651,9 +677,9 @@ __global__ void __launch_bounds__(kPanThreads, 1)
     while (have) {
       const int gc = gs, d0 = t.x * 128;
       const int32_t j = jn;
-      have = advance_by(kPanBuilders);  // this builder's next step
+      have = advance_by(kSSt);  // this builder's next step
       if (have) jn = row_id();          // in flight while this step is built
-      const int round = gc / kPanSStages;
+      const int round = gc / kSSt;
       int ok = 1;
       if (lane == 0 && round > 0 && !mbar_wait(smem_u32(&sempty[bw]), (round - 1) & 1)) ok = 0;
       ok = __shfl_sync(0xffffffffu, ok, 0);
@@ -700,19 +726,21 @@ __global__ void __launch_bounds__(kPanThreads, 1)
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_u32(&sfull[bw]));
     }
-  } else if (warp >= 12) {  // promoters: lanes 32 (warp & 3) .. of the tile
+  } else if (warp >= 16 - kProm) {  // promoters: lanes 32 (warp & 3) .., a column half
     const int rq = warp & 3;
+    const int c_lo = 4 * ((warp - (16 - kProm)) >> 2);  // first 32-column chunk
     const uint32_t lanes = static_cast<uint32_t>(32 * rq) << 16;
     bool ok = true;
     int P = 0;
     for (int64_t u = lo; u < hi && ok; u += stride) {
       const PanUnit t = pan_unit(g, u);
       const int ngroups = (t.ns + kPanGroup - 1) / kPanGroup;
-      const int r = t.x * 128 + 32 * rq + lane, n0 = t.y * 128;
+      const int r = t.x * 128 + 32 * rq + lane, n0 = t.y * kN;
       float* dst = out + t.z * split_stride;
       if (ngroups == 0) {  // an empty slice contributes zeros
         if (!accumulate && r < d)
-          for (int c = n0; c < min(n, n0 + 128); ++c) dst[static_cast<int64_t>(c) * d + r] = 0.f;
+          for (int c = n0 + 32 * c_lo; c < min(n, n0 + 32 * c_lo + 128); ++c)
+            dst[static_cast<int64_t>(c) * d + r] = 0.f;
         continue;
       }
       for (int p = 0; p < ngroups; ++p, ++P) {
@@ -727,19 +755,21 @@ __global__ void __launch_bounds__(kPanThreads, 1)
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const bool last = p == ngroups - 1;
+        // (wide units are one group each, so they never touch the sums)
 #pragma unroll 1
-        for (int cc = 0; cc < 4; ++cc) {
+        for (int cc = c_lo; cc < c_lo + 4; ++cc) {
           uint32_t v[32], sm[32];
           // both loads in flight before one wait
-          tmem_ld32_nowait(tmem + lanes + static_cast<uint32_t>(128 * b + 32 * cc), v);
-          if (p > 0) tmem_ld32_nowait(tmem + lanes + kPanSums + static_cast<uint32_t>(32 * cc), sm);
+          tmem_ld32_nowait(tmem + lanes + static_cast<uint32_t>(kN * b + 32 * cc), v);
+          if (!WIDE && p > 0)
+            tmem_ld32_nowait(tmem + lanes + kPanSums + static_cast<uint32_t>(32 * cc), sm);
           tmem_wait_ld32(v, sm);
-          if (p > 0) {
+          if (!WIDE && p > 0) {
 #pragma unroll
             for (int jj = 0; jj < 32; ++jj)
               v[jj] = __float_as_uint(__fadd_rn(__uint_as_float(sm[jj]), __uint_as_float(v[jj])));
           }
-          if (!last) {
+          if (!WIDE && !last) {
             tmem_st32(tmem + lanes + kPanSums + static_cast<uint32_t>(32 * cc), v);
             continue;
           }
@@ -844,7 +874,8 @@ DenseLayout dense_layout(void* ws, int64_t m, int64_t n, int64_t d, int64_t kmax
   L.didx = reinterpret_cast<int32_t*>(take((m + 1) * sizeof(int32_t)));
   L.Kdev = reinterpret_cast<int32_t*>(take(sizeof(int32_t) * 64));
   const int64_t Kp = (kmax + kBK - 1) / kBK * kBK;
-  L.A3 = reinterpret_cast<uint16_t*>(take(static_cast<size_t>((n + 127) / 128 * 128) * 3 * Kp * 2));
+  // n padded to the widest column tile (256)
+  L.A3 = reinterpret_cast<uint16_t*>(take(static_cast<size_t>((n + 255) / 256 * 256) * 3 * Kp * 2));
   L.scan_tmp = take(static_cast<size_t>(scan_bytes_for(std::max(std::max(m, n), nnz) + 1)));
   L.rpos = reinterpret_cast<int32_t*>(take((std::max<int64_t>(1, nnz) + 1) * sizeof(int32_t)));
   L.rcolptr = reinterpret_cast<int32_t*>(take((n + 1) * sizeof(int32_t)));
@@ -978,16 +1009,17 @@ cudaError_t build_dense_panel(const DenseArgs& a, int32_t K, DenseView* v, cudaS
   uint16_t* A3 = const_cast<uint16_t*>(v->A3);
   if (a.fp8) {
     // E4M3 panel: per-column scales from the panel's largest magnitudes,
-    // then the two terms in the tiled layout (n padded to 128, 2 bytes per
-    // entry)
+    // then the two terms in the tiled layout (n padded to the tile width,
+    // 2 bytes per entry)
     if (Kp < kBK) return cudaErrorNotSupported;
+    const int lg = pan_wide(Kp) ? 8 : 7;
     const unsigned gb = static_cast<unsigned>(
         std::max<int64_t>(1, std::min<int64_t>((a.nnz + 255) / 256, 32LL * num_sms())));
     const unsigned gn = static_cast<unsigned>(
         std::max<int64_t>(1, std::min<int64_t>((a.n + 255) / 256, 32LL * num_sms())));
     cudaError_t e = cudaMemsetAsync(v->cmax, 0, static_cast<size_t>(a.n) * sizeof(uint32_t), s);
     if (e == cudaSuccess)
-      e = cudaMemsetAsync(A3, 0, static_cast<size_t>((a.n + 127) / 128 * 128) * Kp * 2, s);
+      e = cudaMemsetAsync(A3, 0, static_cast<size_t>(((a.n + (1 << lg) - 1) >> lg) << lg) * Kp * 2, s);
     if (e != cudaSuccess) return e;
     if (a.dtype == 0)
       k_panel_colmax<float><<<gb, 256, 0, s>>>(a.n, a.m, a.nnz, a.colptr, a.rowidx,
@@ -1001,27 +1033,28 @@ cudaError_t build_dense_panel(const DenseArgs& a, int32_t K, DenseView* v, cudaS
     uint8_t* A8 = reinterpret_cast<uint8_t*>(A3);
     if (a.dtype == 0)
       k_dense_scatter_fp8<float><<<gb, 256, 0, s>>>(
-          a.n, a.m, static_cast<int32_t>(Kp), a.nnz, a.colptr, a.rowidx,
+          a.n, a.m, static_cast<int32_t>(Kp), lg, a.nnz, a.colptr, a.rowidx,
           static_cast<const float*>(a.values), v->didx, v->colscale, A8);
     else
       k_dense_scatter_fp8<__nv_bfloat16><<<gb, 256, 0, s>>>(
-          a.n, a.m, static_cast<int32_t>(Kp), a.nnz, a.colptr, a.rowidx,
+          a.n, a.m, static_cast<int32_t>(Kp), lg, a.nnz, a.colptr, a.rowidx,
           static_cast<const __nv_bfloat16*>(a.values), v->didx, v->colscale, A8);
     *launches += 3;
     return cudaGetLastError();
   }
+  const int lg = pan_wide(Kp) ? 8 : 7;
   cudaError_t e =
-      cudaMemsetAsync(A3, 0, static_cast<size_t>((a.n + 127) / 128 * 128) * 3 * Kp * 2, s);
+      cudaMemsetAsync(A3, 0, static_cast<size_t>(((a.n + (1 << lg) - 1) >> lg) << lg) * 3 * Kp * 2, s);
   if (e != cudaSuccess) return e;
   const int64_t blocks =
       std::max<int64_t>(1, std::min<int64_t>((a.nnz + 255) / 256, 32LL * num_sms()));
   if (a.dtype == 0)
     k_dense_scatter<float><<<static_cast<unsigned>(blocks), 256, 0, s>>>(
-        a.n, a.m, static_cast<int32_t>(Kp), a.nnz, a.colptr, a.rowidx,
+        a.n, a.m, static_cast<int32_t>(Kp), lg, a.nnz, a.colptr, a.rowidx,
         static_cast<const float*>(a.values), v->didx, A3);
   else
     k_dense_scatter<__nv_bfloat16><<<static_cast<unsigned>(blocks), 256, 0, s>>>(
-        a.n, a.m, static_cast<int32_t>(Kp), a.nnz, a.colptr, a.rowidx,
+        a.n, a.m, static_cast<int32_t>(Kp), lg, a.nnz, a.colptr, a.rowidx,
         static_cast<const __nv_bfloat16*>(a.values), v->didx, A3);
   ++*launches;
   return cudaGetLastError();
@@ -1060,11 +1093,14 @@ cudaError_t launch_tc_gemm(const DenseArgs& a, const DenseView& v, float* Ahat,
   g.d = a.d;
   g.n = a.n;
   g.steps = v.Kp / kBK;
+  // a panel of at most one group: 128 x 256 units (the layout build_dense_panel chose)
+  const bool wide = pan_wide(v.Kp);
+  const int kN = pan_cols(wide);
   g.tiles_d = (a.d + 127) / 128;
-  g.tiles_n = (a.n + 127) / 128;
+  g.tiles_n = (a.n + kN - 1) / kN;
   const int64_t tiles = static_cast<int64_t>(g.tiles_d) * g.tiles_n;
   int64_t splits = 1;
-  if (static_cast<int64_t>(g.steps) * pan_step_bytes(fp8) <= kPanResBytes) {
+  if (wide || static_cast<int64_t>(g.steps) * pan_step_bytes(fp8, false) <= kPanResBytes) {
     g.resident = 1;  // a short panel: each column tile's B stays in shared memory
   } else {
     // split-K by a small cost model in units of one step of one CTA
@@ -1089,8 +1125,9 @@ cudaError_t launch_tc_gemm(const DenseArgs& a, const DenseView& v, float* Ahat,
   g.units = tiles * splits;
   if (g.units >= (int64_t(1) << 31)) return cudaErrorInvalidValue;  // 32-bit unit ids
   const unsigned grid = static_cast<unsigned>(std::min<int64_t>(g.units, sms));
-  const size_t smem = pan_smem_bytes(fp8, g.resident != 0, g.steps);
-  auto kern = fp8 ? k_tc_panel<true> : k_tc_panel<false>;
+  const size_t smem = pan_smem_bytes(fp8, wide, g.resident != 0, g.steps);
+  auto kern = fp8 ? (wide ? k_tc_panel<true, true> : k_tc_panel<true, false>)
+                  : (wide ? k_tc_panel<false, true> : k_tc_panel<false, false>);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(smem));
   if (e != cudaSuccess) return e;

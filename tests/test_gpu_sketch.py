@@ -427,8 +427,11 @@ def test_tensor_core_panel_integer_bit_exact(plan):
 
 
 @pytest.mark.parametrize("plan", TC_PLANS)
-def test_tensor_core_panel_float_tolerance(plan):
-    A = _dense_rows_matrix(9000, 300, 50, 0.003, False, seed=32)
+@pytest.mark.parametrize("every", [50, 97])
+def test_tensor_core_panel_float_tolerance(plan, every):
+    """U(-1,1) values: 180 dense rows (two groups of steps, promoted sums) and
+    93 (one group: 128 x 256 units, the whole unit in one accumulator)."""
+    A = _dense_rows_matrix(9000, 300, every, 0.003, False, seed=32)
     ref = oracle_sketch(A, 301, "pm1")
     got = gpu_sketch(A, 301, "pm1", plan=plan)
     assert rel_fro(got, ref) <= TOL
