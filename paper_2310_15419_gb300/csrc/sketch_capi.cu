@@ -100,7 +100,21 @@ sketch_plan tile_plan(const sketch_s* h, const sketch_csc* A, int32_t R, int32_t
   int64_t g_acc = static_cast<int64_t>(std::ceil(avg_col / 512.0));
   int64_t g = std::max<int64_t>({1, g_fill, g_acc});
   g = std::min<int64_t>({g, P, 4096});
-  p.row_groups = static_cast<int32_t>(std::max<int64_t>(1, g));
+  // One CTA per SM: among g .. 2g row groups take the one whose last wave
+  // of CTAs is fullest (g = 20 on 94 row tiles leaves the 13th wave 37%
+  // full; g = 21 fills it), the smallest on ties
+  const int64_t slots = static_cast<int64_t>(per_sm) * num_sms();
+  int64_t best_g = g;
+  double best_fill = 0.0;
+  for (int64_t c = g; c <= std::min<int64_t>({2 * g, P, 4096}); ++c) {
+    const int64_t units = tiles * cblocks * c;
+    const double fill = double(units) / double(((units + slots - 1) / slots) * slots);
+    if (fill > best_fill + 1e-9) {
+      best_fill = fill;
+      best_g = c;
+    }
+  }
+  p.row_groups = static_cast<int32_t>(std::max<int64_t>(1, best_g));
   return p;
 }
 
