@@ -244,9 +244,10 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity,
 //     issuing tcgen05.mma runs in step with the tensor pipe, so any wait or
 //     commit on one thread would idle the pipe; two threads hide each
 //     other's;
-//   warps 4-11 (the builders): builder w builds the S tile of every step
-//     s = w (mod 8) into S stage w; lane k computes the Philox block of the
-//     step's dense row k (the signs of all 128 rows of S).  BF16: the tile is
+//   warps 4-11 (the builders): builder w fills S stage w, half of the
+//     stages serving each MMA thread (see PanWalk); lane k computes the
+//     Philox block of the step's dense row k (the signs of all 128 rows of
+//     S).  BF16: the tile is
 //     MN-major, so lane k writes its own column (16 B per 8 rows, each pair
 //     of signs spread into two BF16 +-1 by one multiply).  E4M3: the tile is
 //     K-major; four five-stage shuffle transposes give lane L the signs of
@@ -314,6 +315,54 @@ __device__ __forceinline__ void pan_range(const PanelGrid& g, int64_t& lo, int64
     hi = g.units;
     stride = G;
   }
+}
+
+// The CTA's steps in order, each with its group (a unit's steps in groups of
+// kPanGroup; MMA thread g & 1 takes group g) and its index among that MMA
+// thread's steps.  That index places the step in its MMA thread's half of
+// each stage ring, so every stage has one filler and one consumer, both
+// in order: a parity wait then never mistakes a phase two rounds old for
+// the one it waits on (which it could if the two MMA threads shared
+// stages).  Every role walks the same sequence.
+struct PanWalk {
+  int64_t u, hi, stride;
+  PanUnit t;
+  int i;       // step within the unit
+  int P;       // groups before this unit
+  int c0, c1;  // steps of MMA thread 0 and 1 before this one
+  bool valid;
+  __device__ __forceinline__ int cnt(int th) const { return th ? c1 : c0; }
+};
+__device__ __forceinline__ void walk_settle(const PanelGrid& g, PanWalk& w) {
+  while (w.u < w.hi && w.i >= w.t.ns) {
+    w.P += (w.t.ns + kPanGroup - 1) / kPanGroup;
+    w.u += w.stride;
+    w.i = 0;
+    if (w.u < w.hi) w.t = pan_unit(g, w.u);
+  }
+  w.valid = w.u < w.hi;
+}
+__device__ __forceinline__ void walk_init(const PanelGrid& g, PanWalk& w, int64_t lo,
+                                          int64_t hi, int64_t stride) {
+  w.u = lo;
+  w.hi = hi;
+  w.stride = stride;
+  w.i = 0;
+  w.P = 0;
+  w.c0 = w.c1 = 0;
+  w.t = PanUnit{0, 0, 0, 0, 0};
+  if (lo < hi) w.t = pan_unit(g, lo);
+  walk_settle(g, w);
+}
+__device__ __forceinline__ int walk_group(const PanWalk& w) { return w.P + w.i / kPanGroup; }
+__device__ __forceinline__ int walk_thread(const PanWalk& w) { return walk_group(w) & 1; }
+__device__ __forceinline__ void walk_next(const PanelGrid& g, PanWalk& w) {
+  if (walk_thread(w))
+    ++w.c1;
+  else
+    ++w.c0;
+  ++w.i;
+  walk_settle(g, w);
 }
 
 // Shared-memory matrix descriptor (no swizzle): `lbo` the K-direction stride
@@ -466,6 +515,8 @@ __global__ void __launch_bounds__(kPanThreads, 1)
                uint32_t stream_id, int* status) {
   constexpr int kN = pan_cols(WIDE);               // columns of A per unit
   constexpr int kSSt = pan_sstages(WIDE);          // S stages = builder warps
+  constexpr int kSHalf = kSSt / 2;                 // S stages of each MMA thread
+  constexpr int kBHalf = kPanBStages / 2;          // B stages of each MMA thread (streaming)
   constexpr int kProm = pan_promoters(WIDE);       // promoter warps: the last kProm
   constexpr int kTermBytes = pan_term_bytes(FP8, WIDE);
   constexpr uint32_t kTx = pan_step_bytes(FP8, WIDE);
@@ -522,10 +573,10 @@ __global__ void __launch_bounds__(kPanThreads, 1)
 
   if (warp == 0) {
     if (lane == 0) {  // bulk copies of the B operand
-      int gs = 0, loads = 0, yprev = -1;
-      for (int64_t u = lo; u < hi && !failed; u += stride) {
-        const PanUnit t = pan_unit(g, u);
-        if (res) {
+      if (res) {
+        int loads = 0, yprev = -1;
+        for (int64_t u = lo; u < hi && !failed; u += stride) {
+          const PanUnit t = pan_unit(g, u);
           if (t.y == yprev) continue;
           // the previous column tile's B is overwritten once its MMAs are done
           if (loads > 0 && !mbar_wait(smem_u32(&rempty), (loads - 1) & 1)) {
@@ -539,107 +590,113 @@ __global__ void __launch_bounds__(kPanThreads, 1)
                       smem_u32(&rfull));
           ++loads;
           yprev = t.y;
-          continue;
         }
-        for (int i = 0; i < t.ns; ++i, ++gs) {
-          const int bs = gs % kPanBStages, round = gs / kPanBStages;
-          if (gs >= kPanBStages && !mbar_wait(smem_u32(&bempty[bs]), (round - 1) & 1)) {
+      } else {
+        // each step's B block into its MMA thread's half of the B ring
+        PanWalk w;
+        walk_init(g, w, lo, hi, stride);
+        for (; w.valid && !failed; walk_next(g, w)) {
+          const int th = walk_thread(w), c = w.cnt(th);
+          const int bs = th * kBHalf + c % kBHalf, round = c / kBHalf;
+          if (round > 0 && !mbar_wait(smem_u32(&bempty[bs]), (round - 1) & 1)) {
             failed = 1;
             break;
           }
-          if (failed) break;
           mbar_arrive_tx(smem_u32(&bfull[bs]), kTx);
           // the step's B tiles (all terms) are one contiguous block of A3
           bulk_load(smem_u32(tileB(bs, 0, 0)),
-                    A3 + (static_cast<int64_t>(t.y) * g.steps + t.st0 + i) * kTx, kTx,
+                    A3 + (static_cast<int64_t>(w.t.y) * g.steps + w.t.st0 + w.i) * kTx, kTx,
                     smem_u32(&bfull[bs]));
         }
       }
     }
   } else if (warp == 1 || warp == 2) {
-    if (lane == 0) {  // MMA issuers: thread `me` takes the groups P with P % 2 == me
+    if (lane == 0) {  // MMA issuers: thread `me` takes the groups G with G % 2 == me
       const int me = warp - 1;
       bool ok = true;
-      int gs = 0, P = 0, loads = 0, yprev = -1;
-      for (int64_t u = lo; u < hi && ok; u += stride) {
-        const PanUnit t = pan_unit(g, u);
-        if (failed) {
+      int loads = 0, yprev = -1;
+      int64_t ucur = -1;
+      PanWalk w;
+      walk_init(g, w, lo, hi, stride);
+      for (; w.valid; walk_next(g, w)) {
+        if (w.u != ucur) {  // a new unit
+          ucur = w.u;
+          if (failed) {
+            ok = false;
+            break;
+          }
+          if (res && w.t.y != yprev) {
+            // free the previous column tile's B once this thread's MMAs on
+            // it finish (both threads commit), then wait for this one's
+            if (loads > 0)
+              asm volatile(
+                  "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 "
+                  "[%0];" ::"r"(smem_u32(&rempty))
+                  : "memory");
+            if (!mbar_wait(smem_u32(&rfull), loads & 1)) {
+              ok = false;
+              break;
+            }
+            ++loads;
+            yprev = w.t.y;
+          }
+        }
+        const int Pi = walk_group(w);  // the step's group
+        if ((Pi & 1) != me) continue;
+        const int i = w.i, c = w.cnt(me);
+        const int sg = me * kSHalf + c % kSHalf, bs = me * kBHalf + c % kBHalf;
+        if ((i % kPanGroup == 0 && Pi >= 2 &&
+             !mbar_wait(smem_u32(&acc_empty[me]), ((Pi >> 1) - 1) & 1)) ||
+            !mbar_wait(smem_u32(&sfull[sg]), (c / kSHalf) & 1) ||
+            (!res && !mbar_wait(smem_u32(&bfull[bs]), (c / kBHalf) & 1))) {
           ok = false;
           break;
         }
-        if (res && t.y != yprev) {
-          // free the previous column tile's B once this thread's MMAs on it
-          // finish (both threads commit), then wait for this one's
-          if (loads > 0)
-            asm volatile(
-                "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 "
-                "[%0];" ::"r"(smem_u32(&rempty))
-                : "memory");
-          if (!mbar_wait(smem_u32(&rfull), loads & 1)) {
-            ok = false;
-            break;
-          }
-          ++loads;
-          yprev = t.y;
-        }
-        for (int i = 0; i < t.ns; ++i, ++gs) {
-          const int Pi = P + i / kPanGroup;  // the step's group
-          if ((Pi & 1) != me) continue;
-          const int sg = gs % kSSt, bs = gs % kPanBStages;
-          if ((i % kPanGroup == 0 && Pi >= 2 &&
-               !mbar_wait(smem_u32(&acc_empty[me]), ((Pi >> 1) - 1) & 1)) ||
-              !mbar_wait(smem_u32(&sfull[sg]), (gs / kSSt) & 1) ||
-              (!res && !mbar_wait(smem_u32(&bfull[bs]), (gs / kPanBStages) & 1))) {
-            ok = false;
-            break;
-          }
-          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-          const uint32_t acc_addr = tmem + static_cast<uint32_t>(kN * me);
-          if constexpr (FP8) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t acc_addr = tmem + static_cast<uint32_t>(kN * me);
+        if constexpr (FP8) {
 #pragma unroll
-            for (int tt = 0; tt < 2; ++tt) {  // K = 32: the whole step
-              const uint64_t ad = pan_desc(smem_u32(tileS(sg)));
-              const uint64_t bd = pan_desc(smem_u32(tileB(bs, i, tt)), kBLbo);
-              const uint32_t acc = (i % kPanGroup || tt > 0) ? 1u : 0u;
+          for (int tt = 0; tt < 2; ++tt) {  // K = 32: the whole step
+            const uint64_t ad = pan_desc(smem_u32(tileS(sg)));
+            const uint64_t bd = pan_desc(smem_u32(tileB(bs, i, tt)), kBLbo);
+            const uint32_t acc = (i % kPanGroup || tt > 0) ? 1u : 0u;
+            asm volatile(
+                "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+                    acc_addr),
+                "l"(ad), "l"(bd), "r"(kIdesc), "r"(acc)
+                : "memory");
+          }
+        } else {
+#pragma unroll
+          for (int tt = 0; tt < 3; ++tt)
+#pragma unroll
+            for (int kh = 0; kh < 2; ++kh) {
+              const uint64_t ad = pan_desc(smem_u32(tileS(sg)) + kh * 2 * kPanLbo);
+              const uint64_t bd = pan_desc(smem_u32(tileB(bs, i, tt)) + kh * 2 * kBLbo, kBLbo);
+              const uint32_t acc = (i % kPanGroup || tt > 0 || kh > 0) ? 1u : 0u;
               asm volatile(
                   "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-                  "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+                  "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
                       acc_addr),
                   "l"(ad), "l"(bd), "r"(kIdesc), "r"(acc)
                   : "memory");
             }
-          } else {
-#pragma unroll
-            for (int tt = 0; tt < 3; ++tt)
-#pragma unroll
-              for (int kh = 0; kh < 2; ++kh) {
-                const uint64_t ad = pan_desc(smem_u32(tileS(sg)) + kh * 2 * kPanLbo);
-                const uint64_t bd = pan_desc(smem_u32(tileB(bs, i, tt)) + kh * 2 * kBLbo, kBLbo);
-                const uint32_t acc = (i % kPanGroup || tt > 0 || kh > 0) ? 1u : 0u;
-                asm volatile(
-                    "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
-                        acc_addr),
-                    "l"(ad), "l"(bd), "r"(kIdesc), "r"(acc)
-                    : "memory");
-              }
-          }
-          asm volatile(
-              "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                  smem_u32(&sempty[sg]))
-              : "memory");
-          if (!res)
-            asm volatile(
-                "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 "
-                "[%0];" ::"r"(smem_u32(&bempty[bs]))
-                : "memory");
-          if (i % kPanGroup == kPanGroup - 1 || i == t.ns - 1)
-            asm volatile(
-                "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 "
-                "[%0];" ::"r"(smem_u32(&acc_full[me]))
-                : "memory");
         }
-        P += (t.ns + kPanGroup - 1) / kPanGroup;
+        asm volatile(
+            "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                smem_u32(&sempty[sg]))
+            : "memory");
+        if (!res)
+          asm volatile(
+              "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 "
+              "[%0];" ::"r"(smem_u32(&bempty[bs]))
+              : "memory");
+        if (i % kPanGroup == kPanGroup - 1 || i == w.t.ns - 1)
+          asm volatile(
+              "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 "
+              "[%0];" ::"r"(smem_u32(&acc_full[me]))
+              : "memory");
       }
       if (!ok) {  // drain the MMAs this thread issued before the memory is freed
         failed = 1;
@@ -651,35 +708,30 @@ __global__ void __launch_bounds__(kPanThreads, 1)
       }
     }
   } else if (warp >= 4 && warp < 4 + kSSt) {  // S-tile builders
-    const int bw = warp - 4;  // builds steps bw, bw + kSSt, ... into S stage bw
+    // builder bw fills S stage bw: the steps of MMA thread bw / kSHalf whose
+    // index among that thread's steps is bw % kSHalf modulo kSHalf
+    const int bw = warp - 4, th_b = bw / kSHalf, slot = bw % kSHalf;
     const int K = *Kdev;
-    // walk the CTA's steps in order (gs counts them over its units)
-    int64_t u = lo;
-    PanUnit t{};
-    int i = 0, gs = 0;
-    auto advance_by = [&](int k) {  // k steps on, past finished (or empty) units
-      i += k;
-      gs += k;
-      while (u < hi && i >= t.ns) {
-        i -= t.ns;
-        u += stride;
-        if (u < hi) t = pan_unit(g, u);
-      }
-      return u < hi;
+    PanWalk w;
+    walk_init(g, w, lo, hi, stride);
+    auto next_mine = [&]() {
+      while (w.valid &&
+             (walk_thread(w) != th_b || w.cnt(th_b) % kSHalf != slot))
+        walk_next(g, w);
+      return w.valid;
     };
     auto row_id = [&]() {  // this lane's dense row of the current step (0 past K)
-      const int q = (t.st0 + i) * kBK + lane;
+      const int q = (w.t.st0 + w.i) * kBK + lane;
       return q < K ? rows[q] : 0;  // padding rows multiply zeros
     };
-    if (u < hi) t = pan_unit(g, u);
-    bool have = advance_by(bw);
+    bool have = next_mine();
     int32_t jn = have ? row_id() : 0;
     while (have) {
-      const int gc = gs, d0 = t.x * 128;
+      const int round = w.cnt(th_b) / kSHalf, d0 = w.t.x * 128;
       const int32_t j = jn;
-      have = advance_by(kSSt);  // this builder's next step
-      if (have) jn = row_id();          // in flight while this step is built
-      const int round = gc / kSSt;
+      walk_next(g, w);
+      have = next_mine();        // this builder's next step
+      if (have) jn = row_id();   // in flight while this step is built
       int ok = 1;
       if (lane == 0 && round > 0 && !mbar_wait(smem_u32(&sempty[bw]), (round - 1) & 1)) ok = 0;
       ok = __shfl_sync(0xffffffffu, ok, 0);
@@ -1128,8 +1180,7 @@ cudaError_t launch_tc_gemm(const DenseArgs& a, const DenseView& v, float* Ahat,
   const size_t smem = pan_smem_bytes(fp8, wide, g.resident != 0, g.steps);
   auto kern = fp8 ? (wide ? k_tc_panel<true, true> : k_tc_panel<true, false>)
                   : (wide ? k_tc_panel<false, true> : k_tc_panel<false, false>);
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       static_cast<int>(smem));
+  cudaError_t e = raise_smem_limit(reinterpret_cast<const void*>(kern), smem);
   if (e != cudaSuccess) return e;
   const int64_t total = static_cast<int64_t>(a.n) * a.d;
   float* out = splits > 1 ? v.partial : Ahat;

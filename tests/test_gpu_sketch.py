@@ -540,6 +540,32 @@ def test_prepared_data_reused_and_rebuilt_when_A_changes(plan):
     sk.close()
 
 
+@pytest.mark.parametrize("every,fp8", [(97, 0), (40, 0), (20, 0), (97, 1), (20, 1)])
+def test_tensor_core_repeated_applies_identical(every, fp8):
+    """The panel kernel's two MMA threads, S builders and bulk copies meet
+    only through their stage rings; repeated applies of one plan give the
+    same bits every time and a clean status word (short panels: 128 x 256
+    units; 760 and 1520 dense rows: 128 x 128 units, split along K)."""
+    A = _dense_rows_matrix(30_400 if every != 97 else 9000, 700, every, 0.002, False,
+                           seed=41)
+    d = 1000
+    sk = capi.Sketch(A.m, A.n, d, "pm1", seed=2)
+    sk.set_plan(mode=capi.SKETCH_MODE_REGEN, q_tiles=4, split=2, tc_min_row_nnz=300,
+                tc_fp8=fp8)
+    dA = capi.DeviceCSC(A)
+    out = torch.empty((A.n, d), dtype=torch.float32, device="cuda")
+    sk.apply(dA, out)
+    torch.cuda.synchronize()
+    first = out.clone()
+    for _ in range(12):
+        out.fill_(float("nan"))
+        sk.apply(dA, out)
+        torch.cuda.synchronize()
+        assert torch.equal(out, first)
+    assert sk.device_status() == capi.SKETCH_OK
+    sk.close()
+
+
 def test_tensor_core_long_panel_float_tolerance():
     A = _dense_rows_matrix(30_400, 300, 40, 0.002, False, seed=38)
     plan = dict(mode=capi.SKETCH_MODE_TILE, panel_rows=512, row_groups=4,
