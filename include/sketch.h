@@ -105,7 +105,7 @@ typedef struct {
   int32_t split;         /* REGEN: 1, 2, 4 or 8 warps per column           */
   int32_t n_block;       /* PANEL: columns per CTA (<= 1536)               */
   int32_t row_groups;    /* PANEL, TILE: number of row ranges of A         */
-  int32_t panel_rows;    /* TILE: rows of A per panel, 8..1152 (m1)        */
+  int32_t panel_rows;    /* TILE: rows of A per panel, 8..1248 (m1)        */
   int32_t cols_per_warp; /* TILE: 4, 16 or 64 (32 with tile_acc = 1)       */
   int32_t tc_min_row_nnz;/* +-1 only: rows of A with at least this many     */
                          /* nonzeros form a dense panel multiplied on the   */
@@ -227,7 +227,7 @@ int sketch_generate_S(sketch_t h, float* S, int64_t ld_s, sketch_stream_t stream
  * tensor-memory sums, each 32-row x panel_rows tile of S copied from memory
  * (cp.async, 16 bytes a thread) where the other paths generate it.  Same
  * additions as the generated path, so the same bits.  Uses a forced TILE plan
- * with tile_acc = 1 if one is set, else panels of 1152 rows.  Same
+ * with tile_acc = 1 if one is set, else panels of 1248 rows.  Same
  * requirements on S and ld_s as sketch_generate_S; same errors as
  * sketch_apply.  Asynchronous. */
 int sketch_apply_pregen(sketch_t h, const sketch_csc* A, const float* S, int64_t ld_s,

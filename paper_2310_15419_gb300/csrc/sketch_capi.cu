@@ -128,7 +128,7 @@ sketch_plan heuristic_plan(const sketch_s* h, const sketch_csc* A) {
     p.q_tiles = std::max(1, q);
     p.split = avg_col >= 4096 ? 8 : avg_col >= 1024 ? 4 : avg_col >= 256 ? 2 : 1;
   } else {
-    p = A->n > 256 ? tile_plan(h, A, 1152, 1) : tile_plan(h, A, 1024, 0);
+    p = A->n > 256 ? tile_plan(h, A, 1248, 1) : tile_plan(h, A, 1024, 0);
   }
   return p;
 }
@@ -196,10 +196,13 @@ int check_plan(sketch_t h, const sketch_plan& p) {
     if (p.row_groups < 1 || p.row_groups > 65535)
       return fail(h, SKETCH_ERR_ARG, "row_groups must be 1..65535");
   } else if (p.mode == SKETCH_MODE_TILE) {
-    if (p.panel_rows < 8 || p.panel_rows > 1152)
-      return fail(h, SKETCH_ERR_ARG, "panel_rows must be 8..1152");
     if (p.tile_acc != 0 && p.tile_acc != 1)
       return fail(h, SKETCH_ERR_ARG, "tile_acc must be 0 or 1");
+    // the S tile (panel_rows x 32 floats) and the staged entries share the
+    // 227 KB of dynamic shared memory a CTA can have: up to 1248 rows
+    if (p.panel_rows < 8 || p.panel_rows > 1248 ||
+        tile_smem_bytes(p.panel_rows, p.tile_acc) > 232448 - 1024)
+      return fail(h, SKETCH_ERR_ARG, "panel_rows must be 8..1248");
     if (p.tile_acc == 0 && p.cols_per_warp != 4 && p.cols_per_warp != 16 &&
         p.cols_per_warp != 64)
       return fail(h, SKETCH_ERR_ARG, "cols_per_warp must be 4, 16 or 64");
@@ -471,8 +474,8 @@ static std::vector<sketch_plan> candidates(const sketch_s* h, const sketch_csc* 
   }
   // TILE panel heights (the S tile takes R * 128 bytes of shared memory):
   // register sums at 1024 and 512 rows, and for n > 256 the tensor-memory
-  // sums (32 warps per CTA) at 1152 and 1024
-  for (auto [R, tacc] : {std::pair<int32_t, int32_t>{1024, 0}, {512, 0}, {1152, 1}, {1024, 1}}) {
+  // sums (32 warps per CTA) at 1248 and 1024
+  for (auto [R, tacc] : {std::pair<int32_t, int32_t>{1024, 0}, {512, 0}, {1248, 1}, {1024, 1}}) {
     sketch_plan p = tile_plan(h, A, R, tacc);
     if (p.tile_acc != tacc) continue;
     if (tile_workspace_bytes(A->m, A->n, h->d, A->nnz, R, p.row_groups) <= (size_t(8) << 30))
@@ -907,12 +910,12 @@ int sketch_apply_pregen(sketch_t h, const sketch_csc* A, const float* S, int64_t
     return e == cudaSuccess ? SKETCH_OK : cuda_fail(h, e, "cudaMemsetAsync");
   }
   // a forced TILE plan with tensor-memory sums sets R and the row groups;
-  // otherwise panels of 1152 rows
+  // otherwise panels of 1248 rows
   sketch_plan p{};
   if (h->has_forced && h->forced.mode == SKETCH_MODE_TILE && h->forced.tile_acc == 1) {
     p = h->forced;
   } else {
-    p = tile_plan(h, A, 1152, 1);
+    p = tile_plan(h, A, 1248, 1);
     p.tile_acc = 1;
     p.cols_per_warp = 32;
   }

@@ -68,7 +68,7 @@ def test_host_side_argument_errors_need_no_gpu():
 
 def test_tile_plan_checks_need_no_gpu():
     """TILE plans: register sums take 4, 16 or 64 columns per warp, tensor-
-    memory sums (tile_acc = 1) exactly 32; both need panel_rows 8..1152."""
+    memory sums (tile_acc = 1) exactly 32; both need panel_rows 8..1248."""
     from paper_2310_15419_gb300 import capi
     lib = capi.load()
     h = ctypes.c_void_p()
@@ -76,10 +76,11 @@ def test_tile_plan_checks_need_no_gpu():
     T = capi.SKETCH_MODE_TILE
     # mode, q_tiles, split, n_block, row_groups, panel_rows, cols_per_warp, tc, tile_acc
     good = [(T, 0, 0, 0, 1, 1024, 64, 0, 0), (T, 0, 0, 0, 3, 8, 4, 0, 0),
-            (T, 0, 0, 0, 20, 1152, 32, 0, 1), (T, 0, 0, 0, 1, 8, 32, 0, 1)]
+            (T, 0, 0, 0, 20, 1152, 32, 0, 1), (T, 0, 0, 0, 21, 1248, 32, 0, 1),
+            (T, 0, 0, 0, 1, 8, 32, 0, 1)]
     bad = [(T, 0, 0, 0, 1, 1024, 64, 0, 1), (T, 0, 0, 0, 1, 512, 16, 0, 1),
            (T, 0, 0, 0, 1, 512, 32, 0, 0), (T, 0, 0, 0, 1, 512, 32, 0, 2),
-           (T, 0, 0, 0, 1, 1153, 32, 0, 1), (T, 0, 0, 0, 1, 7, 64, 0, 0),
+           (T, 0, 0, 0, 1, 1249, 32, 0, 1), (T, 0, 0, 0, 1, 7, 64, 0, 0),
            (T, 0, 0, 0, 0, 1024, 64, 0, 0)]
     for f in good:
         assert lib.sketch_set_plan(h, ctypes.byref(capi.sketch_plan(*f))) == capi.SKETCH_OK, f
@@ -114,7 +115,7 @@ def test_pregenerated_S_argument_errors_need_no_gpu():
 def test_heuristic_plans_need_no_gpu():
     """With tuning off the plan is the heuristic's, chosen on the host:
     +-1 -> REGEN; U and N -> TILE, with tensor-memory sums (32 warps x 32
-    columns, panels of 1152 rows) when n > 256; very sparse input -> REGEN."""
+    columns, panels of 1248 rows) when n > 256; very sparse input -> REGEN."""
     from paper_2310_15419_gb300 import capi
     lib = capi.load()
 
@@ -133,7 +134,7 @@ def test_heuristic_plans_need_no_gpu():
     for dist in (1, 2):
         p = plan(2_000_000, 1000, 3000, dist, 10_000_000)
         assert (p["mode"], p["panel_rows"], p["cols_per_warp"], p["tile_acc"]) == \
-            (capi.SKETCH_MODE_TILE, 1152, 32, 1)
+            (capi.SKETCH_MODE_TILE, 1248, 32, 1)
         assert p["row_groups"] >= 20          # <= 512 terms of a column per group
         p = plan(100_000, 200, 400, dist, 1_000_000)
         assert (p["mode"], p["panel_rows"], p["cols_per_warp"], p["tile_acc"]) == \
