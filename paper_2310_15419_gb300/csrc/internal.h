@@ -196,5 +196,10 @@ cudaError_t pattern_features(int32_t m, int32_t n, int64_t nnz, const int32_t* c
                              int* status, cudaStream_t s);
 
 int num_sms();
+// Raise a kernel's dynamic shared-memory limit to at least `bytes`; never
+// lowers it.  The attribute belongs to the kernel, not to a thread, so
+// launches from several host threads (the solve server's slots) must not
+// set it down under one another; each size is set once.
+cudaError_t raise_smem_limit(const void* kernel, size_t bytes);
 
 }  // namespace sk

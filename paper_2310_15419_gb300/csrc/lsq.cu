@@ -422,12 +422,12 @@ cudaError_t launch_trtri(const double* W, int64_t d, int n, const double* rdiag,
   if (n <= 4096) {
     int T = 128;
     while (T * 4 < n) T *= 2;
-    cudaFuncSetAttribute(k_trtri<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         static_cast<int>(smem));
+    const cudaError_t e = raise_smem_limit(reinterpret_cast<const void*>(k_trtri<4>), smem);
+    if (e != cudaSuccess) return e;
     k_trtri<4><<<n, T, smem, s>>>(W, d, n, rdiag, Xrow, XTrow);
   } else {
-    cudaFuncSetAttribute(k_trtri<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         static_cast<int>(smem));
+    const cudaError_t e = raise_smem_limit(reinterpret_cast<const void*>(k_trtri<8>), smem);
+    if (e != cudaSuccess) return e;
     k_trtri<8><<<n, 1024, smem, s>>>(W, d, n, rdiag, Xrow, XTrow);
   }
   return cudaGetLastError();
@@ -1346,12 +1346,12 @@ struct LsqState {
   cudaStream_t ls = nullptr;     // internal stream (capturable)
   cudaEvent_t ev[6] = {};
   cudaGraphExec_t graph = nullptr;
-  const void* graph_key[8] = {};  // what the captured iterations read/write
+  const void* graph_key[10] = {};  // what the captured iterations read/write
   cudaGraphExec_t qr_graph = nullptr;  // the QR's n launches, per shape
   int64_t qr_key[3] = {-1, -1, -1};     // (d, n, workspace address) of qr_graph
   int64_t qr_seen[3] = {-1, -1, -1};    // shape of the previous solve
   cudaGraphExec_t jacobi_graph = nullptr;  // one Jacobi sweep, per shape
-  const void* jacobi_key[3] = {};
+  const void* jacobi_key[4] = {};  // the rounds' arrays and n
   int svd_sweeps = 0;                    // sweeps of the last SAP-SVD solve
 };
 
@@ -1719,7 +1719,8 @@ int lsq_solve(sketch_t h, const sketch_csc* A, const double* b, double* x, doubl
     const int n32 = static_cast<int>(n), n2 = n32 + (n32 & 1);
     k_svd_init<<<gb, 256, 0, s>>>(L.W, d, n32, L.Rc, L.Vj);
     h->launches += 1;
-    const void* jkey[3] = {L.Rc, L.Vj, L.rotations};
+    const void* jkey[4] = {L.Rc, L.Vj, L.rotations,
+                           reinterpret_cast<const void*>(static_cast<intptr_t>(n))};
     if (st.jacobi_graph && std::memcmp(jkey, st.jacobi_key, sizeof(jkey)) != 0) {
       cudaGraphExecDestroy(st.jacobi_graph);
       st.jacobi_graph = nullptr;
@@ -1810,11 +1811,15 @@ int lsq_solve(sketch_t h, const sketch_csc* A, const double* b, double* x, doubl
   lsqr_kernels(L, csc, csr, mnz, b, static_cast<int32_t>(m), 1, 1, pdl, pk, s);
   h->launches += 4;
   // iterations: a cached graph of kIterPerGraph iterations, replayed until
-  // the device sets `done`
-  const void* key[8] = {A->colptr, A->rowidx, A->values, st.ws,
-                        reinterpret_cast<const void*>(n), reinterpret_cast<const void*>(m),
-                        reinterpret_cast<const void*>(static_cast<intptr_t>(pk)),
-                        reinterpret_cast<const void*>(d)};
+  // the device sets `done`.  The key holds every value the captured launches
+  // take: A's arrays, the workspace and the shape that lays it out (nnz
+  // places the ordered CSR and everything after it), and the value type.
+  const void* key[10] = {A->colptr, A->rowidx, A->values, st.ws,
+                         reinterpret_cast<const void*>(n), reinterpret_cast<const void*>(m),
+                         reinterpret_cast<const void*>(static_cast<intptr_t>(pk)),
+                         reinterpret_cast<const void*>(d),
+                         reinterpret_cast<const void*>(static_cast<intptr_t>(nnz)),
+                         reinterpret_cast<const void*>(static_cast<intptr_t>(A->dtype))};
   if (st.graph && std::memcmp(key, st.graph_key, sizeof(key)) != 0) {
     cudaGraphExecDestroy(st.graph);
     st.graph = nullptr;

@@ -20,6 +20,8 @@
 //         single vertical block, Sec. 3.2), built on the device: row counts,
 //         exclusive scan, scatter.
 #include <algorithm>
+#include <mutex>
+#include <unordered_map>
 
 #include "common.cuh"
 #include "internal.h"
@@ -720,9 +722,7 @@ cudaError_t launch_panel(const PanelArgs& a, cudaStream_t s, int* launches) {
   float* dst = a.row_groups == 1 ? a.Ahat : a.partial;
 #define SK_PANEL_CASE(DD, CC)                                                \
   if (a.dist == DD && (a.compensated != 0) == CC) {                          \
-    e = cudaFuncSetAttribute(k_panel<DD, CC>,                                \
-                             cudaFuncAttributeMaxDynamicSharedMemorySize,    \
-                             static_cast<int>(smem));                        \
+    e = raise_smem_limit(reinterpret_cast<const void*>(k_panel<DD, CC>), smem); \
     if (e != cudaSuccess) return e;                                          \
     k_panel<DD, CC><<<grid, block, smem, s>>>(                               \
         a.m, a.n, a.d, a.n_block, a.row_groups, a.csr.rowptr, a.csr.ccol,    \
@@ -1224,9 +1224,7 @@ cudaError_t launch_tile(const TileArgs& a, void* ws, cudaStream_t s, int* launch
     return cudaErrorInvalidValue;
 #define SK_TILE_CASE(DD, CC, TT)                                                 \
   if (a.dist == DD && a.cpw == CC && (a.tacc != 0) == TT) {                      \
-    e = cudaFuncSetAttribute(k_tile<DD, CC, TT>,                                 \
-                             cudaFuncAttributeMaxDynamicSharedMemorySize,        \
-                             static_cast<int>(smem));                            \
+    e = raise_smem_limit(reinterpret_cast<const void*>(k_tile<DD, CC, TT>), smem); \
     if (e != cudaSuccess) return e;                                              \
     k_tile<DD, CC, TT><<<grid, block, smem, s>>>(a.m, a.n, a.d, a.R,             \
                                                  static_cast<int32_t>(P), a.G,   \
@@ -1629,6 +1627,18 @@ int num_sms() {
     cached = v > 0 ? v : 1;
   }
   return cached;
+}
+
+cudaError_t raise_smem_limit(const void* kernel, size_t bytes) {
+  static std::mutex mu;
+  static std::unordered_map<const void*, size_t> limit;
+  std::lock_guard<std::mutex> lock(mu);
+  size_t& cur = limit[kernel];
+  if (bytes <= cur) return cudaSuccess;
+  const cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             static_cast<int>(bytes));
+  if (e == cudaSuccess) cur = bytes;
+  return e;
 }
 
 }  // namespace sk
