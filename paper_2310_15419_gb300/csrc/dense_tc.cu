@@ -244,10 +244,10 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity,
 //     issuing tcgen05.mma runs in step with the tensor pipe, so any wait or
 //     commit on one thread would idle the pipe; two threads hide each
 //     other's;
-//   warps 4-11 (the builders): builder w fills S stage w, half of the
-//     stages serving each MMA thread (see PanWalk); lane k computes the
-//     Philox block of the step's dense row k (the signs of all 128 rows of
-//     S).  BF16: the tile is
+//   warps 4-11 (the builders): builder w fills S stage w, for whichever MMA
+//     thread takes the step (a full barrier per stage and MMA thread); lane k
+//     computes the Philox block of the step's dense row k (the signs of all
+//     128 rows of S).  BF16: the tile is
 //     MN-major, so lane k writes its own column (16 B per 8 rows, each pair
 //     of signs spread into two BF16 +-1 by one multiply).  E4M3: the tile is
 //     K-major; four five-stage shuffle transposes give lane L the signs of
@@ -317,21 +317,17 @@ __device__ __forceinline__ void pan_range(const PanelGrid& g, int64_t& lo, int64
   }
 }
 
-// The CTA's steps in order, each with its group (a unit's steps in groups of
-// kPanGroup; MMA thread g & 1 takes group g) and its index among that MMA
-// thread's steps.  That index places the step in its MMA thread's half of
-// each stage ring, so every stage has one filler and one consumer, both
-// in order: a parity wait then never mistakes a phase two rounds old for
-// the one it waits on (which it could if the two MMA threads shared
-// stages).  Every role walks the same sequence.
+// The CTA's steps in order, each with its index s among them (which places
+// it in the stage rings: stage s % stages, round s / stages) and its group
+// (a unit's steps in groups of kPanGroup; MMA thread g & 1 takes group g).
+// Every role walks the same sequence.
 struct PanWalk {
   int64_t u, hi, stride;
   PanUnit t;
-  int i;       // step within the unit
-  int P;       // groups before this unit
-  int c0, c1;  // steps of MMA thread 0 and 1 before this one
+  int i;  // step within the unit
+  int P;  // groups before this unit
+  int s;  // steps before this one
   bool valid;
-  __device__ __forceinline__ int cnt(int th) const { return th ? c1 : c0; }
 };
 __device__ __forceinline__ void walk_settle(const PanelGrid& g, PanWalk& w) {
   while (w.u < w.hi && w.i >= w.t.ns) {
@@ -349,7 +345,7 @@ __device__ __forceinline__ void walk_init(const PanelGrid& g, PanWalk& w, int64_
   w.stride = stride;
   w.i = 0;
   w.P = 0;
-  w.c0 = w.c1 = 0;
+  w.s = 0;
   w.t = PanUnit{0, 0, 0, 0, 0};
   if (lo < hi) w.t = pan_unit(g, lo);
   walk_settle(g, w);
@@ -357,10 +353,7 @@ __device__ __forceinline__ void walk_init(const PanelGrid& g, PanWalk& w, int64_
 __device__ __forceinline__ int walk_group(const PanWalk& w) { return w.P + w.i / kPanGroup; }
 __device__ __forceinline__ int walk_thread(const PanWalk& w) { return walk_group(w) & 1; }
 __device__ __forceinline__ void walk_next(const PanelGrid& g, PanWalk& w) {
-  if (walk_thread(w))
-    ++w.c1;
-  else
-    ++w.c0;
+  ++w.s;
   ++w.i;
   walk_settle(g, w);
 }
@@ -515,8 +508,6 @@ __global__ void __launch_bounds__(kPanThreads, 1)
                uint32_t stream_id, int* status) {
   constexpr int kN = pan_cols(WIDE);               // columns of A per unit
   constexpr int kSSt = pan_sstages(WIDE);          // S stages = builder warps
-  constexpr int kSHalf = kSSt / 2;                 // S stages of each MMA thread
-  constexpr int kBHalf = kPanBStages / 2;          // B stages of each MMA thread (streaming)
   constexpr int kProm = pan_promoters(WIDE);       // promoter warps: the last kProm
   constexpr int kTermBytes = pan_term_bytes(FP8, WIDE);
   constexpr uint32_t kTx = pan_step_bytes(FP8, WIDE);
@@ -524,8 +515,15 @@ __global__ void __launch_bounds__(kPanThreads, 1)
   constexpr uint32_t kIdesc = FP8 ? idesc_fp8(kN) : idesc_bf16(kN);
   static_assert(4 + kSSt <= 16 - kProm, "builders and promoters overlap");
   extern __shared__ uint8_t sm_raw[];
-  __shared__ __align__(8) uint64_t sfull[kSSt], sempty[kSSt],
-      bfull[kPanBStages], bempty[kPanBStages], acc_full[2], acc_empty[2], rfull, rempty,
+  // A stage's consumers alternate between the two MMA threads, so each stage
+  // has one "full" barrier per MMA thread: the thread is its only waiter and
+  // takes its phases in order (one parity bit per stage tracks them), which
+  // a single barrier shared by both threads could not guarantee (a thread
+  // could wait two phases ahead and take an old phase for the one it needs).
+  // The "empty" barriers have one waiter, the filler, which frees rounds in
+  // order: a stage's round r + 1 is filled only after round r is released.
+  __shared__ __align__(8) uint64_t sfull[kSSt][2], sempty[kSSt],
+      bfull[kPanBStages][2], bempty[kPanBStages], acc_full[2], acc_empty[2], rfull, rempty,
       drain_bar[2];
   __shared__ uint32_t tmem_base;
   __shared__ volatile int failed;  // set by any role whose bounded wait gave up
@@ -545,11 +543,12 @@ __global__ void __launch_bounds__(kPanThreads, 1)
   if (tid == 0) {
     failed = 0;
     for (int q = 0; q < kSSt; ++q) {
-      mbar_init(smem_u32(&sfull[q]), 1);   // the builder warp
+      for (int th = 0; th < 2; ++th) mbar_init(smem_u32(&sfull[q][th]), 1);  // the builder warp
       mbar_init(smem_u32(&sempty[q]), 1);  // the MMA commit
     }
     for (int q = 0; q < kPanBStages; ++q) {
-      mbar_init(smem_u32(&bfull[q]), 1);   // the bulk copy with its bytes
+      for (int th = 0; th < 2; ++th)
+        mbar_init(smem_u32(&bfull[q][th]), 1);  // the bulk copy with its bytes
       mbar_init(smem_u32(&bempty[q]), 1);  // the MMA commit
     }
     for (int b = 0; b < 2; ++b) {
@@ -592,21 +591,21 @@ __global__ void __launch_bounds__(kPanThreads, 1)
           yprev = t.y;
         }
       } else {
-        // each step's B block into its MMA thread's half of the B ring
+        // each step's B block into the B ring, signalled to its MMA thread
         PanWalk w;
         walk_init(g, w, lo, hi, stride);
         for (; w.valid && !failed; walk_next(g, w)) {
-          const int th = walk_thread(w), c = w.cnt(th);
-          const int bs = th * kBHalf + c % kBHalf, round = c / kBHalf;
+          const int bs = w.s % kPanBStages, round = w.s / kPanBStages;
           if (round > 0 && !mbar_wait(smem_u32(&bempty[bs]), (round - 1) & 1)) {
             failed = 1;
             break;
           }
-          mbar_arrive_tx(smem_u32(&bfull[bs]), kTx);
+          const uint32_t full = smem_u32(&bfull[bs][walk_thread(w)]);
+          mbar_arrive_tx(full, kTx);
           // the step's B tiles (all terms) are one contiguous block of A3
           bulk_load(smem_u32(tileB(bs, 0, 0)),
                     A3 + (static_cast<int64_t>(w.t.y) * g.steps + w.t.st0 + w.i) * kTx, kTx,
-                    smem_u32(&bfull[bs]));
+                    full);
         }
       }
     }
@@ -615,6 +614,7 @@ __global__ void __launch_bounds__(kPanThreads, 1)
       const int me = warp - 1;
       bool ok = true;
       int loads = 0, yprev = -1;
+      uint32_t spar = 0, bpar = 0;  // parity of the next phase of sfull[.][me], bfull[.][me]
       int64_t ucur = -1;
       PanWalk w;
       walk_init(g, w, lo, hi, stride);
@@ -643,15 +643,16 @@ __global__ void __launch_bounds__(kPanThreads, 1)
         }
         const int Pi = walk_group(w);  // the step's group
         if ((Pi & 1) != me) continue;
-        const int i = w.i, c = w.cnt(me);
-        const int sg = me * kSHalf + c % kSHalf, bs = me * kBHalf + c % kBHalf;
+        const int i = w.i, sg = w.s % kSSt, bs = w.s % kPanBStages;
         if ((i % kPanGroup == 0 && Pi >= 2 &&
              !mbar_wait(smem_u32(&acc_empty[me]), ((Pi >> 1) - 1) & 1)) ||
-            !mbar_wait(smem_u32(&sfull[sg]), (c / kSHalf) & 1) ||
-            (!res && !mbar_wait(smem_u32(&bfull[bs]), (c / kBHalf) & 1))) {
+            !mbar_wait(smem_u32(&sfull[sg][me]), (spar >> sg) & 1u) ||
+            (!res && !mbar_wait(smem_u32(&bfull[bs][me]), (bpar >> bs) & 1u))) {
           ok = false;
           break;
         }
+        spar ^= 1u << sg;
+        if (!res) bpar ^= 1u << bs;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t acc_addr = tmem + static_cast<uint32_t>(kN * me);
         if constexpr (FP8) {
@@ -708,16 +709,13 @@ __global__ void __launch_bounds__(kPanThreads, 1)
       }
     }
   } else if (warp >= 4 && warp < 4 + kSSt) {  // S-tile builders
-    // builder bw fills S stage bw: the steps of MMA thread bw / kSHalf whose
-    // index among that thread's steps is bw % kSHalf modulo kSHalf
-    const int bw = warp - 4, th_b = bw / kSHalf, slot = bw % kSHalf;
+    // builder bw fills S stage bw: the steps s with s % kSSt == bw, in order
+    const int bw = warp - 4;
     const int K = *Kdev;
     PanWalk w;
     walk_init(g, w, lo, hi, stride);
     auto next_mine = [&]() {
-      while (w.valid &&
-             (walk_thread(w) != th_b || w.cnt(th_b) % kSHalf != slot))
-        walk_next(g, w);
+      while (w.valid && w.s % kSSt != bw) walk_next(g, w);
       return w.valid;
     };
     auto row_id = [&]() {  // this lane's dense row of the current step (0 past K)
@@ -727,7 +725,7 @@ __global__ void __launch_bounds__(kPanThreads, 1)
     bool have = next_mine();
     int32_t jn = have ? row_id() : 0;
     while (have) {
-      const int round = w.cnt(th_b) / kSHalf, d0 = w.t.x * 128;
+      const int round = w.s / kSSt, d0 = w.t.x * 128, th = walk_thread(w);
       const int32_t j = jn;
       walk_next(g, w);
       have = next_mine();        // this builder's next step
@@ -776,7 +774,7 @@ __global__ void __launch_bounds__(kPanThreads, 1)
       // generic-proxy writes -> visible to the tensor core, then one arrival
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncwarp();
-      if (lane == 0) mbar_arrive(smem_u32(&sfull[bw]));
+      if (lane == 0) mbar_arrive(smem_u32(&sfull[bw][th]));
     }
   } else if (warp >= 16 - kProm) {  // promoters: lanes 32 (warp & 3) .., a column half
     const int rq = warp & 3;
