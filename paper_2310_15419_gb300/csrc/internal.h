@@ -86,7 +86,8 @@ struct TileArgs {
   uint32_t k0, k1, stream_id;
   int32_t dist;
   int32_t R;    // rows of A per panel (m1)
-  int32_t G;    // row groups (partial sums)
+  int32_t G;    // register sums: row groups (partial copies); tensor-memory
+                // sums: CTAs per column block, each a balanced share of units
   int32_t cpw;  // columns per warp: 4, 16 or 64; 32 with tacc (n1 = warps * cpw)
   int32_t tacc;  // 1: accumulators in tensor memory (32 warps of cpw 32)
   // dist 3: S read from S_mem (d x m, column j at S_mem + j * ld_s; ld_s a
@@ -100,7 +101,7 @@ struct TileArgs {
   int32_t prepared = 0;
 };
 size_t tile_workspace_bytes(int64_t m, int64_t n, int64_t d, int64_t nnz,
-                            int32_t R, int32_t G);
+                            int32_t R, int32_t G, int32_t tacc);
 size_t tile_smem_bytes(int32_t R, int32_t tacc);
 cudaError_t launch_tile(const TileArgs& a, void* ws, cudaStream_t s,
                         int* launches);

@@ -79,8 +79,10 @@ int ensure_workspace(sketch_t h, size_t bytes) {
 static size_t align256(size_t b) { return (b + 255) / 256 * 256; }
 
 // TILE plan for a panel height R: columns per warp covering n (up to 1024
-// per CTA), and row groups that fill the GPU and keep each column's partial
-// sums to ~512 terms.
+// per CTA).  Register sums: row groups that fill the GPU and keep each
+// column's partial sums to ~512 terms.  Tensor-memory sums: one CTA per SM
+// (spread over the column blocks), each a balanced share of the work; two
+// levels of sums keep the chains short.
 sketch_plan tile_plan(const sketch_s* h, const sketch_csc* A, int32_t R, int32_t tile_acc) {
   sketch_plan p{};
   p.mode = SKETCH_MODE_TILE;
@@ -95,6 +97,11 @@ sketch_plan tile_plan(const sketch_s* h, const sketch_csc* A, int32_t R, int32_t
   const int64_t cblocks = (A->n + n1 - 1) / n1;
   const int64_t P = (A->m + R - 1) / R;
   const double avg_col = A->n > 0 ? double(A->nnz) / double(A->n) : 0.0;
+  if (p.tile_acc) {
+    const int64_t g = std::max<int64_t>(1, num_sms() / cblocks);
+    p.row_groups = static_cast<int32_t>(std::min<int64_t>({g, tiles * P, 65535}));
+    return p;
+  }
   const int per_sm = 1;
   int64_t g_fill = (2LL * per_sm * num_sms() + tiles * cblocks - 1) / (tiles * cblocks);
   int64_t g_acc = static_cast<int64_t>(std::ceil(avg_col / 512.0));
@@ -167,7 +174,8 @@ size_t plan_workspace_bytes(const sketch_s* h, const sketch_csc* A,
 static size_t sparse_workspace_bytes(const sketch_s* h, const sketch_csc* A,
                                      const sketch_plan& p) {
   if (p.mode == SKETCH_MODE_TILE)
-    return tile_workspace_bytes(A->m, A->n, h->d, A->nnz, p.panel_rows, p.row_groups);
+    return tile_workspace_bytes(A->m, A->n, h->d, A->nnz, p.panel_rows, p.row_groups,
+                                p.tile_acc);
   if (p.mode != SKETCH_MODE_PANEL) return 0;
   size_t b = align256(csr_workspace_bytes(A->m, A->nnz));
   if (p.row_groups > 1)
@@ -417,8 +425,12 @@ int run_sparse(sketch_t h, const sketch_csc* A, float* Ahat, const sketch_plan& 
     a.stream_id = h->stream_id;
     a.dist = h->dist;
     a.R = p.panel_rows;
-    a.G = std::min<int32_t>(p.row_groups,
-                            static_cast<int32_t>((A->m + p.panel_rows - 1) / p.panel_rows));
+    // register sums: at most one row group per panel; tensor-memory sums:
+    // the shares the workspace was sized for (an empty share does nothing)
+    a.G = p.tile_acc ? p.row_groups
+                     : std::min<int32_t>(p.row_groups, static_cast<int32_t>(
+                                                           (A->m + p.panel_rows - 1) /
+                                                           p.panel_rows));
     a.cpw = p.cols_per_warp;
     a.tacc = p.tile_acc;
     a.status = status;
@@ -478,7 +490,8 @@ static std::vector<sketch_plan> candidates(const sketch_s* h, const sketch_csc* 
   for (auto [R, tacc] : {std::pair<int32_t, int32_t>{1024, 0}, {512, 0}, {1248, 1}, {1024, 1}}) {
     sketch_plan p = tile_plan(h, A, R, tacc);
     if (p.tile_acc != tacc) continue;
-    if (tile_workspace_bytes(A->m, A->n, h->d, A->nnz, R, p.row_groups) <= (size_t(8) << 30))
+    if (tile_workspace_bytes(A->m, A->n, h->d, A->nnz, R, p.row_groups, p.tile_acc) <=
+        (size_t(8) << 30))
       c.push_back(p);
   }
   // +-1 S: densified panels on the tensor cores for rows holding at least
@@ -566,7 +579,7 @@ static uint64_t feature_key(const sketch_s* h, const sketch_csc* A, const Featur
   mix(static_cast<uint64_t>(32 * f.heavy_nnz / std::max<int64_t>(1, A->nnz)));
   mix(static_cast<uint64_t>(lg(f.max_row)));
   mix(static_cast<uint64_t>(lg(f.max_col)));
-  mix(3);  // version of the plan set
+  mix(4);  // version of the plan set (4: tensor-memory TILE shares)
   return k;
 }
 
@@ -935,8 +948,7 @@ int sketch_apply_pregen(sketch_t h, const sketch_csc* A, const float* S, int64_t
   a.stream_id = h->stream_id;
   a.dist = 3;  // S from memory
   a.R = p.panel_rows;
-  a.G = std::min<int32_t>(p.row_groups,
-                          static_cast<int32_t>((A->m + p.panel_rows - 1) / p.panel_rows));
+  a.G = p.row_groups;  // the shares the workspace was sized for
   a.cpw = 32;
   a.tacc = 1;
   a.status = reinterpret_cast<int*>(h->d_small);

@@ -137,22 +137,30 @@ def test_float_within_tolerance_every_plan(dist, plan):
 
 @pytest.mark.parametrize("dist", ["pm1", "uniform", "normal"])
 def test_tile_tensor_memory_sums_equal_register_sums(dist):
-    """TILE keeps a CTA's running sums in registers (16 warps x 64 columns)
-    or in tensor memory (32 warps x 32 columns); the additions are the same,
-    so the bits are.  n = 1100 spreads columns over every warp (all four
-    tensor-memory lane quarters) and two column blocks, the last one ragged;
-    d = 100 leaves a ragged row tile."""
+    """TILE keeps a CTA's running sums in registers (16 warps x 64 columns,
+    one CTA per row tile and row group) or in tensor memory (32 warps x 32
+    columns, CTAs taking balanced shares of the (tile, panel) blocks).  Where
+    every share is whole tiles of at most 32 panels the additions are the
+    same, so the bits are: 4 row tiles over 1, 2 or 4 shares.  Shares that
+    cut tiles (3, 7) or outnumber the blocks (1000, most of them empty) add
+    the pieces in CTA order, within the tolerance.  n = 1100 spreads columns
+    over every warp (all four tensor-memory lane quarters) and two column
+    blocks, the last one ragged; d = 100 leaves a ragged row tile."""
     A = inputs.float_uniform(3000, 1100, 0.01, seed=21)
     d = 100
-    outs = []
-    for tacc, cpw in ((0, 64), (1, 32)):
-        for r, g in ((1024, 2), (136, 1)):
-            outs.append(gpu_sketch(A, d, dist, plan=dict(
-                mode=capi.SKETCH_MODE_TILE, panel_rows=r, row_groups=g, cols_per_warp=cpw,
-                tile_acc=tacc)))
-    assert np.array_equal(outs[0], outs[2]) and np.array_equal(outs[1], outs[3])
     ref = oracle_sketch(A, d, dist)
-    assert rel_fro(outs[2], ref) <= TOL and rel_fro(outs[3], ref) <= TOL
+    for r in (1024, 136):  # 3 and 23 panels
+        base = gpu_sketch(A, d, dist, plan=dict(
+            mode=capi.SKETCH_MODE_TILE, panel_rows=r, row_groups=1, cols_per_warp=64,
+            tile_acc=0))
+        assert rel_fro(base, ref) <= TOL
+        for g in (1, 2, 4, 3, 7, 1000):
+            got = gpu_sketch(A, d, dist, plan=dict(
+                mode=capi.SKETCH_MODE_TILE, panel_rows=r, row_groups=g, cols_per_warp=32,
+                tile_acc=1))
+            if g in (1, 2, 4):
+                assert np.array_equal(got, base), (r, g)
+            assert rel_fro(got, ref) <= TOL, (r, g)
 
 
 @pytest.mark.parametrize("dist", ["pm1", "uniform", "normal"])
@@ -260,7 +268,8 @@ def test_empty_columns_and_tiny_shapes():
 
 def test_long_column_accuracy():
     """One column with 200k nonzeros: FP32 accumulation must stay within the
-    1e-6 gate (two-level sums in REGEN, row groups in PANEL)."""
+    1e-6 gate (two-level sums in REGEN and tensor-memory TILE, row groups in
+    PANEL and register TILE)."""
     m = 400_000
     rng = np.random.default_rng(7)
     rows = np.sort(rng.choice(m, size=200_000, replace=False)).astype(np.int32)
@@ -269,7 +278,13 @@ def test_long_column_accuracy():
     ref = oracle_sketch(A, 256, "uniform")
     for plan in (REGEN_PLANS[4 * 1 + 0], REGEN_PLANS[4 * 1 + 3], None,
                  dict(mode=capi.SKETCH_MODE_TILE, panel_rows=1024,
-                      row_groups=400, cols_per_warp=4)):
+                      row_groups=400, cols_per_warp=4),
+                 # one CTA over all 8 x 2942 (tile, panel) blocks, and three
+                 # shares that cut tiles: two levels of tensor-memory sums
+                 dict(mode=capi.SKETCH_MODE_TILE, panel_rows=136, row_groups=1,
+                      cols_per_warp=32, tile_acc=1),
+                 dict(mode=capi.SKETCH_MODE_TILE, panel_rows=136, row_groups=3,
+                      cols_per_warp=32, tile_acc=1)):
         got = gpu_sketch(A, 256, "uniform", plan=plan)
         assert rel_fro(got, ref) <= TOL, plan
 
@@ -284,7 +299,9 @@ def test_generation_counts():
             (dict(mode=capi.SKETCH_MODE_PANEL, n_block=40, row_groups=3),
              d * np.unique(A.rowidx).size),
             (dict(mode=capi.SKETCH_MODE_TILE, panel_rows=1000, row_groups=2,
-                  cols_per_warp=4), d * A.m)):
+                  cols_per_warp=4), d * A.m),
+            (dict(mode=capi.SKETCH_MODE_TILE, panel_rows=1000, row_groups=5,
+                  cols_per_warp=32, tile_acc=1), d * A.m)):
         sk = capi.Sketch(A.m, A.n, d, "uniform", seed=1)
         sk.set_plan(**plan)
         sk.set_counting(True)
@@ -359,7 +376,7 @@ def skew_large():
     return inputs.skew_large()
 
 
-SKEW_TACC = dict(mode=capi.SKETCH_MODE_TILE, panel_rows=1024, row_groups=20,
+SKEW_TACC = dict(mode=capi.SKETCH_MODE_TILE, panel_rows=1024, row_groups=152,
                  cols_per_warp=32, tile_acc=1)
 
 
