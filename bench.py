@@ -658,7 +658,7 @@ def run_ours(args):
                 sk.set_plan(capi.SKETCH_MODE_PANEL, n_block=min(A.n, 1024), row_groups=40)
             else:
                 if A.n > 256:   # tensor-memory sums, 32 warps x 32 columns
-                    sk.set_plan(capi.SKETCH_MODE_TILE, panel_rows=1248, row_groups=sms,
+                    sk.set_plan(capi.SKETCH_MODE_TILE, panel_rows=1248, row_groups=20,
                                 cols_per_warp=32, tile_acc=1)
                 else:
                     sk.set_plan(capi.SKETCH_MODE_TILE, panel_rows=1024, row_groups=80,

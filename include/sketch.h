@@ -97,23 +97,23 @@ typedef struct {
  * TILE: S is cut into tiles of 32 rows (d1) and A into panels of
  * `panel_rows` rows (m1) and blocks of n1 columns; a CTA generates each
  * (tile, panel) block of S once and sweeps the panel's nonzeros in its
- * columns.  tile_acc = 0: 16 warps, n1 = 16*cols_per_warp, running sums in
- * registers; a CTA takes one of `row_groups` ranges of panels of one tile,
- * and the groups' partial copies of A_hat are added in group order.
- * tile_acc = 1: 32 warps, cols_per_warp = 32, n1 = 1024, running sums in
- * tensor memory in two levels (the first restarts into the second every 32
- * panels); `row_groups` CTAs per column block each take a contiguous share
- * of equal cost of the (tile, panel) blocks in tile-major order, and tiles
- * that several CTAs share are added in CTA order.  Where a CTA owns whole
- * tiles of at most 32 panels, the two forms give the same bits. */
+ * columns, and the panels form `row_groups` contiguous ranges.
+ * tile_acc = 0: 16 warps, n1 = 16*cols_per_warp, running sums in registers;
+ * a CTA takes one range of one tile, and the ranges' partial copies of A_hat
+ * are added in order.  tile_acc = 1: 32 warps, cols_per_warp = 32,
+ * n1 = 1024, running sums in tensor memory; one wave of CTAs (one per SM,
+ * over the column blocks) walks the ranges in order, each CTA taking the
+ * same share of every range's (tile, panel) blocks and adding its sums per
+ * range into a scratch copy of its tiles; tiles that several CTAs share are
+ * added in CTA order.  The additions per tile are those of tile_acc = 0
+ * (sums within a range, then ranges in order), so where every CTA owns
+ * whole tiles the two give the same bits. */
 typedef struct {
   int32_t mode;          /* sketch_mode                                   */
   int32_t q_tiles;       /* REGEN: 1..4 blocks of 128 rows of S per warp  */
   int32_t split;         /* REGEN: 1, 2, 4 or 8 warps per column           */
   int32_t n_block;       /* PANEL: columns per CTA (<= 1536)               */
-  int32_t row_groups;    /* PANEL, TILE (tile_acc = 0): number of row      */
-                         /* ranges of A; TILE (tile_acc = 1): CTAs per     */
-                         /* column block                                   */
+  int32_t row_groups;    /* PANEL, TILE: number of row ranges of A         */
   int32_t panel_rows;    /* TILE: rows of A per panel, 8..1248 (m1)        */
   int32_t cols_per_warp; /* TILE: 4, 16 or 64 (32 with tile_acc = 1)       */
   int32_t tc_min_row_nnz;/* +-1 only: rows of A with at least this many     */

@@ -80,9 +80,9 @@ static size_t align256(size_t b) { return (b + 255) / 256 * 256; }
 
 // TILE plan for a panel height R: columns per warp covering n (up to 1024
 // per CTA).  Register sums: row groups that fill the GPU and keep each
-// column's partial sums to ~512 terms.  Tensor-memory sums: one CTA per SM
-// (spread over the column blocks), each a balanced share of the work; two
-// levels of sums keep the chains short.
+// column's partial sums to ~512 terms.  Tensor-memory sums: one wave of CTAs
+// walks the row groups in order, so the groups only bound the chains (~512
+// terms) and the slice of A shared in L2 (at least 8 groups).
 sketch_plan tile_plan(const sketch_s* h, const sketch_csc* A, int32_t R, int32_t tile_acc) {
   sketch_plan p{};
   p.mode = SKETCH_MODE_TILE;
@@ -98,8 +98,8 @@ sketch_plan tile_plan(const sketch_s* h, const sketch_csc* A, int32_t R, int32_t
   const int64_t P = (A->m + R - 1) / R;
   const double avg_col = A->n > 0 ? double(A->nnz) / double(A->n) : 0.0;
   if (p.tile_acc) {
-    const int64_t g = std::max<int64_t>(1, num_sms() / cblocks);
-    p.row_groups = static_cast<int32_t>(std::min<int64_t>({g, tiles * P, 65535}));
+    const int64_t g = std::max<int64_t>(8, static_cast<int64_t>(std::ceil(avg_col / 512.0)));
+    p.row_groups = static_cast<int32_t>(std::max<int64_t>(1, std::min<int64_t>({g, P, 4096})));
     return p;
   }
   const int per_sm = 1;
@@ -427,10 +427,8 @@ int run_sparse(sketch_t h, const sketch_csc* A, float* Ahat, const sketch_plan& 
     a.R = p.panel_rows;
     // register sums: at most one row group per panel; tensor-memory sums:
     // the shares the workspace was sized for (an empty share does nothing)
-    a.G = p.tile_acc ? p.row_groups
-                     : std::min<int32_t>(p.row_groups, static_cast<int32_t>(
-                                                           (A->m + p.panel_rows - 1) /
-                                                           p.panel_rows));
+    a.G = std::min<int32_t>(p.row_groups,
+                            static_cast<int32_t>((A->m + p.panel_rows - 1) / p.panel_rows));
     a.cpw = p.cols_per_warp;
     a.tacc = p.tile_acc;
     a.status = status;
@@ -579,7 +577,7 @@ static uint64_t feature_key(const sketch_s* h, const sketch_csc* A, const Featur
   mix(static_cast<uint64_t>(32 * f.heavy_nnz / std::max<int64_t>(1, A->nnz)));
   mix(static_cast<uint64_t>(lg(f.max_row)));
   mix(static_cast<uint64_t>(lg(f.max_col)));
-  mix(4);  // version of the plan set (4: tensor-memory TILE shares)
+  mix(5);  // version of the plan set (5: tensor-memory TILE phases)
   return k;
 }
 
@@ -948,7 +946,8 @@ int sketch_apply_pregen(sketch_t h, const sketch_csc* A, const float* S, int64_t
   a.stream_id = h->stream_id;
   a.dist = 3;  // S from memory
   a.R = p.panel_rows;
-  a.G = p.row_groups;  // the shares the workspace was sized for
+  a.G = std::min<int32_t>(p.row_groups,
+                          static_cast<int32_t>((A->m + p.panel_rows - 1) / p.panel_rows));
   a.cpw = 32;
   a.tacc = 1;
   a.status = reinterpret_cast<int*>(h->d_small);

@@ -868,49 +868,24 @@ __device__ __forceinline__ void tmem_wait_st() {
   asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
 
-// Tensor-memory sums (TACC = true) are balanced over the CTAs instead of cut
-// into row groups: the CTAs of a column block split the tile-major sequence
-// of units u = tile * P + panel into contiguous shares of equal cost (a
-// unit's cost: its nonzeros plus a per-row weight for generating S), one
-// share per CTA.  A CTA that covers a whole tile writes its sums straight to
-// A_hat; the others write them to a slot (the CTA's k-th tile), and
-// k_reduce_segments adds a tile's slots in CTA order.  Every tile costs the
-// same, so at most ceil(tiles / CTAs) + 1 tiles meet one CTA and
-// ceil(CTAs / tiles) + 1 CTAs meet one tile.  Long shares keep FP32 chains
-// short with two levels of sums: every kTileLevelPanels panels of a tile the
-// running sums are added into a second set and restarted.
-constexpr int kTileLevelPanels = 32;
+// Tensor-memory sums (TACC = true) run as one wave of C CTAs per column
+// block that walk the G row groups ("phases") in order; in every phase CTA c
+// takes the same share c / C of the phase's units u = tile * Pp + panel
+// (tile-major, Pp panels), so all CTAs sweep the same panels of A at about
+// the same time (shared in L2) and every share costs the same (a tile's
+// units of one phase are the same panels).  A share meets at most
+// ceil(tiles / C) + 1 tiles, always from tile c * tiles / C on.  After a
+// tile's units of a phase the CTA adds its tensor-memory sums into that
+// tile's slot (a 32 x n block in global memory, L2-resident), so each tile
+// gets the register path's additions: running sums over a row group, then
+// the row groups in order.  A tile one CTA owns entirely goes straight to
+// A_hat after the last phase; the other tiles' slots are added in CTA order
+// by k_reduce_segments.
 
-// Weight of a row of A in a unit's cost, in quarters of a nonzero: the time
-// of generating one row of a 32-row S tile against sweeping one nonzero.
-__host__ __device__ constexpr int64_t tile_row_cost4(int dist) {
-  return dist == kNormal ? 16 : dist == kUniform ? 5 : dist == kFromMemory ? 8 : 4;
-}
-// Cost (in quarters) of panels [0, p) of one tile.
-__device__ __forceinline__ int64_t tile_cost_prefix(int32_t p, int32_t m, int32_t n, int32_t R,
-                                                    int64_t w4, const int32_t* __restrict__ off,
-                                                    int32_t nnz) {
-  const int64_t rows = min(static_cast<int64_t>(p) * R, static_cast<int64_t>(m));
-  const int64_t e = min(off[static_cast<int64_t>(p) * (n + 1)], nnz);
-  return w4 * rows + 4 * e;
-}
-// First unit of CTA c of C: the first unit whose cost prefix reaches
-// c / C of the total (c = C gives tiles * P).
-__device__ int32_t tile_share_start(int c, int C, int tiles, int32_t P, int32_t m, int32_t n,
-                                    int32_t R, int64_t w4, const int32_t* __restrict__ off,
-                                    int32_t nnz) {
-  const int64_t ctile = tile_cost_prefix(P, m, n, R, w4, off, nnz);
-  if (c >= C || ctile <= 0) return c >= C ? tiles * P : 0;
-  // floor(ctile * tiles * c / C) without the 64-bit overflow of the product
-  const int64_t tc = static_cast<int64_t>(tiles) * c;
-  const int64_t target = ctile * (tc / C) + ctile * (tc % C) / C;
-  const int64_t x = target / ctile, r = target - x * ctile;
-  int32_t lo = 0, hi = P;  // the first p with prefix(p) >= r
-  while (lo < hi) {
-    const int32_t mid = lo + ((hi - lo) >> 1);
-    if (tile_cost_prefix(mid, m, n, R, w4, off, nnz) < r) lo = mid + 1; else hi = mid;
-  }
-  return static_cast<int32_t>(x * P + lo);
+// CTA c of C owns all of tile x in every phase.
+__host__ __device__ __forceinline__ bool tile_whole(int64_t x, int64_t c, int64_t tiles,
+                                                    int64_t C) {
+  return c * tiles <= x * C && (c + 1) * tiles >= (x + 1) * C;
 }
 
 // TACC = false: 16 warps; the CTA's 32 x (16 * CPW) accumulators live in
@@ -921,17 +896,16 @@ __device__ int32_t tile_share_start(int c, int C, int tiles, int32_t P, int32_t 
 // TACC = true (CPW = 32 only): 32 warps, and the 32 x 1024 accumulators live
 // in tensor memory, 256 columns per CTA (warp w: lanes 32 (w % 4) ..,
 // columns 32 (w / 4) ..), each quad's float4 read, added to and written back
-// after its sweep, the second level of sums 256 columns further; at <= 64
-// registers per thread the SM runs 8 warps per scheduler with the same panel
-// height.  Grid (G, column blocks): CTA blockIdx.x takes share blockIdx.x of
-// G (see above), records its first unit in `bounds` and writes whole tiles
-// to A_hat, the rest to its slots (kslots per CTA, n x 32 floats each).
+// after its sweep; at <= 64 registers per thread the SM runs 8 warps per
+// scheduler with the same panel height.  Grid (C, column blocks): see above;
+// `slots` holds kslots blocks of n x 32 floats per CTA and `sflags` marks
+// the ones k_reduce_segments adds.
 template <int DIST, int CPW, bool TACC>
 __global__ void __launch_bounds__(tile_warps(TACC) * 32, 1)
     k_tile(int32_t m, int32_t n, int32_t d, int32_t R, int32_t P, int32_t G,
            const int2* __restrict__ packed, const int32_t* __restrict__ off, int32_t nnz,
            float* __restrict__ out, float* __restrict__ slots, int32_t kslots,
-           int32_t* __restrict__ bounds, const __grid_constant__ PhiloxKeys keys,
+           int32_t* __restrict__ sflags, const __grid_constant__ PhiloxKeys keys,
            uint32_t stream_id, unsigned long long* gen_count,
            const float* __restrict__ S_mem, int64_t ld_s) {
   static_assert(CPW % 4 == 0, "columns per warp come in quads");
@@ -957,23 +931,11 @@ __global__ void __launch_bounds__(tile_warps(TACC) * 32, 1)
   // this warp's columns: kw0 .. kw0 + ncol - 1 (contiguous)
   const int32_t kw0 = blockIdx.y * (kWarps * CPW) + warp * CPW;
   const int32_t ncol = max(0, min(CPW, n - kw0));
-  // this CTA's units [u0, u1): tensor-memory sums, of the tile-major order
-  // u = tile * P + panel; register sums, the panels of tile blockIdx.x
-  int32_t u0, u1;
-  if constexpr (TACC) {
-    const int64_t w4 = tile_row_cost4(DIST);
-    const int tiles = (d + 31) / 32;
-    u0 = tile_share_start(blockIdx.x, G, tiles, P, m, n, R, w4, off, nnz);
-    u1 = tile_share_start(blockIdx.x + 1, G, tiles, P, m, n, R, w4, off, nnz);
-    if (blockIdx.y == 0 && threadIdx.x == 0) {
-      bounds[blockIdx.x] = u0;
-      if (blockIdx.x == G - 1) bounds[G] = u1;
-    }
-  } else {
-    const int32_t g = blockIdx.z;
-    u0 = static_cast<int32_t>(static_cast<int64_t>(P) * g / G);
-    u1 = static_cast<int32_t>(static_cast<int64_t>(P) * (g + 1) / G);
-  }
+  const int tiles = (d + 31) / 32;
+  // tensor-memory sums: C CTAs per column block; share c starts in tile x0
+  const int32_t C = TACC ? static_cast<int32_t>(gridDim.x) : 1;
+  const int32_t c = blockIdx.x;
+  const int32_t x0 = TACC ? static_cast<int32_t>(static_cast<int64_t>(c) * tiles / C) : c;
   const float* S_lane = S_tile + 4 * i4;
   constexpr int OFFR = (CPW + 32) / 32;  // registers holding CPW + 1 offsets
   constexpr int NQ = CPW / 4;
@@ -984,7 +946,7 @@ __global__ void __launch_bounds__(tile_warps(TACC) * 32, 1)
     if (warp == 0) {
       asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                        static_cast<uint32_t>(__cvta_generic_to_shared(tmem_slot))),
-                   "r"(2 * kTmemCols)
+                   "r"(kTmemCols)
                    : "memory");
       asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -996,10 +958,6 @@ __global__ void __launch_bounds__(tile_warps(TACC) * 32, 1)
 #pragma unroll
     for (int q = 0; q < NQ; ++q) acc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
   }
-  // TACC: the first-level sums restart (are overwritten, not added to) after
-  // they were added into the second level
-  bool fresh = false;
-  int since = 0;  // panels of the current tile since the last restart
   // this warp's column offsets of panel p (CPW + 1 values over OFFR
   // registers); the next unit's are loaded while the current one is swept
   int32_t offv[OFFR];
@@ -1007,347 +965,323 @@ __global__ void __launch_bounds__(tile_warps(TACC) * 32, 1)
     const int32_t* offp = off + static_cast<int64_t>(p) * (n + 1) + kw0;
 #pragma unroll
     for (int u = 0; u < OFFR; ++u) {
-      const int c = lane + 32 * u;
+      const int cc = lane + 32 * u;
       // at most nnz (malformed input can push the scanned offsets past it)
-      offv[u] = (ncol > 0 && c <= ncol && valid) ? min(offp[c], nnz) : 0;
+      offv[u] = (ncol > 0 && cc <= ncol && valid) ? min(offp[cc], nnz) : 0;
     }
   };
-  // the current tile's sums to A_hat (a whole tile) or to this CTA's slot
-  auto flush = [&](int x) {
+  // TACC: a share meets tiles x0 .. in every phase, so the slots holding
+  // sums of earlier phases are those of tiles x0 .. xseen
+  int xseen = x0 - 1;
+  // the sums of tile x over this phase's units: register sums to their row
+  // group's copy (or A_hat); tensor-memory sums added into the tile's slot,
+  // or, for a tile this CTA owns, into A_hat after the last phase
+  auto flush = [&](int x, bool last_phase) {
     const int rows_valid = min(32, d - x * 32);
-    bool whole = true;
-    if constexpr (TACC) whole = u0 <= x * P && u1 >= (x + 1) * P;
-    float* base;
-    int64_t ld;
-    if (whole) {
-      base = out + (TACC ? 0 : static_cast<int64_t>(blockIdx.z) * n * d) + x * 32;
-      ld = d;
-    } else {
-      base = slots + (static_cast<int64_t>(blockIdx.x) * kslots + (x - u0 / P)) * n * 32;
-      ld = 32;
-    }
+    const int k = x - x0;
+    const bool has = TACC && x <= xseen;
+    const bool to_out = !TACC || (last_phase && tile_whole(x, c, tiles, C));
+    float* o_base = out + (TACC ? 0 : static_cast<int64_t>(blockIdx.z) * n * d) + x * 32;
+    float* s_base = TACC ? slots + (static_cast<int64_t>(c) * kslots + k) * n * 32 : nullptr;
 #pragma unroll
     for (int q = 0; q < NQ; ++q) {
-      const int c = 4 * q + cg;
+      const int col = kw0 + 4 * q + cg;
       if (4 * q < ncol) {  // warp-uniform
         float4 r;
         if constexpr (TACC) {
-          uint32_t t1[4], t2[4];
-          tmem_ld4(tacc + 4 * q, t1);
-          tmem_ld4(tacc + kTmemCols + 4 * q, t2);
-          tmem_wait_ld4(t1);
-          tmem_wait_ld4(t2);
-          // level two holds zeros until the first restart: 0 + s = s exactly
-          r = fresh ? make_float4(__uint_as_float(t2[0]), __uint_as_float(t2[1]),
-                                  __uint_as_float(t2[2]), __uint_as_float(t2[3]))
-                    : make_float4(__uint_as_float(t2[0]) + __uint_as_float(t1[0]),
-                                  __uint_as_float(t2[1]) + __uint_as_float(t1[1]),
-                                  __uint_as_float(t2[2]) + __uint_as_float(t1[2]),
-                                  __uint_as_float(t2[3]) + __uint_as_float(t1[3]));
+          uint32_t t[4];
+          tmem_ld4(tacc + 4 * q, t);
+          tmem_wait_ld4(t);
+          r = make_float4(__uint_as_float(t[0]), __uint_as_float(t[1]), __uint_as_float(t[2]),
+                          __uint_as_float(t[3]));
         } else {
           r = acc[q];
         }
-        if (c < ncol) {
-          float* o = base + static_cast<int64_t>(kw0 + c) * ld + 4 * i4;
-          if (4 * i4 + 0 < rows_valid) o[0] = r.x;
-          if (4 * i4 + 1 < rows_valid) o[1] = r.y;
-          if (4 * i4 + 2 < rows_valid) o[2] = r.z;
-          if (4 * i4 + 3 < rows_valid) o[3] = r.w;
+        if (col < n) {
+          float4* sp = TACC ? reinterpret_cast<float4*>(s_base + static_cast<int64_t>(col) * 32 +
+                                                       4 * i4)
+                            : nullptr;
+          if (has) {  // earlier phases first: the row groups' order
+            const float4 e = *sp;
+            r = make_float4(e.x + r.x, e.y + r.y, e.z + r.z, e.w + r.w);
+          }
+          if (to_out) {
+            float* o = o_base + static_cast<int64_t>(col) * d + 4 * i4;
+            if (4 * i4 + 0 < rows_valid) o[0] = r.x;
+            if (4 * i4 + 1 < rows_valid) o[1] = r.y;
+            if (4 * i4 + 2 < rows_valid) o[2] = r.z;
+            if (4 * i4 + 3 < rows_valid) o[3] = r.w;
+          } else {
+            *sp = r;
+          }
         }
       }
     }
   };
-  // TACC: both levels of a new tile's sums start at zero
+  // TACC: a tile's sums start at zero in every phase
   auto zero_sums = [&]() {
     if constexpr (TACC) {
 #pragma unroll
-      for (int q = 0; q < NQ; ++q) {
-        tmem_st4(tacc + 4 * q, make_float4(0.f, 0.f, 0.f, 0.f));
-        tmem_st4(tacc + kTmemCols + 4 * q, make_float4(0.f, 0.f, 0.f, 0.f));
-      }
+      for (int q = 0; q < NQ; ++q) tmem_st4(tacc + 4 * q, make_float4(0.f, 0.f, 0.f, 0.f));
       tmem_wait_st();
-      fresh = false;
-      since = 0;
     }
   };
   int64_t gen_rows = 0;  // S entries generated (thread 0's count)
-  int xcur = -1;
-  if (u0 < u1) load_offsets(TACC ? u0 % P : u0, true);
-
-  for (int32_t u = u0; u < u1; ++u) {
-    const int x = TACC ? u / P : static_cast<int>(blockIdx.x);  // the row tile of S
-    const int32_t p = TACC ? u - x * P : u;                      // the panel of A
-    if (x != xcur) {
-      if (xcur >= 0) flush(xcur);
-      zero_sums();
-      xcur = x;
+  const int nphase = TACC ? G : 1;
+  for (int ph = 0; ph < nphase; ++ph) {
+    // the phase's panels [pa, pa + Pp) and this CTA's units [s0, s1) of them
+    const int32_t g = TACC ? ph : static_cast<int32_t>(blockIdx.z);
+    const int32_t pa = static_cast<int32_t>(static_cast<int64_t>(P) * g / G);
+    const int32_t Pp = static_cast<int32_t>(static_cast<int64_t>(P) * (g + 1) / G) - pa;
+    int32_t s0 = 0, s1 = Pp;
+    if constexpr (TACC) {
+      const int64_t T = static_cast<int64_t>(tiles) * Pp;
+      s0 = static_cast<int32_t>(T * c / C);
+      s1 = static_cast<int32_t>(T * (c + 1) / C);
     }
-    const int rows_valid = min(32, d - x * 32);
-    const int32_t j0 = p * R;
-    const int32_t rows = min(R, m - j0);
-    if constexpr (TACC) gen_rows += static_cast<int64_t>(rows) * rows_valid;
-    // ---- this warp's nonzeros (one contiguous range) copied global ->
-    //      shared asynchronously; the copies land while the S tile is
-    //      generated
-    int32_t e_lo = 0;
-    if (ncol > 0) {
-      e_lo = __shfl_sync(0xffffffffu, offv[0], 0);
-      int32_t o_end = offv[0];  // offv[ncol >> 5] without a dynamic index
-#pragma unroll
-      for (int v = 1; v < OFFR; ++v)
-        if ((ncol >> 5) == v) o_end = offv[v];
-      const int32_t e_hi = __shfl_sync(0xffffffffu, o_end, ncol & 31);
-      const int32_t cnt = min(e_hi - e_lo, wbuf);
-      for (int32_t t = lane; t < cnt; t += 32) {
-        const unsigned dst = static_cast<unsigned>(__cvta_generic_to_shared(ent + t));
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst),
-                     "l"(packed + e_lo + t)
-                     : "memory");
-      }
-#pragma unroll
-      for (int v = 0; v < OFFR; ++v) {
-        const int c = lane + 32 * v;
-        if (c <= ncol) offs[c] = offv[v];
-      }
-    }
-    // ---- S(tile, j0 .. j0 + rows) once into shared memory ---------------
-    for (int idx = threadIdx.x; idx < rows * 8; idx += kWarps * 32) {
-      const int jl = idx >> 3, q = idx & 7;
-      const uint32_t j = static_cast<uint32_t>(j0 + jl);
-      if constexpr (DIST == kFromMemory) {
-        // S read from memory: 16 bytes (rows 4q .. 4q+3 of the tile) by
-        // cp.async; rows past d are zero-filled (src-size below 16)
-        const int valid = min(4, max(0, rows_valid - 4 * q));
-        const float* src = valid > 0 ? S_mem + static_cast<int64_t>(j) * ld_s + x * 32 + 4 * q
-                                     : S_mem;
-        const unsigned dst =
-            static_cast<unsigned>(__cvta_generic_to_shared(&S_tile[jl * 32 + 4 * q]));
-        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src),
-                     "r"(4 * valid)
-                     : "memory");
-      } else {
-        float4 v;
-        if constexpr (DIST == kPM1) {
-          const uint4 xb = philox_block(static_cast<uint32_t>(x >> 2), j, stream_id, keys);
-          const int wsel = x & 3;
-          const uint32_t w =
-              (wsel == 0 ? xb.x : wsel == 1 ? xb.y : wsel == 2 ? xb.z : xb.w) >> (4 * q);
-          v = make_float4((w & 1u) ? -1.f : 1.f, (w & 2u) ? -1.f : 1.f,
-                          (w & 4u) ? -1.f : 1.f, (w & 8u) ? -1.f : 1.f);
-        } else {
-          v = four_entries<DIST>(
-              philox_block(static_cast<uint32_t>(x * 8 + q), j, stream_id, keys));
+    if (s0 >= s1) continue;
+    load_offsets(pa + (TACC ? s0 % Pp : s0), true);
+    int xcur = TACC ? -1 : static_cast<int>(blockIdx.x);
+    for (int32_t u = s0; u < s1; ++u) {
+      const int x = TACC ? u / Pp : static_cast<int>(blockIdx.x);  // the row tile of S
+      const int32_t p = pa + (TACC ? u - x * Pp : u);                // the panel of A
+      if constexpr (TACC) {
+        if (x != xcur) {
+          if (xcur >= 0) flush(xcur, ph == nphase - 1);
+          zero_sums();
+          xcur = x;
         }
-        *reinterpret_cast<float4*>(&S_tile[jl * 32 + 4 * q]) = v;
       }
-    }
-    asm volatile("cp.async.wait_all;" ::: "memory");
-    __syncthreads();
-    // used by the next unit; lands during the sweep
-    if (TACC)
-      load_offsets(p + 1 < P ? p + 1 : 0, u + 1 < u1);
-    else
-      load_offsets(p + 1, p + 1 < u1);
-    // ---- sweep: four columns per step, one per group of eight lanes ------
-    const int32_t buf_end = e_lo + wbuf;
-    // register sums need the quad index at compile time; tensor-memory sums
-    // do not, and a rolled loop keeps them within 64 registers
-    constexpr int kQuadUnroll = TACC ? 1 : NQ;
-#pragma unroll kQuadUnroll
-    for (int q = 0; q < NQ; ++q) {
-      if (4 * q < ncol) {  // warp-uniform
-        const int c = 4 * q + cg;  // this lane's column slot (differs by group)
-        const int32_t lo = offs[c], hi = offs[c + 1];
-        const int32_t cnt = c < ncol ? hi - lo : 0;
-        const int32_t steps = __reduce_max_sync(0xffffffffu, cnt);
-        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (__all_sync(0xffffffffu, c >= ncol || hi <= buf_end)) {
-          // fast path: every entry is staged; lanes past their column's end
-          // read the zero entry at ent[wbuf] (no branch per step).
-          // Two steps per iteration with separate accumulators: both
-          // entries, then both S loads, then the FMAs (more loads in flight)
-          const int2* ep = ent + (lo - e_lo);
-          const int2* zero = ent + wbuf;
-          float4 w = make_float4(0.f, 0.f, 0.f, 0.f);
-          int32_t t = 0;
-          for (; t + 1 < steps; t += 2) {
-            const int2 ja = *(t < cnt ? ep + t : zero);
-            const int2 jb = *(t + 1 < cnt ? ep + t + 1 : zero);
-            const float4 sa = *reinterpret_cast<const float4*>(S_lane + ja.x);
-            const float4 sb = *reinterpret_cast<const float4*>(S_lane + jb.x);
-            const float a = __int_as_float(ja.y), b = __int_as_float(jb.y);
-            v.x = fmaf(a, sa.x, v.x);
-            v.y = fmaf(a, sa.y, v.y);
-            v.z = fmaf(a, sa.z, v.z);
-            v.w = fmaf(a, sa.w, v.w);
-            w.x = fmaf(b, sb.x, w.x);
-            w.y = fmaf(b, sb.y, w.y);
-            w.z = fmaf(b, sb.z, w.z);
-            w.w = fmaf(b, sb.w, w.w);
-          }
-          if (t < steps) {
-            const int2 ja = *(t < cnt ? ep + t : zero);
-            const float4 sa = *reinterpret_cast<const float4*>(S_lane + ja.x);
-            const float a = __int_as_float(ja.y);
-            v.x = fmaf(a, sa.x, v.x);
-            v.y = fmaf(a, sa.y, v.y);
-            v.z = fmaf(a, sa.z, v.z);
-            v.w = fmaf(a, sa.w, v.w);
-          }
-          v.x += w.x;
-          v.y += w.y;
-          v.z += w.z;
-          v.w += w.w;
-        } else {
-          // entries read from global memory; the same split of the sum
-          // (even steps into v, odd steps into w) as the fast path, so the
-          // bits do not depend on how much of the panel was staged
-          float4 w = make_float4(0.f, 0.f, 0.f, 0.f);
-          for (int32_t t = 0; t < steps; t += 2) {
-            if (t < cnt) {
-              const int2 ja = packed[lo + t];
-              const float a = __int_as_float(ja.y);
-              const float4 sv = *reinterpret_cast<const float4*>(S_lane + ja.x);
-              v.x = fmaf(a, sv.x, v.x);
-              v.y = fmaf(a, sv.y, v.y);
-              v.z = fmaf(a, sv.z, v.z);
-              v.w = fmaf(a, sv.w, v.w);
-            }
-            if (t + 1 < cnt) {
-              const int2 jb = packed[lo + t + 1];
-              const float b = __int_as_float(jb.y);
-              const float4 sv = *reinterpret_cast<const float4*>(S_lane + jb.x);
-              w.x = fmaf(b, sv.x, w.x);
-              w.y = fmaf(b, sv.y, w.y);
-              w.z = fmaf(b, sv.z, w.z);
-              w.w = fmaf(b, sv.w, w.w);
-            }
-          }
-          v.x += w.x;
-          v.y += w.y;
-          v.z += w.z;
-          v.w += w.w;
+      const int rows_valid = min(32, d - x * 32);
+      const int32_t j0 = p * R;
+      const int32_t rows = min(R, m - j0);
+      if constexpr (TACC) gen_rows += static_cast<int64_t>(rows) * rows_valid;
+      // ---- this warp's nonzeros (one contiguous range) copied global ->
+      //      shared asynchronously; the copies land while the S tile is
+      //      generated
+      int32_t e_lo = 0;
+      if (ncol > 0) {
+        e_lo = __shfl_sync(0xffffffffu, offv[0], 0);
+        int32_t o_end = offv[0];  // offv[ncol >> 5] without a dynamic index
+#pragma unroll
+        for (int v = 1; v < OFFR; ++v)
+          if ((ncol >> 5) == v) o_end = offv[v];
+        const int32_t e_hi = __shfl_sync(0xffffffffu, o_end, ncol & 31);
+        const int32_t cnt = min(e_hi - e_lo, wbuf);
+        for (int32_t t = lane; t < cnt; t += 32) {
+          const unsigned dst = static_cast<unsigned>(__cvta_generic_to_shared(ent + t));
+          asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst),
+                       "l"(packed + e_lo + t)
+                       : "memory");
         }
-        if constexpr (TACC) {
-          if (fresh) {  // the sums restart with this panel's
-            tmem_st4(tacc + 4 * q, v);
+#pragma unroll
+        for (int v = 0; v < OFFR; ++v) {
+          const int c = lane + 32 * v;
+          if (c <= ncol) offs[c] = offv[v];
+        }
+      }
+      // ---- S(tile, j0 .. j0 + rows) once into shared memory ---------------
+      for (int idx = threadIdx.x; idx < rows * 8; idx += kWarps * 32) {
+        const int jl = idx >> 3, q = idx & 7;
+        const uint32_t j = static_cast<uint32_t>(j0 + jl);
+        if constexpr (DIST == kFromMemory) {
+          // S read from memory: 16 bytes (rows 4q .. 4q+3 of the tile) by
+          // cp.async; rows past d are zero-filled (src-size below 16)
+          const int valid = min(4, max(0, rows_valid - 4 * q));
+          const float* src = valid > 0 ? S_mem + static_cast<int64_t>(j) * ld_s + x * 32 + 4 * q
+                                       : S_mem;
+          const unsigned dst =
+              static_cast<unsigned>(__cvta_generic_to_shared(&S_tile[jl * 32 + 4 * q]));
+          asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src),
+                       "r"(4 * valid)
+                       : "memory");
+        } else {
+          float4 v;
+          if constexpr (DIST == kPM1) {
+            const uint4 xb = philox_block(static_cast<uint32_t>(x >> 2), j, stream_id, keys);
+            const int wsel = x & 3;
+            const uint32_t w =
+                (wsel == 0 ? xb.x : wsel == 1 ? xb.y : wsel == 2 ? xb.z : xb.w) >> (4 * q);
+            v = make_float4((w & 1u) ? -1.f : 1.f, (w & 2u) ? -1.f : 1.f,
+                            (w & 4u) ? -1.f : 1.f, (w & 8u) ? -1.f : 1.f);
           } else {
+            v = four_entries<DIST>(
+                philox_block(static_cast<uint32_t>(x * 8 + q), j, stream_id, keys));
+          }
+          *reinterpret_cast<float4*>(&S_tile[jl * 32 + 4 * q]) = v;
+        }
+      }
+      asm volatile("cp.async.wait_all;" ::: "memory");
+      __syncthreads();
+      // used by the next unit; lands during the sweep
+      load_offsets(pa + (TACC ? (u + 1) % Pp : u + 1), u + 1 < s1);
+      // ---- sweep: four columns per step, one per group of eight lanes ------
+      const int32_t buf_end = e_lo + wbuf;
+      // register sums need the quad index at compile time; tensor-memory sums
+      // do not, and a rolled loop keeps them within 64 registers
+      constexpr int kQuadUnroll = TACC ? 1 : NQ;
+#pragma unroll kQuadUnroll
+      for (int q = 0; q < NQ; ++q) {
+        if (4 * q < ncol) {  // warp-uniform
+          const int c = 4 * q + cg;  // this lane's column slot (differs by group)
+          const int32_t lo = offs[c], hi = offs[c + 1];
+          const int32_t cnt = c < ncol ? hi - lo : 0;
+          const int32_t steps = __reduce_max_sync(0xffffffffu, cnt);
+          float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (__all_sync(0xffffffffu, c >= ncol || hi <= buf_end)) {
+            // fast path: every entry is staged; lanes past their column's end
+            // read the zero entry at ent[wbuf] (no branch per step).
+            // Two steps per iteration with separate accumulators: both
+            // entries, then both S loads, then the FMAs (more loads in flight)
+            const int2* ep = ent + (lo - e_lo);
+            const int2* zero = ent + wbuf;
+            float4 w = make_float4(0.f, 0.f, 0.f, 0.f);
+            int32_t t = 0;
+            for (; t + 1 < steps; t += 2) {
+              const int2 ja = *(t < cnt ? ep + t : zero);
+              const int2 jb = *(t + 1 < cnt ? ep + t + 1 : zero);
+              const float4 sa = *reinterpret_cast<const float4*>(S_lane + ja.x);
+              const float4 sb = *reinterpret_cast<const float4*>(S_lane + jb.x);
+              const float a = __int_as_float(ja.y), b = __int_as_float(jb.y);
+              v.x = fmaf(a, sa.x, v.x);
+              v.y = fmaf(a, sa.y, v.y);
+              v.z = fmaf(a, sa.z, v.z);
+              v.w = fmaf(a, sa.w, v.w);
+              w.x = fmaf(b, sb.x, w.x);
+              w.y = fmaf(b, sb.y, w.y);
+              w.z = fmaf(b, sb.z, w.z);
+              w.w = fmaf(b, sb.w, w.w);
+            }
+            if (t < steps) {
+              const int2 ja = *(t < cnt ? ep + t : zero);
+              const float4 sa = *reinterpret_cast<const float4*>(S_lane + ja.x);
+              const float a = __int_as_float(ja.y);
+              v.x = fmaf(a, sa.x, v.x);
+              v.y = fmaf(a, sa.y, v.y);
+              v.z = fmaf(a, sa.z, v.z);
+              v.w = fmaf(a, sa.w, v.w);
+            }
+            v.x += w.x;
+            v.y += w.y;
+            v.z += w.z;
+            v.w += w.w;
+          } else {
+            // entries read from global memory; the same split of the sum
+            // (even steps into v, odd steps into w) as the fast path, so the
+            // bits do not depend on how much of the panel was staged
+            float4 w = make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int32_t t = 0; t < steps; t += 2) {
+              if (t < cnt) {
+                const int2 ja = packed[lo + t];
+                const float a = __int_as_float(ja.y);
+                const float4 sv = *reinterpret_cast<const float4*>(S_lane + ja.x);
+                v.x = fmaf(a, sv.x, v.x);
+                v.y = fmaf(a, sv.y, v.y);
+                v.z = fmaf(a, sv.z, v.z);
+                v.w = fmaf(a, sv.w, v.w);
+              }
+              if (t + 1 < cnt) {
+                const int2 jb = packed[lo + t + 1];
+                const float b = __int_as_float(jb.y);
+                const float4 sv = *reinterpret_cast<const float4*>(S_lane + jb.x);
+                w.x = fmaf(b, sv.x, w.x);
+                w.y = fmaf(b, sv.y, w.y);
+                w.z = fmaf(b, sv.z, w.z);
+                w.w = fmaf(b, sv.w, w.w);
+              }
+            }
+            v.x += w.x;
+            v.y += w.y;
+            v.z += w.z;
+            v.w += w.w;
+          }
+          if constexpr (TACC) {
             uint32_t prev[4];  // the quad's running sums
             tmem_ld4(tacc + 4 * q, prev);
             tmem_wait_ld4(prev);
-            tmem_st4(tacc + 4 * q, make_float4(__uint_as_float(prev[0]) + v.x,
-                                               __uint_as_float(prev[1]) + v.y,
-                                               __uint_as_float(prev[2]) + v.z,
-                                               __uint_as_float(prev[3]) + v.w));
-          }
-        } else {
-          acc[q].x += v.x;
-          acc[q].y += v.y;
-          acc[q].z += v.z;
-          acc[q].w += v.w;
-        }
-      }
-    }
-    if constexpr (TACC) {
-      fresh = false;
-      // every kTileLevelPanels panels: level two += level one, which restarts
-      if (++since == kTileLevelPanels) {
-        tmem_wait_st();  // the sweep's stores land before they are read back
-#pragma unroll 1
-        for (int q = 0; q < NQ; ++q) {
-          if (4 * q < ncol) {
-            uint32_t t1[4], t2[4];
-            tmem_ld4(tacc + 4 * q, t1);
-            tmem_ld4(tacc + kTmemCols + 4 * q, t2);
-            tmem_wait_ld4(t1);
-            tmem_wait_ld4(t2);
-            tmem_st4(tacc + kTmemCols + 4 * q,
-                     make_float4(__uint_as_float(t2[0]) + __uint_as_float(t1[0]),
-                                 __uint_as_float(t2[1]) + __uint_as_float(t1[1]),
-                                 __uint_as_float(t2[2]) + __uint_as_float(t1[2]),
-                                 __uint_as_float(t2[3]) + __uint_as_float(t1[3])));
+            tmem_st4(tacc + 4 * q,
+                     make_float4(__uint_as_float(prev[0]) + v.x, __uint_as_float(prev[1]) + v.y,
+                                 __uint_as_float(prev[2]) + v.z, __uint_as_float(prev[3]) + v.w));
+          } else {
+            acc[q].x += v.x;
+            acc[q].y += v.y;
+            acc[q].z += v.z;
+            acc[q].w += v.w;
           }
         }
-        fresh = true;
-        since = 0;
       }
-      // this panel's stores complete before the next panel reads them
-      tmem_wait_st();
+      // TACC: this panel's stores complete before the next panel reads them
+      if constexpr (TACC) tmem_wait_st();
+      __syncthreads();
     }
-    __syncthreads();
+    flush(xcur, ph == nphase - 1);
+    xseen = max(xseen, xcur);
+    if constexpr (!TACC)  // one tile: the rows of panels [pa, pa + Pp)
+      gen_rows = (min(static_cast<int64_t>(pa + Pp) * R, static_cast<int64_t>(m)) -
+                  static_cast<int64_t>(pa) * R) *
+                 min(32, d - static_cast<int>(blockIdx.x) * 32);
   }
-  if (xcur >= 0) flush(xcur);
   if constexpr (TACC) {
+    // the slots k_reduce_segments adds: tiles met but not owned
+    if (blockIdx.y == 0)
+      for (int k = threadIdx.x; k < kslots; k += blockDim.x)
+        sflags[static_cast<int64_t>(c) * kslots + k] =
+            (x0 + k <= xseen && !tile_whole(x0 + k, c, tiles, C)) ? 1 : 0;
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0)
       asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(*tmem_slot),
-                   "r"(2 * kTmemCols)
+                   "r"(kTmemCols)
                    : "memory");
-  }
-  if constexpr (!TACC) {  // one tile: the rows of its panels [u0, u1)
-    if (u1 > u0)
-      gen_rows = (min(static_cast<int64_t>(u1) * R, static_cast<int64_t>(m)) -
-                  static_cast<int64_t>(u0) * R) *
-                 min(32, d - static_cast<int>(blockIdx.x) * 32);
   }
   if (gen_count && threadIdx.x == 0 && gen_rows > 0)
     atomicAdd(gen_count, static_cast<unsigned long long>(gen_rows));
 }
 
-// Tensor-memory TILE: A_hat's tiles that several CTAs shared, as the sum of
-// their slots in CTA order.  bounds[c] is CTA c's first unit (bounds[G] =
-// tiles * P).  Block (tile x, 128-column chunk); warp w, lane = row of the
-// tile.  Tiles one CTA covered were written by that CTA.
+// Tensor-memory TILE: the tiles of A_hat that several CTAs met, as the sum
+// of their slots in CTA order (C CTAs; share c starts in tile
+// c * tiles / C, its slot k holds tile c * tiles / C + k and is flagged in
+// sflags when it is to be added).  Block (tile x, 128-column chunk); warp w,
+// lane = row of the tile.  A tile one CTA owns was written by that CTA.
 __global__ void __launch_bounds__(256)
-    k_reduce_segments(int32_t n, int32_t d, int32_t P, int32_t G, int32_t kslots,
-                      const int32_t* __restrict__ bounds, const float* __restrict__ slots,
+    k_reduce_segments(int32_t n, int32_t d, int32_t C, int32_t kslots,
+                      const int32_t* __restrict__ sflags, const float* __restrict__ slots,
                       float* __restrict__ Ahat) {
-  __shared__ int32_t cr[2];
-  const int x = blockIdx.x;
-  if (threadIdx.x == 0) {
-    // first CTA: the last with bounds <= x P; last CTA: the last with
-    // bounds < (x + 1) P
-    int lo = 0, hi = G;
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (bounds[mid] <= x * P) lo = mid; else hi = mid - 1;
-    }
-    cr[0] = lo;
-    lo = 0;
-    hi = G;
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (bounds[mid] < (x + 1) * P) lo = mid; else hi = mid - 1;
-    }
-    cr[1] = lo;
-  }
-  __syncthreads();
-  const int c0 = cr[0], c1 = min(cr[1], G - 1);
-  if (c0 >= c1) return;
+  const int64_t tiles = (d + 31) / 32, x = blockIdx.x;
+  const int64_t cw = x * C / tiles;
+  if (tile_whole(x, cw, tiles, C)) return;
+  // the CTAs whose shares can meet tile x
+  const int64_t c_lo = max(int64_t(0), cw - 1);
+  const int64_t c_hi = min(int64_t(C) - 1, ((x + 1) * C + tiles - 1) / tiles);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int row = x * 32 + lane;
+  const int64_t row = x * 32 + lane;
   if (row >= d) return;
   const int col_end = min(n, static_cast<int>(blockIdx.y + 1) * 128);
   for (int col = blockIdx.y * 128 + warp; col < col_end; col += 8) {
-    float s = 0.f;
+    float acc_s = 0.f;
     bool first = true;
-    for (int c = c0; c <= c1; ++c) {
-      const int32_t b0 = bounds[c];
-      if (b0 >= bounds[c + 1]) continue;  // an empty share
-      const float v = slots[((static_cast<int64_t>(c) * kslots + (x - b0 / P)) * n + col) * 32 +
-                            lane];
-      s = first ? v : s + v;
+    for (int64_t c = c_lo; c <= c_hi; ++c) {
+      const int64_t k = x - c * tiles / C;
+      if (k < 0 || k >= kslots || !sflags[c * kslots + k]) continue;
+      const float v = slots[((c * kslots + k) * n + col) * 32 + lane];
+      acc_s = first ? v : acc_s + v;
       first = false;
     }
-    Ahat[static_cast<int64_t>(col) * d + row] = s;
+    Ahat[static_cast<int64_t>(col) * d + row] = acc_s;
   }
 }
 
-// Slots per CTA of the tensor-memory TILE: tiles one share can meet.
-int32_t tile_kslots(int32_t d, int32_t G) {
+// Slots per CTA of the tensor-memory TILE (C CTAs per column block): the
+// tiles one share can meet.
+int32_t tile_kslots(int32_t d, int32_t C) {
   const int32_t tiles = (d + 31) / 32;
-  return (tiles + G - 1) / G + 1;
+  return (tiles + C - 1) / C + 1;
+}
+
+// CTAs per column block of the tensor-memory TILE: one wave on the GPU.
+int32_t tile_ctas(int32_t n) {
+  const int32_t cblocks = (n + 1023) / 1024;
+  return std::max(1, num_sms() / std::max(1, cblocks));
 }
 
 size_t tile_workspace_bytes(int64_t m, int64_t n, int64_t d, int64_t nnz,
@@ -1357,10 +1291,10 @@ size_t tile_workspace_bytes(int64_t m, int64_t n, int64_t d, int64_t nnz,
   size_t b = align256(nnz * sizeof(int2)) + align256((P + 1) * n * sizeof(int32_t)) +
              2 * align256(cells * sizeof(int32_t)) +
              align256(static_cast<size_t>(scan_levels_bytes(cells)));
-  if (tacc) {  // the CTAs' slots and first units
-    b += align256(static_cast<size_t>(G) * tile_kslots(static_cast<int32_t>(d), G) * n * 32 *
-                  sizeof(float)) +
-         align256((static_cast<size_t>(G) + 1) * sizeof(int32_t));
+  if (tacc) {  // the CTAs' slots and their flags
+    const int32_t C = tile_ctas(static_cast<int32_t>(n));
+    const size_t nslots = static_cast<size_t>(C) * tile_kslots(static_cast<int32_t>(d), C);
+    b += align256(nslots * n * 32 * sizeof(float)) + align256(nslots * sizeof(int32_t));
   } else if (G > 1) {
     b += align256(static_cast<size_t>(G) * n * d * sizeof(float));
   }
@@ -1390,9 +1324,10 @@ cudaError_t launch_tile(const TileArgs& a, void* ws, cudaStream_t s, int* launch
   char* scan_tmp = p;
   p += align256(static_cast<size_t>(scan_levels_bytes(cells)));
   float* partial = reinterpret_cast<float*>(p);  // row groups' copies, or the CTAs' slots
-  const int32_t kslots = a.tacc ? tile_kslots(a.d, a.G) : 0;
-  int32_t* bounds = reinterpret_cast<int32_t*>(
-      p + (a.tacc ? align256(static_cast<size_t>(a.G) * kslots * a.n * 32 * sizeof(float)) : 0));
+  const int32_t C = a.tacc ? tile_ctas(a.n) : 1;  // tensor-memory sums: CTAs per column block
+  const int32_t kslots = a.tacc ? tile_kslots(a.d, C) : 0;
+  int32_t* sflags = reinterpret_cast<int32_t*>(
+      p + (a.tacc ? align256(static_cast<size_t>(C) * kslots * a.n * 32 * sizeof(float)) : 0));
   const int sms = num_sms();
   cudaError_t e;
   if (!a.prepared) {  // the panel-major copy of A, its panel pointers and offsets
@@ -1423,9 +1358,9 @@ cudaError_t launch_tile(const TileArgs& a, void* ws, cudaStream_t s, int* launch
   const int cblocks = (a.n + cols_per_cta - 1) / cols_per_cta;
   if (cblocks > 65535 || a.G > 65535) return cudaErrorInvalidValue;
   if (static_cast<int64_t>(tiles) * P >= (int64_t(1) << 31)) return cudaErrorInvalidValue;
-  // tensor-memory sums: G balanced shares per column block; register sums:
-  // G row groups of each row tile
-  const dim3 grid = a.tacc ? dim3(a.G, cblocks, 1) : dim3(tiles, cblocks, a.G);
+  // tensor-memory sums: C CTAs per column block walking G phases; register
+  // sums: G row groups of each row tile
+  const dim3 grid = a.tacc ? dim3(C, cblocks, 1) : dim3(tiles, cblocks, a.G);
   const dim3 block(tile_warps(a.tacc != 0) * 32);
   const size_t smem = tile_smem_bytes(a.R, a.tacc);
   const PhiloxKeys keys = philox_keys(a.k0, a.k1);
@@ -1443,7 +1378,7 @@ cudaError_t launch_tile(const TileArgs& a, void* ws, cudaStream_t s, int* launch
                                                  static_cast<int32_t>(P), a.G,   \
                                                  packed, off,                    \
                                                  static_cast<int32_t>(a.nnz), dst, \
-                                                 partial, kslots, bounds, keys,  \
+                                                 partial, kslots, sflags, keys,  \
                                                  a.stream_id, a.gen_count,       \
                                                  a.S_mem, a.ld_s);               \
     ++*launches;                                                                 \
@@ -1461,10 +1396,9 @@ cudaError_t launch_tile(const TileArgs& a, void* ws, cudaStream_t s, int* launch
   if (!launched) return cudaErrorInvalidValue;
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (a.tacc) {
-    if (a.G > 1) {  // the tiles that several CTAs shared
+    if (C > 1) {  // the tiles that several CTAs met
       const dim3 rgrid(tiles, (a.n + 127) / 128);
-      k_reduce_segments<<<rgrid, 256, 0, s>>>(a.n, a.d, static_cast<int32_t>(P), a.G, kslots,
-                                             bounds, partial, a.Ahat);
+      k_reduce_segments<<<rgrid, 256, 0, s>>>(a.n, a.d, C, kslots, sflags, partial, a.Ahat);
       ++*launches;
       e = cudaGetLastError();
     }

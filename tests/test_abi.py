@@ -135,7 +135,7 @@ def test_heuristic_plans_need_no_gpu():
         p = plan(2_000_000, 1000, 3000, dist, 10_000_000)
         assert (p["mode"], p["panel_rows"], p["cols_per_warp"], p["tile_acc"]) == \
             (capi.SKETCH_MODE_TILE, 1248, 32, 1)
-        assert p["row_groups"] >= 1           # one CTA per SM (none here: 1)
+        assert p["row_groups"] >= 20          # <= 512 terms of a column per range
         p = plan(100_000, 200, 400, dist, 1_000_000)
         assert (p["mode"], p["panel_rows"], p["cols_per_warp"], p["tile_acc"]) == \
             (capi.SKETCH_MODE_TILE, 1024, 16, 0)
