@@ -874,7 +874,7 @@ __device__ __forceinline__ void tmem_wait_st() {
 // (tile-major, Pp panels), so all CTAs sweep the same panels of A at about
 // the same time (shared in L2) and every share costs the same (a tile's
 // units of one phase are the same panels).  A share meets at most
-// ceil(tiles / C) + 1 tiles, always from tile c * tiles / C on.  After a
+// ceil(tiles / C) + 1 tiles, from tile c * tiles / C or the next on.  After a
 // tile's units of a phase the CTA adds its tensor-memory sums into that
 // tile's slot (a 32 x n block in global memory, L2-resident), so each tile
 // gets the register path's additions: running sums over a row group, then
@@ -970,16 +970,17 @@ __global__ void __launch_bounds__(tile_warps(TACC) * 32, 1)
       offv[u] = (ncol > 0 && cc <= ncol && valid) ? min(offp[cc], nnz) : 0;
     }
   };
-  // TACC: a share meets tiles x0 .. in every phase, so the slots holding
-  // sums of earlier phases are those of tiles x0 .. xseen
-  int xseen = x0 - 1;
+  // TACC: a share meets a run of tiles in every phase, starting at x0 or
+  // x0 + 1, so the slots holding sums of earlier phases are those of the
+  // tiles xlo .. xhi
+  int xlo = 0x7fffffff, xhi = -1;
   // the sums of tile x over this phase's units: register sums to their row
   // group's copy (or A_hat); tensor-memory sums added into the tile's slot,
   // or, for a tile this CTA owns, into A_hat after the last phase
   auto flush = [&](int x, bool last_phase) {
     const int rows_valid = min(32, d - x * 32);
     const int k = x - x0;
-    const bool has = TACC && x <= xseen;
+    const bool has = TACC && xlo <= x && x <= xhi;
     const bool to_out = !TACC || (last_phase && tile_whole(x, c, tiles, C));
     float* o_base = out + (TACC ? 0 : static_cast<int64_t>(blockIdx.z) * n * d) + x * 32;
     float* s_base = TACC ? slots + (static_cast<int64_t>(c) * kslots + k) * n * 32 : nullptr;
@@ -1035,9 +1036,12 @@ __global__ void __launch_bounds__(tile_warps(TACC) * 32, 1)
     const int32_t Pp = static_cast<int32_t>(static_cast<int64_t>(P) * (g + 1) / G) - pa;
     int32_t s0 = 0, s1 = Pp;
     if constexpr (TACC) {
+      // the rounding offset turns with the phase, so the shares one unit
+      // larger than the others are not always the same CTAs'
       const int64_t T = static_cast<int64_t>(tiles) * Pp;
-      s0 = static_cast<int32_t>(T * c / C);
-      s1 = static_cast<int32_t>(T * (c + 1) / C);
+      const int64_t rho = static_cast<int64_t>(ph) * C / G;
+      s0 = static_cast<int32_t>((T * c + rho) / C);
+      s1 = static_cast<int32_t>((T * (c + 1) + rho) / C);
     }
     if (s0 >= s1) continue;
     load_offsets(pa + (TACC ? s0 % Pp : s0), true);
@@ -1215,7 +1219,8 @@ __global__ void __launch_bounds__(tile_warps(TACC) * 32, 1)
       __syncthreads();
     }
     flush(xcur, ph == nphase - 1);
-    xseen = max(xseen, xcur);
+    xlo = min(xlo, TACC ? s0 / Pp : xcur);
+    xhi = max(xhi, xcur);
     if constexpr (!TACC)  // one tile: the rows of panels [pa, pa + Pp)
       gen_rows = (min(static_cast<int64_t>(pa + Pp) * R, static_cast<int64_t>(m)) -
                   static_cast<int64_t>(pa) * R) *
@@ -1226,7 +1231,7 @@ __global__ void __launch_bounds__(tile_warps(TACC) * 32, 1)
     if (blockIdx.y == 0)
       for (int k = threadIdx.x; k < kslots; k += blockDim.x)
         sflags[static_cast<int64_t>(c) * kslots + k] =
-            (x0 + k <= xseen && !tile_whole(x0 + k, c, tiles, C)) ? 1 : 0;
+            (xlo <= x0 + k && x0 + k <= xhi && !tile_whole(x0 + k, c, tiles, C)) ? 1 : 0;
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0)
