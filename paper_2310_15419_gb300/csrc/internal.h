@@ -86,8 +86,9 @@ struct TileArgs {
   uint32_t k0, k1, stream_id;
   int32_t dist;
   int32_t R;    // rows of A per panel (m1)
-  int32_t G;    // register sums: row groups (partial copies); tensor-memory
-                // sums: CTAs per column block, each a balanced share of units
+  int32_t G;    // row ranges of the panels: register sums, one CTA per (tile,
+                // range) writing a partial copy; tensor-memory sums, the phases
+                // one wave of CTAs walks in order
   int32_t cpw;  // columns per warp: 4, 16 or 64; 32 with tacc (n1 = warps * cpw)
   int32_t tacc;  // 1: accumulators in tensor memory (32 warps of cpw 32)
   // dist 3: S read from S_mem (d x m, column j at S_mem + j * ld_s; ld_s a
